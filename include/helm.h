@@ -1,0 +1,247 @@
+/*
+ * helm.h - C ABI of the GB300 shifted-Laplace Helmholtz solver and FWI gradient.
+ *
+ * The library solves the 2D constant-density damped Helmholtz equation of the
+ * paper (Kazemi, "Application of shifted-Laplace preconditioners for
+ * heterogeneous Helmholtz equation - part 2: Full waveform inversion"):
+ *
+ *     -Laplace(u) - omega^2 m^2 (1 - j alpha) u = f            (Eq. 2)
+ *     B u = f                                                  (Eq. 3)
+ *
+ * with m = 1/c the real slowness, alpha the damping of an absorbing layer, by a
+ * Krylov method (BiCGSTAB, or flexible GMRES) preconditioned with the
+ * shifted-Laplace operator M = -Laplace - (beta1 - j beta2) omega^2 m^2 that a
+ * geometric multigrid V-cycle inverts approximately ("Full waveform inversion
+ * in the space-frequency domain", the paragraph after Eq. 9). It also evaluates
+ * the misfit of Eq. 4 and its gradient (Eq. 7) by adjoint solves.
+ *
+ * Discretisation (the paper says only "finite difference"): standard 5-point
+ * Laplacian on a uniform grid, spacing h in x and z; homogeneous Dirichlet
+ * ghosts one node outside the padded grid; an npml-node damping layer on all
+ * four sides with alpha = alpha_max (d/npml)^2 at depth d nodes into the layer
+ * (max over the axes in corners); the slowness in the layer copies the nearest
+ * physical cell. A unit point source is f = 1/h^2 at its node.
+ *
+ * Conventions for every call
+ *  - Return value: a helm_status. Nothing throws across the ABI; nothing traps
+ *    or aborts on the device. helm_strerror() names a status.
+ *  - Layout: row-major [z][x], x fastest. Complex numbers are interleaved
+ *    (re, im) pairs: C99 double _Complex / torch.complex128 for "c128", float
+ *    pairs / torch.complex64 for "c64".
+ *  - Grids: Px x Pz physical nodes; the padded grid used for fields is
+ *    nx = Px + 2 npml by nz = Pz + 2 npml. Source and receiver indices are
+ *    physical node indices (0-based, 0 <= ix < Px, 0 <= iz < Pz).
+ *  - Ownership: the caller owns every buffer it passes; the library copies
+ *    what it needs. Handles are freed by their destroy call. A served result
+ *    stays owned by the library until helm_release().
+ *  - Host or device pointers: field arguments are host pointers unless
+ *    opts->device_ptrs is set, in which case they are device pointers on the
+ *    context's device, read and written in order on the context's stream.
+ *  - Threads: a helm_ctx and its models may be used by one host thread at a
+ *    time, except helm_submit/helm_poll/helm_release, which are thread-safe.
+ */
+#ifndef HELM_H
+#define HELM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct helm_ctx helm_ctx;
+typedef struct helm_model helm_model;
+
+typedef enum {
+    HELM_OK = 0,
+    HELM_PENDING = 1,          /* helm_poll: request not finished yet */
+    HELM_E_INVALID = -1,       /* bad argument (size, index, NaN, null) */
+    HELM_E_NOMEM = -2,         /* device allocation failed / admission refused */
+    HELM_E_NOT_CONVERGED = -3, /* tolerance not reached in max_it; best iterate returned */
+    HELM_E_CUDA = -4,          /* a CUDA call failed */
+    HELM_E_TIMEOUT = -5,       /* helm_poll: timeout_ms elapsed */
+    HELM_E_BUSY = -6           /* serving queue full */
+} helm_status;
+
+typedef enum {
+    HELM_PREC_MIXED = 0, /* complex64 stencil, V-cycle and Krylov; FP64 true residual + refinement */
+    HELM_PREC_FP64 = 1,  /* everything in complex128 (the plain FP64 baseline) */
+    HELM_PREC_FP32 = 2   /* complex64 only, one inner solve, no refinement */
+} helm_precision;
+
+typedef enum { HELM_KRYLOV_BICGSTAB = 0, HELM_KRYLOV_FGMRES = 1 } helm_krylov;
+
+typedef struct {
+    double tol;          /* stop at ||f - B u||_2 / ||f||_2 <= tol, residual formed in FP64 */
+    int max_it;          /* cap on preconditioned Krylov iterations per right-hand side */
+    int krylov;          /* helm_krylov */
+    int restart;         /* FGMRES restart length (<= 64) */
+    int precision;       /* helm_precision */
+    double beta1;        /* shift of M: -Laplace - (beta1 - j beta2) omega^2 m^2 */
+    double beta2;
+    double omega_jacobi; /* damped-Jacobi weight of the V-cycle smoother */
+    double inner_tol;    /* HELM_PREC_MIXED: relative reduction asked of each inner solve */
+    int max_outer;       /* HELM_PREC_MIXED: cap on refinement steps */
+    int check_every;     /* host convergence poll interval, in Krylov iterations */
+    int device_ptrs;     /* 1: f / u_out / gradient buffers are device pointers */
+    int use_graphs;      /* 1: replay the iteration body as a CUDA graph */
+} helm_solve_opts;
+
+typedef struct {
+    int iters;        /* Krylov iterations used */
+    int outer_its;    /* FP64 refinement steps */
+    int converged;    /* 1 if relres <= tol */
+    double relres;    /* final ||f - B u|| / ||f||, computed in FP64 */
+} helm_solve_stats;
+
+/* Fills *opts with the defaults: tol 1e-6, max_it 5000, BiCGSTAB, restart 30,
+ * mixed precision, beta = (1, 0.5), omega_jacobi 0.8, inner_tol 1e-4,
+ * max_outer 20, check_every 10, host pointers, graphs on. */
+void helm_default_opts(helm_solve_opts* opts);
+
+const char* helm_strerror(int status);
+/* Text of the last CUDA or validation error seen by the calling thread. */
+const char* helm_last_error(void);
+
+/* Number of CUDA kernels this library has launched in the process so far
+ * (graph replays counted per kernel node); a profiling aid with no counterpart
+ * in the paper. */
+uint64_t helm_launch_count(void);
+
+/* Creates a context on CUDA device `device`. `cuda_stream` (a cudaStream_t,
+ * nullable) is the stream every call of this context runs on; NULL makes the
+ * library create its own non-blocking stream. */
+int helm_ctx_create(int device, void* cuda_stream, helm_ctx** out);
+void helm_ctx_destroy(helm_ctx* ctx);
+
+/* Model setup (Eq. 2): copies the physical slowness m = 1/c [Pz][Px] (host,
+ * float64, all > 0) to the device, pads it into the npml-node damping layer by
+ * edge replication and builds the multigrid hierarchy (coarse slowness by
+ * injection). h > 0 is the grid spacing in metres; 0 <= alpha_max. */
+int helm_create_model(helm_ctx* ctx, int Px, int Pz, double h, const double* slowness,
+                      int npml, double alpha_max, helm_model** out);
+void helm_destroy_model(helm_model* model);
+
+/* Padded grid size and number of multigrid levels of a model. */
+int helm_model_info(const helm_model* model, int* nx, int* nz, int* nlevels);
+
+/* Forward modelling (Eq. 3): u = B(m, omega_k)^{-1} f_k for k < nrhs, all right-hand
+ * sides in one batched launch sequence. omega[k] is the angular frequency (rad/s).
+ * Right-hand sides: if f is NULL, a unit point source at physical node
+ * (src_ix[k], src_iz[k]); otherwise f is c128 [nrhs][nz][nx] (src_* ignored).
+ * u_out: c128 [nrhs][nz][nx] on the padded grid. opts NULL = defaults.
+ * stats (nullable): [nrhs]. Returns HELM_E_NOT_CONVERGED if any right-hand side
+ * missed tol (u_out then holds the best iterate). */
+int helm_solve(helm_model* model, int nrhs, const double* omega, const int* src_ix,
+               const int* src_iz, const void* f, void* u_out, const helm_solve_opts* opts,
+               helm_solve_stats* stats);
+
+/* Misfit and gradient (Eq. 4 and Eq. 7). For each of nfreq angular frequencies
+ * and nshot point sources: u = B^{-1} f, r = P u - d_obs (P samples the nrec
+ * receiver nodes), lambda = B^{-H} P^T r, and
+ *   J = sum |r|^2 + lambda_reg sum_phys m^2,
+ *   dJ/dm_i = sum 4 omega^2 m_i Re[(1 - j alpha_i) u_i conj(lambda_i)] + 2 lambda_reg m_i,
+ * the layer terms summed onto the physical cell each layer node copies.
+ * d_obs: c128 [nfreq][nshot][nrec]. J_out: one double. grad_out: float64 [Pz][Px].
+ * d_cal_out (nullable): c128 [nfreq][nshot][nrec], the modelled data P u.
+ * d_obs, grad_out and d_cal_out follow opts->device_ptrs. stats (nullable):
+ * [2 * nfreq * nshot], forward solves then adjoint solves. */
+int helm_adjoint_gradient(helm_model* model, int nfreq, const double* omega, int nshot,
+                          const int* src_ix, const int* src_iz, int nrec, const int* rec_ix,
+                          const int* rec_iz, const void* d_obs, double lambda_reg, double* J_out,
+                          double* grad_out, void* d_cal_out, const helm_solve_opts* opts,
+                          helm_solve_stats* stats);
+
+/* The two halves of helm_adjoint_gradient, for an autograd backward that runs
+ * the adjoint solves separately. helm_fwi_forward does the forward solves, the
+ * data residuals and J (same arguments as helm_adjoint_gradient; stats
+ * [nfreq * nshot]) and returns *state, which keeps the wavefields and residuals
+ * on the device. helm_fwi_backward runs the adjoint solves and writes the
+ * gradient (grad_out float64 [Pz][Px], following opts->device_ptrs; stats
+ * [nfreq * nshot]); it may be called more than once. helm_fwi_state_destroy
+ * frees the state; the model must outlive it. */
+typedef struct helm_fwi_state helm_fwi_state;
+int helm_fwi_forward(helm_model* model, int nfreq, const double* omega, int nshot, const int* src_ix,
+                     const int* src_iz, int nrec, const int* rec_ix, const int* rec_iz, const void* d_obs,
+                     double lambda_reg, double* J_out, void* d_cal_out, const helm_solve_opts* opts,
+                     helm_solve_stats* stats, helm_fwi_state** state);
+int helm_fwi_backward(helm_fwi_state* state, double* grad_out, const helm_solve_opts* opts,
+                      helm_solve_stats* stats);
+void helm_fwi_state_destroy(helm_fwi_state* state);
+
+/* Operator application y = B(m, omega_k) u_k (Eq. 3) for parity checks and
+ * bandwidth measurement. precision HELM_PREC_FP64: u, y c128; otherwise c64.
+ * [nrhs][nz][nx] each, following device_ptrs. */
+int helm_apply(helm_model* model, int nrhs, const double* omega, int precision, const void* u,
+               void* y, int device_ptrs);
+
+/* One application of the multigrid V-cycle that approximates M^{-1} r (the
+ * shifted-Laplace preconditioner) on complex64 [nrhs][nz][nx] vectors; for
+ * parity checks of the preconditioner against a CPU restatement. beta and
+ * omega_jacobi as in helm_solve_opts. */
+int helm_vcycle(helm_model* model, int nrhs, const double* omega, double beta1, double beta2,
+                double omega_jacobi, const void* r, void* z, int device_ptrs);
+
+/* Bandwidth measurement of one hot-path kernel (no counterpart in the paper;
+ * it feeds the roofline report). Launches `kernel` (helm_kernel_id) `reps`
+ * times on library-owned zero-filled vectors of nrhs right-hand sides of this
+ * model at angular frequency omega, after three warm-up launches, and returns
+ * the mean time per launch in ms (CUDA events on the context's stream) and the
+ * algorithmic bytes one launch must move (each operand once; the squared
+ * slowness shared by the batch counted once). */
+typedef enum {
+    HELM_KERNEL_APPLY = 0,    /* y = A u, complex64 */
+    HELM_KERNEL_RESTRICT = 1, /* fine-level pre-smooth + residual + full weighting, complex64 */
+    HELM_KERNEL_PROLONG = 2,  /* fine-level prolongation + post-smooth + A + dot, complex64 */
+    HELM_KERNEL_BICG_XR = 3,  /* BiCGSTAB x and r update with its two dots, complex64 */
+    HELM_KERNEL_RESID64 = 4,  /* FP64 true residual r = f - A u */
+    HELM_KERNEL_BICG_P = 5,   /* BiCGSTAB p update, complex64 */
+    HELM_KERNEL_APPLY64 = 6   /* y = A u, complex128 */
+} helm_kernel_id;
+int helm_time_kernel(helm_model* model, int kernel, int nrhs, double omega, int reps, double* ms_per_launch,
+                     double* bytes_per_launch);
+
+/* ---------------------------------------------------------------- serving
+ * Continuous batching: requests enter a host queue; a scheduler thread admits
+ * them while free device memory (minus a reserve) allows, groups requests of the
+ * same grid shape and precision into one batched slot, and runs slots
+ * concurrently on their own streams. Each result is the same as a lone
+ * helm_solve of that request, within the solve tolerance. */
+typedef struct {
+    int Px, Pz;
+    double h;
+    const double* slowness; /* host [Pz][Px], copied at submit */
+    int npml;
+    double alpha_max;
+    double omega;           /* angular frequency */
+    int src_ix, src_iz;     /* physical node of a unit point source */
+    helm_solve_opts opts;   /* device_ptrs must be 0 */
+} helm_request;
+
+typedef struct {
+    const void* u;          /* c128 [nz][nx] host buffer owned by the library until helm_release */
+    int nx, nz;
+    int status;             /* helm_status of the solve */
+    helm_solve_stats stats;
+    double latency_ms;      /* submit to completion */
+    double queue_ms;        /* submit to admission */
+    int batch_size;         /* requests in the slot this one ran in */
+} helm_result;
+
+/* Starts the scheduler (first call) and enqueues a request; *ticket names it. */
+int helm_submit(helm_ctx* ctx, const helm_request* req, uint64_t* ticket);
+/* Waits up to timeout_ms (0 = just look, < 0 = forever) for a request.
+ * HELM_OK fills *result; HELM_PENDING / HELM_E_TIMEOUT leave it untouched. */
+int helm_poll(helm_ctx* ctx, uint64_t ticket, int timeout_ms, helm_result* result);
+/* Frees a finished request's result. */
+int helm_release(helm_ctx* ctx, uint64_t ticket);
+/* Serving limits: max requests per slot, concurrent slots, device-memory reserve
+ * in bytes, and a simulated device-memory budget in bytes (0 = use the real
+ * free memory) for admission tests. */
+int helm_serve_config(helm_ctx* ctx, int max_batch, int max_slots, uint64_t reserve_bytes,
+                      uint64_t budget_bytes);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HELM_H */

@@ -1,0 +1,14 @@
+"""GB300-native shifted-Laplace Helmholtz solver and FWI gradient (arXiv 1712.08743).
+
+The compute path is the CUDA library ``_build/libhelm.so`` behind the C ABI of
+``include/helm.h``; this package is its Python binding (same names).
+"""
+from ._lib import (  # noqa: F401
+    HELM_E_BUSY, HELM_E_CUDA, HELM_E_INVALID, HELM_E_NOMEM, HELM_E_NOT_CONVERGED, HELM_E_TIMEOUT, HELM_OK,
+    HELM_PENDING, HELM_PREC_FP32, HELM_PREC_FP64, HELM_PREC_MIXED, HelmError, load,
+)
+from .api import (  # noqa: F401
+    Context, Model, helm_adjoint_gradient, helm_apply, helm_create_model, helm_ctx_create, helm_ctx_destroy,
+    helm_default_opts, helm_destroy_model, helm_fwi_backward, helm_fwi_forward, helm_poll, helm_release,
+    helm_serve_config, helm_solve, helm_submit, helm_vcycle,
+)

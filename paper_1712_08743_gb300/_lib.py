@@ -1,0 +1,163 @@
+"""ctypes view of the C ABI in ``include/helm.h`` (argument marshalling only).
+
+``load()`` opens the in-tree ``_build/libhelm.so`` and raises if it is missing:
+there is no fallback implementation.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+from . import build as _build
+
+HELM_OK = 0
+HELM_PENDING = 1
+HELM_E_INVALID = -1
+HELM_E_NOMEM = -2
+HELM_E_NOT_CONVERGED = -3
+HELM_E_CUDA = -4
+HELM_E_TIMEOUT = -5
+HELM_E_BUSY = -6
+
+HELM_PREC_MIXED = 0
+HELM_PREC_FP64 = 1
+HELM_PREC_FP32 = 2
+HELM_KERNEL_APPLY = 0
+HELM_KERNEL_RESTRICT = 1
+HELM_KERNEL_PROLONG = 2
+HELM_KERNEL_BICG_XR = 3
+HELM_KERNEL_RESID64 = 4
+HELM_KERNEL_BICG_P = 5
+HELM_KERNEL_APPLY64 = 6
+HELM_KRYLOV_BICGSTAB = 0
+HELM_KRYLOV_FGMRES = 1
+
+
+class helm_solve_opts(C.Structure):
+    _fields_ = [
+        ("tol", C.c_double),
+        ("max_it", C.c_int),
+        ("krylov", C.c_int),
+        ("restart", C.c_int),
+        ("precision", C.c_int),
+        ("beta1", C.c_double),
+        ("beta2", C.c_double),
+        ("omega_jacobi", C.c_double),
+        ("inner_tol", C.c_double),
+        ("max_outer", C.c_int),
+        ("check_every", C.c_int),
+        ("device_ptrs", C.c_int),
+        ("use_graphs", C.c_int),
+    ]
+
+
+class helm_solve_stats(C.Structure):
+    _fields_ = [
+        ("iters", C.c_int),
+        ("outer_its", C.c_int),
+        ("converged", C.c_int),
+        ("relres", C.c_double),
+    ]
+
+
+class helm_request(C.Structure):
+    _fields_ = [
+        ("Px", C.c_int),
+        ("Pz", C.c_int),
+        ("h", C.c_double),
+        ("slowness", C.POINTER(C.c_double)),
+        ("npml", C.c_int),
+        ("alpha_max", C.c_double),
+        ("omega", C.c_double),
+        ("src_ix", C.c_int),
+        ("src_iz", C.c_int),
+        ("opts", helm_solve_opts),
+    ]
+
+
+class helm_result(C.Structure):
+    _fields_ = [
+        ("u", C.c_void_p),
+        ("nx", C.c_int),
+        ("nz", C.c_int),
+        ("status", C.c_int),
+        ("stats", helm_solve_stats),
+        ("latency_ms", C.c_double),
+        ("queue_ms", C.c_double),
+        ("batch_size", C.c_int),
+    ]
+
+
+_P = C.c_void_p
+_I = C.c_int
+_D = C.c_double
+_pI = C.POINTER(C.c_int)
+_pD = C.POINTER(C.c_double)
+_pOpts = C.POINTER(helm_solve_opts)
+_pStats = C.POINTER(helm_solve_stats)
+
+# name -> (restype, argtypes); every function declared in include/helm.h
+SIGNATURES = {
+    "helm_default_opts": (None, [_pOpts]),
+    "helm_strerror": (C.c_char_p, [_I]),
+    "helm_last_error": (C.c_char_p, []),
+    "helm_launch_count": (C.c_uint64, []),
+    "helm_ctx_create": (_I, [_I, _P, C.POINTER(_P)]),
+    "helm_ctx_destroy": (None, [_P]),
+    "helm_create_model": (_I, [_P, _I, _I, _D, _pD, _I, _D, C.POINTER(_P)]),
+    "helm_destroy_model": (None, [_P]),
+    "helm_model_info": (_I, [_P, _pI, _pI, _pI]),
+    "helm_solve": (_I, [_P, _I, _pD, _pI, _pI, _P, _P, _pOpts, _pStats]),
+    "helm_adjoint_gradient": (_I, [_P, _I, _pD, _I, _pI, _pI, _I, _pI, _pI, _P, _D, _pD, _P, _P, _pOpts, _pStats]),
+    "helm_fwi_forward": (_I, [_P, _I, _pD, _I, _pI, _pI, _I, _pI, _pI, _P, _D, _pD, _P, _pOpts, _pStats, C.POINTER(_P)]),
+    "helm_fwi_backward": (_I, [_P, _P, _pOpts, _pStats]),
+    "helm_fwi_state_destroy": (None, [_P]),
+    "helm_apply": (_I, [_P, _I, _pD, _I, _P, _P, _I]),
+    "helm_vcycle": (_I, [_P, _I, _pD, _D, _D, _D, _P, _P, _I]),
+    "helm_time_kernel": (_I, [_P, _I, _I, _D, _I, _pD, _pD]),
+    "helm_submit": (_I, [_P, C.POINTER(helm_request), C.POINTER(C.c_uint64)]),
+    "helm_poll": (_I, [_P, C.c_uint64, _I, C.POINTER(helm_result)]),
+    "helm_release": (_I, [_P, C.c_uint64]),
+    "helm_serve_config": (_I, [_P, _I, _I, C.c_uint64, C.c_uint64]),
+}
+
+_LIB = None
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = False):
+    """Open libhelm.so (optionally building it first). Raises if it is absent."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    path = lib_path()
+    if not os.path.exists(path) and build_if_missing:
+        _build.build()
+    if not os.path.exists(path):
+        raise RuntimeError(f"libhelm.so is not built ({path}); run paper_1712_08743_gb300.build.build() "
+                           "or __graft_entry__.build() first")
+    lib = C.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _LIB = lib
+    return lib
+
+
+class HelmError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        lib = load()
+        msg = lib.helm_strerror(status).decode()
+        detail = lib.helm_last_error().decode()
+        super().__init__(f"{where}: {msg} ({status}){': ' + detail if detail else ''}")
+        self.status = status
+
+
+def check(status: int, where: str, allow=(HELM_OK,)) -> int:
+    if status not in allow:
+        raise HelmError(status, where)
+    return status

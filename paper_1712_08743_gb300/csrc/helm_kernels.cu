@@ -1,0 +1,878 @@
+// helm_kernels.cu - CUDA kernels (sm_103a) of the shifted-Laplace Helmholtz path.
+//
+// Operators, in the grid-scaled form A = h^2 B that every kernel uses:
+//   A u = 4u - u_{i+-1,k} - u_{i,k+-1} - h^2 w^2 m^2 (1 - j alpha) u          (Eq. 2/3)
+//   M u = 4u - u_{i+-1,k} - u_{i,k+-1} - h_l^2 w^2 m^2 (beta1 - j beta2) u    (shifted Laplacian)
+// Zero Dirichlet ghosts lie one node outside each grid. Vectors are batched
+// [nrhs][nz][nx] interleaved complex; right-hand side b uses angular frequency
+// omega_b (w2[b] = omega_b^2). The multigrid level l+1 has floor(n_l / 2)
+// nodes per axis; coarse node I sits on fine node 2I + 1.
+#include "helm_internal.h"
+
+namespace helm {
+
+namespace {
+
+template <typename T>
+__device__ __forceinline__ const T* m2ptr(const LevelDev& L) { return static_cast<const T*>(L.m2); }
+
+__device__ __forceinline__ bool rhs_active(const RhsState* st, int b) { return st == nullptr || st[b].active; }
+
+// Grid-stride extent for 1D vector kernels.
+inline int grid1d(size_t n) {
+    size_t g = (n + 1023) / 1024;
+    if (g < 1) g = 1;
+    if (g > 2048) g = 2048;
+    return (int)g;
+}
+
+}  // namespace
+
+// ===================================================================== model
+__global__ void k_pad_model(const double* __restrict__ m_phys, int Px, int Pz, int npml,
+                            double* __restrict__ m_pad, float* __restrict__ m2f, double* __restrict__ m2d) {
+    const int nx = Px + 2 * npml, nz = Pz + 2 * npml;
+    const size_t n = (size_t)nx * nz;
+    const int k = blockIdx.y;   // model index
+    m_phys += (size_t)k * Px * Pz;
+    m_pad += n * k;
+    m2f += n * k;
+    m2d += n * k;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        int ix = (int)(i % nx), iz = (int)(i / nx);
+        int px = min(max(ix - npml, 0), Px - 1);
+        int pz = min(max(iz - npml, 0), Pz - 1);
+        double m = m_phys[(size_t)pz * Px + px];
+        m_pad[i] = m;
+        m2d[i] = m * m;
+        m2f[i] = (float)(m * m);
+    }
+}
+
+void launch_pad_model(const double* m_phys, int Px, int Pz, int npml, int nmodels, double* m_pad, float* m2f,
+                      double* m2d, cudaStream_t s) {
+    size_t n = (size_t)(Px + 2 * npml) * (Pz + 2 * npml);
+    k_pad_model<<<dim3(grid1d(n), nmodels), 256, 0, s>>>(m_phys, Px, Pz, npml, m_pad, m2f, m2d);
+}
+
+__global__ void k_inject(const double* __restrict__ fine_d, int nxf, int nzf, double* __restrict__ coarse_d,
+                         float* __restrict__ coarse_f, int nxc, int nzc) {
+    const size_t n = (size_t)nxc * nzc;
+    const int k = blockIdx.y;
+    fine_d += (size_t)k * nxf * nzf;
+    coarse_d += n * k;
+    coarse_f += n * k;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        int I = (int)(i % nxc), K = (int)(i / nxc);
+        double v = fine_d[(size_t)(2 * K + 1) * nxf + (2 * I + 1)];
+        coarse_d[i] = v;
+        coarse_f[i] = (float)v;
+    }
+}
+
+// sum of squares of a real array (one block; model setup only)
+__global__ void k_sumsq(const double* __restrict__ a, size_t count, double* out) {
+    __shared__ double sh[32];
+    double acc[1] = {0.0};
+    for (size_t i = threadIdx.x; i < count; i += blockDim.x) acc[0] += a[i] * a[i];
+    block_sum<1>(acc, sh);
+    if (threadIdx.x == 0) *out = acc[0];
+}
+void launch_sumsq(const double* a, size_t count, double* out, cudaStream_t s) { k_sumsq<<<1, 1024, 0, s>>>(a, count, out); }
+
+void launch_inject(const Level& fine, const Level& coarse, int nmodels, cudaStream_t s) {
+    k_inject<<<dim3(grid1d(coarse.n()), nmodels), 256, 0, s>>>(fine.m2d, fine.nx, fine.nz, coarse.m2d, coarse.m2f,
+                                                               coarse.nx, coarse.nz);
+}
+
+// ============================================================ stencil apply
+// y = scale * A u on the fine grid (with the damping layer).
+template <typename T>
+__global__ void __launch_bounds__(256) k_apply(LevelDev L, int npml, double amax, const double* __restrict__ w2,
+                                               const T* __restrict__ u, T* __restrict__ y, T scale) {
+    const int b = blockIdx.z;
+    const int ix = blockIdx.x * 32 + threadIdx.x, iz = blockIdx.y * 8 + threadIdx.y;
+    if (ix >= L.nx || iz >= L.nz) return;
+    const size_t n = (size_t)L.nx * L.nz;
+    const T* ub = u + 2 * n * b;
+    const size_t i = (size_t)iz * L.nx + ix;
+    const T hw = (T)(L.h2 * w2[b]);
+    const T s = hw * (m2ptr<T>(L) + (size_t)b * L.mstride)[i];
+    const T a = (T)layer_alpha(ix, iz, L.nx, L.nz, npml, amax);
+    cx<T> c = ldc(ub, i);
+    cx<T> acc((T(4) - s) * c.re - s * a * c.im, (T(4) - s) * c.im + s * a * c.re);  // (4 - s(1 - j a)) u
+    if (ix > 0) acc = acc - ldc(ub, i - 1);
+    if (ix + 1 < L.nx) acc = acc - ldc(ub, i + 1);
+    if (iz > 0) acc = acc - ldc(ub, i - L.nx);
+    if (iz + 1 < L.nz) acc = acc - ldc(ub, i + L.nx);
+    stc(y + 2 * n * b, i, scale * acc);
+}
+
+template <typename T>
+void launch_apply(const LevelDev& L0, int npml, double amax, const double* w2, const T* u, T* y, T scale,
+                  int nrhs, cudaStream_t s) {
+    dim3 blk(32, 8), grd((L0.nx + 31) / 32, (L0.nz + 7) / 8, nrhs);
+    k_apply<T><<<grd, blk, 0, s>>>(L0, npml, amax, w2, u, y, scale);
+}
+template void launch_apply<float>(const LevelDev&, int, double, const double*, const float*, float*, float, int, cudaStream_t);
+template void launch_apply<double>(const LevelDev&, int, double, const double*, const double*, double*, double, int, cudaStream_t);
+
+// ======================================================= FP64 outer residual
+// r = f - A u in FP64; writes the inner right-hand side rin = r in precision TI
+// and decides, per right-hand side, whether refinement continues.
+template <typename TI>
+__global__ void __launch_bounds__(256) k_resid64(LevelDev L, int npml, double amax, const double* __restrict__ w2,
+                                                 const double* __restrict__ f, const double* __restrict__ u,
+                                                 TI* __restrict__ rin, double* partials, int pstride, RhsState* st,
+                                                 double tol, double inner_floor, int first) {
+    __shared__ double sh[64];
+    const int b = blockIdx.z;
+    if (!st[b].outer_active) return;
+    const int tid = threadIdx.y * 32 + threadIdx.x;
+    const int ix = blockIdx.x * 32 + threadIdx.x, iz = blockIdx.y * 8 + threadIdx.y;
+    const size_t n = (size_t)L.nx * L.nz;
+    double v[2] = {0.0, 0.0};
+    if (ix < L.nx && iz < L.nz) {
+        const double* ub = u + 2 * n * b;
+        const size_t i = (size_t)iz * L.nx + ix;
+        const double s = L.h2 * w2[b] * (static_cast<const double*>(L.m2) + (size_t)b * L.mstride)[i];
+        const double a = layer_alpha(ix, iz, L.nx, L.nz, npml, amax);
+        cx<double> c = ldc(ub, i);
+        cx<double> acc((4.0 - s) * c.re - s * a * c.im, (4.0 - s) * c.im + s * a * c.re);
+        if (ix > 0) acc = acc - ldc(ub, i - 1);
+        if (ix + 1 < L.nx) acc = acc - ldc(ub, i + 1);
+        if (iz > 0) acc = acc - ldc(ub, i - L.nx);
+        if (iz + 1 < L.nz) acc = acc - ldc(ub, i + L.nx);
+        cx<double> fv = ldc(f + 2 * n * b, i);
+        cx<double> r = fv - acc;
+        v[0] = r.re * r.re + r.im * r.im;
+        v[1] = fv.re * fv.re + fv.im * fv.im;
+        reinterpret_cast<typename C2<TI>::type*>(rin)[n * b + i] = {(TI)r.re, (TI)r.im};
+    }
+    (void)tid;
+    const int nblk = gridDim.x * gridDim.y, blk = blockIdx.y * gridDim.x + blockIdx.x;
+    if (last_block_reduce<2>(v, sh, partials + (size_t)b * pstride, nblk, blk, &st[b].counter[0])) {
+        if (threadIdx.x == 0 && threadIdx.y == 0) {
+            RhsState& S = st[b];
+            if (first) S.fnorm2 = v[1];
+            double rel = S.fnorm2 > 0.0 ? sqrt(v[0] / S.fnorm2) : 0.0;
+            S.relres = rel;
+            int go = (rel > tol) && (S.iters < S.max_it);
+            S.outer_active = go;
+            S.active = go;
+            double t = rel > 0.0 ? 0.9 * tol / rel : 1.0;
+            S.tol_rel = t > inner_floor ? t : inner_floor;
+        }
+    }
+}
+
+template <typename TI>
+void launch_resid64(const LevelDev& L0, int npml, double amax, const double* w2, const double* f, const double* u,
+                    TI* rin, double* partials, int pstride, RhsState* st, double tol, double inner_floor, int first,
+                    int nrhs, cudaStream_t s) {
+    dim3 blk(32, 8), grd((L0.nx + 31) / 32, (L0.nz + 7) / 8, nrhs);
+    k_resid64<TI><<<grd, blk, 0, s>>>(L0, npml, amax, w2, f, u, rin, partials, pstride, st, tol, inner_floor, first);
+}
+template void launch_resid64<float>(const LevelDev&, int, double, const double*, const double*, const double*, float*, double*, int, RhsState*, double, double, int, int, cudaStream_t);
+template void launch_resid64<double>(const LevelDev&, int, double, const double*, const double*, const double*, double*, double*, int, RhsState*, double, double, int, int, cudaStream_t);
+
+template <typename TI>
+__global__ void k_refine(const TI* __restrict__ x, double* __restrict__ u, const RhsState* st, size_t n) {
+    const int b = blockIdx.z;
+    if (!st[b].outer_active) return;
+    const TI* xb = x + 2 * n * b;
+    double* ub = u + 2 * n * b;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        cx<TI> d = ldc(xb, i);
+        cx<double> c = ldcc(ub, i);
+        stc(ub, i, cx<double>(c.re + (double)d.re, c.im + (double)d.im));
+    }
+}
+
+template <typename TI>
+void launch_refine(const TI* x, double* u, const RhsState* st, size_t n, int nrhs, cudaStream_t s) {
+    k_refine<TI><<<dim3(grid1d(n), 1, nrhs), 256, 0, s>>>(x, u, st, n);
+}
+template void launch_refine<float>(const float*, double*, const RhsState*, size_t, int, cudaStream_t);
+template void launch_refine<double>(const double*, double*, const RhsState*, size_t, int, cudaStream_t);
+
+// ============================================================== BiCGSTAB
+// Right-preconditioned BiCGSTAB, complex inner product <a, b> = sum conj(a) b.
+template <typename T>
+__global__ void __launch_bounds__(256) k_bicg_init(const T* __restrict__ bv, T* x, T* r, T* rh, T* p, T* v,
+                                                   double* partials, int pstride, RhsState* st, int* nactive,
+                                                   size_t n) {
+    __shared__ double sh[32];
+    const int b = blockIdx.z;
+    if (!st[b].outer_active) return;
+    const size_t off = n * b;
+    double acc[1] = {0.0};
+    const cx<T> z(0, 0);
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        cx<T> c = ldc(bv, off + i);
+        stc(x, off + i, z);
+        stc(r, off + i, c);
+        stc(rh, off + i, c);
+        stc(p, off + i, z);
+        stc(v, off + i, z);
+        acc[0] += (double)c.re * c.re + (double)c.im * c.im;
+    }
+    if (last_block_reduce<1>(acc, sh, partials + (size_t)b * pstride, gridDim.x, blockIdx.x, &st[b].counter[1])) {
+        if (threadIdx.x == 0) {
+            RhsState& S = st[b];
+            S.bnorm2 = acc[0];
+            S.rnorm2 = acc[0];
+            S.rho[0] = acc[0]; S.rho[1] = 0.0;
+            S.alpha[0] = 1.0; S.alpha[1] = 0.0;
+            S.omega[0] = 1.0; S.omega[1] = 0.0;
+            S.beta[0] = 0.0; S.beta[1] = 0.0;
+            S.flag = FLAG_RUNNING;
+            S.active = acc[0] > 0.0;
+            if (S.active) atomicAdd(nactive, 1);
+        }
+    }
+}
+
+template <typename T>
+void launch_bicg_init(const T* b, T* x, T* r, T* rh, T* p, T* v, double* partials, int pstride, RhsState* st,
+                      int* nactive, size_t n, int nrhs, cudaStream_t s) {
+    k_bicg_init<T><<<dim3(grid1d(n), 1, nrhs), 256, 0, s>>>(b, x, r, rh, p, v, partials, pstride, st, nactive, n);
+}
+
+template <typename T>
+__global__ void k_bicg_p(const T* __restrict__ r, T* __restrict__ p, const T* __restrict__ v, const RhsState* st,
+                         size_t n) {
+    const int b = blockIdx.z;
+    if (!st[b].active) return;
+    const cx<T> beta((T)st[b].beta[0], (T)st[b].beta[1]);
+    const cx<T> om((T)st[b].omega[0], (T)st[b].omega[1]);
+    const size_t off = n * b;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        cx<T> pv = ldcc(p, off + i);
+        stc(p, off + i, ldc(r, off + i) + beta * (pv - om * ldc(v, off + i)));
+    }
+}
+
+template <typename T>
+void launch_bicg_p(const T* r, T* p, const T* v, const RhsState* st, size_t n, int nrhs, cudaStream_t s) {
+    k_bicg_p<T><<<dim3(grid1d(n), 1, nrhs), 256, 0, s>>>(r, p, v, st, n);
+}
+
+template <typename T>
+__global__ void k_bicg_s(const T* __restrict__ r, const T* __restrict__ v, T* __restrict__ sv, const RhsState* st,
+                         size_t n) {
+    const int b = blockIdx.z;
+    if (!st[b].active) return;
+    const cx<T> al((T)st[b].alpha[0], (T)st[b].alpha[1]);
+    const size_t off = n * b;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        stc(sv, off + i, ldc(r, off + i) - al * ldc(v, off + i));
+}
+
+template <typename T>
+void launch_bicg_s(const T* r, const T* v, T* sv, const RhsState* st, size_t n, int nrhs, cudaStream_t s) {
+    k_bicg_s<T><<<dim3(grid1d(n), 1, nrhs), 256, 0, s>>>(r, v, sv, st, n);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_bicg_xr(T* x, const T* __restrict__ ph, const T* __restrict__ shv,
+                                                 const T* __restrict__ sv, const T* __restrict__ t,
+                                                 const T* __restrict__ rh, T* r, double* partials, int pstride,
+                                                 RhsState* st, int* nactive, size_t n) {
+    __shared__ double sh[96];
+    const int b = blockIdx.z;
+    if (!st[b].active) return;
+    const cx<T> al((T)st[b].alpha[0], (T)st[b].alpha[1]);
+    const cx<T> om((T)st[b].omega[0], (T)st[b].omega[1]);
+    const size_t off = n * b;
+    T a0 = 0, a1 = 0, a2 = 0;   // <rh, r> (re, im), <r, r>
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        cx<T> xv = ldcc(x, off + i);
+        stc(x, off + i, xv + al * ldc(ph, off + i) + om * ldc(shv, off + i));
+        cx<T> rn = ldc(sv, off + i) - om * ldc(t, off + i);
+        stc(r, off + i, rn);
+        cx<T> q = ldc(rh, off + i);
+        a0 += q.re * rn.re + q.im * rn.im;
+        a1 += q.re * rn.im - q.im * rn.re;
+        a2 += rn.re * rn.re + rn.im * rn.im;
+    }
+    double acc[3] = {(double)a0, (double)a1, (double)a2};
+    if (last_block_reduce<3>(acc, sh, partials + (size_t)b * pstride, gridDim.x, blockIdx.x, &st[b].counter[2])) {
+        if (threadIdx.x == 0) {
+            RhsState& S = st[b];
+            S.iters += 1;
+            S.rnorm2 = acc[2];
+            const double tl = S.tol_rel;
+            int done = 0;
+            if (acc[2] <= tl * tl * S.bnorm2) { done = 1; S.flag = FLAG_CONVERGED; }
+            else if (S.iters >= S.max_it) { done = 1; S.flag = FLAG_MAXIT; }
+            else {
+                // beta = (rho_new / rho) * (alpha / omega)
+                double rr = S.rho[0], ri = S.rho[1];
+                double d1 = rr * rr + ri * ri;
+                double orr = S.omega[0], oi = S.omega[1];
+                double d2 = orr * orr + oi * oi;
+                if (d1 == 0.0 || d2 == 0.0 || !(acc[0] * acc[0] + acc[1] * acc[1] > 0.0)) {
+                    done = 1; S.flag = FLAG_BREAKDOWN;
+                } else {
+                    double qr = (acc[0] * rr + acc[1] * ri) / d1, qi = (acc[1] * rr - acc[0] * ri) / d1;
+                    double wr = (S.alpha[0] * orr + S.alpha[1] * oi) / d2, wi = (S.alpha[1] * orr - S.alpha[0] * oi) / d2;
+                    S.beta[0] = qr * wr - qi * wi;
+                    S.beta[1] = qr * wi + qi * wr;
+                    S.rho[0] = acc[0];
+                    S.rho[1] = acc[1];
+                }
+            }
+            if (done) { S.active = 0; atomicSub(nactive, 1); }
+        }
+    }
+}
+
+template <typename T>
+void launch_bicg_xr(T* x, const T* ph, const T* shv, const T* sv, const T* t, const T* rh, T* r, double* partials,
+                    int pstride, RhsState* st, int* nactive, size_t n, int nrhs, cudaStream_t s) {
+    k_bicg_xr<T><<<dim3(grid1d(n), 1, nrhs), 256, 0, s>>>(x, ph, shv, sv, t, rh, r, partials, pstride, st, nactive, n);
+}
+
+// ======================================================== V-cycle: restrict
+// From a level-l right-hand side f (zero initial guess): one damped-Jacobi
+// sweep u1 = wj D^-1 f, residual r = f - M u1, full weighting, times 4 for the
+// coarse grid-scaled system: fc = (1/4) [1 2 1; 2 4 2; 1 2 1] * r.
+constexpr int RCX = 32, RCZ = 8;                    // coarse tile per block
+constexpr int RFW = 2 * RCX + 3, RFH = 2 * RCZ + 3; // fine region (u1) per block
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_restrict(LevelDev Lf, LevelDev Lc, const double* __restrict__ w2, T b1, T b2,
+                                                  T wj, const T* __restrict__ f, T* __restrict__ fc,
+                                                  const RhsState* st) {
+    __shared__ cx<T> F[RFH][RFW];
+    __shared__ cx<T> U[RFH][RFW];
+    const int b = blockIdx.z;
+    if (!rhs_active(st, b)) return;
+    const int I0 = blockIdx.x * RCX, K0 = blockIdx.y * RCZ;
+    const int gx0 = 2 * I0 - 1, gz0 = 2 * K0 - 1;
+    const T hw = (T)(Lf.h2 * w2[b]);
+    const T* m2 = m2ptr<T>(Lf) + (size_t)b * Lf.mstride;
+    const size_t nf = (size_t)Lf.nx * Lf.nz;
+    const T* fb = f + 2 * nf * b;
+    for (int idx = threadIdx.x; idx < RFW * RFH; idx += blockDim.x) {
+        const int lz = idx / RFW, lx = idx - lz * RFW;
+        const int gx = gx0 + lx, gz = gz0 + lz;
+        cx<T> fv(0, 0), uv(0, 0);
+        if (gx >= 0 && gx < Lf.nx && gz >= 0 && gz < Lf.nz) {
+            const size_t i = (size_t)gz * Lf.nx + gx;
+            fv = ldc(fb, i);
+            const T s = hw * __ldg(m2 + i);
+            uv = wj * cdiv(fv, cx<T>(T(4) - s * b1, s * b2));
+        }
+        F[lz][lx] = fv;
+        U[lz][lx] = uv;
+    }
+    __syncthreads();
+    constexpr int W2 = RFW - 2, H2 = RFH - 2;
+    for (int idx = threadIdx.x; idx < W2 * H2; idx += blockDim.x) {
+        const int lz = 1 + idx / W2, lx = 1 + idx % W2;
+        const int gx = gx0 + lx, gz = gz0 + lz;
+        cx<T> r(0, 0);
+        if (gx < Lf.nx && gz < Lf.nz) {   // gx, gz >= 0 here
+            const size_t i = (size_t)gz * Lf.nx + gx;
+            const T s = hw * __ldg(m2 + i);
+            const cx<T> c = U[lz][lx];
+            cx<T> mu((T(4) - s * b1) * c.re - s * b2 * c.im, (T(4) - s * b1) * c.im + s * b2 * c.re);
+            mu = mu - U[lz][lx - 1] - U[lz][lx + 1] - U[lz - 1][lx] - U[lz + 1][lx];
+            r = F[lz][lx] - mu;
+        }
+        F[lz][lx] = r;   // each element read and written by this thread only
+    }
+    __syncthreads();
+    const int cxl = threadIdx.x % RCX, czl = threadIdx.x / RCX;
+    const int I = I0 + cxl, K = K0 + czl;
+    if (I < Lc.nx && K < Lc.nz) {
+        const int lx = 2 * cxl + 2, lz = 2 * czl + 2;
+        cx<T> a = T(4) * F[lz][lx];
+        a = a + T(2) * (F[lz][lx - 1] + F[lz][lx + 1] + F[lz - 1][lx] + F[lz + 1][lx]);
+        a = a + F[lz - 1][lx - 1] + F[lz - 1][lx + 1] + F[lz + 1][lx - 1] + F[lz + 1][lx + 1];
+        const size_t nc = (size_t)Lc.nx * Lc.nz;
+        stc(fc + 2 * nc * b, (size_t)K * Lc.nx + I, T(0.25) * a);
+    }
+}
+
+template <typename T>
+void launch_restrict(const LevelDev& Lf, const LevelDev& Lc, const double* w2, double b1, double b2, double wj,
+                     const T* f, T* fc, const RhsState* st, int nrhs, cudaStream_t s) {
+    dim3 grd((Lc.nx + RCX - 1) / RCX, (Lc.nz + RCZ - 1) / RCZ, nrhs);
+    k_restrict<T><<<grd, RCX * RCZ, 0, s>>>(Lf, Lc, w2, (T)b1, (T)b2, (T)wj, f, fc, st);
+}
+
+// ========================================================= V-cycle: prolong
+// On a level-l tile: u1 = wj D^-1 f, u2 = u1 + P e (bilinear), one post-sweep
+// u3 = u2 + wj D^-1 (f - M u2). Modes 1 and 2 (finest level inside BiCGSTAB)
+// also apply A to u3 and reduce the dot products the next scalar needs.
+// fine tile per block: 64 x 16 in FP32, 32 x 16 in FP64 (static shared memory < 48 KB)
+template <typename T> struct PTile { static constexpr int X = sizeof(T) == 4 ? 64 : 32, Z = 16; };
+
+template <typename T, int MODE>
+__global__ void __launch_bounds__(256) k_prolong(LevelDev Lf, LevelDev Lc, int npml, double amax,
+                                                 const double* __restrict__ w2, T b1, T b2, T wj,
+                                                 const T* __restrict__ f, const T* __restrict__ ec,
+                                                 T* __restrict__ out, T* __restrict__ y, const T* __restrict__ aux,
+                                                 double* partials, int pstride, RhsState* st) {
+    constexpr int H = (MODE == 0) ? 1 : 2;
+    constexpr int PFX = PTile<T>::X, PFZ = PTile<T>::Z;
+    constexpr int RW = PFX + 2 * H, RH = PFZ + 2 * H;          // f, u2 region
+    constexpr int EW = PFX / 2 + H + 1, EH = PFZ / 2 + H + 1;  // coarse region
+    constexpr int SW = PFX + 2, SH = PFZ + 2;                  // u3 region (modes 1, 2)
+    __shared__ cx<T> F[RH][RW];
+    __shared__ cx<T> U2[RH][RW];
+    __shared__ cx<T> E[EH][EW];
+    __shared__ cx<T> U3[(MODE == 0) ? 1 : SH][(MODE == 0) ? 1 : SW];
+    __shared__ double shred[96];
+
+    const int b = blockIdx.z;
+    if (!rhs_active(st, b)) return;
+    const int x0 = blockIdx.x * PFX, z0 = blockIdx.y * PFZ;
+    const int gx0 = x0 - H, gz0 = z0 - H;
+    const int cx0 = x0 / 2 - H, cz0 = z0 / 2 - H;
+    const T hw = (T)(Lf.h2 * w2[b]);
+    const T* m2 = m2ptr<T>(Lf) + (size_t)b * Lf.mstride;
+    const size_t nf = (size_t)Lf.nx * Lf.nz, nc = (size_t)Lc.nx * Lc.nz;
+    const T* fb = f + 2 * nf * b;
+    const T* eb = ec + 2 * nc * b;
+
+    for (int idx = threadIdx.x; idx < EW * EH; idx += blockDim.x) {
+        const int lz = idx / EW, lx = idx - lz * EW;
+        const int I = cx0 + lx, K = cz0 + lz;
+        cx<T> e(0, 0);
+        if (I >= 0 && I < Lc.nx && K >= 0 && K < Lc.nz) e = ldc(eb, (size_t)K * Lc.nx + I);
+        E[lz][lx] = e;
+    }
+    for (int idx = threadIdx.x; idx < RW * RH; idx += blockDim.x) {
+        const int lz = idx / RW, lx = idx - lz * RW;
+        const int gx = gx0 + lx, gz = gz0 + lz;
+        cx<T> fv(0, 0);
+        if (gx >= 0 && gx < Lf.nx && gz >= 0 && gz < Lf.nz) fv = ldc(fb, (size_t)gz * Lf.nx + gx);
+        F[lz][lx] = fv;
+    }
+    __syncthreads();
+    // u2 = wj D^-1 f + P e on the region (zero outside the grid)
+    for (int idx = threadIdx.x; idx < RW * RH; idx += blockDim.x) {
+        const int lz = idx / RW, lx = idx - lz * RW;
+        const int gx = gx0 + lx, gz = gz0 + lz;
+        cx<T> u(0, 0);
+        if (gx >= 0 && gx < Lf.nx && gz >= 0 && gz < Lf.nz) {
+            const T s = hw * __ldg(m2 + (size_t)gz * Lf.nx + gx);
+            u = wj * cdiv(F[lz][lx], cx<T>(T(4) - s * b1, s * b2));
+            // bilinear prolongation: odd fine index -> one coarse node, even -> two halves
+            int ia, ib, ka, kb;
+            T wa, wb, va, vb;
+            if (gx & 1) { ia = (gx - 1) / 2; ib = ia; wa = T(1); wb = T(0); }
+            else { ia = gx / 2 - 1; ib = gx / 2; wa = T(0.5); wb = T(0.5); }
+            if (gz & 1) { ka = (gz - 1) / 2; kb = ka; va = T(1); vb = T(0); }
+            else { ka = gz / 2 - 1; kb = gz / 2; va = T(0.5); vb = T(0.5); }
+            ia -= cx0; ib -= cx0; ka -= cz0; kb -= cz0;
+            cx<T> pe = (va * wa) * E[ka][ia] + (va * wb) * E[ka][ib] + (vb * wa) * E[kb][ia] + (vb * wb) * E[kb][ib];
+            u = u + pe;
+        }
+        U2[lz][lx] = u;
+    }
+    __syncthreads();
+
+    if (MODE == 0) {
+        // post-smooth on the tile, write the correction
+        T* ob = out + 2 * nf * b;
+        for (int idx = threadIdx.x; idx < PFX * PFZ; idx += blockDim.x) {
+            const int tz = idx / PFX, tx = idx - tz * PFX;
+            const int gx = x0 + tx, gz = z0 + tz;
+            if (gx >= Lf.nx || gz >= Lf.nz) continue;
+            const int lx = tx + H, lz = tz + H;
+            const size_t i = (size_t)gz * Lf.nx + gx;
+            const T s = hw * __ldg(m2 + i);
+            const cx<T> D(T(4) - s * b1, s * b2);
+            const cx<T> c = U2[lz][lx];
+            cx<T> mu((T(4) - s * b1) * c.re - s * b2 * c.im, (T(4) - s * b1) * c.im + s * b2 * c.re);
+            mu = mu - U2[lz][lx - 1] - U2[lz][lx + 1] - U2[lz - 1][lx] - U2[lz + 1][lx];
+            stc(ob, i, c + wj * cdiv(F[lz][lx] - mu, D));
+        }
+        return;
+    } else {
+        // post-smooth on tile + 1 halo into U3
+        for (int idx = threadIdx.x; idx < SW * SH; idx += blockDim.x) {
+            const int sz = idx / SW, sx = idx - sz * SW;
+            const int gx = x0 - 1 + sx, gz = z0 - 1 + sz;
+            cx<T> u3(0, 0);
+            if (gx >= 0 && gx < Lf.nx && gz >= 0 && gz < Lf.nz) {
+                const int lx = sx + 1, lz = sz + 1;
+                const T s = hw * __ldg(m2 + (size_t)gz * Lf.nx + gx);
+                const cx<T> D(T(4) - s * b1, s * b2);
+                const cx<T> c = U2[lz][lx];
+                cx<T> mu((T(4) - s * b1) * c.re - s * b2 * c.im, (T(4) - s * b1) * c.im + s * b2 * c.re);
+                mu = mu - U2[lz][lx - 1] - U2[lz][lx + 1] - U2[lz - 1][lx] - U2[lz + 1][lx];
+                u3 = c + wj * cdiv(F[lz][lx] - mu, D);
+            }
+            U3[sz][sx] = u3;
+        }
+        __syncthreads();
+        // y = A u3 on the tile (fine operator with damping), dots
+        T* ob = out + 2 * nf * b;
+        T* yb = y + 2 * nf * b;
+        const T* ab = aux + 2 * nf * b;
+        T d0 = 0, d1 = 0, d2 = 0;
+        for (int idx = threadIdx.x; idx < PFX * PFZ; idx += blockDim.x) {
+            const int tz = idx / PFX, tx = idx - tz * PFX;
+            const int gx = x0 + tx, gz = z0 + tz;
+            if (gx >= Lf.nx || gz >= Lf.nz) continue;
+            const int sx = tx + 1, sz = tz + 1;
+            const size_t i = (size_t)gz * Lf.nx + gx;
+            const T s = hw * __ldg(m2 + i);
+            const T a = (T)layer_alpha(gx, gz, Lf.nx, Lf.nz, npml, amax);
+            const cx<T> c = U3[sz][sx];
+            cx<T> yv((T(4) - s) * c.re - s * a * c.im, (T(4) - s) * c.im + s * a * c.re);
+            yv = yv - U3[sz][sx - 1] - U3[sz][sx + 1] - U3[sz - 1][sx] - U3[sz + 1][sx];
+            stc(ob, i, c);
+            stc(yb, i, yv);
+            if (MODE == 1) {          // <rh, v>
+                const cx<T> q = ldc(ab, i);
+                d0 += q.re * yv.re + q.im * yv.im;
+                d1 += q.re * yv.im - q.im * yv.re;
+            } else {                  // <t, s>, <t, t> with s = f
+                const cx<T> sv = F[tz + H][tx + H];
+                d0 += yv.re * sv.re + yv.im * sv.im;
+                d1 += yv.re * sv.im - yv.im * sv.re;
+                d2 += yv.re * yv.re + yv.im * yv.im;
+            }
+        }
+        double acc[3] = {(double)d0, (double)d1, (double)d2};
+        const int nblk = gridDim.x * gridDim.y, blk = blockIdx.y * gridDim.x + blockIdx.x;
+        if (last_block_reduce<3>(acc, shred, partials + (size_t)b * pstride, nblk, blk, &st[b].counter[3])) {
+            if (threadIdx.x == 0) {
+                RhsState& S = st[b];
+                if (MODE == 1) {   // alpha = rho / <rh, v>
+                    double dd = acc[0] * acc[0] + acc[1] * acc[1];
+                    if (!(dd > 0.0)) {
+                        S.flag = FLAG_BREAKDOWN;
+                        S.active = 0;
+                        S.alpha[0] = 0.0; S.alpha[1] = 0.0;
+                    } else {
+                        S.alpha[0] = (S.rho[0] * acc[0] + S.rho[1] * acc[1]) / dd;
+                        S.alpha[1] = (S.rho[1] * acc[0] - S.rho[0] * acc[1]) / dd;
+                    }
+                } else {           // omega = <t, s> / <t, t>
+                    if (acc[2] > 0.0) { S.omega[0] = acc[0] / acc[2]; S.omega[1] = acc[1] / acc[2]; }
+                    else { S.omega[0] = 0.0; S.omega[1] = 0.0; }
+                }
+            }
+        }
+    }
+}
+
+template <typename T>
+void launch_prolong(int mode, const LevelDev& Lf, const LevelDev& Lc, int npml, double amax, const double* w2,
+                    double b1, double b2, double wj, const T* f, const T* ec, T* out, T* y, const T* aux,
+                    double* partials, int pstride, RhsState* st, int nrhs, cudaStream_t s) {
+    constexpr int PFX = PTile<T>::X, PFZ = PTile<T>::Z;
+    dim3 grd((Lf.nx + PFX - 1) / PFX, (Lf.nz + PFZ - 1) / PFZ, nrhs);
+    if (mode == 0)
+        k_prolong<T, 0><<<grd, 256, 0, s>>>(Lf, Lc, npml, amax, w2, (T)b1, (T)b2, (T)wj, f, ec, out, y, aux, partials, pstride, st);
+    else if (mode == 1)
+        k_prolong<T, 1><<<grd, 256, 0, s>>>(Lf, Lc, npml, amax, w2, (T)b1, (T)b2, (T)wj, f, ec, out, y, aux, partials, pstride, st);
+    else
+        k_prolong<T, 2><<<grd, 256, 0, s>>>(Lf, Lc, npml, amax, w2, (T)b1, (T)b2, (T)wj, f, ec, out, y, aux, partials, pstride, st);
+}
+
+// ======================================================= V-cycle: coarsest
+// e = M_L^{-1} f with the precomputed dense inverse of the coarsest level
+// (one per distinct frequency); one warp per row.
+template <typename T>
+__global__ void __launch_bounds__(256) k_coarse(int n, const T* __restrict__ minv, const int* __restrict__ slot,
+                                                const T* __restrict__ fL, T* __restrict__ eL, const RhsState* st) {
+    __shared__ cx<T> fs[kCoarseHardMax];
+    const int b = blockIdx.x;
+    if (!rhs_active(st, b)) return;
+    for (int j = threadIdx.x; j < n; j += blockDim.x) fs[j] = ldc(fL, (size_t)n * b + j);
+    __syncthreads();
+    const T* Mb = minv + 2 * (size_t)n * n * slot[b];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int row = warp; row < n; row += nw) {
+        T re = 0, im = 0;
+        for (int j = lane; j < n; j += 32) {
+            const cx<T> a = ldc(Mb, (size_t)row * n + j);
+            const cx<T> v = fs[j];
+            re += a.re * v.re - a.im * v.im;
+            im += a.re * v.im + a.im * v.re;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            re += __shfl_xor_sync(0xffffffffu, re, o);
+            im += __shfl_xor_sync(0xffffffffu, im, o);
+        }
+        if (lane == 0) stc(eL, (size_t)n * b + row, cx<T>(re, im));
+    }
+}
+
+template <typename T>
+void launch_coarse(int n, const T* minv, const int* slot, const T* fL, T* eL, const RhsState* st, int nrhs,
+                   cudaStream_t s) {
+    k_coarse<T><<<nrhs, 256, 0, s>>>(n, minv, slot, fL, eL, st);
+}
+
+// Dense inverse of the coarsest shifted-Laplace matrix, Gauss-Jordan with
+// partial pivoting in FP64; one block per distinct frequency.
+__global__ void __launch_bounds__(1024) k_coarse_invert(int nx, int nz, double h2, const double* __restrict__ m2all,
+                                                        const double* __restrict__ w2s, const int* __restrict__ mods,
+                                                        double b1, double b2, double2* work, float2* minv_f,
+                                                        double2* minv_d) {
+    const int n = nx * nz, w = 2 * n;
+    const int sl = blockIdx.x;
+    double2* A = work + (size_t)sl * n * w;
+    const double hw = h2 * w2s[sl];
+    const double* m2 = m2all + (size_t)mods[sl] * n;
+    __shared__ double2 fac[kCoarseHardMax];
+    __shared__ double red_v[32];
+    __shared__ int red_i[32];
+    __shared__ int s_piv;
+    __shared__ double2 s_pinv;
+    for (int idx = threadIdx.x; idx < n * w; idx += blockDim.x) {
+        const int i = idx / w, j = idx - i * w;
+        double2 v = make_double2(0.0, 0.0);
+        if (j < n) {
+            const int ix = i % nx, iz = i / nx, jx = j % nx, jz = j / nx;
+            if (i == j) { const double s = hw * m2[i]; v = make_double2(4.0 - s * b1, s * b2); }
+            else if ((iz == jz && abs(ix - jx) == 1) || (ix == jx && abs(iz - jz) == 1)) v = make_double2(-1.0, 0.0);
+        } else if (j - n == i) {
+            v = make_double2(1.0, 0.0);
+        }
+        A[idx] = v;
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    for (int k = 0; k < n; ++k) {
+        // pivot search over rows k..n-1 (ties -> lowest row)
+        double best = -1.0;
+        int bi = n;
+        for (int i = k + threadIdx.x; i < n; i += blockDim.x) {
+            const double2 a = A[(size_t)i * w + k];
+            const double m = a.x * a.x + a.y * a.y;
+            if (m > best) { best = m; bi = i; }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+            const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+            if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+        }
+        if (lane == 0) { red_v[warp] = best; red_i[warp] = bi; }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double bb = -1.0; int ii = n;
+            for (int q = 0; q < nwarps; ++q)
+                if (red_v[q] > bb || (red_v[q] == bb && red_i[q] < ii)) { bb = red_v[q]; ii = red_i[q]; }
+            s_piv = ii;
+        }
+        __syncthreads();
+        const int p = s_piv;
+        if (p != k)
+            for (int j = threadIdx.x; j < w; j += blockDim.x) {
+                const double2 t = A[(size_t)k * w + j];
+                A[(size_t)k * w + j] = A[(size_t)p * w + j];
+                A[(size_t)p * w + j] = t;
+            }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            const double2 a = A[(size_t)k * w + k];
+            const double d = a.x * a.x + a.y * a.y;
+            s_pinv = make_double2(a.x / d, -a.y / d);
+        }
+        __syncthreads();
+        const double2 pi = s_pinv;
+        for (int j = k + threadIdx.x; j < w; j += blockDim.x) {
+            const double2 a = A[(size_t)k * w + j];
+            A[(size_t)k * w + j] = make_double2(a.x * pi.x - a.y * pi.y, a.x * pi.y + a.y * pi.x);
+        }
+        for (int i = threadIdx.x; i < n; i += blockDim.x) fac[i] = A[(size_t)i * w + k];
+        __syncthreads();
+        const int cols = w - k;
+        for (int idx = threadIdx.x; idx < n * cols; idx += blockDim.x) {
+            const int i = idx / cols, j = k + (idx - i * cols);
+            if (i == k) continue;
+            const double2 fi = fac[i];
+            const double2 kj = A[(size_t)k * w + j];
+            double2 a = A[(size_t)i * w + j];
+            a.x -= fi.x * kj.x - fi.y * kj.y;
+            a.y -= fi.x * kj.y + fi.y * kj.x;
+            A[(size_t)i * w + j] = a;
+        }
+        __syncthreads();
+    }
+    (void)warp;
+    for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+        const int i = idx / n, j = idx - i * n;
+        const double2 a = A[(size_t)i * w + n + j];
+        minv_d[(size_t)sl * n * n + idx] = a;
+        minv_f[(size_t)sl * n * n + idx] = make_float2((float)a.x, (float)a.y);
+    }
+}
+
+void launch_coarse_invert(const LevelDev& Lc, const double* w2_slots, const int* mod_slots, int nslots, double b1,
+                          double b2, double2* work, float2* minv_f, double2* minv_d, cudaStream_t s) {
+    k_coarse_invert<<<nslots, 1024, 0, s>>>(Lc.nx, Lc.nz, Lc.h2, static_cast<const double*>(Lc.m2), w2_slots,
+                                            mod_slots, b1, b2, work, minv_f, minv_d);
+}
+
+// ============================================================ right-hand sides
+__global__ void k_point_rhs(double* f, const int* __restrict__ src_flat, size_t n) {
+    const int b = blockIdx.x;
+    if (threadIdx.x == 0) {
+        const size_t i = (size_t)n * b + src_flat[b];
+        f[2 * i] = 1.0;      // grid-scaled: h^2 * (1/h^2)
+        f[2 * i + 1] = 0.0;
+    }
+}
+
+void launch_point_rhs(double* f, const int* src_flat, int nrhs, size_t n, cudaStream_t s) {
+    cudaMemsetAsync(f, 0, sizeof(double) * 2 * n * nrhs, s);
+    k_point_rhs<<<nrhs, 32, 0, s>>>(f, src_flat, n);
+}
+
+__global__ void k_scale(const double* __restrict__ in, double* __restrict__ out, double sc, size_t count) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x)
+        out[i] = sc * in[i];
+}
+void launch_scale_rhs(const double* fin, double* f, double scale, size_t count, cudaStream_t s) {
+    k_scale<<<grid1d(count), 256, 0, s>>>(fin, f, scale, count * 2);
+}
+
+template <typename T>
+__global__ void k_cast(const double* __restrict__ in, T* __restrict__ out, size_t count) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x)
+        out[i] = (T)in[i];
+}
+template <typename T>
+void launch_cast_complex(const double* in, T* out, size_t count, cudaStream_t s) {
+    k_cast<T><<<grid1d(count), 256, 0, s>>>(in, out, 2 * count);
+}
+template <typename T>
+__global__ void k_widen(const T* __restrict__ in, double* __restrict__ out, size_t count) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x)
+        out[i] = (double)in[i];
+}
+template <typename T>
+void launch_to_c128(const T* in, double* out, size_t count, cudaStream_t s) {
+    k_widen<T><<<grid1d(count), 256, 0, s>>>(in, out, 2 * count);
+}
+template void launch_cast_complex<float>(const double*, float*, size_t, cudaStream_t);
+template void launch_cast_complex<double>(const double*, double*, size_t, cudaStream_t);
+template void launch_to_c128<float>(const float*, double*, size_t, cudaStream_t);
+template void launch_to_c128<double>(const double*, double*, size_t, cudaStream_t);
+
+// ================================================================ gradient
+// d_cal = P u at the receiver nodes, r = d_cal - d_obs, per-RHS sum |r|^2.
+__global__ void k_sample(const double* __restrict__ u, const int* __restrict__ rec_flat, int nrec,
+                         const double* __restrict__ d_obs, double* __restrict__ d_cal, double* __restrict__ resid,
+                         double* __restrict__ jpart, size_t n) {
+    __shared__ double sh[32];
+    const int b = blockIdx.x;
+    double acc[1] = {0.0};
+    for (int k = threadIdx.x; k < nrec; k += blockDim.x) {
+        const size_t i = (size_t)n * b + rec_flat[k];
+        const size_t o = (size_t)nrec * b + k;
+        const double ur = u[2 * i], ui = u[2 * i + 1];
+        if (d_cal) { d_cal[2 * o] = ur; d_cal[2 * o + 1] = ui; }
+        const double rr = ur - d_obs[2 * o], ri = ui - d_obs[2 * o + 1];
+        resid[2 * o] = rr;
+        resid[2 * o + 1] = ri;
+        acc[0] += rr * rr + ri * ri;
+    }
+    block_sum<1>(acc, sh);
+    if (threadIdx.x == 0) jpart[b] = acc[0];
+}
+
+void launch_sample(const double* u, const int* rec_flat, int nrec, const double* d_obs, double* d_cal, double* resid,
+                   double* jpart, size_t n, int nrhs, cudaStream_t s) {
+    k_sample<<<nrhs, 256, 0, s>>>(u, rec_flat, nrec, d_obs, d_cal, resid, jpart, n);
+}
+
+// Adjoint right-hand side of the grid-scaled system: h^2 conj(P^T r), summed in
+// receiver order by one thread per right-hand side.
+__global__ void k_adjoint_rhs(const double* __restrict__ resid, const int* __restrict__ rec_flat, int nrec,
+                              double h2, double* f, size_t n, int nrhs) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nrhs) return;
+    for (int k = 0; k < nrec; ++k) {
+        const size_t i = (size_t)n * b + rec_flat[k];
+        const size_t o = (size_t)nrec * b + k;
+        f[2 * i] += h2 * resid[2 * o];
+        f[2 * i + 1] -= h2 * resid[2 * o + 1];
+    }
+}
+
+void launch_adjoint_rhs(const double* resid, const int* rec_flat, int nrec, double h2, double* f, size_t n, int nrhs,
+                        cudaStream_t s) {
+    cudaMemsetAsync(f, 0, sizeof(double) * 2 * n * nrhs, s);
+    k_adjoint_rhs<<<(nrhs + 63) / 64, 64, 0, s>>>(resid, rec_flat, nrec, h2, f, n, nrhs);
+}
+
+// g_pad += sum_b 4 w_b^2 m Re[(1 - j alpha) u_b w_b], w_b = conj(lambda_b) = B^{-1} conj(P^T r_b).
+__global__ void k_grad_accum(const double* __restrict__ u, const double* __restrict__ wv, const double* __restrict__ w2,
+                             const double* __restrict__ m_pad, int nx, int nz, int npml, double amax,
+                             double* __restrict__ g_pad, int nrhs) {
+    const size_t n = (size_t)nx * nz;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const int ix = (int)(i % nx), iz = (int)(i / nx);
+        const double a = layer_alpha(ix, iz, nx, nz, npml, amax);
+        double acc = 0.0;
+        for (int b = 0; b < nrhs; ++b) {
+            const cx<double> uu = ldc(u, n * b + i), ww = ldc(wv, n * b + i);
+            const cx<double> q = uu * ww;
+            acc += 4.0 * w2[b] * (q.re + a * q.im);    // Re[(1 - j a) q]
+        }
+        g_pad[i] += m_pad[i] * acc;
+    }
+}
+
+void launch_grad_accum(const double* u, const double* w, const double* w2, const double* m_pad, int nx, int nz,
+                       int npml, double amax, double* g_pad, int nrhs, cudaStream_t s) {
+    k_grad_accum<<<grid1d((size_t)nx * nz), 256, 0, s>>>(u, w, w2, m_pad, nx, nz, npml, amax, g_pad, nrhs);
+}
+
+// g = E^T g_pad + 2 lam m on the physical cells: each edge cell also collects
+// the layer nodes that copy its slowness.
+__global__ void k_fold(const double* __restrict__ g_pad, const double* __restrict__ m_pad, int Px, int Pz, int npml,
+                       double lam, double* __restrict__ g) {
+    const int nx = Px + 2 * npml;
+    const size_t n = (size_t)Px * Pz;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const int px = (int)(i % Px), pz = (int)(i / Px);
+        const int xlo = px == 0 ? 0 : px + npml, xhi = px == Px - 1 ? nx - 1 : px + npml;
+        const int zlo = pz == 0 ? 0 : pz + npml, zhi = pz == Pz - 1 ? Pz + 2 * npml - 1 : pz + npml;
+        double acc = 0.0;
+        for (int iz = zlo; iz <= zhi; ++iz)
+            for (int ix = xlo; ix <= xhi; ++ix) acc += g_pad[(size_t)iz * nx + ix];
+        const double m = m_pad[(size_t)(pz + npml) * nx + px + npml];
+        g[i] = acc + 2.0 * lam * m;
+    }
+}
+
+void launch_fold(const double* g_pad, const double* m_pad, int Px, int Pz, int npml, double lam, double* g,
+                 cudaStream_t s) {
+    k_fold<<<grid1d((size_t)Px * Pz), 256, 0, s>>>(g_pad, m_pad, Px, Pz, npml, lam, g);
+}
+
+// ------------------------------------------------------- instantiations
+
+#define HELM_INST(T)                                                                                              \
+    template void launch_bicg_init<T>(const T*, T*, T*, T*, T*, T*, double*, int, RhsState*, int*, size_t, int,   \
+                                      cudaStream_t);                                                              \
+    template void launch_bicg_p<T>(const T*, T*, const T*, const RhsState*, size_t, int, cudaStream_t);           \
+    template void launch_bicg_s<T>(const T*, const T*, T*, const RhsState*, size_t, int, cudaStream_t);           \
+    template void launch_bicg_xr<T>(T*, const T*, const T*, const T*, const T*, const T*, T*, double*, int,       \
+                                    RhsState*, int*, size_t, int, cudaStream_t);                                  \
+    template void launch_restrict<T>(const LevelDev&, const LevelDev&, const double*, double, double, double,     \
+                                     const T*, T*, const RhsState*, int, cudaStream_t);                           \
+    template void launch_prolong<T>(int, const LevelDev&, const LevelDev&, int, double, const double*, double,    \
+                                    double, double, const T*, const T*, T*, T*, const T*, double*, int,           \
+                                    RhsState*, int, cudaStream_t);                                                \
+    template void launch_coarse<T>(int, const T*, const int*, const T*, T*, const RhsState*, int, cudaStream_t);
+HELM_INST(float)
+HELM_INST(double)
+#undef HELM_INST
+
+}  // namespace helm

@@ -1,0 +1,556 @@
+// helm_solver.cu - host side of the batched solver: multigrid hierarchy,
+// right-preconditioned BiCGSTAB in complex64 or complex128, FP64 residual and
+// iterative refinement, and the adjoint-state gradient.
+//
+// Every step of the computation runs in the kernels of helm_kernels.cu; this
+// file only sizes buffers, orders launches on one stream and reads back the
+// per-right-hand-side convergence state every `check_every` iterations.
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstring>
+#include <functional>
+#include <map>
+#include <memory>
+#include <vector>
+
+#include "helm_internal.h"
+#include "helm_solver.h"
+
+namespace helm {
+
+static thread_local std::string g_last_error;
+static std::atomic<unsigned long long> g_launches{0};
+void count_launches(unsigned long long k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+unsigned long long launches() { return g_launches.load(std::memory_order_relaxed); }
+void set_last_error(const std::string& s) { g_last_error = s; }
+const char* last_error() { return g_last_error.c_str(); }
+
+namespace {
+
+// Stream-ordered device allocation freed on scope exit.
+struct DBuf {
+    void* p = nullptr;
+    cudaStream_t s = nullptr;
+    DBuf() = default;
+    DBuf(const DBuf&) = delete;
+    DBuf& operator=(const DBuf&) = delete;
+    ~DBuf() { if (p) cudaFreeAsync(p, s); }
+    cudaError_t alloc(size_t bytes, cudaStream_t st) {
+        s = st;
+        return cudaMallocAsync(&p, bytes ? bytes : 16, st);
+    }
+    template <typename T> T* as() const { return static_cast<T*>(p); }
+};
+
+#define TRY_ALLOC(buf, bytes, st)                                                        \
+    do {                                                                                 \
+        cudaError_t e_ = (buf).alloc((bytes), (st));                                     \
+        if (e_ != cudaSuccess) {                                                         \
+            cudaGetLastError();                                                          \
+            set_last_error(std::string("device allocation failed: ") + cudaGetErrorString(e_)); \
+            return HELM_E_NOMEM;                                                         \
+        }                                                                                \
+    } while (0)
+
+int max_blocks_per_rhs(const helm_model* m) {
+    const Level& L0 = m->lv[0];
+    size_t g1 = std::min<size_t>(2048, (L0.n() + 1023) / 1024);
+    size_t g2 = (size_t)((L0.nx + 31) / 32) * ((L0.nz + 7) / 8);   // resid64 / apply tiles
+    size_t g3 = (size_t)((L0.nx + 31) / 32) * ((L0.nz + 15) / 16); // prolong tiles (FP64: 32 x 16)
+    return (int)std::max<size_t>(std::max(g1, g2), std::max<size_t>(g3, 1));
+}
+
+}  // namespace
+
+int coarsest_points(const helm_model* m) { return (int)m->lv.back().n(); }
+
+// --------------------------------------------------------------- workspace
+template <typename T>
+struct Inner {
+    DBuf x, r, rh, p, v, sv, t, ph, shv;
+    std::vector<std::unique_ptr<DBuf>> fl, el;   // per level l >= 1
+};
+
+// Per-solve state shared by the outer and inner loops.
+struct SolveCtx {
+    const helm_model* m;
+    cudaStream_t s;
+    int nrhs;
+    helm_solve_opts o;
+    const double* w2;       // device [nrhs]
+    RhsState* st;           // device [nrhs]
+    double* partials;       // device [nrhs * pstride]
+    int pstride;
+    int* nactive;           // device
+    const int* slot;        // device [nrhs]
+    int ncoarse;
+    const void* minv;       // float2* or double2* [nslots][n][n]
+};
+
+template <typename T>
+static void vcycle(const SolveCtx& c, Inner<T>& w, const T* in, T* out, int mode, T* y, const T* aux) {
+    const helm_model* m = c.m;
+    const bool dbl = sizeof(T) == 8;
+    const int L = (int)m->lv.size() - 1;
+    const double b1 = c.o.beta1, b2 = c.o.beta2, wj = c.o.omega_jacobi;
+    // down: level 0 -> 1 from `in`, then level l -> l + 1
+    launch_restrict<T>(level_dev(m, 0, dbl), level_dev(m, 1, dbl), c.w2, b1, b2, wj, in,
+                       w.fl[1]->template as<T>(), c.st, c.nrhs, c.s);
+    for (int l = 1; l < L; ++l)
+        launch_restrict<T>(level_dev(m, l, dbl), level_dev(m, l + 1, dbl), c.w2, b1, b2, wj,
+                           w.fl[l]->template as<T>(), w.fl[l + 1]->template as<T>(), c.st, c.nrhs, c.s);
+    launch_coarse<T>(c.ncoarse, static_cast<const T*>(c.minv), c.slot, w.fl[L]->template as<T>(),
+                     w.el[L]->template as<T>(), c.st, c.nrhs, c.s);
+    for (int l = L - 1; l >= 1; --l)
+        launch_prolong<T>(0, level_dev(m, l, dbl), level_dev(m, l + 1, dbl), m->npml, m->alpha_max, c.w2,
+                          b1, b2, wj, w.fl[l]->template as<T>(), w.el[l + 1]->template as<T>(),
+                          w.el[l]->template as<T>(), nullptr, nullptr, nullptr, 0, c.st, c.nrhs, c.s);
+    launch_prolong<T>(mode, level_dev(m, 0, dbl), level_dev(m, 1, dbl), m->npml, m->alpha_max, c.w2, b1,
+                      b2, wj, in, w.el[1]->template as<T>(), out, y, aux, c.partials, c.pstride, c.st, c.nrhs, c.s);
+}
+
+template <typename T>
+static int alloc_inner(const SolveCtx& c, Inner<T>& w) {
+    const size_t n = c.m->n(), vb = sizeof(T) * 2 * n * c.nrhs;
+    TRY_ALLOC(w.x, vb, c.s); TRY_ALLOC(w.r, vb, c.s); TRY_ALLOC(w.rh, vb, c.s);
+    TRY_ALLOC(w.p, vb, c.s); TRY_ALLOC(w.v, vb, c.s); TRY_ALLOC(w.sv, vb, c.s);
+    TRY_ALLOC(w.t, vb, c.s); TRY_ALLOC(w.ph, vb, c.s); TRY_ALLOC(w.shv, vb, c.s);
+    const int nl = (int)c.m->lv.size();
+    w.fl.resize(nl);
+    w.el.resize(nl);
+    for (int l = 1; l < nl; ++l) {
+        const size_t b = sizeof(T) * 2 * c.m->lv[l].n() * c.nrhs;
+        w.fl[l].reset(new DBuf());
+        w.el[l].reset(new DBuf());
+        TRY_ALLOC(*w.fl[l], b, c.s);
+        TRY_ALLOC(*w.el[l], b, c.s);
+    }
+    return HELM_OK;
+}
+
+// kernels one BiCGSTAB iteration launches: p, s and x/r updates plus two
+// V-cycles of (levels - 1) restrictions, one coarse solve and (levels - 1)
+// prolongations
+static int kernels_per_iteration(const helm_model* m) { return 3 + 2 * (2 * ((int)m->lv.size() - 1) + 1); }
+
+template <typename T>
+static void bicg_iteration(const SolveCtx& c, Inner<T>& w) {
+    const size_t n = c.m->n();
+    T *x = w.x.template as<T>(), *r = w.r.template as<T>(), *rh = w.rh.template as<T>();
+    T *p = w.p.template as<T>(), *v = w.v.template as<T>(), *sv = w.sv.template as<T>();
+    T *t = w.t.template as<T>(), *ph = w.ph.template as<T>(), *shv = w.shv.template as<T>();
+    launch_bicg_p<T>(r, p, v, c.st, n, c.nrhs, c.s);
+    vcycle<T>(c, w, p, ph, 1, v, rh);              // p^ = V(p), v = A p^, alpha
+    launch_bicg_s<T>(r, v, sv, c.st, n, c.nrhs, c.s);
+    vcycle<T>(c, w, sv, shv, 2, t, nullptr);       // s^ = V(s), t = A s^, omega
+    launch_bicg_xr<T>(x, ph, shv, sv, t, rh, r, c.partials, c.pstride, c.st, c.nactive, n, c.nrhs, c.s);
+}
+
+// Inner BiCGSTAB on rin for the right-hand sides whose outer step is active.
+// Leaves the correction in w.x. `graph` caches the captured iteration chunk.
+template <typename T>
+static int inner_solve(const SolveCtx& c, Inner<T>& w, const T* rin, cudaGraphExec_t* graph, int* iters_done) {
+    const size_t n = c.m->n();
+    HELM_CUDA_TRY(cudaMemsetAsync(c.nactive, 0, sizeof(int), c.s));
+    count_launches(1);
+    launch_bicg_init<T>(rin, w.x.template as<T>(), w.r.template as<T>(), w.rh.template as<T>(), w.p.template as<T>(),
+                        w.v.template as<T>(), c.partials, c.pstride, c.st, c.nactive, n, c.nrhs, c.s);
+    const int chunk = std::max(1, c.o.check_every);
+    if (c.o.use_graphs && *graph == nullptr) {
+        cudaGraph_t g;
+        HELM_CUDA_TRY(cudaStreamBeginCapture(c.s, cudaStreamCaptureModeThreadLocal));
+        for (int k = 0; k < chunk; ++k) bicg_iteration<T>(c, w);
+        cudaError_t e = cudaStreamEndCapture(c.s, &g);
+        if (e != cudaSuccess) { set_last_error(cudaGetErrorString(e)); return HELM_E_CUDA; }
+        e = cudaGraphInstantiate(graph, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) { set_last_error(cudaGetErrorString(e)); *graph = nullptr; return HELM_E_CUDA; }
+    }
+    int h_active = 0;
+    int done = 0;
+    // every right-hand side stops by itself at max_it; the extra chunk bounds the loop
+    const int limit = c.o.max_it + chunk;
+    while (done < limit) {
+        if (c.o.use_graphs) {
+            HELM_CUDA_TRY(cudaGraphLaunch(*graph, c.s));
+        } else {
+            for (int k = 0; k < chunk; ++k) bicg_iteration<T>(c, w);
+        }
+        count_launches((unsigned long long)chunk * kernels_per_iteration(c.m));
+        done += chunk;
+        HELM_CUDA_TRY(cudaMemcpyAsync(&h_active, c.nactive, sizeof(int), cudaMemcpyDeviceToHost, c.s));
+        HELM_CUDA_TRY(cudaStreamSynchronize(c.s));
+        if (h_active <= 0) break;
+    }
+    HELM_CUDA_TRY(cudaGetLastError());
+    *iters_done += done;
+    return HELM_OK;
+}
+
+// Dense inverses of the coarsest level, one per distinct frequency.
+struct CoarseSet {
+    DBuf work, mf, md, slot, w2s, mods;
+    int n = 0, nslots = 0;
+};
+
+static int build_coarse(const helm_model* m, cudaStream_t s, int nrhs, const double* h_w2, double b1, double b2,
+                        CoarseSet& cs) {
+    // one dense inverse per distinct (model, frequency) pair
+    std::map<std::pair<int, double>, int> uniq;
+    std::vector<int> slot(nrhs), mods;
+    std::vector<double> w2s;
+    for (int b = 0; b < nrhs; ++b) {
+        const int mod = m->nmodels > 1 ? b : 0;
+        const auto key = std::make_pair(mod, h_w2[b]);
+        auto it = uniq.find(key);
+        if (it == uniq.end()) {
+            it = uniq.emplace(key, (int)w2s.size()).first;
+            w2s.push_back(h_w2[b]);
+            mods.push_back(mod);
+        }
+        slot[b] = it->second;
+    }
+    const Level& Lc = m->lv.back();
+    cs.n = (int)Lc.n();
+    cs.nslots = (int)w2s.size();
+    const size_t nn = (size_t)cs.n * cs.n;
+    TRY_ALLOC(cs.work, sizeof(double2) * nn * 2 * cs.nslots, s);
+    TRY_ALLOC(cs.mf, sizeof(float2) * nn * cs.nslots, s);
+    TRY_ALLOC(cs.md, sizeof(double2) * nn * cs.nslots, s);
+    TRY_ALLOC(cs.slot, sizeof(int) * nrhs, s);
+    TRY_ALLOC(cs.w2s, sizeof(double) * cs.nslots, s);
+    TRY_ALLOC(cs.mods, sizeof(int) * cs.nslots, s);
+    HELM_CUDA_TRY(cudaMemcpyAsync(cs.slot.p, slot.data(), sizeof(int) * nrhs, cudaMemcpyHostToDevice, s));
+    HELM_CUDA_TRY(cudaMemcpyAsync(cs.w2s.p, w2s.data(), sizeof(double) * cs.nslots, cudaMemcpyHostToDevice, s));
+    HELM_CUDA_TRY(cudaMemcpyAsync(cs.mods.p, mods.data(), sizeof(int) * cs.nslots, cudaMemcpyHostToDevice, s));
+    count_launches(1);
+    launch_coarse_invert(level_dev(m, (int)m->lv.size() - 1, true), cs.w2s.as<double>(), cs.mods.as<int>(), cs.nslots,
+                         b1, b2, cs.work.as<double2>(), cs.mf.as<float2>(), cs.md.as<double2>(), s);
+    HELM_CUDA_TRY(cudaGetLastError());
+    // the host vectors above must outlive the copies
+    HELM_CUDA_TRY(cudaStreamSynchronize(s));
+    return HELM_OK;
+}
+
+template <typename T>
+static int solve_impl(const helm_model* m, cudaStream_t s, int nrhs, const double* h_w2, const double* f64,
+                      double* u64, const helm_solve_opts& o, helm_solve_stats* stats) {
+    const size_t n = m->n();
+    SolveCtx c;
+    c.m = m;
+    c.s = s;
+    c.nrhs = nrhs;
+    c.o = o;
+    c.pstride = 3 * max_blocks_per_rhs(m);
+    DBuf w2, st, part, nact, rin;
+    TRY_ALLOC(w2, sizeof(double) * nrhs, s);
+    TRY_ALLOC(st, sizeof(RhsState) * nrhs, s);
+    TRY_ALLOC(part, sizeof(double) * (size_t)c.pstride * nrhs, s);
+    TRY_ALLOC(nact, sizeof(int), s);
+    TRY_ALLOC(rin, sizeof(T) * 2 * n * nrhs, s);
+    CoarseSet cs;
+    int rc = build_coarse(m, s, nrhs, h_w2, o.beta1, o.beta2, cs);
+    if (rc != HELM_OK) return rc;
+    c.w2 = w2.as<double>();
+    c.st = st.as<RhsState>();
+    c.partials = part.as<double>();
+    c.nactive = nact.as<int>();
+    c.slot = cs.slot.as<int>();
+    c.ncoarse = cs.n;
+    c.minv = sizeof(T) == 8 ? (const void*)cs.md.p : (const void*)cs.mf.p;
+    Inner<T> w;
+    rc = alloc_inner<T>(c, w);
+    if (rc != HELM_OK) return rc;
+
+    std::vector<RhsState> hs(nrhs);
+    std::memset(hs.data(), 0, sizeof(RhsState) * nrhs);
+    for (auto& S : hs) { S.outer_active = 1; S.active = 1; S.max_it = o.max_it; }
+    HELM_CUDA_TRY(cudaMemcpyAsync(c.st, hs.data(), sizeof(RhsState) * nrhs, cudaMemcpyHostToDevice, s));
+    HELM_CUDA_TRY(cudaMemcpyAsync(w2.p, h_w2, sizeof(double) * nrhs, cudaMemcpyHostToDevice, s));
+    HELM_CUDA_TRY(cudaMemsetAsync(part.p, 0, sizeof(double) * (size_t)c.pstride * nrhs, s));
+    HELM_CUDA_TRY(cudaMemsetAsync(u64, 0, sizeof(double) * 2 * n * nrhs, s));
+
+    double floor_tol = 0.0;
+    int max_outer = o.max_outer;
+    if (o.precision == HELM_PREC_MIXED) floor_tol = o.inner_tol;
+    if (o.precision == HELM_PREC_FP32) { floor_tol = o.tol; max_outer = 1; }
+    if (o.precision == HELM_PREC_FP64) floor_tol = 0.0;
+
+    std::vector<int> outer_count(nrhs, 0);
+    cudaGraphExec_t graph = nullptr;
+    int iters_done = 0;
+    const LevelDev L0 = level_dev(m, 0, true);
+    for (int outer = 0;; ++outer) {
+        launch_resid64<T>(L0, m->npml, m->alpha_max, c.w2, f64, u64, rin.as<T>(), c.partials, c.pstride, c.st, o.tol,
+                          floor_tol, outer == 0, nrhs, s);
+        count_launches(1);
+        HELM_CUDA_TRY(cudaGetLastError());
+        HELM_CUDA_TRY(cudaMemcpyAsync(hs.data(), c.st, sizeof(RhsState) * nrhs, cudaMemcpyDeviceToHost, s));
+        HELM_CUDA_TRY(cudaStreamSynchronize(s));
+        int any = 0;
+        for (int b = 0; b < nrhs; ++b)
+            if (hs[b].outer_active) { any = 1; }
+        if (!any || outer >= max_outer) break;
+        for (int b = 0; b < nrhs; ++b) outer_count[b] += hs[b].outer_active;
+        rc = inner_solve<T>(c, w, rin.as<T>(), &graph, &iters_done);
+        if (rc != HELM_OK) break;
+        launch_refine<T>(w.x.template as<T>(), u64, c.st, n, nrhs, s);
+        count_launches(1);
+    }
+    if (graph) cudaGraphExecDestroy(graph);
+    if (rc != HELM_OK) return rc;
+    HELM_CUDA_TRY(cudaGetLastError());
+    int status = HELM_OK;
+    for (int b = 0; b < nrhs; ++b) {
+        const bool conv = hs[b].relres <= o.tol;
+        if (!conv) status = HELM_E_NOT_CONVERGED;
+        if (stats) {
+            stats[b].iters = hs[b].iters;
+            stats[b].outer_its = outer_count[b];
+            stats[b].converged = conv ? 1 : 0;
+            stats[b].relres = hs[b].relres;
+        }
+    }
+    return status;
+}
+
+int solve_batch(const helm_model* m, cudaStream_t s, int nrhs, const double* h_w2, const double* f64, double* u64,
+                const helm_solve_opts& o, helm_solve_stats* stats) {
+    if (o.precision == HELM_PREC_FP64) return solve_impl<double>(m, s, nrhs, h_w2, f64, u64, o, stats);
+    return solve_impl<float>(m, s, nrhs, h_w2, f64, u64, o, stats);
+}
+
+size_t solve_bytes(int nx, int nz, int nlev_n_sum_extra, int nrhs, int precision) {
+    const size_t n = (size_t)nx * nz;
+    const size_t ts = precision == HELM_PREC_FP64 ? 8 : 4;
+    // inner: 9 vectors + rin; levels ~ 2 * n / 3; outer: f64, u64
+    size_t b = (size_t)nrhs * n * 2 * ts * 10 + (size_t)nrhs * n * 2 * ts * 2 / 3 + (size_t)nrhs * n * 16 * 2;
+    b += (size_t)nlev_n_sum_extra;
+    return b + (64u << 20);
+}
+
+// One standalone V-cycle z = V(r) on the fine level, complex64, for checks.
+int vcycle_once(const helm_model* m, cudaStream_t s, int nrhs, const double* h_w2, double b1, double b2, double wj,
+                const float* r, float* z) {
+    SolveCtx c;
+    c.m = m;
+    c.s = s;
+    c.nrhs = nrhs;
+    helm_default_opts(&c.o);
+    c.o.beta1 = b1;
+    c.o.beta2 = b2;
+    c.o.omega_jacobi = wj;
+    c.pstride = 3 * max_blocks_per_rhs(m);
+    DBuf w2;
+    TRY_ALLOC(w2, sizeof(double) * nrhs, s);
+    HELM_CUDA_TRY(cudaMemcpyAsync(w2.p, h_w2, sizeof(double) * nrhs, cudaMemcpyHostToDevice, s));
+    CoarseSet cs;
+    int rc = build_coarse(m, s, nrhs, h_w2, b1, b2, cs);
+    if (rc != HELM_OK) return rc;
+    c.w2 = w2.as<double>();
+    c.st = nullptr;
+    c.partials = nullptr;
+    c.nactive = nullptr;
+    c.slot = cs.slot.as<int>();
+    c.ncoarse = cs.n;
+    c.minv = cs.mf.p;
+    Inner<float> w;
+    const int nl = (int)m->lv.size();
+    w.fl.resize(nl);
+    w.el.resize(nl);
+    for (int l = 1; l < nl; ++l) {
+        const size_t b = sizeof(float) * 2 * m->lv[l].n() * nrhs;
+        w.fl[l].reset(new DBuf());
+        w.el[l].reset(new DBuf());
+        TRY_ALLOC(*w.fl[l], b, s);
+        TRY_ALLOC(*w.el[l], b, s);
+    }
+    vcycle<float>(c, w, r, z, 0, nullptr, nullptr);
+    HELM_CUDA_TRY(cudaGetLastError());
+    HELM_CUDA_TRY(cudaStreamSynchronize(s));
+    return HELM_OK;
+}
+
+// ------------------------------------------------------- kernel timing
+// Launches one hot-path kernel `reps` times on scratch vectors of nrhs
+// right-hand sides (filled with byte 0x3C) and returns the mean time per launch (CUDA events on `s`)
+// and the algorithmic bytes one launch must move (each input read once, each
+// output written once; the squared slowness, shared by all right-hand sides,
+// counted once).
+int time_kernel(const helm_model* m, cudaStream_t s, int kernel, int nrhs, double hw2, int reps, double* ms,
+                double* bytes) {
+    const size_t n = m->n();
+    const size_t v32 = sizeof(float) * 2 * n * nrhs, v64 = sizeof(double) * 2 * n * nrhs;
+    const int nvec = 8;
+    std::vector<std::unique_ptr<DBuf>> v(nvec);
+    const bool dbl = (kernel == HELM_KERNEL_RESID64 || kernel == HELM_KERNEL_APPLY64);
+    for (int k = 0; k < nvec; ++k) {
+        v[k].reset(new DBuf());
+        TRY_ALLOC(*v[k], dbl ? v64 : v32, s);
+        // byte 0x3C gives small normal, non-zero values in both precisions
+        HELM_CUDA_TRY(cudaMemsetAsync(v[k]->p, 0x3C, dbl ? v64 : v32, s));
+    }
+    DBuf w2, st, part, nact, fc, rin;
+    const int pstride = 3 * max_blocks_per_rhs(m);
+    TRY_ALLOC(w2, sizeof(double) * nrhs, s);
+    TRY_ALLOC(st, sizeof(RhsState) * nrhs, s);
+    TRY_ALLOC(part, sizeof(double) * (size_t)pstride * nrhs, s);
+    TRY_ALLOC(nact, sizeof(int), s);
+    TRY_ALLOC(fc, sizeof(float) * 2 * m->lv[1].n() * nrhs, s);
+    TRY_ALLOC(rin, v32, s);
+    HELM_CUDA_TRY(cudaMemsetAsync(fc.p, 0x3C, sizeof(float) * 2 * m->lv[1].n() * nrhs, s));
+    std::vector<double> hw(nrhs, hw2);
+    std::vector<RhsState> hs(nrhs);
+    std::memset(hs.data(), 0, sizeof(RhsState) * nrhs);
+    for (auto& S : hs) {
+        // bnorm2 < 0 keeps the convergence test false, so every launch does its full work
+        S.active = 1; S.outer_active = 1; S.max_it = 1 << 30; S.tol_rel = 1.0; S.bnorm2 = -1.0; S.fnorm2 = 1.0;
+        S.rho[0] = 1.0; S.alpha[0] = 0.5; S.omega[0] = 0.5; S.beta[0] = 0.5;
+    }
+    HELM_CUDA_TRY(cudaMemcpyAsync(w2.p, hw.data(), sizeof(double) * nrhs, cudaMemcpyHostToDevice, s));
+    HELM_CUDA_TRY(cudaMemcpyAsync(st.p, hs.data(), sizeof(RhsState) * nrhs, cudaMemcpyHostToDevice, s));
+    HELM_CUDA_TRY(cudaMemsetAsync(part.p, 0, sizeof(double) * (size_t)pstride * nrhs, s));
+    const double N = (double)n, B = (double)nrhs;
+    auto F = [&](int k) { return v[k]->as<float>(); };
+    auto D = [&](int k) { return v[k]->as<double>(); };
+    RhsState* S = st.as<RhsState>();
+    std::function<void()> launch;
+    switch (kernel) {
+        case HELM_KERNEL_APPLY:
+            launch = [&] { launch_apply<float>(level_dev(m, 0, false), m->npml, m->alpha_max, w2.as<double>(), F(0), F(1), 1.0f, nrhs, s); };
+            *bytes = N * (16.0 * B + 4.0);
+            break;
+        case HELM_KERNEL_APPLY64:
+            launch = [&] { launch_apply<double>(level_dev(m, 0, true), m->npml, m->alpha_max, w2.as<double>(), D(0), D(1), 1.0, nrhs, s); };
+            *bytes = N * (32.0 * B + 8.0);
+            break;
+        case HELM_KERNEL_RESTRICT:
+            launch = [&] { launch_restrict<float>(level_dev(m, 0, false), level_dev(m, 1, false), w2.as<double>(), 1.0, 0.5, 0.8, F(0), fc.as<float>(), S, nrhs, s); };
+            *bytes = N * (8.0 * B + 4.0) + 8.0 * B * (double)m->lv[1].n();
+            break;
+        case HELM_KERNEL_PROLONG:
+            launch = [&] { launch_prolong<float>(1, level_dev(m, 0, false), level_dev(m, 1, false), m->npml, m->alpha_max, w2.as<double>(), 1.0, 0.5, 0.8, F(0), fc.as<float>(), F(1), F(2), F(3), part.as<double>(), pstride, S, nrhs, s); };
+            *bytes = N * (32.0 * B + 4.0) + 8.0 * B * (double)m->lv[1].n();
+            break;
+        case HELM_KERNEL_BICG_XR:
+            launch = [&] { launch_bicg_xr<float>(F(0), F(1), F(2), F(3), F(4), F(5), F(6), part.as<double>(), pstride, S, nact.as<int>(), n, nrhs, s); };
+            *bytes = N * B * 64.0;
+            break;
+        case HELM_KERNEL_BICG_P:
+            launch = [&] { launch_bicg_p<float>(F(0), F(1), F(2), S, n, nrhs, s); };
+            *bytes = N * B * 32.0;
+            break;
+        case HELM_KERNEL_RESID64:
+            launch = [&] { launch_resid64<float>(level_dev(m, 0, true), m->npml, m->alpha_max, w2.as<double>(), D(0), D(1), rin.as<float>(), part.as<double>(), pstride, S, 0.0, 1e-4, 0, nrhs, s); };
+            *bytes = N * (40.0 * B + 8.0);
+            break;
+        default:
+            return HELM_E_INVALID;
+    }
+    for (int k = 0; k < 3; ++k) launch();
+    // keep every right-hand side active (the kernels may have flagged convergence)
+    HELM_CUDA_TRY(cudaMemcpyAsync(st.p, hs.data(), sizeof(RhsState) * nrhs, cudaMemcpyHostToDevice, s));
+    cudaEvent_t e0, e1;
+    HELM_CUDA_TRY(cudaEventCreate(&e0));
+    HELM_CUDA_TRY(cudaEventCreate(&e1));
+    HELM_CUDA_TRY(cudaEventRecord(e0, s));
+    for (int k = 0; k < reps; ++k) launch();
+    HELM_CUDA_TRY(cudaEventRecord(e1, s));
+    HELM_CUDA_TRY(cudaEventSynchronize(e1));
+    float t = 0.f;
+    cudaEventElapsedTime(&t, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    HELM_CUDA_TRY(cudaGetLastError());
+    *ms = (double)t / reps;
+    return HELM_OK;
+}
+
+// ------------------------------------------------------------ gradient
+// Forward half of the misfit gradient (Eq. 4): all shots and frequencies in one
+// batch, u kept on the device for the adjoint half.
+int fwi_forward(const helm_model* m, cudaStream_t s, int nfreq, const double* omega, int nshot, const int* src_flat_h,
+                int nrec, const int* rec_flat_h, const double* d_obs_dev, double lam, double* J_out, double* d_cal_dev,
+                const helm_solve_opts& o, helm_solve_stats* stats, FwiState** out) {
+    *out = nullptr;
+    const int nrhs = nfreq * nshot;
+    const size_t n = m->n();
+    std::unique_ptr<FwiState> st(new FwiState());
+    st->m = m;
+    st->nrhs = nrhs;
+    st->nrec = nrec;
+    st->w2.resize(nrhs);
+    st->hw2.resize(nrhs);
+    std::vector<int> src(nrhs);
+    for (int f = 0; f < nfreq; ++f)
+        for (int k = 0; k < nshot; ++k) {
+            st->w2[f * nshot + k] = omega[f] * omega[f];
+            st->hw2[f * nshot + k] = m->h * m->h * omega[f] * omega[f];
+            src[f * nshot + k] = src_flat_h[k];
+        }
+    auto am = [&](void** p, size_t b) {
+        if (cudaMalloc(p, b ? b : 16) != cudaSuccess) { cudaGetLastError(); return false; }
+        return true;
+    };
+    if (!am((void**)&st->u64, sizeof(double) * 2 * n * nrhs) || !am((void**)&st->resid, sizeof(double) * 2 * (size_t)nrec * nrhs) ||
+        !am((void**)&st->drec, sizeof(int) * nrec) || !am((void**)&st->dw2, sizeof(double) * nrhs)) {
+        set_last_error("device allocation failed");
+        return HELM_E_NOMEM;
+    }
+    DBuf f64, dsrc, jpart;
+    TRY_ALLOC(f64, sizeof(double) * 2 * n * nrhs, s);
+    TRY_ALLOC(dsrc, sizeof(int) * nrhs, s);
+    TRY_ALLOC(jpart, sizeof(double) * nrhs, s);
+    HELM_CUDA_TRY(cudaMemcpyAsync(dsrc.p, src.data(), sizeof(int) * nrhs, cudaMemcpyHostToDevice, s));
+    HELM_CUDA_TRY(cudaMemcpyAsync(st->drec, rec_flat_h, sizeof(int) * nrec, cudaMemcpyHostToDevice, s));
+    HELM_CUDA_TRY(cudaMemcpyAsync(st->dw2, st->w2.data(), sizeof(double) * nrhs, cudaMemcpyHostToDevice, s));
+    launch_point_rhs(f64.as<double>(), dsrc.as<int>(), nrhs, n, s);
+    int rc = solve_batch(m, s, nrhs, st->hw2.data(), f64.as<double>(), st->u64, o, stats);
+    if (rc != HELM_OK && rc != HELM_E_NOT_CONVERGED) return rc;
+    launch_sample(st->u64, st->drec, nrec, d_obs_dev, d_cal_dev, st->resid, jpart.as<double>(), n, nrhs, s);
+    HELM_CUDA_TRY(cudaGetLastError());
+    std::vector<double> jp(nrhs);
+    HELM_CUDA_TRY(cudaMemcpyAsync(jp.data(), jpart.p, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, s));
+    HELM_CUDA_TRY(cudaStreamSynchronize(s));
+    double J = 0.0;
+    for (int b = 0; b < nrhs; ++b) J += jp[b];
+    st->lam = lam;
+    *J_out = J + lam * m->msq_sum;
+    *out = st.release();
+    return rc;
+}
+
+// Adjoint half (Eq. 7): B w = conj(P^T r) per shot and frequency (lambda =
+// conj(w) because B is complex symmetric), then the gradient accumulation and
+// the fold of the layer onto the physical cells.
+int fwi_backward(FwiState* st, cudaStream_t s, double* grad_dev, const helm_solve_opts& o, helm_solve_stats* stats) {
+    const helm_model* m = st->m;
+    const int nrhs = st->nrhs;
+    const size_t n = m->n();
+    DBuf f64, w64, gpad;
+    TRY_ALLOC(f64, sizeof(double) * 2 * n * nrhs, s);
+    TRY_ALLOC(w64, sizeof(double) * 2 * n * nrhs, s);
+    TRY_ALLOC(gpad, sizeof(double) * n, s);
+    HELM_CUDA_TRY(cudaMemsetAsync(gpad.p, 0, sizeof(double) * n, s));
+    launch_adjoint_rhs(st->resid, st->drec, st->nrec, m->h * m->h, f64.as<double>(), n, nrhs, s);
+    int rc = solve_batch(m, s, nrhs, st->hw2.data(), f64.as<double>(), w64.as<double>(), o, stats);
+    if (rc != HELM_OK && rc != HELM_E_NOT_CONVERGED) return rc;
+    launch_grad_accum(st->u64, w64.as<double>(), st->dw2, m->m_pad, m->nx, m->nz, m->npml, m->alpha_max,
+                      gpad.as<double>(), nrhs, s);
+    launch_fold(gpad.as<double>(), m->m_pad, m->Px, m->Pz, m->npml, st->lam, grad_dev, s);
+    HELM_CUDA_TRY(cudaGetLastError());
+    HELM_CUDA_TRY(cudaStreamSynchronize(s));
+    return rc;
+}
+
+void fwi_free(FwiState* st) {
+    if (!st) return;
+    if (st->u64) cudaFree(st->u64);
+    if (st->resid) cudaFree(st->resid);
+    if (st->drec) cudaFree(st->drec);
+    if (st->dw2) cudaFree(st->dw2);
+    delete st;
+}
+
+}  // namespace helm

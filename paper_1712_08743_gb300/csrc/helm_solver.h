@@ -1,0 +1,53 @@
+// helm_solver.h - entry points of the batched solver used by the C ABI and the
+// serving scheduler.
+#pragma once
+
+#include "helm_internal.h"
+
+namespace helm {
+
+const char* last_error();
+void count_launches(unsigned long long k);   // kernels launched by this library (profiling)
+unsigned long long launches();
+
+// Solves A u_b = f_b (grid-scaled, f64 device [nrhs][n] c128) for every right-hand
+// side b; h_w2[b] = (h_b omega_b)^2 on the host, h_b the fine spacing of its model
+// and omega_b its angular frequency. u64 is a device [nrhs][n] c128 output.
+// Synchronous on `s`.
+int solve_batch(const helm_model* m, cudaStream_t s, int nrhs, const double* h_w2, const double* f64, double* u64,
+                const helm_solve_opts& o, helm_solve_stats* stats);
+
+// Device bytes a batch of nrhs solves on an nx x nz grid needs (upper estimate).
+size_t solve_bytes(int nx, int nz, int extra, int nrhs, int precision);
+
+int vcycle_once(const helm_model* m, cudaStream_t s, int nrhs, const double* h_w2, double b1, double b2, double wj,
+                const float* r, float* z);
+
+// Misfit (Eq. 4) and its gradient (Eq. 7), split so that an autograd backward
+// runs the adjoint solves: fwi_forward keeps the wavefields and data residuals
+// on the device in a FwiState; fwi_backward consumes them.
+struct FwiState {
+    const helm_model* m = nullptr;
+    int nrhs = 0, nrec = 0;
+    double lam = 0;
+    std::vector<double> w2, hw2;
+    double* u64 = nullptr;    // device [nrhs][n] c128 forward wavefields
+    double* resid = nullptr;  // device [nrhs][nrec] c128 data residuals P u - d_obs
+    int* drec = nullptr;      // device [nrec] flat receiver nodes
+    double* dw2 = nullptr;    // device [nrhs] omega^2
+};
+int fwi_forward(const helm_model* m, cudaStream_t s, int nfreq, const double* omega, int nshot, const int* src_flat_h,
+                int nrec, const int* rec_flat_h, const double* d_obs_dev, double lam, double* J_out, double* d_cal_dev,
+                const helm_solve_opts& o, helm_solve_stats* stats, FwiState** out);
+int fwi_backward(FwiState* st, cudaStream_t s, double* grad_dev, const helm_solve_opts& o, helm_solve_stats* stats);
+void fwi_free(FwiState* st);
+
+int coarsest_points(const helm_model* m);
+
+int time_kernel(const helm_model* m, cudaStream_t s, int kernel, int nrhs, double hw2, int reps, double* ms,
+                double* bytes);
+
+int create_model(helm_ctx* ctx, cudaStream_t s, int Px, int Pz, double h, const double* slowness, int nmodels,
+                 int npml, double alpha_max, helm_model** out);
+
+}  // namespace helm

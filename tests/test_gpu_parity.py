@@ -1,0 +1,236 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle.
+
+Tolerances (relative L2 unless stated): operator apply 1e-13 (FP64) / 2e-6 (FP32);
+V-cycle 2e-5 (complex64 against a complex128 restatement); wavefields 1e-6 for
+FP64 and FP64-refined solves, 1e-4 for pure complex64 solves; gradient 1e-5.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import multigrid as mg
+from synth import models
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def hg():
+    import paper_1712_08743_gb300 as hg
+
+    hg.load(build_if_missing=True)
+    return hg
+
+
+@pytest.fixture(scope="module")
+def ctx(hg):
+    c = hg.Context(0)
+    yield c
+    c.close()
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b)))
+
+
+# grids: the small plain case, a ragged one (partial tiles, odd/even levels), the batched case
+GRIDS = [
+    ("c1", lambda: models.c1_model()),
+    ("ragged", lambda: models.Model("ragged", np.random.default_rng(11).uniform(1500, 3500, (23, 37)), 10.0,
+                                    np.array([[5, 2]]), np.array([7.0]), npml=10)),
+    ("c3", lambda: models.c3_model()),
+]
+
+
+@pytest.mark.parametrize("name,make", GRIDS)
+def test_apply_matches_oracle_operator(hg, ctx, name, make):
+    mdl = make()
+    model = hg.helm_create_model(ctx, mdl.slowness, mdl.h, mdl.npml, mdl.alpha_max)
+    rng = np.random.default_rng(1)
+    om = 2 * np.pi * np.array([3.0, 7.5])
+    u = models.random_complex(rng, (2, model.nz, model.nx))
+    m_pad = oracle.pad_slowness(mdl.slowness, mdl.npml)
+    alpha = oracle.damping_profile(mdl.Px, mdl.Pz, mdl.npml, mdl.alpha_max)
+    y64 = hg.helm_apply(model, om, u, hg.HELM_PREC_FP64)
+    u32 = u.astype(np.complex64)
+    y32 = hg.helm_apply(model, om, u32, hg.HELM_PREC_FP32)
+    for k in range(2):
+        B = oracle.operator(m_pad, mdl.h, om[k], alpha)
+        ref = (B @ u[k].ravel()).reshape(model.nz, model.nx)
+        assert rel(y64[k], ref) < 1e-13
+        ref32 = (B @ u32[k].astype(np.complex128).ravel()).reshape(model.nz, model.nx)
+        assert rel(y32[k], ref32) < 2e-6
+    model.close()
+
+
+@pytest.mark.parametrize("name,make", GRIDS)
+def test_vcycle_matches_restatement(hg, ctx, name, make):
+    mdl = make()
+    model = hg.helm_create_model(ctx, mdl.slowness, mdl.h, mdl.npml, mdl.alpha_max)
+    rng = np.random.default_rng(2)
+    om = 2 * np.pi * np.array([4.0, 6.0])
+    r = models.random_complex(rng, (2, model.nz, model.nx), np.complex64)
+    for beta, wj in [((1.0, 0.5), 0.8), ((1.0, 1.0), 0.6)]:
+        z = hg.helm_vcycle(model, om, r, beta, wj)
+        m2 = oracle.pad_slowness(mdl.slowness, mdl.npml) ** 2
+        assert len(mg.level_shapes(model.nx, model.nz)) == model.nlevels
+        for k in range(2):
+            V = mg.VCycle(m2, (mdl.h * om[k]) ** 2, beta, wj)
+            ref = V.apply(r[k].astype(np.complex128).ravel()).reshape(model.nz, model.nx)
+            assert rel(z[k], ref) < 2e-5, (name, beta, k, rel(z[k], ref))
+    model.close()
+
+
+@pytest.mark.parametrize("precision,tol,bound", [("fp64", 1e-10, 1e-6), ("mixed", 1e-10, 1e-6), ("fp32", 1e-5, 1e-4)])
+def test_c1_wavefield_matches_oracle(hg, ctx, precision, tol, bound):
+    mdl = models.c1_model()
+    model = hg.helm_create_model(ctx, mdl.slowness, mdl.h, mdl.npml, mdl.alpha_max)
+    u, stats, st = hg.helm_solve(model, mdl.omegas, mdl.sources, opts=dict(tol=tol, precision=precision))
+    ref = oracle.solve_fields(mdl.slowness, mdl.h, mdl.omegas[0], mdl.sources, mdl.npml, mdl.alpha_max)
+    assert st == hg.HELM_OK and stats[0]["converged"] and stats[0]["relres"] <= tol, stats
+    assert rel(u, ref) < bound, rel(u, ref)
+    # physical part alone, as reported
+    p = slice(mdl.npml, -mdl.npml)
+    assert rel(u[0][p, p], ref[0][p, p]) < bound
+    model.close()
+
+
+def test_ragged_grid_general_rhs(hg, ctx):
+    mdl = GRIDS[1][1]()
+    model = hg.helm_create_model(ctx, mdl.slowness, mdl.h, mdl.npml, mdl.alpha_max)
+    rng = np.random.default_rng(3)
+    F = models.random_complex(rng, (3, model.nz, model.nx))
+    om = 2 * np.pi * np.array([2.0, 7.0, 13.0])
+    for precision in ("fp64", "mixed"):
+        u, stats, st = hg.helm_solve(model, om, f=F, opts=dict(tol=1e-11, precision=precision))
+        for k in range(3):
+            ref = oracle.solve_fields(mdl.slowness, mdl.h, om[k], None, mdl.npml, mdl.alpha_max,
+                                      F=F[k].reshape(1, -1))[0]
+            assert rel(u[k], ref) < 1e-6, (precision, k, rel(u[k], ref))
+    model.close()
+
+
+def test_batch_equals_each_alone_and_oracle(hg, ctx):
+    mdl = models.c3_model()
+    model = hg.helm_create_model(ctx, mdl.slowness, mdl.h, mdl.npml, mdl.alpha_max)
+    shots = mdl.sources[[0, 31, 63]]
+    om = np.repeat(mdl.omegas[[0, 4]], 3)
+    src = np.tile(shots, (2, 1))
+    opts = dict(tol=1e-10)
+    ub, sb, _ = hg.helm_solve(model, om, src, opts=opts)
+    for k in (0, 4):
+        ua, sa, _ = hg.helm_solve(model, om[k:k + 1], src[k:k + 1], opts=opts)
+        assert np.array_equal(ua[0], ub[k]) and sa[0]["iters"] == sb[k]["iters"]
+    for k in (0, 5):
+        ref = oracle.solve_fields(mdl.slowness, mdl.h, om[k], src[k:k + 1], mdl.npml, mdl.alpha_max)[0]
+        assert rel(ub[k], ref) < 1e-6
+    model.close()
+
+
+def test_not_converged_status_and_best_iterate(hg, ctx):
+    mdl = models.c1_model()
+    model = hg.helm_create_model(ctx, mdl.slowness, mdl.h, mdl.npml, mdl.alpha_max)
+    u, stats, st = hg.helm_solve(model, mdl.omegas, mdl.sources, opts=dict(tol=1e-10, max_it=4, check_every=2))
+    assert st == hg.HELM_E_NOT_CONVERGED
+    assert not stats[0]["converged"] and 0 < stats[0]["iters"] <= 4 + 2 and 0 < stats[0]["relres"] < 1
+    assert np.all(np.isfinite(u))
+    model.close()
+
+
+def test_invalid_arguments(hg, ctx):
+    m = np.full((30, 30), 1 / 2000.0)
+    m[3, 4] = np.nan
+    with pytest.raises(hg.HelmError):
+        hg.helm_create_model(ctx, m, 10.0)
+    model = hg.helm_create_model(ctx, np.full((30, 30), 1 / 2000.0), 10.0, 10)
+    with pytest.raises(hg.HelmError):
+        hg.helm_solve(model, [2 * np.pi * 5], [[30, 0]])
+    with pytest.raises(hg.HelmError):
+        hg.helm_solve(model, [-1.0], [[3, 0]])
+    model.close()
+
+
+def _small_fwi(seed=0):
+    rng = np.random.default_rng(seed)
+    Px, Pz, h, npml = 48, 32, 10.0, 10
+    c_true = models.layered_model(rng, Px, Pz, h, 4)
+    c0 = np.full_like(c_true, c_true.mean())
+    src = np.array([[6, 1], [24, 1], [40, 1]])
+    rec = np.array([[i, 1] for i in range(0, Px, 4)])
+    om = 2 * np.pi * np.array([6.0, 9.0])
+    d_obs = np.stack([oracle.sample_receivers(oracle.solve_fields(1 / c_true, h, w, src, npml), rec, npml) for w in om])
+    return 1 / c0, h, npml, src, rec, om, d_obs
+
+
+def test_gradient_matches_oracle_and_differences(hg, ctx):
+    m0, h, npml, src, rec, om, d_obs = _small_fwi()
+    lam = 1e-3
+    model = hg.helm_create_model(ctx, m0, h, npml, 0.5)
+    opts = dict(tol=1e-12)
+    J, g, dcal, stats, st = hg.helm_adjoint_gradient(model, om, src, rec, d_obs, lam, opts)
+    Jr, gr = oracle.gradient(m0, h, om, src, rec, d_obs, lam, npml)
+    assert abs(J - Jr) / Jr < 1e-8
+    assert rel(g, gr) < 1e-5
+    # central differences of the GPU misfit at three cells (one on the edge)
+    for (iz, ix) in [(0, 0), (10, 20), (31, 47)]:
+        e = 1e-4 * m0[iz, ix]
+        Js = []
+        for sgn in (1, -1):
+            mp = m0.copy()
+            mp[iz, ix] += sgn * e
+            mm = hg.helm_create_model(ctx, mp, h, npml, 0.5)
+            Js.append(hg.helm_adjoint_gradient(mm, om, src, rec, d_obs, lam, opts)[0])
+            mm.close()
+        fd = (Js[0] - Js[1]) / (2 * e)
+        assert abs(fd - g[iz, ix]) / abs(g[iz, ix]) < 1e-4, ((iz, ix), fd, g[iz, ix])
+    model.close()
+
+
+def test_autograd_backward_runs_adjoint(hg, ctx):
+    import torch
+
+    from paper_1712_08743_gb300.autograd import FWIProblem, HelmFWI
+
+    m0, h, npml, src, rec, om, d_obs = _small_fwi(1)
+    prob = FWIProblem(ctx, h, om, src, rec, d_obs, 1e-3, npml, 0.5, dict(tol=1e-12))
+    m = torch.tensor(m0, dtype=torch.float64, device="cuda", requires_grad=True)
+    J = HelmFWI.apply(m, prob)
+    J.backward()
+    Jr, gr = oracle.gradient(m0, h, om, src, rec, d_obs, 1e-3, npml)
+    assert abs(J.item() - Jr) / Jr < 1e-8
+    assert rel(m.grad.cpu().numpy(), gr) < 1e-5
+
+
+def test_served_results_equal_lone_solves(hg):
+    ctx = hg.Context(0)
+    hg.helm_serve_config(ctx, max_batch=4, max_slots=2)
+    reqs = []
+    for i in range(6):
+        n = 64 if i % 2 == 0 else 96
+        rng = np.random.default_rng(100 + i)
+        f = float(rng.uniform(3, 8))
+        h = 1500.0 / (12 * f)
+        c = models.layered_model(rng, n, n, h, 5)
+        reqs.append((1 / c, h, 2 * np.pi * f, (n // 2, 2)))
+    opts = dict(tol=1e-8)
+    tickets = [hg.helm_submit(ctx, m, h, w, s, opts=opts) for (m, h, w, s) in reqs]
+    served = [hg.helm_poll(ctx, t, 120000) for t in tickets]
+    for (m, h, w, s), res, t in zip(reqs, served, tickets):
+        assert res is not None and res.status == hg.HELM_OK and res.latency_ms >= res.queue_ms >= 0
+        model = hg.helm_create_model(ctx, m, h)
+        u, st, _ = hg.helm_solve(model, [w], [s], opts=opts)
+        assert rel(res.u, u[0]) < 1e-8
+        model.close()
+        hg.helm_release(ctx, t)
+    assert max(r.batch_size for r in served) >= 2
+    ctx.close()
+
+
+def test_serving_refuses_what_cannot_fit(hg):
+    ctx = hg.Context(0)
+    hg.helm_serve_config(ctx, max_batch=4, max_slots=1, reserve_bytes=0, budget_bytes=1 << 20)
+    m = np.full((200, 200), 1 / 2000.0)
+    t = hg.helm_submit(ctx, m, 10.0, 2 * np.pi * 5, (100, 2))
+    res = hg.helm_poll(ctx, t, 60000)
+    assert res is not None and res.status == hg.HELM_E_NOMEM
+    ctx.close()

@@ -1,0 +1,68 @@
+"""Pins for the CPU restatement of the multigrid preconditioner (oracle/multigrid.py).
+
+The restatement is checked against facts independent of its code: full weighting
+is a quarter of the transpose of bilinear interpolation, interpolation is exact
+for linear functions, the V-cycle used as a stationary iteration converges to
+the direct solution of M u = f, and damped Jacobi damps the checkerboard mode.
+"""
+import numpy as np
+import scipy.sparse.linalg as spla
+
+from oracle import multigrid as mg
+from synth import models
+
+
+def test_level_shapes_rule():
+    assert mg.level_shapes(141, 141)[-1] == (8, 8)
+    assert mg.level_shapes(441, 241) == [(441, 241), (220, 120), (110, 60), (55, 30), (27, 15), (13, 7)]
+    assert mg.level_shapes(1041, 1041)[-1] == (8, 8)
+    s = mg.level_shapes(1064, 1064)
+    assert all(a[0] // 2 == b[0] for a, b in zip(s, s[1:]))
+
+
+def test_full_weighting_is_quarter_transpose_of_bilinear():
+    for nx, nz in [(9, 7), (10, 8), (17, 12), (6, 11)]:
+        P = mg.prolongation(nx, nz).toarray()
+        R = mg.full_weighting(nx, nz).toarray()
+        np.testing.assert_allclose(R, P.T / 4.0, rtol=0, atol=1e-15)
+
+
+def test_bilinear_reproduces_linear_functions():
+    nx, nz = 21, 15
+    nxc, nzc = nx // 2, nz // 2
+    Xc, Zc = np.meshgrid(2 * np.arange(nxc) + 1.0, 2 * np.arange(nzc) + 1.0)
+    a, b, c = 0.3, -1.7, 2.2
+    u = mg.prolongation(nx, nz) @ (a + b * Xc + c * Zc).ravel()
+    X, Z = np.meshgrid(np.arange(nx, dtype=float), np.arange(nz, dtype=float))
+    exact = a + b * X + c * Z
+    inner = (X >= 1) & (X <= 2 * nxc - 1) & (Z >= 1) & (Z <= 2 * nzc - 1)
+    np.testing.assert_allclose(u.reshape(nz, nx)[inner], exact[inner], rtol=0, atol=1e-12)
+
+
+def test_vcycle_iteration_converges_to_direct_solution():
+    rng = np.random.default_rng(4)
+    mdl = models.c1_model()
+    m_pad = np.pad(mdl.slowness, 20, mode="edge")
+    hw2 = (mdl.h * mdl.omegas[0]) ** 2
+    V = mg.VCycle(m_pad ** 2, hw2, beta=(1.0, 0.5))
+    M = V.M[0]
+    f = models.random_complex(rng, M.shape[0])
+    exact = spla.spsolve(M.tocsc(), f)
+    u = np.zeros_like(f)
+    errs = []
+    for _ in range(200):
+        u = u + V.apply(f - M @ u)
+        errs.append(np.linalg.norm(u - exact) / np.linalg.norm(exact))
+    assert errs[-1] < 1e-6, errs[::20]
+    assert all(b < a for a, b in zip(errs[::20], errs[20::20]))
+
+
+def test_jacobi_damps_checkerboard():
+    nx = nz = 33
+    m2 = np.full((nz, nx), (1 / 2000.0) ** 2)
+    M = mg.shifted_laplacian(m2, (10.0 * 2 * np.pi * 5.0) ** 2, complex(1.0, -0.5))
+    D = M.diagonal()
+    X, Z = np.meshgrid(np.arange(nx), np.arange(nz))
+    e = ((-1.0) ** (X + Z)).ravel().astype(complex)
+    e2 = e - 0.8 * (M @ e) / D       # error propagation of one sweep for M u = 0
+    assert np.linalg.norm(e2) < 0.7 * np.linalg.norm(e)
