@@ -63,20 +63,19 @@ __device__ __forceinline__ void stc(double* p, size_t i, cx<double> a) {
 // ------------------------------------------------------------ damping layer
 // alpha of Eq. 2 at padded node (ix, iz): alpha_max (d / npml)^2 with d the
 // node distance into the layer, the larger of the two axes in corners.
-__host__ __device__ __forceinline__ double layer_alpha(int ix, int iz, int nx, int nz, int npml,
-                                                      double alpha_max) {
-    if (npml <= 0) return 0.0;
-    int dx = npml - ix;
-    int t = ix - (nx - 1 - npml);
-    dx = dx > t ? dx : t;
-    int dz = npml - iz;
-    t = iz - (nz - 1 - npml);
-    dz = dz > t ? dz : t;
-    int d = dx > dz ? dx : dz;
-    if (d <= 0) return 0.0;
-    double r = double(d) / double(npml);
-    return alpha_max * r * r;
+// Same profile from the integer layer depth, with acoef = alpha_max / npml^2
+// precomputed on the host: no division on the device, in the kernel's precision.
+__device__ __forceinline__ int layer_depth(int ix, int iz, int nx, int nz, int npml) {
+    const int dx = max(npml - ix, ix - (nx - 1 - npml));
+    const int dz = max(npml - iz, iz - (nz - 1 - npml));
+    return max(max(dx, dz), 0);
 }
+template <typename T>
+__device__ __forceinline__ T layer_alpha_t(int ix, int iz, int nx, int nz, int npml, T acoef) {
+    const int d = layer_depth(ix, iz, nx, nz, npml);
+    return acoef * (T)(d * d);
+}
+inline double layer_coef(int npml, double alpha_max) { return npml > 0 ? alpha_max / ((double)npml * npml) : 0.0; }
 
 // ------------------------------------------------------- solver state per RHS
 enum RhsFlag : int { FLAG_RUNNING = 0, FLAG_CONVERGED = 1, FLAG_BREAKDOWN = 2, FLAG_MAXIT = 3 };

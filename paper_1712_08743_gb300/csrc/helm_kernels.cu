@@ -88,7 +88,7 @@ void launch_inject(const Level& fine, const Level& coarse, int nmodels, cudaStre
 // ============================================================ stencil apply
 // y = scale * A u on the fine grid (with the damping layer).
 template <typename T>
-__global__ void __launch_bounds__(256) k_apply(LevelDev L, int npml, double amax, const double* __restrict__ w2,
+__global__ void __launch_bounds__(256) k_apply(LevelDev L, int npml, double acoef, const double* __restrict__ w2,
                                                const T* __restrict__ u, T* __restrict__ y, T scale) {
     const int b = blockIdx.z;
     const int ix = blockIdx.x * 32 + threadIdx.x, iz = blockIdx.y * 8 + threadIdx.y;
@@ -98,7 +98,7 @@ __global__ void __launch_bounds__(256) k_apply(LevelDev L, int npml, double amax
     const size_t i = (size_t)iz * L.nx + ix;
     const T hw = (T)(L.h2 * w2[b]);
     const T s = hw * (m2ptr<T>(L) + (size_t)b * L.mstride)[i];
-    const T a = (T)layer_alpha(ix, iz, L.nx, L.nz, npml, amax);
+    const T a = layer_alpha_t<T>(ix, iz, L.nx, L.nz, npml, (T)acoef);
     cx<T> c = ldc(ub, i);
     cx<T> acc((T(4) - s) * c.re - s * a * c.im, (T(4) - s) * c.im + s * a * c.re);  // (4 - s(1 - j a)) u
     if (ix > 0) acc = acc - ldc(ub, i - 1);
@@ -112,7 +112,7 @@ template <typename T>
 void launch_apply(const LevelDev& L0, int npml, double amax, const double* w2, const T* u, T* y, T scale,
                   int nrhs, cudaStream_t s) {
     dim3 blk(32, 8), grd((L0.nx + 31) / 32, (L0.nz + 7) / 8, nrhs);
-    k_apply<T><<<grd, blk, 0, s>>>(L0, npml, amax, w2, u, y, scale);
+    k_apply<T><<<grd, blk, 0, s>>>(L0, npml, layer_coef(npml, amax), w2, u, y, scale);
 }
 template void launch_apply<float>(const LevelDev&, int, double, const double*, const float*, float*, float, int, cudaStream_t);
 template void launch_apply<double>(const LevelDev&, int, double, const double*, const double*, double*, double, int, cudaStream_t);
@@ -121,7 +121,7 @@ template void launch_apply<double>(const LevelDev&, int, double, const double*, 
 // r = f - A u in FP64; writes the inner right-hand side rin = r in precision TI
 // and decides, per right-hand side, whether refinement continues.
 template <typename TI>
-__global__ void __launch_bounds__(256) k_resid64(LevelDev L, int npml, double amax, const double* __restrict__ w2,
+__global__ void __launch_bounds__(256) k_resid64(LevelDev L, int npml, double acoef, const double* __restrict__ w2,
                                                  const double* __restrict__ f, const double* __restrict__ u,
                                                  TI* __restrict__ rin, double* partials, int pstride, RhsState* st,
                                                  double tol, double inner_floor, int first) {
@@ -136,7 +136,7 @@ __global__ void __launch_bounds__(256) k_resid64(LevelDev L, int npml, double am
         const double* ub = u + 2 * n * b;
         const size_t i = (size_t)iz * L.nx + ix;
         const double s = L.h2 * w2[b] * (static_cast<const double*>(L.m2) + (size_t)b * L.mstride)[i];
-        const double a = layer_alpha(ix, iz, L.nx, L.nz, npml, amax);
+        const double a = layer_alpha_t<double>(ix, iz, L.nx, L.nz, npml, acoef);
         cx<double> c = ldc(ub, i);
         cx<double> acc((4.0 - s) * c.re - s * a * c.im, (4.0 - s) * c.im + s * a * c.re);
         if (ix > 0) acc = acc - ldc(ub, i - 1);
@@ -171,7 +171,7 @@ void launch_resid64(const LevelDev& L0, int npml, double amax, const double* w2,
                     TI* rin, double* partials, int pstride, RhsState* st, double tol, double inner_floor, int first,
                     int nrhs, cudaStream_t s) {
     dim3 blk(32, 8), grd((L0.nx + 31) / 32, (L0.nz + 7) / 8, nrhs);
-    k_resid64<TI><<<grd, blk, 0, s>>>(L0, npml, amax, w2, f, u, rin, partials, pstride, st, tol, inner_floor, first);
+    k_resid64<TI><<<grd, blk, 0, s>>>(L0, npml, layer_coef(npml, amax), w2, f, u, rin, partials, pstride, st, tol, inner_floor, first);
 }
 template void launch_resid64<float>(const LevelDev&, int, double, const double*, const double*, const double*, float*, double*, int, RhsState*, double, double, int, int, cudaStream_t);
 template void launch_resid64<double>(const LevelDev&, int, double, const double*, const double*, const double*, double*, double*, int, RhsState*, double, double, int, int, cudaStream_t);
@@ -412,7 +412,7 @@ void launch_restrict(const LevelDev& Lf, const LevelDev& Lc, const double* w2, d
 template <typename T> struct PTile { static constexpr int X = sizeof(T) == 4 ? 64 : 32, Z = 16; };
 
 template <typename T, int MODE>
-__global__ void __launch_bounds__(256) k_prolong(LevelDev Lf, LevelDev Lc, int npml, double amax,
+__global__ void __launch_bounds__(256) k_prolong(LevelDev Lf, LevelDev Lc, int npml, double acoef,
                                                  const double* __restrict__ w2, T b1, T b2, T wj,
                                                  const T* __restrict__ f, const T* __restrict__ ec,
                                                  T* __restrict__ out, T* __restrict__ y, const T* __restrict__ aux,
@@ -524,7 +524,7 @@ __global__ void __launch_bounds__(256) k_prolong(LevelDev Lf, LevelDev Lc, int n
             const int sx = tx + 1, sz = tz + 1;
             const size_t i = (size_t)gz * Lf.nx + gx;
             const T s = hw * __ldg(m2 + i);
-            const T a = (T)layer_alpha(gx, gz, Lf.nx, Lf.nz, npml, amax);
+            const T a = layer_alpha_t<T>(gx, gz, Lf.nx, Lf.nz, npml, (T)acoef);
             const cx<T> c = U3[sz][sx];
             cx<T> yv((T(4) - s) * c.re - s * a * c.im, (T(4) - s) * c.im + s * a * c.re);
             yv = yv - U3[sz][sx - 1] - U3[sz][sx + 1] - U3[sz - 1][sx] - U3[sz + 1][sx];
@@ -572,11 +572,11 @@ void launch_prolong(int mode, const LevelDev& Lf, const LevelDev& Lc, int npml, 
     constexpr int PFX = PTile<T>::X, PFZ = PTile<T>::Z;
     dim3 grd((Lf.nx + PFX - 1) / PFX, (Lf.nz + PFZ - 1) / PFZ, nrhs);
     if (mode == 0)
-        k_prolong<T, 0><<<grd, 256, 0, s>>>(Lf, Lc, npml, amax, w2, (T)b1, (T)b2, (T)wj, f, ec, out, y, aux, partials, pstride, st);
+        k_prolong<T, 0><<<grd, 256, 0, s>>>(Lf, Lc, npml, layer_coef(npml, amax), w2, (T)b1, (T)b2, (T)wj, f, ec, out, y, aux, partials, pstride, st);
     else if (mode == 1)
-        k_prolong<T, 1><<<grd, 256, 0, s>>>(Lf, Lc, npml, amax, w2, (T)b1, (T)b2, (T)wj, f, ec, out, y, aux, partials, pstride, st);
+        k_prolong<T, 1><<<grd, 256, 0, s>>>(Lf, Lc, npml, layer_coef(npml, amax), w2, (T)b1, (T)b2, (T)wj, f, ec, out, y, aux, partials, pstride, st);
     else
-        k_prolong<T, 2><<<grd, 256, 0, s>>>(Lf, Lc, npml, amax, w2, (T)b1, (T)b2, (T)wj, f, ec, out, y, aux, partials, pstride, st);
+        k_prolong<T, 2><<<grd, 256, 0, s>>>(Lf, Lc, npml, layer_coef(npml, amax), w2, (T)b1, (T)b2, (T)wj, f, ec, out, y, aux, partials, pstride, st);
 }
 
 // ======================================================= V-cycle: coarsest
@@ -812,12 +812,12 @@ void launch_adjoint_rhs(const double* resid, const int* rec_flat, int nrec, doub
 
 // g_pad += sum_b 4 w_b^2 m Re[(1 - j alpha) u_b w_b], w_b = conj(lambda_b) = B^{-1} conj(P^T r_b).
 __global__ void k_grad_accum(const double* __restrict__ u, const double* __restrict__ wv, const double* __restrict__ w2,
-                             const double* __restrict__ m_pad, int nx, int nz, int npml, double amax,
+                             const double* __restrict__ m_pad, int nx, int nz, int npml, double acoef,
                              double* __restrict__ g_pad, int nrhs) {
     const size_t n = (size_t)nx * nz;
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
         const int ix = (int)(i % nx), iz = (int)(i / nx);
-        const double a = layer_alpha(ix, iz, nx, nz, npml, amax);
+        const double a = layer_alpha_t<double>(ix, iz, nx, nz, npml, acoef);
         double acc = 0.0;
         for (int b = 0; b < nrhs; ++b) {
             const cx<double> uu = ldc(u, n * b + i), ww = ldc(wv, n * b + i);
@@ -830,7 +830,7 @@ __global__ void k_grad_accum(const double* __restrict__ u, const double* __restr
 
 void launch_grad_accum(const double* u, const double* w, const double* w2, const double* m_pad, int nx, int nz,
                        int npml, double amax, double* g_pad, int nrhs, cudaStream_t s) {
-    k_grad_accum<<<grid1d((size_t)nx * nz), 256, 0, s>>>(u, w, w2, m_pad, nx, nz, npml, amax, g_pad, nrhs);
+    k_grad_accum<<<grid1d((size_t)nx * nz), 256, 0, s>>>(u, w, w2, m_pad, nx, nz, npml, layer_coef(npml, amax), g_pad, nrhs);
 }
 
 // g = E^T g_pad + 2 lam m on the physical cells: each edge cell also collects
