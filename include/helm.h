@@ -201,6 +201,26 @@ typedef enum {
 int helm_time_kernel(helm_model* model, int kernel, int nrhs, double omega, int reps, double* ms_per_launch,
                      double* bytes_per_launch);
 
+/* helm_vcycle for callers that cannot allocate device memory (no counterpart in
+ * the paper). helm_vcycle allocates its level vectors and the coarsest-level
+ * inverse on every call; this variant runs the same kernels, with the same
+ * result, on a fixed 64 MiB scratch array compiled into the library (present on
+ * every GPU that loads the library until the process exits), for code whose
+ * device memory is owned by another allocator or must not grow after start-up.
+ * It calls no cudaMalloc, cudaFree or other allocating routine.
+ *  - r, z: device pointers, complex64 [nrhs][nz][nx], on the context's device;
+ *    the call is synchronous on the context's stream. nrhs <= 256.
+ *  - Sizes whose level vectors and coarsest-level inverses do not fit in the
+ *    64 MiB return HELM_E_INVALID (helm_last_error() gives the bytes needed).
+ *  - The first call on a device looks up the scratch array's device address
+ *    (cudaGetSymbolAddress); make that first call before any stream capture.
+ *  - Every call on a device shares the one array and leaves its contents
+ *    behind; each call writes every byte it reads, so nothing needs clearing.
+ *    Calls that overlap on the GPU (other threads or streams) race: serialise
+ *    them. */
+int helm_vcycle_noalloc(helm_model* model, int nrhs, const double* omega, double beta1, double beta2,
+                        double omega_jacobi, const void* r, void* z);
+
 /* ---------------------------------------------------------------- serving
  * Continuous batching: requests enter a host queue; a scheduler thread admits
  * them while free device memory (minus a reserve) allows, groups requests of the

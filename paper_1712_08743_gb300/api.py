@@ -231,6 +231,20 @@ def helm_vcycle(model: Model, omega, r, beta=(1.0, 0.5), omega_jacobi: float = 0
     return z
 
 
+def helm_vcycle_noalloc(model: Model, omega, r, z, beta=(1.0, 0.5), omega_jacobi: float = 0.8):
+    """helm_vcycle on the library's fixed scratch array (no device allocation).
+
+    r, z: contiguous complex64 CUDA tensors [nrhs][nz][nx]; z is written in place.
+    For callers that must not allocate device memory; see include/helm.h.
+    """
+    om = _np(omega, np.float64).reshape(-1)
+    torch.cuda.synchronize()
+    st = model.lib.helm_vcycle_noalloc(model.handle, om.size, _ptr_d(om), float(beta[0]), float(beta[1]),
+                                       float(omega_jacobi), C.c_void_p(r.data_ptr()), C.c_void_p(z.data_ptr()))
+    check(st, "helm_vcycle_noalloc")
+    return z
+
+
 # ----------------------------------------------------------------- gradient
 def _geometry(omegas, src, rec):
     om = _np(omegas, np.float64).reshape(-1)
