@@ -44,6 +44,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--krylov", default="bicgstab", choices=["bicgstab", "fgmres"])
     return ap.parse_args()
 
 
@@ -171,7 +172,7 @@ def run_ours(args):
         import torch.distributed as dist
 
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    from paper_1712_08743_gb300 import _lib, api, build
+    from paper_1712_08743_gb300 import _lib, api, build, shard
     from synth import models
 
     build.build()
@@ -183,7 +184,8 @@ def run_ours(args):
     model = api.helm_create_model(ctx, mdl.slowness, mdl.h, mdl.npml, mdl.alpha_max)
     n = model.n
     om = mdl.omegas
-    opts = api.helm_default_opts(tol=1e-6, precision="mixed")
+    kry = {"bicgstab": _lib.HELM_KRYLOV_BICGSTAB, "fgmres": _lib.HELM_KRYLOV_FGMRES}[args.krylov]
+    opts = api.helm_default_opts(tol=1e-6, precision="mixed", krylov=kry)
     # device-resident input (point source, grid-scaled form is built by the library from f)
     f_host = np.zeros((1, model.nz, model.nx), np.complex128)
     sx, sz = mdl.sources[0]
@@ -220,12 +222,7 @@ def run_ours(args):
     clocks = clk.summary()
     ms = [a.elapsed_time(b) for a, b in ev]
     t_total = sum(ms) / 1e3
-    if world > 1:
-        import torch.distributed as dist
-
-        t = torch.tensor([t_total], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_total = float(t.item())
+    t_total = shard.allreduce_max(t_total)     # max over ranks (no-op at N = 1)
     value = world * args.steps / t_total
     conv = all(s["converged"] for s in stats_all)
 
@@ -244,7 +241,7 @@ def run_ours(args):
     # plain FP64 GPU solve of the same problem (the baseline the precision split must beat)
     fp64 = None
     if not args.no_fp64:
-        o64 = api.helm_default_opts(tol=1e-6, precision="fp64")
+        o64 = api.helm_default_opts(tol=1e-6, precision="fp64", krylov=kry)
         step(o64)
         t64 = []
         its64 = None
@@ -295,7 +292,8 @@ def run_ours(args):
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "grid": f"{model.nx}x{model.nz} padded ({mdl.Px}x{mdl.Pz} physical)",
                        "unknowns": n, "precision": "complex64 inner, FP64 residual/refinement",
-                       "krylov": "BiCGSTAB + V(1,1) shifted-Laplace MG, beta=(1,0.5)",
+                       "krylov": ("BiCGSTAB" if args.krylov == "bicgstab" else "FGMRES(30)") +
+                                 " + shifted-Laplace Galerkin MG (V above the tail level, F below), beta=(1,0.5)",
                        "levels": model.nlevels, "l2": "flushed between timed steps (258 MB write)",
                        "parallelism": f"replicas x{world}"},
             "p50_ms": float(np.percentile(ms, 50)), "p99_ms": float(np.percentile(ms, 99)),

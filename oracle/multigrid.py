@@ -1,26 +1,30 @@
 """CPU restatement of the shifted-Laplace multigrid preconditioner (complex128).
 
-TEST INFRASTRUCTURE ONLY: used by tests/ to check the CUDA V-cycle; never by the
-product path.
+TEST INFRASTRUCTURE ONLY: used by tests/ to check the CUDA preconditioner; never
+by the product path.
 
 The paper preconditions its Krylov data-modelling engine with a shifted-Laplace
 operator (Section "Full waveform inversion in the space-frequency domain", the
 paragraph after Eq. 9; shift "1 + j" in Section "Examples"). It does not say how
 the preconditioner is inverted. The reading used here, which the CUDA path
-implements, is one geometric multigrid V(1,1)-cycle per application:
+implements, is one multigrid cycle per application:
 
-* M_l = 4 - (neighbours) - (h_l omega)^2 m_l^2 (beta1 - j beta2), the grid-scaled
-  5-point shifted Laplacian on level l (no damping term), zero Dirichlet ghosts.
-* Level l + 1 has floor(n/2) nodes per axis; coarse node I sits on fine node 2I+1;
-  h_{l+1} = 2 h_l; coarse m^2 by injection. Coarsening stops once a level has at
-  most 128 nodes or an axis has fewer than 4; the coarsest level is solved exactly.
-* Pre-smoothing: one damped-Jacobi sweep from a zero guess, u = w_J D^-1 f.
-* Restriction: full weighting (1/16)[1 2 1; 2 4 2; 1 2 1] of the residual, times 4
-  because the coarse grid-scaled system carries h_{l+1}^2 = 4 h_l^2.
-* Prolongation: bilinear interpolation, then one post-smoothing Jacobi sweep.
+* Finest level: M_0 = 4 - (neighbours) - (h omega)^2 m^2 (beta1 - j beta2), the
+  grid-scaled 5-point shifted Laplacian (no damping term), zero Dirichlet ghosts.
+* Level l + 1 has floor(n/2) nodes per axis; coarse node I sits on fine node
+  2I+1. Coarsening stops once a level has at most 128 nodes or an axis has
+  fewer than 4.
+* Coarse operators are Galerkin products M_{l+1} = P^T M_l P with P bilinear
+  interpolation; restriction is P^T (full weighting times 4).
+* Smoother: damped Jacobi (default weight 0.5), one sweep before (from a zero
+  guess) and one after each coarse correction.
+* Cycle: a V-cycle on the levels above lt, the first level with at most 24576
+  nodes (lt >= 1); from lt down, an F-cycle whose second coarse correction is a
+  V-cycle; the coarsest level is solved exactly.
 
-Operators are explicit scipy.sparse matrices assembled node by node, so the
-restatement shares nothing with the fused CUDA kernels.
+Operators are explicit scipy.sparse matrices (Galerkin products by sparse
+matrix multiplication), so the restatement shares nothing with the fused CUDA
+kernels.
 """
 from __future__ import annotations
 
@@ -29,6 +33,7 @@ import scipy.sparse as sp
 import scipy.sparse.linalg as spla
 
 COARSE_MAX = 128
+TAIL_MAX = 24576
 
 
 def level_shapes(nx: int, nz: int):
@@ -89,31 +94,44 @@ def full_weighting(nxf: int, nzf: int) -> sp.csr_matrix:
     return sp.csr_matrix((vals, (rows, cols)), shape=(nxc * nzc, nxf * nzf))
 
 
-class VCycle:
-    """One V(1,1)-cycle approximating M^{-1} for grid-scaled (h omega)^2 = hw2."""
+def tail_level(shapes) -> int:
+    """First level (>= 1) with at most TAIL_MAX nodes: the F-cycle starts there."""
+    for l in range(1, len(shapes)):
+        if shapes[l][0] * shapes[l][1] <= TAIL_MAX:
+            return l
+    return len(shapes) - 1
 
-    def __init__(self, m2_pad: np.ndarray, hw2: float, beta=(1.0, 0.5), omega_jacobi: float = 0.8):
+
+class VCycle:
+    """One preconditioner application approximating M^{-1} for grid-scaled (h omega)^2 = hw2."""
+
+    def __init__(self, m2_pad: np.ndarray, hw2: float, beta=(1.0, 0.5), omega_jacobi: float = 0.5):
         nz, nx = m2_pad.shape
         self.wj = omega_jacobi
         bt = complex(beta[0], -beta[1])
-        self.M, self.P, self.R, self.shapes = [], [], [], level_shapes(nx, nz)
-        m2 = np.asarray(m2_pad, float)
-        for l, (lx, lz) in enumerate(self.shapes):
-            self.M.append(shifted_laplacian(m2, hw2 * 4.0 ** l, bt))
-            if l + 1 < len(self.shapes):
-                self.P.append(prolongation(lx, lz))
-                self.R.append(full_weighting(lx, lz))
-                m2 = m2[1::2, 1::2][: lz // 2, : lx // 2]
+        self.shapes = level_shapes(nx, nz)
+        self.lt = tail_level(self.shapes)
+        self.M = [shifted_laplacian(np.asarray(m2_pad, float), hw2, bt)]
+        self.P = []
+        for l, (lx, lz) in enumerate(self.shapes[:-1]):
+            P = prolongation(lx, lz)
+            self.P.append(P)
+            self.M.append((P.T @ self.M[-1] @ P).tocsr())
         self.coarse = spla.splu(sp.csc_matrix(self.M[-1]))
 
-    def apply(self, f: np.ndarray, level: int = 0) -> np.ndarray:
-        """z = V(f) for a flat complex vector on `level`."""
+    def cycle(self, f: np.ndarray, level: int, kind: str) -> np.ndarray:
+        """kind 'V' or 'F' from `level` with a zero initial guess."""
         if level == len(self.M) - 1:
             return self.coarse.solve(f)
-        M = self.M[level]
+        M, P = self.M[level], self.P[level]
         D = M.diagonal()
         u = self.wj * f / D
-        r = f - M @ u
-        e = self.apply(4.0 * (self.R[level] @ r), level + 1)
-        u = u + self.P[level] @ e
+        sub = "F" if kind == "F" else ("F" if level + 1 == self.lt else "V")
+        u = u + P @ self.cycle(P.T @ (f - M @ u), level + 1, sub)
+        if kind == "F":
+            u = u + P @ self.cycle(P.T @ (f - M @ u), level + 1, "V")
         return u + self.wj * (f - M @ u) / D
+
+    def apply(self, f: np.ndarray) -> np.ndarray:
+        """z = cycle(f) on the finest level: V above lt, F from lt down."""
+        return self.cycle(f, 0, "F" if self.lt == 0 else "V")

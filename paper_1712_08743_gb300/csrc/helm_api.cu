@@ -85,6 +85,17 @@ int create_model(helm_ctx* ctx, cudaStream_t s, int Px, int Pz, double h, const 
         delete m;
         return HELM_E_INVALID;
     }
+    const int L = (int)m->lv.size() - 1;
+    m->lf = L;
+    for (int l = 1; l <= L; ++l)
+        if (m->lv[l].n() <= (size_t)kFcycleMaxPoints) { m->lf = l; break; }
+    m->lt = L;
+    for (int l = m->lf; l <= L; ++l)
+        if (m->lv[l].n() <= (size_t)kTailMaxPoints) { m->lt = l; break; }
+    m->tail_smem32 = tail_smem_bytes(m, sizeof(float));
+    m->tail_smem64 = tail_smem_bytes(m, sizeof(double));
+    if (m->tail_smem64 > 227u * 1024u) { set_last_error("tail levels exceed shared memory"); delete m; return HELM_E_INVALID; }
+    if (L + 1 > kMaxLevels) { set_last_error("too many levels"); delete m; return HELM_E_INVALID; }
     auto fail = [&](cudaError_t e) {
         set_last_error(cudaGetErrorString(e));
         cudaGetLastError();
@@ -93,17 +104,29 @@ int create_model(helm_ctx* ctx, cudaStream_t s, int Px, int Pz, double h, const 
     };
     cudaError_t e = cudaMalloc(&m->m_pad, sizeof(double) * m->n() * nmodels);
     if (e != cudaSuccess) return fail(e);
-    for (auto& L : m->lv) {
-        if ((e = cudaMalloc(&L.m2f, sizeof(float) * L.n() * nmodels)) != cudaSuccess) return fail(e);
-        if ((e = cudaMalloc(&L.m2d, sizeof(double) * L.n() * nmodels)) != cudaSuccess) return fail(e);
+    if ((e = cudaMalloc(&m->lv[0].m2f, sizeof(float) * m->n() * nmodels)) != cudaSuccess) return fail(e);
+    if ((e = cudaMalloc(&m->lv[0].m2d, sizeof(double) * m->n() * nmodels)) != cudaSuccess) return fail(e);
+    for (int l = 1; l <= L; ++l) {
+        Level& Lv = m->lv[l];
+        if ((e = cudaMalloc(&Lv.gkf, sizeof(float) * kGalerkinCoefs * Lv.n() * nmodels)) != cudaSuccess) return fail(e);
+        if ((e = cudaMalloc(&Lv.gkd, sizeof(double) * kGalerkinCoefs * Lv.n() * nmodels)) != cudaSuccess) return fail(e);
     }
+    const std::vector<int> opsf = tail_schedule(m->lt, L, true), opsv = tail_schedule(m->lt, L, false);
+    m->nops_f = (int)opsf.size();
+    m->nops_v = (int)opsv.size();
+    if ((e = cudaMalloc(&m->ops_f, sizeof(int) * opsf.size())) != cudaSuccess) return fail(e);
+    if ((e = cudaMalloc(&m->ops_v, sizeof(int) * opsv.size())) != cudaSuccess) return fail(e);
     DevMem phys, msq;
     if ((e = cudaMalloc(&phys.p, sizeof(double) * np * nmodels)) != cudaSuccess) return fail(e);
     if ((e = cudaMalloc(&msq.p, sizeof(double))) != cudaSuccess) return fail(e);
     if ((e = cudaMemcpyAsync(phys.p, slowness, sizeof(double) * np * nmodels, cudaMemcpyHostToDevice, s)) != cudaSuccess)
         return fail(e);
+    if ((e = cudaMemcpyAsync(m->ops_f, opsf.data(), sizeof(int) * opsf.size(), cudaMemcpyHostToDevice, s)) != cudaSuccess)
+        return fail(e);
+    if ((e = cudaMemcpyAsync(m->ops_v, opsv.data(), sizeof(int) * opsv.size(), cudaMemcpyHostToDevice, s)) != cudaSuccess)
+        return fail(e);
     launch_pad_model(static_cast<double*>(phys.p), Px, Pz, npml, nmodels, m->m_pad, m->lv[0].m2f, m->lv[0].m2d, s);
-    for (size_t l = 1; l < m->lv.size(); ++l) launch_inject(m->lv[l - 1], m->lv[l], nmodels, s);
+    for (int l = 1; l <= L; ++l) launch_galerkin(m, l, s);
     launch_sumsq(static_cast<double*>(phys.p), np, static_cast<double*>(msq.p), s);
     if ((e = cudaMemcpyAsync(&m->msq_sum, msq.p, sizeof(double), cudaMemcpyDeviceToHost, s)) != cudaSuccess) return fail(e);
     if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return fail(e);
@@ -126,7 +149,7 @@ void helm_default_opts(helm_solve_opts* o) {
     o->precision = HELM_PREC_MIXED;
     o->beta1 = 1.0;
     o->beta2 = 0.5;
-    o->omega_jacobi = 0.8;
+    o->omega_jacobi = 0.5;
     o->inner_tol = 1e-4;
     o->max_outer = 20;
     o->check_every = 10;
@@ -193,9 +216,13 @@ void helm_destroy_model(helm_model* m) {
     if (!m) return;
     DeviceGuard g(m->ctx->device);
     if (m->m_pad) cudaFree(m->m_pad);
+    if (m->ops_f) cudaFree(m->ops_f);
+    if (m->ops_v) cudaFree(m->ops_v);
     for (auto& L : m->lv) {
         if (L.m2f) cudaFree(L.m2f);
         if (L.m2d) cudaFree(L.m2d);
+        if (L.gkf) cudaFree(L.gkf);
+        if (L.gkd) cudaFree(L.gkd);
     }
     delete m;
 }
@@ -214,7 +241,6 @@ int helm_solve(helm_model* m, int nrhs, const double* omega, const int* src_ix, 
     helm_solve_opts o;
     if (opts) o = *opts; else helm_default_opts(&o);
     if (check_opts(o) != HELM_OK) return HELM_E_INVALID;
-    if (o.krylov != HELM_KRYLOV_BICGSTAB) { set_last_error("FGMRES is not available in this build"); return HELM_E_INVALID; }
     std::vector<double> w2(nrhs);
     for (int b = 0; b < nrhs; ++b) {
         if (!finite_pos(omega[b])) return HELM_E_INVALID;
@@ -356,7 +382,7 @@ int helm_fwi_forward(helm_model* m, int nfreq, const double* omega, int nshot, c
     if (!std::isfinite(lambda_reg) || lambda_reg < 0.0) return HELM_E_INVALID;
     helm_solve_opts o;
     if (opts) o = *opts; else helm_default_opts(&o);
-    if (check_opts(o) != HELM_OK || o.krylov != HELM_KRYLOV_BICGSTAB) return HELM_E_INVALID;
+    if (check_opts(o) != HELM_OK) return HELM_E_INVALID;
     for (int f = 0; f < nfreq; ++f)
         if (!finite_pos(omega[f])) return HELM_E_INVALID;
     std::vector<int> sf(nshot), rf(nrec);
@@ -403,7 +429,7 @@ int helm_fwi_backward(helm_fwi_state* state, double* grad_out, const helm_solve_
     if (!state || !state->st || !grad_out) return HELM_E_INVALID;
     helm_solve_opts o;
     if (opts) o = *opts; else helm_default_opts(&o);
-    if (check_opts(o) != HELM_OK || o.krylov != HELM_KRYLOV_BICGSTAB) return HELM_E_INVALID;
+    if (check_opts(o) != HELM_OK) return HELM_E_INVALID;
     helm_model* m = state->m;
     DeviceGuard g(m->ctx->device);
     cudaStream_t s = m->ctx->stream;

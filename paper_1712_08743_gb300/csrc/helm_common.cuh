@@ -25,14 +25,14 @@ template <typename T> __device__ __forceinline__ cx<T> operator*(cx<T> a, cx<T> 
 }
 template <typename T> __device__ __forceinline__ cx<T> operator*(T s, cx<T> a) { return {s * a.re, s * a.im}; }
 template <typename T> __device__ __forceinline__ cx<T> conjx(cx<T> a) { return {a.re, -a.im}; }
+// Reciprocal of |b|^2 in complex division: the FP32 smoother and preconditioner
+// use the hardware approximate divide (max 2 ulp), FP64 keeps the IEEE divide.
+__device__ __forceinline__ float rcp_fast(float d) { return __fdividef(1.0f, d); }
+__device__ __forceinline__ double rcp_fast(double d) { return 1.0 / d; }
 template <typename T> __device__ __forceinline__ cx<T> cdiv(cx<T> a, cx<T> b) {
     T d = b.re * b.re + b.im * b.im;
-    T inv = T(1) / d;
+    T inv = rcp_fast(d);
     return {(a.re * b.re + a.im * b.im) * inv, (a.im * b.re - a.re * b.im) * inv};
-}
-template <typename T> __device__ __forceinline__ cx<T> cinv(cx<T> b) {
-    T inv = T(1) / (b.re * b.re + b.im * b.im);
-    return {b.re * inv, -b.im * inv};
 }
 
 // 8- or 16-byte vector loads/stores of one complex value.
@@ -83,6 +83,7 @@ enum RhsFlag : int { FLAG_RUNNING = 0, FLAG_CONVERGED = 1, FLAG_BREAKDOWN = 2, F
 struct RhsState {
     // Krylov scalars (BiCGSTAB); complex values as (re, im)
     double rho[2], alpha[2], omega[2], beta[2];
+    double rho_prev[2];  // rho before the last x/r update (for resuming after a residual replacement)
     double bnorm2;       // ||b||^2 of the inner system
     double rnorm2;       // ||r||^2 of the recursive residual
     double tol_rel;      // inner relative tolerance on ||r|| / ||b||
@@ -93,7 +94,7 @@ struct RhsState {
     int flag;            // RhsFlag of the last inner solve
     int outer_active;    // 1 while the outer refinement continues
     int max_it;
-    int pad_;
+    int kfg;             // FGMRES: Arnoldi steps of the current cycle
     unsigned int counter[4];  // last-block election counters, one per reduction site
 };
 

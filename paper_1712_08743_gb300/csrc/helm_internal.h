@@ -17,25 +17,39 @@ namespace helm {
 
 constexpr int kCoarseMaxPoints = 128;   // coarsening stops once a level has this few nodes
 constexpr int kCoarseHardMax = 256;     // largest coarsest level the dense inverse accepts
-constexpr int kMaxRestart = 64;
+constexpr int kFcycleMaxPoints = 24576; // the F-cycle starts at the first level this small
+constexpr int kTailMaxPoints = 3072;    // levels this small run in shared memory, one block per RHS
+constexpr int kMaxLevels = 24;
+constexpr int kMaxRestart = 32;
+constexpr int kFgPartials = 16 * 5 * 512;   // FGMRES dot partials per RHS (2 x 8 values x 5 chunks x 512 blocks)
+constexpr int kGalerkinCoefs = 10;      // per coarse node: G (c, e, n, ne, nw) then K (c, e, n, ne, nw)
 
-// One multigrid level as the kernels see it: dims, (h_l / h_0)^2, and the
-// squared slowness on that level (coarse levels take it by injection from node
-// (2I+1, 2K+1)). Right-hand side b reads model b * mstride / n: mstride = 0
-// when every right-hand side shares one model, n for one model per RHS. The
-// per-RHS factor (h_0 omega_b)^2 is passed separately.
+// One multigrid level as the kernels see it. The finest level carries the
+// squared slowness m2 and the 5-point operator; every coarser level carries
+// its Galerkin operator M_l = G_l - (h_0 omega)^2 (beta1 - j beta2) K_l, with
+// G_l = P^T G_{l-1} P (G_0 the 5-point Laplacian) and K_l = P^T K_{l-1} P
+// (K_0 = diag(m^2)), stored as 9-point symmetric stencils: gk = [10][n] reals
+// (G then K; centre, east, north, north-east, north-west coefficient of each
+// node; the other four come from the neighbours by symmetry). Right-hand side
+// b reads model b * mstride / n (mstride = 0: one model shared by the batch,
+// n: one model per RHS), likewise gkstride. The per-RHS factor
+// (h_0 omega_b)^2 is passed separately.
 struct LevelDev {
     int nx, nz;
-    double h2;
-    const void* m2;   // float* or double*, per the kernel's precision
+    double h2;          // (h_l / h_0)^2 on the finest level (1); unused on Galerkin levels
+    const void* m2;     // finest level: float* or double* per the kernel's precision
     size_t mstride;
+    const void* gk;     // Galerkin levels: float* or double* [nmodels][10][n]
+    size_t gkstride;
 };
 
 struct Level {
     int nx = 0, nz = 0;
     double h = 0;
-    float* m2f = nullptr;
+    float* m2f = nullptr;    // finest level only
     double* m2d = nullptr;
+    float* gkf = nullptr;    // Galerkin levels (l >= 1)
+    double* gkd = nullptr;
     size_t n() const { return (size_t)nx * nz; }
 };
 
@@ -57,6 +71,12 @@ struct helm_model {
     int Px = 0, Pz = 0, npml = 0, nx = 0, nz = 0;
     double h = 0, alpha_max = 0;
     int nmodels = 1;                      // > 1: one slowness model per right-hand side (serving batches)
+    int lf = 1;                           // first level of the F-cycle (V-cycle above)
+    int lt = 1;                           // first level handled by the shared-memory tail kernel (lt >= lf)
+    int* ops_f = nullptr;                 // device: tail schedules, F- and V-cycle from level lt
+    int* ops_v = nullptr;
+    int nops_f = 0, nops_v = 0;
+    size_t tail_smem32 = 0, tail_smem64 = 0;   // dynamic shared memory of the tail kernel
     double* m_pad = nullptr;              // device [nmodels][nz][nx] slowness (float64)
     double msq_sum = 0;                   // sum of m^2 over the physical cells
     std::vector<helm::Level> lv;          // lv[0] is the padded fine grid
@@ -85,14 +105,38 @@ inline LevelDev level_dev(const helm_model* m, int l, bool dbl) {
     d.h2 = (L.h / m->lv[0].h) * (L.h / m->lv[0].h);
     d.m2 = dbl ? (const void*)L.m2d : (const void*)L.m2f;
     d.mstride = m->nmodels > 1 ? L.n() : 0;
+    d.gk = dbl ? (const void*)L.gkd : (const void*)L.gkf;
+    d.gkstride = m->nmodels > 1 ? kGalerkinCoefs * L.n() : 0;
     return d;
 }
+
+// Tail schedule entries: op type in the low byte, level above it.
+enum TailOp : int { OP_SMOOTH0 = 0, OP_RESID = 1, OP_RESTRICT = 2, OP_PROLONG_ADD = 3, OP_JACOBI = 4,
+                    OP_COARSE = 5, OP_OUTPUT = 6, OP_LOAD = 7 };
+std::vector<int> tail_schedule(int lt, int L, bool fcycle);
+size_t tail_smem_bytes(const helm_model* m, size_t elem);
+
+// Arguments of the tail kernel: levels lt..L of the cycle for one RHS per
+// block, every vector of those levels in shared memory.
+struct TailArgs {
+    int lt, L;
+    LevelDev lv[kMaxLevels];
+    const void* in;           // right-hand side on level lt, [nrhs][n_lt]
+    void* out;                // correction on level lt, [nrhs][n_lt]
+    int accumulate;           // 1: out += correction
+    const void* minv;         // dense coarsest inverses [nslots][nL][nL]
+    const int* slot;
+    const int* ops;
+    int nops;
+    const double* w2;         // (h_0 omega_b)^2
+    double b1, b2, wj;
+};
 
 // Kernel launchers (helm_kernels.cu). All run on `s`; none synchronises.
 // `st` may be null where noted; vectors are [nrhs][level n] interleaved complex.
 void launch_pad_model(const double* m_phys, int Px, int Pz, int npml, int nmodels, double* m_pad, float* m2f,
                       double* m2d, cudaStream_t s);
-void launch_inject(const Level& fine, const Level& coarse, int nmodels, cudaStream_t s);
+void launch_galerkin(const helm_model* m, int l, cudaStream_t s);   // builds level l >= 1 from level l - 1
 void launch_sumsq(const double* a, size_t count, double* out, cudaStream_t s);
 
 template <typename T>
@@ -103,13 +147,16 @@ void launch_apply(const LevelDev& L0, int npml, double amax, const double* w2, c
 template <typename TI>
 void launch_resid64(const LevelDev& L0, int npml, double amax, const double* w2, const double* f,
                     const double* u, TI* rin, double* partials, int pstride, RhsState* st,
-                    double tol, double inner_floor, int first, int nrhs, cudaStream_t s);
+                    double tol, double inner_floor, double inner_fac, int first, int nrhs, cudaStream_t s);
 template <typename TI>
 void launch_refine(const TI* x, double* u, const RhsState* st, size_t n, int nrhs, cudaStream_t s);
 
 template <typename T>
 void launch_bicg_init(const T* b, T* x, T* r, T* rh, T* p, T* v, double* partials, int pstride,
                       RhsState* st, int* nactive, size_t n, int nrhs, cudaStream_t s);
+template <typename T>
+void launch_bicg_resume(const T* rin, T* x, T* r, T* rh, T* p, T* v, double* partials, int pstride,
+                        RhsState* st, int* nactive, size_t n, int nrhs, cudaStream_t s);
 template <typename T>
 void launch_bicg_p(const T* r, T* p, const T* v, const RhsState* st, size_t n, int nrhs, cudaStream_t s);
 template <typename T>
@@ -119,22 +166,60 @@ void launch_bicg_xr(T* x, const T* ph, const T* sh, const T* sv, const T* t, con
                     double* partials, int pstride, RhsState* st, int* nactive, size_t n, int nrhs,
                     cudaStream_t s);
 
-// V-cycle pieces
+// V-cycle pieces. restrict / prolong on the finest level use the 5-point
+// operator; on Galerkin levels (1 <= l < lt) the 9-point one.
+template <typename T>
+void launch_tail(const TailArgs& a, size_t smem, int nrhs, const RhsState* st, cudaStream_t s);
+// F-cycle step on a grid level: u2 = wj D^-1 f + P e (e the first coarse
+// correction), residual f - M u2, restricted to level l + 1.
+template <typename T>
+void launch_correct_restrict(const LevelDev& Lf, const LevelDev& Lc, const double* w2, double b1, double b2,
+                             double wj, const T* f, const T* ec, T* fc, const RhsState* st, int nrhs, cudaStream_t s);
 template <typename T>
 void launch_restrict(const LevelDev& Lf, const LevelDev& Lc, const double* w2, double b1, double b2,
                      double wj, const T* f, T* fc, const RhsState* st, int nrhs, cudaStream_t s);
 // mode 0: out = smoothed correction; 1: out = p^, y = A p^, alpha = rho/<rh, y>;
-// 2: out = s^, y = A s^, omega = <y, s>/<y, y>.
+// 2: out = s^, y = A s^, omega = <y, s>/<y, y>; 3: out = z, y = A z (no dots).
 template <typename T>
 void launch_prolong(int mode, const LevelDev& Lf, const LevelDev& Lc, int npml, double amax,
                     const double* w2, double b1, double b2, double wj, const T* f, const T* ec, T* out,
                     T* y, const T* aux, double* partials, int pstride, RhsState* st, int nrhs,
-                    cudaStream_t s);
+                    cudaStream_t s, int accumulate = 0);
 template <typename T>
 void launch_coarse(int n, const T* minv, const int* slot, const T* fL, T* eL, const RhsState* st,
                    int nrhs, cudaStream_t s);
 void launch_coarse_invert(const LevelDev& Lc, const double* w2_slots, const int* mod_slots, int nslots,
                           double b1, double b2, double2* work, float2* minv_f, double2* minv_d, cudaStream_t s);
+
+// FGMRES state on the device, per RHS: Hessenberg H [(m+1) x m], rotated
+// right-hand side g [m+1], Givens cosines cs / sines sn [m], solution y [m],
+// projection coefficients tmp [m+1] and the subdiagonal norms hsub [m].
+struct FgDev {
+    int m;
+    double2* H;
+    double2* g;
+    double* cs;
+    double2* sn;
+    double2* y;
+    double2* tmp;
+    double* hsub;
+};
+template <typename T>
+void launch_fg_norm(const T* rin, double* partials, int pstride, RhsState* st, const FgDev& fg, int* nactive,
+                    size_t n, int nrhs, cudaStream_t s);
+template <typename T>
+void launch_fg_scale(const T* w, T* v, const RhsState* st, const FgDev& fg, int j, size_t n, int nrhs,
+                     cudaStream_t s);
+template <typename T>
+void launch_fg_dots(const T* V, size_t vstride, const T* w, int j, int add, double* partials, int pstride,
+                    RhsState* st, const FgDev& fg, size_t n, int nrhs, cudaStream_t s);
+template <typename T>
+void launch_fg_axpy(const T* V, size_t vstride, T* w, int j, int norm, double* partials, int pstride, RhsState* st,
+                    const FgDev& fg, int* nactive, size_t n, int nrhs, cudaStream_t s);
+void launch_fg_backsolve(const RhsState* st, const FgDev& fg, int nrhs, cudaStream_t s);
+template <typename T>
+void launch_fg_update(const T* Z, size_t zstride, T* x, const RhsState* st, const FgDev& fg, size_t n, int nrhs,
+                      cudaStream_t s);
 
 // right-hand sides and gradient
 void launch_point_rhs(double* f, const int* src_flat, int nrhs, size_t n, cudaStream_t s);

@@ -7,6 +7,9 @@
 // [nrhs][nz][nx] interleaved complex; right-hand side b uses angular frequency
 // omega_b (w2[b] = omega_b^2). The multigrid level l+1 has floor(n_l / 2)
 // nodes per axis; coarse node I sits on fine node 2I + 1.
+#include <functional>
+#include <vector>
+
 #include "helm_internal.h"
 
 namespace helm {
@@ -55,21 +58,6 @@ void launch_pad_model(const double* m_phys, int Px, int Pz, int npml, int nmodel
     k_pad_model<<<dim3(grid1d(n), nmodels), 256, 0, s>>>(m_phys, Px, Pz, npml, m_pad, m2f, m2d);
 }
 
-__global__ void k_inject(const double* __restrict__ fine_d, int nxf, int nzf, double* __restrict__ coarse_d,
-                         float* __restrict__ coarse_f, int nxc, int nzc) {
-    const size_t n = (size_t)nxc * nzc;
-    const int k = blockIdx.y;
-    fine_d += (size_t)k * nxf * nzf;
-    coarse_d += n * k;
-    coarse_f += n * k;
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-        int I = (int)(i % nxc), K = (int)(i / nxc);
-        double v = fine_d[(size_t)(2 * K + 1) * nxf + (2 * I + 1)];
-        coarse_d[i] = v;
-        coarse_f[i] = (float)v;
-    }
-}
-
 // sum of squares of a real array (one block; model setup only)
 __global__ void k_sumsq(const double* __restrict__ a, size_t count, double* out) {
     __shared__ double sh[32];
@@ -79,11 +67,6 @@ __global__ void k_sumsq(const double* __restrict__ a, size_t count, double* out)
     if (threadIdx.x == 0) *out = acc[0];
 }
 void launch_sumsq(const double* a, size_t count, double* out, cudaStream_t s) { k_sumsq<<<1, 1024, 0, s>>>(a, count, out); }
-
-void launch_inject(const Level& fine, const Level& coarse, int nmodels, cudaStream_t s) {
-    k_inject<<<dim3(grid1d(coarse.n()), nmodels), 256, 0, s>>>(fine.m2d, fine.nx, fine.nz, coarse.m2d, coarse.m2f,
-                                                               coarse.nx, coarse.nz);
-}
 
 // ============================================================ stencil apply
 // y = scale * A u on the fine grid (with the damping layer).
@@ -124,7 +107,7 @@ template <typename TI>
 __global__ void __launch_bounds__(256) k_resid64(LevelDev L, int npml, double acoef, const double* __restrict__ w2,
                                                  const double* __restrict__ f, const double* __restrict__ u,
                                                  TI* __restrict__ rin, double* partials, int pstride, RhsState* st,
-                                                 double tol, double inner_floor, int first) {
+                                                 double tol, double inner_floor, double inner_fac, int first) {
     __shared__ double sh[64];
     const int b = blockIdx.z;
     if (!st[b].outer_active) return;
@@ -160,7 +143,7 @@ __global__ void __launch_bounds__(256) k_resid64(LevelDev L, int npml, double ac
             int go = (rel > tol) && (S.iters < S.max_it);
             S.outer_active = go;
             S.active = go;
-            double t = rel > 0.0 ? 0.9 * tol / rel : 1.0;
+            double t = rel > 0.0 ? inner_fac * tol / rel : 1.0;
             S.tol_rel = t > inner_floor ? t : inner_floor;
         }
     }
@@ -168,13 +151,14 @@ __global__ void __launch_bounds__(256) k_resid64(LevelDev L, int npml, double ac
 
 template <typename TI>
 void launch_resid64(const LevelDev& L0, int npml, double amax, const double* w2, const double* f, const double* u,
-                    TI* rin, double* partials, int pstride, RhsState* st, double tol, double inner_floor, int first,
-                    int nrhs, cudaStream_t s) {
+                    TI* rin, double* partials, int pstride, RhsState* st, double tol, double inner_floor,
+                    double inner_fac, int first, int nrhs, cudaStream_t s) {
     dim3 blk(32, 8), grd((L0.nx + 31) / 32, (L0.nz + 7) / 8, nrhs);
-    k_resid64<TI><<<grd, blk, 0, s>>>(L0, npml, layer_coef(npml, amax), w2, f, u, rin, partials, pstride, st, tol, inner_floor, first);
+    k_resid64<TI><<<grd, blk, 0, s>>>(L0, npml, layer_coef(npml, amax), w2, f, u, rin, partials, pstride, st, tol,
+                                      inner_floor, inner_fac, first);
 }
-template void launch_resid64<float>(const LevelDev&, int, double, const double*, const double*, const double*, float*, double*, int, RhsState*, double, double, int, int, cudaStream_t);
-template void launch_resid64<double>(const LevelDev&, int, double, const double*, const double*, const double*, double*, double*, int, RhsState*, double, double, int, int, cudaStream_t);
+template void launch_resid64<float>(const LevelDev&, int, double, const double*, const double*, const double*, float*, double*, int, RhsState*, double, double, double, int, int, cudaStream_t);
+template void launch_resid64<double>(const LevelDev&, int, double, const double*, const double*, const double*, double*, double*, int, RhsState*, double, double, double, int, int, cudaStream_t);
 
 template <typename TI>
 __global__ void k_refine(const TI* __restrict__ x, double* __restrict__ u, const RhsState* st, size_t n) {
@@ -238,6 +222,82 @@ void launch_bicg_init(const T* b, T* x, T* r, T* rh, T* p, T* v, double* partial
                       int* nactive, size_t n, int nrhs, cudaStream_t s) {
     k_bicg_init<T><<<dim3(grid1d(n), 1, nrhs), 256, 0, s>>>(b, x, r, rh, p, v, partials, pstride, st, nactive, n);
 }
+
+// Residual replacement ("reliable update") between refinement steps: r is
+// replaced by the new true residual rin, x restarts from zero, and the Krylov
+// recurrence continues with the same shadow vector and search direction:
+// rho' = <rh, r>, beta = (rho' / rho_prev) (alpha / omega). A right-hand side
+// whose last inner solve did not converge (breakdown or cap) restarts instead.
+template <typename T>
+__global__ void __launch_bounds__(256) k_bicg_resume(const T* __restrict__ rin, T* x, T* r, T* rh, T* p, T* v,
+                                                     double* partials, int pstride, RhsState* st, int* nactive,
+                                                     size_t n) {
+    __shared__ double sh[96];
+    const int b = blockIdx.z;
+    if (!st[b].outer_active) return;
+    const bool restart = st[b].flag != FLAG_CONVERGED;
+    const size_t off = n * b;
+    const cx<T> z(0, 0);
+    T a0 = 0, a1 = 0, a2 = 0;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const cx<T> c = ldc(rin, off + i);
+        stc(x, off + i, z);
+        stc(r, off + i, c);
+        cx<T> q;
+        if (restart) {
+            stc(rh, off + i, c);
+            stc(p, off + i, z);
+            stc(v, off + i, z);
+            q = c;
+        } else {
+            q = ldcc(rh, off + i);
+        }
+        a0 += q.re * c.re + q.im * c.im;
+        a1 += q.re * c.im - q.im * c.re;
+        a2 += c.re * c.re + c.im * c.im;
+    }
+    double acc[3] = {(double)a0, (double)a1, (double)a2};
+    if (last_block_reduce<3>(acc, sh, partials + (size_t)b * pstride, gridDim.x, blockIdx.x, &st[b].counter[1])) {
+        if (threadIdx.x == 0) {
+            RhsState& S = st[b];
+            S.bnorm2 = acc[2];
+            S.rnorm2 = acc[2];
+            if (restart) {
+                S.rho[0] = acc[2]; S.rho[1] = 0.0;
+                S.alpha[0] = 1.0; S.alpha[1] = 0.0;
+                S.omega[0] = 1.0; S.omega[1] = 0.0;
+                S.beta[0] = 0.0; S.beta[1] = 0.0;
+            } else {
+                const double rr = S.rho_prev[0], ri = S.rho_prev[1], d1 = rr * rr + ri * ri;
+                const double orr = S.omega[0], oi = S.omega[1], d2 = orr * orr + oi * oi;
+                if (d1 > 0.0 && d2 > 0.0) {
+                    const double qr = (acc[0] * rr + acc[1] * ri) / d1, qi = (acc[1] * rr - acc[0] * ri) / d1;
+                    const double wr = (S.alpha[0] * orr + S.alpha[1] * oi) / d2;
+                    const double wi = (S.alpha[1] * orr - S.alpha[0] * oi) / d2;
+                    S.beta[0] = qr * wr - qi * wi;
+                    S.beta[1] = qr * wi + qi * wr;
+                } else {
+                    S.beta[0] = 0.0; S.beta[1] = 0.0;
+                }
+                S.rho[0] = acc[0];
+                S.rho[1] = acc[1];
+            }
+            S.flag = FLAG_RUNNING;
+            S.active = acc[2] > 0.0;
+            if (S.active) atomicAdd(nactive, 1);
+        }
+    }
+}
+
+template <typename T>
+void launch_bicg_resume(const T* rin, T* x, T* r, T* rh, T* p, T* v, double* partials, int pstride, RhsState* st,
+                        int* nactive, size_t n, int nrhs, cudaStream_t s) {
+    k_bicg_resume<T><<<dim3(grid1d(n), 1, nrhs), 256, 0, s>>>(rin, x, r, rh, p, v, partials, pstride, st, nactive, n);
+}
+template void launch_bicg_resume<float>(const float*, float*, float*, float*, float*, float*, double*, int, RhsState*,
+                                        int*, size_t, int, cudaStream_t);
+template void launch_bicg_resume<double>(const double*, double*, double*, double*, double*, double*, double*, int,
+                                         RhsState*, int*, size_t, int, cudaStream_t);
 
 template <typename T>
 __global__ void k_bicg_p(const T* __restrict__ r, T* __restrict__ p, const T* __restrict__ v, const RhsState* st,
@@ -319,6 +379,8 @@ __global__ void __launch_bounds__(256) k_bicg_xr(T* x, const T* __restrict__ ph,
                     double wr = (S.alpha[0] * orr + S.alpha[1] * oi) / d2, wi = (S.alpha[1] * orr - S.alpha[0] * oi) / d2;
                     S.beta[0] = qr * wr - qi * wi;
                     S.beta[1] = qr * wi + qi * wr;
+                    S.rho_prev[0] = S.rho[0];
+                    S.rho_prev[1] = S.rho[1];
                     S.rho[0] = acc[0];
                     S.rho[1] = acc[1];
                 }
@@ -334,14 +396,165 @@ void launch_bicg_xr(T* x, const T* ph, const T* shv, const T* sv, const T* t, co
     k_bicg_xr<T><<<dim3(grid1d(n), 1, nrhs), 256, 0, s>>>(x, ph, shv, sv, t, rh, r, partials, pstride, st, nactive, n);
 }
 
+// ===================================================== Galerkin operators
+// Complex coefficient of stored stencil entry k (0 centre, 1 east, 2 north,
+// 3 north-east, 4 north-west) at node i: G_k - hw (b1 - j b2) K_k.
+template <typename T>
+__device__ __forceinline__ cx<T> gcoef(const T* __restrict__ gk, size_t n, size_t i, int k, T hb1, T hb2) {
+    const T g = __ldg(gk + (size_t)k * n + i), q = __ldg(gk + (size_t)(5 + k) * n + i);
+    return cx<T>(g - hb1 * q, hb2 * q);
+}
+
+// M u at node (ix, iz) of a Galerkin level; U points at u of that node inside a
+// row-major tile of row pitch W whose out-of-grid entries are zero.
+template <typename T>
+__device__ __forceinline__ cx<T> mop9(const T* __restrict__ gk, size_t n, int nx, int nz, int ix, int iz,
+                                      const cx<T>* U, int W, T hb1, T hb2) {
+    const size_t i = (size_t)iz * nx + ix;
+    cx<T> acc = gcoef(gk, n, i, 0, hb1, hb2) * U[0];
+    const bool e = ix + 1 < nx, w = ix > 0, no = iz + 1 < nz, so = iz > 0;
+    if (e) acc = acc + gcoef(gk, n, i, 1, hb1, hb2) * U[1];
+    if (w) acc = acc + gcoef(gk, n, i - 1, 1, hb1, hb2) * U[-1];
+    if (no) acc = acc + gcoef(gk, n, i, 2, hb1, hb2) * U[W];
+    if (so) acc = acc + gcoef(gk, n, i - nx, 2, hb1, hb2) * U[-W];
+    if (no && e) acc = acc + gcoef(gk, n, i, 3, hb1, hb2) * U[W + 1];
+    if (so && w) acc = acc + gcoef(gk, n, i - nx - 1, 3, hb1, hb2) * U[-W - 1];
+    if (no && w) acc = acc + gcoef(gk, n, i, 4, hb1, hb2) * U[W - 1];
+    if (so && e) acc = acc + gcoef(gk, n, i - nx + 1, 4, hb1, hb2) * U[-W + 1];
+    return acc;
+}
+
+// Shifted-Laplace diagonal and M u for either kind of level, u in a tile.
+template <typename T, bool GAL>
+struct LevelOp {
+    const T* m2;   // finest level
+    const T* gk;   // Galerkin levels
+    size_t n;
+    int nx, nz;
+    T hw, b1, b2;  // hw = (h_l omega)^2 on the finest level, (h_0 omega)^2 on Galerkin levels
+    __device__ __forceinline__ cx<T> diag(size_t i) const {
+        if constexpr (GAL) return gcoef(gk, n, i, 0, hw * b1, hw * b2);
+        else {
+            const T s = hw * __ldg(m2 + i);
+            return cx<T>(T(4) - s * b1, s * b2);
+        }
+    }
+    __device__ __forceinline__ cx<T> apply(int ix, int iz, const cx<T>* U, int W) const {
+        if constexpr (GAL) return mop9(gk, n, nx, nz, ix, iz, U, W, hw * b1, hw * b2);
+        else {
+            const size_t i = (size_t)iz * nx + ix;
+            const T s = hw * __ldg(m2 + i);
+            const cx<T> c = U[0];
+            cx<T> mu((T(4) - s * b1) * c.re - s * b2 * c.im, (T(4) - s * b1) * c.im + s * b2 * c.re);
+            return mu - U[-1] - U[1] - U[-W] - U[W];
+        }
+    }
+};
+
+template <typename T, bool GAL>
+__device__ __forceinline__ LevelOp<T, GAL> level_op(const LevelDev& L, int b, double w2b) {
+    LevelOp<T, GAL> op;
+    op.n = (size_t)L.nx * L.nz;
+    op.nx = L.nx;
+    op.nz = L.nz;
+    op.m2 = GAL ? nullptr : static_cast<const T*>(L.m2) + (size_t)b * L.mstride;
+    op.gk = GAL ? static_cast<const T*>(L.gk) + (size_t)b * L.gkstride : nullptr;
+    op.hw = (T)(GAL ? w2b : L.h2 * w2b);
+    return op;
+}
+
+// Builds level l's Galerkin stencils from level l - 1 (one thread per coarse
+// node, FP64): coef(I -> J) = sum_a sum_b P[a, I] M[a, b] P[b, J] over the fine
+// 3 x 3 support a of I and the fine 9-point neighbours b of a, separately for G
+// and K. The finest level's G is the 5-point Laplacian and K = diag(m^2).
+__device__ __forceinline__ double w1d(int d) { return d == 0 ? 1.0 : ((d == 1 || d == -1) ? 0.5 : 0.0); }
+
+__device__ __forceinline__ void fine_stencil(bool fine0, const double* m2, const double* gk, size_t n, int nx, int nz,
+                                             int ax, int az, int dx, int dz, double* g, double* k) {
+    // coefficient of fine operator from a = (ax, az) to b = a + (dx, dz); both in the grid
+    *g = 0.0;
+    *k = 0.0;
+    if (fine0) {
+        if (dx == 0 && dz == 0) { *g = 4.0; *k = m2[(size_t)az * nx + ax]; }
+        else if ((dx == 0) != (dz == 0)) *g = -1.0;
+        return;
+    }
+    // stored forward entries: (1,0) e, (0,1) n, (1,1) ne, (-1,1) nw
+    int sx = ax, sz = az, ent;
+    if (dx == 0 && dz == 0) ent = 0;
+    else if (dz == 0) { ent = 1; if (dx < 0) sx = ax - 1; }
+    else if (dx == 0) { ent = 2; if (dz < 0) sz = az - 1; }
+    else if (dx == dz) { ent = 3; if (dx < 0) { sx = ax - 1; sz = az - 1; } }
+    else { ent = 4; if (dz < 0) { sx = ax + 1; sz = az - 1; } }
+    const size_t i = (size_t)sz * nx + sx;
+    *g = gk[(size_t)ent * n + i];
+    *k = gk[(size_t)(5 + ent) * n + i];
+}
+
+__global__ void k_galerkin(int fine0, const double* __restrict__ m2f, const double* __restrict__ gkf, int nxf, int nzf,
+                           size_t mstride_f, size_t gstride_f, double* __restrict__ gkc, float* __restrict__ gkc32,
+                           int nxc, int nzc) {
+    const size_t nf = (size_t)nxf * nzf, nc = (size_t)nxc * nzc;
+    const int model = blockIdx.y;
+    const double* m2 = fine0 ? m2f + (size_t)model * mstride_f : nullptr;
+    const double* gk = fine0 ? nullptr : gkf + (size_t)model * gstride_f;
+    double* out = gkc + (size_t)model * kGalerkinCoefs * nc;
+    float* out32 = gkc32 + (size_t)model * kGalerkinCoefs * nc;
+    const int ddx[5] = {0, 1, 0, 1, -1}, ddz[5] = {0, 0, 1, 1, 1};
+    for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < nc; c += (size_t)gridDim.x * blockDim.x) {
+        const int Ix = (int)(c % nxc), Iz = (int)(c / nxc);
+        double G[5] = {0, 0, 0, 0, 0}, K[5] = {0, 0, 0, 0, 0};
+        for (int az = 2 * Iz; az <= 2 * Iz + 2; ++az) {
+            if (az >= nzf) continue;
+            for (int ax = 2 * Ix; ax <= 2 * Ix + 2; ++ax) {
+                if (ax >= nxf) continue;
+                const double pa = w1d(ax - (2 * Ix + 1)) * w1d(az - (2 * Iz + 1));
+                for (int dz = -1; dz <= 1; ++dz) {
+                    const int bz = az + dz;
+                    if (bz < 0 || bz >= nzf) continue;
+                    for (int dx = -1; dx <= 1; ++dx) {
+                        const int bx = ax + dx;
+                        if (bx < 0 || bx >= nxf) continue;
+                        double g, k;
+                        fine_stencil(fine0, m2, gk, nf, nxf, nzf, ax, az, dx, dz, &g, &k);
+                        if (g == 0.0 && k == 0.0) continue;
+                        for (int e = 0; e < 5; ++e) {
+                            const int Jx = Ix + ddx[e], Jz = Iz + ddz[e];
+                            if (Jx < 0 || Jx >= nxc || Jz >= nzc) continue;
+                            const double pb = w1d(bx - (2 * Jx + 1)) * w1d(bz - (2 * Jz + 1));
+                            if (pb == 0.0) continue;
+                            G[e] += pa * g * pb;
+                            K[e] += pa * k * pb;
+                        }
+                    }
+                }
+            }
+        }
+        for (int e = 0; e < 5; ++e) {
+            out[(size_t)e * nc + c] = G[e];
+            out[(size_t)(5 + e) * nc + c] = K[e];
+            out32[(size_t)e * nc + c] = (float)G[e];
+            out32[(size_t)(5 + e) * nc + c] = (float)K[e];
+        }
+    }
+}
+
+void launch_galerkin(const helm_model* m, int l, cudaStream_t s) {
+    const Level& F = m->lv[l - 1];
+    const Level& C = m->lv[l];
+    const int fine0 = (l == 1);
+    k_galerkin<<<dim3(grid1d(C.n()), m->nmodels), 256, 0, s>>>(fine0, F.m2d, F.gkd, F.nx, F.nz, F.n(),
+                                                              kGalerkinCoefs * F.n(), C.gkd, C.gkf, C.nx, C.nz);
+}
+
 // ======================================================== V-cycle: restrict
 // From a level-l right-hand side f (zero initial guess): one damped-Jacobi
-// sweep u1 = wj D^-1 f, residual r = f - M u1, full weighting, times 4 for the
-// coarse grid-scaled system: fc = (1/4) [1 2 1; 2 4 2; 1 2 1] * r.
+// sweep u1 = wj D^-1 f, residual r = f - M u1, and the restriction P^T r to
+// level l + 1 (full weighting times 4: (1/4) [1 2 1; 2 4 2; 1 2 1] * r).
 constexpr int RCX = 32, RCZ = 8;                    // coarse tile per block
 constexpr int RFW = 2 * RCX + 3, RFH = 2 * RCZ + 3; // fine region (u1) per block
 
-template <typename T>
+template <typename T, bool GAL>
 __global__ void __launch_bounds__(256) k_restrict(LevelDev Lf, LevelDev Lc, const double* __restrict__ w2, T b1, T b2,
                                                   T wj, const T* __restrict__ f, T* __restrict__ fc,
                                                   const RhsState* st) {
@@ -351,8 +564,9 @@ __global__ void __launch_bounds__(256) k_restrict(LevelDev Lf, LevelDev Lc, cons
     if (!rhs_active(st, b)) return;
     const int I0 = blockIdx.x * RCX, K0 = blockIdx.y * RCZ;
     const int gx0 = 2 * I0 - 1, gz0 = 2 * K0 - 1;
-    const T hw = (T)(Lf.h2 * w2[b]);
-    const T* m2 = m2ptr<T>(Lf) + (size_t)b * Lf.mstride;
+    LevelOp<T, GAL> op = level_op<T, GAL>(Lf, b, w2[b]);
+    op.b1 = b1;
+    op.b2 = b2;
     const size_t nf = (size_t)Lf.nx * Lf.nz;
     const T* fb = f + 2 * nf * b;
     for (int idx = threadIdx.x; idx < RFW * RFH; idx += blockDim.x) {
@@ -362,8 +576,7 @@ __global__ void __launch_bounds__(256) k_restrict(LevelDev Lf, LevelDev Lc, cons
         if (gx >= 0 && gx < Lf.nx && gz >= 0 && gz < Lf.nz) {
             const size_t i = (size_t)gz * Lf.nx + gx;
             fv = ldc(fb, i);
-            const T s = hw * __ldg(m2 + i);
-            uv = wj * cdiv(fv, cx<T>(T(4) - s * b1, s * b2));
+            uv = wj * cdiv(fv, op.diag(i));
         }
         F[lz][lx] = fv;
         U[lz][lx] = uv;
@@ -374,14 +587,7 @@ __global__ void __launch_bounds__(256) k_restrict(LevelDev Lf, LevelDev Lc, cons
         const int lz = 1 + idx / W2, lx = 1 + idx % W2;
         const int gx = gx0 + lx, gz = gz0 + lz;
         cx<T> r(0, 0);
-        if (gx < Lf.nx && gz < Lf.nz) {   // gx, gz >= 0 here
-            const size_t i = (size_t)gz * Lf.nx + gx;
-            const T s = hw * __ldg(m2 + i);
-            const cx<T> c = U[lz][lx];
-            cx<T> mu((T(4) - s * b1) * c.re - s * b2 * c.im, (T(4) - s * b1) * c.im + s * b2 * c.re);
-            mu = mu - U[lz][lx - 1] - U[lz][lx + 1] - U[lz - 1][lx] - U[lz + 1][lx];
-            r = F[lz][lx] - mu;
-        }
+        if (gx < Lf.nx && gz < Lf.nz) r = F[lz][lx] - op.apply(gx, gz, &U[lz][lx], RFW);   // gx, gz >= 0 here
         F[lz][lx] = r;   // each element read and written by this thread only
     }
     __syncthreads();
@@ -401,22 +607,26 @@ template <typename T>
 void launch_restrict(const LevelDev& Lf, const LevelDev& Lc, const double* w2, double b1, double b2, double wj,
                      const T* f, T* fc, const RhsState* st, int nrhs, cudaStream_t s) {
     dim3 grd((Lc.nx + RCX - 1) / RCX, (Lc.nz + RCZ - 1) / RCZ, nrhs);
-    k_restrict<T><<<grd, RCX * RCZ, 0, s>>>(Lf, Lc, w2, (T)b1, (T)b2, (T)wj, f, fc, st);
+    if (Lf.m2)
+        k_restrict<T, false><<<grd, RCX * RCZ, 0, s>>>(Lf, Lc, w2, (T)b1, (T)b2, (T)wj, f, fc, st);
+    else
+        k_restrict<T, true><<<grd, RCX * RCZ, 0, s>>>(Lf, Lc, w2, (T)b1, (T)b2, (T)wj, f, fc, st);
 }
 
 // ========================================================= V-cycle: prolong
 // On a level-l tile: u1 = wj D^-1 f, u2 = u1 + P e (bilinear), one post-sweep
 // u3 = u2 + wj D^-1 (f - M u2). Modes 1 and 2 (finest level inside BiCGSTAB)
-// also apply A to u3 and reduce the dot products the next scalar needs.
+// also apply A to u3 and reduce the dot products the next scalar needs; mode 3
+// (FGMRES) applies A without dots.
 // fine tile per block: 64 x 16 in FP32, 32 x 16 in FP64 (static shared memory < 48 KB)
 template <typename T> struct PTile { static constexpr int X = sizeof(T) == 4 ? 64 : 32, Z = 16; };
 
-template <typename T, int MODE>
+template <typename T, int MODE, bool GAL>
 __global__ void __launch_bounds__(256) k_prolong(LevelDev Lf, LevelDev Lc, int npml, double acoef,
                                                  const double* __restrict__ w2, T b1, T b2, T wj,
                                                  const T* __restrict__ f, const T* __restrict__ ec,
                                                  T* __restrict__ out, T* __restrict__ y, const T* __restrict__ aux,
-                                                 double* partials, int pstride, RhsState* st) {
+                                                 double* partials, int pstride, RhsState* st, int accumulate) {
     constexpr int H = (MODE == 0) ? 1 : 2;
     constexpr int PFX = PTile<T>::X, PFZ = PTile<T>::Z;
     constexpr int RW = PFX + 2 * H, RH = PFZ + 2 * H;          // f, u2 region
@@ -433,8 +643,9 @@ __global__ void __launch_bounds__(256) k_prolong(LevelDev Lf, LevelDev Lc, int n
     const int x0 = blockIdx.x * PFX, z0 = blockIdx.y * PFZ;
     const int gx0 = x0 - H, gz0 = z0 - H;
     const int cx0 = x0 / 2 - H, cz0 = z0 / 2 - H;
-    const T hw = (T)(Lf.h2 * w2[b]);
-    const T* m2 = m2ptr<T>(Lf) + (size_t)b * Lf.mstride;
+    LevelOp<T, GAL> op = level_op<T, GAL>(Lf, b, w2[b]);
+    op.b1 = b1;
+    op.b2 = b2;
     const size_t nf = (size_t)Lf.nx * Lf.nz, nc = (size_t)Lc.nx * Lc.nz;
     const T* fb = f + 2 * nf * b;
     const T* eb = ec + 2 * nc * b;
@@ -460,8 +671,7 @@ __global__ void __launch_bounds__(256) k_prolong(LevelDev Lf, LevelDev Lc, int n
         const int gx = gx0 + lx, gz = gz0 + lz;
         cx<T> u(0, 0);
         if (gx >= 0 && gx < Lf.nx && gz >= 0 && gz < Lf.nz) {
-            const T s = hw * __ldg(m2 + (size_t)gz * Lf.nx + gx);
-            u = wj * cdiv(F[lz][lx], cx<T>(T(4) - s * b1, s * b2));
+            u = wj * cdiv(F[lz][lx], op.diag((size_t)gz * Lf.nx + gx));
             // bilinear prolongation: odd fine index -> one coarse node, even -> two halves
             int ia, ib, ka, kb;
             T wa, wb, va, vb;
@@ -486,12 +696,10 @@ __global__ void __launch_bounds__(256) k_prolong(LevelDev Lf, LevelDev Lc, int n
             if (gx >= Lf.nx || gz >= Lf.nz) continue;
             const int lx = tx + H, lz = tz + H;
             const size_t i = (size_t)gz * Lf.nx + gx;
-            const T s = hw * __ldg(m2 + i);
-            const cx<T> D(T(4) - s * b1, s * b2);
             const cx<T> c = U2[lz][lx];
-            cx<T> mu((T(4) - s * b1) * c.re - s * b2 * c.im, (T(4) - s * b1) * c.im + s * b2 * c.re);
-            mu = mu - U2[lz][lx - 1] - U2[lz][lx + 1] - U2[lz - 1][lx] - U2[lz + 1][lx];
-            stc(ob, i, c + wj * cdiv(F[lz][lx] - mu, D));
+            const cx<T> mu = op.apply(gx, gz, &U2[lz][lx], RW);
+            const cx<T> v = c + wj * cdiv(F[lz][lx] - mu, op.diag(i));
+            stc(ob, i, accumulate ? ldcc(ob, i) + v : v);
         }
         return;
     } else {
@@ -502,12 +710,9 @@ __global__ void __launch_bounds__(256) k_prolong(LevelDev Lf, LevelDev Lc, int n
             cx<T> u3(0, 0);
             if (gx >= 0 && gx < Lf.nx && gz >= 0 && gz < Lf.nz) {
                 const int lx = sx + 1, lz = sz + 1;
-                const T s = hw * __ldg(m2 + (size_t)gz * Lf.nx + gx);
-                const cx<T> D(T(4) - s * b1, s * b2);
                 const cx<T> c = U2[lz][lx];
-                cx<T> mu((T(4) - s * b1) * c.re - s * b2 * c.im, (T(4) - s * b1) * c.im + s * b2 * c.re);
-                mu = mu - U2[lz][lx - 1] - U2[lz][lx + 1] - U2[lz - 1][lx] - U2[lz + 1][lx];
-                u3 = c + wj * cdiv(F[lz][lx] - mu, D);
+                const cx<T> mu = op.apply(gx, gz, &U2[lz][lx], RW);
+                u3 = c + wj * cdiv(F[lz][lx] - mu, op.diag((size_t)gz * Lf.nx + gx));
             }
             U3[sz][sx] = u3;
         }
@@ -516,6 +721,8 @@ __global__ void __launch_bounds__(256) k_prolong(LevelDev Lf, LevelDev Lc, int n
         T* ob = out + 2 * nf * b;
         T* yb = y + 2 * nf * b;
         const T* ab = aux + 2 * nf * b;
+        const T* m2 = static_cast<const T*>(Lf.m2) + (size_t)b * Lf.mstride;
+        const T hw = (T)(Lf.h2 * w2[b]);
         T d0 = 0, d1 = 0, d2 = 0;
         for (int idx = threadIdx.x; idx < PFX * PFZ; idx += blockDim.x) {
             const int tz = idx / PFX, tx = idx - tz * PFX;
@@ -534,13 +741,14 @@ __global__ void __launch_bounds__(256) k_prolong(LevelDev Lf, LevelDev Lc, int n
                 const cx<T> q = ldc(ab, i);
                 d0 += q.re * yv.re + q.im * yv.im;
                 d1 += q.re * yv.im - q.im * yv.re;
-            } else {                  // <t, s>, <t, t> with s = f
+            } else if (MODE == 2) {   // <t, s>, <t, t> with s = f
                 const cx<T> sv = F[tz + H][tx + H];
                 d0 += yv.re * sv.re + yv.im * sv.im;
                 d1 += yv.re * sv.im - yv.im * sv.re;
                 d2 += yv.re * yv.re + yv.im * yv.im;
             }
         }
+        if (MODE == 3) return;        // FGMRES: z and A z only
         double acc[3] = {(double)d0, (double)d1, (double)d2};
         const int nblk = gridDim.x * gridDim.y, blk = blockIdx.y * gridDim.x + blockIdx.x;
         if (last_block_reduce<3>(acc, shred, partials + (size_t)b * pstride, nblk, blk, &st[b].counter[3])) {
@@ -568,15 +776,20 @@ __global__ void __launch_bounds__(256) k_prolong(LevelDev Lf, LevelDev Lc, int n
 template <typename T>
 void launch_prolong(int mode, const LevelDev& Lf, const LevelDev& Lc, int npml, double amax, const double* w2,
                     double b1, double b2, double wj, const T* f, const T* ec, T* out, T* y, const T* aux,
-                    double* partials, int pstride, RhsState* st, int nrhs, cudaStream_t s) {
+                    double* partials, int pstride, RhsState* st, int nrhs, cudaStream_t s, int accumulate) {
     constexpr int PFX = PTile<T>::X, PFZ = PTile<T>::Z;
     dim3 grd((Lf.nx + PFX - 1) / PFX, (Lf.nz + PFZ - 1) / PFZ, nrhs);
-    if (mode == 0)
-        k_prolong<T, 0><<<grd, 256, 0, s>>>(Lf, Lc, npml, layer_coef(npml, amax), w2, (T)b1, (T)b2, (T)wj, f, ec, out, y, aux, partials, pstride, st);
+    const double ac = layer_coef(npml, amax);
+    if (mode == 0 && !Lf.m2)
+        k_prolong<T, 0, true><<<grd, 256, 0, s>>>(Lf, Lc, npml, ac, w2, (T)b1, (T)b2, (T)wj, f, ec, out, y, aux, partials, pstride, st, accumulate);
+    else if (mode == 0)
+        k_prolong<T, 0, false><<<grd, 256, 0, s>>>(Lf, Lc, npml, ac, w2, (T)b1, (T)b2, (T)wj, f, ec, out, y, aux, partials, pstride, st, accumulate);
     else if (mode == 1)
-        k_prolong<T, 1><<<grd, 256, 0, s>>>(Lf, Lc, npml, layer_coef(npml, amax), w2, (T)b1, (T)b2, (T)wj, f, ec, out, y, aux, partials, pstride, st);
+        k_prolong<T, 1, false><<<grd, 256, 0, s>>>(Lf, Lc, npml, ac, w2, (T)b1, (T)b2, (T)wj, f, ec, out, y, aux, partials, pstride, st, accumulate);
+    else if (mode == 2)
+        k_prolong<T, 2, false><<<grd, 256, 0, s>>>(Lf, Lc, npml, ac, w2, (T)b1, (T)b2, (T)wj, f, ec, out, y, aux, partials, pstride, st, accumulate);
     else
-        k_prolong<T, 2><<<grd, 256, 0, s>>>(Lf, Lc, npml, layer_coef(npml, amax), w2, (T)b1, (T)b2, (T)wj, f, ec, out, y, aux, partials, pstride, st);
+        k_prolong<T, 3, false><<<grd, 256, 0, s>>>(Lf, Lc, npml, ac, w2, (T)b1, (T)b2, (T)wj, f, ec, out, y, aux, partials, pstride, st, accumulate);
 }
 
 // ======================================================= V-cycle: coarsest
@@ -615,17 +828,17 @@ void launch_coarse(int n, const T* minv, const int* slot, const T* fL, T* eL, co
     k_coarse<T><<<nrhs, 256, 0, s>>>(n, minv, slot, fL, eL, st);
 }
 
-// Dense inverse of the coarsest shifted-Laplace matrix, Gauss-Jordan with
-// partial pivoting in FP64; one block per distinct frequency.
-__global__ void __launch_bounds__(1024) k_coarse_invert(int nx, int nz, double h2, const double* __restrict__ m2all,
-                                                        const double* __restrict__ w2s, const int* __restrict__ mods,
-                                                        double b1, double b2, double2* work, float2* minv_f,
-                                                        double2* minv_d) {
+// Dense inverse of the coarsest Galerkin shifted-Laplace matrix, Gauss-Jordan
+// with partial pivoting in FP64; one block per distinct (model, frequency).
+__global__ void __launch_bounds__(1024) k_coarse_invert(int nx, int nz, const double* __restrict__ gkall,
+                                                        size_t gkstride, const double* __restrict__ w2s,
+                                                        const int* __restrict__ mods, double b1, double b2,
+                                                        double2* work, float2* minv_f, double2* minv_d) {
     const int n = nx * nz, w = 2 * n;
     const int sl = blockIdx.x;
     double2* A = work + (size_t)sl * n * w;
-    const double hw = h2 * w2s[sl];
-    const double* m2 = m2all + (size_t)mods[sl] * n;
+    const double hw = w2s[sl];
+    const double* gk = gkall + (size_t)mods[sl] * gkstride;
     __shared__ double2 fac[kCoarseHardMax];
     __shared__ double red_v[32];
     __shared__ int red_i[32];
@@ -636,8 +849,18 @@ __global__ void __launch_bounds__(1024) k_coarse_invert(int nx, int nz, double h
         double2 v = make_double2(0.0, 0.0);
         if (j < n) {
             const int ix = i % nx, iz = i / nx, jx = j % nx, jz = j / nx;
-            if (i == j) { const double s = hw * m2[i]; v = make_double2(4.0 - s * b1, s * b2); }
-            else if ((iz == jz && abs(ix - jx) == 1) || (ix == jx && abs(iz - jz) == 1)) v = make_double2(-1.0, 0.0);
+            const int dx = jx - ix, dz = jz - iz;
+            if (dx >= -1 && dx <= 1 && dz >= -1 && dz <= 1) {
+                // stored forward entry of the pair (i, j): at i for (1,0) (0,1) (1,1) (-1,1), else at j
+                int ent, at;
+                if (dx == 0 && dz == 0) { ent = 0; at = i; }
+                else if (dz == 0) { ent = 1; at = dx > 0 ? i : j; }
+                else if (dx == 0) { ent = 2; at = dz > 0 ? i : j; }
+                else if (dx == dz) { ent = 3; at = dx > 0 ? i : j; }
+                else { ent = 4; at = dz > 0 ? i : j; }
+                const double g = gk[(size_t)ent * n + at], q = gk[(size_t)(5 + ent) * n + at];
+                v = make_double2(g - hw * b1 * q, hw * b2 * q);
+            }
         } else if (j - n == i) {
             v = make_double2(1.0, 0.0);
         }
@@ -713,9 +936,262 @@ __global__ void __launch_bounds__(1024) k_coarse_invert(int nx, int nz, double h
 
 void launch_coarse_invert(const LevelDev& Lc, const double* w2_slots, const int* mod_slots, int nslots, double b1,
                           double b2, double2* work, float2* minv_f, double2* minv_d, cudaStream_t s) {
-    k_coarse_invert<<<nslots, 1024, 0, s>>>(Lc.nx, Lc.nz, Lc.h2, static_cast<const double*>(Lc.m2), w2_slots,
-                                            mod_slots, b1, b2, work, minv_f, minv_d);
+    k_coarse_invert<<<nslots, 1024, 0, s>>>(Lc.nx, Lc.nz, static_cast<const double*>(Lc.gk),
+                                            kGalerkinCoefs * (size_t)Lc.nx * Lc.nz, w2_slots, mod_slots, b1, b2,
+                                            work, minv_f, minv_d);
 }
+
+// ================================================================ tail
+// Levels lt..L of the cycle in one block per right-hand side, every vector of
+// those levels in shared memory (f, u and r per level, laid out level after
+// level), following a schedule of passes. Each pass covers one level and ends
+// with a block barrier; coefficients are read through the read-only path.
+template <typename T>
+__global__ void __launch_bounds__(1024) k_tail(TailArgs a, const RhsState* st) {
+    extern __shared__ __align__(16) unsigned char tail_smem[];
+    const int b = blockIdx.x;
+    if (!rhs_active(st, b)) return;
+    const T hw = (T)a.w2[b], b1 = (T)a.b1, b2 = (T)a.b2, wj = (T)a.wj;
+    const T hb1 = hw * b1, hb2 = hw * b2;
+    const int tid = threadIdx.x, nth = blockDim.x;
+    cx<T>* base = reinterpret_cast<cx<T>*>(tail_smem);
+    // vector offsets per level (f, u, r)
+    size_t off[kMaxLevels];
+    {
+        size_t o = 0;
+        for (int l = a.lt; l <= a.L; ++l) { off[l] = o; o += 3 * (size_t)a.lv[l].nx * a.lv[l].nz; }
+    }
+    for (int k = 0; k < a.nops; ++k) {
+        const int op = a.ops[k], type = op & 255, l = op >> 8;
+        const LevelDev& L = a.lv[l];
+        const int nx = L.nx, nz = L.nz;
+        const size_t n = (size_t)nx * nz;
+        const T* gk = static_cast<const T*>(L.gk) + (size_t)b * L.gkstride;
+        cx<T>* f = base + off[l];
+        cx<T>* u = f + n;
+        cx<T>* r = u + n;
+        switch (type) {
+            case OP_LOAD: {
+                const T* in = static_cast<const T*>(a.in);
+                for (size_t p = tid; p < n; p += nth) f[p] = ldc(in, n * b + p);
+                break;
+            }
+            case OP_SMOOTH0:
+                for (size_t p = tid; p < n; p += nth) u[p] = wj * cdiv(f[p], gcoef(gk, n, p, 0, hb1, hb2));
+                break;
+            case OP_RESID:
+                for (size_t p = tid; p < n; p += nth) {
+                    const int ix = (int)(p % nx), iz = (int)(p / nx);
+                    r[p] = f[p] - mop9(gk, n, nx, nz, ix, iz, u + p, nx, hb1, hb2);
+                }
+                break;
+            case OP_JACOBI:
+                for (size_t p = tid; p < n; p += nth) u[p] = u[p] + wj * cdiv(r[p], gcoef(gk, n, p, 0, hb1, hb2));
+                break;
+            case OP_RESTRICT: {
+                const LevelDev& C = a.lv[l + 1];
+                const size_t nc = (size_t)C.nx * C.nz;
+                cx<T>* fc = base + off[l + 1];
+                for (size_t q = tid; q < nc; q += nth) {
+                    const int I = (int)(q % C.nx), K = (int)(q / C.nx);
+                    cx<T> acc(0, 0);
+                    for (int dz = -1; dz <= 1; ++dz) {
+                        const int jz = 2 * K + 1 + dz;
+                        if (jz >= nz) continue;
+                        for (int dx = -1; dx <= 1; ++dx) {
+                            const int jx = 2 * I + 1 + dx;
+                            if (jx >= nx) continue;
+                            const T wgt = T((2 - (dx < 0 ? -dx : dx)) * (2 - (dz < 0 ? -dz : dz))) * T(0.25);
+                            acc = acc + wgt * r[(size_t)jz * nx + jx];
+                        }
+                    }
+                    fc[q] = acc;
+                }
+                break;
+            }
+            case OP_PROLONG_ADD: {
+                const LevelDev& C = a.lv[l + 1];
+                const size_t nc = (size_t)C.nx * C.nz;
+                const cx<T>* uc = base + off[l + 1] + nc;
+                for (size_t p = tid; p < n; p += nth) {
+                    const int jx = (int)(p % nx), jz = (int)(p / nx);
+                    int ia, ib, ka, kb;
+                    T wa, wb, va, vb;
+                    if (jx & 1) { ia = (jx - 1) / 2; ib = ia; wa = T(1); wb = T(0); }
+                    else { ia = jx / 2 - 1; ib = jx / 2; wa = T(0.5); wb = T(0.5); }
+                    if (jz & 1) { ka = (jz - 1) / 2; kb = ka; va = T(1); vb = T(0); }
+                    else { ka = jz / 2 - 1; kb = jz / 2; va = T(0.5); vb = T(0.5); }
+                    cx<T> acc(0, 0);
+                    const bool iao = ia >= 0 && ia < C.nx, ibo = ib >= 0 && ib < C.nx;
+                    const bool kao = ka >= 0 && ka < C.nz, kbo = kb >= 0 && kb < C.nz;
+                    if (kao && iao) acc = acc + (va * wa) * uc[(size_t)ka * C.nx + ia];
+                    if (kao && ibo && wb != T(0)) acc = acc + (va * wb) * uc[(size_t)ka * C.nx + ib];
+                    if (kbo && iao && vb != T(0)) acc = acc + (vb * wa) * uc[(size_t)kb * C.nx + ia];
+                    if (kbo && ibo && vb != T(0) && wb != T(0)) acc = acc + (vb * wb) * uc[(size_t)kb * C.nx + ib];
+                    u[p] = u[p] + acc;
+                }
+                break;
+            }
+            case OP_COARSE: {
+                const T* Mb = static_cast<const T*>(a.minv) + 2 * n * n * a.slot[b];
+                const int lane = tid & 31, warp = tid >> 5, nw = nth >> 5;
+                for (int row = warp; row < (int)n; row += nw) {
+                    T re = 0, im = 0;
+                    for (int j = lane; j < (int)n; j += 32) {
+                        const cx<T> m = ldc(Mb, (size_t)row * n + j);
+                        const cx<T> v = f[j];
+                        re += m.re * v.re - m.im * v.im;
+                        im += m.re * v.im + m.im * v.re;
+                    }
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) {
+                        re += __shfl_xor_sync(0xffffffffu, re, o);
+                        im += __shfl_xor_sync(0xffffffffu, im, o);
+                    }
+                    if (lane == 0) u[row] = cx<T>(re, im);
+                }
+                break;
+            }
+            case OP_OUTPUT: {
+                T* o = static_cast<T*>(a.out);
+                for (size_t p = tid; p < n; p += nth)
+                    stc(o, n * b + p, a.accumulate ? ldcc(o, n * b + p) + u[p] : u[p]);
+                break;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+size_t tail_smem_bytes(const helm_model* m, size_t elem) {
+    size_t v = 0;
+    for (size_t l = m->lt; l < m->lv.size(); ++l) v += 3 * m->lv[l].n();
+    return v * 2 * elem;
+}
+
+template <typename T>
+void launch_tail(const TailArgs& a, size_t smem, int nrhs, const RhsState* st, cudaStream_t s) {
+    static bool attr_set = false;   // one-time opt-in to more than 48 KB of dynamic shared memory
+    if (!attr_set) {
+        cudaFuncSetAttribute(k_tail<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+        attr_set = true;
+    }
+    k_tail<T><<<nrhs, 1024, smem, s>>>(a, st);
+}
+template void launch_tail<float>(const TailArgs&, size_t, int, const RhsState*, cudaStream_t);
+template void launch_tail<double>(const TailArgs&, size_t, int, const RhsState*, cudaStream_t);
+
+// Schedule of the tail: LOAD the right-hand side of level lt, an F-cycle (whose
+// second coarse correction is a V-cycle) or a V-cycle from lt, OUTPUT.
+std::vector<int> tail_schedule(int lt, int L, bool fcycle) {
+    std::vector<int> ops;
+    auto put = [&](int type, int l) { ops.push_back(type | (l << 8)); };
+    std::function<void(int)> V = [&](int l) {
+        if (l == L) { put(OP_COARSE, l); return; }
+        put(OP_SMOOTH0, l); put(OP_RESID, l); put(OP_RESTRICT, l);
+        V(l + 1);
+        put(OP_PROLONG_ADD, l); put(OP_RESID, l); put(OP_JACOBI, l);
+    };
+    std::function<void(int)> F = [&](int l) {
+        if (l == L) { put(OP_COARSE, l); return; }
+        put(OP_SMOOTH0, l); put(OP_RESID, l); put(OP_RESTRICT, l);
+        F(l + 1);
+        put(OP_PROLONG_ADD, l); put(OP_RESID, l); put(OP_RESTRICT, l);
+        V(l + 1);
+        put(OP_PROLONG_ADD, l); put(OP_RESID, l); put(OP_JACOBI, l);
+    };
+    put(OP_LOAD, lt);
+    if (fcycle) F(lt); else V(lt);
+    put(OP_OUTPUT, lt);
+    return ops;
+}
+
+// ============================================== F-cycle: correct + restrict
+// u2 = wj D^-1 f + P e on the fine region of a coarse tile, r = f - M u2,
+// restricted to level l + 1 (the second coarse correction of an F-cycle).
+template <typename T, bool GAL>
+__global__ void __launch_bounds__(256) k_correct_restrict(LevelDev Lf, LevelDev Lc, const double* __restrict__ w2,
+                                                          T b1, T b2, T wj, const T* __restrict__ f,
+                                                          const T* __restrict__ ec, T* __restrict__ fc,
+                                                          const RhsState* st) {
+    constexpr int CEW = RCX + 2, CEH = RCZ + 2;   // coarse region feeding P on the fine region
+    __shared__ cx<T> F[RFH][RFW];
+    __shared__ cx<T> U[RFH][RFW];
+    __shared__ cx<T> E[CEH][CEW];
+    const int b = blockIdx.z;
+    if (!rhs_active(st, b)) return;
+    const int I0 = blockIdx.x * RCX, K0 = blockIdx.y * RCZ;
+    const int gx0 = 2 * I0 - 1, gz0 = 2 * K0 - 1;
+    const int cx0 = I0 - 1, cz0 = K0 - 1;
+    LevelOp<T, GAL> op = level_op<T, GAL>(Lf, b, w2[b]);
+    op.b1 = b1;
+    op.b2 = b2;
+    const size_t nf = (size_t)Lf.nx * Lf.nz, nc = (size_t)Lc.nx * Lc.nz;
+    const T* fb = f + 2 * nf * b;
+    const T* eb = ec + 2 * nc * b;
+    for (int idx = threadIdx.x; idx < CEW * CEH; idx += blockDim.x) {
+        const int lz = idx / CEW, lx = idx - lz * CEW;
+        const int I = cx0 + lx, K = cz0 + lz;
+        cx<T> e(0, 0);
+        if (I >= 0 && I < Lc.nx && K >= 0 && K < Lc.nz) e = ldc(eb, (size_t)K * Lc.nx + I);
+        E[lz][lx] = e;
+    }
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < RFW * RFH; idx += blockDim.x) {
+        const int lz = idx / RFW, lx = idx - lz * RFW;
+        const int gx = gx0 + lx, gz = gz0 + lz;
+        cx<T> fv(0, 0), uv(0, 0);
+        if (gx >= 0 && gx < Lf.nx && gz >= 0 && gz < Lf.nz) {
+            const size_t i = (size_t)gz * Lf.nx + gx;
+            fv = ldc(fb, i);
+            uv = wj * cdiv(fv, op.diag(i));
+            int ia, ib, ka, kb;
+            T wa, wb, va, vb;
+            if (gx & 1) { ia = (gx - 1) / 2; ib = ia; wa = T(1); wb = T(0); }
+            else { ia = gx / 2 - 1; ib = gx / 2; wa = T(0.5); wb = T(0.5); }
+            if (gz & 1) { ka = (gz - 1) / 2; kb = ka; va = T(1); vb = T(0); }
+            else { ka = gz / 2 - 1; kb = gz / 2; va = T(0.5); vb = T(0.5); }
+            ia -= cx0; ib -= cx0; ka -= cz0; kb -= cz0;
+            uv = uv + (va * wa) * E[ka][ia] + (va * wb) * E[ka][ib] + (vb * wa) * E[kb][ia] + (vb * wb) * E[kb][ib];
+        }
+        F[lz][lx] = fv;
+        U[lz][lx] = uv;
+    }
+    __syncthreads();
+    constexpr int W2 = RFW - 2, H2 = RFH - 2;
+    for (int idx = threadIdx.x; idx < W2 * H2; idx += blockDim.x) {
+        const int lz = 1 + idx / W2, lx = 1 + idx % W2;
+        const int gx = gx0 + lx, gz = gz0 + lz;
+        cx<T> r(0, 0);
+        if (gx < Lf.nx && gz < Lf.nz) r = F[lz][lx] - op.apply(gx, gz, &U[lz][lx], RFW);
+        F[lz][lx] = r;
+    }
+    __syncthreads();
+    const int cxl = threadIdx.x % RCX, czl = threadIdx.x / RCX;
+    const int I = I0 + cxl, K = K0 + czl;
+    if (I < Lc.nx && K < Lc.nz) {
+        const int lx = 2 * cxl + 2, lz = 2 * czl + 2;
+        cx<T> a = T(4) * F[lz][lx];
+        a = a + T(2) * (F[lz][lx - 1] + F[lz][lx + 1] + F[lz - 1][lx] + F[lz + 1][lx]);
+        a = a + F[lz - 1][lx - 1] + F[lz - 1][lx + 1] + F[lz + 1][lx - 1] + F[lz + 1][lx + 1];
+        stc(fc + 2 * nc * b, (size_t)K * Lc.nx + I, T(0.25) * a);
+    }
+}
+
+template <typename T>
+void launch_correct_restrict(const LevelDev& Lf, const LevelDev& Lc, const double* w2, double b1, double b2,
+                             double wj, const T* f, const T* ec, T* fc, const RhsState* st, int nrhs, cudaStream_t s) {
+    dim3 grd((Lc.nx + RCX - 1) / RCX, (Lc.nz + RCZ - 1) / RCZ, nrhs);
+    if (Lf.m2)
+        k_correct_restrict<T, false><<<grd, RCX * RCZ, 0, s>>>(Lf, Lc, w2, (T)b1, (T)b2, (T)wj, f, ec, fc, st);
+    else
+        k_correct_restrict<T, true><<<grd, RCX * RCZ, 0, s>>>(Lf, Lc, w2, (T)b1, (T)b2, (T)wj, f, ec, fc, st);
+}
+template void launch_correct_restrict<float>(const LevelDev&, const LevelDev&, const double*, double, double, double,
+                                             const float*, const float*, float*, const RhsState*, int, cudaStream_t);
+template void launch_correct_restrict<double>(const LevelDev&, const LevelDev&, const double*, double, double, double,
+                                              const double*, const double*, double*, const RhsState*, int,
+                                              cudaStream_t);
 
 // ============================================================ right-hand sides
 __global__ void k_point_rhs(double* f, const int* __restrict__ src_flat, size_t n) {
@@ -869,7 +1345,7 @@ void launch_fold(const double* g_pad, const double* m_pad, int Px, int Pz, int n
                                      const T*, T*, const RhsState*, int, cudaStream_t);                           \
     template void launch_prolong<T>(int, const LevelDev&, const LevelDev&, int, double, const double*, double,    \
                                     double, double, const T*, const T*, T*, T*, const T*, double*, int,           \
-                                    RhsState*, int, cudaStream_t);                                                \
+                                    RhsState*, int, cudaStream_t, int);                                           \
     template void launch_coarse<T>(int, const T*, const int*, const T*, T*, const RhsState*, int, cudaStream_t);
 HELM_INST(float)
 HELM_INST(double)

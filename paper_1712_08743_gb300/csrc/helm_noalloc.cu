@@ -89,8 +89,8 @@ extern "C" int helm_vcycle_noalloc(helm_model* m, int nrhs, const double* omega,
     const size_t o_work = take(sizeof(double2) * nc * nc * 2 * nslots);
     const size_t o_mf = take(sizeof(float2) * nc * nc * nslots);
     const size_t o_md = take(sizeof(double2) * nc * nc * nslots);
-    size_t o_f[64], o_e[64];
-    for (int l = 1; l <= L; ++l) {
+    size_t o_f[kMaxLevels], o_e[kMaxLevels];
+    for (int l = 1; l <= m->lt; ++l) {
         o_f[l] = take(sizeof(float) * 2 * m->lv[l].n() * nrhs);
         o_e[l] = take(sizeof(float) * 2 * m->lv[l].n() * nrhs);
     }
@@ -117,23 +117,25 @@ extern "C" int helm_vcycle_noalloc(helm_model* m, int nrhs, const double* omega,
                              reinterpret_cast<const int*>(base + o_mods), nslots, beta1, beta2,
                              reinterpret_cast<double2*>(base + o_work), reinterpret_cast<float2*>(base + o_mf),
                              reinterpret_cast<double2*>(base + o_md), s);
-        auto F = [&](int l) { return reinterpret_cast<float*>(base + o_f[l]); };
-        auto E = [&](int l) { return reinterpret_cast<float*>(base + o_e[l]); };
-        const float* rin = static_cast<const float*>(r);
-        launch_restrict<float>(level_dev(m, 0, false), level_dev(m, 1, false), dw2, beta1, beta2, omega_jacobi, rin,
-                               F(1), nullptr, nrhs, s);
-        for (int l = 1; l < L; ++l)
-            launch_restrict<float>(level_dev(m, l, false), level_dev(m, l + 1, false), dw2, beta1, beta2,
-                                   omega_jacobi, F(l), F(l + 1), nullptr, nrhs, s);
-        launch_coarse<float>((int)nc, reinterpret_cast<const float*>(base + o_mf),
-                             reinterpret_cast<const int*>(base + o_slot), F(L), E(L), nullptr, nrhs, s);
-        for (int l = L - 1; l >= 1; --l)
-            launch_prolong<float>(0, level_dev(m, l, false), level_dev(m, l + 1, false), m->npml, m->alpha_max, dw2,
-                                  beta1, beta2, omega_jacobi, F(l), E(l + 1), E(l), nullptr, nullptr, nullptr, 0,
-                                  nullptr, nrhs, s);
-        launch_prolong<float>(0, level_dev(m, 0, false), level_dev(m, 1, false), m->npml, m->alpha_max, dw2, beta1,
-                              beta2, omega_jacobi, rin, E(1), static_cast<float*>(z), nullptr, nullptr, nullptr, 0,
-                              nullptr, nrhs, s);
+        MgCall mc;
+        mc.w2 = dw2;
+        mc.b1 = beta1;
+        mc.b2 = beta2;
+        mc.wj = omega_jacobi;
+        mc.st = nullptr;
+        mc.nrhs = nrhs;
+        mc.s = s;
+        mc.minv = base + o_mf;
+        mc.slot = reinterpret_cast<const int*>(base + o_slot);
+        mc.partials = nullptr;
+        mc.pstride = 0;
+        MgLevels<float> B;
+        std::memset(&B, 0, sizeof(B));
+        for (int l = 1; l <= m->lt; ++l) {
+            B.f[l] = reinterpret_cast<float*>(base + o_f[l]);
+            B.e[l] = reinterpret_cast<float*>(base + o_e[l]);
+        }
+        mg_apply<float>(m, mc, B, static_cast<const float*>(r), static_cast<float*>(z), 0, nullptr, nullptr);
         e = cudaGetLastError();
     }
     // the host arrays above are the sources of the copies: wait before returning

@@ -64,7 +64,8 @@ static bool same_batch(const helm_request& a, const helm_request& b) {
     return a.Px == b.Px && a.Pz == b.Pz && a.npml == b.npml && a.alpha_max == b.alpha_max &&
            x.precision == y.precision && x.tol == y.tol && x.max_it == y.max_it && x.beta1 == y.beta1 &&
            x.beta2 == y.beta2 && x.omega_jacobi == y.omega_jacobi && x.inner_tol == y.inner_tol &&
-           x.max_outer == y.max_outer && x.check_every == y.check_every && x.use_graphs == y.use_graphs;
+           x.max_outer == y.max_outer && x.check_every == y.check_every && x.use_graphs == y.use_graphs &&
+           x.krylov == y.krylov && x.restart == y.restart;
 }
 
 static uint64_t batch_bytes(const helm_request& r, int nb) {
@@ -235,7 +236,8 @@ int helm_submit(helm_ctx* ctx, const helm_request* req, uint64_t* ticket) {
     if (r.Px < 1 || r.Pz < 1 || r.npml < 0 || !(r.h > 0.0) || !(r.omega > 0.0) || !(r.alpha_max >= 0.0))
         return HELM_E_INVALID;
     if (r.src_ix < 0 || r.src_ix >= r.Px || r.src_iz < 0 || r.src_iz >= r.Pz) return HELM_E_INVALID;
-    if (r.opts.device_ptrs || r.opts.krylov != HELM_KRYLOV_BICGSTAB || !(r.opts.tol > 0.0) || r.opts.max_it < 1 ||
+    if (r.opts.device_ptrs || (r.opts.krylov != HELM_KRYLOV_BICGSTAB && r.opts.krylov != HELM_KRYLOV_FGMRES) ||
+        r.opts.restart < 1 || r.opts.restart > kMaxRestart || !(r.opts.tol > 0.0) || r.opts.max_it < 1 ||
         r.opts.check_every < 1 || r.opts.max_outer < 1 || !(r.opts.omega_jacobi > 0.0) || !(r.opts.inner_tol > 0.0) ||
         r.opts.precision < HELM_PREC_MIXED || r.opts.precision > HELM_PREC_FP32)
         return HELM_E_INVALID;

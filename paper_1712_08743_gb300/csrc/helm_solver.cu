@@ -69,7 +69,9 @@ int coarsest_points(const helm_model* m) { return (int)m->lv.back().n(); }
 template <typename T>
 struct Inner {
     DBuf x, r, rh, p, v, sv, t, ph, shv;
-    std::vector<std::unique_ptr<DBuf>> fl, el;   // per level l >= 1
+    // per level 1 <= l <= lt: right-hand side and correction (deeper levels live
+    // in the tail kernel's shared memory)
+    std::vector<std::unique_ptr<DBuf>> fl, el;
 };
 
 // Per-solve state shared by the outer and inner loops.
@@ -89,25 +91,98 @@ struct SolveCtx {
 };
 
 template <typename T>
-static void vcycle(const SolveCtx& c, Inner<T>& w, const T* in, T* out, int mode, T* y, const T* aux) {
-    const helm_model* m = c.m;
+static void mg_cycle(const helm_model* m, const MgCall& c, const MgLevels<T>& B, int l, bool F, int acc) {
     const bool dbl = sizeof(T) == 8;
-    const int L = (int)m->lv.size() - 1;
-    const double b1 = c.o.beta1, b2 = c.o.beta2, wj = c.o.omega_jacobi;
-    // down: level 0 -> 1 from `in`, then level l -> l + 1
-    launch_restrict<T>(level_dev(m, 0, dbl), level_dev(m, 1, dbl), c.w2, b1, b2, wj, in,
-                       w.fl[1]->template as<T>(), c.st, c.nrhs, c.s);
-    for (int l = 1; l < L; ++l)
-        launch_restrict<T>(level_dev(m, l, dbl), level_dev(m, l + 1, dbl), c.w2, b1, b2, wj,
-                           w.fl[l]->template as<T>(), w.fl[l + 1]->template as<T>(), c.st, c.nrhs, c.s);
-    launch_coarse<T>(c.ncoarse, static_cast<const T*>(c.minv), c.slot, w.fl[L]->template as<T>(),
-                     w.el[L]->template as<T>(), c.st, c.nrhs, c.s);
-    for (int l = L - 1; l >= 1; --l)
-        launch_prolong<T>(0, level_dev(m, l, dbl), level_dev(m, l + 1, dbl), m->npml, m->alpha_max, c.w2,
-                          b1, b2, wj, w.fl[l]->template as<T>(), w.el[l + 1]->template as<T>(),
-                          w.el[l]->template as<T>(), nullptr, nullptr, nullptr, 0, c.st, c.nrhs, c.s);
-    launch_prolong<T>(mode, level_dev(m, 0, dbl), level_dev(m, 1, dbl), m->npml, m->alpha_max, c.w2, b1,
-                      b2, wj, in, w.el[1]->template as<T>(), out, y, aux, c.partials, c.pstride, c.st, c.nrhs, c.s);
+    if (l >= m->lt) {
+        TailArgs a;
+        std::memset(&a, 0, sizeof(a));
+        a.lt = m->lt;
+        a.L = (int)m->lv.size() - 1;
+        for (int q = 0; q <= a.L; ++q) a.lv[q] = level_dev(m, q, dbl);
+        a.in = B.f[l];
+        a.out = B.e[l];
+        a.accumulate = acc;
+        a.minv = c.minv;
+        a.slot = c.slot;
+        a.ops = F ? m->ops_f : m->ops_v;
+        a.nops = F ? m->nops_f : m->nops_v;
+        a.w2 = c.w2;
+        a.b1 = c.b1;
+        a.b2 = c.b2;
+        a.wj = c.wj;
+        launch_tail<T>(a, dbl ? m->tail_smem64 : m->tail_smem32, c.nrhs, c.st, c.s);
+        return;
+    }
+    const LevelDev Lf = level_dev(m, l, dbl), Lc = level_dev(m, l + 1, dbl);
+    launch_restrict<T>(Lf, Lc, c.w2, c.b1, c.b2, c.wj, B.f[l], B.f[l + 1], c.st, c.nrhs, c.s);
+    mg_cycle<T>(m, c, B, l + 1, F || (l + 1 == m->lf), 0);
+    if (F) {
+        launch_correct_restrict<T>(Lf, Lc, c.w2, c.b1, c.b2, c.wj, B.f[l], B.e[l + 1], B.f[l + 1], c.st, c.nrhs, c.s);
+        mg_cycle<T>(m, c, B, l + 1, false, 1);
+    }
+    launch_prolong<T>(0, Lf, Lc, m->npml, m->alpha_max, c.w2, c.b1, c.b2, c.wj, B.f[l], B.e[l + 1], B.e[l], nullptr,
+                      nullptr, nullptr, 0, c.st, c.nrhs, c.s, acc);
+}
+
+template <typename T>
+void mg_apply(const helm_model* m, const MgCall& c, const MgLevels<T>& B, const T* in, T* out, int mode, T* y,
+              const T* aux) {
+    const bool dbl = sizeof(T) == 8;
+    const LevelDev L0 = level_dev(m, 0, dbl), L1 = level_dev(m, 1, dbl);
+    launch_restrict<T>(L0, L1, c.w2, c.b1, c.b2, c.wj, in, B.f[1], c.st, c.nrhs, c.s);
+    mg_cycle<T>(m, c, B, 1, m->lf == 1, 0);
+    launch_prolong<T>(mode, L0, L1, m->npml, m->alpha_max, c.w2, c.b1, c.b2, c.wj, in, B.e[1], out, y, aux,
+                      c.partials, c.pstride, c.st, c.nrhs, c.s);
+}
+template void mg_apply<float>(const helm_model*, const MgCall&, const MgLevels<float>&, const float*, float*, int,
+                              float*, const float*);
+template void mg_apply<double>(const helm_model*, const MgCall&, const MgLevels<double>&, const double*, double*, int,
+                               double*, const double*);
+
+static int count_cycle(const helm_model* m, int l, bool F) {
+    if (l >= m->lt) return 1;
+    int k = 2 + count_cycle(m, l + 1, F || (l + 1 == m->lf));
+    if (F) k += 1 + count_cycle(m, l + 1, false);
+    return k;
+}
+int mg_kernels_per_apply(const helm_model* m) { return 2 + count_cycle(m, 1, m->lf == 1); }
+
+template <typename T>
+static void vcycle(const SolveCtx& c, Inner<T>& w, const T* in, T* out, int mode, T* y, const T* aux) {
+    MgCall mc;
+    mc.w2 = c.w2;
+    mc.b1 = c.o.beta1;
+    mc.b2 = c.o.beta2;
+    mc.wj = c.o.omega_jacobi;
+    mc.st = c.st;
+    mc.nrhs = c.nrhs;
+    mc.s = c.s;
+    mc.minv = c.minv;
+    mc.slot = c.slot;
+    mc.partials = c.partials;
+    mc.pstride = c.pstride;
+    MgLevels<T> B;
+    std::memset(&B, 0, sizeof(B));
+    for (int l = 1; l <= c.m->lt; ++l) {
+        B.f[l] = w.fl[l]->template as<T>();
+        B.e[l] = w.el[l]->template as<T>();
+    }
+    mg_apply<T>(c.m, mc, B, in, out, mode, y, aux);
+}
+
+template <typename T>
+static int alloc_levels(const helm_model* m, cudaStream_t s, int nrhs, Inner<T>& w) {
+    const int nl = (int)m->lv.size();
+    w.fl.resize(nl);
+    w.el.resize(nl);
+    for (int l = 1; l < nl && l <= m->lt; ++l) {
+        const size_t b = sizeof(T) * 2 * m->lv[l].n() * nrhs;
+        w.fl[l].reset(new DBuf());
+        w.el[l].reset(new DBuf());
+        TRY_ALLOC(*w.fl[l], b, s);
+        TRY_ALLOC(*w.el[l], b, s);
+    }
+    return HELM_OK;
 }
 
 template <typename T>
@@ -116,23 +191,12 @@ static int alloc_inner(const SolveCtx& c, Inner<T>& w) {
     TRY_ALLOC(w.x, vb, c.s); TRY_ALLOC(w.r, vb, c.s); TRY_ALLOC(w.rh, vb, c.s);
     TRY_ALLOC(w.p, vb, c.s); TRY_ALLOC(w.v, vb, c.s); TRY_ALLOC(w.sv, vb, c.s);
     TRY_ALLOC(w.t, vb, c.s); TRY_ALLOC(w.ph, vb, c.s); TRY_ALLOC(w.shv, vb, c.s);
-    const int nl = (int)c.m->lv.size();
-    w.fl.resize(nl);
-    w.el.resize(nl);
-    for (int l = 1; l < nl; ++l) {
-        const size_t b = sizeof(T) * 2 * c.m->lv[l].n() * c.nrhs;
-        w.fl[l].reset(new DBuf());
-        w.el[l].reset(new DBuf());
-        TRY_ALLOC(*w.fl[l], b, c.s);
-        TRY_ALLOC(*w.el[l], b, c.s);
-    }
-    return HELM_OK;
+    return alloc_levels<T>(c.m, c.s, c.nrhs, w);
 }
 
 // kernels one BiCGSTAB iteration launches: p, s and x/r updates plus two
-// V-cycles of (levels - 1) restrictions, one coarse solve and (levels - 1)
-// prolongations
-static int kernels_per_iteration(const helm_model* m) { return 3 + 2 * (2 * ((int)m->lv.size() - 1) + 1); }
+// preconditioner applications
+static int kernels_per_iteration(const helm_model* m) { return 3 + 2 * mg_kernels_per_apply(m); }
 
 template <typename T>
 static void bicg_iteration(const SolveCtx& c, Inner<T>& w) {
@@ -150,12 +214,19 @@ static void bicg_iteration(const SolveCtx& c, Inner<T>& w) {
 // Inner BiCGSTAB on rin for the right-hand sides whose outer step is active.
 // Leaves the correction in w.x. `graph` caches the captured iteration chunk.
 template <typename T>
-static int inner_solve(const SolveCtx& c, Inner<T>& w, const T* rin, cudaGraphExec_t* graph, int* iters_done) {
+static int inner_solve(const SolveCtx& c, Inner<T>& w, const T* rin, cudaGraphExec_t* graph, int* iters_done,
+                       bool resume) {
     const size_t n = c.m->n();
     HELM_CUDA_TRY(cudaMemsetAsync(c.nactive, 0, sizeof(int), c.s));
     count_launches(1);
-    launch_bicg_init<T>(rin, w.x.template as<T>(), w.r.template as<T>(), w.rh.template as<T>(), w.p.template as<T>(),
-                        w.v.template as<T>(), c.partials, c.pstride, c.st, c.nactive, n, c.nrhs, c.s);
+    if (resume)
+        launch_bicg_resume<T>(rin, w.x.template as<T>(), w.r.template as<T>(), w.rh.template as<T>(),
+                              w.p.template as<T>(), w.v.template as<T>(), c.partials, c.pstride, c.st, c.nactive, n,
+                              c.nrhs, c.s);
+    else
+        launch_bicg_init<T>(rin, w.x.template as<T>(), w.r.template as<T>(), w.rh.template as<T>(),
+                            w.p.template as<T>(), w.v.template as<T>(), c.partials, c.pstride, c.st, c.nactive, n,
+                            c.nrhs, c.s);
     const int chunk = std::max(1, c.o.check_every);
     if (c.o.use_graphs && *graph == nullptr) {
         cudaGraph_t g;
@@ -185,6 +256,88 @@ static int inner_solve(const SolveCtx& c, Inner<T>& w, const T* rin, cudaGraphEx
     }
     HELM_CUDA_TRY(cudaGetLastError());
     *iters_done += done;
+    return HELM_OK;
+}
+
+// FGMRES buffers: V [(m+1)][nrhs][n], Z [m][nrhs][n] and the small FP64 state.
+template <typename T>
+struct FgBufs {
+    DBuf V, Z, H, g, cs, sn, y, tmp, hsub;
+    FgDev dev;
+};
+
+template <typename T>
+static int alloc_fg(const SolveCtx& c, FgBufs<T>& f) {
+    const int m = c.o.restart, nrhs = c.nrhs;
+    const size_t vb = sizeof(T) * 2 * c.m->n() * nrhs;
+    TRY_ALLOC(f.V, vb * (m + 1), c.s);
+    TRY_ALLOC(f.Z, vb * m, c.s);
+    TRY_ALLOC(f.H, sizeof(double2) * (size_t)nrhs * (m + 1) * m, c.s);
+    TRY_ALLOC(f.g, sizeof(double2) * (size_t)nrhs * (m + 1), c.s);
+    TRY_ALLOC(f.cs, sizeof(double) * (size_t)nrhs * m, c.s);
+    TRY_ALLOC(f.sn, sizeof(double2) * (size_t)nrhs * m, c.s);
+    TRY_ALLOC(f.y, sizeof(double2) * (size_t)nrhs * m, c.s);
+    TRY_ALLOC(f.tmp, sizeof(double2) * (size_t)nrhs * (m + 1), c.s);
+    TRY_ALLOC(f.hsub, sizeof(double) * (size_t)nrhs * m, c.s);
+    HELM_CUDA_TRY(cudaMemsetAsync(f.H.p, 0, sizeof(double2) * (size_t)nrhs * (m + 1) * m, c.s));
+    f.dev.m = m;
+    f.dev.H = f.H.template as<double2>();
+    f.dev.g = f.g.template as<double2>();
+    f.dev.cs = f.cs.template as<double>();
+    f.dev.sn = f.sn.template as<double2>();
+    f.dev.y = f.y.template as<double2>();
+    f.dev.tmp = f.tmp.template as<double2>();
+    f.dev.hsub = f.hsub.template as<double>();
+    return HELM_OK;
+}
+
+// One FGMRES cycle of at most m Arnoldi steps from a zero guess on rin; the
+// correction is left in w.x.
+template <typename T>
+static void fgmres_cycle(const SolveCtx& c, Inner<T>& w, FgBufs<T>& f, const T* rin) {
+    const size_t n = c.m->n(), vs = n * c.nrhs;
+    const int m = f.dev.m;
+    T* V = f.V.template as<T>();
+    T* Z = f.Z.template as<T>();
+    T* wv = w.v.template as<T>();
+    launch_fg_norm<T>(rin, c.partials, c.pstride, c.st, f.dev, c.nactive, n, c.nrhs, c.s);
+    launch_fg_scale<T>(rin, V, c.st, f.dev, -1, n, c.nrhs, c.s);
+    for (int j = 0; j < m; ++j) {
+        T* Vj = V + 2 * vs * j;
+        vcycle<T>(c, w, Vj, Z + 2 * vs * j, 3, wv, nullptr);          // z_j = M^-1 v_j, w = A z_j
+        launch_fg_dots<T>(V, vs, wv, j, 0, c.partials, c.pstride, c.st, f.dev, n, c.nrhs, c.s);
+        launch_fg_axpy<T>(V, vs, wv, j, 0, c.partials, c.pstride, c.st, f.dev, c.nactive, n, c.nrhs, c.s);
+        launch_fg_dots<T>(V, vs, wv, j, 1, c.partials, c.pstride, c.st, f.dev, n, c.nrhs, c.s);
+        launch_fg_axpy<T>(V, vs, wv, j, 1, c.partials, c.pstride, c.st, f.dev, c.nactive, n, c.nrhs, c.s);
+        if (j + 1 < m) launch_fg_scale<T>(wv, V + 2 * vs * (j + 1), c.st, f.dev, j, n, c.nrhs, c.s);
+    }
+    launch_fg_backsolve(c.st, f.dev, c.nrhs, c.s);
+    launch_fg_update<T>(Z, vs, w.x.template as<T>(), c.st, f.dev, n, c.nrhs, c.s);
+}
+
+template <typename T>
+static int fgmres_inner(const SolveCtx& c, Inner<T>& w, FgBufs<T>& f, const T* rin, cudaGraphExec_t* graph,
+                        int* iters_done) {
+    HELM_CUDA_TRY(cudaMemsetAsync(c.nactive, 0, sizeof(int), c.s));
+    if (c.o.use_graphs) {
+        if (*graph == nullptr) {
+            cudaGraph_t g;
+            HELM_CUDA_TRY(cudaStreamBeginCapture(c.s, cudaStreamCaptureModeThreadLocal));
+            fgmres_cycle<T>(c, w, f, rin);
+            cudaError_t e = cudaStreamEndCapture(c.s, &g);
+            if (e != cudaSuccess) { set_last_error(cudaGetErrorString(e)); return HELM_E_CUDA; }
+            e = cudaGraphInstantiate(graph, g, 0);
+            cudaGraphDestroy(g);
+            if (e != cudaSuccess) { set_last_error(cudaGetErrorString(e)); *graph = nullptr; return HELM_E_CUDA; }
+        }
+        HELM_CUDA_TRY(cudaGraphLaunch(*graph, c.s));
+    } else {
+        fgmres_cycle<T>(c, w, f, rin);
+    }
+    const int m = f.dev.m;
+    count_launches(4 + (unsigned long long)m * (mg_kernels_per_apply(c.m) + 5));
+    HELM_CUDA_TRY(cudaGetLastError());
+    *iters_done += m;
     return HELM_OK;
 }
 
@@ -243,6 +396,7 @@ static int solve_impl(const helm_model* m, cudaStream_t s, int nrhs, const doubl
     c.nrhs = nrhs;
     c.o = o;
     c.pstride = 3 * max_blocks_per_rhs(m);
+    if (o.krylov == HELM_KRYLOV_FGMRES) c.pstride = std::max(c.pstride, kFgPartials);
     DBuf w2, st, part, nact, rin;
     TRY_ALLOC(w2, sizeof(double) * nrhs, s);
     TRY_ALLOC(st, sizeof(RhsState) * nrhs, s);
@@ -262,6 +416,12 @@ static int solve_impl(const helm_model* m, cudaStream_t s, int nrhs, const doubl
     Inner<T> w;
     rc = alloc_inner<T>(c, w);
     if (rc != HELM_OK) return rc;
+    const bool fgm = o.krylov == HELM_KRYLOV_FGMRES;
+    FgBufs<T> fb;
+    if (fgm) {
+        rc = alloc_fg<T>(c, fb);
+        if (rc != HELM_OK) return rc;
+    }
 
     std::vector<RhsState> hs(nrhs);
     std::memset(hs.data(), 0, sizeof(RhsState) * nrhs);
@@ -271,11 +431,15 @@ static int solve_impl(const helm_model* m, cudaStream_t s, int nrhs, const doubl
     HELM_CUDA_TRY(cudaMemsetAsync(part.p, 0, sizeof(double) * (size_t)c.pstride * nrhs, s));
     HELM_CUDA_TRY(cudaMemsetAsync(u64, 0, sizeof(double) * 2 * n * nrhs, s));
 
-    double floor_tol = 0.0;
+    // inner target per outer step: max(floor, fac * tol / relres). The complex64-only
+    // mode has no refinement, so it asks its one inner solve for a margin below tol
+    // to absorb the drift between the recursive and the true residual.
+    double floor_tol = 0.0, inner_fac = 0.9;
     int max_outer = o.max_outer;
     if (o.precision == HELM_PREC_MIXED) floor_tol = o.inner_tol;
-    if (o.precision == HELM_PREC_FP32) { floor_tol = o.tol; max_outer = 1; }
-    if (o.precision == HELM_PREC_FP64) floor_tol = 0.0;
+    if (o.precision == HELM_PREC_FP32) { inner_fac = 0.2; max_outer = 1; }
+    // FGMRES restarts through the outer refinement: allow enough cycles for max_it
+    if (fgm) max_outer = std::max(max_outer, (o.max_it + o.restart - 1) / o.restart + 1);
 
     std::vector<int> outer_count(nrhs, 0);
     cudaGraphExec_t graph = nullptr;
@@ -283,7 +447,7 @@ static int solve_impl(const helm_model* m, cudaStream_t s, int nrhs, const doubl
     const LevelDev L0 = level_dev(m, 0, true);
     for (int outer = 0;; ++outer) {
         launch_resid64<T>(L0, m->npml, m->alpha_max, c.w2, f64, u64, rin.as<T>(), c.partials, c.pstride, c.st, o.tol,
-                          floor_tol, outer == 0, nrhs, s);
+                          floor_tol, inner_fac, outer == 0, nrhs, s);
         count_launches(1);
         HELM_CUDA_TRY(cudaGetLastError());
         HELM_CUDA_TRY(cudaMemcpyAsync(hs.data(), c.st, sizeof(RhsState) * nrhs, cudaMemcpyDeviceToHost, s));
@@ -293,7 +457,9 @@ static int solve_impl(const helm_model* m, cudaStream_t s, int nrhs, const doubl
             if (hs[b].outer_active) { any = 1; }
         if (!any || outer >= max_outer) break;
         for (int b = 0; b < nrhs; ++b) outer_count[b] += hs[b].outer_active;
-        rc = inner_solve<T>(c, w, rin.as<T>(), &graph, &iters_done);
+        // BiCGSTAB keeps its recurrence across refinement steps (residual replacement)
+        rc = fgm ? fgmres_inner<T>(c, w, fb, rin.as<T>(), &graph, &iters_done)
+                 : inner_solve<T>(c, w, rin.as<T>(), &graph, &iters_done, outer > 0);
         if (rc != HELM_OK) break;
         launch_refine<T>(w.x.template as<T>(), u64, c.st, n, nrhs, s);
         count_launches(1);
@@ -356,16 +522,8 @@ int vcycle_once(const helm_model* m, cudaStream_t s, int nrhs, const double* h_w
     c.ncoarse = cs.n;
     c.minv = cs.mf.p;
     Inner<float> w;
-    const int nl = (int)m->lv.size();
-    w.fl.resize(nl);
-    w.el.resize(nl);
-    for (int l = 1; l < nl; ++l) {
-        const size_t b = sizeof(float) * 2 * m->lv[l].n() * nrhs;
-        w.fl[l].reset(new DBuf());
-        w.el[l].reset(new DBuf());
-        TRY_ALLOC(*w.fl[l], b, s);
-        TRY_ALLOC(*w.el[l], b, s);
-    }
+    rc = alloc_levels<float>(m, s, nrhs, w);
+    if (rc != HELM_OK) return rc;
     vcycle<float>(c, w, r, z, 0, nullptr, nullptr);
     HELM_CUDA_TRY(cudaGetLastError());
     HELM_CUDA_TRY(cudaStreamSynchronize(s));
@@ -442,7 +600,7 @@ int time_kernel(const helm_model* m, cudaStream_t s, int kernel, int nrhs, doubl
             *bytes = N * B * 32.0;
             break;
         case HELM_KERNEL_RESID64:
-            launch = [&] { launch_resid64<float>(level_dev(m, 0, true), m->npml, m->alpha_max, w2.as<double>(), D(0), D(1), rin.as<float>(), part.as<double>(), pstride, S, 0.0, 1e-4, 0, nrhs, s); };
+            launch = [&] { launch_resid64<float>(level_dev(m, 0, true), m->npml, m->alpha_max, w2.as<double>(), D(0), D(1), rin.as<float>(), part.as<double>(), pstride, S, 0.0, 1e-4, 0.9, 0, nrhs, s); };
             *bytes = N * (40.0 * B + 8.0);
             break;
         default:

@@ -44,6 +44,31 @@ void fwi_free(FwiState* st);
 
 int coarsest_points(const helm_model* m);
 
+// One application of the multigrid preconditioner z ~ M^{-1} in (V-cycle above
+// level lf, F-cycle from lf, levels >= lt in the shared-memory tail kernel).
+// f[l], e[l] (l >= 1): per-level right-hand side and correction buffers
+// [nrhs][n_l]. mode as launch_prolong on the finest level.
+struct MgCall {
+    const double* w2;       // (h omega)^2 per RHS, device
+    double b1, b2, wj;
+    RhsState* st;           // nullable
+    int nrhs;
+    cudaStream_t s;
+    const void* minv;       // coarsest dense inverses in the kernel's precision
+    const int* slot;
+    double* partials;       // finest-level dot reductions (modes 1, 2)
+    int pstride;
+};
+template <typename T>
+struct MgLevels {
+    T* f[kMaxLevels];
+    T* e[kMaxLevels];
+};
+template <typename T>
+void mg_apply(const helm_model* m, const MgCall& c, const MgLevels<T>& B, const T* in, T* out, int mode, T* y,
+              const T* aux);
+int mg_kernels_per_apply(const helm_model* m);
+
 int time_kernel(const helm_model* m, cudaStream_t s, int kernel, int nrhs, double hw2, int reps, double* ms,
                 double* bytes);
 

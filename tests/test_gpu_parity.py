@@ -81,7 +81,7 @@ def test_vcycle_matches_restatement(hg, ctx, name, make):
     model.close()
 
 
-@pytest.mark.parametrize("precision,tol,bound", [("fp64", 1e-10, 1e-6), ("mixed", 1e-10, 1e-6), ("fp32", 1e-5, 1e-4)])
+@pytest.mark.parametrize("precision,tol,bound", [("fp64", 1e-10, 1e-6), ("mixed", 1e-10, 1e-6), ("fp32", 5e-5, 1e-4)])
 def test_c1_wavefield_matches_oracle(hg, ctx, precision, tol, bound):
     mdl = models.c1_model()
     model = hg.helm_create_model(ctx, mdl.slowness, mdl.h, mdl.npml, mdl.alpha_max)
@@ -92,6 +92,29 @@ def test_c1_wavefield_matches_oracle(hg, ctx, precision, tol, bound):
     # physical part alone, as reported
     p = slice(mdl.npml, -mdl.npml)
     assert rel(u[0][p, p], ref[0][p, p]) < bound
+    model.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_fgmres_matches_oracle_and_bicgstab(hg, ctx, precision):
+    """Flexible GMRES (restart 20) on the small case and a batched pair of the batched
+    case: same wavefields as the oracle, and as BiCGSTAB, within the solve tolerance."""
+    mdl = models.c1_model()
+    model = hg.helm_create_model(ctx, mdl.slowness, mdl.h, mdl.npml, mdl.alpha_max)
+    opts = dict(tol=1e-10, precision=precision, krylov=hg.HELM_KRYLOV_FGMRES, restart=20)
+    u, stats, st = hg.helm_solve(model, mdl.omegas, mdl.sources, opts=opts)
+    ref = oracle.solve_fields(mdl.slowness, mdl.h, mdl.omegas[0], mdl.sources, mdl.npml, mdl.alpha_max)
+    assert st == hg.HELM_OK and stats[0]["converged"], stats
+    assert rel(u, ref) < 1e-6
+    model.close()
+    m3 = models.c3_model()
+    model = hg.helm_create_model(ctx, m3.slowness, m3.h, m3.npml, m3.alpha_max)
+    om = m3.omegas[[0, 4]]
+    src = m3.sources[[5, 40]]
+    uf, sf, _ = hg.helm_solve(model, om, src, opts=opts)
+    ub, sb, _ = hg.helm_solve(model, om, src, opts=dict(tol=1e-10, precision=precision))
+    for k in range(2):
+        assert sf[k]["converged"] and rel(uf[k], ub[k]) < 1e-6
     model.close()
 
 

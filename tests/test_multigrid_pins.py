@@ -39,6 +39,34 @@ def test_bilinear_reproduces_linear_functions():
     np.testing.assert_allclose(u.reshape(nz, nx)[inner], exact[inner], rtol=0, atol=1e-12)
 
 
+def test_galerkin_coarse_operator_closed_form():
+    """For constant coefficients, P^T M P of the grid-scaled 5-point Laplacian with bilinear
+    P is the textbook 9-point stencil (1/4)[-1 -2 -1; -2 12 -2; -1 -2 -1], and P^T diag(c) P is
+    c times the tensor square of the 1D stencil [1/4, 3/2, 1/4] (interior nodes)."""
+    nx = nz = 41
+    c = 3.7e-7
+    V = mg.VCycle(np.full((nz, nx), c), 0.0)                      # hw2 = 0: pure Laplacian
+    M1 = V.M[1].toarray()
+    n1 = nx // 2
+    i = (n1 // 2) * n1 + n1 // 2
+    lap = {(0, 0): 3.0, (1, 0): -0.5, (0, 1): -0.5, (1, 1): -0.25, (-1, 1): -0.25}
+    for (dx, dz), v in lap.items():
+        assert abs(M1[i, i + dz * n1 + dx] - v) < 1e-14
+        assert abs(M1[i, i - dz * n1 - dx] - v) < 1e-14
+    P = mg.prolongation(nx, nz)
+    K1 = (P.T @ (c * P)).toarray() / c
+    one = {0: 1.5, 1: 0.25, -1: 0.25}
+    for dz in (-1, 0, 1):
+        for dx in (-1, 0, 1):
+            assert abs(K1[i, i + dz * n1 + dx] - one[dx] * one[dz]) < 1e-14
+
+
+def test_tail_level_rule():
+    assert mg.tail_level(mg.level_shapes(1041, 1041)) == 3      # 130 x 130 = 16900 nodes
+    assert mg.tail_level(mg.level_shapes(441, 241)) == 2        # 110 x 60
+    assert mg.tail_level(mg.level_shapes(141, 141)) == 1        # 70 x 70
+
+
 def test_vcycle_iteration_converges_to_direct_solution():
     rng = np.random.default_rng(4)
     mdl = models.c1_model()
@@ -54,7 +82,8 @@ def test_vcycle_iteration_converges_to_direct_solution():
         u = u + V.apply(f - M @ u)
         errs.append(np.linalg.norm(u - exact) / np.linalg.norm(exact))
     assert errs[-1] < 1e-6, errs[::20]
-    assert all(b < a for a, b in zip(errs[::20], errs[20::20]))
+    # contracting until round-off
+    assert all(b < a for a, b in zip(errs[::20], errs[20::20]) if a > 1e-12)
 
 
 def test_jacobi_damps_checkerboard():
