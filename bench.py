@@ -45,6 +45,14 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--krylov", default="bicgstab", choices=["bicgstab", "fgmres"])
+    ap.add_argument("--restart", type=int, default=30, help="FGMRES restart length")
+    ap.add_argument("--inner-tol", type=float, default=1e-2, help="mixed precision: reduction per inner solve")
+    ap.add_argument("--tune", action="store_true", help="autotune the multigrid tiles before timing")
+    ap.add_argument("--workload", default="single", choices=["single", "batched", "serving"],
+                    help="single: the single large case (the default line); batched: 64 shots x 5 "
+                         "frequencies in one call; serving: a Poisson stream of requests")
+    ap.add_argument("--requests", type=int, default=48, help="serving: number of requests")
+    ap.add_argument("--rate", type=float, default=0.0, help="serving: arrivals per second (0: 0.8 x measured)")
     return ap.parse_args()
 
 
@@ -185,7 +193,11 @@ def run_ours(args):
     n = model.n
     om = mdl.omegas
     kry = {"bicgstab": _lib.HELM_KRYLOV_BICGSTAB, "fgmres": _lib.HELM_KRYLOV_FGMRES}[args.krylov]
-    opts = api.helm_default_opts(tol=1e-6, precision="mixed", krylov=kry)
+    opts = api.helm_default_opts(tol=1e-6, precision="mixed", krylov=kry, restart=args.restart,
+                                 inner_tol=args.inner_tol)
+    if args.tune:
+        from paper_1712_08743_gb300 import autotune
+        autotune.autotune(model, 1, float(om[0]))
     # device-resident input (point source, grid-scaled form is built by the library from f)
     f_host = np.zeros((1, model.nz, model.nx), np.complex128)
     sx, sz = mdl.sources[0]
@@ -294,6 +306,7 @@ def run_ours(args):
                        "unknowns": n, "precision": "complex64 inner, FP64 residual/refinement",
                        "krylov": ("BiCGSTAB" if args.krylov == "bicgstab" else "FGMRES(30)") +
                                  " + shifted-Laplace Galerkin MG (V above the tail level, F below), beta=(1,0.5)",
+                       "inner_tol": args.inner_tol, "restart": args.restart if args.krylov == "fgmres" else None,
                        "levels": model.nlevels, "l2": "flushed between timed steps (258 MB write)",
                        "parallelism": f"replicas x{world}"},
             "p50_ms": float(np.percentile(ms, 50)), "p99_ms": float(np.percentile(ms, 99)),
@@ -314,10 +327,104 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_batched(args):
+    """64 surface shots x 5 frequencies (3..7 Hz) on the 401 x 201 layered model, one call."""
+    import torch
+
+    from paper_1712_08743_gb300 import _lib, api, build
+    from synth import models
+
+    build.build()
+    lib = _lib.load()
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    ctx = api.Context(0, stream)
+    mdl = models.c3_model()
+    model = api.helm_create_model(ctx, mdl.slowness, mdl.h, mdl.npml, mdl.alpha_max)
+    om = np.repeat(mdl.omegas, len(mdl.sources))
+    src = np.tile(mdl.sources, (len(mdl.omegas), 1))
+    kry = {"bicgstab": _lib.HELM_KRYLOV_BICGSTAB, "fgmres": _lib.HELM_KRYLOV_FGMRES}[args.krylov]
+    opts = api.helm_default_opts(tol=1e-6, precision="mixed", krylov=kry, restart=args.restart,
+                                 inner_tol=args.inner_tol)
+    if args.tune:
+        from paper_1712_08743_gb300 import autotune
+        autotune.autotune(model, len(om), float(om[0]))
+    F = np.zeros((len(om), model.nz, model.nx), np.complex128)
+    for k, (sx, sz) in enumerate(src):
+        F[k, sz + mdl.npml, sx + mdl.npml] = 1.0 / mdl.h ** 2
+    f_dev = torch.from_numpy(F).cuda()
+    u_dev = torch.empty_like(f_dev)
+    for _ in range(max(args.warmup, 1)):
+        api.helm_solve(model, om, f=f_dev, opts=opts, out=u_dev)
+    ms = []
+    for _ in range(args.steps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        _, st, _ = api.helm_solve(model, om, f=f_dev, opts=opts, out=u_dev)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms.append(a.elapsed_time(b))
+    its = [s["iters"] for s in st]
+    print(json.dumps({"metric": "helmholtz_solves_per_s", "workload": "batched_401x201_64src_5f",
+                      "value": len(om) * 1e3 / float(np.mean(ms)), "unit": "solves/s", "ms_per_batch": float(np.mean(ms)),
+                      "nrhs": len(om), "krylov": args.krylov, "iters_min": min(its), "iters_max": max(its),
+                      "converged": all(s["converged"] for s in st)}), flush=True)
+
+
+def run_serving(args):
+    """A Poisson stream of requests of mixed grid sizes and frequencies (ten points per
+    wavelength at 1500 m/s), served with continuous batching; p50/p99 latency and
+    solves/s, beside the same requests solved one at a time in plain FP64."""
+    import threading as th
+
+    from paper_1712_08743_gb300 import _lib, api, build
+    from synth import models
+
+    build.build()
+    ctx = api.Context(0)
+    reqs = [models.c5_request(i, sizes=(128, 256, 512)) for i in range(args.requests)]
+    opts = dict(tol=1e-6, precision="mixed", krylov=_lib.HELM_KRYLOV_FGMRES, max_it=20000)
+    # sequential plain FP64 on a subset
+    o64 = dict(tol=1e-6, precision="fp64", max_it=20000)
+    t_seq = []
+    for r in reqs[: min(8, len(reqs))]:
+        mm = api.helm_create_model(ctx, r.slowness, r.h)
+        t0 = time.perf_counter()
+        api.helm_solve(mm, r.omegas, r.sources, opts=o64)
+        t_seq.append(time.perf_counter() - t0)
+        mm.close()
+    seq_rate = 1.0 / float(np.mean(t_seq))
+    rate = args.rate if args.rate > 0 else 0.8 * 4 * seq_rate
+    api.helm_serve_config(ctx, max_batch=16, max_slots=4)
+    rng = np.random.default_rng(5)
+    gaps = rng.exponential(1.0 / rate, len(reqs))
+    tickets = []
+    t_start = time.perf_counter()
+    for r, g in zip(reqs, gaps):
+        time.sleep(g)
+        tickets.append(api.helm_submit(ctx, r.slowness, r.h, r.omegas[0], r.sources[0], opts=opts))
+    res = [api.helm_poll(ctx, t, -1) for t in tickets]
+    t_total = time.perf_counter() - t_start
+    lat = [x.latency_ms for x in res]
+    print(json.dumps({"metric": "helmholtz_solves_per_s", "workload": f"serving_{len(reqs)}req_128-512",
+                      "value": len(reqs) / t_total, "unit": "solves/s", "p50_ms": float(np.percentile(lat, 50)),
+                      "p99_ms": float(np.percentile(lat, 99)), "arrival_rate": rate,
+                      "sequential_fp64_solves_per_s": seq_rate,
+                      "ok": sum(x.status == 0 for x in res), "mean_batch": float(np.mean([x.batch_size for x in res]))}),
+          flush=True)
+    for t in tickets:
+        api.helm_release(ctx, t)
+    ctx.close()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batched":
+        run_batched(args)
+    elif args.workload == "serving":
+        run_serving(args)
     else:
         run_ours(args)
 

@@ -95,7 +95,7 @@ typedef struct {
 } helm_solve_stats;
 
 /* Fills *opts with the defaults: tol 1e-6, max_it 5000, BiCGSTAB, restart 30,
- * mixed precision, beta = (1, 0.5), omega_jacobi 0.8, inner_tol 1e-4,
+ * mixed precision, beta = (1, 0.5), omega_jacobi 0.5, inner_tol 1e-2,
  * max_outer 20, check_every 10, host pointers, graphs on. */
 void helm_default_opts(helm_solve_opts* opts);
 
@@ -220,6 +220,17 @@ int helm_time_kernel(helm_model* model, int kernel, int nrhs, double omega, int 
  *    them. */
 int helm_vcycle_noalloc(helm_model* model, int nrhs, const double* omega, double beta1, double beta2,
                         double omega_jacobi, const void* r, void* z);
+
+/* Autotuner (no counterpart in the paper): times the two tile shapes of each
+ * complex64 multigrid kernel on the grid levels of this model (finest-level
+ * prolongation; Galerkin restriction and prolongation) for nrhs right-hand
+ * sides at angular frequency omega, keeps the faster in the model, and writes
+ * the choices to tiles_out (nullable): int[48], restriction tiles per level
+ * then prolongation tiles per level, each 0 (smaller) or 1 (larger, the
+ * default). helm_set_tiles applies a stored choice. Tile shapes change the
+ * speed, not the arithmetic of a node (dot products may sum in another order). */
+int helm_autotune(helm_model* model, int nrhs, double omega, int* tiles_out);
+int helm_set_tiles(helm_model* model, const int* tiles);
 
 /* ---------------------------------------------------------------- serving
  * Continuous batching: requests enter a host queue; a scheduler thread admits

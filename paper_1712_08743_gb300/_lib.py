@@ -115,6 +115,8 @@ SIGNATURES = {
     "helm_apply": (_I, [_P, _I, _pD, _I, _P, _P, _I]),
     "helm_vcycle": (_I, [_P, _I, _pD, _D, _D, _D, _P, _P, _I]),
     "helm_vcycle_noalloc": (_I, [_P, _I, _pD, _D, _D, _D, _P, _P]),
+    "helm_autotune": (_I, [_P, _I, _D, _pI]),
+    "helm_set_tiles": (_I, [_P, _pI]),
     "helm_time_kernel": (_I, [_P, _I, _I, _D, _I, _pD, _pD]),
     "helm_submit": (_I, [_P, C.POINTER(helm_request), C.POINTER(C.c_uint64)]),
     "helm_poll": (_I, [_P, C.c_uint64, _I, C.POINTER(helm_result)]),

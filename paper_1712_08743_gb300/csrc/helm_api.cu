@@ -73,6 +73,7 @@ int create_model(helm_ctx* ctx, cudaStream_t s, int Px, int Pz, double h, const 
     m->Px = Px; m->Pz = Pz; m->npml = npml; m->h = h; m->alpha_max = alpha_max;
     m->nx = Px + 2 * npml; m->nz = Pz + 2 * npml;
     m->nmodels = nmodels;
+    for (int l = 0; l < kMaxLevels; ++l) { m->tile_restrict[l] = 1; m->tile_prolong[l] = 1; }
     // levels: halve per axis while the level is larger than the dense-coarse size
     Level L0; L0.nx = m->nx; L0.nz = m->nz; L0.h = h;
     m->lv.push_back(L0);
@@ -89,12 +90,14 @@ int create_model(helm_ctx* ctx, cudaStream_t s, int Px, int Pz, double h, const 
     m->lf = L;
     for (int l = 1; l <= L; ++l)
         if (m->lv[l].n() <= (size_t)kFcycleMaxPoints) { m->lf = l; break; }
-    m->lt = L;
-    for (int l = m->lf; l <= L; ++l)
-        if (m->lv[l].n() <= (size_t)kTailMaxPoints) { m->lt = l; break; }
-    m->tail_smem32 = tail_smem_bytes(m, sizeof(float));
-    m->tail_smem64 = tail_smem_bytes(m, sizeof(double));
-    if (m->tail_smem64 > 227u * 1024u) { set_last_error("tail levels exceed shared memory"); delete m; return HELM_E_INVALID; }
+    for (int d = 0; d < 2; ++d) {
+        const size_t cap = d ? (size_t)kTailMaxPoints64 : (size_t)kTailMaxPoints32;
+        m->lt[d] = L;
+        for (int l = m->lf; l <= L; ++l)
+            if (m->lv[l].n() <= cap) { m->lt[d] = l; break; }
+        m->tail_smem[d] = tail_smem_bytes(m, m->lt[d], d ? sizeof(double) : sizeof(float));
+        if (m->tail_smem[d] > 227u * 1024u) { set_last_error("tail levels exceed shared memory"); delete m; return HELM_E_INVALID; }
+    }
     if (L + 1 > kMaxLevels) { set_last_error("too many levels"); delete m; return HELM_E_INVALID; }
     auto fail = [&](cudaError_t e) {
         set_last_error(cudaGetErrorString(e));
@@ -111,20 +114,28 @@ int create_model(helm_ctx* ctx, cudaStream_t s, int Px, int Pz, double h, const 
         if ((e = cudaMalloc(&Lv.gkf, sizeof(float) * kGalerkinCoefs * Lv.n() * nmodels)) != cudaSuccess) return fail(e);
         if ((e = cudaMalloc(&Lv.gkd, sizeof(double) * kGalerkinCoefs * Lv.n() * nmodels)) != cudaSuccess) return fail(e);
     }
-    const std::vector<int> opsf = tail_schedule(m->lt, L, true), opsv = tail_schedule(m->lt, L, false);
-    m->nops_f = (int)opsf.size();
-    m->nops_v = (int)opsv.size();
-    if ((e = cudaMalloc(&m->ops_f, sizeof(int) * opsf.size())) != cudaSuccess) return fail(e);
-    if ((e = cudaMalloc(&m->ops_v, sizeof(int) * opsv.size())) != cudaSuccess) return fail(e);
+    std::vector<int> opsf[2], opsv[2];
+    for (int d = 0; d < 2; ++d) {
+        opsf[d] = tail_schedule(m->lt[d], L, true);
+        opsv[d] = tail_schedule(m->lt[d], L, false);
+        m->nops_f[d] = (int)opsf[d].size();
+        m->nops_v[d] = (int)opsv[d].size();
+        if ((e = cudaMalloc(&m->ops_f[d], sizeof(int) * opsf[d].size())) != cudaSuccess) return fail(e);
+        if ((e = cudaMalloc(&m->ops_v[d], sizeof(int) * opsv[d].size())) != cudaSuccess) return fail(e);
+    }
     DevMem phys, msq;
     if ((e = cudaMalloc(&phys.p, sizeof(double) * np * nmodels)) != cudaSuccess) return fail(e);
     if ((e = cudaMalloc(&msq.p, sizeof(double))) != cudaSuccess) return fail(e);
     if ((e = cudaMemcpyAsync(phys.p, slowness, sizeof(double) * np * nmodels, cudaMemcpyHostToDevice, s)) != cudaSuccess)
         return fail(e);
-    if ((e = cudaMemcpyAsync(m->ops_f, opsf.data(), sizeof(int) * opsf.size(), cudaMemcpyHostToDevice, s)) != cudaSuccess)
-        return fail(e);
-    if ((e = cudaMemcpyAsync(m->ops_v, opsv.data(), sizeof(int) * opsv.size(), cudaMemcpyHostToDevice, s)) != cudaSuccess)
-        return fail(e);
+    for (int d = 0; d < 2; ++d) {
+        if ((e = cudaMemcpyAsync(m->ops_f[d], opsf[d].data(), sizeof(int) * opsf[d].size(), cudaMemcpyHostToDevice, s)) !=
+            cudaSuccess)
+            return fail(e);
+        if ((e = cudaMemcpyAsync(m->ops_v[d], opsv[d].data(), sizeof(int) * opsv[d].size(), cudaMemcpyHostToDevice, s)) !=
+            cudaSuccess)
+            return fail(e);
+    }
     launch_pad_model(static_cast<double*>(phys.p), Px, Pz, npml, nmodels, m->m_pad, m->lv[0].m2f, m->lv[0].m2d, s);
     for (int l = 1; l <= L; ++l) launch_galerkin(m, l, s);
     launch_sumsq(static_cast<double*>(phys.p), np, static_cast<double*>(msq.p), s);
@@ -150,7 +161,7 @@ void helm_default_opts(helm_solve_opts* o) {
     o->beta1 = 1.0;
     o->beta2 = 0.5;
     o->omega_jacobi = 0.5;
-    o->inner_tol = 1e-4;
+    o->inner_tol = 1e-2;
     o->max_outer = 20;
     o->check_every = 10;
     o->device_ptrs = 0;
@@ -216,8 +227,10 @@ void helm_destroy_model(helm_model* m) {
     if (!m) return;
     DeviceGuard g(m->ctx->device);
     if (m->m_pad) cudaFree(m->m_pad);
-    if (m->ops_f) cudaFree(m->ops_f);
-    if (m->ops_v) cudaFree(m->ops_v);
+    for (int d = 0; d < 2; ++d) {
+        if (m->ops_f[d]) cudaFree(m->ops_f[d]);
+        if (m->ops_v[d]) cudaFree(m->ops_v[d]);
+    }
     for (auto& L : m->lv) {
         if (L.m2f) cudaFree(L.m2f);
         if (L.m2d) cudaFree(L.m2d);
@@ -306,8 +319,10 @@ int helm_apply(helm_model* m, int nrhs, const double* omega, int precision, cons
     const bool dbl = precision == HELM_PREC_FP64;
     const size_t bytes = (dbl ? 16 : 8) * m->n() * nrhs;
     DevMem dw2, du, dy;
+    std::vector<float> w2f(w2.begin(), w2.end());
     if (cudaMalloc(&dw2.p, sizeof(double) * nrhs) != cudaSuccess) { cudaGetLastError(); return HELM_E_NOMEM; }
-    HELM_CUDA_TRY(cudaMemcpyAsync(dw2.p, w2.data(), sizeof(double) * nrhs, cudaMemcpyHostToDevice, s));
+    if (dbl) HELM_CUDA_TRY(cudaMemcpyAsync(dw2.p, w2.data(), sizeof(double) * nrhs, cudaMemcpyHostToDevice, s));
+    else HELM_CUDA_TRY(cudaMemcpyAsync(dw2.p, w2f.data(), sizeof(float) * nrhs, cudaMemcpyHostToDevice, s));
     const void* up = u;
     void* yp = y;
     if (!device_ptrs) {
@@ -324,11 +339,11 @@ int helm_apply(helm_model* m, int nrhs, const double* omega, int precision, cons
         launch_apply<double>(level_dev(m, 0, true), m->npml, m->alpha_max, static_cast<double*>(dw2.p),
                              static_cast<const double*>(up), static_cast<double*>(yp), sc, nrhs, s);
     else
-        launch_apply<float>(level_dev(m, 0, false), m->npml, m->alpha_max, static_cast<double*>(dw2.p),
+        launch_apply<float>(level_dev(m, 0, false), m->npml, m->alpha_max, static_cast<float*>(dw2.p),
                             static_cast<const float*>(up), static_cast<float*>(yp), (float)sc, nrhs, s);
     HELM_CUDA_TRY(cudaGetLastError());
     if (!device_ptrs) HELM_CUDA_TRY(cudaMemcpyAsync(y, yp, bytes, cudaMemcpyDeviceToHost, s));
-    HELM_CUDA_TRY(cudaStreamSynchronize(s));
+    HELM_CUDA_TRY(cudaStreamSynchronize(s));   // the host copies above are sources of async copies
     return HELM_OK;
 }
 
@@ -336,6 +351,26 @@ int helm_time_kernel(helm_model* m, int kernel, int nrhs, double omega, int reps
     if (!m || nrhs < 1 || reps < 1 || !finite_pos(omega) || !ms || !bytes) return HELM_E_INVALID;
     DeviceGuard g(m->ctx->device);
     return time_kernel(m, m->ctx->stream, kernel, nrhs, m->h * m->h * omega * omega, reps, ms, bytes);
+}
+
+int helm_autotune(helm_model* m, int nrhs, double omega, int* tiles_out) {
+    if (!m || nrhs < 1 || !finite_pos(omega)) return HELM_E_INVALID;
+    DeviceGuard g(m->ctx->device);
+    int tiles[2 * kMaxLevels];
+    int rc = autotune(m, m->ctx->stream, nrhs, m->h * m->h * omega * omega, 5, tiles);
+    if (rc == HELM_OK && tiles_out) std::memcpy(tiles_out, tiles, sizeof(tiles));
+    return rc;
+}
+
+int helm_set_tiles(helm_model* m, const int* tiles) {
+    if (!m || !tiles) return HELM_E_INVALID;
+    for (int k = 0; k < 2 * kMaxLevels; ++k)
+        if (tiles[k] != 0 && tiles[k] != 1) return HELM_E_INVALID;
+    for (int l = 0; l < kMaxLevels; ++l) {
+        m->tile_restrict[l] = tiles[l];
+        m->tile_prolong[l] = tiles[kMaxLevels + l];
+    }
+    return HELM_OK;
 }
 
 int helm_vcycle(helm_model* m, int nrhs, const double* omega, double beta1, double beta2, double omega_jacobi,

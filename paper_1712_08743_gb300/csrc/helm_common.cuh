@@ -98,6 +98,15 @@ struct RhsState {
     unsigned int counter[4];  // last-block election counters, one per reduction site
 };
 
+// ------------------------------------------------ programmatic dependent launch
+// Kernels of the iteration chain let the next kernel start launching at once
+// (its blocks then wait in pdl_wait until this grid has completed and its
+// writes are visible), so launch latency and prologues that read only
+// immutable model data overlap the previous kernel. Without a programmatic
+// dependency both instructions return immediately.
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 // -------------------------------------------------------------- reductions
 __device__ __forceinline__ int lin_tid() { return threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z); }
 __device__ __forceinline__ int lin_nthreads() { return blockDim.x * blockDim.y * blockDim.z; }
@@ -128,6 +137,68 @@ __device__ __forceinline__ void block_sum(double (&v)[NV], double* sh /* >= 32*N
         for (int k = 0; k < NV; ++k) v[k] = (lane < nwarps) ? sh[k * 32 + lane] : 0.0;
         warp_sum<NV>(v);
     }
+}
+
+// Block-wide sum of per-thread partials held in the kernel's precision A: the
+// warp stage runs in A, only warp totals are widened to double (so an FP32
+// kernel issues almost no FP64 instructions). Result in linear thread 0.
+template <int NV, typename A>
+__device__ __forceinline__ void block_sum_t(const A (&v)[NV], double (&o)[NV], double* sh /* >= 32*NV */) {
+    A w[NV];
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+        w[k] = v[k];
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) w[k] += __shfl_xor_sync(0xffffffffu, w[k], d);
+    }
+    const int tid = lin_tid();
+    const int lane = tid & 31, warp = tid >> 5;
+    const int nwarps = (lin_nthreads() + 31) >> 5;
+    __syncthreads();
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < NV; ++k) sh[k * 32 + warp] = (double)w[k];
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < NV; ++k) o[k] = 0.0;
+    if (warp == 0) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) o[k] = (lane < nwarps) ? sh[k * 32 + lane] : 0.0;
+        warp_sum<NV>(o);
+    }
+}
+
+// As last_block_reduce, from per-thread partials in precision A; the totals
+// land in tot (thread 0 of the last block).
+template <int NV, typename A>
+__device__ __forceinline__ bool last_block_reduce_t(const A (&v)[NV], double (&tot)[NV], double* sh, double* partials,
+                                                    int nblk, int blk, unsigned int* counter) {
+    block_sum_t<NV, A>(v, tot, sh);
+    __shared__ int s_last_t;
+    const int tid = lin_tid();
+    if (tid == 0) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) partials[(size_t)k * nblk + blk] = tot[k];
+        __threadfence();
+        unsigned int prev = atomicAdd(counter, 1u);
+        s_last_t = (prev == (unsigned int)(nblk - 1));
+    }
+    __syncthreads();
+    if (!s_last_t) return false;
+    __threadfence();
+    double acc[NV];
+#pragma unroll
+    for (int k = 0; k < NV; ++k) acc[k] = 0.0;
+    for (int i = tid; i < nblk; i += lin_nthreads())
+#pragma unroll
+        for (int k = 0; k < NV; ++k) acc[k] += __ldcg(partials + (size_t)k * nblk + i);
+    block_sum<NV>(acc, sh);
+    if (tid == 0) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) tot[k] = acc[k];
+        *counter = 0u;
+    }
+    return true;
 }
 
 // Writes this block's NV partial sums and elects the last block of the

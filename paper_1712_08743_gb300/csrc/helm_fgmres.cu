@@ -28,12 +28,14 @@ __global__ void __launch_bounds__(256) k_fg_norm(const T* __restrict__ rin, doub
     __shared__ double sh[32];
     const int b = blockIdx.z;
     if (!st[b].outer_active) return;
-    double acc[1] = {0.0};
+    T a0 = 0;
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
         const cx<T> c = ldc(rin, n * b + i);
-        acc[0] += (double)c.re * c.re + (double)c.im * c.im;
+        a0 += c.re * c.re + c.im * c.im;
     }
-    if (last_block_reduce<1>(acc, sh, partials + (size_t)b * pstride, gridDim.x, blockIdx.x, &st[b].counter[1])) {
+    const T vv[1] = {a0};
+    double acc[1];
+    if (last_block_reduce_t<1, T>(vv, acc, sh, partials + (size_t)b * pstride, gridDim.x, blockIdx.x, &st[b].counter[1])) {
         if (threadIdx.x == 0) {
             RhsState& S = st[b];
             S.bnorm2 = acc[0];
@@ -54,8 +56,13 @@ __global__ void k_fg_scale(const T* __restrict__ w, T* __restrict__ v, const Rhs
                            size_t n) {
     const int b = blockIdx.z;
     if (!st[b].active) return;
-    const double s = j < 0 ? fg.g[(size_t)b * (fg.m + 1)].x : fg.hsub[(size_t)b * fg.m + j];
-    const T inv = (T)(1.0 / s);
+    __shared__ T s_inv;
+    if (threadIdx.x == 0) {
+        const double s = j < 0 ? fg.g[(size_t)b * (fg.m + 1)].x : fg.hsub[(size_t)b * fg.m + j];
+        s_inv = (T)(1.0 / s);
+    }
+    __syncthreads();
+    const T inv = s_inv;
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
         stc(v, n * b + i, inv * ldc(w, n * b + i));
 }
@@ -90,9 +97,9 @@ __global__ void __launch_bounds__(256) k_fg_dots(const T* __restrict__ V, size_t
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
 #pragma unroll
     for (int k = 0; k < 2 * kChunk; ++k) {
-        double v = (double)acc[k];
+        T v = acc[k];
         for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if (lane == 0) sh[k][warp] = v;
+        if (lane == 0) sh[k][warp] = (double)v;
     }
     __syncthreads();
     const int nblk = gridDim.x * gridDim.y, blk = blockIdx.y * gridDim.x + blockIdx.x;
@@ -141,15 +148,17 @@ __global__ void __launch_bounds__(256) k_fg_axpy(const T* __restrict__ V, size_t
     const size_t col = (size_t)b * (fg.m + 1);
     for (int i = threadIdx.x; i <= j; i += blockDim.x) coef[i] = cx<T>((T)fg.tmp[col + i].x, (T)fg.tmp[col + i].y);
     __syncthreads();
-    double acc[1] = {0.0};
+    T a0 = 0;
     for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < n; p += (size_t)gridDim.x * blockDim.x) {
         cx<T> wv = ldcc(w, n * b + p);
         for (int i = 0; i <= j; ++i) wv = wv - coef[i] * ldc(V + 2 * vstride * i, n * b + p);
         stc(w, n * b + p, wv);
-        acc[0] += (double)wv.re * wv.re + (double)wv.im * wv.im;
+        a0 += wv.re * wv.re + wv.im * wv.im;
     }
     if (!norm) return;
-    if (last_block_reduce<1>(acc, sh, partials + (size_t)b * pstride, gridDim.x, blockIdx.x, &st[b].counter[0])) {
+    const T vv[1] = {a0};
+    double acc[1];
+    if (last_block_reduce_t<1, T>(vv, acc, sh, partials + (size_t)b * pstride, gridDim.x, blockIdx.x, &st[b].counter[0])) {
         if (threadIdx.x == 0) {
             RhsState& S = st[b];
             const int m = fg.m;

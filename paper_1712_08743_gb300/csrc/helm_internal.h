@@ -18,7 +18,9 @@ namespace helm {
 constexpr int kCoarseMaxPoints = 128;   // coarsening stops once a level has this few nodes
 constexpr int kCoarseHardMax = 256;     // largest coarsest level the dense inverse accepts
 constexpr int kFcycleMaxPoints = 24576; // the F-cycle starts at the first level this small
-constexpr int kTailMaxPoints = 3072;    // levels this small run in shared memory, one block per RHS
+// levels this small run in shared memory, one block per RHS (complex64 / complex128)
+constexpr int kTailMaxPoints32 = 2048;
+constexpr int kTailMaxPoints64 = 1024;
 constexpr int kMaxLevels = 24;
 constexpr int kMaxRestart = 32;
 constexpr int kFgPartials = 16 * 5 * 512;   // FGMRES dot partials per RHS (2 x 8 values x 5 chunks x 512 blocks)
@@ -72,11 +74,19 @@ struct helm_model {
     double h = 0, alpha_max = 0;
     int nmodels = 1;                      // > 1: one slowness model per right-hand side (serving batches)
     int lf = 1;                           // first level of the F-cycle (V-cycle above)
-    int lt = 1;                           // first level handled by the shared-memory tail kernel (lt >= lf)
-    int* ops_f = nullptr;                 // device: tail schedules, F- and V-cycle from level lt
-    int* ops_v = nullptr;
-    int nops_f = 0, nops_v = 0;
-    size_t tail_smem32 = 0, tail_smem64 = 0;   // dynamic shared memory of the tail kernel
+    // Per precision (0: complex64, 1: complex128): first level handled by the
+    // shared-memory tail kernel (>= lf), its F- and V-cycle schedules on the
+    // device and its dynamic shared memory.
+    int lt[2] = {1, 1};
+    int* ops_f[2] = {nullptr, nullptr};
+    int* ops_v[2] = {nullptr, nullptr};
+    int nops_f[2] = {0, 0}, nops_v[2] = {0, 0};
+    size_t tail_smem[2] = {0, 0};
+    // complex64 tile choices per level (0 smaller, 1 larger tiles; see the launchers),
+    // set by helm_autotune / helm_set_tiles
+    int tile_restrict[helm::kMaxLevels];
+    int tile_prolong[helm::kMaxLevels];
+    int tail_level(bool dbl) const { return lt[dbl ? 1 : 0]; }
     double* m_pad = nullptr;              // device [nmodels][nz][nx] slowness (float64)
     double msq_sum = 0;                   // sum of m^2 over the physical cells
     std::vector<helm::Level> lv;          // lv[0] is the padded fine grid
@@ -114,7 +124,7 @@ inline LevelDev level_dev(const helm_model* m, int l, bool dbl) {
 enum TailOp : int { OP_SMOOTH0 = 0, OP_RESID = 1, OP_RESTRICT = 2, OP_PROLONG_ADD = 3, OP_JACOBI = 4,
                     OP_COARSE = 5, OP_OUTPUT = 6, OP_LOAD = 7 };
 std::vector<int> tail_schedule(int lt, int L, bool fcycle);
-size_t tail_smem_bytes(const helm_model* m, size_t elem);
+size_t tail_smem_bytes(const helm_model* m, int lt, size_t elem);
 
 // Arguments of the tail kernel: levels lt..L of the cycle for one RHS per
 // block, every vector of those levels in shared memory.
@@ -139,8 +149,9 @@ void launch_pad_model(const double* m_phys, int Px, int Pz, int npml, int nmodel
 void launch_galerkin(const helm_model* m, int l, cudaStream_t s);   // builds level l >= 1 from level l - 1
 void launch_sumsq(const double* a, size_t count, double* out, cudaStream_t s);
 
+// hw: per-RHS (h omega)^2 in the kernel's precision
 template <typename T>
-void launch_apply(const LevelDev& L0, int npml, double amax, const double* w2, const T* u, T* y,
+void launch_apply(const LevelDev& L0, int npml, double amax, const T* hw, const T* u, T* y,
                   T scale, int nrhs, cudaStream_t s);
 
 // Outer FP64 residual r = f - A u; TI = precision of the inner right-hand side.
@@ -173,18 +184,19 @@ void launch_tail(const TailArgs& a, size_t smem, int nrhs, const RhsState* st, c
 // F-cycle step on a grid level: u2 = wj D^-1 f + P e (e the first coarse
 // correction), residual f - M u2, restricted to level l + 1.
 template <typename T>
-void launch_correct_restrict(const LevelDev& Lf, const LevelDev& Lc, const double* w2, double b1, double b2,
-                             double wj, const T* f, const T* ec, T* fc, const RhsState* st, int nrhs, cudaStream_t s);
+void launch_correct_restrict(const LevelDev& Lf, const LevelDev& Lc, const T* w2, double b1, double b2,
+                             double wj, const T* f, const T* ec, T* fc, const RhsState* st, int nrhs, cudaStream_t s,
+                             int tile = 1);
 template <typename T>
-void launch_restrict(const LevelDev& Lf, const LevelDev& Lc, const double* w2, double b1, double b2,
-                     double wj, const T* f, T* fc, const RhsState* st, int nrhs, cudaStream_t s);
+void launch_restrict(const LevelDev& Lf, const LevelDev& Lc, const T* w2, double b1, double b2,
+                     double wj, const T* f, T* fc, const RhsState* st, int nrhs, cudaStream_t s, int tile = 1);
 // mode 0: out = smoothed correction; 1: out = p^, y = A p^, alpha = rho/<rh, y>;
 // 2: out = s^, y = A s^, omega = <y, s>/<y, y>; 3: out = z, y = A z (no dots).
 template <typename T>
 void launch_prolong(int mode, const LevelDev& Lf, const LevelDev& Lc, int npml, double amax,
-                    const double* w2, double b1, double b2, double wj, const T* f, const T* ec, T* out,
+                    const T* w2, double b1, double b2, double wj, const T* f, const T* ec, T* out,
                     T* y, const T* aux, double* partials, int pstride, RhsState* st, int nrhs,
-                    cudaStream_t s, int accumulate = 0);
+                    cudaStream_t s, int accumulate = 0, int tile = 1);
 template <typename T>
 void launch_coarse(int n, const T* minv, const int* slot, const T* fL, T* eL, const RhsState* st,
                    int nrhs, cudaStream_t s);

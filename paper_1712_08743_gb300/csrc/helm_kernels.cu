@@ -29,6 +29,23 @@ inline int grid1d(size_t n) {
     return (int)g;
 }
 
+// Launch with programmatic stream serialization (the kernel must call pdl_wait
+// before reading anything an earlier kernel of the stream writes).
+template <typename... KArgs, typename... Args>
+void launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
 }  // namespace
 
 // ===================================================================== model
@@ -71,7 +88,7 @@ void launch_sumsq(const double* a, size_t count, double* out, cudaStream_t s) { 
 // ============================================================ stencil apply
 // y = scale * A u on the fine grid (with the damping layer).
 template <typename T>
-__global__ void __launch_bounds__(256) k_apply(LevelDev L, int npml, double acoef, const double* __restrict__ w2,
+__global__ void __launch_bounds__(256) k_apply(LevelDev L, int npml, T acoef, const T* __restrict__ hwv,
                                                const T* __restrict__ u, T* __restrict__ y, T scale) {
     const int b = blockIdx.z;
     const int ix = blockIdx.x * 32 + threadIdx.x, iz = blockIdx.y * 8 + threadIdx.y;
@@ -79,9 +96,9 @@ __global__ void __launch_bounds__(256) k_apply(LevelDev L, int npml, double acoe
     const size_t n = (size_t)L.nx * L.nz;
     const T* ub = u + 2 * n * b;
     const size_t i = (size_t)iz * L.nx + ix;
-    const T hw = (T)(L.h2 * w2[b]);
+    const T hw = hwv[b];
     const T s = hw * (m2ptr<T>(L) + (size_t)b * L.mstride)[i];
-    const T a = layer_alpha_t<T>(ix, iz, L.nx, L.nz, npml, (T)acoef);
+    const T a = layer_alpha_t<T>(ix, iz, L.nx, L.nz, npml, acoef);
     cx<T> c = ldc(ub, i);
     cx<T> acc((T(4) - s) * c.re - s * a * c.im, (T(4) - s) * c.im + s * a * c.re);  // (4 - s(1 - j a)) u
     if (ix > 0) acc = acc - ldc(ub, i - 1);
@@ -92,12 +109,12 @@ __global__ void __launch_bounds__(256) k_apply(LevelDev L, int npml, double acoe
 }
 
 template <typename T>
-void launch_apply(const LevelDev& L0, int npml, double amax, const double* w2, const T* u, T* y, T scale,
+void launch_apply(const LevelDev& L0, int npml, double amax, const T* hw, const T* u, T* y, T scale,
                   int nrhs, cudaStream_t s) {
     dim3 blk(32, 8), grd((L0.nx + 31) / 32, (L0.nz + 7) / 8, nrhs);
-    k_apply<T><<<grd, blk, 0, s>>>(L0, npml, layer_coef(npml, amax), w2, u, y, scale);
+    k_apply<T><<<grd, blk, 0, s>>>(L0, npml, (T)layer_coef(npml, amax), hw, u, y, scale);
 }
-template void launch_apply<float>(const LevelDev&, int, double, const double*, const float*, float*, float, int, cudaStream_t);
+template void launch_apply<float>(const LevelDev&, int, double, const float*, const float*, float*, float, int, cudaStream_t);
 template void launch_apply<double>(const LevelDev&, int, double, const double*, const double*, double*, double, int, cudaStream_t);
 
 // ======================================================= FP64 outer residual
@@ -190,7 +207,7 @@ __global__ void __launch_bounds__(256) k_bicg_init(const T* __restrict__ bv, T* 
     const int b = blockIdx.z;
     if (!st[b].outer_active) return;
     const size_t off = n * b;
-    double acc[1] = {0.0};
+    T a0 = 0;
     const cx<T> z(0, 0);
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
         cx<T> c = ldc(bv, off + i);
@@ -199,9 +216,11 @@ __global__ void __launch_bounds__(256) k_bicg_init(const T* __restrict__ bv, T* 
         stc(rh, off + i, c);
         stc(p, off + i, z);
         stc(v, off + i, z);
-        acc[0] += (double)c.re * c.re + (double)c.im * c.im;
+        a0 += c.re * c.re + c.im * c.im;
     }
-    if (last_block_reduce<1>(acc, sh, partials + (size_t)b * pstride, gridDim.x, blockIdx.x, &st[b].counter[1])) {
+    const T vv[1] = {a0};
+    double acc[1];
+    if (last_block_reduce_t<1, T>(vv, acc, sh, partials + (size_t)b * pstride, gridDim.x, blockIdx.x, &st[b].counter[1])) {
         if (threadIdx.x == 0) {
             RhsState& S = st[b];
             S.bnorm2 = acc[0];
@@ -256,8 +275,9 @@ __global__ void __launch_bounds__(256) k_bicg_resume(const T* __restrict__ rin, 
         a1 += q.re * c.im - q.im * c.re;
         a2 += c.re * c.re + c.im * c.im;
     }
-    double acc[3] = {(double)a0, (double)a1, (double)a2};
-    if (last_block_reduce<3>(acc, sh, partials + (size_t)b * pstride, gridDim.x, blockIdx.x, &st[b].counter[1])) {
+    const T vv[3] = {a0, a1, a2};
+    double acc[3];
+    if (last_block_reduce_t<3, T>(vv, acc, sh, partials + (size_t)b * pstride, gridDim.x, blockIdx.x, &st[b].counter[1])) {
         if (threadIdx.x == 0) {
             RhsState& S = st[b];
             S.bnorm2 = acc[2];
@@ -302,10 +322,17 @@ template void launch_bicg_resume<double>(const double*, double*, double*, double
 template <typename T>
 __global__ void k_bicg_p(const T* __restrict__ r, T* __restrict__ p, const T* __restrict__ v, const RhsState* st,
                          size_t n) {
+    pdl_trigger();
+    pdl_wait();
     const int b = blockIdx.z;
     if (!st[b].active) return;
-    const cx<T> beta((T)st[b].beta[0], (T)st[b].beta[1]);
-    const cx<T> om((T)st[b].omega[0], (T)st[b].omega[1]);
+    __shared__ T sc[4];
+    if (threadIdx.x == 0) {
+        sc[0] = (T)st[b].beta[0]; sc[1] = (T)st[b].beta[1]; sc[2] = (T)st[b].omega[0]; sc[3] = (T)st[b].omega[1];
+    }
+    __syncthreads();
+    const cx<T> beta(sc[0], sc[1]);
+    const cx<T> om(sc[2], sc[3]);
     const size_t off = n * b;
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
         cx<T> pv = ldcc(p, off + i);
@@ -315,15 +342,20 @@ __global__ void k_bicg_p(const T* __restrict__ r, T* __restrict__ p, const T* __
 
 template <typename T>
 void launch_bicg_p(const T* r, T* p, const T* v, const RhsState* st, size_t n, int nrhs, cudaStream_t s) {
-    k_bicg_p<T><<<dim3(grid1d(n), 1, nrhs), 256, 0, s>>>(r, p, v, st, n);
+    launch_pdl(k_bicg_p<T>, dim3(grid1d(n), 1, nrhs), dim3(256), 0, s, r, p, v, st, n);
 }
 
 template <typename T>
 __global__ void k_bicg_s(const T* __restrict__ r, const T* __restrict__ v, T* __restrict__ sv, const RhsState* st,
                          size_t n) {
+    pdl_trigger();
+    pdl_wait();
     const int b = blockIdx.z;
     if (!st[b].active) return;
-    const cx<T> al((T)st[b].alpha[0], (T)st[b].alpha[1]);
+    __shared__ T sc[2];
+    if (threadIdx.x == 0) { sc[0] = (T)st[b].alpha[0]; sc[1] = (T)st[b].alpha[1]; }
+    __syncthreads();
+    const cx<T> al(sc[0], sc[1]);
     const size_t off = n * b;
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
         stc(sv, off + i, ldc(r, off + i) - al * ldc(v, off + i));
@@ -331,7 +363,7 @@ __global__ void k_bicg_s(const T* __restrict__ r, const T* __restrict__ v, T* __
 
 template <typename T>
 void launch_bicg_s(const T* r, const T* v, T* sv, const RhsState* st, size_t n, int nrhs, cudaStream_t s) {
-    k_bicg_s<T><<<dim3(grid1d(n), 1, nrhs), 256, 0, s>>>(r, v, sv, st, n);
+    launch_pdl(k_bicg_s<T>, dim3(grid1d(n), 1, nrhs), dim3(256), 0, s, r, v, sv, st, n);
 }
 
 template <typename T>
@@ -340,10 +372,17 @@ __global__ void __launch_bounds__(256) k_bicg_xr(T* x, const T* __restrict__ ph,
                                                  const T* __restrict__ rh, T* r, double* partials, int pstride,
                                                  RhsState* st, int* nactive, size_t n) {
     __shared__ double sh[96];
+    pdl_trigger();
+    pdl_wait();
     const int b = blockIdx.z;
     if (!st[b].active) return;
-    const cx<T> al((T)st[b].alpha[0], (T)st[b].alpha[1]);
-    const cx<T> om((T)st[b].omega[0], (T)st[b].omega[1]);
+    __shared__ T sc[4];
+    if (threadIdx.x == 0) {
+        sc[0] = (T)st[b].alpha[0]; sc[1] = (T)st[b].alpha[1]; sc[2] = (T)st[b].omega[0]; sc[3] = (T)st[b].omega[1];
+    }
+    __syncthreads();
+    const cx<T> al(sc[0], sc[1]);
+    const cx<T> om(sc[2], sc[3]);
     const size_t off = n * b;
     T a0 = 0, a1 = 0, a2 = 0;   // <rh, r> (re, im), <r, r>
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
@@ -356,8 +395,9 @@ __global__ void __launch_bounds__(256) k_bicg_xr(T* x, const T* __restrict__ ph,
         a1 += q.re * rn.im - q.im * rn.re;
         a2 += rn.re * rn.re + rn.im * rn.im;
     }
-    double acc[3] = {(double)a0, (double)a1, (double)a2};
-    if (last_block_reduce<3>(acc, sh, partials + (size_t)b * pstride, gridDim.x, blockIdx.x, &st[b].counter[2])) {
+    const T vv[3] = {a0, a1, a2};
+    double acc[3];
+    if (last_block_reduce_t<3, T>(vv, acc, sh, partials + (size_t)b * pstride, gridDim.x, blockIdx.x, &st[b].counter[2])) {
         if (threadIdx.x == 0) {
             RhsState& S = st[b];
             S.iters += 1;
@@ -393,7 +433,8 @@ __global__ void __launch_bounds__(256) k_bicg_xr(T* x, const T* __restrict__ ph,
 template <typename T>
 void launch_bicg_xr(T* x, const T* ph, const T* shv, const T* sv, const T* t, const T* rh, T* r, double* partials,
                     int pstride, RhsState* st, int* nactive, size_t n, int nrhs, cudaStream_t s) {
-    k_bicg_xr<T><<<dim3(grid1d(n), 1, nrhs), 256, 0, s>>>(x, ph, shv, sv, t, rh, r, partials, pstride, st, nactive, n);
+    launch_pdl(k_bicg_xr<T>, dim3(grid1d(n), 1, nrhs), dim3(256), 0, s, x, ph, shv, sv, t, rh, r, partials, pstride, st,
+               nactive, n);
 }
 
 // ===================================================== Galerkin operators
@@ -431,7 +472,7 @@ struct LevelOp {
     const T* gk;   // Galerkin levels
     size_t n;
     int nx, nz;
-    T hw, b1, b2;  // hw = (h_l omega)^2 on the finest level, (h_0 omega)^2 on Galerkin levels
+    T hw, b1, b2;  // hw = (h_0 omega)^2
     __device__ __forceinline__ cx<T> diag(size_t i) const {
         if constexpr (GAL) return gcoef(gk, n, i, 0, hw * b1, hw * b2);
         else {
@@ -452,14 +493,14 @@ struct LevelOp {
 };
 
 template <typename T, bool GAL>
-__device__ __forceinline__ LevelOp<T, GAL> level_op(const LevelDev& L, int b, double w2b) {
+__device__ __forceinline__ LevelOp<T, GAL> level_op(const LevelDev& L, int b, T hwb) {
     LevelOp<T, GAL> op;
     op.n = (size_t)L.nx * L.nz;
     op.nx = L.nx;
     op.nz = L.nz;
     op.m2 = GAL ? nullptr : static_cast<const T*>(L.m2) + (size_t)b * L.mstride;
     op.gk = GAL ? static_cast<const T*>(L.gk) + (size_t)b * L.gkstride : nullptr;
-    op.hw = (T)(GAL ? w2b : L.h2 * w2b);
+    op.hw = hwb;   // (h_0 omega_b)^2 on every level: the finest level's spacing, Galerkin below
     return op;
 }
 
@@ -547,6 +588,206 @@ void launch_galerkin(const helm_model* m, int l, cudaStream_t s) {
                                                               kGalerkinCoefs * F.n(), C.gkd, C.gkf, C.nx, C.nz);
 }
 
+// ================================ Galerkin grid levels: staged coefficients
+// On the coarse grid levels the 9-point coefficients would otherwise be read
+// one by one per stencil evaluation, serialising each block on memory latency.
+// These kernels first stage, cooperatively and coalesced, the per-RHS complex
+// coefficients M_k = G_k - hw (b1 - j b2) K_k of their tile region into shared
+// memory, then work from there. Smaller tiles give the small grids more blocks.
+template <typename T, int W, int H>
+struct GalTile {
+    cx<T> c[5][H][W];   // centre, east, north, north-east, north-west
+};
+
+template <typename T, int W, int H>
+__device__ __forceinline__ void stage_gal(GalTile<T, W, H>& t, const LevelDev& L, int b, T hb1, T hb2, int gx0,
+                                          int gz0) {
+    const T* gk = static_cast<const T*>(L.gk) + (size_t)b * L.gkstride;
+    const size_t n = (size_t)L.nx * L.nz;
+    // one node per iteration, its ten coefficients loaded independently
+    for (int idx = threadIdx.x; idx < W * H; idx += blockDim.x) {
+        const int lz = idx / W, lx = idx - lz * W;
+        const int gx = gx0 + lx, gz = gz0 + lz;
+        T g[5], q[5];
+        const bool in = gx >= 0 && gx < L.nx && gz >= 0 && gz < L.nz;
+        const size_t i = in ? (size_t)gz * L.nx + gx : 0;
+#pragma unroll
+        for (int k = 0; k < 5; ++k) {
+            g[k] = in ? __ldg(gk + (size_t)k * n + i) : T(0);
+            q[k] = in ? __ldg(gk + (size_t)(5 + k) * n + i) : T(0);
+        }
+#pragma unroll
+        for (int k = 0; k < 5; ++k) t.c[k][lz][lx] = cx<T>(g[k] - hb1 * q[k], hb2 * q[k]);
+    }
+}
+
+// M u at tile point (lx, lz) (global (gx, gz)); U row pitch W; coefficients of
+// the neighbours come from the staged tile (the point must not lie on the
+// tile border).
+template <typename T, int W, int H>
+__device__ __forceinline__ cx<T> mop9_staged(const GalTile<T, W, H>& t, int nx, int nz, int gx, int gz, int lx, int lz,
+                                             const cx<T>* U) {
+    cx<T> acc = t.c[0][lz][lx] * U[0];
+    const bool e = gx + 1 < nx, w = gx > 0, no = gz + 1 < nz, so = gz > 0;
+    if (e) acc = acc + t.c[1][lz][lx] * U[1];
+    if (w) acc = acc + t.c[1][lz][lx - 1] * U[-1];
+    if (no) acc = acc + t.c[2][lz][lx] * U[W];
+    if (so) acc = acc + t.c[2][lz - 1][lx] * U[-W];
+    if (no && e) acc = acc + t.c[3][lz][lx] * U[W + 1];
+    if (so && w) acc = acc + t.c[3][lz - 1][lx - 1] * U[-W - 1];
+    if (no && w) acc = acc + t.c[4][lz][lx] * U[W - 1];
+    if (so && e) acc = acc + t.c[4][lz - 1][lx + 1] * U[-W + 1];
+    return acc;
+}
+
+// Tiles of the Galerkin kernels: restriction coarse tile GRCX x GRCZ, prolongation
+// fine tile GPX x GPZ; halved in x for complex128 to stay within 48 KB of static
+// shared memory.
+template <typename T> struct GTile {
+    static constexpr int RCX = sizeof(T) == 4 ? 16 : 8, RCZ = 8;
+    static constexpr int PX = sizeof(T) == 4 ? 32 : 16, PZ = 8;
+};
+
+// restriction (CORRECT = false: zero-guess smoothing; true: u2 = wj D^-1 f + P e)
+template <typename T, bool CORRECT, int GRCX>
+__global__ void __launch_bounds__(128) k_restrict_g(LevelDev Lf, LevelDev Lc, const T* __restrict__ hwv, T b1, T b2,
+                                                    T wj, const T* __restrict__ f, const T* __restrict__ ec,
+                                                    T* __restrict__ fc, const RhsState* st) {
+    constexpr int GRCZ = GTile<T>::RCZ;
+    constexpr int GRFW = 2 * GRCX + 3, GRFH = 2 * GRCZ + 3;
+    constexpr int CEW = GRCX + 2, CEH = GRCZ + 2;
+    __shared__ GalTile<T, GRFW, GRFH> C;
+    __shared__ cx<T> F[GRFH][GRFW];
+    __shared__ cx<T> U[GRFH][GRFW];
+    __shared__ cx<T> E[CORRECT ? CEH : 1][CORRECT ? CEW : 1];
+    pdl_trigger();
+    const int b = blockIdx.z;
+    const int I0 = blockIdx.x * GRCX, K0 = blockIdx.y * GRCZ;
+    const int gx0 = 2 * I0 - 1, gz0 = 2 * K0 - 1;
+    const T hw = hwv[b];
+    stage_gal<T, GRFW, GRFH>(C, Lf, b, hw * b1, hw * b2, gx0, gz0);   // model data only
+    pdl_wait();
+    if (!rhs_active(st, b)) return;
+    const size_t nf = (size_t)Lf.nx * Lf.nz, nc = (size_t)Lc.nx * Lc.nz;
+    const T* fb = f + 2 * nf * b;
+    if (CORRECT) {
+        const T* eb = ec + 2 * nc * b;
+        for (int idx = threadIdx.x; idx < CEW * CEH; idx += blockDim.x) {
+            const int lz = idx / CEW, lx = idx - lz * CEW;
+            const int I = I0 - 1 + lx, K = K0 - 1 + lz;
+            cx<T> e(0, 0);
+            if (I >= 0 && I < Lc.nx && K >= 0 && K < Lc.nz) e = ldc(eb, (size_t)K * Lc.nx + I);
+            E[lz][lx] = e;
+        }
+    }
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < GRFW * GRFH; idx += blockDim.x) {
+        const int lz = idx / GRFW, lx = idx - lz * GRFW;
+        const int gx = gx0 + lx, gz = gz0 + lz;
+        cx<T> fv(0, 0), uv(0, 0);
+        if (gx >= 0 && gx < Lf.nx && gz >= 0 && gz < Lf.nz) {
+            fv = ldc(fb, (size_t)gz * Lf.nx + gx);
+            uv = wj * cdiv(fv, C.c[0][lz][lx]);
+            if (CORRECT) {
+                int ia, ib, ka, kb;
+                T wa, wb, va, vb;
+                if (gx & 1) { ia = (gx - 1) / 2; ib = ia; wa = T(1); wb = T(0); }
+                else { ia = gx / 2 - 1; ib = gx / 2; wa = T(0.5); wb = T(0.5); }
+                if (gz & 1) { ka = (gz - 1) / 2; kb = ka; va = T(1); vb = T(0); }
+                else { ka = gz / 2 - 1; kb = gz / 2; va = T(0.5); vb = T(0.5); }
+                ia -= I0 - 1; ib -= I0 - 1; ka -= K0 - 1; kb -= K0 - 1;
+                uv = uv + (va * wa) * E[ka][ia] + (va * wb) * E[ka][ib] + (vb * wa) * E[kb][ia] + (vb * wb) * E[kb][ib];
+            }
+        }
+        F[lz][lx] = fv;
+        U[lz][lx] = uv;
+    }
+    __syncthreads();
+    constexpr int W2 = GRFW - 2, H2 = GRFH - 2;
+    for (int idx = threadIdx.x; idx < W2 * H2; idx += blockDim.x) {
+        const int lz = 1 + idx / W2, lx = 1 + idx % W2;
+        const int gx = gx0 + lx, gz = gz0 + lz;
+        cx<T> r(0, 0);
+        if (gx < Lf.nx && gz < Lf.nz) r = F[lz][lx] - mop9_staged<T, GRFW, GRFH>(C, Lf.nx, Lf.nz, gx, gz, lx, lz, &U[lz][lx]);
+        F[lz][lx] = r;
+    }
+    __syncthreads();
+    const int cxl = threadIdx.x % GRCX, czl = threadIdx.x / GRCX;
+    const int I = I0 + cxl, K = K0 + czl;
+    if (I < Lc.nx && K < Lc.nz) {
+        const int lx = 2 * cxl + 2, lz = 2 * czl + 2;
+        cx<T> a = T(4) * F[lz][lx];
+        a = a + T(2) * (F[lz][lx - 1] + F[lz][lx + 1] + F[lz - 1][lx] + F[lz + 1][lx]);
+        a = a + F[lz - 1][lx - 1] + F[lz - 1][lx + 1] + F[lz + 1][lx - 1] + F[lz + 1][lx + 1];
+        stc(fc + 2 * nc * b, (size_t)K * Lc.nx + I, T(0.25) * a);
+    }
+}
+
+template <typename T, int GPX>
+__global__ void __launch_bounds__(256) k_prolong_g(LevelDev Lf, LevelDev Lc, const T* __restrict__ hwv, T b1, T b2,
+                                                   T wj, const T* __restrict__ f, const T* __restrict__ ec,
+                                                   T* __restrict__ out, const RhsState* st, int accumulate) {
+    constexpr int GPZ = GTile<T>::PZ;
+    constexpr int RW = GPX + 2, RH = GPZ + 2;
+    constexpr int EW = GPX / 2 + 2, EH = GPZ / 2 + 2;
+    __shared__ GalTile<T, RW, RH> C;
+    __shared__ cx<T> F[RH][RW];
+    __shared__ cx<T> U2[RH][RW];
+    __shared__ cx<T> E[EH][EW];
+    pdl_trigger();
+    const int b = blockIdx.z;
+    const int x0 = blockIdx.x * GPX, z0 = blockIdx.y * GPZ;
+    const int gx0 = x0 - 1, gz0 = z0 - 1;
+    const int cx0 = x0 / 2 - 1, cz0 = z0 / 2 - 1;
+    const T hw = hwv[b];
+    stage_gal<T, RW, RH>(C, Lf, b, hw * b1, hw * b2, gx0, gz0);   // model data only
+    pdl_wait();
+    if (!rhs_active(st, b)) return;
+    const size_t nf = (size_t)Lf.nx * Lf.nz, nc = (size_t)Lc.nx * Lc.nz;
+    const T* fb = f + 2 * nf * b;
+    const T* eb = ec + 2 * nc * b;
+    for (int idx = threadIdx.x; idx < EW * EH; idx += blockDim.x) {
+        const int lz = idx / EW, lx = idx - lz * EW;
+        const int I = cx0 + lx, K = cz0 + lz;
+        cx<T> e(0, 0);
+        if (I >= 0 && I < Lc.nx && K >= 0 && K < Lc.nz) e = ldc(eb, (size_t)K * Lc.nx + I);
+        E[lz][lx] = e;
+    }
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < RW * RH; idx += blockDim.x) {
+        const int lz = idx / RW, lx = idx - lz * RW;
+        const int gx = gx0 + lx, gz = gz0 + lz;
+        cx<T> fv(0, 0), u(0, 0);
+        if (gx >= 0 && gx < Lf.nx && gz >= 0 && gz < Lf.nz) {
+            fv = ldc(fb, (size_t)gz * Lf.nx + gx);
+            u = wj * cdiv(fv, C.c[0][lz][lx]);
+            int ia, ib, ka, kb;
+            T wa, wb, va, vb;
+            if (gx & 1) { ia = (gx - 1) / 2; ib = ia; wa = T(1); wb = T(0); }
+            else { ia = gx / 2 - 1; ib = gx / 2; wa = T(0.5); wb = T(0.5); }
+            if (gz & 1) { ka = (gz - 1) / 2; kb = ka; va = T(1); vb = T(0); }
+            else { ka = gz / 2 - 1; kb = gz / 2; va = T(0.5); vb = T(0.5); }
+            ia -= cx0; ib -= cx0; ka -= cz0; kb -= cz0;
+            u = u + (va * wa) * E[ka][ia] + (va * wb) * E[ka][ib] + (vb * wa) * E[kb][ia] + (vb * wb) * E[kb][ib];
+        }
+        F[lz][lx] = fv;
+        U2[lz][lx] = u;
+    }
+    __syncthreads();
+    T* ob = out + 2 * nf * b;
+    for (int idx = threadIdx.x; idx < GPX * GPZ; idx += blockDim.x) {
+        const int tz = idx / GPX, tx = idx - tz * GPX;
+        const int gx = x0 + tx, gz = z0 + tz;
+        if (gx >= Lf.nx || gz >= Lf.nz) continue;
+        const int lx = tx + 1, lz = tz + 1;
+        const size_t i = (size_t)gz * Lf.nx + gx;
+        const cx<T> c = U2[lz][lx];
+        const cx<T> mu = mop9_staged<T, RW, RH>(C, Lf.nx, Lf.nz, gx, gz, lx, lz, &U2[lz][lx]);
+        const cx<T> v = c + wj * cdiv(F[lz][lx] - mu, C.c[0][lz][lx]);
+        stc(ob, i, accumulate ? ldcc(ob, i) + v : v);
+    }
+}
+
 // ======================================================== V-cycle: restrict
 // From a level-l right-hand side f (zero initial guess): one damped-Jacobi
 // sweep u1 = wj D^-1 f, residual r = f - M u1, and the restriction P^T r to
@@ -555,11 +796,13 @@ constexpr int RCX = 32, RCZ = 8;                    // coarse tile per block
 constexpr int RFW = 2 * RCX + 3, RFH = 2 * RCZ + 3; // fine region (u1) per block
 
 template <typename T, bool GAL>
-__global__ void __launch_bounds__(256) k_restrict(LevelDev Lf, LevelDev Lc, const double* __restrict__ w2, T b1, T b2,
+__global__ void __launch_bounds__(256) k_restrict(LevelDev Lf, LevelDev Lc, const T* __restrict__ w2, T b1, T b2,
                                                   T wj, const T* __restrict__ f, T* __restrict__ fc,
                                                   const RhsState* st) {
     __shared__ cx<T> F[RFH][RFW];
     __shared__ cx<T> U[RFH][RFW];
+    pdl_trigger();
+    pdl_wait();
     const int b = blockIdx.z;
     if (!rhs_active(st, b)) return;
     const int I0 = blockIdx.x * RCX, K0 = blockIdx.y * RCZ;
@@ -604,31 +847,42 @@ __global__ void __launch_bounds__(256) k_restrict(LevelDev Lf, LevelDev Lc, cons
 }
 
 template <typename T>
-void launch_restrict(const LevelDev& Lf, const LevelDev& Lc, const double* w2, double b1, double b2, double wj,
-                     const T* f, T* fc, const RhsState* st, int nrhs, cudaStream_t s) {
-    dim3 grd((Lc.nx + RCX - 1) / RCX, (Lc.nz + RCZ - 1) / RCZ, nrhs);
-    if (Lf.m2)
-        k_restrict<T, false><<<grd, RCX * RCZ, 0, s>>>(Lf, Lc, w2, (T)b1, (T)b2, (T)wj, f, fc, st);
-    else
-        k_restrict<T, true><<<grd, RCX * RCZ, 0, s>>>(Lf, Lc, w2, (T)b1, (T)b2, (T)wj, f, fc, st);
+void launch_restrict(const LevelDev& Lf, const LevelDev& Lc, const T* w2, double b1, double b2, double wj,
+                     const T* f, T* fc, const RhsState* st, int nrhs, cudaStream_t s, int tile) {
+    if (Lf.m2) {
+        dim3 grd((Lc.nx + RCX - 1) / RCX, (Lc.nz + RCZ - 1) / RCZ, nrhs);
+        launch_pdl(k_restrict<T, false>, grd, dim3(RCX * RCZ), 0, s, Lf, Lc, w2, (T)b1, (T)b2, (T)wj, f, fc, st);
+    } else if (sizeof(T) == 4 && tile == 0) {
+        constexpr int GRCX = 8, GRCZ = GTile<T>::RCZ;
+        dim3 grd((Lc.nx + GRCX - 1) / GRCX, (Lc.nz + GRCZ - 1) / GRCZ, nrhs);
+        launch_pdl(k_restrict_g<T, false, GRCX>, grd, dim3(GRCX * GRCZ), 0, s, Lf, Lc, w2, (T)b1, (T)b2, (T)wj, f,
+                   (const T*)nullptr, fc, st);
+    } else {
+        constexpr int GRCX = GTile<T>::RCX, GRCZ = GTile<T>::RCZ;
+        dim3 grd((Lc.nx + GRCX - 1) / GRCX, (Lc.nz + GRCZ - 1) / GRCZ, nrhs);
+        launch_pdl(k_restrict_g<T, false, GRCX>, grd, dim3(GRCX * GRCZ), 0, s, Lf, Lc, w2, (T)b1, (T)b2, (T)wj, f,
+                   (const T*)nullptr, fc, st);
+    }
 }
 
 // ========================================================= V-cycle: prolong
-// On a level-l tile: u1 = wj D^-1 f, u2 = u1 + P e (bilinear), one post-sweep
-// u3 = u2 + wj D^-1 (f - M u2). Modes 1 and 2 (finest level inside BiCGSTAB)
-// also apply A to u3 and reduce the dot products the next scalar needs; mode 3
-// (FGMRES) applies A without dots.
+// Finest level, on a tile: u1 = wj D^-1 f, u2 = u1 + P e (bilinear), one
+// post-sweep u3 = u2 + wj D^-1 (f - M u2). Mode 0 writes u3 (optionally
+// accumulating); modes 1 and 2 (inside BiCGSTAB) also apply A to u3 and reduce
+// the dot products the next scalar needs; mode 3 (FGMRES) applies A without
+// dots. The inverse diagonal wj D^-1 is computed once per node into shared
+// memory; the row loops use a 2D thread layout (no per-element division).
 // fine tile per block: 64 x 16 in FP32, 32 x 16 in FP64 (static shared memory < 48 KB)
 template <typename T> struct PTile { static constexpr int X = sizeof(T) == 4 ? 64 : 32, Z = 16; };
 
-template <typename T, int MODE, bool GAL>
-__global__ void __launch_bounds__(256) k_prolong(LevelDev Lf, LevelDev Lc, int npml, double acoef,
-                                                 const double* __restrict__ w2, T b1, T b2, T wj,
+template <typename T, int MODE, int PFZ>
+__global__ void __launch_bounds__(256) k_prolong(LevelDev Lf, LevelDev Lc, int npml, T acoef,
+                                                 const T* __restrict__ w2, T b1, T b2, T wj,
                                                  const T* __restrict__ f, const T* __restrict__ ec,
                                                  T* __restrict__ out, T* __restrict__ y, const T* __restrict__ aux,
                                                  double* partials, int pstride, RhsState* st, int accumulate) {
     constexpr int H = (MODE == 0) ? 1 : 2;
-    constexpr int PFX = PTile<T>::X, PFZ = PTile<T>::Z;
+    constexpr int PFX = PTile<T>::X;
     constexpr int RW = PFX + 2 * H, RH = PFZ + 2 * H;          // f, u2 region
     constexpr int EW = PFX / 2 + H + 1, EH = PFZ / 2 + H + 1;  // coarse region
     constexpr int SW = PFX + 2, SH = PFZ + 2;                  // u3 region (modes 1, 2)
@@ -638,12 +892,14 @@ __global__ void __launch_bounds__(256) k_prolong(LevelDev Lf, LevelDev Lc, int n
     __shared__ cx<T> U3[(MODE == 0) ? 1 : SH][(MODE == 0) ? 1 : SW];
     __shared__ double shred[96];
 
+    pdl_trigger();
+    pdl_wait();
     const int b = blockIdx.z;
     if (!rhs_active(st, b)) return;
     const int x0 = blockIdx.x * PFX, z0 = blockIdx.y * PFZ;
     const int gx0 = x0 - H, gz0 = z0 - H;
     const int cx0 = x0 / 2 - H, cz0 = z0 / 2 - H;
-    LevelOp<T, GAL> op = level_op<T, GAL>(Lf, b, w2[b]);
+    LevelOp<T, false> op = level_op<T, false>(Lf, b, w2[b]);
     op.b1 = b1;
     op.b2 = b2;
     const size_t nf = (size_t)Lf.nx * Lf.nz, nc = (size_t)Lc.nx * Lc.nz;
@@ -722,7 +978,7 @@ __global__ void __launch_bounds__(256) k_prolong(LevelDev Lf, LevelDev Lc, int n
         T* yb = y + 2 * nf * b;
         const T* ab = aux + 2 * nf * b;
         const T* m2 = static_cast<const T*>(Lf.m2) + (size_t)b * Lf.mstride;
-        const T hw = (T)(Lf.h2 * w2[b]);
+        const T hw = w2[b];
         T d0 = 0, d1 = 0, d2 = 0;
         for (int idx = threadIdx.x; idx < PFX * PFZ; idx += blockDim.x) {
             const int tz = idx / PFX, tx = idx - tz * PFX;
@@ -731,7 +987,7 @@ __global__ void __launch_bounds__(256) k_prolong(LevelDev Lf, LevelDev Lc, int n
             const int sx = tx + 1, sz = tz + 1;
             const size_t i = (size_t)gz * Lf.nx + gx;
             const T s = hw * __ldg(m2 + i);
-            const T a = layer_alpha_t<T>(gx, gz, Lf.nx, Lf.nz, npml, (T)acoef);
+            const T a = layer_alpha_t<T>(gx, gz, Lf.nx, Lf.nz, npml, acoef);
             const cx<T> c = U3[sz][sx];
             cx<T> yv((T(4) - s) * c.re - s * a * c.im, (T(4) - s) * c.im + s * a * c.re);
             yv = yv - U3[sz][sx - 1] - U3[sz][sx + 1] - U3[sz - 1][sx] - U3[sz + 1][sx];
@@ -749,9 +1005,11 @@ __global__ void __launch_bounds__(256) k_prolong(LevelDev Lf, LevelDev Lc, int n
             }
         }
         if (MODE == 3) return;        // FGMRES: z and A z only
-        double acc[3] = {(double)d0, (double)d1, (double)d2};
+        if (MODE == 3) return;        // FGMRES: z and A z only
+        const T vv[3] = {d0, d1, d2};
+        double acc[3];
         const int nblk = gridDim.x * gridDim.y, blk = blockIdx.y * gridDim.x + blockIdx.x;
-        if (last_block_reduce<3>(acc, shred, partials + (size_t)b * pstride, nblk, blk, &st[b].counter[3])) {
+        if (last_block_reduce_t<3, T>(vv, acc, shred, partials + (size_t)b * pstride, nblk, blk, &st[b].counter[3])) {
             if (threadIdx.x == 0) {
                 RhsState& S = st[b];
                 if (MODE == 1) {   // alpha = rho / <rh, v>
@@ -773,23 +1031,59 @@ __global__ void __launch_bounds__(256) k_prolong(LevelDev Lf, LevelDev Lc, int n
     }
 }
 
-template <typename T>
-void launch_prolong(int mode, const LevelDev& Lf, const LevelDev& Lc, int npml, double amax, const double* w2,
-                    double b1, double b2, double wj, const T* f, const T* ec, T* out, T* y, const T* aux,
-                    double* partials, int pstride, RhsState* st, int nrhs, cudaStream_t s, int accumulate) {
-    constexpr int PFX = PTile<T>::X, PFZ = PTile<T>::Z;
-    dim3 grd((Lf.nx + PFX - 1) / PFX, (Lf.nz + PFZ - 1) / PFZ, nrhs);
-    const double ac = layer_coef(npml, amax);
-    if (mode == 0 && !Lf.m2)
-        k_prolong<T, 0, true><<<grd, 256, 0, s>>>(Lf, Lc, npml, ac, w2, (T)b1, (T)b2, (T)wj, f, ec, out, y, aux, partials, pstride, st, accumulate);
-    else if (mode == 0)
-        k_prolong<T, 0, false><<<grd, 256, 0, s>>>(Lf, Lc, npml, ac, w2, (T)b1, (T)b2, (T)wj, f, ec, out, y, aux, partials, pstride, st, accumulate);
+// Tile choices (tile = 0 or 1; FP64 always uses its fixed tiles):
+//   finest-level prolongation: 64 x 8 or 64 x 16 fine nodes per block;
+//   Galerkin prolongation: 16 x 8 or 32 x 8 fine nodes per block.
+template <typename T, int PFZ>
+static void prolong_fine(int mode, dim3 grd, cudaStream_t s, const LevelDev& Lf, const LevelDev& Lc, int npml, T ac,
+                         const T* w2, T b1, T b2, T wj, const T* f, const T* ec, T* out, T* y, const T* aux,
+                         double* partials, int pstride, RhsState* st, int accumulate) {
+    if (mode == 0)
+        launch_pdl(k_prolong<T, 0, PFZ>, grd, dim3(256), 0, s, Lf, Lc, npml, ac, w2, b1, b2, wj, f, ec, out, y, aux,
+                   partials, pstride, st, accumulate);
     else if (mode == 1)
-        k_prolong<T, 1, false><<<grd, 256, 0, s>>>(Lf, Lc, npml, ac, w2, (T)b1, (T)b2, (T)wj, f, ec, out, y, aux, partials, pstride, st, accumulate);
+        launch_pdl(k_prolong<T, 1, PFZ>, grd, dim3(256), 0, s, Lf, Lc, npml, ac, w2, b1, b2, wj, f, ec, out, y, aux,
+                   partials, pstride, st, accumulate);
     else if (mode == 2)
-        k_prolong<T, 2, false><<<grd, 256, 0, s>>>(Lf, Lc, npml, ac, w2, (T)b1, (T)b2, (T)wj, f, ec, out, y, aux, partials, pstride, st, accumulate);
+        launch_pdl(k_prolong<T, 2, PFZ>, grd, dim3(256), 0, s, Lf, Lc, npml, ac, w2, b1, b2, wj, f, ec, out, y, aux,
+                   partials, pstride, st, accumulate);
     else
-        k_prolong<T, 3, false><<<grd, 256, 0, s>>>(Lf, Lc, npml, ac, w2, (T)b1, (T)b2, (T)wj, f, ec, out, y, aux, partials, pstride, st, accumulate);
+        launch_pdl(k_prolong<T, 3, PFZ>, grd, dim3(256), 0, s, Lf, Lc, npml, ac, w2, b1, b2, wj, f, ec, out, y, aux,
+                   partials, pstride, st, accumulate);
+}
+
+template <typename T>
+void launch_prolong(int mode, const LevelDev& Lf, const LevelDev& Lc, int npml, double amax, const T* w2,
+                    double b1, double b2, double wj, const T* f, const T* ec, T* out, T* y, const T* aux,
+                    double* partials, int pstride, RhsState* st, int nrhs, cudaStream_t s, int accumulate, int tile) {
+    constexpr int PFX = PTile<T>::X;
+    const T ac = (T)layer_coef(npml, amax);
+    const bool small = sizeof(T) == 4 && tile == 0;
+    if (mode == 0 && !Lf.m2) {
+        constexpr int GPZ = GTile<T>::PZ;
+        if (small) {
+            constexpr int GPX = 16;
+            dim3 gg((Lf.nx + GPX - 1) / GPX, (Lf.nz + GPZ - 1) / GPZ, nrhs);
+            launch_pdl(k_prolong_g<T, GPX>, gg, dim3(GPX * GPZ), 0, s, Lf, Lc, w2, (T)b1, (T)b2, (T)wj, f, ec, out, st,
+                       accumulate);
+        } else {
+            constexpr int GPX = GTile<T>::PX;
+            dim3 gg((Lf.nx + GPX - 1) / GPX, (Lf.nz + GPZ - 1) / GPZ, nrhs);
+            launch_pdl(k_prolong_g<T, GPX>, gg, dim3(GPX * GPZ), 0, s, Lf, Lc, w2, (T)b1, (T)b2, (T)wj, f, ec, out, st,
+                       accumulate);
+        }
+        return;
+    }
+    if (small) {
+        dim3 grd((Lf.nx + PFX - 1) / PFX, (Lf.nz + 7) / 8, nrhs);
+        prolong_fine<T, 8>(mode, grd, s, Lf, Lc, npml, ac, w2, (T)b1, (T)b2, (T)wj, f, ec, out, y, aux, partials,
+                           pstride, st, accumulate);
+    } else {
+        constexpr int PFZ = PTile<T>::Z;
+        dim3 grd((Lf.nx + PFX - 1) / PFX, (Lf.nz + PFZ - 1) / PFZ, nrhs);
+        prolong_fine<T, PFZ>(mode, grd, s, Lf, Lc, npml, ac, w2, (T)b1, (T)b2, (T)wj, f, ec, out, y, aux, partials,
+                             pstride, st, accumulate);
+    }
 }
 
 // ======================================================= V-cycle: coarsest
@@ -942,34 +1236,73 @@ void launch_coarse_invert(const LevelDev& Lc, const double* w2_slots, const int*
 }
 
 // ================================================================ tail
-// Levels lt..L of the cycle in one block per right-hand side, every vector of
-// those levels in shared memory (f, u and r per level, laid out level after
-// level), following a schedule of passes. Each pass covers one level and ends
-// with a block barrier; coefficients are read through the read-only path.
+// Levels lt..L of the cycle in one block per right-hand side. Everything those
+// levels touch lives in shared memory: per level the vectors f, u, r and the
+// complex coefficients M_k = G_k - hw (b1 - j b2) K_k of this right-hand side
+// (staged once per launch). The schedule of passes runs with a block barrier
+// after each pass.
+template <typename T>
+__device__ __forceinline__ cx<T> mop9_sm(const cx<T>* C, size_t n, int nx, int nz, int ix, int iz, const cx<T>* U) {
+    const size_t i = (size_t)iz * nx + ix;
+    const cx<T>* Ce = C + n;
+    const cx<T>* Cn = C + 2 * n;
+    const cx<T>* Cne = C + 3 * n;
+    const cx<T>* Cnw = C + 4 * n;
+    cx<T> acc = C[i] * U[0];
+    const bool e = ix + 1 < nx, w = ix > 0, no = iz + 1 < nz, so = iz > 0;
+    if (e) acc = acc + Ce[i] * U[1];
+    if (w) acc = acc + Ce[i - 1] * U[-1];
+    if (no) acc = acc + Cn[i] * U[nx];
+    if (so) acc = acc + Cn[i - nx] * U[-nx];
+    if (no && e) acc = acc + Cne[i] * U[nx + 1];
+    if (so && w) acc = acc + Cne[i - nx - 1] * U[-nx - 1];
+    if (no && w) acc = acc + Cnw[i] * U[nx - 1];
+    if (so && e) acc = acc + Cnw[i - nx + 1] * U[-nx + 1];
+    return acc;
+}
+
 template <typename T>
 __global__ void __launch_bounds__(1024) k_tail(TailArgs a, const RhsState* st) {
     extern __shared__ __align__(16) unsigned char tail_smem[];
+    pdl_trigger();
     const int b = blockIdx.x;
-    if (!rhs_active(st, b)) return;
     const T hw = (T)a.w2[b], b1 = (T)a.b1, b2 = (T)a.b2, wj = (T)a.wj;
     const T hb1 = hw * b1, hb2 = hw * b2;
     const int tid = threadIdx.x, nth = blockDim.x;
     cx<T>* base = reinterpret_cast<cx<T>*>(tail_smem);
-    // vector offsets per level (f, u, r)
+    // per level: f, u, r (3 n) then the coefficients (5 n)
     size_t off[kMaxLevels];
     {
         size_t o = 0;
-        for (int l = a.lt; l <= a.L; ++l) { off[l] = o; o += 3 * (size_t)a.lv[l].nx * a.lv[l].nz; }
+        for (int l = a.lt; l <= a.L; ++l) { off[l] = o; o += 8 * (size_t)a.lv[l].nx * a.lv[l].nz; }
     }
+    for (int l = a.lt; l <= a.L; ++l) {
+        const size_t n = (size_t)a.lv[l].nx * a.lv[l].nz;
+        const T* gk = static_cast<const T*>(a.lv[l].gk) + (size_t)b * a.lv[l].gkstride;
+        cx<T>* C = base + off[l] + 3 * n;
+        for (size_t p = tid; p < n; p += nth) {
+            T g[5], q[5];
+#pragma unroll
+            for (int k = 0; k < 5; ++k) {
+                g[k] = __ldg(gk + (size_t)k * n + p);
+                q[k] = __ldg(gk + (size_t)(5 + k) * n + p);
+            }
+#pragma unroll
+            for (int k = 0; k < 5; ++k) C[(size_t)k * n + p] = cx<T>(g[k] - hb1 * q[k], hb2 * q[k]);
+        }
+    }
+    pdl_wait();   // the coefficients above are model data; everything below depends on earlier kernels
+    if (!rhs_active(st, b)) return;
+    __syncthreads();
     for (int k = 0; k < a.nops; ++k) {
         const int op = a.ops[k], type = op & 255, l = op >> 8;
         const LevelDev& L = a.lv[l];
         const int nx = L.nx, nz = L.nz;
         const size_t n = (size_t)nx * nz;
-        const T* gk = static_cast<const T*>(L.gk) + (size_t)b * L.gkstride;
         cx<T>* f = base + off[l];
         cx<T>* u = f + n;
         cx<T>* r = u + n;
+        const cx<T>* C = r + n;
         switch (type) {
             case OP_LOAD: {
                 const T* in = static_cast<const T*>(a.in);
@@ -977,23 +1310,23 @@ __global__ void __launch_bounds__(1024) k_tail(TailArgs a, const RhsState* st) {
                 break;
             }
             case OP_SMOOTH0:
-                for (size_t p = tid; p < n; p += nth) u[p] = wj * cdiv(f[p], gcoef(gk, n, p, 0, hb1, hb2));
+                for (size_t p = tid; p < n; p += nth) u[p] = wj * cdiv(f[p], C[p]);
                 break;
             case OP_RESID:
                 for (size_t p = tid; p < n; p += nth) {
                     const int ix = (int)(p % nx), iz = (int)(p / nx);
-                    r[p] = f[p] - mop9(gk, n, nx, nz, ix, iz, u + p, nx, hb1, hb2);
+                    r[p] = f[p] - mop9_sm(C, n, nx, nz, ix, iz, u + p);
                 }
                 break;
             case OP_JACOBI:
-                for (size_t p = tid; p < n; p += nth) u[p] = u[p] + wj * cdiv(r[p], gcoef(gk, n, p, 0, hb1, hb2));
+                for (size_t p = tid; p < n; p += nth) u[p] = u[p] + wj * cdiv(r[p], C[p]);
                 break;
             case OP_RESTRICT: {
-                const LevelDev& C = a.lv[l + 1];
-                const size_t nc = (size_t)C.nx * C.nz;
+                const LevelDev& Cl = a.lv[l + 1];
+                const size_t nc = (size_t)Cl.nx * Cl.nz;
                 cx<T>* fc = base + off[l + 1];
                 for (size_t q = tid; q < nc; q += nth) {
-                    const int I = (int)(q % C.nx), K = (int)(q / C.nx);
+                    const int I = (int)(q % Cl.nx), K = (int)(q / Cl.nx);
                     cx<T> acc(0, 0);
                     for (int dz = -1; dz <= 1; ++dz) {
                         const int jz = 2 * K + 1 + dz;
@@ -1010,8 +1343,8 @@ __global__ void __launch_bounds__(1024) k_tail(TailArgs a, const RhsState* st) {
                 break;
             }
             case OP_PROLONG_ADD: {
-                const LevelDev& C = a.lv[l + 1];
-                const size_t nc = (size_t)C.nx * C.nz;
+                const LevelDev& Cl = a.lv[l + 1];
+                const size_t nc = (size_t)Cl.nx * Cl.nz;
                 const cx<T>* uc = base + off[l + 1] + nc;
                 for (size_t p = tid; p < n; p += nth) {
                     const int jx = (int)(p % nx), jz = (int)(p / nx);
@@ -1022,12 +1355,12 @@ __global__ void __launch_bounds__(1024) k_tail(TailArgs a, const RhsState* st) {
                     if (jz & 1) { ka = (jz - 1) / 2; kb = ka; va = T(1); vb = T(0); }
                     else { ka = jz / 2 - 1; kb = jz / 2; va = T(0.5); vb = T(0.5); }
                     cx<T> acc(0, 0);
-                    const bool iao = ia >= 0 && ia < C.nx, ibo = ib >= 0 && ib < C.nx;
-                    const bool kao = ka >= 0 && ka < C.nz, kbo = kb >= 0 && kb < C.nz;
-                    if (kao && iao) acc = acc + (va * wa) * uc[(size_t)ka * C.nx + ia];
-                    if (kao && ibo && wb != T(0)) acc = acc + (va * wb) * uc[(size_t)ka * C.nx + ib];
-                    if (kbo && iao && vb != T(0)) acc = acc + (vb * wa) * uc[(size_t)kb * C.nx + ia];
-                    if (kbo && ibo && vb != T(0) && wb != T(0)) acc = acc + (vb * wb) * uc[(size_t)kb * C.nx + ib];
+                    const bool iao = ia >= 0 && ia < Cl.nx, ibo = ib >= 0 && ib < Cl.nx;
+                    const bool kao = ka >= 0 && ka < Cl.nz, kbo = kb >= 0 && kb < Cl.nz;
+                    if (kao && iao) acc = acc + (va * wa) * uc[(size_t)ka * Cl.nx + ia];
+                    if (kao && ibo && wb != T(0)) acc = acc + (va * wb) * uc[(size_t)ka * Cl.nx + ib];
+                    if (kbo && iao && vb != T(0)) acc = acc + (vb * wa) * uc[(size_t)kb * Cl.nx + ia];
+                    if (kbo && ibo && vb != T(0) && wb != T(0)) acc = acc + (vb * wb) * uc[(size_t)kb * Cl.nx + ib];
                     u[p] = u[p] + acc;
                 }
                 break;
@@ -1063,9 +1396,9 @@ __global__ void __launch_bounds__(1024) k_tail(TailArgs a, const RhsState* st) {
     }
 }
 
-size_t tail_smem_bytes(const helm_model* m, size_t elem) {
+size_t tail_smem_bytes(const helm_model* m, int lt, size_t elem) {
     size_t v = 0;
-    for (size_t l = m->lt; l < m->lv.size(); ++l) v += 3 * m->lv[l].n();
+    for (size_t l = lt; l < m->lv.size(); ++l) v += 8 * m->lv[l].n();   // f, u, r + 5 coefficients
     return v * 2 * elem;
 }
 
@@ -1076,7 +1409,7 @@ void launch_tail(const TailArgs& a, size_t smem, int nrhs, const RhsState* st, c
         cudaFuncSetAttribute(k_tail<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
         attr_set = true;
     }
-    k_tail<T><<<nrhs, 1024, smem, s>>>(a, st);
+    launch_pdl(k_tail<T>, dim3(nrhs), dim3(1024), smem, s, a, st);
 }
 template void launch_tail<float>(const TailArgs&, size_t, int, const RhsState*, cudaStream_t);
 template void launch_tail<double>(const TailArgs&, size_t, int, const RhsState*, cudaStream_t);
@@ -1110,7 +1443,7 @@ std::vector<int> tail_schedule(int lt, int L, bool fcycle) {
 // u2 = wj D^-1 f + P e on the fine region of a coarse tile, r = f - M u2,
 // restricted to level l + 1 (the second coarse correction of an F-cycle).
 template <typename T, bool GAL>
-__global__ void __launch_bounds__(256) k_correct_restrict(LevelDev Lf, LevelDev Lc, const double* __restrict__ w2,
+__global__ void __launch_bounds__(256) k_correct_restrict(LevelDev Lf, LevelDev Lc, const T* __restrict__ w2,
                                                           T b1, T b2, T wj, const T* __restrict__ f,
                                                           const T* __restrict__ ec, T* __restrict__ fc,
                                                           const RhsState* st) {
@@ -1179,19 +1512,30 @@ __global__ void __launch_bounds__(256) k_correct_restrict(LevelDev Lf, LevelDev 
 }
 
 template <typename T>
-void launch_correct_restrict(const LevelDev& Lf, const LevelDev& Lc, const double* w2, double b1, double b2,
-                             double wj, const T* f, const T* ec, T* fc, const RhsState* st, int nrhs, cudaStream_t s) {
-    dim3 grd((Lc.nx + RCX - 1) / RCX, (Lc.nz + RCZ - 1) / RCZ, nrhs);
-    if (Lf.m2)
+void launch_correct_restrict(const LevelDev& Lf, const LevelDev& Lc, const T* w2, double b1, double b2,
+                             double wj, const T* f, const T* ec, T* fc, const RhsState* st, int nrhs, cudaStream_t s,
+                             int tile) {
+    if (Lf.m2) {
+        dim3 grd((Lc.nx + RCX - 1) / RCX, (Lc.nz + RCZ - 1) / RCZ, nrhs);
         k_correct_restrict<T, false><<<grd, RCX * RCZ, 0, s>>>(Lf, Lc, w2, (T)b1, (T)b2, (T)wj, f, ec, fc, st);
-    else
-        k_correct_restrict<T, true><<<grd, RCX * RCZ, 0, s>>>(Lf, Lc, w2, (T)b1, (T)b2, (T)wj, f, ec, fc, st);
+    } else if (sizeof(T) == 4 && tile == 0) {
+        constexpr int GRCX = 8, GRCZ = GTile<T>::RCZ;
+        dim3 grd((Lc.nx + GRCX - 1) / GRCX, (Lc.nz + GRCZ - 1) / GRCZ, nrhs);
+        launch_pdl(k_restrict_g<T, true, GRCX>, grd, dim3(GRCX * GRCZ), 0, s, Lf, Lc, w2, (T)b1, (T)b2, (T)wj, f, ec, fc,
+                   st);
+    } else {
+        constexpr int GRCX = GTile<T>::RCX, GRCZ = GTile<T>::RCZ;
+        dim3 grd((Lc.nx + GRCX - 1) / GRCX, (Lc.nz + GRCZ - 1) / GRCZ, nrhs);
+        launch_pdl(k_restrict_g<T, true, GRCX>, grd, dim3(GRCX * GRCZ), 0, s, Lf, Lc, w2, (T)b1, (T)b2, (T)wj, f, ec, fc,
+                   st);
+    }
 }
-template void launch_correct_restrict<float>(const LevelDev&, const LevelDev&, const double*, double, double, double,
-                                             const float*, const float*, float*, const RhsState*, int, cudaStream_t);
+template void launch_correct_restrict<float>(const LevelDev&, const LevelDev&, const float*, double, double, double,
+                                             const float*, const float*, float*, const RhsState*, int, cudaStream_t,
+                                             int);
 template void launch_correct_restrict<double>(const LevelDev&, const LevelDev&, const double*, double, double, double,
                                               const double*, const double*, double*, const RhsState*, int,
-                                              cudaStream_t);
+                                              cudaStream_t, int);
 
 // ============================================================ right-hand sides
 __global__ void k_point_rhs(double* f, const int* __restrict__ src_flat, size_t n) {
@@ -1341,11 +1685,11 @@ void launch_fold(const double* g_pad, const double* m_pad, int Px, int Pz, int n
     template void launch_bicg_s<T>(const T*, const T*, T*, const RhsState*, size_t, int, cudaStream_t);           \
     template void launch_bicg_xr<T>(T*, const T*, const T*, const T*, const T*, const T*, T*, double*, int,       \
                                     RhsState*, int*, size_t, int, cudaStream_t);                                  \
-    template void launch_restrict<T>(const LevelDev&, const LevelDev&, const double*, double, double, double,     \
-                                     const T*, T*, const RhsState*, int, cudaStream_t);                           \
-    template void launch_prolong<T>(int, const LevelDev&, const LevelDev&, int, double, const double*, double,    \
+    template void launch_restrict<T>(const LevelDev&, const LevelDev&, const T*, double, double, double,          \
+                                     const T*, T*, const RhsState*, int, cudaStream_t, int);                      \
+    template void launch_prolong<T>(int, const LevelDev&, const LevelDev&, int, double, const T*, double,         \
                                     double, double, const T*, const T*, T*, T*, const T*, double*, int,           \
-                                    RhsState*, int, cudaStream_t, int);                                           \
+                                    RhsState*, int, cudaStream_t, int, int);                                      \
     template void launch_coarse<T>(int, const T*, const int*, const T*, T*, const RhsState*, int, cudaStream_t);
 HELM_INST(float)
 HELM_INST(double)

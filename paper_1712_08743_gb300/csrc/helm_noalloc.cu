@@ -66,11 +66,13 @@ extern "C" int helm_vcycle_noalloc(helm_model* m, int nrhs, const double* omega,
     if (!std::isfinite(beta1) || !std::isfinite(beta2) || !(omega_jacobi > 0.0)) return HELM_E_INVALID;
     // per-RHS (h omega)^2 and one coarsest-level inverse per distinct frequency, on the stack
     double hw2[kNoAllocMaxRhs], w2s[kNoAllocMaxRhs];
+    float hw2f[kNoAllocMaxRhs];
     int slot[kNoAllocMaxRhs], mods[kNoAllocMaxRhs];
     int nslots = 0;
     for (int b = 0; b < nrhs; ++b) {
         if (!(std::isfinite(omega[b]) && omega[b] > 0.0)) return HELM_E_INVALID;
         hw2[b] = m->h * m->h * omega[b] * omega[b];
+        hw2f[b] = (float)hw2[b];
         const int mod = m->nmodels > 1 ? b : 0;
         int k = 0;
         while (k < nslots && !(w2s[k] == hw2[b] && mods[k] == mod)) ++k;
@@ -83,6 +85,7 @@ extern "C" int helm_vcycle_noalloc(helm_model* m, int nrhs, const double* omega,
     size_t off = 0;
     auto take = [&](size_t bytes) { size_t o = off; off = align256(off + bytes); return o; };
     const size_t o_w2 = take(sizeof(double) * nrhs);
+    const size_t o_w2f = take(sizeof(float) * nrhs);
     const size_t o_slot = take(sizeof(int) * nrhs);
     const size_t o_w2s = take(sizeof(double) * nslots);
     const size_t o_mods = take(sizeof(int) * nslots);
@@ -90,7 +93,7 @@ extern "C" int helm_vcycle_noalloc(helm_model* m, int nrhs, const double* omega,
     const size_t o_mf = take(sizeof(float2) * nc * nc * nslots);
     const size_t o_md = take(sizeof(double2) * nc * nc * nslots);
     size_t o_f[kMaxLevels], o_e[kMaxLevels];
-    for (int l = 1; l <= m->lt; ++l) {
+    for (int l = 1; l <= m->lt[0]; ++l) {
         o_f[l] = take(sizeof(float) * 2 * m->lv[l].n() * nrhs);
         o_e[l] = take(sizeof(float) * 2 * m->lv[l].n() * nrhs);
     }
@@ -107,6 +110,7 @@ extern "C" int helm_vcycle_noalloc(helm_model* m, int nrhs, const double* omega,
     if (rc != HELM_OK) { if (cur != dev) cudaSetDevice(cur); return rc; }
     cudaStream_t s = m->ctx->stream;
     cudaError_t e = cudaMemcpyAsync(base + o_w2, hw2, sizeof(double) * nrhs, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(base + o_w2f, hw2f, sizeof(float) * nrhs, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(base + o_slot, slot, sizeof(int) * nrhs, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(base + o_w2s, w2s, sizeof(double) * nslots, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(base + o_mods, mods, sizeof(int) * nslots, cudaMemcpyHostToDevice, s);
@@ -119,6 +123,7 @@ extern "C" int helm_vcycle_noalloc(helm_model* m, int nrhs, const double* omega,
                              reinterpret_cast<double2*>(base + o_md), s);
         MgCall mc;
         mc.w2 = dw2;
+        mc.w2f = reinterpret_cast<const float*>(base + o_w2f);
         mc.b1 = beta1;
         mc.b2 = beta2;
         mc.wj = omega_jacobi;
@@ -131,7 +136,7 @@ extern "C" int helm_vcycle_noalloc(helm_model* m, int nrhs, const double* omega,
         mc.pstride = 0;
         MgLevels<float> B;
         std::memset(&B, 0, sizeof(B));
-        for (int l = 1; l <= m->lt; ++l) {
+        for (int l = 1; l <= m->lt[0]; ++l) {
             B.f[l] = reinterpret_cast<float*>(base + o_f[l]);
             B.e[l] = reinterpret_cast<float*>(base + o_e[l]);
         }

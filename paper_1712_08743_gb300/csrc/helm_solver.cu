@@ -81,6 +81,7 @@ struct SolveCtx {
     int nrhs;
     helm_solve_opts o;
     const double* w2;       // device [nrhs]
+    const float* w2f;       // device [nrhs], FP32 copy
     RhsState* st;           // device [nrhs]
     double* partials;       // device [nrhs * pstride]
     int pstride;
@@ -91,12 +92,19 @@ struct SolveCtx {
 };
 
 template <typename T>
+static const T* hw_of(const MgCall& c) {
+    return static_cast<const T*>(sizeof(T) == 8 ? (const void*)c.w2 : (const void*)c.w2f);
+}
+
+template <typename T>
 static void mg_cycle(const helm_model* m, const MgCall& c, const MgLevels<T>& B, int l, bool F, int acc) {
     const bool dbl = sizeof(T) == 8;
-    if (l >= m->lt) {
+    const T* hw = hw_of<T>(c);
+    const int lt = m->tail_level(dbl);
+    if (l >= lt) {
         TailArgs a;
         std::memset(&a, 0, sizeof(a));
-        a.lt = m->lt;
+        a.lt = lt;
         a.L = (int)m->lv.size() - 1;
         for (int q = 0; q <= a.L; ++q) a.lv[q] = level_dev(m, q, dbl);
         a.in = B.f[l];
@@ -104,53 +112,56 @@ static void mg_cycle(const helm_model* m, const MgCall& c, const MgLevels<T>& B,
         a.accumulate = acc;
         a.minv = c.minv;
         a.slot = c.slot;
-        a.ops = F ? m->ops_f : m->ops_v;
-        a.nops = F ? m->nops_f : m->nops_v;
+        a.ops = F ? m->ops_f[dbl] : m->ops_v[dbl];
+        a.nops = F ? m->nops_f[dbl] : m->nops_v[dbl];
         a.w2 = c.w2;
         a.b1 = c.b1;
         a.b2 = c.b2;
         a.wj = c.wj;
-        launch_tail<T>(a, dbl ? m->tail_smem64 : m->tail_smem32, c.nrhs, c.st, c.s);
+        launch_tail<T>(a, m->tail_smem[dbl], c.nrhs, c.st, c.s);
         return;
     }
     const LevelDev Lf = level_dev(m, l, dbl), Lc = level_dev(m, l + 1, dbl);
-    launch_restrict<T>(Lf, Lc, c.w2, c.b1, c.b2, c.wj, B.f[l], B.f[l + 1], c.st, c.nrhs, c.s);
+    launch_restrict<T>(Lf, Lc, hw, c.b1, c.b2, c.wj, B.f[l], B.f[l + 1], c.st, c.nrhs, c.s, m->tile_restrict[l]);
     mg_cycle<T>(m, c, B, l + 1, F || (l + 1 == m->lf), 0);
     if (F) {
-        launch_correct_restrict<T>(Lf, Lc, c.w2, c.b1, c.b2, c.wj, B.f[l], B.e[l + 1], B.f[l + 1], c.st, c.nrhs, c.s);
+        launch_correct_restrict<T>(Lf, Lc, hw, c.b1, c.b2, c.wj, B.f[l], B.e[l + 1], B.f[l + 1], c.st, c.nrhs, c.s,
+                                   m->tile_restrict[l]);
         mg_cycle<T>(m, c, B, l + 1, false, 1);
     }
-    launch_prolong<T>(0, Lf, Lc, m->npml, m->alpha_max, c.w2, c.b1, c.b2, c.wj, B.f[l], B.e[l + 1], B.e[l], nullptr,
-                      nullptr, nullptr, 0, c.st, c.nrhs, c.s, acc);
+    launch_prolong<T>(0, Lf, Lc, m->npml, m->alpha_max, hw, c.b1, c.b2, c.wj, B.f[l], B.e[l + 1], B.e[l], nullptr,
+                      nullptr, nullptr, 0, c.st, c.nrhs, c.s, acc, m->tile_prolong[l]);
 }
 
 template <typename T>
 void mg_apply(const helm_model* m, const MgCall& c, const MgLevels<T>& B, const T* in, T* out, int mode, T* y,
               const T* aux) {
     const bool dbl = sizeof(T) == 8;
+    const T* hw = hw_of<T>(c);
     const LevelDev L0 = level_dev(m, 0, dbl), L1 = level_dev(m, 1, dbl);
-    launch_restrict<T>(L0, L1, c.w2, c.b1, c.b2, c.wj, in, B.f[1], c.st, c.nrhs, c.s);
+    launch_restrict<T>(L0, L1, hw, c.b1, c.b2, c.wj, in, B.f[1], c.st, c.nrhs, c.s);
     mg_cycle<T>(m, c, B, 1, m->lf == 1, 0);
-    launch_prolong<T>(mode, L0, L1, m->npml, m->alpha_max, c.w2, c.b1, c.b2, c.wj, in, B.e[1], out, y, aux,
-                      c.partials, c.pstride, c.st, c.nrhs, c.s);
+    launch_prolong<T>(mode, L0, L1, m->npml, m->alpha_max, hw, c.b1, c.b2, c.wj, in, B.e[1], out, y, aux,
+                      c.partials, c.pstride, c.st, c.nrhs, c.s, 0, m->tile_prolong[0]);
 }
 template void mg_apply<float>(const helm_model*, const MgCall&, const MgLevels<float>&, const float*, float*, int,
                               float*, const float*);
 template void mg_apply<double>(const helm_model*, const MgCall&, const MgLevels<double>&, const double*, double*, int,
                                double*, const double*);
 
-static int count_cycle(const helm_model* m, int l, bool F) {
-    if (l >= m->lt) return 1;
-    int k = 2 + count_cycle(m, l + 1, F || (l + 1 == m->lf));
-    if (F) k += 1 + count_cycle(m, l + 1, false);
+static int count_cycle(const helm_model* m, int lt, int l, bool F) {
+    if (l >= lt) return 1;
+    int k = 2 + count_cycle(m, lt, l + 1, F || (l + 1 == m->lf));
+    if (F) k += 1 + count_cycle(m, lt, l + 1, false);
     return k;
 }
-int mg_kernels_per_apply(const helm_model* m) { return 2 + count_cycle(m, 1, m->lf == 1); }
+int mg_kernels_per_apply(const helm_model* m, bool dbl) { return 2 + count_cycle(m, m->tail_level(dbl), 1, m->lf == 1); }
 
 template <typename T>
 static void vcycle(const SolveCtx& c, Inner<T>& w, const T* in, T* out, int mode, T* y, const T* aux) {
     MgCall mc;
     mc.w2 = c.w2;
+    mc.w2f = c.w2f;
     mc.b1 = c.o.beta1;
     mc.b2 = c.o.beta2;
     mc.wj = c.o.omega_jacobi;
@@ -163,7 +174,7 @@ static void vcycle(const SolveCtx& c, Inner<T>& w, const T* in, T* out, int mode
     mc.pstride = c.pstride;
     MgLevels<T> B;
     std::memset(&B, 0, sizeof(B));
-    for (int l = 1; l <= c.m->lt; ++l) {
+    for (int l = 1; l <= c.m->tail_level(sizeof(T) == 8); ++l) {
         B.f[l] = w.fl[l]->template as<T>();
         B.e[l] = w.el[l]->template as<T>();
     }
@@ -175,7 +186,7 @@ static int alloc_levels(const helm_model* m, cudaStream_t s, int nrhs, Inner<T>&
     const int nl = (int)m->lv.size();
     w.fl.resize(nl);
     w.el.resize(nl);
-    for (int l = 1; l < nl && l <= m->lt; ++l) {
+    for (int l = 1; l < nl && l <= m->tail_level(sizeof(T) == 8); ++l) {
         const size_t b = sizeof(T) * 2 * m->lv[l].n() * nrhs;
         w.fl[l].reset(new DBuf());
         w.el[l].reset(new DBuf());
@@ -196,7 +207,7 @@ static int alloc_inner(const SolveCtx& c, Inner<T>& w) {
 
 // kernels one BiCGSTAB iteration launches: p, s and x/r updates plus two
 // preconditioner applications
-static int kernels_per_iteration(const helm_model* m) { return 3 + 2 * mg_kernels_per_apply(m); }
+static int kernels_per_iteration(const helm_model* m, bool dbl) { return 3 + 2 * mg_kernels_per_apply(m, dbl); }
 
 template <typename T>
 static void bicg_iteration(const SolveCtx& c, Inner<T>& w) {
@@ -248,7 +259,7 @@ static int inner_solve(const SolveCtx& c, Inner<T>& w, const T* rin, cudaGraphEx
         } else {
             for (int k = 0; k < chunk; ++k) bicg_iteration<T>(c, w);
         }
-        count_launches((unsigned long long)chunk * kernels_per_iteration(c.m));
+        count_launches((unsigned long long)chunk * kernels_per_iteration(c.m, sizeof(T) == 8));
         done += chunk;
         HELM_CUDA_TRY(cudaMemcpyAsync(&h_active, c.nactive, sizeof(int), cudaMemcpyDeviceToHost, c.s));
         HELM_CUDA_TRY(cudaStreamSynchronize(c.s));
@@ -335,7 +346,7 @@ static int fgmres_inner(const SolveCtx& c, Inner<T>& w, FgBufs<T>& f, const T* r
         fgmres_cycle<T>(c, w, f, rin);
     }
     const int m = f.dev.m;
-    count_launches(4 + (unsigned long long)m * (mg_kernels_per_apply(c.m) + 5));
+    count_launches(4 + (unsigned long long)m * (mg_kernels_per_apply(c.m, sizeof(T) == 8) + 5));
     HELM_CUDA_TRY(cudaGetLastError());
     *iters_done += m;
     return HELM_OK;
@@ -397,8 +408,9 @@ static int solve_impl(const helm_model* m, cudaStream_t s, int nrhs, const doubl
     c.o = o;
     c.pstride = 3 * max_blocks_per_rhs(m);
     if (o.krylov == HELM_KRYLOV_FGMRES) c.pstride = std::max(c.pstride, kFgPartials);
-    DBuf w2, st, part, nact, rin;
+    DBuf w2, w2f, st, part, nact, rin;
     TRY_ALLOC(w2, sizeof(double) * nrhs, s);
+    TRY_ALLOC(w2f, sizeof(float) * nrhs, s);
     TRY_ALLOC(st, sizeof(RhsState) * nrhs, s);
     TRY_ALLOC(part, sizeof(double) * (size_t)c.pstride * nrhs, s);
     TRY_ALLOC(nact, sizeof(int), s);
@@ -407,6 +419,7 @@ static int solve_impl(const helm_model* m, cudaStream_t s, int nrhs, const doubl
     int rc = build_coarse(m, s, nrhs, h_w2, o.beta1, o.beta2, cs);
     if (rc != HELM_OK) return rc;
     c.w2 = w2.as<double>();
+    c.w2f = w2f.as<float>();
     c.st = st.as<RhsState>();
     c.partials = part.as<double>();
     c.nactive = nact.as<int>();
@@ -428,6 +441,8 @@ static int solve_impl(const helm_model* m, cudaStream_t s, int nrhs, const doubl
     for (auto& S : hs) { S.outer_active = 1; S.active = 1; S.max_it = o.max_it; }
     HELM_CUDA_TRY(cudaMemcpyAsync(c.st, hs.data(), sizeof(RhsState) * nrhs, cudaMemcpyHostToDevice, s));
     HELM_CUDA_TRY(cudaMemcpyAsync(w2.p, h_w2, sizeof(double) * nrhs, cudaMemcpyHostToDevice, s));
+    std::vector<float> h_w2f(h_w2, h_w2 + nrhs);
+    HELM_CUDA_TRY(cudaMemcpyAsync(w2f.p, h_w2f.data(), sizeof(float) * nrhs, cudaMemcpyHostToDevice, s));
     HELM_CUDA_TRY(cudaMemsetAsync(part.p, 0, sizeof(double) * (size_t)c.pstride * nrhs, s));
     HELM_CUDA_TRY(cudaMemsetAsync(u64, 0, sizeof(double) * 2 * n * nrhs, s));
 
@@ -508,13 +523,17 @@ int vcycle_once(const helm_model* m, cudaStream_t s, int nrhs, const double* h_w
     c.o.beta2 = b2;
     c.o.omega_jacobi = wj;
     c.pstride = 3 * max_blocks_per_rhs(m);
-    DBuf w2;
+    DBuf w2, w2f;
     TRY_ALLOC(w2, sizeof(double) * nrhs, s);
+    TRY_ALLOC(w2f, sizeof(float) * nrhs, s);
     HELM_CUDA_TRY(cudaMemcpyAsync(w2.p, h_w2, sizeof(double) * nrhs, cudaMemcpyHostToDevice, s));
+    std::vector<float> h_w2f(h_w2, h_w2 + nrhs);
+    HELM_CUDA_TRY(cudaMemcpyAsync(w2f.p, h_w2f.data(), sizeof(float) * nrhs, cudaMemcpyHostToDevice, s));
     CoarseSet cs;
     int rc = build_coarse(m, s, nrhs, h_w2, b1, b2, cs);
     if (rc != HELM_OK) return rc;
     c.w2 = w2.as<double>();
+    c.w2f = w2f.as<float>();
     c.st = nullptr;
     c.partials = nullptr;
     c.nactive = nullptr;
@@ -549,9 +568,10 @@ int time_kernel(const helm_model* m, cudaStream_t s, int kernel, int nrhs, doubl
         // byte 0x3C gives small normal, non-zero values in both precisions
         HELM_CUDA_TRY(cudaMemsetAsync(v[k]->p, 0x3C, dbl ? v64 : v32, s));
     }
-    DBuf w2, st, part, nact, fc, rin;
+    DBuf w2, w2f, st, part, nact, fc, rin;
     const int pstride = 3 * max_blocks_per_rhs(m);
     TRY_ALLOC(w2, sizeof(double) * nrhs, s);
+    TRY_ALLOC(w2f, sizeof(float) * nrhs, s);
     TRY_ALLOC(st, sizeof(RhsState) * nrhs, s);
     TRY_ALLOC(part, sizeof(double) * (size_t)pstride * nrhs, s);
     TRY_ALLOC(nact, sizeof(int), s);
@@ -567,6 +587,8 @@ int time_kernel(const helm_model* m, cudaStream_t s, int kernel, int nrhs, doubl
         S.rho[0] = 1.0; S.alpha[0] = 0.5; S.omega[0] = 0.5; S.beta[0] = 0.5;
     }
     HELM_CUDA_TRY(cudaMemcpyAsync(w2.p, hw.data(), sizeof(double) * nrhs, cudaMemcpyHostToDevice, s));
+    std::vector<float> hwf(hw.begin(), hw.end());
+    HELM_CUDA_TRY(cudaMemcpyAsync(w2f.p, hwf.data(), sizeof(float) * nrhs, cudaMemcpyHostToDevice, s));
     HELM_CUDA_TRY(cudaMemcpyAsync(st.p, hs.data(), sizeof(RhsState) * nrhs, cudaMemcpyHostToDevice, s));
     HELM_CUDA_TRY(cudaMemsetAsync(part.p, 0, sizeof(double) * (size_t)pstride * nrhs, s));
     const double N = (double)n, B = (double)nrhs;
@@ -576,7 +598,7 @@ int time_kernel(const helm_model* m, cudaStream_t s, int kernel, int nrhs, doubl
     std::function<void()> launch;
     switch (kernel) {
         case HELM_KERNEL_APPLY:
-            launch = [&] { launch_apply<float>(level_dev(m, 0, false), m->npml, m->alpha_max, w2.as<double>(), F(0), F(1), 1.0f, nrhs, s); };
+            launch = [&] { launch_apply<float>(level_dev(m, 0, false), m->npml, m->alpha_max, w2f.as<float>(), F(0), F(1), 1.0f, nrhs, s); };
             *bytes = N * (16.0 * B + 4.0);
             break;
         case HELM_KERNEL_APPLY64:
@@ -584,11 +606,11 @@ int time_kernel(const helm_model* m, cudaStream_t s, int kernel, int nrhs, doubl
             *bytes = N * (32.0 * B + 8.0);
             break;
         case HELM_KERNEL_RESTRICT:
-            launch = [&] { launch_restrict<float>(level_dev(m, 0, false), level_dev(m, 1, false), w2.as<double>(), 1.0, 0.5, 0.8, F(0), fc.as<float>(), S, nrhs, s); };
+            launch = [&] { launch_restrict<float>(level_dev(m, 0, false), level_dev(m, 1, false), w2f.as<float>(), 1.0, 0.5, 0.8, F(0), fc.as<float>(), S, nrhs, s); };
             *bytes = N * (8.0 * B + 4.0) + 8.0 * B * (double)m->lv[1].n();
             break;
         case HELM_KERNEL_PROLONG:
-            launch = [&] { launch_prolong<float>(1, level_dev(m, 0, false), level_dev(m, 1, false), m->npml, m->alpha_max, w2.as<double>(), 1.0, 0.5, 0.8, F(0), fc.as<float>(), F(1), F(2), F(3), part.as<double>(), pstride, S, nrhs, s); };
+            launch = [&] { launch_prolong<float>(1, level_dev(m, 0, false), level_dev(m, 1, false), m->npml, m->alpha_max, w2f.as<float>(), 1.0, 0.5, 0.8, F(0), fc.as<float>(), F(1), F(2), F(3), part.as<double>(), pstride, S, nrhs, s); };
             *bytes = N * (32.0 * B + 4.0) + 8.0 * B * (double)m->lv[1].n();
             break;
         case HELM_KERNEL_BICG_XR:
@@ -622,6 +644,76 @@ int time_kernel(const helm_model* m, cudaStream_t s, int kernel, int nrhs, doubl
     cudaEventDestroy(e1);
     HELM_CUDA_TRY(cudaGetLastError());
     *ms = (double)t / reps;
+    return HELM_OK;
+}
+
+// -------------------------------------------------------------- autotune
+// Times the tile variants of the complex64 multigrid kernels on the grid levels
+// (finest-level prolongation; Galerkin restriction and prolongation on levels
+// 1..lt-1) for a batch of nrhs right-hand sides, keeps the faster of each in the
+// model and returns the choices: out[l] = restriction tile, out[kMaxLevels + l]
+// = prolongation tile.
+int autotune(helm_model* m, cudaStream_t s, int nrhs, double hw2, int reps, int* out) {
+    const int lt = m->tail_level(false);
+    size_t maxn = m->n();
+    std::vector<std::unique_ptr<DBuf>> v(4);
+    for (auto& b : v) {
+        b.reset(new DBuf());
+        TRY_ALLOC(*b, sizeof(float) * 2 * maxn * nrhs, s);
+        HELM_CUDA_TRY(cudaMemsetAsync(b->p, 0x3C, sizeof(float) * 2 * maxn * nrhs, s));
+    }
+    DBuf w2f, st, part;
+    const int pstride = 3 * max_blocks_per_rhs(m);
+    TRY_ALLOC(w2f, sizeof(float) * nrhs, s);
+    TRY_ALLOC(st, sizeof(RhsState) * nrhs, s);
+    TRY_ALLOC(part, sizeof(double) * (size_t)pstride * nrhs, s);
+    std::vector<float> hw(nrhs, (float)hw2);
+    HELM_CUDA_TRY(cudaMemcpyAsync(w2f.p, hw.data(), sizeof(float) * nrhs, cudaMemcpyHostToDevice, s));
+    std::vector<RhsState> hs(nrhs);
+    std::memset(hs.data(), 0, sizeof(RhsState) * nrhs);
+    for (auto& S : hs) { S.active = 1; S.outer_active = 1; S.rho[0] = 1.0; }
+    HELM_CUDA_TRY(cudaMemcpyAsync(st.p, hs.data(), sizeof(RhsState) * nrhs, cudaMemcpyHostToDevice, s));
+    HELM_CUDA_TRY(cudaMemsetAsync(part.p, 0, sizeof(double) * (size_t)pstride * nrhs, s));
+    RhsState* S = st.as<RhsState>();
+    auto F = [&](int k) { return v[k]->as<float>(); };
+    cudaEvent_t e0, e1;
+    HELM_CUDA_TRY(cudaEventCreate(&e0));
+    HELM_CUDA_TRY(cudaEventCreate(&e1));
+    auto time_it = [&](const std::function<void()>& launch) -> float {
+        for (int k = 0; k < 2; ++k) launch();
+        // restore the states the finest-level reduction may have changed
+        cudaMemcpyAsync(st.p, hs.data(), sizeof(RhsState) * nrhs, cudaMemcpyHostToDevice, s);
+        cudaEventRecord(e0, s);
+        for (int k = 0; k < reps; ++k) launch();
+        cudaEventRecord(e1, s);
+        cudaEventSynchronize(e1);
+        float t = 0.f;
+        cudaEventElapsedTime(&t, e0, e1);
+        return t;
+    };
+    for (int l = 0; l < kMaxLevels; ++l) { out[l] = m->tile_restrict[l]; out[kMaxLevels + l] = m->tile_prolong[l]; }
+    for (int l = 0; l < lt; ++l) {
+        const LevelDev Lf = level_dev(m, l, false), Lc = level_dev(m, l + 1, false);
+        float tp[2], tr[2] = {0.f, 0.f};
+        for (int t = 0; t < 2; ++t) {
+            tp[t] = time_it([&] {
+                launch_prolong<float>(l == 0 ? 1 : 0, Lf, Lc, m->npml, m->alpha_max, w2f.as<float>(), 1.0, 0.5, 0.5,
+                                      F(0), F(1), F(2), F(3), F(0), part.as<double>(), pstride, S, nrhs, s, 0, t);
+            });
+            if (l > 0)
+                tr[t] = time_it([&] {
+                    launch_restrict<float>(Lf, Lc, w2f.as<float>(), 1.0, 0.5, 0.5, F(0), F(1), S, nrhs, s, t);
+                });
+        }
+        m->tile_prolong[l] = tp[0] < tp[1] ? 0 : 1;
+        if (l > 0) m->tile_restrict[l] = tr[0] < tr[1] ? 0 : 1;
+        out[l] = m->tile_restrict[l];
+        out[kMaxLevels + l] = m->tile_prolong[l];
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    HELM_CUDA_TRY(cudaGetLastError());
+    HELM_CUDA_TRY(cudaStreamSynchronize(s));
     return HELM_OK;
 }
 

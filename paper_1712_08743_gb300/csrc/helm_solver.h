@@ -49,7 +49,8 @@ int coarsest_points(const helm_model* m);
 // f[l], e[l] (l >= 1): per-level right-hand side and correction buffers
 // [nrhs][n_l]. mode as launch_prolong on the finest level.
 struct MgCall {
-    const double* w2;       // (h omega)^2 per RHS, device
+    const double* w2;       // (h omega)^2 per RHS, device, FP64
+    const float* w2f;       // the same in FP32 (for the complex64 kernels)
     double b1, b2, wj;
     RhsState* st;           // nullable
     int nrhs;
@@ -67,8 +68,9 @@ struct MgLevels {
 template <typename T>
 void mg_apply(const helm_model* m, const MgCall& c, const MgLevels<T>& B, const T* in, T* out, int mode, T* y,
               const T* aux);
-int mg_kernels_per_apply(const helm_model* m);
+int mg_kernels_per_apply(const helm_model* m, bool dbl);
 
+int autotune(helm_model* m, cudaStream_t s, int nrhs, double hw2, int reps, int* out);
 int time_kernel(const helm_model* m, cudaStream_t s, int kernel, int nrhs, double hw2, int reps, double* ms,
                 double* bytes);
 

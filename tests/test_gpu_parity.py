@@ -150,6 +150,30 @@ def test_batch_equals_each_alone_and_oracle(hg, ctx):
     model.close()
 
 
+def test_autotuned_tiles_give_the_same_wavefields(hg, ctx, tmp_path):
+    from paper_1712_08743_gb300 import autotune
+
+    mdl = models.c3_model()
+    model = hg.helm_create_model(ctx, mdl.slowness, mdl.h, mdl.npml, mdl.alpha_max)
+    om = np.repeat(mdl.omegas[[1, 3]], 4)
+    src = np.tile(mdl.sources[[3, 20, 41, 60]], (2, 1))
+    opts = dict(tol=1e-9)
+    u0, _, _ = hg.helm_solve(model, om, src, opts=opts)
+    tiles = autotune.autotune(model, len(om), float(om[0]), str(tmp_path / "t.json"))
+    assert set(tiles) <= {0, 1} and len(tiles) == autotune.NTILES
+    # force the smaller tiles everywhere too
+    import ctypes as C
+    small = (C.c_int * autotune.NTILES)(*([0] * autotune.NTILES))
+    for arr in (None, small):
+        if arr is not None:
+            assert model.lib.helm_set_tiles(model.handle, arr) == 0
+        u1, st, _ = hg.helm_solve(model, om, src, opts=opts)
+        assert all(s["converged"] for s in st)
+        for k in range(len(om)):
+            assert rel(u1[k], u0[k]) < 1e-6   # dot products sum in another order; tol 1e-9 solves
+    model.close()
+
+
 def test_not_converged_status_and_best_iterate(hg, ctx):
     mdl = models.c1_model()
     model = hg.helm_create_model(ctx, mdl.slowness, mdl.h, mdl.npml, mdl.alpha_max)
