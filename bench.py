@@ -51,6 +51,8 @@ def parse():
     ap.add_argument("--workload", default="single", choices=["single", "batched", "serving"],
                     help="single: the single large case (the default line); batched: 64 shots x 5 "
                          "frequencies in one call; serving: a Poisson stream of requests")
+    ap.add_argument("--kernels-only", action="store_true",
+                    help="time only the hot kernels alone (the roofline legs), print one line per kernel")
     ap.add_argument("--requests", type=int, default=48, help="serving: number of requests")
     ap.add_argument("--rate", type=float, default=0.0, help="serving: arrivals per second (0: 0.8 x measured)")
     return ap.parse_args()
@@ -171,6 +173,50 @@ def run_reference(args):
 
 
 # ---------------------------------------------------------------- our arm
+KERNELS = (("bicg_xr", "HELM_KERNEL_BICG_XR"), ("prolong_fine", "HELM_KERNEL_PROLONG"),
+           ("restrict_fine", "HELM_KERNEL_RESTRICT"), ("stencil_apply", "HELM_KERNEL_APPLY"),
+           ("bicg_p", "HELM_KERNEL_BICG_P"), ("resid64", "HELM_KERNEL_RESID64"))
+
+
+def time_kernels(lib, api, _lib, model, omega, reps=20):
+    """Each hot kernel timed alone (CUDA events on the library's stream, inside
+    helm_time_kernel) on a batch large enough that one launch moves more than
+    three times the L2 size, so consecutive launches cannot run from L2."""
+    out = {}
+    for name, kid_name in KERNELS:
+        kid = getattr(_lib, kid_name)
+        tms, byt = api.C.c_double(), api.C.c_double()
+        # bytes of one right-hand side first (one launch of a single-RHS batch)
+        api.check(lib.helm_time_kernel(model.handle, kid, 1, omega, 1, api.C.byref(tms), api.C.byref(byt)),
+                  "helm_time_kernel")
+        nb = int(min(64, max(8, -(-3 * L2_BYTES // int(byt.value)))))
+        api.check(lib.helm_time_kernel(model.handle, kid, nb, omega, reps, api.C.byref(tms), api.C.byref(byt)),
+                  "helm_time_kernel")
+        out[name] = {"ms": tms.value, "bytes": byt.value, "gbs": byt.value / tms.value / 1e6, "nrhs": nb}
+    return out
+
+
+def run_kernels_only(args):
+    import torch
+
+    from paper_1712_08743_gb300 import _lib, api, build
+    from synth import models
+
+    build.build()
+    lib = _lib.load()
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    ctx = api.Context(0, stream)
+    mdl = models.c2_model()
+    model = api.helm_create_model(ctx, mdl.slowness, mdl.h, mdl.npml, mdl.alpha_max)
+    peak, kind = measured_peaks()
+    for name, k in time_kernels(lib, api, _lib, model, float(mdl.omegas[0]), reps=max(args.steps, 1)).items():
+        print(json.dumps({"kernel": name, "workload": WORKLOAD, **k, "frac": k["gbs"] / peak,
+                          "peak": peak, "peak_kind": kind}), flush=True)
+    model.close()
+    ctx.close()
+
+
 def run_ours(args):
     import torch
 
@@ -270,15 +316,7 @@ def run_ours(args):
 
     # roofline of the dominant kernel and of the stencil, each timed alone on inputs > L2
     peak, peak_kind = measured_peaks()
-    kern = {}
-    for name, kid in (("bicg_xr", _lib.HELM_KERNEL_BICG_XR), ("prolong_fine", _lib.HELM_KERNEL_PROLONG),
-                      ("restrict_fine", _lib.HELM_KERNEL_RESTRICT), ("stencil_apply", _lib.HELM_KERNEL_APPLY),
-                      ("bicg_p", _lib.HELM_KERNEL_BICG_P), ("resid64", _lib.HELM_KERNEL_RESID64)):
-        nb = 8
-        tms, byt = api.C.c_double(), api.C.c_double()
-        api.check(lib.helm_time_kernel(model.handle, kid, nb, float(om[0]), 20, api.C.byref(tms),
-                                       api.C.byref(byt)), "helm_time_kernel")
-        kern[name] = {"ms": tms.value, "bytes": byt.value, "gbs": byt.value / tms.value / 1e6, "nrhs": nb}
+    kern = time_kernels(lib, api, _lib, model, float(om[0]))
     dom = "bicg_xr"
     traffic = None
     prof = os.path.join(ROOT, "profiles", "traffic.json")
@@ -421,6 +459,8 @@ def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.kernels_only:
+        run_kernels_only(args)
     elif args.workload == "batched":
         run_batched(args)
     elif args.workload == "serving":

@@ -83,7 +83,6 @@ enum RhsFlag : int { FLAG_RUNNING = 0, FLAG_CONVERGED = 1, FLAG_BREAKDOWN = 2, F
 struct RhsState {
     // Krylov scalars (BiCGSTAB); complex values as (re, im)
     double rho[2], alpha[2], omega[2], beta[2];
-    double rho_prev[2];  // rho before the last x/r update (for resuming after a residual replacement)
     double bnorm2;       // ||b||^2 of the inner system
     double rnorm2;       // ||r||^2 of the recursive residual
     double tol_rel;      // inner relative tolerance on ||r|| / ||b||

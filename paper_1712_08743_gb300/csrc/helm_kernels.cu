@@ -86,32 +86,67 @@ __global__ void k_sumsq(const double* __restrict__ a, size_t count, double* out)
 void launch_sumsq(const double* a, size_t count, double* out, cudaStream_t s) { k_sumsq<<<1, 1024, 0, s>>>(a, count, out); }
 
 // ============================================================ stencil apply
-// y = scale * A u on the fine grid (with the damping layer).
+// y = scale * A u on the fine grid (with the damping layer). Each thread owns
+// one column x and marches down ZCH rows, keeping rows z-1, z, z+1 in
+// registers: one coalesced load per node (plus the block's two halo rows);
+// the x-neighbours come from the adjacent lanes by warp shuffles (the warp's
+// edge lanes load theirs).
+// Each thread owns AP_R consecutive rows of one column: the AP_R + 2 rows it
+// needs are loaded up front (AP_R + 2 independent loads in flight per thread),
+// the x neighbours come from the adjacent lanes by shuffle, and only the two
+// warp-edge lanes read a neighbour from memory.
+constexpr int AP_X = 32, AP_Y = 8, AP_R = 4;
+
 template <typename T>
-__global__ void __launch_bounds__(256) k_apply(LevelDev L, int npml, T acoef, const T* __restrict__ hwv,
-                                               const T* __restrict__ u, T* __restrict__ y, T scale) {
+__global__ void __launch_bounds__(AP_X * AP_Y) k_apply(LevelDev L, int npml, T acoef, const T* __restrict__ hwv,
+                                                       const T* __restrict__ u, T* __restrict__ y, T scale) {
     const int b = blockIdx.z;
-    const int ix = blockIdx.x * 32 + threadIdx.x, iz = blockIdx.y * 8 + threadIdx.y;
-    if (ix >= L.nx || iz >= L.nz) return;
-    const size_t n = (size_t)L.nx * L.nz;
+    const int nx = L.nx, nz = L.nz;
+    const int ix = blockIdx.x * AP_X + threadIdx.x;
+    const int z0 = (blockIdx.y * AP_Y + threadIdx.y) * AP_R;
+    if (z0 >= nz) return;  // whole warp leaves together (threadIdx.y is uniform in a warp)
+    const size_t n = (size_t)nx * nz;
     const T* ub = u + 2 * n * b;
-    const size_t i = (size_t)iz * L.nx + ix;
+    T* yb = y + 2 * n * b;
+    const T* m2 = m2ptr<T>(L) + (size_t)b * L.mstride;
     const T hw = hwv[b];
-    const T s = hw * (m2ptr<T>(L) + (size_t)b * L.mstride)[i];
-    const T a = layer_alpha_t<T>(ix, iz, L.nx, L.nz, npml, acoef);
-    cx<T> c = ldc(ub, i);
-    cx<T> acc((T(4) - s) * c.re - s * a * c.im, (T(4) - s) * c.im + s * a * c.re);  // (4 - s(1 - j a)) u
-    if (ix > 0) acc = acc - ldc(ub, i - 1);
-    if (ix + 1 < L.nx) acc = acc - ldc(ub, i + 1);
-    if (iz > 0) acc = acc - ldc(ub, i - L.nx);
-    if (iz + 1 < L.nz) acc = acc - ldc(ub, i + L.nx);
-    stc(y + 2 * n * b, i, scale * acc);
+    const bool xin = ix < nx;
+    const int lane = threadIdx.x;
+    cx<T> v[AP_R + 2];
+#pragma unroll
+    for (int k = 0; k < AP_R + 2; ++k) {
+        const int z = z0 - 1 + k;
+        v[k] = (xin && z >= 0 && z < nz) ? ldc(ub, (size_t)z * nx + ix) : cx<T>(0, 0);
+    }
+    T mm[AP_R];
+#pragma unroll
+    for (int k = 0; k < AP_R; ++k) {
+        const int z = z0 + k;
+        mm[k] = (xin && z < nz) ? __ldg(m2 + (size_t)z * nx + ix) : T(0);
+    }
+#pragma unroll
+    for (int k = 0; k < AP_R; ++k) {
+        const int z = z0 + k;
+        const cx<T> cur = v[k + 1];
+        cx<T> l(__shfl_up_sync(0xffffffffu, cur.re, 1), __shfl_up_sync(0xffffffffu, cur.im, 1));
+        cx<T> r(__shfl_down_sync(0xffffffffu, cur.re, 1), __shfl_down_sync(0xffffffffu, cur.im, 1));
+        if (z < nz && xin) {
+            const size_t i = (size_t)z * nx + ix;
+            if (lane == 0) l = ix > 0 ? ldc(ub, i - 1) : cx<T>(0, 0);
+            if (lane == AP_X - 1 || ix + 1 >= nx) r = ix + 1 < nx ? ldc(ub, i + 1) : cx<T>(0, 0);
+            const T s = hw * mm[k];
+            const T a = layer_alpha_t<T>(ix, z, nx, nz, npml, acoef);
+            cx<T> acc((T(4) - s) * cur.re - s * a * cur.im, (T(4) - s) * cur.im + s * a * cur.re);
+            acc = acc - l - r - v[k] - v[k + 2];
+            stc(yb, i, scale * acc);
+        }
+    }
 }
 
 template <typename T>
 void launch_apply(const LevelDev& L0, int npml, double amax, const T* hw, const T* u, T* y, T scale,
                   int nrhs, cudaStream_t s) {
-    dim3 blk(32, 8), grd((L0.nx + 31) / 32, (L0.nz + 7) / 8, nrhs);
+    dim3 blk(AP_X, AP_Y), grd((L0.nx + AP_X - 1) / AP_X, (L0.nz + AP_Y * AP_R - 1) / (AP_Y * AP_R), nrhs);
     k_apply<T><<<grd, blk, 0, s>>>(L0, npml, (T)layer_coef(npml, amax), hw, u, y, scale);
 }
 template void launch_apply<float>(const LevelDev&, int, double, const float*, const float*, float*, float, int, cudaStream_t);
@@ -245,7 +280,9 @@ void launch_bicg_init(const T* b, T* x, T* r, T* rh, T* p, T* v, double* partial
 // Residual replacement ("reliable update") between refinement steps: r is
 // replaced by the new true residual rin, x restarts from zero, and the Krylov
 // recurrence continues with the same shadow vector and search direction:
-// rho' = <rh, r>, beta = (rho' / rho_prev) (alpha / omega). A right-hand side
+// rho' = <rh, r>, beta = (rho' / rho) (alpha / omega), where rho, alpha and
+// omega are those of the last iteration (k_bicg_xr does not advance rho on the
+// iteration that retires a right-hand side). A right-hand side
 // whose last inner solve did not converge (breakdown or cap) restarts instead.
 template <typename T>
 __global__ void __launch_bounds__(256) k_bicg_resume(const T* __restrict__ rin, T* x, T* r, T* rh, T* p, T* v,
@@ -288,7 +325,7 @@ __global__ void __launch_bounds__(256) k_bicg_resume(const T* __restrict__ rin, 
                 S.omega[0] = 1.0; S.omega[1] = 0.0;
                 S.beta[0] = 0.0; S.beta[1] = 0.0;
             } else {
-                const double rr = S.rho_prev[0], ri = S.rho_prev[1], d1 = rr * rr + ri * ri;
+                const double rr = S.rho[0], ri = S.rho[1], d1 = rr * rr + ri * ri;
                 const double orr = S.omega[0], oi = S.omega[1], d2 = orr * orr + oi * oi;
                 if (d1 > 0.0 && d2 > 0.0) {
                     const double qr = (acc[0] * rr + acc[1] * ri) / d1, qi = (acc[1] * rr - acc[0] * ri) / d1;
@@ -404,7 +441,8 @@ __global__ void __launch_bounds__(256) k_bicg_xr(T* x, const T* __restrict__ ph,
             S.rnorm2 = acc[2];
             const double tl = S.tol_rel;
             int done = 0;
-            if (acc[2] <= tl * tl * S.bnorm2) { done = 1; S.flag = FLAG_CONVERGED; }
+            if (S.flag == FLAG_BREAKDOWN) done = 1;
+            else if (acc[2] <= tl * tl * S.bnorm2) { done = 1; S.flag = FLAG_CONVERGED; }
             else if (S.iters >= S.max_it) { done = 1; S.flag = FLAG_MAXIT; }
             else {
                 // beta = (rho_new / rho) * (alpha / omega)
@@ -419,8 +457,6 @@ __global__ void __launch_bounds__(256) k_bicg_xr(T* x, const T* __restrict__ ph,
                     double wr = (S.alpha[0] * orr + S.alpha[1] * oi) / d2, wi = (S.alpha[1] * orr - S.alpha[0] * oi) / d2;
                     S.beta[0] = qr * wr - qi * wi;
                     S.beta[1] = qr * wi + qi * wr;
-                    S.rho_prev[0] = S.rho[0];
-                    S.rho_prev[1] = S.rho[1];
                     S.rho[0] = acc[0];
                     S.rho[1] = acc[1];
                 }
@@ -435,6 +471,19 @@ void launch_bicg_xr(T* x, const T* ph, const T* shv, const T* sv, const T* t, co
                     int pstride, RhsState* st, int* nactive, size_t n, int nrhs, cudaStream_t s) {
     launch_pdl(k_bicg_xr<T>, dim3(grid1d(n), 1, nrhs), dim3(256), 0, s, x, ph, shv, sv, t, rh, r, partials, pstride, st,
                nactive, n);
+}
+
+// Bilinear prolongation along one axis at fine index g (coarse node I sits on
+// fine 2I+1): odd g takes coarse (g-1)/2 with weight 1, even g takes g/2-1 and
+// g/2 with weight 1/2 each. Branch-free: a = (g-1)>>1, b = g>>1 (arithmetic
+// shift, so g = 0 gives a = -1).
+template <typename T>
+__device__ __forceinline__ void bil_axis(int g, int& a, int& b, T& wa, T& wb) {
+    const bool odd = g & 1;
+    a = (g - 1) >> 1;
+    b = g >> 1;
+    wa = odd ? T(1) : T(0.5);
+    wb = odd ? T(0) : T(0.5);
 }
 
 // ===================================================== Galerkin operators
@@ -691,10 +740,8 @@ __global__ void __launch_bounds__(128) k_restrict_g(LevelDev Lf, LevelDev Lc, co
             if (CORRECT) {
                 int ia, ib, ka, kb;
                 T wa, wb, va, vb;
-                if (gx & 1) { ia = (gx - 1) / 2; ib = ia; wa = T(1); wb = T(0); }
-                else { ia = gx / 2 - 1; ib = gx / 2; wa = T(0.5); wb = T(0.5); }
-                if (gz & 1) { ka = (gz - 1) / 2; kb = ka; va = T(1); vb = T(0); }
-                else { ka = gz / 2 - 1; kb = gz / 2; va = T(0.5); vb = T(0.5); }
+                bil_axis<T>(gx, ia, ib, wa, wb);
+                bil_axis<T>(gz, ka, kb, va, vb);
                 ia -= I0 - 1; ib -= I0 - 1; ka -= K0 - 1; kb -= K0 - 1;
                 uv = uv + (va * wa) * E[ka][ia] + (va * wb) * E[ka][ib] + (vb * wa) * E[kb][ia] + (vb * wb) * E[kb][ib];
             }
@@ -763,10 +810,8 @@ __global__ void __launch_bounds__(256) k_prolong_g(LevelDev Lf, LevelDev Lc, con
             u = wj * cdiv(fv, C.c[0][lz][lx]);
             int ia, ib, ka, kb;
             T wa, wb, va, vb;
-            if (gx & 1) { ia = (gx - 1) / 2; ib = ia; wa = T(1); wb = T(0); }
-            else { ia = gx / 2 - 1; ib = gx / 2; wa = T(0.5); wb = T(0.5); }
-            if (gz & 1) { ka = (gz - 1) / 2; kb = ka; va = T(1); vb = T(0); }
-            else { ka = gz / 2 - 1; kb = gz / 2; va = T(0.5); vb = T(0.5); }
+            bil_axis<T>(gx, ia, ib, wa, wb);
+            bil_axis<T>(gz, ka, kb, va, vb);
             ia -= cx0; ib -= cx0; ka -= cz0; kb -= cz0;
             u = u + (va * wa) * E[ka][ia] + (va * wb) * E[ka][ib] + (vb * wa) * E[kb][ia] + (vb * wb) * E[kb][ib];
         }
@@ -931,10 +976,8 @@ __global__ void __launch_bounds__(256) k_prolong(LevelDev Lf, LevelDev Lc, int n
             // bilinear prolongation: odd fine index -> one coarse node, even -> two halves
             int ia, ib, ka, kb;
             T wa, wb, va, vb;
-            if (gx & 1) { ia = (gx - 1) / 2; ib = ia; wa = T(1); wb = T(0); }
-            else { ia = gx / 2 - 1; ib = gx / 2; wa = T(0.5); wb = T(0.5); }
-            if (gz & 1) { ka = (gz - 1) / 2; kb = ka; va = T(1); vb = T(0); }
-            else { ka = gz / 2 - 1; kb = gz / 2; va = T(0.5); vb = T(0.5); }
+            bil_axis<T>(gx, ia, ib, wa, wb);
+            bil_axis<T>(gz, ka, kb, va, vb);
             ia -= cx0; ib -= cx0; ka -= cz0; kb -= cz0;
             cx<T> pe = (va * wa) * E[ka][ia] + (va * wb) * E[ka][ib] + (vb * wa) * E[kb][ia] + (vb * wb) * E[kb][ib];
             u = u + pe;
@@ -1005,7 +1048,6 @@ __global__ void __launch_bounds__(256) k_prolong(LevelDev Lf, LevelDev Lc, int n
             }
         }
         if (MODE == 3) return;        // FGMRES: z and A z only
-        if (MODE == 3) return;        // FGMRES: z and A z only
         const T vv[3] = {d0, d1, d2};
         double acc[3];
         const int nblk = gridDim.x * gridDim.y, blk = blockIdx.y * gridDim.x + blockIdx.x;
@@ -1015,8 +1057,9 @@ __global__ void __launch_bounds__(256) k_prolong(LevelDev Lf, LevelDev Lc, int n
                 if (MODE == 1) {   // alpha = rho / <rh, v>
                     double dd = acc[0] * acc[0] + acc[1] * acc[1];
                     if (!(dd > 0.0)) {
+                        // stays active: the iteration finishes with alpha = 0 (a
+                        // minimal-residual step on r) and k_bicg_xr retires it
                         S.flag = FLAG_BREAKDOWN;
-                        S.active = 0;
                         S.alpha[0] = 0.0; S.alpha[1] = 0.0;
                     } else {
                         S.alpha[0] = (S.rho[0] * acc[0] + S.rho[1] * acc[1]) / dd;
@@ -1480,10 +1523,8 @@ __global__ void __launch_bounds__(256) k_correct_restrict(LevelDev Lf, LevelDev 
             uv = wj * cdiv(fv, op.diag(i));
             int ia, ib, ka, kb;
             T wa, wb, va, vb;
-            if (gx & 1) { ia = (gx - 1) / 2; ib = ia; wa = T(1); wb = T(0); }
-            else { ia = gx / 2 - 1; ib = gx / 2; wa = T(0.5); wb = T(0.5); }
-            if (gz & 1) { ka = (gz - 1) / 2; kb = ka; va = T(1); vb = T(0); }
-            else { ka = gz / 2 - 1; kb = gz / 2; va = T(0.5); vb = T(0.5); }
+            bil_axis<T>(gx, ia, ib, wa, wb);
+            bil_axis<T>(gz, ka, kb, va, vb);
             ia -= cx0; ib -= cx0; ka -= cz0; kb -= cz0;
             uv = uv + (va * wa) * E[ka][ia] + (va * wb) * E[ka][ib] + (vb * wa) * E[kb][ia] + (vb * wb) * E[kb][ib];
         }
