@@ -46,7 +46,7 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--krylov", default="bicgstab", choices=["bicgstab", "fgmres"])
     ap.add_argument("--restart", type=int, default=30, help="FGMRES restart length")
-    ap.add_argument("--inner-tol", type=float, default=1e-2, help="mixed precision: reduction per inner solve")
+    ap.add_argument("--inner-tol", type=float, default=1e-1, help="mixed precision: reduction per inner solve")
     ap.add_argument("--tune", action="store_true", help="autotune the multigrid tiles before timing")
     ap.add_argument("--workload", default="single", choices=["single", "batched", "serving"],
                     help="single: the single large case (the default line); batched: 64 shots x 5 "

@@ -115,21 +115,30 @@ __global__ void __launch_bounds__(256) k_fg_dots(const T* __restrict__ V, size_t
     __syncthreads();
     if (!s_last) return;
     __threadfence();
-    // the last block: every (chunk, value) summed over the x-blocks of its chunk in order
-    const int nx = gridDim.x, nchunk = gridDim.y;
+    // the last block: one warp per basis vector i <= j sums the partials of the
+    // x-blocks of its chunk, lane-strided then by a fixed shuffle tree (the order
+    // does not depend on timing, so the result is deterministic)
+    const int nx = gridDim.x;
     const size_t col = (size_t)b * (fg.m + 1);
-    for (int t = threadIdx.x; t < nchunk * kChunk; t += blockDim.x) {
-        const int c = t / kChunk, k = t % kChunk, i = c * kChunk + k;
-        if (i > j) continue;
+    for (int i = warp; i <= j; i += nw) {
+        const int c = i / kChunk, k = i % kChunk;
+        const double* pre = part + (size_t)(2 * k) * nblk + (size_t)c * nx;
+        const double* pim = part + (size_t)(2 * k + 1) * nblk + (size_t)c * nx;
         double re = 0.0, im = 0.0;
-        for (int x = 0; x < nx; ++x) {
-            const int bb = c * nx + x;
-            re += __ldcg(part + (size_t)(2 * k) * nblk + bb);
-            im += __ldcg(part + (size_t)(2 * k + 1) * nblk + bb);
+        for (int x = lane; x < nx; x += 32) {
+            re += __ldcg(pre + x);
+            im += __ldcg(pim + x);
         }
-        fg.tmp[col + i] = make_double2(re, im);
-        double2& h = fg.H[(col + i) * fg.m + j];
-        if (add) { h.x += re; h.y += im; } else { h = make_double2(re, im); }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            re += __shfl_xor_sync(0xffffffffu, re, o);
+            im += __shfl_xor_sync(0xffffffffu, im, o);
+        }
+        if (lane == 0) {
+            fg.tmp[col + i] = make_double2(re, im);
+            double2& h = fg.H[(col + i) * fg.m + j];
+            if (add) { h.x += re; h.y += im; } else { h = make_double2(re, im); }
+        }
     }
     if (threadIdx.x == 0) st[b].counter[2] = 0u;
 }
