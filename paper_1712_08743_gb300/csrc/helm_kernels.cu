@@ -112,17 +112,49 @@ __global__ void __launch_bounds__(AP_X * AP_Y) k_apply(LevelDev L, int npml, T a
     const T hw = hwv[b];
     const bool xin = ix < nx;
     const int lane = threadIdx.x;
+    // Blocks whose nodes and neighbours all lie inside the grid and outside the
+    // damping layer (alpha = 0) take a path without bounds tests or alpha.
+    const int bx0 = blockIdx.x * AP_X, bz0 = blockIdx.y * AP_Y * AP_R;
+    if (bx0 >= npml && bx0 + AP_X - 1 <= nx - 1 - npml && bz0 >= npml && bz0 + AP_Y * AP_R - 1 <= nz - 1 - npml &&
+        npml >= 1) {
+        cx<T> v[AP_R + 2], e[AP_R];
+        T mm[AP_R];
+        const bool edge = lane == 0 || lane == AP_X - 1;
+        const int ex = lane == 0 ? ix - 1 : ix + 1;
+#pragma unroll
+        for (int k = 0; k < AP_R + 2; ++k) v[k] = ldc(ub, (z0 - 1 + k) * nx + ix);
+#pragma unroll
+        for (int k = 0; k < AP_R; ++k) {
+            mm[k] = __ldg(m2 + (z0 + k) * nx + ix);
+            e[k] = edge ? ldc(ub, (z0 + k) * nx + ex) : cx<T>(0, 0);
+        }
+#pragma unroll
+        for (int k = 0; k < AP_R; ++k) {
+            const cx<T> cur = v[k + 1];
+            cx<T> l(__shfl_up_sync(0xffffffffu, cur.re, 1), __shfl_up_sync(0xffffffffu, cur.im, 1));
+            cx<T> r(__shfl_down_sync(0xffffffffu, cur.re, 1), __shfl_down_sync(0xffffffffu, cur.im, 1));
+            if (lane == 0) l = e[k];
+            if (lane == AP_X - 1) r = e[k];
+            const T dd = T(4) - hw * mm[k];
+            cx<T> acc(dd * cur.re, dd * cur.im);
+            acc = acc - ((l + r) + (v[k] + v[k + 2]));
+            stc(yb, (z0 + k) * nx + ix, scale * acc);
+        }
+        return;
+    }
+    // layer depth along x is fixed per thread; alpha = acoef max(dx, dz, 0)^2
+    const int dxd = max(npml - ix, ix - (nx - 1 - npml));
     cx<T> v[AP_R + 2];
 #pragma unroll
     for (int k = 0; k < AP_R + 2; ++k) {
         const int z = z0 - 1 + k;
-        v[k] = (xin && z >= 0 && z < nz) ? ldc(ub, (size_t)z * nx + ix) : cx<T>(0, 0);
+        v[k] = (xin && z >= 0 && z < nz) ? ldc(ub, z * nx + ix) : cx<T>(0, 0);
     }
     T mm[AP_R];
 #pragma unroll
     for (int k = 0; k < AP_R; ++k) {
         const int z = z0 + k;
-        mm[k] = (xin && z < nz) ? __ldg(m2 + (size_t)z * nx + ix) : T(0);
+        mm[k] = (xin && z < nz) ? __ldg(m2 + z * nx + ix) : T(0);
     }
 #pragma unroll
     for (int k = 0; k < AP_R; ++k) {
@@ -131,13 +163,16 @@ __global__ void __launch_bounds__(AP_X * AP_Y) k_apply(LevelDev L, int npml, T a
         cx<T> l(__shfl_up_sync(0xffffffffu, cur.re, 1), __shfl_up_sync(0xffffffffu, cur.im, 1));
         cx<T> r(__shfl_down_sync(0xffffffffu, cur.re, 1), __shfl_down_sync(0xffffffffu, cur.im, 1));
         if (z < nz && xin) {
-            const size_t i = (size_t)z * nx + ix;
+            const int i = z * nx + ix;
             if (lane == 0) l = ix > 0 ? ldc(ub, i - 1) : cx<T>(0, 0);
-            if (lane == AP_X - 1 || ix + 1 >= nx) r = ix + 1 < nx ? ldc(ub, i + 1) : cx<T>(0, 0);
+            if (lane == AP_X - 1) r = ix + 1 < nx ? ldc(ub, i + 1) : cx<T>(0, 0);
+            else if (ix + 1 >= nx) r = cx<T>(0, 0);
+            const int d = max(max(dxd, max(npml - z, z - (nz - 1 - npml))), 0);
             const T s = hw * mm[k];
-            const T a = layer_alpha_t<T>(ix, z, nx, nz, npml, acoef);
-            cx<T> acc((T(4) - s) * cur.re - s * a * cur.im, (T(4) - s) * cur.im + s * a * cur.re);
-            acc = acc - l - r - v[k] - v[k + 2];
+            const T sa = s * (acoef * (T)(d * d));
+            const T dd = T(4) - s;
+            cx<T> acc(dd * cur.re - sa * cur.im, dd * cur.im + sa * cur.re);
+            acc = acc - ((l + r) + (v[k] + v[k + 2]));
             stc(yb, i, scale * acc);
         }
     }
@@ -835,68 +870,144 @@ __global__ void __launch_bounds__(256) k_prolong_g(LevelDev Lf, LevelDev Lc, con
 
 // ======================================================== V-cycle: restrict
 // From a level-l right-hand side f (zero initial guess): one damped-Jacobi
-// sweep u1 = wj D^-1 f, residual r = f - M u1, and the restriction P^T r to
+// sweep u1 = wj D^-1 f, residual r = f - M u1 and the restriction P^T r to
 // level l + 1 (full weighting times 4: (1/4) [1 2 1; 2 4 2; 1 2 1] * r).
 constexpr int RCX = 32, RCZ = 8;                    // coarse tile per block
 constexpr int RFW = 2 * RCX + 3, RFH = 2 * RCZ + 3; // fine region (u1) per block
 
-template <typename T, bool GAL>
+// Shuffles of a complex value from the lane below / above.
+template <typename T> __device__ __forceinline__ cx<T> sh_up(cx<T> a) {
+    return cx<T>(__shfl_up_sync(0xffffffffu, a.re, 1), __shfl_up_sync(0xffffffffu, a.im, 1));
+}
+template <typename T> __device__ __forceinline__ cx<T> sh_dn(cx<T> a) {
+    return cx<T>(__shfl_down_sync(0xffffffffu, a.re, 1), __shfl_down_sync(0xffffffffu, a.im, 1));
+}
+
+// Finest level. M = D - N there (D = 4 - (h omega m)^2 (b1 - j b2), N the sum of
+// the four neighbours), so r = f - D u1 + N u1 = (1 - wj) f + N u1: one complex
+// reciprocal per node and no complex product in the residual.
+// Column marching, no shared memory: lane j of a warp owns the fine columns
+// 2I and 2I + 1 of coarse column I = I0 + j (the odd one is the coarse node's
+// centre); lanes 1..30 write their coarse column, so warps step by 30 coarse
+// columns. The warp walks down the fine rows of `ks` coarse rows two at a time,
+// holding u1 of three rows in registers and loading two rows ahead; the
+// neighbour columns across a lane boundary come by shuffle. r is zero outside
+// the grid.
+constexpr int RM_COLS = 30;   // coarse columns per warp
+
+// The marching loop; EDGE = false when every row and column the warp touches
+// lies inside the grid, so no bounds test is needed.
+template <typename T, bool EDGE>
+__device__ __forceinline__ void restrict_march(int nx, int nz, int cnx, int c0, int I, int lane, int K0, int K1,
+                                               const T* __restrict__ fb, const T* __restrict__ m2, T sb1, T sb2,
+                                               T wj, T* __restrict__ fcb) {
+    const T omw = T(1) - wj;
+    const bool in0 = !EDGE || (c0 >= 0 && c0 < nx), in1 = !EDGE || (c0 + 1 >= 0 && c0 + 1 < nx);
+    struct Row { cx<T> f0, f1; T m0, m1; };
+    auto ld = [&](int z) -> Row {
+        Row r;
+        const bool zin = !EDGE || (z >= 0 && z < nz);
+        const int i = z * nx + c0;
+        r.f0 = (zin && in0) ? ldc(fb, i) : cx<T>(0, 0);
+        r.f1 = (zin && in1) ? ldc(fb, i + 1) : cx<T>(0, 0);
+        r.m0 = (zin && in0) ? __ldg(m2 + i) : T(0);
+        r.m1 = (zin && in1) ? __ldg(m2 + i + 1) : T(0);
+        return r;
+    };
+    auto u1of = [&](cx<T> fv, T mv) -> cx<T> {   // wj D^-1 f (zero where f is)
+        const T dr = T(4) - sb1 * mv, di = sb2 * mv;
+        const T sc = wj * rcp_fast(dr * dr + di * di);
+        return cx<T>(sc * (fv.re * dr + fv.im * di), sc * (fv.im * dr - fv.re * di));
+    };
+    // r of row z at both columns from u1 of rows z-1 (a), z (c), z+1 (d); x
+    // neighbours: u1 at c0 - 1 is the lower lane's odd column, at c0 + 2 the
+    // upper lane's even column
+    auto resid = [&](int z, const Row& rz, cx<T> a0, cx<T> a1, cx<T> c0v, cx<T> c1v, cx<T> d0v, cx<T> d1v,
+                     cx<T>& r0, cx<T>& r1) {
+        const cx<T> wl = sh_up(c1v), er = sh_dn(c0v);
+        r0 = omw * rz.f0 + (a0 + d0v) + (wl + c1v);
+        r1 = omw * rz.f1 + (a1 + d1v) + (c0v + er);
+        if (EDGE) {
+            const bool zin = z < nz;
+            if (!(zin && in0)) r0 = cx<T>(0, 0);
+            if (!(zin && in1)) r1 = cx<T>(0, 0);
+        }
+    };
+    // horizontal full weighting at the centre column: r(2I) + 2 r(2I+1) + r(2I+2)
+    auto hsum = [&](cx<T> r0, cx<T> r1) -> cx<T> { return (r0 + sh_dn(r0)) + T(2) * r1; };
+    const bool wr = lane >= 1 && lane <= RM_COLS && I < cnx;
+
+    Row A = ld(2 * K0 - 1), B = ld(2 * K0), C = ld(2 * K0 + 1), D = ld(2 * K0 + 2);
+    cx<T> ua0 = u1of(A.f0, A.m0), ua1 = u1of(A.f1, A.m1);   // u1 of row 2K-1
+    cx<T> ub0 = u1of(B.f0, B.m0), ub1 = u1of(B.f1, B.m1);   // u1 of row 2K
+    cx<T> acc(0, 0);
+    for (int K = K0; K < K1; ++K) {
+        // held: u1 of rows 2K-1, 2K, f of row 2K (B); raw rows 2K+1 (C), 2K+2 (D)
+        const Row E = ld(2 * K + 3), F = ld(2 * K + 4);
+        const cx<T> uc0 = u1of(C.f0, C.m0), uc1 = u1of(C.f1, C.m1);
+        const cx<T> ud0 = u1of(D.f0, D.m0), ud1 = u1of(D.f1, D.m1);
+        cx<T> r0, r1, s0, s1;
+        resid(2 * K, B, ua0, ua1, ub0, ub1, uc0, uc1, r0, r1);
+        resid(2 * K + 1, C, ub0, ub1, uc0, uc1, ud0, ud1, s0, s1);
+        const cx<T> h0 = hsum(r0, r1), h1 = hsum(s0, s1);
+        if (K > K0) {
+            acc = acc + h0;   // completes coarse row K - 1
+            if (wr) stc(fcb, (size_t)(K - 1) * cnx + I, T(0.25) * acc);
+        }
+        acc = h0 + T(2) * h1;
+        ua0 = uc0; ua1 = uc1; ub0 = ud0; ub1 = ud1;
+        B = D; C = E; D = F;
+    }
+    cx<T> r0, r1;
+    resid(2 * K1, B, ua0, ua1, ub0, ub1, u1of(C.f0, C.m0), u1of(C.f1, C.m1), r0, r1);
+    acc = acc + hsum(r0, r1);
+    if (wr) stc(fcb, (size_t)(K1 - 1) * cnx + I, T(0.25) * acc);
+}
+
+template <typename T>
 __global__ void __launch_bounds__(256) k_restrict(LevelDev Lf, LevelDev Lc, const T* __restrict__ w2, T b1, T b2,
                                                   T wj, const T* __restrict__ f, T* __restrict__ fc,
-                                                  const RhsState* st) {
-    __shared__ cx<T> F[RFH][RFW];
-    __shared__ cx<T> U[RFH][RFW];
+                                                  const RhsState* st, int ks) {
     pdl_trigger();
     pdl_wait();
     const int b = blockIdx.z;
     if (!rhs_active(st, b)) return;
-    const int I0 = blockIdx.x * RCX, K0 = blockIdx.y * RCZ;
-    const int gx0 = 2 * I0 - 1, gz0 = 2 * K0 - 1;
-    LevelOp<T, GAL> op = level_op<T, GAL>(Lf, b, w2[b]);
-    op.b1 = b1;
-    op.b2 = b2;
-    const size_t nf = (size_t)Lf.nx * Lf.nz;
+    const int lane = threadIdx.x & 31;
+    const int Ib = (blockIdx.x * 8 + (threadIdx.x >> 5)) * RM_COLS - 1;   // coarse column of lane 0
+    if (Ib + 1 >= Lc.nx) return;   // uniform in the warp; the kernel has no block barrier
+    const int nx = Lf.nx, nz = Lf.nz;
+    const int I = Ib + lane;
+    const int K0 = blockIdx.y * ks, K1 = min(K0 + ks, Lc.nz);
+    const size_t nf = (size_t)nx * nz;
     const T* fb = f + 2 * nf * b;
-    for (int idx = threadIdx.x; idx < RFW * RFH; idx += blockDim.x) {
-        const int lz = idx / RFW, lx = idx - lz * RFW;
-        const int gx = gx0 + lx, gz = gz0 + lz;
-        cx<T> fv(0, 0), uv(0, 0);
-        if (gx >= 0 && gx < Lf.nx && gz >= 0 && gz < Lf.nz) {
-            const size_t i = (size_t)gz * Lf.nx + gx;
-            fv = ldc(fb, i);
-            uv = wj * cdiv(fv, op.diag(i));
-        }
-        F[lz][lx] = fv;
-        U[lz][lx] = uv;
-    }
-    __syncthreads();
-    constexpr int W2 = RFW - 2, H2 = RFH - 2;
-    for (int idx = threadIdx.x; idx < W2 * H2; idx += blockDim.x) {
-        const int lz = 1 + idx / W2, lx = 1 + idx % W2;
-        const int gx = gx0 + lx, gz = gz0 + lz;
-        cx<T> r(0, 0);
-        if (gx < Lf.nx && gz < Lf.nz) r = F[lz][lx] - op.apply(gx, gz, &U[lz][lx], RFW);   // gx, gz >= 0 here
-        F[lz][lx] = r;   // each element read and written by this thread only
-    }
-    __syncthreads();
-    const int cxl = threadIdx.x % RCX, czl = threadIdx.x / RCX;
-    const int I = I0 + cxl, K = K0 + czl;
-    if (I < Lc.nx && K < Lc.nz) {
-        const int lx = 2 * cxl + 2, lz = 2 * czl + 2;
-        cx<T> a = T(4) * F[lz][lx];
-        a = a + T(2) * (F[lz][lx - 1] + F[lz][lx + 1] + F[lz - 1][lx] + F[lz + 1][lx]);
-        a = a + F[lz - 1][lx - 1] + F[lz - 1][lx + 1] + F[lz + 1][lx - 1] + F[lz + 1][lx + 1];
-        const size_t nc = (size_t)Lc.nx * Lc.nz;
-        stc(fc + 2 * nc * b, (size_t)K * Lc.nx + I, T(0.25) * a);
-    }
+    const T* m2 = static_cast<const T*>(Lf.m2) + (size_t)b * Lf.mstride;
+    const T hw = w2[b];
+    T* fcb = fc + 2 * ((size_t)Lc.nx * Lc.nz) * b;
+    // fine columns 2 Ib .. 2 Ib + 63 and rows 2 K0 - 1 .. 2 K1 + 2 inside the grid?
+    const bool edge = Ib < 0 || 2 * Ib + 63 >= nx || K0 == 0 || 2 * K1 + 2 >= nz;
+    if (edge)
+        restrict_march<T, true>(nx, nz, Lc.nx, 2 * I, I, lane, K0, K1, fb, m2, hw * b1, hw * b2, wj, fcb);
+    else
+        restrict_march<T, false>(nx, nz, Lc.nx, 2 * I, I, lane, K0, K1, fb, m2, hw * b1, hw * b2, wj, fcb);
+}
+
+// Rows per block of the marching kernels: long segments amortise the rows
+// recomputed at segment ends; short ones give enough warps when the batch is
+// small (aim: 32 warps per SM on 152 SMs).
+inline int march_rows(int col_warps, int rows, int nrhs, int longest) {
+    int zs = longest;
+    while (zs > 4 && (size_t)col_warps * ((rows + zs - 1) / zs) * nrhs < 152u * 32u) zs /= 2;
+    return zs;
 }
 
 template <typename T>
 void launch_restrict(const LevelDev& Lf, const LevelDev& Lc, const T* w2, double b1, double b2, double wj,
                      const T* f, T* fc, const RhsState* st, int nrhs, cudaStream_t s, int tile) {
     if (Lf.m2) {
-        dim3 grd((Lc.nx + RCX - 1) / RCX, (Lc.nz + RCZ - 1) / RCZ, nrhs);
-        launch_pdl(k_restrict<T, false>, grd, dim3(RCX * RCZ), 0, s, Lf, Lc, w2, (T)b1, (T)b2, (T)wj, f, fc, st);
+        const int cw = (Lc.nx + RM_COLS - 1) / RM_COLS;
+        const int ks = march_rows(cw, Lc.nz, nrhs, 16);
+        dim3 grd((cw + 7) / 8, (Lc.nz + ks - 1) / ks, nrhs);
+        launch_pdl(k_restrict<T>, grd, dim3(256), 0, s, Lf, Lc, w2, (T)b1, (T)b2, (T)wj, f, fc, st, ks);
     } else if (sizeof(T) == 4 && tile == 0) {
         constexpr int GRCX = 8, GRCZ = GTile<T>::RCZ;
         dim3 grd((Lc.nx + GRCX - 1) / GRCX, (Lc.nz + GRCZ - 1) / GRCZ, nrhs);
@@ -911,143 +1022,210 @@ void launch_restrict(const LevelDev& Lf, const LevelDev& Lc, const T* w2, double
 }
 
 // ========================================================= V-cycle: prolong
-// Finest level, on a tile: u1 = wj D^-1 f, u2 = u1 + P e (bilinear), one
-// post-sweep u3 = u2 + wj D^-1 (f - M u2). Mode 0 writes u3 (optionally
-// accumulating); modes 1 and 2 (inside BiCGSTAB) also apply A to u3 and reduce
-// the dot products the next scalar needs; mode 3 (FGMRES) applies A without
-// dots. The inverse diagonal wj D^-1 is computed once per node into shared
-// memory; the row loops use a 2D thread layout (no per-element division).
-// fine tile per block: 64 x 16 in FP32, 32 x 16 in FP64 (static shared memory < 48 KB)
-template <typename T> struct PTile { static constexpr int X = sizeof(T) == 4 ? 64 : 32, Z = 16; };
+// Finest level: u1 = wj D^-1 f, u2 = u1 + P e (bilinear), one post-sweep
+// u3 = u2 + wj D^-1 (f - M u2). With M = D - N on this level the sweep is
+// u3 = (1 - wj) u2 + (wj D^-1) (f + N u2): one complex reciprocal per node and
+// no complex product of M. Mode 0 writes u3 (optionally accumulating); modes 1
+// and 2 (inside BiCGSTAB) also apply A to u3 and reduce the dot products the
+// next scalar needs; mode 3 (FGMRES) applies A without dots.
+// Column marching, no shared memory for the fields: lane j of a warp owns the
+// fine columns 2J and 2J + 1 of coarse column J = Jb + j (2J + 1 is the coarse
+// node's column, so the bilinear weights are fixed per column); lanes 1..30
+// write, so warps step by 60 fine columns. The warp walks down `zs` fine rows
+// two at a time (u2 of rows 2K, 2K+1; u3 of rows 2K-1, 2K; outputs of rows
+// 2K-2, 2K-1), holding the rows it still needs in registers and loading two
+// rows ahead; neighbours across a lane boundary come by shuffle.
+constexpr int PM_COLS = 60;   // fine output columns per warp
 
-template <typename T, int MODE, int PFZ>
-__global__ void __launch_bounds__(256) k_prolong(LevelDev Lf, LevelDev Lc, int npml, T acoef,
+template <typename T, int MODE, bool EDGE>
+__device__ __forceinline__ void prolong_march(int nx, int nz, int cnx, int cnz, int J, int lane, int Z0, int Z1,
+                                              int npml, T acoef, T hw, T b1, T b2, T wj, const T* __restrict__ fb,
+                                              const T* __restrict__ eb, const T* __restrict__ ab,
+                                              const T* __restrict__ m2, T* __restrict__ ob, T* __restrict__ yb,
+                                              int accumulate, T& d0, T& d1, T& d2) {
+    const int c0 = 2 * J;
+    const bool in0 = !EDGE || (c0 >= 0 && c0 < nx), in1 = !EDGE || (c0 + 1 >= 0 && c0 + 1 < nx);
+    const bool ein = !EDGE || (J >= 0 && J < cnx);
+    const bool outl = lane >= 1 && lane <= PM_COLS / 2;
+    const T sb1 = hw * b1, sb2 = hw * b2, omw = T(1) - wj;
+    struct Row { cx<T> f0, f1; T m0, m1; };
+    auto ld = [&](int z) -> Row {
+        Row r;
+        const bool zin = !EDGE || (z >= 0 && z < nz);
+        const int i = z * nx + c0;
+        r.f0 = (zin && in0) ? ldc(fb, i) : cx<T>(0, 0);
+        r.f1 = (zin && in1) ? ldc(fb, i + 1) : cx<T>(0, 0);
+        r.m0 = (zin && in0) ? __ldg(m2 + i) : T(0);
+        r.m1 = (zin && in1) ? __ldg(m2 + i + 1) : T(0);
+        return r;
+    };
+    // e(K, J); lane 0 also reads e(K, J - 1), which the other lanes take from
+    // the lane below
+    struct ERow { cx<T> e, w; };
+    const bool wlo = lane == 0 && (!EDGE || (J - 1 >= 0 && J - 1 < cnx));
+    auto erow = [&](int K) -> ERow {
+        ERow r;
+        const bool kin = !EDGE || (K >= 0 && K < cnz);
+        r.e = (ein && kin) ? ldc(eb, (size_t)K * cnx + J) : cx<T>(0, 0);
+        r.w = (wlo && kin) ? ldc(eb, (size_t)K * cnx + J - 1) : cx<T>(0, 0);
+        return r;
+    };
+    auto dinv = [&](T mv) -> cx<T> {   // wj D^-1
+        const T dr = T(4) - sb1 * mv, di = sb2 * mv;
+        const T sc = wj * rcp_fast(dr * dr + di * di);
+        return cx<T>(sc * dr, -sc * di);
+    };
+    // u2 of row z at both columns; ev = e(K, J) of the coarse rows above and
+    // below (equal for odd z): column 2J + 1 takes e(J), column 2J the mean of
+    // e(J - 1) (lower lane) and e(J)
+    auto u2row = [&](int z, const Row& r, const ERow& ea, const ERow& ec2, cx<T>& p0, cx<T>& p1) {
+        const cx<T> ev = T(0.5) * (ea.e + ec2.e);
+        const cx<T> up = sh_up(ev);
+        const cx<T> left = lane == 0 ? T(0.5) * (ea.w + ec2.w) : up;
+        const cx<T> pe0 = T(0.5) * (left + ev);
+        p0 = dinv(r.m0) * r.f0 + pe0;
+        p1 = dinv(r.m1) * r.f1 + ev;
+        if (EDGE) {
+            const bool zin = z >= 0 && z < nz;
+            if (!(zin && in0)) p0 = cx<T>(0, 0);
+            if (!(zin && in1)) p1 = cx<T>(0, 0);
+        }
+    };
+    // u3 of row z from u2 of rows z-1 (a), z (c), z+1 (d)
+    auto u3row = [&](int z, const Row& r, cx<T> a0, cx<T> a1, cx<T> c0v, cx<T> c1v, cx<T> d0v, cx<T> d1v,
+                     cx<T>& q0, cx<T>& q1) {
+        const cx<T> wl = sh_up(c1v), er = sh_dn(c0v);
+        q0 = omw * c0v + dinv(r.m0) * (r.f0 + ((wl + c1v) + (a0 + d0v)));
+        q1 = omw * c1v + dinv(r.m1) * (r.f1 + ((c0v + er) + (a1 + d1v)));
+        if (EDGE) {
+            const bool zin = z >= 0 && z < nz;
+            if (!(zin && in0)) q0 = cx<T>(0, 0);
+            if (!(zin && in1)) q1 = cx<T>(0, 0);
+        }
+    };
+    // y = A u3 at row z (fine operator with damping) from u3 of rows z-1, z, z+1
+    const int dx0 = max(npml - c0, c0 - (nx - 1 - npml)), dx1 = max(npml - c0 - 1, c0 + 1 - (nx - 1 - npml));
+    auto arow = [&](int z, const Row& r, cx<T> a0, cx<T> a1, cx<T> c0v, cx<T> c1v, cx<T> d0v, cx<T> d1v,
+                    cx<T>& y0, cx<T>& y1) {
+        const cx<T> wl = sh_up(c1v), er = sh_dn(c0v);
+        const int dz = max(npml - z, z - (nz - 1 - npml));
+        const int e0 = max(max(dx0, dz), 0), e1 = max(max(dx1, dz), 0);
+        const T s0 = hw * r.m0, s1 = hw * r.m1;
+        const T a0s = s0 * (acoef * (T)(e0 * e0)), a1s = s1 * (acoef * (T)(e1 * e1));
+        const T g0 = T(4) - s0, g1 = T(4) - s1;
+        y0 = cx<T>(g0 * c0v.re - a0s * c0v.im, g0 * c0v.im + a0s * c0v.re) - ((wl + c1v) + (a0 + d0v));
+        y1 = cx<T>(g1 * c1v.re - a1s * c1v.im, g1 * c1v.im + a1s * c1v.re) - ((c0v + er) + (a1 + d1v));
+    };
+    auto lda = [&](int z, cx<T>& q0, cx<T>& q1) {
+        const bool ok = outl && z >= Z0 && z < Z1;
+        const int i = z * nx + c0;
+        q0 = (ok && in0) ? ldc(ab, i) : cx<T>(0, 0);
+        q1 = (ok && in1) ? ldc(ab, i + 1) : cx<T>(0, 0);
+    };
+
+    const int Ks = Z0 / 2 - 1, Ke = (Z1 + 1) / 2;   // Z0 is even
+    // state at the top of iteration K: u2 of rows 2K-2 (pa), 2K-1 (pb); u3 of
+    // rows 2K-3 (qa), 2K-2 (qb); the rows 2K-2 (RA), 2K-1 (RB) and the raw rows
+    // 2K (RC), 2K+1 (RD); e(K-1, J) (elo) and e(K, J) (ehi)
+    cx<T> pa0(0, 0), pa1(0, 0), pb0(0, 0), pb1(0, 0), qa0(0, 0), qa1(0, 0), qb0(0, 0), qb1(0, 0);
+    Row RA, RB;
+    RA.f0 = RA.f1 = RB.f0 = RB.f1 = cx<T>(0, 0);
+    RA.m0 = RA.m1 = RB.m0 = RB.m1 = T(0);
+    Row RC = ld(2 * Ks), RD = ld(2 * Ks + 1);
+    ERow elo = erow(Ks - 1), ehi = erow(Ks);
+    cx<T> qr0(0, 0), qr1(0, 0), qs0(0, 0), qs1(0, 0);   // mode 1: shadow residual of the output rows
+    if constexpr (MODE == 1) { lda(2 * Ks - 2, qr0, qr1); lda(2 * Ks - 1, qs0, qs1); }
+    for (int K = Ks; K <= Ke; ++K) {
+        const Row RE = ld(2 * K + 2), RF = ld(2 * K + 3);
+        const ERow enx = erow(K + 1);
+        cx<T> qn0(0, 0), qn1(0, 0), qm0(0, 0), qm1(0, 0);
+        if constexpr (MODE == 1) { lda(2 * K, qn0, qn1); lda(2 * K + 1, qm0, qm1); }
+        cx<T> pc0, pc1, pd0, pd1, qc0, qc1, qd0, qd1;
+        u2row(2 * K, RC, elo, ehi, pc0, pc1);       // even row: mean of e(K-1), e(K)
+        u2row(2 * K + 1, RD, ehi, ehi, pd0, pd1);   // odd row: e(K)
+        u3row(2 * K - 1, RB, pa0, pa1, pb0, pb1, pc0, pc1, qc0, qc1);
+        u3row(2 * K, RC, pb0, pb1, pc0, pc1, pd0, pd1, qd0, qd1);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int z = 2 * K - 2 + h;
+            const cx<T> c0v = h ? qc0 : qb0, c1v = h ? qc1 : qb1;
+            const bool wr = outl && z >= Z0 && z < Z1;
+            const int i = z * nx + c0;
+            if constexpr (MODE == 0) {
+                if (wr) {
+                    if (in0) stc(ob, i, accumulate ? ldcc(ob, i) + c0v : c0v);
+                    if (in1) stc(ob, i + 1, accumulate ? ldcc(ob, i + 1) + c1v : c1v);
+                }
+            } else {
+                cx<T> y0, y1;
+                if (h) arow(z, RB, qb0, qb1, qc0, qc1, qd0, qd1, y0, y1);
+                else arow(z, RA, qa0, qa1, qb0, qb1, qc0, qc1, y0, y1);
+                if (wr) {
+                    if (in0) { stc(ob, i, c0v); stc(yb, i, y0); }
+                    if (in1) { stc(ob, i + 1, c1v); stc(yb, i + 1, y1); }
+                    if (!in0) y0 = cx<T>(0, 0);
+                    if (!in1) y1 = cx<T>(0, 0);
+                    if constexpr (MODE == 1) {          // <rh, v>
+                        const cx<T> q0 = h ? qs0 : qr0, q1 = h ? qs1 : qr1;
+                        d0 += (q0.re * y0.re + q0.im * y0.im) + (q1.re * y1.re + q1.im * y1.im);
+                        d1 += (q0.re * y0.im - q0.im * y0.re) + (q1.re * y1.im - q1.im * y1.re);
+                    } else if constexpr (MODE == 2) {   // <t, s>, <t, t> with s = f
+                        const Row& R = h ? RB : RA;
+                        d0 += (y0.re * R.f0.re + y0.im * R.f0.im) + (y1.re * R.f1.re + y1.im * R.f1.im);
+                        d1 += (y0.re * R.f0.im - y0.im * R.f0.re) + (y1.re * R.f1.im - y1.im * R.f1.re);
+                        d2 += (y0.re * y0.re + y0.im * y0.im) + (y1.re * y1.re + y1.im * y1.im);
+                    }
+                }
+            }
+        }
+        pa0 = pc0; pa1 = pc1; pb0 = pd0; pb1 = pd1;
+        qa0 = qc0; qa1 = qc1; qb0 = qd0; qb1 = qd1;
+        RA = RC; RB = RD; RC = RE; RD = RF;
+        elo = ehi; ehi = enx;
+        qr0 = qn0; qr1 = qn1; qs0 = qm0; qs1 = qm1;
+    }
+}
+
+constexpr int PM_WARPS = 4;   // warps per block of the marching prolongation
+
+template <typename T, int MODE>
+__global__ void __launch_bounds__(32 * PM_WARPS) k_prolong(LevelDev Lf, LevelDev Lc, int npml, T acoef,
                                                  const T* __restrict__ w2, T b1, T b2, T wj,
                                                  const T* __restrict__ f, const T* __restrict__ ec,
                                                  T* __restrict__ out, T* __restrict__ y, const T* __restrict__ aux,
-                                                 double* partials, int pstride, RhsState* st, int accumulate) {
-    constexpr int H = (MODE == 0) ? 1 : 2;
-    constexpr int PFX = PTile<T>::X;
-    constexpr int RW = PFX + 2 * H, RH = PFZ + 2 * H;          // f, u2 region
-    constexpr int EW = PFX / 2 + H + 1, EH = PFZ / 2 + H + 1;  // coarse region
-    constexpr int SW = PFX + 2, SH = PFZ + 2;                  // u3 region (modes 1, 2)
-    __shared__ cx<T> F[RH][RW];
-    __shared__ cx<T> U2[RH][RW];
-    __shared__ cx<T> E[EH][EW];
-    __shared__ cx<T> U3[(MODE == 0) ? 1 : SH][(MODE == 0) ? 1 : SW];
+                                                 double* partials, int pstride, RhsState* st, int accumulate, int zs) {
     __shared__ double shred[96];
-
     pdl_trigger();
     pdl_wait();
     const int b = blockIdx.z;
-    if (!rhs_active(st, b)) return;
-    const int x0 = blockIdx.x * PFX, z0 = blockIdx.y * PFZ;
-    const int gx0 = x0 - H, gz0 = z0 - H;
-    const int cx0 = x0 / 2 - H, cz0 = z0 / 2 - H;
-    LevelOp<T, false> op = level_op<T, false>(Lf, b, w2[b]);
-    op.b1 = b1;
-    op.b2 = b2;
-    const size_t nf = (size_t)Lf.nx * Lf.nz, nc = (size_t)Lc.nx * Lc.nz;
+    if (!rhs_active(st, b)) return;   // uniform in the block
+    const int lane = threadIdx.x & 31;
+    const int nx = Lf.nx, nz = Lf.nz, cnx = Lc.nx, cnz = Lc.nz;
+    const int Jb = (blockIdx.x * PM_WARPS + (threadIdx.x >> 5)) * (PM_COLS / 2) - 1;   // coarse column of lane 0
+    const int Z0 = blockIdx.y * zs, Z1 = min(Z0 + zs, nz);
+    const size_t nf = (size_t)nx * nz, nc = (size_t)cnx * cnz;
     const T* fb = f + 2 * nf * b;
     const T* eb = ec + 2 * nc * b;
-
-    for (int idx = threadIdx.x; idx < EW * EH; idx += blockDim.x) {
-        const int lz = idx / EW, lx = idx - lz * EW;
-        const int I = cx0 + lx, K = cz0 + lz;
-        cx<T> e(0, 0);
-        if (I >= 0 && I < Lc.nx && K >= 0 && K < Lc.nz) e = ldc(eb, (size_t)K * Lc.nx + I);
-        E[lz][lx] = e;
+    const T* ab = aux + 2 * nf * b;
+    const T* m2 = static_cast<const T*>(Lf.m2) + (size_t)b * Lf.mstride;
+    T* ob = out + 2 * nf * b;
+    T* yb = y + 2 * nf * b;
+    const T hw = w2[b];
+    T d0 = 0, d1 = 0, d2 = 0;
+    if (2 * (Jb + 1) < nx) {   // the warp has output columns (uniform in the warp)
+        // fine columns 2 Jb .. 2 Jb + 63, coarse columns Jb .. Jb + 31 and rows
+        // Z0 - 4 .. Z1 + 3 (coarse rows Z0/2 - 2 .. Z1/2 + 2) inside the grid?
+        const bool edge = Jb < 0 || 2 * Jb + 63 >= nx || Jb + 31 >= cnx || Z0 < 4 || Z1 + 3 >= nz ||
+                          Z0 / 2 - 2 < 0 || Z1 / 2 + 2 >= cnz;
+        if (edge)
+            prolong_march<T, MODE, true>(nx, nz, cnx, cnz, Jb + lane, lane, Z0, Z1, npml, acoef, hw, b1, b2, wj, fb,
+                                         eb, ab, m2, ob, yb, accumulate, d0, d1, d2);
+        else
+            prolong_march<T, MODE, false>(nx, nz, cnx, cnz, Jb + lane, lane, Z0, Z1, npml, acoef, hw, b1, b2, wj, fb,
+                                          eb, ab, m2, ob, yb, accumulate, d0, d1, d2);
     }
-    for (int idx = threadIdx.x; idx < RW * RH; idx += blockDim.x) {
-        const int lz = idx / RW, lx = idx - lz * RW;
-        const int gx = gx0 + lx, gz = gz0 + lz;
-        cx<T> fv(0, 0);
-        if (gx >= 0 && gx < Lf.nx && gz >= 0 && gz < Lf.nz) fv = ldc(fb, (size_t)gz * Lf.nx + gx);
-        F[lz][lx] = fv;
-    }
-    __syncthreads();
-    // u2 = wj D^-1 f + P e on the region (zero outside the grid)
-    for (int idx = threadIdx.x; idx < RW * RH; idx += blockDim.x) {
-        const int lz = idx / RW, lx = idx - lz * RW;
-        const int gx = gx0 + lx, gz = gz0 + lz;
-        cx<T> u(0, 0);
-        if (gx >= 0 && gx < Lf.nx && gz >= 0 && gz < Lf.nz) {
-            u = wj * cdiv(F[lz][lx], op.diag((size_t)gz * Lf.nx + gx));
-            // bilinear prolongation: odd fine index -> one coarse node, even -> two halves
-            int ia, ib, ka, kb;
-            T wa, wb, va, vb;
-            bil_axis<T>(gx, ia, ib, wa, wb);
-            bil_axis<T>(gz, ka, kb, va, vb);
-            ia -= cx0; ib -= cx0; ka -= cz0; kb -= cz0;
-            cx<T> pe = (va * wa) * E[ka][ia] + (va * wb) * E[ka][ib] + (vb * wa) * E[kb][ia] + (vb * wb) * E[kb][ib];
-            u = u + pe;
-        }
-        U2[lz][lx] = u;
-    }
-    __syncthreads();
-
-    if (MODE == 0) {
-        // post-smooth on the tile, write the correction
-        T* ob = out + 2 * nf * b;
-        for (int idx = threadIdx.x; idx < PFX * PFZ; idx += blockDim.x) {
-            const int tz = idx / PFX, tx = idx - tz * PFX;
-            const int gx = x0 + tx, gz = z0 + tz;
-            if (gx >= Lf.nx || gz >= Lf.nz) continue;
-            const int lx = tx + H, lz = tz + H;
-            const size_t i = (size_t)gz * Lf.nx + gx;
-            const cx<T> c = U2[lz][lx];
-            const cx<T> mu = op.apply(gx, gz, &U2[lz][lx], RW);
-            const cx<T> v = c + wj * cdiv(F[lz][lx] - mu, op.diag(i));
-            stc(ob, i, accumulate ? ldcc(ob, i) + v : v);
-        }
-        return;
-    } else {
-        // post-smooth on tile + 1 halo into U3
-        for (int idx = threadIdx.x; idx < SW * SH; idx += blockDim.x) {
-            const int sz = idx / SW, sx = idx - sz * SW;
-            const int gx = x0 - 1 + sx, gz = z0 - 1 + sz;
-            cx<T> u3(0, 0);
-            if (gx >= 0 && gx < Lf.nx && gz >= 0 && gz < Lf.nz) {
-                const int lx = sx + 1, lz = sz + 1;
-                const cx<T> c = U2[lz][lx];
-                const cx<T> mu = op.apply(gx, gz, &U2[lz][lx], RW);
-                u3 = c + wj * cdiv(F[lz][lx] - mu, op.diag((size_t)gz * Lf.nx + gx));
-            }
-            U3[sz][sx] = u3;
-        }
-        __syncthreads();
-        // y = A u3 on the tile (fine operator with damping), dots
-        T* ob = out + 2 * nf * b;
-        T* yb = y + 2 * nf * b;
-        const T* ab = aux + 2 * nf * b;
-        const T* m2 = static_cast<const T*>(Lf.m2) + (size_t)b * Lf.mstride;
-        const T hw = w2[b];
-        T d0 = 0, d1 = 0, d2 = 0;
-        for (int idx = threadIdx.x; idx < PFX * PFZ; idx += blockDim.x) {
-            const int tz = idx / PFX, tx = idx - tz * PFX;
-            const int gx = x0 + tx, gz = z0 + tz;
-            if (gx >= Lf.nx || gz >= Lf.nz) continue;
-            const int sx = tx + 1, sz = tz + 1;
-            const size_t i = (size_t)gz * Lf.nx + gx;
-            const T s = hw * __ldg(m2 + i);
-            const T a = layer_alpha_t<T>(gx, gz, Lf.nx, Lf.nz, npml, acoef);
-            const cx<T> c = U3[sz][sx];
-            cx<T> yv((T(4) - s) * c.re - s * a * c.im, (T(4) - s) * c.im + s * a * c.re);
-            yv = yv - U3[sz][sx - 1] - U3[sz][sx + 1] - U3[sz - 1][sx] - U3[sz + 1][sx];
-            stc(ob, i, c);
-            stc(yb, i, yv);
-            if (MODE == 1) {          // <rh, v>
-                const cx<T> q = ldc(ab, i);
-                d0 += q.re * yv.re + q.im * yv.im;
-                d1 += q.re * yv.im - q.im * yv.re;
-            } else if (MODE == 2) {   // <t, s>, <t, t> with s = f
-                const cx<T> sv = F[tz + H][tx + H];
-                d0 += yv.re * sv.re + yv.im * sv.im;
-                d1 += yv.re * sv.im - yv.im * sv.re;
-                d2 += yv.re * yv.re + yv.im * yv.im;
-            }
-        }
-        if (MODE == 3) return;        // FGMRES: z and A z only
+    if constexpr (MODE == 0 || MODE == 3) return;
+    else {
         const T vv[3] = {d0, d1, d2};
         double acc[3];
         const int nblk = gridDim.x * gridDim.y, blk = blockIdx.y * gridDim.x + blockIdx.x;
@@ -1074,32 +1252,17 @@ __global__ void __launch_bounds__(256) k_prolong(LevelDev Lf, LevelDev Lc, int n
     }
 }
 
-// Tile choices (tile = 0 or 1; FP64 always uses its fixed tiles):
-//   finest-level prolongation: 64 x 8 or 64 x 16 fine nodes per block;
-//   Galerkin prolongation: 16 x 8 or 32 x 8 fine nodes per block.
-template <typename T, int PFZ>
-static void prolong_fine(int mode, dim3 grd, cudaStream_t s, const LevelDev& Lf, const LevelDev& Lc, int npml, T ac,
-                         const T* w2, T b1, T b2, T wj, const T* f, const T* ec, T* out, T* y, const T* aux,
-                         double* partials, int pstride, RhsState* st, int accumulate) {
-    if (mode == 0)
-        launch_pdl(k_prolong<T, 0, PFZ>, grd, dim3(256), 0, s, Lf, Lc, npml, ac, w2, b1, b2, wj, f, ec, out, y, aux,
-                   partials, pstride, st, accumulate);
-    else if (mode == 1)
-        launch_pdl(k_prolong<T, 1, PFZ>, grd, dim3(256), 0, s, Lf, Lc, npml, ac, w2, b1, b2, wj, f, ec, out, y, aux,
-                   partials, pstride, st, accumulate);
-    else if (mode == 2)
-        launch_pdl(k_prolong<T, 2, PFZ>, grd, dim3(256), 0, s, Lf, Lc, npml, ac, w2, b1, b2, wj, f, ec, out, y, aux,
-                   partials, pstride, st, accumulate);
-    else
-        launch_pdl(k_prolong<T, 3, PFZ>, grd, dim3(256), 0, s, Lf, Lc, npml, ac, w2, b1, b2, wj, f, ec, out, y, aux,
-                   partials, pstride, st, accumulate);
+// Grid of the marching prolongation for a fine level of nx x nz nodes.
+inline dim3 prolong_grid(int nx, int nz, int nrhs, int longest, int* zs) {
+    const int cw = (nx + PM_COLS - 1) / PM_COLS;
+    *zs = march_rows(cw, nz, nrhs, longest);
+    return dim3((cw + PM_WARPS - 1) / PM_WARPS, (nz + *zs - 1) / *zs, nrhs);
 }
 
 template <typename T>
 void launch_prolong(int mode, const LevelDev& Lf, const LevelDev& Lc, int npml, double amax, const T* w2,
                     double b1, double b2, double wj, const T* f, const T* ec, T* out, T* y, const T* aux,
                     double* partials, int pstride, RhsState* st, int nrhs, cudaStream_t s, int accumulate, int tile) {
-    constexpr int PFX = PTile<T>::X;
     const T ac = (T)layer_coef(npml, amax);
     const bool small = sizeof(T) == 4 && tile == 0;
     if (mode == 0 && !Lf.m2) {
@@ -1117,16 +1280,21 @@ void launch_prolong(int mode, const LevelDev& Lf, const LevelDev& Lc, int npml, 
         }
         return;
     }
-    if (small) {
-        dim3 grd((Lf.nx + PFX - 1) / PFX, (Lf.nz + 7) / 8, nrhs);
-        prolong_fine<T, 8>(mode, grd, s, Lf, Lc, npml, ac, w2, (T)b1, (T)b2, (T)wj, f, ec, out, y, aux, partials,
-                           pstride, st, accumulate);
-    } else {
-        constexpr int PFZ = PTile<T>::Z;
-        dim3 grd((Lf.nx + PFX - 1) / PFX, (Lf.nz + PFZ - 1) / PFZ, nrhs);
-        prolong_fine<T, PFZ>(mode, grd, s, Lf, Lc, npml, ac, w2, (T)b1, (T)b2, (T)wj, f, ec, out, y, aux, partials,
-                             pstride, st, accumulate);
-    }
+    // finest level: the tile choice is the longest row segment (16 or 32 rows)
+    int zs = 0;
+    const dim3 grd = prolong_grid(Lf.nx, Lf.nz, nrhs, tile == 0 ? 16 : 32, &zs);
+    if (mode == 0)
+        launch_pdl(k_prolong<T, 0>, grd, dim3(32 * PM_WARPS), 0, s, Lf, Lc, npml, ac, w2, (T)b1, (T)b2, (T)wj, f, ec, out, y, aux,
+                   partials, pstride, st, accumulate, zs);
+    else if (mode == 1)
+        launch_pdl(k_prolong<T, 1>, grd, dim3(32 * PM_WARPS), 0, s, Lf, Lc, npml, ac, w2, (T)b1, (T)b2, (T)wj, f, ec, out, y, aux,
+                   partials, pstride, st, accumulate, zs);
+    else if (mode == 2)
+        launch_pdl(k_prolong<T, 2>, grd, dim3(32 * PM_WARPS), 0, s, Lf, Lc, npml, ac, w2, (T)b1, (T)b2, (T)wj, f, ec, out, y, aux,
+                   partials, pstride, st, accumulate, zs);
+    else
+        launch_pdl(k_prolong<T, 3>, grd, dim3(32 * PM_WARPS), 0, s, Lf, Lc, npml, ac, w2, (T)b1, (T)b2, (T)wj, f, ec, out, y, aux,
+                   partials, pstride, st, accumulate, zs);
 }
 
 // ======================================================= V-cycle: coarsest

@@ -57,7 +57,8 @@ int max_blocks_per_rhs(const helm_model* m) {
     const Level& L0 = m->lv[0];
     size_t g1 = std::min<size_t>(2048, (L0.n() + 1023) / 1024);
     size_t g2 = (size_t)((L0.nx + 31) / 32) * ((L0.nz + 7) / 8);   // resid64 / apply tiles
-    size_t g3 = (size_t)((L0.nx + 31) / 32) * ((L0.nz + 15) / 16); // prolong tiles (FP64: 32 x 16)
+    // marching prolongation: 4 warps of 60 columns per block, row segments of at least 4
+    size_t g3 = (size_t)((L0.nx + 60 * 4 - 1) / (60 * 4)) * ((L0.nz + 3) / 4);
     return (int)std::max<size_t>(std::max(g1, g2), std::max<size_t>(g3, 1));
 }
 
