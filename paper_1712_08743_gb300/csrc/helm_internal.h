@@ -124,7 +124,7 @@ inline LevelDev level_dev(const helm_model* m, int l, bool dbl) {
 enum TailOp : int { OP_SMOOTH0 = 0, OP_RESID = 1, OP_RESTRICT = 2, OP_PROLONG_ADD = 3, OP_JACOBI = 4,
                     OP_COARSE = 5, OP_OUTPUT = 6, OP_LOAD = 7 };
 std::vector<int> tail_schedule(int lt, int L, bool fcycle);
-size_t tail_smem_bytes(const helm_model* m, int lt, size_t elem);
+size_t tail_smem_bytes(const helm_model* m, int lt, size_t elem, bool* minv_smem = nullptr, int* minv_off = nullptr);
 
 // Arguments of the tail kernel: levels lt..L of the cycle for one RHS per
 // block, every vector of those levels in shared memory.
@@ -138,6 +138,9 @@ struct TailArgs {
     const int* slot;
     const int* ops;
     int nops;
+    int minv_smem;            // 1: the coarsest inverse is staged in shared memory at minv_off
+    int minv_off;
+    int off[kMaxLevels];      // level l's arrays in shared memory (complex elements), l = lt..L
     const double* w2;         // (h_0 omega_b)^2
     double b1, b2, wj;
 };

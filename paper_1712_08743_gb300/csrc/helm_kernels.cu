@@ -1452,28 +1452,39 @@ void launch_coarse_invert(const LevelDev& Lc, const double* w2_slots, const int*
 // complex coefficients M_k = G_k - hw (b1 - j b2) K_k of this right-hand side
 // (staged once per launch). The schedule of passes runs with a block barrier
 // after each pass.
+// M u at node p = (iz, ix) of a tail level held in shared memory; C = the five
+// coefficient arrays (c, e, n, ne, nw) of n nodes each, U = &u[p].
 template <typename T>
-__device__ __forceinline__ cx<T> mop9_sm(const cx<T>* C, size_t n, int nx, int nz, int ix, int iz, const cx<T>* U) {
-    const size_t i = (size_t)iz * nx + ix;
+__device__ __forceinline__ cx<T> mop9_sm(const cx<T>* C, int n, int nx, int nz, int ix, int iz, int p,
+                                         const cx<T>* U) {
     const cx<T>* Ce = C + n;
     const cx<T>* Cn = C + 2 * n;
     const cx<T>* Cne = C + 3 * n;
     const cx<T>* Cnw = C + 4 * n;
-    cx<T> acc = C[i] * U[0];
+    cx<T> acc = C[p] * U[0];
     const bool e = ix + 1 < nx, w = ix > 0, no = iz + 1 < nz, so = iz > 0;
-    if (e) acc = acc + Ce[i] * U[1];
-    if (w) acc = acc + Ce[i - 1] * U[-1];
-    if (no) acc = acc + Cn[i] * U[nx];
-    if (so) acc = acc + Cn[i - nx] * U[-nx];
-    if (no && e) acc = acc + Cne[i] * U[nx + 1];
-    if (so && w) acc = acc + Cne[i - nx - 1] * U[-nx - 1];
-    if (no && w) acc = acc + Cnw[i] * U[nx - 1];
-    if (so && e) acc = acc + Cnw[i - nx + 1] * U[-nx + 1];
+    if (e) acc = acc + Ce[p] * U[1];
+    if (w) acc = acc + Ce[p - 1] * U[-1];
+    if (no) {
+        acc = acc + Cn[p] * U[nx];
+        if (e) acc = acc + Cne[p] * U[nx + 1];
+        if (w) acc = acc + Cnw[p] * U[nx - 1];
+    }
+    if (so) {
+        acc = acc + Cn[p - nx] * U[-nx];
+        if (w) acc = acc + Cne[p - nx - 1] * U[-nx - 1];
+        if (e) acc = acc + Cnw[p - nx + 1] * U[-nx + 1];
+    }
     return acc;
 }
 
+// Row and column of node p of a level with nx columns: (p + 1/2) / nx in FP32 is
+// never within rounding of an integer for the level sizes of the tail
+// (p < 2^16, nx < 2^10), so the truncation is exact.
+__device__ __forceinline__ int tail_row(int p, float rnx) { return (int)(((float)p + 0.5f) * rnx); }
+
 template <typename T>
-__global__ void __launch_bounds__(1024) k_tail(TailArgs a, const RhsState* st) {
+__global__ void __launch_bounds__(1024) k_tail(const __grid_constant__ TailArgs a, const RhsState* st) {
     extern __shared__ __align__(16) unsigned char tail_smem[];
     pdl_trigger();
     const int b = blockIdx.x;
@@ -1481,17 +1492,14 @@ __global__ void __launch_bounds__(1024) k_tail(TailArgs a, const RhsState* st) {
     const T hb1 = hw * b1, hb2 = hw * b2;
     const int tid = threadIdx.x, nth = blockDim.x;
     cx<T>* base = reinterpret_cast<cx<T>*>(tail_smem);
-    // per level: f, u, r (3 n) then the coefficients (5 n)
-    size_t off[kMaxLevels];
-    {
-        size_t o = 0;
-        for (int l = a.lt; l <= a.L; ++l) { off[l] = o; o += 8 * (size_t)a.lv[l].nx * a.lv[l].nz; }
-    }
+    // per level (at a.off[l]): f, u, r (3 n) then the coefficients (5 n); then
+    // the coarsest inverse of this right-hand side's frequency when it fits
+    const int* off = a.off;
     for (int l = a.lt; l <= a.L; ++l) {
-        const size_t n = (size_t)a.lv[l].nx * a.lv[l].nz;
+        const int n = a.lv[l].nx * a.lv[l].nz;
         const T* gk = static_cast<const T*>(a.lv[l].gk) + (size_t)b * a.lv[l].gkstride;
         cx<T>* C = base + off[l] + 3 * n;
-        for (size_t p = tid; p < n; p += nth) {
+        for (int p = tid; p < n; p += nth) {
             T g[5], q[5];
 #pragma unroll
             for (int k = 0; k < 5; ++k) {
@@ -1502,14 +1510,20 @@ __global__ void __launch_bounds__(1024) k_tail(TailArgs a, const RhsState* st) {
             for (int k = 0; k < 5; ++k) C[(size_t)k * n + p] = cx<T>(g[k] - hb1 * q[k], hb2 * q[k]);
         }
     }
+    const int nL = a.lv[a.L].nx * a.lv[a.L].nz;
+    const T* Mg = static_cast<const T*>(a.minv) + 2 * (size_t)nL * nL * a.slot[b];
+    cx<T>* Ms = base + a.minv_off;
+    // the inverse is written by k_coarse_invert before the first ordinary launch of the solve
+    if (a.minv_smem)
+        for (int t = tid; t < nL * nL; t += nth) Ms[t] = ldc(Mg, t);
     pdl_wait();   // the coefficients above are model data; everything below depends on earlier kernels
     if (!rhs_active(st, b)) return;
     __syncthreads();
     for (int k = 0; k < a.nops; ++k) {
         const int op = a.ops[k], type = op & 255, l = op >> 8;
-        const LevelDev& L = a.lv[l];
-        const int nx = L.nx, nz = L.nz;
-        const size_t n = (size_t)nx * nz;
+        const int nx = a.lv[l].nx, nz = a.lv[l].nz;
+        const int n = nx * nz;
+        const float rnx = 1.0f / (float)nx;
         cx<T>* f = base + off[l];
         cx<T>* u = f + n;
         cx<T>* r = u + n;
@@ -1517,72 +1531,75 @@ __global__ void __launch_bounds__(1024) k_tail(TailArgs a, const RhsState* st) {
         switch (type) {
             case OP_LOAD: {
                 const T* in = static_cast<const T*>(a.in);
-                for (size_t p = tid; p < n; p += nth) f[p] = ldc(in, n * b + p);
+                for (int p = tid; p < n; p += nth) f[p] = ldc(in, (size_t)n * b + p);
                 break;
             }
             case OP_SMOOTH0:
-                for (size_t p = tid; p < n; p += nth) u[p] = wj * cdiv(f[p], C[p]);
+                for (int p = tid; p < n; p += nth) u[p] = wj * cdiv(f[p], C[p]);
                 break;
             case OP_RESID:
-                for (size_t p = tid; p < n; p += nth) {
-                    const int ix = (int)(p % nx), iz = (int)(p / nx);
-                    r[p] = f[p] - mop9_sm(C, n, nx, nz, ix, iz, u + p);
+                for (int p = tid; p < n; p += nth) {
+                    const int iz = tail_row(p, rnx), ix = p - iz * nx;
+                    r[p] = f[p] - mop9_sm(C, n, nx, nz, ix, iz, p, u + p);
                 }
                 break;
             case OP_JACOBI:
-                for (size_t p = tid; p < n; p += nth) u[p] = u[p] + wj * cdiv(r[p], C[p]);
+                for (int p = tid; p < n; p += nth) u[p] = u[p] + wj * cdiv(r[p], C[p]);
                 break;
             case OP_RESTRICT: {
-                const LevelDev& Cl = a.lv[l + 1];
-                const size_t nc = (size_t)Cl.nx * Cl.nz;
+                const int cnx = a.lv[l + 1].nx, nc = cnx * a.lv[l + 1].nz;
+                const float rcnx = 1.0f / (float)cnx;
                 cx<T>* fc = base + off[l + 1];
-                for (size_t q = tid; q < nc; q += nth) {
-                    const int I = (int)(q % Cl.nx), K = (int)(q / Cl.nx);
-                    cx<T> acc(0, 0);
-                    for (int dz = -1; dz <= 1; ++dz) {
-                        const int jz = 2 * K + 1 + dz;
-                        if (jz >= nz) continue;
-                        for (int dx = -1; dx <= 1; ++dx) {
-                            const int jx = 2 * I + 1 + dx;
-                            if (jx >= nx) continue;
-                            const T wgt = T((2 - (dx < 0 ? -dx : dx)) * (2 - (dz < 0 ? -dz : dz))) * T(0.25);
-                            acc = acc + wgt * r[(size_t)jz * nx + jx];
-                        }
+                for (int q = tid; q < nc; q += nth) {
+                    const int K = tail_row(q, rcnx), I = q - K * cnx;
+                    const int x = 2 * I + 1;
+                    const cx<T>* r0 = r + (2 * K) * nx;
+                    const cx<T>* r1 = r0 + nx;
+                    const bool e = x + 1 < nx, z2 = 2 * K + 2 < nz;
+                    cx<T> h0 = r0[x - 1] + T(2) * r0[x], hm = r1[x - 1] + T(2) * r1[x], hp(0, 0);
+                    if (e) { h0 = h0 + r0[x + 1]; hm = hm + r1[x + 1]; }
+                    if (z2) {
+                        const cx<T>* r2 = r1 + nx;
+                        hp = r2[x - 1] + T(2) * r2[x];
+                        if (e) hp = hp + r2[x + 1];
                     }
-                    fc[q] = acc;
+                    fc[q] = T(0.25) * ((h0 + hp) + T(2) * hm);
                 }
                 break;
             }
             case OP_PROLONG_ADD: {
-                const LevelDev& Cl = a.lv[l + 1];
-                const size_t nc = (size_t)Cl.nx * Cl.nz;
-                const cx<T>* uc = base + off[l + 1] + nc;
-                for (size_t p = tid; p < n; p += nth) {
-                    const int jx = (int)(p % nx), jz = (int)(p / nx);
-                    int ia, ib, ka, kb;
-                    T wa, wb, va, vb;
-                    if (jx & 1) { ia = (jx - 1) / 2; ib = ia; wa = T(1); wb = T(0); }
-                    else { ia = jx / 2 - 1; ib = jx / 2; wa = T(0.5); wb = T(0.5); }
-                    if (jz & 1) { ka = (jz - 1) / 2; kb = ka; va = T(1); vb = T(0); }
-                    else { ka = jz / 2 - 1; kb = jz / 2; va = T(0.5); vb = T(0.5); }
-                    cx<T> acc(0, 0);
-                    const bool iao = ia >= 0 && ia < Cl.nx, ibo = ib >= 0 && ib < Cl.nx;
-                    const bool kao = ka >= 0 && ka < Cl.nz, kbo = kb >= 0 && kb < Cl.nz;
-                    if (kao && iao) acc = acc + (va * wa) * uc[(size_t)ka * Cl.nx + ia];
-                    if (kao && ibo && wb != T(0)) acc = acc + (va * wb) * uc[(size_t)ka * Cl.nx + ib];
-                    if (kbo && iao && vb != T(0)) acc = acc + (vb * wa) * uc[(size_t)kb * Cl.nx + ia];
-                    if (kbo && ibo && vb != T(0) && wb != T(0)) acc = acc + (vb * wb) * uc[(size_t)kb * Cl.nx + ib];
-                    u[p] = u[p] + acc;
+                const int cnx = a.lv[l + 1].nx, cnz = a.lv[l + 1].nz;
+                const cx<T>* uc = base + off[l + 1] + cnx * cnz;
+                for (int p = tid; p < n; p += nth) {
+                    const int jz = tail_row(p, rnx), jx = p - jz * nx;
+                    // coarse rows (jz-1)/2 and jz/2 (one row, weight 1, for odd jz), columns likewise
+                    const int ka = (jz - 1) >> 1, kb = jz >> 1, ia = (jx - 1) >> 1, ib = jx >> 1;
+                    const bool zo = jz & 1, xo = jx & 1;
+                    auto hrow = [&](int K) -> cx<T> {
+                        const cx<T>* e = uc + K * cnx;
+                        if (xo) return e[ia];
+                        cx<T> h(0, 0);
+                        if (ia >= 0) h = e[ia];
+                        if (ib < cnx) h = h + e[ib];
+                        return T(0.5) * h;
+                    };
+                    cx<T> add(0, 0);
+                    if (zo) add = hrow(ka);
+                    else {
+                        if (ka >= 0) add = hrow(ka);
+                        if (kb < cnz) add = add + hrow(kb);
+                        add = T(0.5) * add;
+                    }
+                    u[p] = u[p] + add;
                 }
                 break;
             }
             case OP_COARSE: {
-                const T* Mb = static_cast<const T*>(a.minv) + 2 * n * n * a.slot[b];
                 const int lane = tid & 31, warp = tid >> 5, nw = nth >> 5;
-                for (int row = warp; row < (int)n; row += nw) {
+                for (int row = warp; row < n; row += nw) {
                     T re = 0, im = 0;
-                    for (int j = lane; j < (int)n; j += 32) {
-                        const cx<T> m = ldc(Mb, (size_t)row * n + j);
+                    for (int j = lane; j < n; j += 32) {
+                        const cx<T> m = a.minv_smem ? Ms[row * n + j] : ldc(Mg, (size_t)row * n + j);
                         const cx<T> v = f[j];
                         re += m.re * v.re - m.im * v.im;
                         im += m.re * v.im + m.im * v.re;
@@ -1598,8 +1615,8 @@ __global__ void __launch_bounds__(1024) k_tail(TailArgs a, const RhsState* st) {
             }
             case OP_OUTPUT: {
                 T* o = static_cast<T*>(a.out);
-                for (size_t p = tid; p < n; p += nth)
-                    stc(o, n * b + p, a.accumulate ? ldcc(o, n * b + p) + u[p] : u[p]);
+                for (int p = tid; p < n; p += nth)
+                    stc(o, (size_t)n * b + p, a.accumulate ? ldcc(o, (size_t)n * b + p) + u[p] : u[p]);
                 break;
             }
         }
@@ -1607,10 +1624,17 @@ __global__ void __launch_bounds__(1024) k_tail(TailArgs a, const RhsState* st) {
     }
 }
 
-size_t tail_smem_bytes(const helm_model* m, int lt, size_t elem) {
+// Shared memory of the tail for levels lt..L: 8 complex arrays per level
+// (f, u, r, five coefficients), then the coarsest inverse when the total stays
+// within 227 KB (TailArgs::minv_smem).
+size_t tail_smem_bytes(const helm_model* m, int lt, size_t elem, bool* minv_smem, int* minv_off) {
     size_t v = 0;
     for (size_t l = lt; l < m->lv.size(); ++l) v += 8 * m->lv[l].n();   // f, u, r + 5 coefficients
-    return v * 2 * elem;
+    const size_t nL = m->lv.back().n();
+    const bool fit = (v + nL * nL) * 2 * elem <= 227u * 1024u;
+    if (minv_smem) *minv_smem = fit;
+    if (minv_off) *minv_off = (int)v;
+    return (fit ? v + nL * nL : v) * 2 * elem;
 }
 
 template <typename T>

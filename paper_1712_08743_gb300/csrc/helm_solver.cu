@@ -115,6 +115,10 @@ static void mg_cycle(const helm_model* m, const MgCall& c, const MgLevels<T>& B,
         a.slot = c.slot;
         a.ops = F ? m->ops_f[dbl] : m->ops_v[dbl];
         a.nops = F ? m->nops_f[dbl] : m->nops_v[dbl];
+        bool ms = false;
+        tail_smem_bytes(m, lt, sizeof(T), &ms, &a.minv_off);
+        a.minv_smem = ms ? 1 : 0;
+        for (int q = lt, o = 0; q <= a.L; ++q) { a.off[q] = o; o += 8 * (int)m->lv[q].n(); }
         a.w2 = c.w2;
         a.b1 = c.b1;
         a.b2 = c.b2;
