@@ -355,6 +355,11 @@ def run_ours(args):
     roof = {"bound": "hbm", "kernel": dom, "achieved": kern[dom]["gbs"], "peak": peak, "unit": "GB/s",
             "frac": kern[dom]["gbs"] / peak, "traffic": traffic, "peak_kind": f"{peak_kind} burst copy",
             "bytes_per_launch": kern[dom]["bytes"], "kernels": kern}
+    # shares of the step's device time per kernel, from the committed ncu launch list of this workload
+    shares = os.path.join(ROOT, "profiles", "launch_shares.json")
+    if os.path.exists(shares):
+        with open(shares) as f:
+            roof["time_shares"] = json.load(f)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
