@@ -169,6 +169,29 @@ int helm_fwi_backward(helm_fwi_state* state, double* grad_out, const helm_solve_
                       helm_solve_stats* stats);
 void helm_fwi_state_destroy(helm_fwi_state* state);
 
+/* Gauss-Newton Hessian-vector product (Eq. 8 without its second term, the
+ * approximation Eq. 9 uses): hdm_out = 2 Re[Jac^H Jac dm] + 2 lambda_reg dm,
+ * with Jac the Jacobian of the receiver data P u with respect to the physical
+ * slowness, at the model, acquisition and wavefields of `state` (from
+ * helm_fwi_forward; lambda_reg is the state's). Per shot and frequency it runs
+ * one Born solve B du = 2 omega^2 m (1 - j alpha) u (E dm) and one adjoint solve
+ * with the sampled du as data, on the same solver and options as helm_solve.
+ * dm, hdm_out: float64 [Pz][Px], host or device following opts->device_ptrs;
+ * stats (nullable): [2 nfreq nshot], Born solves then adjoint solves. The
+ * result is symmetric in dm and positive definite for lambda_reg > 0. Returns
+ * HELM_E_NOT_CONVERGED (result still written) if a solve missed its tolerance. */
+int helm_gn_hvp(helm_fwi_state* state, const double* dm, double* hdm_out, const helm_solve_opts* opts,
+                helm_solve_stats* stats);
+
+/* One Gauss-Newton step (Eq. 9): dm_out = -H^{-1} grad by cg_iters (1..1000)
+ * conjugate-gradient iterations from zero, each one helm_gn_hvp. grad: the
+ * gradient at the state's model (helm_fwi_backward); grad, dm_out float64
+ * [Pz][Px] following opts->device_ptrs. cg_rel_out (host, nullable):
+ * [cg_iters + 1] relative residuals ||grad + H dm_k|| / ||grad||. Needs
+ * lambda_reg > 0 (HELM_E_INVALID otherwise). */
+int helm_gn_step(helm_fwi_state* state, const double* grad, int cg_iters, double* dm_out, double* cg_rel_out,
+                 const helm_solve_opts* opts);
+
 /* Operator application y = B(m, omega_k) u_k (Eq. 3) for parity checks and
  * bandwidth measurement. precision HELM_PREC_FP64: u, y c128; otherwise c64.
  * [nrhs][nz][nx] each, following device_ptrs. */

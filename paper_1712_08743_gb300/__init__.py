@@ -9,6 +9,7 @@ from ._lib import (  # noqa: F401
 )
 from .api import (  # noqa: F401
     Context, Model, helm_adjoint_gradient, helm_apply, helm_create_model, helm_ctx_create, helm_ctx_destroy,
-    helm_default_opts, helm_destroy_model, helm_fwi_backward, helm_fwi_forward, helm_poll, helm_release,
+    helm_default_opts, helm_destroy_model, helm_fwi_backward, helm_fwi_forward, helm_gn_hvp, helm_gn_step, helm_poll,
+    helm_release,
     helm_serve_config, helm_solve, helm_submit, helm_vcycle,
 )

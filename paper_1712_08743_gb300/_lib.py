@@ -112,6 +112,8 @@ SIGNATURES = {
     "helm_fwi_forward": (_I, [_P, _I, _pD, _I, _pI, _pI, _I, _pI, _pI, _P, _D, _pD, _P, _pOpts, _pStats, C.POINTER(_P)]),
     "helm_fwi_backward": (_I, [_P, _P, _pOpts, _pStats]),
     "helm_fwi_state_destroy": (None, [_P]),
+    "helm_gn_hvp": (_I, [_P, _P, _P, _pOpts, _pStats]),
+    "helm_gn_step": (_I, [_P, _P, _I, _P, _pD, _pOpts]),
     "helm_apply": (_I, [_P, _I, _pD, _I, _P, _P, _I]),
     "helm_vcycle": (_I, [_P, _I, _pD, _D, _D, _D, _P, _P, _I]),
     "helm_vcycle_noalloc": (_I, [_P, _I, _pD, _D, _D, _D, _P, _P]),

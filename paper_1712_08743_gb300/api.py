@@ -322,6 +322,32 @@ def helm_fwi_backward(model: Model, state: FwiState, opts=None, grad_out=None):
     return g, st
 
 
+def helm_gn_hvp(model: Model, state: FwiState, dm, opts=None):
+    """Gauss-Newton Hessian-vector product (Eq. 8 without its second term):
+    (H dm [Pz][Px] float64, status)."""
+    lib = model.lib
+    x = _np(dm, np.float64).reshape(model.Pz, model.Px)
+    out = np.empty_like(x)
+    o = _opts(opts, device_ptrs=0)
+    st = lib.helm_gn_hvp(state.handle, C.c_void_p(x.ctypes.data), C.c_void_p(out.ctypes.data), C.byref(o), None)
+    check(st, "helm_gn_hvp", allow=(_lib.HELM_OK, _lib.HELM_E_NOT_CONVERGED))
+    return out, st
+
+
+def helm_gn_step(model: Model, state: FwiState, grad, cg_iters: int, opts=None):
+    """One Gauss-Newton step (Eq. 9) by cg_iters CG iterations from zero:
+    (dm [Pz][Px] float64, relative CG residuals [cg_iters + 1], status)."""
+    lib = model.lib
+    g = _np(grad, np.float64).reshape(model.Pz, model.Px)
+    dm = np.empty_like(g)
+    rel = np.empty(int(cg_iters) + 1, np.float64)
+    o = _opts(opts, device_ptrs=0)
+    st = lib.helm_gn_step(state.handle, C.c_void_p(g.ctypes.data), int(cg_iters), C.c_void_p(dm.ctypes.data),
+                          _ptr_d(rel), C.byref(o))
+    check(st, "helm_gn_step", allow=(_lib.HELM_OK, _lib.HELM_E_NOT_CONVERGED))
+    return dm, rel, st
+
+
 # ------------------------------------------------------------------ serving
 @dataclass
 class ServedResult:

@@ -484,6 +484,74 @@ int helm_fwi_backward(helm_fwi_state* state, double* grad_out, const helm_solve_
     return rc;
 }
 
+int helm_gn_hvp(helm_fwi_state* state, const double* dm, double* hdm_out, const helm_solve_opts* opts,
+                helm_solve_stats* stats) {
+    if (!state || !state->st || !dm || !hdm_out) return HELM_E_INVALID;
+    helm_solve_opts o;
+    if (opts) o = *opts; else helm_default_opts(&o);
+    if (check_opts(o) != HELM_OK) return HELM_E_INVALID;
+    helm_model* m = state->m;
+    DeviceGuard g(m->ctx->device);
+    cudaStream_t s = m->ctx->stream;
+    const size_t bytes = sizeof(double) * (size_t)m->Px * m->Pz;
+    DevMem ddm, dh;
+    const double* dm_p = dm;
+    double* h_p = hdm_out;
+    if (!o.device_ptrs) {
+        if (cudaMalloc(&ddm.p, bytes) != cudaSuccess || cudaMalloc(&dh.p, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            return HELM_E_NOMEM;
+        }
+        HELM_CUDA_TRY(cudaMemcpyAsync(ddm.p, dm, bytes, cudaMemcpyHostToDevice, s));
+        dm_p = static_cast<const double*>(ddm.p);
+        h_p = static_cast<double*>(dh.p);
+    }
+    int rc = gn_hvp(state->st, s, dm_p, h_p, o, stats);
+    if (rc != HELM_OK && rc != HELM_E_NOT_CONVERGED) return rc;
+    if (!o.device_ptrs) {
+        HELM_CUDA_TRY(cudaMemcpyAsync(hdm_out, h_p, bytes, cudaMemcpyDeviceToHost, s));
+        HELM_CUDA_TRY(cudaStreamSynchronize(s));
+    }
+    return rc;
+}
+
+int helm_gn_step(helm_fwi_state* state, const double* grad, int cg_iters, double* dm_out, double* cg_rel_out,
+                 const helm_solve_opts* opts) {
+    if (!state || !state->st || !grad || !dm_out || cg_iters < 1 || cg_iters > 1000) return HELM_E_INVALID;
+    if (!(state->st->lam > 0.0)) {
+        set_last_error("helm_gn_step needs lambda_reg > 0 (the Gauss-Newton Hessian is then positive definite)");
+        return HELM_E_INVALID;
+    }
+    helm_solve_opts o;
+    if (opts) o = *opts; else helm_default_opts(&o);
+    if (check_opts(o) != HELM_OK) return HELM_E_INVALID;
+    helm_model* m = state->m;
+    DeviceGuard g(m->ctx->device);
+    cudaStream_t s = m->ctx->stream;
+    const size_t bytes = sizeof(double) * (size_t)m->Px * m->Pz;
+    DevMem dgrad, ddm;
+    const double* g_p = grad;
+    double* dm_p = dm_out;
+    if (!o.device_ptrs) {
+        if (cudaMalloc(&dgrad.p, bytes) != cudaSuccess || cudaMalloc(&ddm.p, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            return HELM_E_NOMEM;
+        }
+        HELM_CUDA_TRY(cudaMemcpyAsync(dgrad.p, grad, bytes, cudaMemcpyHostToDevice, s));
+        g_p = static_cast<const double*>(dgrad.p);
+        dm_p = static_cast<double*>(ddm.p);
+    }
+    std::vector<double> rel(cg_iters + 1, 0.0);
+    int rc = gn_step(state->st, s, g_p, cg_iters, dm_p, rel.data(), o);
+    if (rc != HELM_OK && rc != HELM_E_NOT_CONVERGED) return rc;
+    if (!o.device_ptrs) {
+        HELM_CUDA_TRY(cudaMemcpyAsync(dm_out, dm_p, bytes, cudaMemcpyDeviceToHost, s));
+        HELM_CUDA_TRY(cudaStreamSynchronize(s));
+    }
+    if (cg_rel_out) std::memcpy(cg_rel_out, rel.data(), sizeof(double) * rel.size());
+    return rc;
+}
+
 void helm_fwi_state_destroy(helm_fwi_state* state) {
     if (!state) return;
     DeviceGuard g(state->m->ctx->device);

@@ -249,7 +249,13 @@ void launch_adjoint_rhs(const double* resid, const int* rec_flat, int nrec, doub
                         size_t n, int nrhs, cudaStream_t s);
 void launch_grad_accum(const double* u, const double* w, const double* w2, const double* m_pad,
                        int nx, int nz, int npml, double amax, double* g_pad, int nrhs, cudaStream_t s);
-void launch_fold(const double* g_pad, const double* m_pad, int Px, int Pz, int npml, double lam,
-                 double* g, cudaStream_t s);
+void launch_fold(const double* g_pad, const double* m_pad, int Px, int Pz, int npml, double lam, double* g,
+                 cudaStream_t s, const double* reg = nullptr);   // reg: physical vector of the 2 lam term (null: m)
+void launch_expand(const double* dm, int Px, int Pz, int npml, double* dm_pad, cudaStream_t s);
+void launch_born_rhs(const double* u, const double* dm_pad, const double* m_pad, const double* hw2, int nx, int nz,
+                     int npml, double amax, double* f, int nrhs, cudaStream_t s);
+int dot_blocks(size_t n);
+void launch_dot_partials(const double* a, const double* b, size_t n, double* part, cudaStream_t s);
+void launch_axpby(double alpha, const double* x, double beta, double* y, size_t n, cudaStream_t s);
 
 }  // namespace helm

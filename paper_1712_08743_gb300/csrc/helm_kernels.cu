@@ -7,6 +7,7 @@
 // [nrhs][nz][nx] interleaved complex; right-hand side b uses angular frequency
 // omega_b (w2[b] = omega_b^2). The multigrid level l+1 has floor(n_l / 2)
 // nodes per axis; coarse node I sits on fine node 2I + 1.
+#include <algorithm>
 #include <functional>
 #include <vector>
 
@@ -1886,10 +1887,11 @@ void launch_grad_accum(const double* u, const double* w, const double* w2, const
     k_grad_accum<<<grid1d((size_t)nx * nz), 256, 0, s>>>(u, w, w2, m_pad, nx, nz, npml, layer_coef(npml, amax), g_pad, nrhs);
 }
 
-// g = E^T g_pad + 2 lam m on the physical cells: each edge cell also collects
-// the layer nodes that copy its slowness.
+// g = E^T g_pad + 2 lam x on the physical cells, x = the slowness (reg null) or
+// the physical vector reg: each edge cell also collects the layer nodes that
+// copy its slowness.
 __global__ void k_fold(const double* __restrict__ g_pad, const double* __restrict__ m_pad, int Px, int Pz, int npml,
-                       double lam, double* __restrict__ g) {
+                       double lam, const double* __restrict__ reg, double* __restrict__ g) {
     const int nx = Px + 2 * npml;
     const size_t n = (size_t)Px * Pz;
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
@@ -1899,14 +1901,82 @@ __global__ void k_fold(const double* __restrict__ g_pad, const double* __restric
         double acc = 0.0;
         for (int iz = zlo; iz <= zhi; ++iz)
             for (int ix = xlo; ix <= xhi; ++ix) acc += g_pad[(size_t)iz * nx + ix];
-        const double m = m_pad[(size_t)(pz + npml) * nx + px + npml];
-        g[i] = acc + 2.0 * lam * m;
+        const double x = reg ? reg[i] : m_pad[(size_t)(pz + npml) * nx + px + npml];
+        g[i] = acc + 2.0 * lam * x;
     }
 }
 
 void launch_fold(const double* g_pad, const double* m_pad, int Px, int Pz, int npml, double lam, double* g,
-                 cudaStream_t s) {
-    k_fold<<<grid1d((size_t)Px * Pz), 256, 0, s>>>(g_pad, m_pad, Px, Pz, npml, lam, g);
+                 cudaStream_t s, const double* reg) {
+    k_fold<<<grid1d((size_t)Px * Pz), 256, 0, s>>>(g_pad, m_pad, Px, Pz, npml, lam, reg, g);
+}
+
+// ------------------------------------------------------ Gauss-Newton (Eq. 9)
+// E dm: a physical perturbation copied onto the padded grid (edge replication,
+// as the slowness itself).
+__global__ void k_expand(const double* __restrict__ dm, int Px, int Pz, int npml, double* __restrict__ dm_pad) {
+    const int nx = Px + 2 * npml, nz = Pz + 2 * npml;
+    const size_t n = (size_t)nx * nz;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const int ix = (int)(i % nx), iz = (int)(i / nx);
+        const int px = min(max(ix - npml, 0), Px - 1), pz = min(max(iz - npml, 0), Pz - 1);
+        dm_pad[i] = dm[(size_t)pz * Px + px];
+    }
+}
+
+void launch_expand(const double* dm, int Px, int Pz, int npml, double* dm_pad, cudaStream_t s) {
+    k_expand<<<grid1d((size_t)(Px + 2 * npml) * (Pz + 2 * npml)), 256, 0, s>>>(dm, Px, Pz, npml, dm_pad);
+}
+
+// Born right-hand side of the grid-scaled system: the first-order change of
+// B(m) u = f under m -> m + dm is B du = -(dB/dm . dm) u = 2 omega^2 m (1 - j alpha)
+// dm u, times h^2: f_b = 2 (h omega_b)^2 m dm (1 - j alpha) u_b.
+__global__ void k_born_rhs(const double* __restrict__ u, const double* __restrict__ dm_pad,
+                           const double* __restrict__ m_pad, const double* __restrict__ hw2, int nx, int nz, int npml,
+                           double acoef, double* __restrict__ f) {
+    const size_t n = (size_t)nx * nz;
+    const int b = blockIdx.z;
+    const double c = 2.0 * hw2[b];
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const int ix = (int)(i % nx), iz = (int)(i / nx);
+        const double a = layer_alpha_t<double>(ix, iz, nx, nz, npml, acoef);
+        const double s = c * m_pad[i] * dm_pad[i];
+        const cx<double> uu = ldc(u, n * b + i);
+        stc(f, n * b + i, cx<double>(s * (uu.re + a * uu.im), s * (uu.im - a * uu.re)));   // s (1 - j a) u
+    }
+}
+
+void launch_born_rhs(const double* u, const double* dm_pad, const double* m_pad, const double* hw2, int nx, int nz,
+                     int npml, double amax, double* f, int nrhs, cudaStream_t s) {
+    k_born_rhs<<<dim3(grid1d((size_t)nx * nz), 1, nrhs), 256, 0, s>>>(u, dm_pad, m_pad, hw2, nx, nz, npml,
+                                                                     layer_coef(npml, amax), f);
+}
+
+// Per-block partial sums of a . b over n reals (the host adds the partials in
+// block order, so the result does not depend on timing).
+__global__ void k_dot_partials(const double* __restrict__ a, const double* __restrict__ b, size_t n, double* part) {
+    __shared__ double sh[32];
+    double acc[1] = {0.0};
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        acc[0] += a[i] * b[i];
+    block_sum<1>(acc, sh);
+    if (threadIdx.x == 0) part[blockIdx.x] = acc[0];
+}
+
+int dot_blocks(size_t n) { return std::min(grid1d(n), 256); }
+
+void launch_dot_partials(const double* a, const double* b, size_t n, double* part, cudaStream_t s) {
+    k_dot_partials<<<dot_blocks(n), 256, 0, s>>>(a, b, n, part);
+}
+
+// y = alpha x + beta y over n reals
+__global__ void k_axpby(double alpha, const double* __restrict__ x, double beta, double* __restrict__ y, size_t n) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        y[i] = alpha * x[i] + beta * y[i];
+}
+
+void launch_axpby(double alpha, const double* x, double beta, double* y, size_t n, cudaStream_t s) {
+    k_axpby<<<grid1d(n), 256, 0, s>>>(alpha, x, beta, y, n);
 }
 
 // ------------------------------------------------------- instantiations

@@ -799,6 +799,108 @@ int fwi_backward(FwiState* st, cudaStream_t s, double* grad_dev, const helm_solv
     return rc;
 }
 
+// ------------------------------------------------------- Gauss-Newton (Eq. 9)
+// H dm for the Gauss-Newton Hessian of J (Eq. 8 without its second term):
+// H dm = 2 Re[Jac^H Jac dm] + 2 lam dm, Jac the Jacobian of the receiver data
+// P u with respect to the physical slowness, at the model and wavefields of
+// the forward state. Per shot and frequency: one Born solve
+// B du = 2 omega^2 m (1 - j alpha) u (E dm), dd = P du, one adjoint solve
+// B w = conj(P^T dd); then the accumulation and fold of the gradient with w in
+// place of the adjoint field.
+int gn_hvp(FwiState* st, cudaStream_t s, const double* dm_dev, double* hdm_dev, const helm_solve_opts& o,
+           helm_solve_stats* stats) {
+    const helm_model* m = st->m;
+    const int nrhs = st->nrhs;
+    const size_t n = m->n();
+    DBuf dmpad, f64, du, w64, gpad, zero, dd, jp, dhw2;
+    TRY_ALLOC(dmpad, sizeof(double) * n, s);
+    TRY_ALLOC(f64, sizeof(double) * 2 * n * nrhs, s);
+    TRY_ALLOC(du, sizeof(double) * 2 * n * nrhs, s);
+    TRY_ALLOC(w64, sizeof(double) * 2 * n * nrhs, s);
+    TRY_ALLOC(gpad, sizeof(double) * n, s);
+    TRY_ALLOC(zero, sizeof(double) * 2 * (size_t)st->nrec * nrhs, s);
+    TRY_ALLOC(dd, sizeof(double) * 2 * (size_t)st->nrec * nrhs, s);
+    TRY_ALLOC(jp, sizeof(double) * nrhs, s);
+    TRY_ALLOC(dhw2, sizeof(double) * nrhs, s);
+    HELM_CUDA_TRY(cudaMemcpyAsync(dhw2.p, st->hw2.data(), sizeof(double) * nrhs, cudaMemcpyHostToDevice, s));
+    HELM_CUDA_TRY(cudaMemsetAsync(zero.p, 0, sizeof(double) * 2 * (size_t)st->nrec * nrhs, s));
+    HELM_CUDA_TRY(cudaMemsetAsync(gpad.p, 0, sizeof(double) * n, s));
+    launch_expand(dm_dev, m->Px, m->Pz, m->npml, dmpad.as<double>(), s);
+    launch_born_rhs(st->u64, dmpad.as<double>(), m->m_pad, dhw2.as<double>(), m->nx, m->nz, m->npml, m->alpha_max,
+                    f64.as<double>(), nrhs, s);
+    int rc1 = solve_batch(m, s, nrhs, st->hw2.data(), f64.as<double>(), du.as<double>(), o, stats);
+    if (rc1 != HELM_OK && rc1 != HELM_E_NOT_CONVERGED) return rc1;
+    // dd = P du (the sampling kernel with zero observed data)
+    launch_sample(du.as<double>(), st->drec, st->nrec, zero.as<double>(), nullptr, dd.as<double>(), jp.as<double>(), n,
+                  nrhs, s);
+    launch_adjoint_rhs(dd.as<double>(), st->drec, st->nrec, m->h * m->h, f64.as<double>(), n, nrhs, s);
+    int rc2 = solve_batch(m, s, nrhs, st->hw2.data(), f64.as<double>(), w64.as<double>(), o,
+                          stats ? stats + nrhs : nullptr);
+    if (rc2 != HELM_OK && rc2 != HELM_E_NOT_CONVERGED) return rc2;
+    launch_grad_accum(st->u64, w64.as<double>(), st->dw2, m->m_pad, m->nx, m->nz, m->npml, m->alpha_max,
+                      gpad.as<double>(), nrhs, s);
+    launch_fold(gpad.as<double>(), m->m_pad, m->Px, m->Pz, m->npml, st->lam, hdm_dev, s, dm_dev);
+    HELM_CUDA_TRY(cudaGetLastError());
+    HELM_CUDA_TRY(cudaStreamSynchronize(s));
+    return (rc1 == HELM_E_NOT_CONVERGED || rc2 == HELM_E_NOT_CONVERGED) ? HELM_E_NOT_CONVERGED : HELM_OK;
+}
+
+static int dev_dot(const double* a, const double* b, size_t n, DBuf& part, cudaStream_t s, double* out) {
+    const int nb = dot_blocks(n);
+    launch_dot_partials(a, b, n, part.as<double>(), s);
+    std::vector<double> h(nb);
+    HELM_CUDA_TRY(cudaMemcpyAsync(h.data(), part.p, sizeof(double) * nb, cudaMemcpyDeviceToHost, s));
+    HELM_CUDA_TRY(cudaStreamSynchronize(s));
+    double acc = 0.0;
+    for (int k = 0; k < nb; ++k) acc += h[k];
+    *out = acc;
+    return HELM_OK;
+}
+
+// One Gauss-Newton step (Eq. 9): dm = -H^{-1} g by conjugate gradients from
+// dm = 0 (H symmetric positive definite for lam > 0), `iters` Hessian-vector
+// products. rel[k] = ||g + H dm_k|| / ||g|| after k iterations (k = 0..iters).
+int gn_step(FwiState* st, cudaStream_t s, const double* g_dev, int iters, double* dm_dev, double* rel,
+            const helm_solve_opts& o) {
+    const helm_model* m = st->m;
+    const size_t np = (size_t)m->Px * m->Pz;
+    DBuf r, p, hp, part;
+    TRY_ALLOC(r, sizeof(double) * np, s);
+    TRY_ALLOC(p, sizeof(double) * np, s);
+    TRY_ALLOC(hp, sizeof(double) * np, s);
+    TRY_ALLOC(part, sizeof(double) * dot_blocks(np), s);
+    HELM_CUDA_TRY(cudaMemsetAsync(dm_dev, 0, sizeof(double) * np, s));
+    HELM_CUDA_TRY(cudaMemsetAsync(r.p, 0, sizeof(double) * np, s));
+    launch_axpby(-1.0, g_dev, 0.0, r.as<double>(), np, s);                 // r = -g
+    HELM_CUDA_TRY(cudaMemcpyAsync(p.p, r.p, sizeof(double) * np, cudaMemcpyDeviceToDevice, s));
+    double rr = 0.0;
+    int rc = dev_dot(r.as<double>(), r.as<double>(), np, part, s, &rr);
+    if (rc != HELM_OK) return rc;
+    const double g0 = std::sqrt(rr);
+    if (rel) rel[0] = 1.0;
+    int status = HELM_OK;
+    for (int k = 0; k < iters; ++k) {
+        if (!(rr > 0.0)) { if (rel) for (int q = k + 1; q <= iters; ++q) rel[q] = 0.0; break; }
+        rc = gn_hvp(st, s, p.as<double>(), hp.as<double>(), o, nullptr);
+        if (rc == HELM_E_NOT_CONVERGED) status = rc;
+        else if (rc != HELM_OK) return rc;
+        double php = 0.0;
+        if ((rc = dev_dot(p.as<double>(), hp.as<double>(), np, part, s, &php)) != HELM_OK) return rc;
+        if (!(php > 0.0)) { set_last_error("Gauss-Newton Hessian not positive along the search direction"); return HELM_E_INVALID; }
+        const double alpha = rr / php;
+        launch_axpby(alpha, p.as<double>(), 1.0, dm_dev, np, s);          // dm += alpha p
+        launch_axpby(-alpha, hp.as<double>(), 1.0, r.as<double>(), np, s); // r -= alpha H p
+        double rr_new = 0.0;
+        if ((rc = dev_dot(r.as<double>(), r.as<double>(), np, part, s, &rr_new)) != HELM_OK) return rc;
+        if (rel) rel[k + 1] = g0 > 0.0 ? std::sqrt(rr_new) / g0 : 0.0;
+        launch_axpby(1.0, r.as<double>(), rr_new / rr, p.as<double>(), np, s);   // p = r + beta p
+        rr = rr_new;
+    }
+    HELM_CUDA_TRY(cudaGetLastError());
+    HELM_CUDA_TRY(cudaStreamSynchronize(s));
+    return status;
+}
+
 void fwi_free(FwiState* st) {
     if (!st) return;
     if (st->u64) cudaFree(st->u64);

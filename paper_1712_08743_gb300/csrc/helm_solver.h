@@ -41,6 +41,12 @@ int fwi_forward(const helm_model* m, cudaStream_t s, int nfreq, const double* om
                 const helm_solve_opts& o, helm_solve_stats* stats, FwiState** out);
 int fwi_backward(FwiState* st, cudaStream_t s, double* grad_dev, const helm_solve_opts& o, helm_solve_stats* stats);
 void fwi_free(FwiState* st);
+// Gauss-Newton Hessian-vector product and step (Eq. 8 without its second term, Eq. 9); device vectors
+// of the physical model size. stats (gn_hvp): [2 nrhs], Born solves then adjoint solves.
+int gn_hvp(FwiState* st, cudaStream_t s, const double* dm_dev, double* hdm_dev, const helm_solve_opts& o,
+           helm_solve_stats* stats);
+int gn_step(FwiState* st, cudaStream_t s, const double* g_dev, int iters, double* dm_dev, double* rel,
+            const helm_solve_opts& o);
 
 int coarsest_points(const helm_model* m);
 

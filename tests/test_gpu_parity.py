@@ -233,6 +233,39 @@ def test_gradient_matches_oracle_and_differences(hg, ctx):
     model.close()
 
 
+def test_gauss_newton_product_and_step_match_oracle(hg, ctx):
+    """Eq. 8 without its second term and Eq. 9: the GPU Hessian-vector product against
+    the oracle's (and its symmetry), and a 4-iteration CG step against the oracle's."""
+    m0, h, npml, src, rec, om, d_obs = _small_fwi(2)
+    lam = 1e2
+    model = hg.helm_create_model(ctx, m0, h, npml, 0.5)
+    opts = dict(tol=1e-11)
+    J, dcal, state, _, st = hg.helm_fwi_forward(model, om, src, rec, d_obs, lam, opts)
+    assert st == hg.HELM_OK
+    g, st = hg.helm_fwi_backward(model, state, opts)
+    rng = np.random.default_rng(5)
+    x = rng.standard_normal(m0.shape) * m0
+    y = rng.standard_normal(m0.shape) * m0
+    hx, st = hg.helm_gn_hvp(model, state, x, opts)
+    assert st == hg.HELM_OK
+    hy, _ = hg.helm_gn_hvp(model, state, y, opts)
+    hx_ref = oracle.gn_hvp(m0, h, om, src, rec, lam, x, npml)
+    assert rel(hx, hx_ref) < 1e-6
+    assert abs(np.sum(x * hy) - np.sum(y * hx)) <= 1e-7 * abs(np.sum(x * hy))
+    dm, relres, st = hg.helm_gn_step(model, state, g, 4, opts)
+    dm_ref, rel_ref = oracle.gn_step(m0, h, om, src, rec, lam, g, 4, npml)
+    assert rel(dm, dm_ref) < 1e-5
+    np.testing.assert_allclose(relres, rel_ref, rtol=1e-4)
+    assert relres[-1] < relres[0]
+    # the step lowers the misfit of Eq. 4
+    m1 = hg.helm_create_model(ctx, m0 + dm, h, npml, 0.5)
+    J1 = hg.helm_adjoint_gradient(m1, om, src, rec, d_obs, lam, opts)[0]
+    m1.close()
+    assert J1 < J
+    state.close()
+    model.close()
+
+
 def test_autograd_backward_runs_adjoint(hg, ctx):
     import torch
 
