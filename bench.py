@@ -49,12 +49,14 @@ def parse():
     ap.add_argument("--restart", type=int, default=30, help="FGMRES restart length")
     ap.add_argument("--inner-tol", type=float, default=1e-1, help="mixed precision: reduction per inner solve")
     ap.add_argument("--tune", action="store_true", help="autotune the multigrid tiles before timing")
-    ap.add_argument("--workload", default="single", choices=["single", "batched", "serving"],
+    ap.add_argument("--workload", default="single", choices=["single", "batched", "serving", "gn"],
                     help="single: the single large case (the default line); batched: 64 shots x 5 "
-                         "frequencies in one call; serving: a Poisson stream of requests")
+                         "frequencies in one call; serving: a Poisson stream of requests; gn: one "
+                         "Gauss-Newton iteration of the gradient case")
     ap.add_argument("--kernels-only", action="store_true",
                     help="time only the hot kernels alone (the roofline legs), print one line per kernel")
     ap.add_argument("--requests", type=int, default=48, help="serving: number of requests")
+    ap.add_argument("--cg", type=int, default=5, help="gn: conjugate-gradient iterations per Gauss-Newton step")
     ap.add_argument("--rate", type=float, default=0.0, help="serving: arrivals per second (0: 0.8 x measured)")
     return ap.parse_args()
 
@@ -463,6 +465,61 @@ def run_batched(args):
                       "converged": all(s["converged"] for s in st)}), flush=True)
 
 
+def run_gn(args):
+    """One Gauss-Newton iteration (Eq. 9) of the gradient case: 401 x 201 smoothed
+    start model, 32 shots x 4 frequencies (3..6 Hz), 201 receivers, lambda = 1e-3;
+    forward solves and misfit, adjoint solves and gradient, then `--cg` CG
+    iterations, each one Born and one adjoint solve per shot and frequency."""
+    import torch
+
+    import oracle
+    from paper_1712_08743_gb300 import _lib, api, build
+    from synth import models
+
+    build.build()
+    _lib.load()
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    ctx = api.Context(0, stream)
+    true, start = models.c4_models()
+    om = true.omegas
+    # observed data from the true model (oracle solves; input preparation, not timed)
+    d_obs = np.stack([oracle.sample_receivers(
+        oracle.solve_fields(true.slowness, true.h, w, true.sources, true.npml, true.alpha_max), true.receivers,
+        true.npml) for w in om])
+    model = api.helm_create_model(ctx, start.slowness, start.h, start.npml, start.alpha_max)
+    opts = dict(tol=1e-6, precision="mixed")
+    lam = 1e-3
+    nrhs = len(om) * len(start.sources)
+
+    def iteration():
+        t0 = time.perf_counter()
+        J, _, state, _, _ = api.helm_fwi_forward(model, om, start.sources, start.receivers, d_obs, lam, opts)
+        t1 = time.perf_counter()
+        g, _ = api.helm_fwi_backward(model, state, opts)
+        t2 = time.perf_counter()
+        dm, rel, _ = api.helm_gn_step(model, state, g, args.cg, opts)
+        t3 = time.perf_counter()
+        state.close()
+        return J, rel, (t1 - t0, t2 - t1, t3 - t2)
+
+    for _ in range(max(args.warmup, 1)):
+        iteration()
+    times = []
+    for _ in range(max(args.steps, 1)):
+        J, rel, t = iteration()
+        times.append(t)
+    tf, tb, tg = (float(np.mean([t[k] for t in times])) for k in range(3))
+    solves = nrhs * (2 + 2 * args.cg)
+    print(json.dumps({"metric": "gauss_newton_iterations_per_s", "workload": "gradient_401x201_32shots_4f_gn",
+                      "value": 1.0 / (tf + tb + tg), "unit": "iterations/s", "steps": len(times),
+                      "cg_iters": args.cg, "solves_per_iteration": solves,
+                      "solves_per_s": solves / (tf + tb + tg), "forward_s": tf, "gradient_s": tb, "cg_s": tg,
+                      "misfit": J, "cg_relres": [float(x) for x in rel]}), flush=True)
+    model.close()
+    ctx.close()
+
+
 def run_serving(args):
     """A Poisson stream of requests of mixed grid sizes and frequencies (ten points per
     wavelength at 1500 m/s), served with continuous batching; p50/p99 latency and
@@ -517,6 +574,8 @@ def main():
         run_kernels_only(args)
     elif args.workload == "batched":
         run_batched(args)
+    elif args.workload == "gn":
+        run_gn(args)
     elif args.workload == "serving":
         run_serving(args)
     else:
