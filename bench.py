@@ -49,10 +49,10 @@ def parse():
     ap.add_argument("--restart", type=int, default=30, help="FGMRES restart length")
     ap.add_argument("--inner-tol", type=float, default=1e-1, help="mixed precision: reduction per inner solve")
     ap.add_argument("--tune", action="store_true", help="autotune the multigrid tiles before timing")
-    ap.add_argument("--workload", default="single", choices=["single", "batched", "serving", "gn"],
+    ap.add_argument("--workload", default="single", choices=["single", "batched", "serving", "gn", "ablation"],
                     help="single: the single large case (the default line); batched: 64 shots x 5 "
                          "frequencies in one call; serving: a Poisson stream of requests; gn: one "
-                         "Gauss-Newton iteration of the gradient case")
+                         "Gauss-Newton iteration of the gradient case; ablation: preconditioner on/off")
     ap.add_argument("--kernels-only", action="store_true",
                     help="time only the hot kernels alone (the roofline legs), print one line per kernel")
     ap.add_argument("--requests", type=int, default=48, help="serving: number of requests")
@@ -520,6 +520,44 @@ def run_gn(args):
     ctx.close()
 
 
+def run_ablation(args):
+    """Preconditioner ablation on the batched case's model (401 x 201 physical,
+    h = 10 m), one surface source, 3, 5 and 7 Hz: Krylov iterations and time to
+    relres 1e-6 with the shifted-Laplace multigrid preconditioner at shift
+    beta = (1, 0.5) and at the paper's (1, 1), and without a preconditioner."""
+    import torch
+
+    from paper_1712_08743_gb300 import _lib, api, build
+    from synth import models
+
+    build.build()
+    _lib.load()
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    ctx = api.Context(0, stream)
+    mdl = models.c3_model()
+    model = api.helm_create_model(ctx, mdl.slowness, mdl.h, mdl.npml, mdl.alpha_max)
+    src = mdl.sources[len(mdl.sources) // 2: len(mdl.sources) // 2 + 1]
+    kry = {"bicgstab": _lib.HELM_KRYLOV_BICGSTAB, "fgmres": _lib.HELM_KRYLOV_FGMRES}[args.krylov]
+    rows = []
+    for f_hz in (3.0, 5.0, 7.0):
+        om = np.array([2 * np.pi * f_hz])
+        for name, extra in (("MG beta=(1,0.5)", dict(beta=(1.0, 0.5))), ("MG beta=(1,1)", dict(beta=(1.0, 1.0))),
+                            ("none", dict(precond=_lib.HELM_PRECOND_NONE))):
+            opts = dict(tol=1e-6, precision="mixed", krylov=kry, restart=30, max_it=40000, **extra)
+            api.helm_solve(model, om, src, opts=opts)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            _, st, status = api.helm_solve(model, om, src, opts=opts)
+            dt = time.perf_counter() - t0
+            rows.append({"f_hz": f_hz, "preconditioner": name, "iters": st[0]["iters"], "ms": 1e3 * dt,
+                         "converged": bool(st[0]["converged"]), "relres": st[0]["relres"]})
+    print(json.dumps({"metric": "krylov_iterations", "workload": "ablation_401x201_1src_3-7Hz",
+                      "krylov": args.krylov, "rows": rows}), flush=True)
+    model.close()
+    ctx.close()
+
+
 def run_serving(args):
     """A Poisson stream of requests of mixed grid sizes and frequencies (ten points per
     wavelength at 1500 m/s), served with continuous batching; p50/p99 latency and
@@ -576,6 +614,8 @@ def main():
         run_batched(args)
     elif args.workload == "gn":
         run_gn(args)
+    elif args.workload == "ablation":
+        run_ablation(args)
     elif args.workload == "serving":
         run_serving(args)
     else:

@@ -71,11 +71,16 @@ typedef enum {
 
 typedef enum { HELM_KRYLOV_BICGSTAB = 0, HELM_KRYLOV_FGMRES = 1 } helm_krylov;
 
+/* Preconditioner of the Krylov solve: the shifted-Laplace operator M inverted
+ * approximately by one multigrid cycle, or none (plain BiCGSTAB / GMRES on
+ * Eq. 3, for the comparison the paper's examples make). */
+typedef enum { HELM_PRECOND_MG = 0, HELM_PRECOND_NONE = 1 } helm_precond;
+
 typedef struct {
     double tol;          /* stop at ||f - B u||_2 / ||f||_2 <= tol, residual formed in FP64 */
     int max_it;          /* cap on preconditioned Krylov iterations per right-hand side */
     int krylov;          /* helm_krylov */
-    int restart;         /* FGMRES restart length (<= 64) */
+    int restart;         /* FGMRES restart length (<= 32) */
     int precision;       /* helm_precision */
     double beta1;        /* shift of M: -Laplace - (beta1 - j beta2) omega^2 m^2 */
     double beta2;
@@ -85,6 +90,7 @@ typedef struct {
     int check_every;     /* host convergence poll interval, in Krylov iterations */
     int device_ptrs;     /* 1: f / u_out / gradient buffers are device pointers */
     int use_graphs;      /* 1: replay the iteration body as a CUDA graph */
+    int precond;         /* helm_precond: the shifted-Laplace multigrid (default) or none (ablation) */
 } helm_solve_opts;
 
 typedef struct {
@@ -96,7 +102,7 @@ typedef struct {
 
 /* Fills *opts with the defaults: tol 1e-6, max_it 5000, BiCGSTAB, restart 30,
  * mixed precision, beta = (1, 0.5), omega_jacobi 0.5, inner_tol 1e-2,
- * max_outer 20, check_every 10, host pointers, graphs on. */
+ * max_outer 20, check_every 10, host pointers, graphs on, multigrid preconditioner. */
 void helm_default_opts(helm_solve_opts* opts);
 
 const char* helm_strerror(int status);

@@ -22,6 +22,8 @@ HELM_E_BUSY = -6
 HELM_PREC_MIXED = 0
 HELM_PREC_FP64 = 1
 HELM_PREC_FP32 = 2
+HELM_PRECOND_MG = 0
+HELM_PRECOND_NONE = 1
 HELM_KERNEL_APPLY = 0
 HELM_KERNEL_RESTRICT = 1
 HELM_KERNEL_PROLONG = 2
@@ -48,6 +50,7 @@ class helm_solve_opts(C.Structure):
         ("check_every", C.c_int),
         ("device_ptrs", C.c_int),
         ("use_graphs", C.c_int),
+        ("precond", C.c_int),
     ]
 
 

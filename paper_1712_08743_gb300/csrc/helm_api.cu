@@ -44,6 +44,7 @@ int check_opts(const helm_solve_opts& o) {
     if (!std::isfinite(o.beta1) || !std::isfinite(o.beta2) || !(o.omega_jacobi > 0.0) || o.omega_jacobi > 2.0)
         return HELM_E_INVALID;
     if (!(o.inner_tol > 0.0) || o.inner_tol >= 1.0) return HELM_E_INVALID;
+    if (o.precond != HELM_PRECOND_MG && o.precond != HELM_PRECOND_NONE) return HELM_E_INVALID;
     return HELM_OK;
 }
 

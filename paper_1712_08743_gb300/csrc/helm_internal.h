@@ -156,6 +156,10 @@ void launch_sumsq(const double* a, size_t count, double* out, cudaStream_t s);
 template <typename T>
 void launch_apply(const LevelDev& L0, int npml, double amax, const T* hw, const T* u, T* y,
                   T scale, int nrhs, cudaStream_t s);
+// y = A u with the unpreconditioned BiCGSTAB dot products (mode 1: alpha, mode 2: omega)
+template <typename T>
+void launch_apply_dots(int mode, const LevelDev& L0, int npml, double amax, const T* hw, const T* u, T* y,
+                       const T* aux, double* partials, int pstride, RhsState* st, int nrhs, cudaStream_t s);
 
 // Outer FP64 residual r = f - A u; TI = precision of the inner right-hand side.
 template <typename TI>

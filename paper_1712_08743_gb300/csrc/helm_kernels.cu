@@ -188,6 +188,82 @@ void launch_apply(const LevelDev& L0, int npml, double amax, const T* hw, const 
 template void launch_apply<float>(const LevelDev&, int, double, const float*, const float*, float*, float, int, cudaStream_t);
 template void launch_apply<double>(const LevelDev&, int, double, const double*, const double*, double*, double, int, cudaStream_t);
 
+// y = A u with the dot products of the unpreconditioned BiCGSTAB (the
+// preconditioner-free path of the ablation): mode 1 <aux, y> -> alpha, mode 2
+// <y, u>, <y, y> -> omega, as the fused prolongation does after a cycle.
+template <typename T, int MODE>
+__global__ void __launch_bounds__(256) k_apply_dots(LevelDev L, int npml, T acoef, const T* __restrict__ hwv,
+                                                    const T* __restrict__ u, T* __restrict__ y,
+                                                    const T* __restrict__ aux, double* partials, int pstride,
+                                                    RhsState* st) {
+    __shared__ double shred[96];
+    pdl_trigger();
+    pdl_wait();
+    const int b = blockIdx.z;
+    if (!rhs_active(st, b)) return;
+    const int ix = blockIdx.x * 32 + threadIdx.x, iz = blockIdx.y * 8 + threadIdx.y;
+    const size_t n = (size_t)L.nx * L.nz;
+    T d0 = 0, d1 = 0, d2 = 0;
+    if (ix < L.nx && iz < L.nz) {
+        const T* ub = u + 2 * n * b;
+        const size_t i = (size_t)iz * L.nx + ix;
+        const T s = hwv[b] * (m2ptr<T>(L) + (size_t)b * L.mstride)[i];
+        const T a = layer_alpha_t<T>(ix, iz, L.nx, L.nz, npml, acoef);
+        const cx<T> c = ldc(ub, i);
+        cx<T> yv((T(4) - s) * c.re - s * a * c.im, (T(4) - s) * c.im + s * a * c.re);
+        if (ix > 0) yv = yv - ldc(ub, i - 1);
+        if (ix + 1 < L.nx) yv = yv - ldc(ub, i + 1);
+        if (iz > 0) yv = yv - ldc(ub, i - L.nx);
+        if (iz + 1 < L.nz) yv = yv - ldc(ub, i + L.nx);
+        stc(y + 2 * n * b, i, yv);
+        if (MODE == 1) {
+            const cx<T> q = ldc(aux + 2 * n * b, i);
+            d0 = q.re * yv.re + q.im * yv.im;
+            d1 = q.re * yv.im - q.im * yv.re;
+        } else {
+            d0 = yv.re * c.re + yv.im * c.im;
+            d1 = yv.re * c.im - yv.im * c.re;
+            d2 = yv.re * yv.re + yv.im * yv.im;
+        }
+    }
+    const T vv[3] = {d0, d1, d2};
+    double acc[3];
+    const int nblk = gridDim.x * gridDim.y, blk = blockIdx.y * gridDim.x + blockIdx.x;
+    if (last_block_reduce_t<3, T>(vv, acc, shred, partials + (size_t)b * pstride, nblk, blk, &st[b].counter[3])) {
+        if (threadIdx.x == 0 && threadIdx.y == 0) {
+            RhsState& S = st[b];
+            if (MODE == 1) {
+                const double dd = acc[0] * acc[0] + acc[1] * acc[1];
+                if (!(dd > 0.0)) {
+                    S.flag = FLAG_BREAKDOWN;
+                    S.alpha[0] = 0.0; S.alpha[1] = 0.0;
+                } else {
+                    S.alpha[0] = (S.rho[0] * acc[0] + S.rho[1] * acc[1]) / dd;
+                    S.alpha[1] = (S.rho[1] * acc[0] - S.rho[0] * acc[1]) / dd;
+                }
+            } else {
+                if (acc[2] > 0.0) { S.omega[0] = acc[0] / acc[2]; S.omega[1] = acc[1] / acc[2]; }
+                else { S.omega[0] = 0.0; S.omega[1] = 0.0; }
+            }
+        }
+    }
+}
+
+template <typename T>
+void launch_apply_dots(int mode, const LevelDev& L0, int npml, double amax, const T* hw, const T* u, T* y,
+                       const T* aux, double* partials, int pstride, RhsState* st, int nrhs, cudaStream_t s) {
+    dim3 blk(32, 8), grd((L0.nx + 31) / 32, (L0.nz + 7) / 8, nrhs);
+    const T ac = (T)layer_coef(npml, amax);
+    if (mode == 1)
+        launch_pdl(k_apply_dots<T, 1>, grd, blk, 0, s, L0, npml, ac, hw, u, y, aux, partials, pstride, st);
+    else
+        launch_pdl(k_apply_dots<T, 2>, grd, blk, 0, s, L0, npml, ac, hw, u, y, aux, partials, pstride, st);
+}
+template void launch_apply_dots<float>(int, const LevelDev&, int, double, const float*, const float*, float*,
+                                       const float*, double*, int, RhsState*, int, cudaStream_t);
+template void launch_apply_dots<double>(int, const LevelDev&, int, double, const double*, const double*, double*,
+                                        const double*, double*, int, RhsState*, int, cudaStream_t);
+
 // ======================================================= FP64 outer residual
 // r = f - A u in FP64; writes the inner right-hand side rin = r in precision TI
 // and decides, per right-hand side, whether refinement continues.

@@ -212,7 +212,9 @@ static int alloc_inner(const SolveCtx& c, Inner<T>& w) {
 
 // kernels one BiCGSTAB iteration launches: p, s and x/r updates plus two
 // preconditioner applications
-static int kernels_per_iteration(const helm_model* m, bool dbl) { return 3 + 2 * mg_kernels_per_apply(m, dbl); }
+static int kernels_per_iteration(const helm_model* m, bool dbl, int precond) {
+    return precond == HELM_PRECOND_NONE ? 5 : 3 + 2 * mg_kernels_per_apply(m, dbl);
+}
 
 template <typename T>
 static void bicg_iteration(const SolveCtx& c, Inner<T>& w) {
@@ -221,6 +223,18 @@ static void bicg_iteration(const SolveCtx& c, Inner<T>& w) {
     T *p = w.p.template as<T>(), *v = w.v.template as<T>(), *sv = w.sv.template as<T>();
     T *t = w.t.template as<T>(), *ph = w.ph.template as<T>(), *shv = w.shv.template as<T>();
     launch_bicg_p<T>(r, p, v, c.st, n, c.nrhs, c.s);
+    if (c.o.precond == HELM_PRECOND_NONE) {
+        // plain BiCGSTAB: p^ = p, s^ = s
+        const LevelDev L0 = level_dev(c.m, 0, sizeof(T) == 8);
+        const T* hw = static_cast<const T*>(sizeof(T) == 8 ? (const void*)c.w2 : (const void*)c.w2f);
+        launch_apply_dots<T>(1, L0, c.m->npml, c.m->alpha_max, hw, p, v, rh, c.partials, c.pstride, c.st, c.nrhs,
+                             c.s);
+        launch_bicg_s<T>(r, v, sv, c.st, n, c.nrhs, c.s);
+        launch_apply_dots<T>(2, L0, c.m->npml, c.m->alpha_max, hw, sv, t, nullptr, c.partials, c.pstride, c.st,
+                             c.nrhs, c.s);
+        launch_bicg_xr<T>(x, p, sv, sv, t, rh, r, c.partials, c.pstride, c.st, c.nactive, n, c.nrhs, c.s);
+        return;
+    }
     vcycle<T>(c, w, p, ph, 1, v, rh);              // p^ = V(p), v = A p^, alpha
     launch_bicg_s<T>(r, v, sv, c.st, n, c.nrhs, c.s);
     vcycle<T>(c, w, sv, shv, 2, t, nullptr);       // s^ = V(s), t = A s^, omega
@@ -264,7 +278,7 @@ static int inner_solve(const SolveCtx& c, Inner<T>& w, const T* rin, cudaGraphEx
         } else {
             for (int k = 0; k < chunk; ++k) bicg_iteration<T>(c, w);
         }
-        count_launches((unsigned long long)chunk * kernels_per_iteration(c.m, sizeof(T) == 8));
+        count_launches((unsigned long long)chunk * kernels_per_iteration(c.m, sizeof(T) == 8, c.o.precond));
         done += chunk;
         HELM_CUDA_TRY(cudaMemcpyAsync(&h_active, c.nactive, sizeof(int), cudaMemcpyDeviceToHost, c.s));
         HELM_CUDA_TRY(cudaStreamSynchronize(c.s));
@@ -320,7 +334,14 @@ static void fgmres_cycle(const SolveCtx& c, Inner<T>& w, FgBufs<T>& f, const T* 
     launch_fg_scale<T>(rin, V, c.st, f.dev, -1, n, c.nrhs, c.s);
     for (int j = 0; j < m; ++j) {
         T* Vj = V + 2 * vs * j;
-        vcycle<T>(c, w, Vj, Z + 2 * vs * j, 3, wv, nullptr);          // z_j = M^-1 v_j, w = A z_j
+        if (c.o.precond == HELM_PRECOND_NONE) {                        // z_j = v_j, w = A v_j
+            cudaMemcpyAsync(Z + 2 * vs * j, Vj, sizeof(T) * 2 * vs, cudaMemcpyDeviceToDevice, c.s);
+            launch_apply<T>(level_dev(c.m, 0, sizeof(T) == 8), c.m->npml, c.m->alpha_max,
+                            static_cast<const T*>(sizeof(T) == 8 ? (const void*)c.w2 : (const void*)c.w2f), Vj, wv,
+                            T(1), c.nrhs, c.s);
+        } else {
+            vcycle<T>(c, w, Vj, Z + 2 * vs * j, 3, wv, nullptr);        // z_j = M^-1 v_j, w = A z_j
+        }
         launch_fg_dots<T>(V, vs, wv, j, 0, c.partials, c.pstride, c.st, f.dev, n, c.nrhs, c.s);
         launch_fg_axpy<T>(V, vs, wv, j, 0, c.partials, c.pstride, c.st, f.dev, c.nactive, n, c.nrhs, c.s);
         launch_fg_dots<T>(V, vs, wv, j, 1, c.partials, c.pstride, c.st, f.dev, n, c.nrhs, c.s);
@@ -351,7 +372,7 @@ static int fgmres_inner(const SolveCtx& c, Inner<T>& w, FgBufs<T>& f, const T* r
         fgmres_cycle<T>(c, w, f, rin);
     }
     const int m = f.dev.m;
-    count_launches(4 + (unsigned long long)m * (mg_kernels_per_apply(c.m, sizeof(T) == 8) + 5));
+    count_launches(4 + (unsigned long long)m * ((c.o.precond == HELM_PRECOND_NONE ? 1 : mg_kernels_per_apply(c.m, sizeof(T) == 8)) + 5));
     HELM_CUDA_TRY(cudaGetLastError());
     *iters_done += m;
     return HELM_OK;

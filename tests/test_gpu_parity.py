@@ -95,6 +95,23 @@ def test_c1_wavefield_matches_oracle(hg, ctx, precision, tol, bound):
     model.close()
 
 
+@pytest.mark.parametrize("krylov", ["bicgstab", "fgmres"])
+def test_unpreconditioned_solve_matches_oracle(hg, ctx, krylov):
+    """The preconditioner-free path of the ablation solves the same system (more iterations)."""
+    mdl = models.c1_model()
+    model = hg.helm_create_model(ctx, mdl.slowness, mdl.h, mdl.npml, mdl.alpha_max)
+    ref = oracle.solve_fields(mdl.slowness, mdl.h, mdl.omegas[0], mdl.sources, mdl.npml, mdl.alpha_max)[0]
+    kr = hg.HELM_KRYLOV_BICGSTAB if krylov == "bicgstab" else hg.HELM_KRYLOV_FGMRES
+    u, st, status = hg.helm_solve(model, mdl.omegas, mdl.sources,
+                                  opts=dict(tol=1e-10, precision="mixed", krylov=kr, restart=30, max_it=50000,
+                                            precond=hg.HELM_PRECOND_NONE))
+    assert status == hg.HELM_OK, st
+    assert rel(u[0], ref) < 1e-6
+    _, stp, _ = hg.helm_solve(model, mdl.omegas, mdl.sources, opts=dict(tol=1e-10, precision="mixed", krylov=kr))
+    assert st[0]["iters"] > 2 * stp[0]["iters"]      # the preconditioner pays for itself
+    model.close()
+
+
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_fgmres_matches_oracle_and_bicgstab(hg, ctx, precision):
     """Flexible GMRES (restart 20) on the small case and a batched pair of the batched
