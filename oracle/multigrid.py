@@ -18,9 +18,11 @@ implements, is one multigrid cycle per application:
   interpolation; restriction is P^T (full weighting times 4).
 * Smoother: damped Jacobi (default weight 0.5), one sweep before (from a zero
   guess) and one after each coarse correction.
-* Cycle: a V-cycle on the levels above lt, the first level with at most 24576
-  nodes (lt >= 1); from lt down, an F-cycle whose second coarse correction is a
-  V-cycle; the coarsest level is solved exactly.
+* Cycle: a V-cycle on the levels above lf; from lf down, an F-cycle whose
+  second coarse correction is a V-cycle; the coarsest level is solved exactly.
+  lf (>= 1) is the first level whose spacing 2^l h gives k h >= 0.7 for the
+  shortest wavelength (h omega 2^l m_max >= 0.7: fewer than about 9 nodes per
+  wavelength), and no later than the first level with at most 24576 nodes.
 
 Operators are explicit scipy.sparse matrices (Galerkin products by sparse
 matrix multiplication), so the restatement shares nothing with the fused CUDA
@@ -102,6 +104,19 @@ def tail_level(shapes) -> int:
     return len(shapes) - 1
 
 
+FCYCLE_KH = 0.7
+
+
+def fcycle_level(shapes, hw2: float, m_max: float) -> int:
+    """First level of the F-cycle: the first l >= 1 with sqrt(hw2) 2^l m_max >= 0.7,
+    at most tail_level(shapes) (hw2 = (h omega)^2 on the finest level)."""
+    cap = tail_level(shapes)
+    for l in range(1, cap):
+        if np.sqrt(hw2) * 2.0 ** l * m_max >= FCYCLE_KH:
+            return l
+    return cap
+
+
 class VCycle:
     """One preconditioner application approximating M^{-1} for grid-scaled (h omega)^2 = hw2."""
 
@@ -110,7 +125,7 @@ class VCycle:
         self.wj = omega_jacobi
         bt = complex(beta[0], -beta[1])
         self.shapes = level_shapes(nx, nz)
-        self.lt = tail_level(self.shapes)
+        self.lt = fcycle_level(self.shapes, hw2, float(np.sqrt(np.max(m2_pad))))
         self.M = [shifted_laplacian(np.asarray(m2_pad, float), hw2, bt)]
         self.P = []
         for l, (lx, lz) in enumerate(self.shapes[:-1]):

@@ -91,6 +91,7 @@ int create_model(helm_ctx* ctx, cudaStream_t s, int Px, int Pz, double h, const 
     m->lf = L;
     for (int l = 1; l <= L; ++l)
         if (m->lv[l].n() <= (size_t)kFcycleMaxPoints) { m->lf = l; break; }
+    for (size_t i = 0; i < np * (size_t)nmodels; ++i) m->m_max = std::max(m->m_max, slowness[i]);
     for (int d = 0; d < 2; ++d) {
         const size_t cap = d ? (size_t)kTailMaxPoints64 : (size_t)kTailMaxPoints32;
         m->lt[d] = L;

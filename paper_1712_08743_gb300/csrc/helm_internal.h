@@ -17,7 +17,8 @@ namespace helm {
 
 constexpr int kCoarseMaxPoints = 128;   // coarsening stops once a level has this few nodes
 constexpr int kCoarseHardMax = 256;     // largest coarsest level the dense inverse accepts
-constexpr int kFcycleMaxPoints = 24576; // the F-cycle starts at the first level this small
+constexpr int kFcycleMaxPoints = 24576; // the F-cycle starts no later than the first level this small
+constexpr double kFcycleKh = 0.7;       // ... and at the first level where k h of the shortest wavelength reaches this
 // levels this small run in shared memory, one block per RHS (complex64 / complex128)
 constexpr int kTailMaxPoints32 = 2048;
 constexpr int kTailMaxPoints64 = 1024;
@@ -73,7 +74,8 @@ struct helm_model {
     int Px = 0, Pz = 0, npml = 0, nx = 0, nz = 0;
     double h = 0, alpha_max = 0;
     int nmodels = 1;                      // > 1: one slowness model per right-hand side (serving batches)
-    int lf = 1;                           // first level of the F-cycle (V-cycle above)
+    int lf = 1;                           // first level with at most kFcycleMaxPoints nodes (latest F-cycle start)
+    double m_max = 0;                     // largest slowness of the model(s): the shortest wavelength
     // Per precision (0: complex64, 1: complex128): first level handled by the
     // shared-memory tail kernel (>= lf), its F- and V-cycle schedules on the
     // device and its dynamic shared memory.

@@ -324,10 +324,13 @@ void launch_resid64(const LevelDev& L0, int npml, double amax, const double* w2,
 template void launch_resid64<float>(const LevelDev&, int, double, const double*, const double*, const double*, float*, double*, int, RhsState*, double, double, double, int, int, cudaStream_t);
 template void launch_resid64<double>(const LevelDev&, int, double, const double*, const double*, const double*, double*, double*, int, RhsState*, double, double, double, int, int, cudaStream_t);
 
+// u += x for the right-hand sides still refining; an inner solve whose residual
+// overflowed (a divergent unpreconditioned iteration) leaves u, the best iterate
+// so far, as it was.
 template <typename TI>
 __global__ void k_refine(const TI* __restrict__ x, double* __restrict__ u, const RhsState* st, size_t n) {
     const int b = blockIdx.z;
-    if (!st[b].outer_active) return;
+    if (!st[b].outer_active || !isfinite(st[b].rnorm2)) return;
     const TI* xb = x + 2 * n * b;
     double* ub = u + 2 * n * b;
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {

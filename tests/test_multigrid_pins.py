@@ -95,3 +95,15 @@ def test_jacobi_damps_checkerboard():
     e = ((-1.0) ** (X + Z)).ravel().astype(complex)
     e2 = e - 0.8 * (M @ e) / D       # error propagation of one sweep for M u = 0
     assert np.linalg.norm(e2) < 0.7 * np.linalg.norm(e)
+
+
+def test_fcycle_level_rule():
+    """The F-cycle starts at the first level where the shortest wavelength has
+    k h >= 0.7, never later than the node-count level: 1041^2 at h = 5 m, 15 Hz and
+    1950 m/s gives k h = 0.48 on level 1, 0.97 on level 2 and 1.93 on level 3."""
+    shapes = mg.level_shapes(1041, 1041)
+    hw2 = (5.0 * 2 * np.pi * 15.0) ** 2
+    assert mg.tail_level(shapes) == 3
+    assert mg.fcycle_level(shapes, hw2, 1 / 1950.0) == 2
+    assert mg.fcycle_level(shapes, hw2 / 100, 1 / 1950.0) == 3     # 1.5 Hz: capped by the node count
+    assert mg.fcycle_level(shapes, hw2 * 4, 1 / 1950.0) == 1        # 30 Hz: k h = 0.97 on level 1
