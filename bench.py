@@ -47,7 +47,7 @@ def parse():
     ap.add_argument("--no-fgmres", action="store_true", help="skip the FGMRES(10) leg of the single-case line")
     ap.add_argument("--krylov", default="bicgstab", choices=["bicgstab", "fgmres"])
     ap.add_argument("--restart", type=int, default=30, help="FGMRES restart length")
-    ap.add_argument("--inner-tol", type=float, default=1e-1, help="mixed precision: reduction per inner solve")
+    ap.add_argument("--inner-tol", type=float, default=5e-2, help="mixed precision: reduction per inner solve")
     ap.add_argument("--tune", action="store_true", help="autotune the multigrid tiles before timing")
     ap.add_argument("--workload", default="single", choices=["single", "batched", "serving", "gn", "ablation"],
                     help="single: the single large case (the default line); batched: 64 shots x 5 "
