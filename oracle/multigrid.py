@@ -23,8 +23,6 @@ implements, is one multigrid cycle per application:
   lf (>= 1) is the first level whose spacing 2^l h gives k h >= 0.7 for the
   shortest wavelength (h omega 2^l m_max >= 0.7: fewer than about 9 nodes per
   wavelength), and no later than the first level with at most 24576 nodes.
-  Levels below lf whose k h reaches 4 (dominated by the mass term) take
-  V-cycles again.
 
 Operators are explicit scipy.sparse matrices (Galerkin products by sparse
 matrix multiplication), so the restatement shares nothing with the fused CUDA
@@ -119,17 +117,6 @@ def fcycle_level(shapes, hw2: float, m_max: float) -> int:
     return cap
 
 
-FCYCLE_KH_END = 4.0
-
-
-def fcycle_end(shapes, hw2: float, m_max: float, lf: int) -> int:
-    """First level below lf where k h reaches 4 (V-cycles from there); len(shapes) if none."""
-    for l in range(lf + 1, len(shapes)):
-        if np.sqrt(hw2) * 2.0 ** l * m_max >= FCYCLE_KH_END:
-            return l
-    return len(shapes)
-
-
 class VCycle:
     """One preconditioner application approximating M^{-1} for grid-scaled (h omega)^2 = hw2."""
 
@@ -138,9 +125,7 @@ class VCycle:
         self.wj = omega_jacobi
         bt = complex(beta[0], -beta[1])
         self.shapes = level_shapes(nx, nz)
-        m_max = float(np.sqrt(np.max(m2_pad)))
-        self.lt = fcycle_level(self.shapes, hw2, m_max)
-        self.fend = fcycle_end(self.shapes, hw2, m_max, self.lt)
+        self.lt = fcycle_level(self.shapes, hw2, float(np.sqrt(np.max(m2_pad))))
         self.M = [shifted_laplacian(np.asarray(m2_pad, float), hw2, bt)]
         self.P = []
         for l, (lx, lz) in enumerate(self.shapes[:-1]):
@@ -157,8 +142,6 @@ class VCycle:
         D = M.diagonal()
         u = self.wj * f / D
         sub = "F" if kind == "F" else ("F" if level + 1 == self.lt else "V")
-        if level + 1 >= self.fend:
-            sub = "V"
         u = u + P @ self.cycle(P.T @ (f - M @ u), level + 1, sub)
         if kind == "F":
             u = u + P @ self.cycle(P.T @ (f - M @ u), level + 1, "V")

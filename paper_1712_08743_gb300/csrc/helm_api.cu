@@ -116,17 +116,28 @@ int create_model(helm_ctx* ctx, cudaStream_t s, int Px, int Pz, double h, const 
         if ((e = cudaMalloc(&Lv.gkf, sizeof(float) * kGalerkinCoefs * Lv.n() * nmodels)) != cudaSuccess) return fail(e);
         if ((e = cudaMalloc(&Lv.gkd, sizeof(double) * kGalerkinCoefs * Lv.n() * nmodels)) != cudaSuccess) return fail(e);
     }
-    for (int d = 0; d < 2; ++d)
-        if (tail_schedule(m->lt[d], L, true, L + 1).size() > (size_t)kMaxTailOps) {
-            set_last_error("tail schedule too long");
-            helm_destroy_model(m);
-            return HELM_E_INVALID;
-        }
+    std::vector<int> opsf[2], opsv[2];
+    for (int d = 0; d < 2; ++d) {
+        opsf[d] = tail_schedule(m->lt[d], L, true);
+        opsv[d] = tail_schedule(m->lt[d], L, false);
+        m->nops_f[d] = (int)opsf[d].size();
+        m->nops_v[d] = (int)opsv[d].size();
+        if ((e = cudaMalloc(&m->ops_f[d], sizeof(int) * opsf[d].size())) != cudaSuccess) return fail(e);
+        if ((e = cudaMalloc(&m->ops_v[d], sizeof(int) * opsv[d].size())) != cudaSuccess) return fail(e);
+    }
     DevMem phys, msq;
     if ((e = cudaMalloc(&phys.p, sizeof(double) * np * nmodels)) != cudaSuccess) return fail(e);
     if ((e = cudaMalloc(&msq.p, sizeof(double))) != cudaSuccess) return fail(e);
     if ((e = cudaMemcpyAsync(phys.p, slowness, sizeof(double) * np * nmodels, cudaMemcpyHostToDevice, s)) != cudaSuccess)
         return fail(e);
+    for (int d = 0; d < 2; ++d) {
+        if ((e = cudaMemcpyAsync(m->ops_f[d], opsf[d].data(), sizeof(int) * opsf[d].size(), cudaMemcpyHostToDevice, s)) !=
+            cudaSuccess)
+            return fail(e);
+        if ((e = cudaMemcpyAsync(m->ops_v[d], opsv[d].data(), sizeof(int) * opsv[d].size(), cudaMemcpyHostToDevice, s)) !=
+            cudaSuccess)
+            return fail(e);
+    }
     launch_pad_model(static_cast<double*>(phys.p), Px, Pz, npml, nmodels, m->m_pad, m->lv[0].m2f, m->lv[0].m2d, s);
     for (int l = 1; l <= L; ++l) launch_galerkin(m, l, s);
     launch_sumsq(static_cast<double*>(phys.p), np, static_cast<double*>(msq.p), s);
@@ -218,6 +229,10 @@ void helm_destroy_model(helm_model* m) {
     if (!m) return;
     DeviceGuard g(m->ctx->device);
     if (m->m_pad) cudaFree(m->m_pad);
+    for (int d = 0; d < 2; ++d) {
+        if (m->ops_f[d]) cudaFree(m->ops_f[d]);
+        if (m->ops_v[d]) cudaFree(m->ops_v[d]);
+    }
     for (auto& L : m->lv) {
         if (L.m2f) cudaFree(L.m2f);
         if (L.m2d) cudaFree(L.m2d);

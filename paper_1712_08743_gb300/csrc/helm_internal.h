@@ -18,13 +18,11 @@ namespace helm {
 constexpr int kCoarseMaxPoints = 128;   // coarsening stops once a level has this few nodes
 constexpr int kCoarseHardMax = 256;     // largest coarsest level the dense inverse accepts
 constexpr int kFcycleMaxPoints = 24576; // the F-cycle starts no later than the first level this small
-constexpr double kFcycleKh = 0.7;       // ... and at the first level where k h of the shortest wavelength reaches this;
-constexpr double kFcycleKhEnd = 4.0;    // levels with k h at least this (mass-dominated) take V-cycles again
+constexpr double kFcycleKh = 0.7;       // ... and at the first level where k h of the shortest wavelength reaches this
 // levels this small run in shared memory, one block per RHS (complex64 / complex128)
 constexpr int kTailMaxPoints32 = 2048;
 constexpr int kTailMaxPoints64 = 1024;
 constexpr int kMaxLevels = 24;
-constexpr int kMaxTailOps = 256;        // longest tail schedule (an F-cycle over 6 levels has 113 operations)
 constexpr int kMaxRestart = 32;
 constexpr int kFgPartials = 16 * 5 * 512;   // FGMRES dot partials per RHS (2 x 8 values x 5 chunks x 512 blocks)
 constexpr int kGalerkinCoefs = 10;      // per coarse node: G (c, e, n, ne, nw) then K (c, e, n, ne, nw)
@@ -79,8 +77,12 @@ struct helm_model {
     int lf = 1;                           // first level with at most kFcycleMaxPoints nodes (latest F-cycle start)
     double m_max = 0;                     // largest slowness of the model(s): the shortest wavelength
     // Per precision (0: complex64, 1: complex128): first level handled by the
-    // shared-memory tail kernel (>= lf) and its dynamic shared memory.
+    // shared-memory tail kernel (>= lf), its F- and V-cycle schedules on the
+    // device and its dynamic shared memory.
     int lt[2] = {1, 1};
+    int* ops_f[2] = {nullptr, nullptr};
+    int* ops_v[2] = {nullptr, nullptr};
+    int nops_f[2] = {0, 0}, nops_v[2] = {0, 0};
     size_t tail_smem[2] = {0, 0};
     // complex64 tile choices per level (0 smaller, 1 larger tiles; see the launchers),
     // set by helm_autotune / helm_set_tiles
@@ -123,7 +125,7 @@ inline LevelDev level_dev(const helm_model* m, int l, bool dbl) {
 // Tail schedule entries: op type in the low byte, level above it.
 enum TailOp : int { OP_SMOOTH0 = 0, OP_RESID = 1, OP_RESTRICT = 2, OP_PROLONG_ADD = 3, OP_JACOBI = 4,
                     OP_COARSE = 5, OP_OUTPUT = 6, OP_LOAD = 7 };
-std::vector<int> tail_schedule(int lt, int L, bool fcycle, int fend);
+std::vector<int> tail_schedule(int lt, int L, bool fcycle);
 size_t tail_smem_bytes(const helm_model* m, int lt, size_t elem, bool* minv_smem = nullptr, int* minv_off = nullptr);
 
 // Arguments of the tail kernel: levels lt..L of the cycle for one RHS per
@@ -136,8 +138,8 @@ struct TailArgs {
     int accumulate;           // 1: out += correction
     const void* minv;         // dense coarsest inverses [nslots][nL][nL]
     const int* slot;
+    const int* ops;
     int nops;
-    int ops[kMaxTailOps];     // the schedule (tail_schedule), passed by value
     int minv_smem;            // 1: the coarsest inverse is staged in shared memory at minv_off
     int minv_off;
     int off[kMaxLevels];      // level l's arrays in shared memory (complex elements), l = lt..L

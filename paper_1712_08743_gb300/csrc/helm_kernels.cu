@@ -1731,7 +1731,7 @@ template void launch_tail<double>(const TailArgs&, size_t, int, const RhsState*,
 
 // Schedule of the tail: LOAD the right-hand side of level lt, an F-cycle (whose
 // second coarse correction is a V-cycle) or a V-cycle from lt, OUTPUT.
-std::vector<int> tail_schedule(int lt, int L, bool fcycle, int fend) {
+std::vector<int> tail_schedule(int lt, int L, bool fcycle) {
     std::vector<int> ops;
     auto put = [&](int type, int l) { ops.push_back(type | (l << 8)); };
     std::function<void(int)> V = [&](int l) {
@@ -1743,13 +1743,13 @@ std::vector<int> tail_schedule(int lt, int L, bool fcycle, int fend) {
     std::function<void(int)> F = [&](int l) {
         if (l == L) { put(OP_COARSE, l); return; }
         put(OP_SMOOTH0, l); put(OP_RESID, l); put(OP_RESTRICT, l);
-        if (l + 1 < fend) F(l + 1); else V(l + 1);
+        F(l + 1);
         put(OP_PROLONG_ADD, l); put(OP_RESID, l); put(OP_RESTRICT, l);
         V(l + 1);
         put(OP_PROLONG_ADD, l); put(OP_RESID, l); put(OP_JACOBI, l);
     };
     put(OP_LOAD, lt);
-    if (fcycle && lt < fend) F(lt); else V(lt);
+    if (fcycle) F(lt); else V(lt);
     put(OP_OUTPUT, lt);
     return ops;
 }

@@ -129,7 +129,7 @@ extern "C" int helm_vcycle_noalloc(helm_model* m, int nrhs, const double* omega,
         mc.wj = omega_jacobi;
         mc.st = nullptr;
         mc.nrhs = nrhs;
-        fcycle_levels(m, hw2, nrhs, &mc.lf, &mc.fend);
+        mc.lf = fcycle_level(m, hw2, nrhs);
         mc.s = s;
         mc.minv = base + o_mf;
         mc.slot = reinterpret_cast<const int*>(base + o_slot);

@@ -90,7 +90,7 @@ struct SolveCtx {
     const int* slot;        // device [nrhs]
     int ncoarse;
     const void* minv;       // float2* or double2* [nslots][n][n]
-    int lf, fend;           // F-cycle on levels lf .. fend - 1 for this batch
+    int lf;                 // first level of the F-cycle for this batch
 };
 
 template <typename T>
@@ -114,9 +114,8 @@ static void mg_cycle(const helm_model* m, const MgCall& c, const MgLevels<T>& B,
         a.accumulate = acc;
         a.minv = c.minv;
         a.slot = c.slot;
-        const std::vector<int> ops = tail_schedule(lt, a.L, F, c.fend);
-        a.nops = (int)std::min<size_t>(ops.size(), kMaxTailOps);   // model setup checks the longest schedule fits
-        std::copy(ops.begin(), ops.begin() + a.nops, a.ops);
+        a.ops = F ? m->ops_f[dbl] : m->ops_v[dbl];
+        a.nops = F ? m->nops_f[dbl] : m->nops_v[dbl];
         bool ms = false;
         tail_smem_bytes(m, lt, sizeof(T), &ms, &a.minv_off);
         a.minv_smem = ms ? 1 : 0;
@@ -130,7 +129,7 @@ static void mg_cycle(const helm_model* m, const MgCall& c, const MgLevels<T>& B,
     }
     const LevelDev Lf = level_dev(m, l, dbl), Lc = level_dev(m, l + 1, dbl);
     launch_restrict<T>(Lf, Lc, hw, c.b1, c.b2, c.wj, B.f[l], B.f[l + 1], c.st, c.nrhs, c.s, m->tile_restrict[l]);
-    mg_cycle<T>(m, c, B, l + 1, (F || l + 1 == c.lf) && l + 1 < c.fend, 0);
+    mg_cycle<T>(m, c, B, l + 1, F || (l + 1 == c.lf), 0);
     if (F) {
         launch_correct_restrict<T>(Lf, Lc, hw, c.b1, c.b2, c.wj, B.f[l], B.e[l + 1], B.f[l + 1], c.st, c.nrhs, c.s,
                                    m->tile_restrict[l]);
@@ -147,7 +146,7 @@ void mg_apply(const helm_model* m, const MgCall& c, const MgLevels<T>& B, const 
     const T* hw = hw_of<T>(c);
     const LevelDev L0 = level_dev(m, 0, dbl), L1 = level_dev(m, 1, dbl);
     launch_restrict<T>(L0, L1, hw, c.b1, c.b2, c.wj, in, B.f[1], c.st, c.nrhs, c.s);
-    mg_cycle<T>(m, c, B, 1, c.lf == 1 && 1 < c.fend, 0);
+    mg_cycle<T>(m, c, B, 1, c.lf == 1, 0);
     launch_prolong<T>(mode, L0, L1, m->npml, m->alpha_max, hw, c.b1, c.b2, c.wj, in, B.e[1], out, y, aux,
                       c.partials, c.pstride, c.st, c.nrhs, c.s, 0, m->tile_prolong[0]);
 }
@@ -156,28 +155,23 @@ template void mg_apply<float>(const helm_model*, const MgCall&, const MgLevels<f
 template void mg_apply<double>(const helm_model*, const MgCall&, const MgLevels<double>&, const double*, double*, int,
                                double*, const double*);
 
-static int count_cycle(const helm_model* m, int lt, int l, bool F, int lf, int fend) {
+static int count_cycle(const helm_model* m, int lt, int l, bool F, int lf) {
     if (l >= lt) return 1;
-    int k = 2 + count_cycle(m, lt, l + 1, (F || l + 1 == lf) && l + 1 < fend, lf, fend);
-    if (F) k += 1 + count_cycle(m, lt, l + 1, false, lf, fend);
+    int k = 2 + count_cycle(m, lt, l + 1, F || (l + 1 == lf), lf);
+    if (F) k += 1 + count_cycle(m, lt, l + 1, false, lf);
     return k;
 }
-int mg_kernels_per_apply(const helm_model* m, bool dbl, int lf, int fend) {
-    return 2 + count_cycle(m, m->tail_level(dbl), 1, lf == 1 && 1 < fend, lf, fend);
+int mg_kernels_per_apply(const helm_model* m, bool dbl, int lf) {
+    return 2 + count_cycle(m, m->tail_level(dbl), 1, lf == 1, lf);
 }
 
-void fcycle_levels(const helm_model* m, const double* h_w2, int nrhs, int* lf, int* fend) {
+int fcycle_level(const helm_model* m, const double* h_w2, int nrhs) {
     double w = INFINITY;
     for (int b = 0; b < nrhs; ++b) w = std::min(w, h_w2[b]);
     const double hw = std::sqrt(std::max(w, 0.0));   // h omega_min on the finest level
-    const int L = (int)m->lv.size() - 1;
-    auto kh = [&](int l) { return hw * std::ldexp(1.0, l) * m->m_max; };
-    *lf = m->lf;
     for (int l = 1; l < m->lf; ++l)
-        if (kh(l) >= kFcycleKh) { *lf = l; break; }
-    *fend = L + 1;
-    for (int l = *lf + 1; l <= L; ++l)
-        if (kh(l) >= kFcycleKhEnd) { *fend = l; break; }
+        if (hw * std::ldexp(1.0, l) * m->m_max >= kFcycleKh) return l;
+    return m->lf;
 }
 
 template <typename T>
@@ -191,7 +185,6 @@ static void vcycle(const SolveCtx& c, Inner<T>& w, const T* in, T* out, int mode
     mc.st = c.st;
     mc.nrhs = c.nrhs;
     mc.lf = c.lf;
-    mc.fend = c.fend;
     mc.s = c.s;
     mc.minv = c.minv;
     mc.slot = c.slot;
@@ -232,8 +225,8 @@ static int alloc_inner(const SolveCtx& c, Inner<T>& w) {
 
 // kernels one BiCGSTAB iteration launches: p, s and x/r updates plus two
 // preconditioner applications
-static int kernels_per_iteration(const helm_model* m, bool dbl, int precond, int lf, int fend) {
-    return precond == HELM_PRECOND_NONE ? 5 : 3 + 2 * mg_kernels_per_apply(m, dbl, lf, fend);
+static int kernels_per_iteration(const helm_model* m, bool dbl, int precond, int lf) {
+    return precond == HELM_PRECOND_NONE ? 5 : 3 + 2 * mg_kernels_per_apply(m, dbl, lf);
 }
 
 template <typename T>
@@ -298,7 +291,7 @@ static int inner_solve(const SolveCtx& c, Inner<T>& w, const T* rin, cudaGraphEx
         } else {
             for (int k = 0; k < chunk; ++k) bicg_iteration<T>(c, w);
         }
-        count_launches((unsigned long long)chunk * kernels_per_iteration(c.m, sizeof(T) == 8, c.o.precond, c.lf, c.fend));
+        count_launches((unsigned long long)chunk * kernels_per_iteration(c.m, sizeof(T) == 8, c.o.precond, c.lf));
         done += chunk;
         HELM_CUDA_TRY(cudaMemcpyAsync(&h_active, c.nactive, sizeof(int), cudaMemcpyDeviceToHost, c.s));
         HELM_CUDA_TRY(cudaStreamSynchronize(c.s));
@@ -392,7 +385,7 @@ static int fgmres_inner(const SolveCtx& c, Inner<T>& w, FgBufs<T>& f, const T* r
         fgmres_cycle<T>(c, w, f, rin);
     }
     const int m = f.dev.m;
-    count_launches(4 + (unsigned long long)m * ((c.o.precond == HELM_PRECOND_NONE ? 1 : mg_kernels_per_apply(c.m, sizeof(T) == 8, c.lf, c.fend)) + 5));
+    count_launches(4 + (unsigned long long)m * ((c.o.precond == HELM_PRECOND_NONE ? 1 : mg_kernels_per_apply(c.m, sizeof(T) == 8, c.lf)) + 5));
     HELM_CUDA_TRY(cudaGetLastError());
     *iters_done += m;
     return HELM_OK;
@@ -454,7 +447,7 @@ static int solve_impl(const helm_model* m, cudaStream_t s, int nrhs, const doubl
     c.o = o;
     c.pstride = 3 * max_blocks_per_rhs(m);
     if (o.krylov == HELM_KRYLOV_FGMRES) c.pstride = std::max(c.pstride, kFgPartials);
-    fcycle_levels(m, h_w2, nrhs, &c.lf, &c.fend);
+    c.lf = fcycle_level(m, h_w2, nrhs);
     DBuf w2, w2f, st, part, nact, rin;
     TRY_ALLOC(w2, sizeof(double) * nrhs, s);
     TRY_ALLOC(w2f, sizeof(float) * nrhs, s);
@@ -570,7 +563,7 @@ int vcycle_once(const helm_model* m, cudaStream_t s, int nrhs, const double* h_w
     c.o.beta2 = b2;
     c.o.omega_jacobi = wj;
     c.pstride = 3 * max_blocks_per_rhs(m);
-    fcycle_levels(m, h_w2, nrhs, &c.lf, &c.fend);
+    c.lf = fcycle_level(m, h_w2, nrhs);
     DBuf w2, w2f;
     TRY_ALLOC(w2, sizeof(double) * nrhs, s);
     TRY_ALLOC(w2f, sizeof(float) * nrhs, s);

@@ -65,18 +65,14 @@ struct MgCall {
     const int* slot;
     double* partials;       // finest-level dot reductions (modes 1, 2)
     int pstride;
-    int lf;                 // first level of the F-cycle (fcycle_levels)
-    int fend;               // first level below lf that takes V-cycles again
+    int lf;                 // first level of the F-cycle (fcycle_level)
 };
 // First level of the F-cycle for a batch with grid-scaled (h omega_b)^2 = h_w2[b]:
 // the first level l >= 1 whose spacing 2^l h gives k h >= kFcycleKh for the
 // shortest wavelength of the lowest frequency (omega_min 2^l h m_max >= 0.7,
 // fewer than about 9 nodes per wavelength), and no later than the first level
 // with at most kFcycleMaxPoints nodes.
-// fend: the first level whose k h for that wavelength reaches kFcycleKhEnd (4):
-// from there down the cycle is a V-cycle again (those levels are dominated by
-// the mass term, where damped Jacobi alone is a good solver); L + 1 if none.
-void fcycle_levels(const helm_model* m, const double* h_w2, int nrhs, int* lf, int* fend);
+int fcycle_level(const helm_model* m, const double* h_w2, int nrhs);
 template <typename T>
 struct MgLevels {
     T* f[kMaxLevels];
@@ -85,7 +81,7 @@ struct MgLevels {
 template <typename T>
 void mg_apply(const helm_model* m, const MgCall& c, const MgLevels<T>& B, const T* in, T* out, int mode, T* y,
               const T* aux);
-int mg_kernels_per_apply(const helm_model* m, bool dbl, int lf, int fend);
+int mg_kernels_per_apply(const helm_model* m, bool dbl, int lf);
 
 int autotune(helm_model* m, cudaStream_t s, int nrhs, double hw2, int reps, int* out);
 int time_kernel(const helm_model* m, cudaStream_t s, int kernel, int nrhs, double hw2, int reps, double* ms,

@@ -107,6 +107,3 @@ def test_fcycle_level_rule():
     assert mg.fcycle_level(shapes, hw2, 1 / 1950.0) == 2
     assert mg.fcycle_level(shapes, hw2 / 100, 1 / 1950.0) == 3     # 1.5 Hz: capped by the node count
     assert mg.fcycle_level(shapes, hw2 * 4, 1 / 1950.0) == 1        # 30 Hz: k h = 0.97 on level 1
-    # V-cycles again from the first level below lf with k h >= 4: level 5 (k h = 7.7)
-    assert mg.fcycle_end(shapes, hw2, 1 / 1950.0, 2) == 5
-    assert mg.fcycle_end(shapes, hw2 / 100, 1 / 1950.0, 3) == len(shapes)
