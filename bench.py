@@ -35,6 +35,8 @@ sys.path.insert(0, ROOT)
 
 WORKLOAD = "single_large_1001x1001_h5m_15Hz_layered12_anom3_seed2_mixed_tol1e-6"
 L2_BYTES = 129 * 2 ** 20
+REORTH = {"always": 0, "never": 1, "ifneeded": 2}        # helm_reorth
+GS_NAME = {"always": "CGS2", "never": "CGS", "ifneeded": "CGS + DGKS second pass"}
 
 
 def parse():
@@ -50,6 +52,8 @@ def parse():
                     help="Krylov method (default: FGMRES(10) for the single case, the paper's engine, with "
                          "BiCGSTAB timed beside it; BiCGSTAB for the batched and ablation workloads)")
     ap.add_argument("--restart", type=int, default=10, help="FGMRES restart length")
+    ap.add_argument("--reorth", default="never", choices=["always", "never", "ifneeded"],
+                    help="FGMRES Gram-Schmidt: second pass always (CGS2), never, or by the DGKS test")
     ap.add_argument("--inner-tol", type=float, default=5e-2, help="mixed precision: reduction per inner solve")
     ap.add_argument("--tune", action="store_true", help="autotune the multigrid tiles before timing")
     ap.add_argument("--workload", default="single", choices=["single", "batched", "serving", "gn", "ablation"],
@@ -271,8 +275,9 @@ def run_ours(args):
     n = model.n
     om = mdl.omegas
     kry = {"bicgstab": _lib.HELM_KRYLOV_BICGSTAB, "fgmres": _lib.HELM_KRYLOV_FGMRES}[args.krylov]
+    ro = REORTH[args.reorth]
     opts = api.helm_default_opts(tol=1e-6, precision="mixed", krylov=kry, restart=args.restart,
-                                 inner_tol=args.inner_tol, max_it=20000)
+                                 inner_tol=args.inner_tol, max_it=20000, reorth=ro)
     if args.tune:
         from paper_1712_08743_gb300 import autotune
         autotune.autotune(model, 1, float(om[0]))
@@ -331,7 +336,8 @@ def run_ours(args):
     # plain FP64 GPU solve of the same problem (the baseline the precision split must beat)
     fp64 = None
     if not args.no_fp64:
-        o64 = api.helm_default_opts(tol=1e-6, precision="fp64", krylov=kry, restart=args.restart, max_it=20000)
+        o64 = api.helm_default_opts(tol=1e-6, precision="fp64", krylov=kry, restart=args.restart, max_it=20000,
+                                    reorth=ro)
         step(o64)
         t64 = []
         its64 = None
@@ -356,8 +362,8 @@ def run_ours(args):
             alt_name = f"BiCGSTAB (inner reduction {args.inner_tol:g})"
         else:
             oalt = api.helm_default_opts(tol=1e-6, precision="mixed", krylov=_lib.HELM_KRYLOV_FGMRES, restart=10,
-                                         max_it=20000)
-            alt_name = "FGMRES(10)"
+                                         max_it=20000, reorth=ro)
+            alt_name = f"FGMRES(10, {GS_NAME[args.reorth]})"
         step(oalt)
         talt = []
         stalt = None
@@ -408,8 +414,10 @@ def run_ours(args):
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "grid": f"{model.nx}x{model.nz} padded ({mdl.Px}x{mdl.Pz} physical)",
                        "unknowns": n, "precision": "complex64 inner, FP64 residual/refinement",
-                       "krylov": ("BiCGSTAB" if args.krylov == "bicgstab" else f"FGMRES({args.restart})") +
-                                 " + shifted-Laplace Galerkin MG (V above the tail level, F below), beta=(1,0.5)",
+                       "krylov": ("BiCGSTAB" if args.krylov == "bicgstab" else
+                                  f"FGMRES({args.restart}, {GS_NAME[args.reorth]})") +
+                                 " + shifted-Laplace Galerkin MG (V-cycle above the first level where k h of the "
+                                 "shortest wavelength reaches 0.7, F-cycle from there), beta=(1,0.5)",
                        "inner_tol": args.inner_tol, "restart": args.restart if args.krylov == "fgmres" else None,
                        "levels": model.nlevels, "l2": "flushed between timed steps (258 MB write)",
                        "parallelism": f"replicas x{world}"},
@@ -580,7 +588,7 @@ def run_serving(args):
     build.build()
     ctx = api.Context(0)
     reqs = [models.c5_request(i, sizes=(128, 256, 512)) for i in range(args.requests)]
-    opts = dict(tol=1e-6, precision="mixed", krylov=_lib.HELM_KRYLOV_FGMRES, max_it=20000)
+    opts = dict(tol=1e-6, precision="mixed", krylov=_lib.HELM_KRYLOV_FGMRES, max_it=20000, reorth=REORTH[args.reorth])
     # sequential plain FP64 on a subset
     o64 = dict(tol=1e-6, precision="fp64", max_it=20000)
     t_seq = []

@@ -76,6 +76,14 @@ typedef enum { HELM_KRYLOV_BICGSTAB = 0, HELM_KRYLOV_FGMRES = 1 } helm_krylov;
  * Eq. 3, for the comparison the paper's examples make). */
 typedef enum { HELM_PRECOND_MG = 0, HELM_PRECOND_NONE = 1 } helm_precond;
 
+/* Gram-Schmidt of the FGMRES Arnoldi step (classical, on the stored basis):
+ * a second pass on every step (CGS2), none (one pass), or a second pass only
+ * where the first removed more than 1 - 1/sqrt(2) of the new vector's norm
+ * (the Daniel-Gragg-Kaufman-Stewart test). The FP64 outer refinement recomputes
+ * the true residual after every cycle, so one pass only loses inner accuracy
+ * where the basis loses orthogonality within a cycle. */
+typedef enum { HELM_REORTH_ALWAYS = 0, HELM_REORTH_NEVER = 1, HELM_REORTH_IFNEEDED = 2 } helm_reorth;
+
 typedef struct {
     double tol;          /* stop at ||f - B u||_2 / ||f||_2 <= tol, residual formed in FP64 */
     int max_it;          /* cap on preconditioned Krylov iterations per right-hand side */
@@ -91,6 +99,7 @@ typedef struct {
     int device_ptrs;     /* 1: f / u_out / gradient buffers are device pointers */
     int use_graphs;      /* 1: replay the iteration body as a CUDA graph */
     int precond;         /* helm_precond: the shifted-Laplace multigrid (default) or none (ablation) */
+    int reorth;          /* helm_reorth: FGMRES Gram-Schmidt passes (default HELM_REORTH_ALWAYS) */
 } helm_solve_opts;
 
 typedef struct {
@@ -102,7 +111,8 @@ typedef struct {
 
 /* Fills *opts with the defaults: tol 1e-6, max_it 5000, BiCGSTAB, restart 30,
  * mixed precision, beta = (1, 0.5), omega_jacobi 0.5, inner_tol 1e-2,
- * max_outer 20, check_every 10, host pointers, graphs on, multigrid preconditioner. */
+ * max_outer 20, check_every 10, host pointers, graphs on, multigrid preconditioner,
+ * two Gram-Schmidt passes. */
 void helm_default_opts(helm_solve_opts* opts);
 
 const char* helm_strerror(int status);

@@ -24,6 +24,9 @@ HELM_PREC_FP64 = 1
 HELM_PREC_FP32 = 2
 HELM_PRECOND_MG = 0
 HELM_PRECOND_NONE = 1
+HELM_REORTH_ALWAYS = 0
+HELM_REORTH_NEVER = 1
+HELM_REORTH_IFNEEDED = 2
 HELM_KERNEL_APPLY = 0
 HELM_KERNEL_RESTRICT = 1
 HELM_KERNEL_PROLONG = 2
@@ -51,6 +54,7 @@ class helm_solve_opts(C.Structure):
         ("device_ptrs", C.c_int),
         ("use_graphs", C.c_int),
         ("precond", C.c_int),
+        ("reorth", C.c_int),
     ]
 
 

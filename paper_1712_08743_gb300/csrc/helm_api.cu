@@ -45,6 +45,7 @@ int check_opts(const helm_solve_opts& o) {
         return HELM_E_INVALID;
     if (!(o.inner_tol > 0.0) || o.inner_tol >= 1.0) return HELM_E_INVALID;
     if (o.precond != HELM_PRECOND_MG && o.precond != HELM_PRECOND_NONE) return HELM_E_INVALID;
+    if (o.reorth < HELM_REORTH_ALWAYS || o.reorth > HELM_REORTH_IFNEEDED) return HELM_E_INVALID;
     return HELM_OK;
 }
 

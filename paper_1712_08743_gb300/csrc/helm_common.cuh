@@ -94,6 +94,7 @@ struct RhsState {
     int outer_active;    // 1 while the outer refinement continues
     int max_it;
     int kfg;             // FGMRES: Arnoldi steps of the current cycle
+    int reorth;          // FGMRES: 1 if the current column takes a second Gram-Schmidt pass
     unsigned int counter[4];  // last-block election counters, one per reduction site
 };
 

@@ -3,25 +3,52 @@
 //
 // One call of the inner solver runs one FGMRES cycle of at most m Arnoldi steps
 // from a zero guess; restarts happen through the FP64 outer refinement, which
-// recomputes the true residual. The Arnoldi vectors are orthogonalised by
-// classical Gram-Schmidt with one reorthogonalisation (CGS2); dot products
-// accumulate per block in FP64 and the small Hessenberg least-squares problem
-// (Givens rotations, back substitution) is solved in FP64 on the device.
+// recomputes the true residual. The basis is stored unnormalised: V'_i = s_i V_i
+// with V_i orthonormal and s_i kept in FP64 (s_0 = 1), so A Z'_j is written
+// straight into slot j+1 and orthogonalised there, and no scaling pass is
+// needed. With Z_j = Z'_j / s_j the Arnoldi relation A Z_j = sum_i h_ij V_i holds
+// for h_ij = <V'_i, A Z'_j> / (s_i s_j) and h_{j+1,j} = s_{j+1} / s_j; the
+// correction is x = sum_j (y_j / s_j) Z'_j. Gram-Schmidt is classical, with a
+// second pass always (CGS2), never, or when the first pass removed more than
+// 1 - 1/sqrt(2) of the vector's norm (the Daniel-Gragg-Kaufman-Stewart test).
+// Dot products accumulate per block in FP64 and the small Hessenberg
+// least-squares problem (Givens rotations, back substitution) is solved in FP64
+// on the device.
 #include "helm_internal.h"
 
 namespace helm {
 
 namespace {
-inline int grid1d_fg(size_t n) {
-    size_t g = (n + 1023) / 1024;
-    if (g < 1) g = 1;
-    if (g > 512) g = 512;
-    return (int)g;
+constexpr int kChunk = 8;                                          // Arnoldi vectors per block in the dot products
+constexpr int kMaxChunks = (kMaxRestart - 1 + kChunk) / kChunk;     // chunks of the longest basis
+constexpr int kFgMaxBlocks = 1024;                                 // blocks per RHS (and chunk)
+
+// Blocks per RHS of a grid-stride kernel: about two points per thread, at most
+// one wave of the kernel's resident blocks on every SM.
+template <auto Kernel>
+int fg_grid(size_t n) {
+    static int per_sm = 0;
+    if (per_sm == 0) {
+        int nb = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, Kernel, 256, 0);
+        per_sm = nb > 0 ? nb : 1;
+    }
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const size_t cap = std::min<size_t>(kFgMaxBlocks, (size_t)std::max(1, per_sm * sms));
+    return (int)std::max<size_t>(1, std::min<size_t>((n + 511) / 512, cap));
 }
-constexpr int kChunk = 8;   // Arnoldi vectors per block in the dot-product kernel
 }  // namespace
 
-// ||rin||; beta = g[0]; the RHS iterates if its outer step is active and rin != 0.
+// Partials per RHS that the FGMRES kernels need on n points: 2 kChunk + 1 sums
+// per block and chunk in the dot products, the most of any of them.
+int fg_partials(size_t n) {
+    return (2 * kChunk + 1) * kMaxChunks * (int)std::min<size_t>(kFgMaxBlocks, std::max<size_t>(1, (n + 511) / 512));
+}
+
+// ||rin||; beta = g[0], s_0 = 1; the RHS iterates if its outer step is active
+// and rin != 0.
 template <typename T>
 __global__ void __launch_bounds__(256) k_fg_norm(const T* __restrict__ rin, double* partials, int pstride,
                                                  RhsState* st, FgDev fg, int* nactive, size_t n) {
@@ -41,62 +68,85 @@ __global__ void __launch_bounds__(256) k_fg_norm(const T* __restrict__ rin, doub
             S.bnorm2 = acc[0];
             S.rnorm2 = acc[0];
             S.kfg = 0;
+            S.reorth = 0;
             S.flag = FLAG_RUNNING;
             S.active = acc[0] > 0.0;
             fg.g[(size_t)b * (fg.m + 1)] = make_double2(sqrt(acc[0]), 0.0);
+            fg.s[(size_t)b * (fg.m + 1)] = 1.0;
             if (S.active) atomicAdd(nactive, 1);
         }
     }
 }
 
-// v = w / scale with scale = g[0] (j < 0: first vector) or the norm of w
-// recorded before the rotation of column j.
+// V'_0 = rin / beta.
 template <typename T>
-__global__ void k_fg_scale(const T* __restrict__ w, T* __restrict__ v, const RhsState* st, FgDev fg, int j,
-                           size_t n) {
+__global__ void k_fg_scale(const T* __restrict__ rin, T* __restrict__ v, const RhsState* st, FgDev fg, size_t n) {
     const int b = blockIdx.z;
     if (!st[b].active) return;
-    __shared__ T s_inv;
-    if (threadIdx.x == 0) {
-        const double s = j < 0 ? fg.g[(size_t)b * (fg.m + 1)].x : fg.hsub[(size_t)b * fg.m + j];
-        s_inv = (T)(1.0 / s);
-    }
-    __syncthreads();
-    const T inv = s_inv;
+    const T inv = (T)(1.0 / fg.g[(size_t)b * (fg.m + 1)].x);
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
-        stc(v, n * b + i, inv * ldc(w, n * b + i));
+        stc(v, n * b + i, inv * ldc(rin, n * b + i));
 }
 
-// h_i = <V_i, w> for i <= j; blockIdx.y picks a chunk of kChunk vectors. The
-// last block of the RHS writes tmp = h and sets (add = 0) or adds (add = 1) h
-// into column j of H.
-template <typename T>
+// d_i = <V'_i, w> for i <= j (w = A Z'_j, unnormalised, in basis slot j+1);
+// blockIdx.y picks a chunk of NV vectors (NV = the smallest of 1, 2, 4, 8 that
+// covers j + 1, else 8). The last block of the RHS writes the projection
+// coefficients tmp_i = d_i / s_i^2 and sets (add = 0) or adds (add = 1)
+// h_ij = d_i / (s_i s_j) into column j of H. With `wnorm` the chunk-0 blocks also
+// sum ||w||^2 into wn2 (for the second-pass test). With `check` an RHS whose
+// first pass asked for no second pass skips the kernel.
+template <typename T, int NV>
 __global__ void __launch_bounds__(256) k_fg_dots(const T* __restrict__ V, size_t vstride, const T* __restrict__ w,
-                                                 int j, int add, double* partials, int pstride, RhsState* st,
-                                                 FgDev fg, size_t n) {
-    __shared__ double sh[2 * kChunk][33];
+                                                 int j, int add, int wnorm, int check, double* partials, int pstride,
+                                                 RhsState* st, FgDev fg, size_t n) {
+    constexpr int NA = 2 * NV + 1;
+    __shared__ double sh[NA][33];
     __shared__ int s_last;
     const int b = blockIdx.z;
-    if (!st[b].active) return;
-    const int i0 = blockIdx.y * kChunk;
-    T acc[2 * kChunk];
+    if (!st[b].active || (check && !st[b].reorth)) return;
+    const int i0 = blockIdx.y * NV;
+    const int nv = min(NV, j + 1 - i0);
+    const bool wn = wnorm && blockIdx.y == 0;
+    // basis vectors of this chunk (slots past nv alias the first: never used)
+    const T* vp[NV];
 #pragma unroll
-    for (int k = 0; k < 2 * kChunk; ++k) acc[k] = 0;
-    for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < n; p += (size_t)gridDim.x * blockDim.x) {
-        const cx<T> wv = ldc(w, n * b + p);
+    for (int k = 0; k < NV; ++k) vp[k] = V + 2 * (vstride * (size_t)(i0 + (k < nv ? k : 0)) + n * b);
+    const T* wb = w + 2 * n * b;
+    T acc[NA];
 #pragma unroll
-        for (int k = 0; k < kChunk; ++k) {
-            if (i0 + k <= j) {
-                const cx<T> q = ldc(V + 2 * vstride * (i0 + k), n * b + p);
-                acc[2 * k] += q.re * wv.re + q.im * wv.im;
-                acc[2 * k + 1] += q.re * wv.im - q.im * wv.re;
+    for (int k = 0; k < NA; ++k) acc[k] = 0;
+    // two points per thread and step, every load of the step issued before use
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    for (; p + stride < n; p += 2 * stride) {
+        const cx<T> w0 = ldc(wb, p), w1 = ldc(wb, p + stride);
+        cx<T> q0[NV], q1[NV];
+#pragma unroll
+        for (int k = 0; k < NV; ++k)
+            if (k < nv) { q0[k] = ldc(vp[k], p); q1[k] = ldc(vp[k], p + stride); }
+#pragma unroll
+        for (int k = 0; k < NV; ++k)
+            if (k < nv) {
+                acc[2 * k] += (q0[k].re * w0.re + q0[k].im * w0.im) + (q1[k].re * w1.re + q1[k].im * w1.im);
+                acc[2 * k + 1] += (q0[k].re * w0.im - q0[k].im * w0.re) + (q1[k].re * w1.im - q1[k].im * w1.re);
             }
-        }
+        if (wn) acc[2 * NV] += (w0.re * w0.re + w0.im * w0.im) + (w1.re * w1.re + w1.im * w1.im);
     }
-    // block reduction of the 2 * kChunk partial sums
+    if (p < n) {
+        const cx<T> w0 = ldc(wb, p);
+#pragma unroll
+        for (int k = 0; k < NV; ++k)
+            if (k < nv) {
+                const cx<T> q = ldc(vp[k], p);
+                acc[2 * k] += q.re * w0.re + q.im * w0.im;
+                acc[2 * k + 1] += q.re * w0.im - q.im * w0.re;
+            }
+        if (wn) acc[2 * NV] += w0.re * w0.re + w0.im * w0.im;
+    }
+    // block reduction of the partial sums
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
 #pragma unroll
-    for (int k = 0; k < 2 * kChunk; ++k) {
+    for (int k = 0; k < NA; ++k) {
         T v = acc[k];
         for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
         if (lane == 0) sh[k][warp] = (double)v;
@@ -104,7 +154,7 @@ __global__ void __launch_bounds__(256) k_fg_dots(const T* __restrict__ V, size_t
     __syncthreads();
     const int nblk = gridDim.x * gridDim.y, blk = blockIdx.y * gridDim.x + blockIdx.x;
     double* part = partials + (size_t)b * pstride;
-    if (threadIdx.x < 2 * kChunk) {
+    if (threadIdx.x < NA) {
         double v = 0.0;
         for (int q = 0; q < nw; ++q) v += sh[threadIdx.x][q];
         part[(size_t)threadIdx.x * nblk + blk] = v;
@@ -115,19 +165,31 @@ __global__ void __launch_bounds__(256) k_fg_dots(const T* __restrict__ V, size_t
     __syncthreads();
     if (!s_last) return;
     __threadfence();
-    // the last block: one warp per basis vector i <= j sums the partials of the
-    // x-blocks of its chunk, lane-strided then by a fixed shuffle tree (the order
-    // does not depend on timing, so the result is deterministic)
+    // the last block: one warp per basis vector i <= j (and one more for ||w||^2)
+    // sums the partials of the x-blocks of its chunk, lane-strided then by a fixed
+    // shuffle tree (the order does not depend on timing, so the result is
+    // deterministic)
     const int nx = gridDim.x;
     const size_t col = (size_t)b * (fg.m + 1);
-    for (int i = warp; i <= j; i += nw) {
-        const int c = i / kChunk, k = i % kChunk;
+    const double* s = fg.s + col;
+    const int nsum = j + 1 + (wnorm ? 1 : 0);
+    for (int i = warp; i < nsum; i += nw) {
+        const bool isn = i > j;
+        const int c = isn ? 0 : i / NV, k = isn ? NV : i % NV;
         const double* pre = part + (size_t)(2 * k) * nblk + (size_t)c * nx;
         const double* pim = part + (size_t)(2 * k + 1) * nblk + (size_t)c * nx;
+        // eight loads per lane in flight, then summed in a fixed order
         double re = 0.0, im = 0.0;
-        for (int x = lane; x < nx; x += 32) {
-            re += __ldcg(pre + x);
-            im += __ldcg(pim + x);
+        for (int x0 = 0; x0 < nx; x0 += 256) {
+            double vr[8], vi[8];
+#pragma unroll
+            for (int t = 0; t < 8; ++t) {
+                const int x = x0 + lane + 32 * t;
+                vr[t] = x < nx ? __ldcg(pre + x) : 0.0;
+                vi[t] = (x < nx && !isn) ? __ldcg(pim + x) : 0.0;
+            }
+#pragma unroll
+            for (int t = 0; t < 8; ++t) { re += vr[t]; im += vi[t]; }
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
@@ -135,113 +197,173 @@ __global__ void __launch_bounds__(256) k_fg_dots(const T* __restrict__ V, size_t
             im += __shfl_xor_sync(0xffffffffu, im, o);
         }
         if (lane == 0) {
-            fg.tmp[col + i] = make_double2(re, im);
-            double2& h = fg.H[(col + i) * fg.m + j];
-            if (add) { h.x += re; h.y += im; } else { h = make_double2(re, im); }
+            if (isn) {
+                fg.wn2[b] = re;
+            } else {
+                const double si = s[i], inv2 = 1.0 / (si * si), invh = 1.0 / (si * s[j]);
+                fg.tmp[col + i] = make_double2(re * inv2, im * inv2);
+                double2& h = fg.H[(col + i) * fg.m + j];
+                if (add) { h.x += re * invh; h.y += im * invh; } else { h = make_double2(re * invh, im * invh); }
+            }
         }
     }
     if (threadIdx.x == 0) st[b].counter[2] = 0u;
 }
 
-// w -= sum_{i <= j} tmp_i V_i; with `norm`, also ||w||^2 and, in the last
-// block, H[j+1][j] = ||w||, the Givens rotations of column j and the
-// convergence test |g_{j+1}| <= tol_rel * beta.
-template <typename T>
+// Column j of the Arnoldi relation is complete (||w'|| = hn2^(1/2) after the
+// last pass): s_{j+1}, h_{j+1,j} = s_{j+1} / s_j, the previous Givens rotations
+// on column j, the new rotation zeroing h_{j+1,j}, and the convergence test
+// |g_{j+1}| <= tol_rel * beta.
+__device__ void fg_finish_column(RhsState& S, const FgDev& fg, int b, int j, double hn2, int* nactive) {
+    const int m = fg.m;
+    const size_t col = (size_t)b * (m + 1);
+    double2* H = fg.H + col * m;                   // H[i * m + j]
+    const double sn1 = sqrt(hn2);
+    fg.s[col + j + 1] = sn1;
+    const double hn = sn1 / fg.s[col + j];
+    // previous rotations on column j
+    for (int i = 0; i < j; ++i) {
+        const double c = fg.cs[(size_t)b * m + i];
+        const double2 s = fg.sn[(size_t)b * m + i];
+        const double2 a = H[(size_t)i * m + j], d = H[(size_t)(i + 1) * m + j];
+        // [a; d] <- [c a + s d; -conj(s) a + c d]
+        H[(size_t)i * m + j] = make_double2(c * a.x + s.x * d.x - s.y * d.y, c * a.y + s.x * d.y + s.y * d.x);
+        H[(size_t)(i + 1) * m + j] = make_double2(-(s.x * a.x + s.y * a.y) + c * d.x, -(s.x * a.y - s.y * a.x) + c * d.y);
+    }
+    // new rotation zeroing h_{j+1,j}
+    const double2 a = H[(size_t)j * m + j];
+    const double bb = hn;
+    const double an = sqrt(a.x * a.x + a.y * a.y);
+    double c;
+    double2 s;
+    if (an == 0.0) { c = 0.0; s = make_double2(1.0, 0.0); }
+    else {
+        const double t = sqrt(an * an + bb * bb);
+        c = an / t;
+        s = make_double2(a.x / an * bb / t, a.y / an * bb / t);   // (a/|a|) conj(b) / t, b real
+    }
+    fg.cs[(size_t)b * m + j] = c;
+    fg.sn[(size_t)b * m + j] = s;
+    const double t2 = sqrt(an * an + bb * bb);
+    H[(size_t)j * m + j] = an == 0.0 ? make_double2(bb, 0.0) : make_double2(a.x / an * t2, a.y / an * t2);
+    H[(size_t)(j + 1) * m + j] = make_double2(0.0, 0.0);
+    double2* g = fg.g + col;
+    const double2 gj = g[j];
+    g[j + 1] = make_double2(-(s.x * gj.x + s.y * gj.y), -(s.x * gj.y - s.y * gj.x));   // -conj(s) g_j
+    g[j] = make_double2(c * gj.x, c * gj.y);
+    S.kfg = j + 1;
+    S.iters += 1;
+    const double res = sqrt(g[j + 1].x * g[j + 1].x + g[j + 1].y * g[j + 1].y);
+    S.rnorm2 = res * res;
+    int done = 0;
+    if (res <= S.tol_rel * sqrt(S.bnorm2) || hn == 0.0) { done = 1; S.flag = FLAG_CONVERGED; }
+    else if (j + 1 >= m) { done = 1; S.flag = FLAG_MAXIT; }
+    else if (S.iters >= S.max_it) { done = 1; S.flag = FLAG_MAXIT; }
+    if (done) { S.active = 0; atomicSub(nactive, 1); }
+}
+
+// w -= sum_{i <= j} tmp_i V'_i in place (w is basis slot j+1). mode 0: no norm
+// (a second pass follows); mode 1: ||w||^2 and the column is finished; mode 2:
+// ||w||^2, then a second pass is requested (S.reorth = 1) if ||w||^2 < wn2 / 2,
+// else the column is finished. With `check` an RHS whose first pass asked for
+// no second pass skips the kernel.
+template <typename T, int NV>
 __global__ void __launch_bounds__(256) k_fg_axpy(const T* __restrict__ V, size_t vstride, T* __restrict__ w, int j,
-                                                 int norm, double* partials, int pstride, RhsState* st, FgDev fg,
-                                                 int* nactive, size_t n) {
+                                                 int mode, int check, double* partials, int pstride, RhsState* st,
+                                                 FgDev fg, int* nactive, size_t n) {
     __shared__ double sh[32];
     __shared__ cx<T> coef[kMaxRestart + 1];
     const int b = blockIdx.z;
-    if (!st[b].active) return;
+    if (!st[b].active || (check && !st[b].reorth)) return;
     const size_t col = (size_t)b * (fg.m + 1);
     for (int i = threadIdx.x; i <= j; i += blockDim.x) coef[i] = cx<T>((T)fg.tmp[col + i].x, (T)fg.tmp[col + i].y);
     __syncthreads();
     T a0 = 0;
-    for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < n; p += (size_t)gridDim.x * blockDim.x) {
-        cx<T> wv = ldcc(w, n * b + p);
-        for (int i = 0; i <= j; ++i) wv = wv - coef[i] * ldc(V + 2 * vstride * i, n * b + p);
-        stc(w, n * b + p, wv);
-        a0 += wv.re * wv.re + wv.im * wv.im;
+    T* wb = w + 2 * n * b;
+    const T* vb = V + 2 * n * b;
+    // two points per thread and step; the basis in chunks of NV vectors, every
+    // load of a chunk issued before use
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    for (; p + stride < n; p += 2 * stride) {
+        cx<T> w0 = ldcc(wb, p), w1 = ldcc(wb, p + stride);
+        for (int i0 = 0; i0 <= j; i0 += NV) {
+            const int nv = min(NV, j + 1 - i0);
+            cx<T> q0[NV], q1[NV];
+#pragma unroll
+            for (int k = 0; k < NV; ++k)
+                if (k < nv) {
+                    const T* v = vb + 2 * vstride * (size_t)(i0 + k);
+                    q0[k] = ldc(v, p);
+                    q1[k] = ldc(v, p + stride);
+                }
+#pragma unroll
+            for (int k = 0; k < NV; ++k)
+                if (k < nv) { w0 = w0 - coef[i0 + k] * q0[k]; w1 = w1 - coef[i0 + k] * q1[k]; }
+        }
+        stc(wb, p, w0);
+        stc(wb, p + stride, w1);
+        a0 += (w0.re * w0.re + w0.im * w0.im) + (w1.re * w1.re + w1.im * w1.im);
     }
-    if (!norm) return;
+    if (p < n) {
+        cx<T> w0 = ldcc(wb, p);
+        for (int i = 0; i <= j; ++i) w0 = w0 - coef[i] * ldc(vb + 2 * vstride * (size_t)i, p);
+        stc(wb, p, w0);
+        a0 += w0.re * w0.re + w0.im * w0.im;
+    }
+    if (mode == 0) return;
     const T vv[1] = {a0};
     double acc[1];
     if (last_block_reduce_t<1, T>(vv, acc, sh, partials + (size_t)b * pstride, gridDim.x, blockIdx.x, &st[b].counter[0])) {
         if (threadIdx.x == 0) {
             RhsState& S = st[b];
-            const int m = fg.m;
-            double2* H = fg.H + col * m;                   // H[i * m + j]
-            const double hn = sqrt(acc[0]);
-            H[(size_t)(j + 1) * m + j] = make_double2(hn, 0.0);
-            // previous rotations on column j
-            for (int i = 0; i < j; ++i) {
-                const double c = fg.cs[(size_t)b * m + i];
-                const double2 s = fg.sn[(size_t)b * m + i];
-                const double2 a = H[(size_t)i * m + j], d = H[(size_t)(i + 1) * m + j];
-                // [a; d] <- [c a + s d; -conj(s) a + c d]
-                H[(size_t)i * m + j] = make_double2(c * a.x + s.x * d.x - s.y * d.y, c * a.y + s.x * d.y + s.y * d.x);
-                H[(size_t)(i + 1) * m + j] = make_double2(-(s.x * a.x + s.y * a.y) + c * d.x, -(s.x * a.y - s.y * a.x) + c * d.y);
+            if (mode == 2 && acc[0] < 0.5 * fg.wn2[b]) {
+                S.reorth = 1;
+            } else {
+                S.reorth = 0;
+                fg_finish_column(S, fg, b, j, acc[0], nactive);
             }
-            // new rotation zeroing H[j+1][j]
-            const double2 a = H[(size_t)j * m + j];
-            const double bb = hn;
-            const double an = sqrt(a.x * a.x + a.y * a.y);
-            double c;
-            double2 s;
-            if (an == 0.0) { c = 0.0; s = make_double2(1.0, 0.0); }
-            else {
-                const double t = sqrt(an * an + bb * bb);
-                c = an / t;
-                s = make_double2(a.x / an * bb / t, a.y / an * bb / t);   // (a/|a|) conj(b) / t, b real
-            }
-            fg.cs[(size_t)b * m + j] = c;
-            fg.sn[(size_t)b * m + j] = s;
-            const double t2 = sqrt(an * an + bb * bb);
-            H[(size_t)j * m + j] = an == 0.0 ? make_double2(bb, 0.0) : make_double2(a.x / an * t2, a.y / an * t2);
-            H[(size_t)(j + 1) * m + j] = make_double2(0.0, 0.0);
-            double2* g = fg.g + col;
-            const double2 gj = g[j];
-            g[j + 1] = make_double2(-(s.x * gj.x + s.y * gj.y), -(s.x * gj.y - s.y * gj.x));   // -conj(s) g_j
-            g[j] = make_double2(c * gj.x, c * gj.y);
-            S.kfg = j + 1;
-            S.iters += 1;
-            const double res = sqrt(g[j + 1].x * g[j + 1].x + g[j + 1].y * g[j + 1].y);
-            S.rnorm2 = res * res;
-            // keep H[j+1][j] for the next basis vector's scaling
-            fg.hsub[(size_t)b * m + j] = hn;
-            int done = 0;
-            if (res <= S.tol_rel * sqrt(S.bnorm2) || hn == 0.0) { done = 1; S.flag = FLAG_CONVERGED; }
-            else if (j + 1 >= m) { done = 1; S.flag = FLAG_MAXIT; }
-            else if (S.iters >= S.max_it) { done = 1; S.flag = FLAG_MAXIT; }
-            if (done) { S.active = 0; atomicSub(nactive, 1); }
         }
     }
 }
 
-// y = R^{-1} g on the k = kfg leading rows (FP64, one thread per RHS).
-__global__ void k_fg_backsolve(const RhsState* st, FgDev fg, int nrhs) {
-    const int b = blockIdx.x * blockDim.x + threadIdx.x;
-    if (b >= nrhs || !st[b].outer_active) return;
+// y = R^{-1} g on the k = kfg leading rows (FP64), one warp per RHS: the warp
+// stages the triangle and g in shared memory with all its loads in flight, then
+// lane 0 substitutes backwards.
+__global__ void __launch_bounds__(32) k_fg_backsolve(const RhsState* st, FgDev fg) {
+    extern __shared__ double2 fg_tri[];                  // R [k][k] (upper part), then g [k]
+    const int b = blockIdx.x;
+    if (!st[b].outer_active) return;
     const int m = fg.m, k = st[b].kfg;
     const size_t col = (size_t)b * (m + 1);
     const double2* H = fg.H + col * m;
+    double2* R = fg_tri;
+    double2* gk = fg_tri + k * k;
+    for (int idx = threadIdx.x; idx < k * k; idx += 32) {
+        const int i = idx / k, q = idx - i * k;
+        if (q >= i) R[idx] = H[(size_t)i * m + q];
+    }
+    for (int i = threadIdx.x; i < k; i += 32) gk[i] = fg.g[col + i];
+    __syncwarp();
+    if (threadIdx.x != 0) return;
     double2* y = fg.y + (size_t)b * m;
     for (int i = k - 1; i >= 0; --i) {
-        double2 acc = fg.g[col + i];
+        double2 acc = gk[i];
         for (int q = i + 1; q < k; ++q) {
-            const double2 h = H[(size_t)i * m + q];
-            acc.x -= h.x * y[q].x - h.y * y[q].y;
-            acc.y -= h.x * y[q].y + h.y * y[q].x;
+            const double2 h = R[i * k + q], yq = gk[q];      // gk[q] holds y_q once solved
+            acc.x -= h.x * yq.x - h.y * yq.y;
+            acc.y -= h.x * yq.y + h.y * yq.x;
         }
-        const double2 d = H[(size_t)i * m + i];
+        const double2 d = R[i * k + i];
         const double dd = d.x * d.x + d.y * d.y;
-        y[i] = dd > 0.0 ? make_double2((acc.x * d.x + acc.y * d.y) / dd, (acc.y * d.x - acc.x * d.y) / dd)
-                        : make_double2(0.0, 0.0);
+        const double2 yi = dd > 0.0 ? make_double2((acc.x * d.x + acc.y * d.y) / dd, (acc.y * d.x - acc.x * d.y) / dd)
+                                    : make_double2(0.0, 0.0);
+        gk[i] = yi;
+        y[i] = yi;
     }
 }
 
-// x = sum_{i < kfg} y_i Z_i for every RHS whose outer step is active.
+// x = sum_{i < kfg} (y_i / s_i) Z'_i for every RHS whose outer step is active.
 template <typename T>
 __global__ void k_fg_update(const T* __restrict__ Z, size_t zstride, T* __restrict__ x, const RhsState* st, FgDev fg,
                             size_t n) {
@@ -249,12 +371,25 @@ __global__ void k_fg_update(const T* __restrict__ Z, size_t zstride, T* __restri
     const int b = blockIdx.z;
     if (!st[b].outer_active) return;
     const int k = st[b].kfg;
-    for (int i = threadIdx.x; i < k; i += blockDim.x)
-        coef[i] = cx<T>((T)fg.y[(size_t)b * fg.m + i].x, (T)fg.y[(size_t)b * fg.m + i].y);
+    for (int i = threadIdx.x; i < k; i += blockDim.x) {
+        const double2 y = fg.y[(size_t)b * fg.m + i];
+        const double inv = 1.0 / fg.s[(size_t)b * (fg.m + 1) + i];
+        coef[i] = cx<T>((T)(y.x * inv), (T)(y.y * inv));
+    }
     __syncthreads();
+    const T* zb = Z + 2 * n * b;
     for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < n; p += (size_t)gridDim.x * blockDim.x) {
         cx<T> acc(0, 0);
-        for (int i = 0; i < k; ++i) acc = acc + coef[i] * ldc(Z + 2 * zstride * i, n * b + p);
+        for (int i0 = 0; i0 < k; i0 += kChunk) {
+            const int nv = min(kChunk, k - i0);
+            cx<T> q[kChunk];
+#pragma unroll
+            for (int t = 0; t < kChunk; ++t)
+                if (t < nv) q[t] = ldc(zb + 2 * zstride * (size_t)(i0 + t), p);
+#pragma unroll
+            for (int t = 0; t < kChunk; ++t)
+                if (t < nv) acc = acc + coef[i0 + t] * q[t];
+        }
         stc(x, n * b + p, acc);
     }
 }
@@ -263,42 +398,59 @@ __global__ void k_fg_update(const T* __restrict__ Z, size_t zstride, T* __restri
 template <typename T>
 void launch_fg_norm(const T* rin, double* partials, int pstride, RhsState* st, const FgDev& fg, int* nactive,
                     size_t n, int nrhs, cudaStream_t s) {
-    k_fg_norm<T><<<dim3(grid1d_fg(n), 1, nrhs), 256, 0, s>>>(rin, partials, pstride, st, fg, nactive, n);
+    k_fg_norm<T><<<dim3(fg_grid<k_fg_norm<T>>(n), 1, nrhs), 256, 0, s>>>(rin, partials, pstride, st, fg, nactive, n);
 }
 template <typename T>
-void launch_fg_scale(const T* w, T* v, const RhsState* st, const FgDev& fg, int j, size_t n, int nrhs,
-                     cudaStream_t s) {
-    k_fg_scale<T><<<dim3(grid1d_fg(n), 1, nrhs), 256, 0, s>>>(w, v, st, fg, j, n);
+void launch_fg_scale(const T* rin, T* v, const RhsState* st, const FgDev& fg, size_t n, int nrhs, cudaStream_t s) {
+    k_fg_scale<T><<<dim3(fg_grid<k_fg_scale<T>>(n), 1, nrhs), 256, 0, s>>>(rin, v, st, fg, n);
+}
+template <typename T, int NV>
+static void fg_dots_nv(const T* V, size_t vstride, const T* w, int j, int add, int wnorm, int check, double* partials,
+                       int pstride, RhsState* st, const FgDev& fg, size_t n, int nrhs, cudaStream_t s) {
+    const int nchunk = (j + NV) / NV;
+    k_fg_dots<T, NV><<<dim3(fg_grid<k_fg_dots<T, NV>>(n), nchunk, nrhs), 256, 0, s>>>(
+        V, vstride, w, j, add, wnorm, check, partials, pstride, st, fg, n);
 }
 template <typename T>
-void launch_fg_dots(const T* V, size_t vstride, const T* w, int j, int add, double* partials, int pstride,
-                    RhsState* st, const FgDev& fg, size_t n, int nrhs, cudaStream_t s) {
-    const int nchunk = (j + kChunk) / kChunk;
-    k_fg_dots<T><<<dim3(grid1d_fg(n), nchunk, nrhs), 256, 0, s>>>(V, vstride, w, j, add, partials, pstride, st, fg, n);
+void launch_fg_dots(const T* V, size_t vstride, const T* w, int j, int add, int wnorm, int check, double* partials,
+                    int pstride, RhsState* st, const FgDev& fg, size_t n, int nrhs, cudaStream_t s) {
+    if (j < 1) fg_dots_nv<T, 1>(V, vstride, w, j, add, wnorm, check, partials, pstride, st, fg, n, nrhs, s);
+    else if (j < 2) fg_dots_nv<T, 2>(V, vstride, w, j, add, wnorm, check, partials, pstride, st, fg, n, nrhs, s);
+    else if (j < 4) fg_dots_nv<T, 4>(V, vstride, w, j, add, wnorm, check, partials, pstride, st, fg, n, nrhs, s);
+    else fg_dots_nv<T, kChunk>(V, vstride, w, j, add, wnorm, check, partials, pstride, st, fg, n, nrhs, s);
+}
+template <typename T, int NV>
+static void fg_axpy_nv(const T* V, size_t vstride, T* w, int j, int mode, int check, double* partials, int pstride,
+                       RhsState* st, const FgDev& fg, int* nactive, size_t n, int nrhs, cudaStream_t s) {
+    k_fg_axpy<T, NV><<<dim3(fg_grid<k_fg_axpy<T, NV>>(n), 1, nrhs), 256, 0, s>>>(V, vstride, w, j, mode, check,
+                                                                                partials, pstride, st, fg, nactive, n);
 }
 template <typename T>
-void launch_fg_axpy(const T* V, size_t vstride, T* w, int j, int norm, double* partials, int pstride, RhsState* st,
-                    const FgDev& fg, int* nactive, size_t n, int nrhs, cudaStream_t s) {
-    k_fg_axpy<T><<<dim3(grid1d_fg(n), 1, nrhs), 256, 0, s>>>(V, vstride, w, j, norm, partials, pstride, st, fg,
-                                                            nactive, n);
+void launch_fg_axpy(const T* V, size_t vstride, T* w, int j, int mode, int check, double* partials, int pstride,
+                    RhsState* st, const FgDev& fg, int* nactive, size_t n, int nrhs, cudaStream_t s) {
+    if (j < 1) fg_axpy_nv<T, 1>(V, vstride, w, j, mode, check, partials, pstride, st, fg, nactive, n, nrhs, s);
+    else if (j < 2) fg_axpy_nv<T, 2>(V, vstride, w, j, mode, check, partials, pstride, st, fg, nactive, n, nrhs, s);
+    else if (j < 4) fg_axpy_nv<T, 4>(V, vstride, w, j, mode, check, partials, pstride, st, fg, nactive, n, nrhs, s);
+    else fg_axpy_nv<T, kChunk>(V, vstride, w, j, mode, check, partials, pstride, st, fg, nactive, n, nrhs, s);
 }
 void launch_fg_backsolve(const RhsState* st, const FgDev& fg, int nrhs, cudaStream_t s) {
-    k_fg_backsolve<<<(nrhs + 63) / 64, 64, 0, s>>>(st, fg, nrhs);
+    const size_t smem = sizeof(double2) * ((size_t)fg.m * fg.m + fg.m);
+    k_fg_backsolve<<<nrhs, 32, smem, s>>>(st, fg);
 }
 template <typename T>
 void launch_fg_update(const T* Z, size_t zstride, T* x, const RhsState* st, const FgDev& fg, size_t n, int nrhs,
                       cudaStream_t s) {
-    k_fg_update<T><<<dim3(grid1d_fg(n), 1, nrhs), 256, 0, s>>>(Z, zstride, x, st, fg, n);
+    k_fg_update<T><<<dim3(fg_grid<k_fg_update<T>>(n), 1, nrhs), 256, 0, s>>>(Z, zstride, x, st, fg, n);
 }
 
 #define HELM_FG_INST(T)                                                                                             \
     template void launch_fg_norm<T>(const T*, double*, int, RhsState*, const FgDev&, int*, size_t, int,             \
                                     cudaStream_t);                                                                  \
-    template void launch_fg_scale<T>(const T*, T*, const RhsState*, const FgDev&, int, size_t, int, cudaStream_t);  \
-    template void launch_fg_dots<T>(const T*, size_t, const T*, int, int, double*, int, RhsState*, const FgDev&,    \
-                                    size_t, int, cudaStream_t);                                                     \
-    template void launch_fg_axpy<T>(const T*, size_t, T*, int, int, double*, int, RhsState*, const FgDev&, int*,    \
-                                    size_t, int, cudaStream_t);                                                     \
+    template void launch_fg_scale<T>(const T*, T*, const RhsState*, const FgDev&, size_t, int, cudaStream_t);       \
+    template void launch_fg_dots<T>(const T*, size_t, const T*, int, int, int, int, double*, int, RhsState*,        \
+                                    const FgDev&, size_t, int, cudaStream_t);                                       \
+    template void launch_fg_axpy<T>(const T*, size_t, T*, int, int, int, double*, int, RhsState*, const FgDev&,     \
+                                    int*, size_t, int, cudaStream_t);                                               \
     template void launch_fg_update<T>(const T*, size_t, T*, const RhsState*, const FgDev&, size_t, int,             \
                                       cudaStream_t);
 HELM_FG_INST(float)

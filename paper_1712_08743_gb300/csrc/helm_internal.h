@@ -24,7 +24,6 @@ constexpr int kTailMaxPoints32 = 2048;
 constexpr int kTailMaxPoints64 = 1024;
 constexpr int kMaxLevels = 24;
 constexpr int kMaxRestart = 32;
-constexpr int kFgPartials = 16 * 5 * 512;   // FGMRES dot partials per RHS (2 x 8 values x 5 chunks x 512 blocks)
 constexpr int kGalerkinCoefs = 10;      // per coarse node: G (c, e, n, ne, nw) then K (c, e, n, ne, nw)
 
 // One multigrid level as the kernels see it. The finest level carries the
@@ -122,9 +121,12 @@ inline LevelDev level_dev(const helm_model* m, int l, bool dbl) {
     return d;
 }
 
-// Tail schedule entries: op type in the low byte, level above it.
-enum TailOp : int { OP_SMOOTH0 = 0, OP_RESID = 1, OP_RESTRICT = 2, OP_PROLONG_ADD = 3, OP_JACOBI = 4,
-                    OP_COARSE = 5, OP_OUTPUT = 6, OP_LOAD = 7 };
+// Tail schedule entries: op type in the low byte, level above it. LOAD and
+// RESTRICT also take the zero-guess smoothing step of the level they fill (when
+// it is not the coarsest); POST is the residual and Jacobi step after a coarse
+// correction, written to r, which holds a level's result (as does COARSE).
+enum TailOp : int { OP_RESID = 1, OP_RESTRICT = 2, OP_PROLONG_ADD = 3, OP_POST = 4, OP_COARSE = 5, OP_OUTPUT = 6,
+                    OP_LOAD = 7 };
 std::vector<int> tail_schedule(int lt, int L, bool fcycle);
 size_t tail_smem_bytes(const helm_model* m, int lt, size_t elem, bool* minv_smem = nullptr, int* minv_off = nullptr);
 
@@ -214,7 +216,8 @@ void launch_coarse_invert(const LevelDev& Lc, const double* w2_slots, const int*
 
 // FGMRES state on the device, per RHS: Hessenberg H [(m+1) x m], rotated
 // right-hand side g [m+1], Givens cosines cs / sines sn [m], solution y [m],
-// projection coefficients tmp [m+1] and the subdiagonal norms hsub [m].
+// projection coefficients tmp [m+1], the norms s [m+1] of the unnormalised
+// basis vectors, and ||w||^2 before Gram-Schmidt wn2 [1].
 struct FgDev {
     int m;
     double2* H;
@@ -223,21 +226,22 @@ struct FgDev {
     double2* sn;
     double2* y;
     double2* tmp;
-    double* hsub;
+    double* s;
+    double* wn2;
 };
 template <typename T>
 void launch_fg_norm(const T* rin, double* partials, int pstride, RhsState* st, const FgDev& fg, int* nactive,
                     size_t n, int nrhs, cudaStream_t s);
 template <typename T>
-void launch_fg_scale(const T* w, T* v, const RhsState* st, const FgDev& fg, int j, size_t n, int nrhs,
-                     cudaStream_t s);
+void launch_fg_scale(const T* rin, T* v, const RhsState* st, const FgDev& fg, size_t n, int nrhs, cudaStream_t s);
 template <typename T>
-void launch_fg_dots(const T* V, size_t vstride, const T* w, int j, int add, double* partials, int pstride,
-                    RhsState* st, const FgDev& fg, size_t n, int nrhs, cudaStream_t s);
+void launch_fg_dots(const T* V, size_t vstride, const T* w, int j, int add, int wnorm, int check, double* partials,
+                    int pstride, RhsState* st, const FgDev& fg, size_t n, int nrhs, cudaStream_t s);
 template <typename T>
-void launch_fg_axpy(const T* V, size_t vstride, T* w, int j, int norm, double* partials, int pstride, RhsState* st,
-                    const FgDev& fg, int* nactive, size_t n, int nrhs, cudaStream_t s);
+void launch_fg_axpy(const T* V, size_t vstride, T* w, int j, int mode, int check, double* partials, int pstride,
+                    RhsState* st, const FgDev& fg, int* nactive, size_t n, int nrhs, cudaStream_t s);
 void launch_fg_backsolve(const RhsState* st, const FgDev& fg, int nrhs, cudaStream_t s);
+int fg_partials(size_t n);   // reduction partials per RHS the FGMRES kernels need on n points
 template <typename T>
 void launch_fg_update(const T* Z, size_t zstride, T* x, const RhsState* st, const FgDev& fg, size_t n, int nrhs,
                       cudaStream_t s);

@@ -1564,7 +1564,7 @@ __device__ __forceinline__ cx<T> mop9_sm(const cx<T>* C, int n, int nx, int nz, 
 __device__ __forceinline__ int tail_row(int p, float rnx) { return (int)(((float)p + 0.5f) * rnx); }
 
 template <typename T>
-__global__ void __launch_bounds__(1024) k_tail(const __grid_constant__ TailArgs a, const RhsState* st) {
+__global__ void __launch_bounds__(1024, 1) k_tail(const __grid_constant__ TailArgs a, const RhsState* st) {
     extern __shared__ __align__(16) unsigned char tail_smem[];
     pdl_trigger();
     const int b = blockIdx.x;
@@ -1611,25 +1611,34 @@ __global__ void __launch_bounds__(1024) k_tail(const __grid_constant__ TailArgs 
         switch (type) {
             case OP_LOAD: {
                 const T* in = static_cast<const T*>(a.in);
-                for (int p = tid; p < n; p += nth) f[p] = ldc(in, (size_t)n * b + p);
+                const bool sm = l < a.L;
+                for (int p = tid; p < n; p += nth) {
+                    const cx<T> fv = ldc(in, (size_t)n * b + p);
+                    f[p] = fv;
+                    if (sm) u[p] = wj * cdiv(fv, C[p]);
+                }
                 break;
             }
-            case OP_SMOOTH0:
-                for (int p = tid; p < n; p += nth) u[p] = wj * cdiv(f[p], C[p]);
-                break;
             case OP_RESID:
                 for (int p = tid; p < n; p += nth) {
                     const int iz = tail_row(p, rnx), ix = p - iz * nx;
                     r[p] = f[p] - mop9_sm(C, n, nx, nz, ix, iz, p, u + p);
                 }
                 break;
-            case OP_JACOBI:
-                for (int p = tid; p < n; p += nth) u[p] = u[p] + wj * cdiv(r[p], C[p]);
+            case OP_POST:
+                for (int p = tid; p < n; p += nth) {
+                    const int iz = tail_row(p, rnx), ix = p - iz * nx;
+                    const cx<T> res = f[p] - mop9_sm(C, n, nx, nz, ix, iz, p, u + p);
+                    r[p] = u[p] + wj * cdiv(res, C[p]);
+                }
                 break;
             case OP_RESTRICT: {
                 const int cnx = a.lv[l + 1].nx, nc = cnx * a.lv[l + 1].nz;
                 const float rcnx = 1.0f / (float)cnx;
                 cx<T>* fc = base + off[l + 1];
+                cx<T>* uc = fc + nc;
+                const cx<T>* Cc = fc + 3 * nc;
+                const bool sm = l + 1 < a.L;
                 for (int q = tid; q < nc; q += nth) {
                     const int K = tail_row(q, rcnx), I = q - K * cnx;
                     const int x = 2 * I + 1;
@@ -1643,13 +1652,15 @@ __global__ void __launch_bounds__(1024) k_tail(const __grid_constant__ TailArgs 
                         hp = r2[x - 1] + T(2) * r2[x];
                         if (e) hp = hp + r2[x + 1];
                     }
-                    fc[q] = T(0.25) * ((h0 + hp) + T(2) * hm);
+                    const cx<T> fv = T(0.25) * ((h0 + hp) + T(2) * hm);
+                    fc[q] = fv;
+                    if (sm) uc[q] = wj * cdiv(fv, Cc[q]);
                 }
                 break;
             }
             case OP_PROLONG_ADD: {
                 const int cnx = a.lv[l + 1].nx, cnz = a.lv[l + 1].nz;
-                const cx<T>* uc = base + off[l + 1] + cnx * cnz;
+                const cx<T>* uc = base + off[l + 1] + 2 * cnx * cnz;    // the coarse level's result (its r)
                 for (int p = tid; p < n; p += nth) {
                     const int jz = tail_row(p, rnx), jx = p - jz * nx;
                     // coarse rows (jz-1)/2 and jz/2 (one row, weight 1, for odd jz), columns likewise
@@ -1689,14 +1700,14 @@ __global__ void __launch_bounds__(1024) k_tail(const __grid_constant__ TailArgs 
                         re += __shfl_xor_sync(0xffffffffu, re, o);
                         im += __shfl_xor_sync(0xffffffffu, im, o);
                     }
-                    if (lane == 0) u[row] = cx<T>(re, im);
+                    if (lane == 0) r[row] = cx<T>(re, im);
                 }
                 break;
             }
             case OP_OUTPUT: {
                 T* o = static_cast<T*>(a.out);
                 for (int p = tid; p < n; p += nth)
-                    stc(o, (size_t)n * b + p, a.accumulate ? ldcc(o, (size_t)n * b + p) + u[p] : u[p]);
+                    stc(o, (size_t)n * b + p, a.accumulate ? ldcc(o, (size_t)n * b + p) + r[p] : r[p]);
                 break;
             }
         }
@@ -1731,22 +1742,25 @@ template void launch_tail<double>(const TailArgs&, size_t, int, const RhsState*,
 
 // Schedule of the tail: LOAD the right-hand side of level lt, an F-cycle (whose
 // second coarse correction is a V-cycle) or a V-cycle from lt, OUTPUT.
+// The zero-guess smoothing u = wj D^-1 f of each level is done by the op that
+// writes its f (LOAD or the parent's RESTRICT), and the closing residual and
+// Jacobi steps are one op (POST) that leaves the level's result in r.
 std::vector<int> tail_schedule(int lt, int L, bool fcycle) {
     std::vector<int> ops;
     auto put = [&](int type, int l) { ops.push_back(type | (l << 8)); };
     std::function<void(int)> V = [&](int l) {
         if (l == L) { put(OP_COARSE, l); return; }
-        put(OP_SMOOTH0, l); put(OP_RESID, l); put(OP_RESTRICT, l);
+        put(OP_RESID, l); put(OP_RESTRICT, l);
         V(l + 1);
-        put(OP_PROLONG_ADD, l); put(OP_RESID, l); put(OP_JACOBI, l);
+        put(OP_PROLONG_ADD, l); put(OP_POST, l);
     };
     std::function<void(int)> F = [&](int l) {
         if (l == L) { put(OP_COARSE, l); return; }
-        put(OP_SMOOTH0, l); put(OP_RESID, l); put(OP_RESTRICT, l);
+        put(OP_RESID, l); put(OP_RESTRICT, l);
         F(l + 1);
         put(OP_PROLONG_ADD, l); put(OP_RESID, l); put(OP_RESTRICT, l);
         V(l + 1);
-        put(OP_PROLONG_ADD, l); put(OP_RESID, l); put(OP_JACOBI, l);
+        put(OP_PROLONG_ADD, l); put(OP_POST, l);
     };
     put(OP_LOAD, lt);
     if (fcycle) F(lt); else V(lt);

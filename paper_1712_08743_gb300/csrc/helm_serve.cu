@@ -65,7 +65,7 @@ static bool same_batch(const helm_request& a, const helm_request& b) {
            x.precision == y.precision && x.tol == y.tol && x.max_it == y.max_it && x.beta1 == y.beta1 &&
            x.beta2 == y.beta2 && x.omega_jacobi == y.omega_jacobi && x.inner_tol == y.inner_tol &&
            x.max_outer == y.max_outer && x.check_every == y.check_every && x.use_graphs == y.use_graphs &&
-           x.krylov == y.krylov && x.restart == y.restart;
+           x.krylov == y.krylov && x.restart == y.restart && x.precond == y.precond && x.reorth == y.reorth;
 }
 
 static uint64_t batch_bytes(const helm_request& r, int nb) {
@@ -239,7 +239,9 @@ int helm_submit(helm_ctx* ctx, const helm_request* req, uint64_t* ticket) {
     if (r.opts.device_ptrs || (r.opts.krylov != HELM_KRYLOV_BICGSTAB && r.opts.krylov != HELM_KRYLOV_FGMRES) ||
         r.opts.restart < 1 || r.opts.restart > kMaxRestart || !(r.opts.tol > 0.0) || r.opts.max_it < 1 ||
         r.opts.check_every < 1 || r.opts.max_outer < 1 || !(r.opts.omega_jacobi > 0.0) || !(r.opts.inner_tol > 0.0) ||
-        r.opts.precision < HELM_PREC_MIXED || r.opts.precision > HELM_PREC_FP32)
+        r.opts.precision < HELM_PREC_MIXED || r.opts.precision > HELM_PREC_FP32 ||
+        (r.opts.precond != HELM_PRECOND_MG && r.opts.precond != HELM_PRECOND_NONE) ||
+        r.opts.reorth < HELM_REORTH_ALWAYS || r.opts.reorth > HELM_REORTH_IFNEEDED)
         return HELM_E_INVALID;
     const size_t np = (size_t)r.Px * r.Pz;
     for (size_t i = 0; i < np; ++i)

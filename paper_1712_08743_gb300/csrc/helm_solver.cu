@@ -217,9 +217,12 @@ static int alloc_levels(const helm_model* m, cudaStream_t s, int nrhs, Inner<T>&
 template <typename T>
 static int alloc_inner(const SolveCtx& c, Inner<T>& w) {
     const size_t n = c.m->n(), vb = sizeof(T) * 2 * n * c.nrhs;
-    TRY_ALLOC(w.x, vb, c.s); TRY_ALLOC(w.r, vb, c.s); TRY_ALLOC(w.rh, vb, c.s);
-    TRY_ALLOC(w.p, vb, c.s); TRY_ALLOC(w.v, vb, c.s); TRY_ALLOC(w.sv, vb, c.s);
-    TRY_ALLOC(w.t, vb, c.s); TRY_ALLOC(w.ph, vb, c.s); TRY_ALLOC(w.shv, vb, c.s);
+    TRY_ALLOC(w.x, vb, c.s);
+    if (c.o.krylov == HELM_KRYLOV_BICGSTAB) {      // FGMRES keeps its vectors in FgBufs
+        TRY_ALLOC(w.r, vb, c.s); TRY_ALLOC(w.rh, vb, c.s);
+        TRY_ALLOC(w.p, vb, c.s); TRY_ALLOC(w.v, vb, c.s); TRY_ALLOC(w.sv, vb, c.s);
+        TRY_ALLOC(w.t, vb, c.s); TRY_ALLOC(w.ph, vb, c.s); TRY_ALLOC(w.shv, vb, c.s);
+    }
     return alloc_levels<T>(c.m, c.s, c.nrhs, w);
 }
 
@@ -305,7 +308,7 @@ static int inner_solve(const SolveCtx& c, Inner<T>& w, const T* rin, cudaGraphEx
 // FGMRES buffers: V [(m+1)][nrhs][n], Z [m][nrhs][n] and the small FP64 state.
 template <typename T>
 struct FgBufs {
-    DBuf V, Z, H, g, cs, sn, y, tmp, hsub;
+    DBuf V, Z, H, g, cs, sn, y, tmp, sc, wn2;
     FgDev dev;
 };
 
@@ -321,7 +324,8 @@ static int alloc_fg(const SolveCtx& c, FgBufs<T>& f) {
     TRY_ALLOC(f.sn, sizeof(double2) * (size_t)nrhs * m, c.s);
     TRY_ALLOC(f.y, sizeof(double2) * (size_t)nrhs * m, c.s);
     TRY_ALLOC(f.tmp, sizeof(double2) * (size_t)nrhs * (m + 1), c.s);
-    TRY_ALLOC(f.hsub, sizeof(double) * (size_t)nrhs * m, c.s);
+    TRY_ALLOC(f.sc, sizeof(double) * (size_t)nrhs * (m + 1), c.s);
+    TRY_ALLOC(f.wn2, sizeof(double) * (size_t)nrhs, c.s);
     HELM_CUDA_TRY(cudaMemsetAsync(f.H.p, 0, sizeof(double2) * (size_t)nrhs * (m + 1) * m, c.s));
     f.dev.m = m;
     f.dev.H = f.H.template as<double2>();
@@ -330,7 +334,8 @@ static int alloc_fg(const SolveCtx& c, FgBufs<T>& f) {
     f.dev.sn = f.sn.template as<double2>();
     f.dev.y = f.y.template as<double2>();
     f.dev.tmp = f.tmp.template as<double2>();
-    f.dev.hsub = f.hsub.template as<double>();
+    f.dev.s = f.sc.template as<double>();
+    f.dev.wn2 = f.wn2.template as<double>();
     return HELM_OK;
 }
 
@@ -339,27 +344,32 @@ static int alloc_fg(const SolveCtx& c, FgBufs<T>& f) {
 template <typename T>
 static void fgmres_cycle(const SolveCtx& c, Inner<T>& w, FgBufs<T>& f, const T* rin) {
     const size_t n = c.m->n(), vs = n * c.nrhs;
-    const int m = f.dev.m;
+    const int m = f.dev.m, ro = c.o.reorth;
     T* V = f.V.template as<T>();
     T* Z = f.Z.template as<T>();
-    T* wv = w.v.template as<T>();
     launch_fg_norm<T>(rin, c.partials, c.pstride, c.st, f.dev, c.nactive, n, c.nrhs, c.s);
-    launch_fg_scale<T>(rin, V, c.st, f.dev, -1, n, c.nrhs, c.s);
+    launch_fg_scale<T>(rin, V, c.st, f.dev, n, c.nrhs, c.s);
     for (int j = 0; j < m; ++j) {
         T* Vj = V + 2 * vs * j;
-        if (c.o.precond == HELM_PRECOND_NONE) {                        // z_j = v_j, w = A v_j
+        T* W = V + 2 * vs * (j + 1);                                    // A Z'_j, orthogonalised in place
+        if (c.o.precond == HELM_PRECOND_NONE) {                        // Z'_j = V'_j, w = A V'_j
             cudaMemcpyAsync(Z + 2 * vs * j, Vj, sizeof(T) * 2 * vs, cudaMemcpyDeviceToDevice, c.s);
             launch_apply<T>(level_dev(c.m, 0, sizeof(T) == 8), c.m->npml, c.m->alpha_max,
-                            static_cast<const T*>(sizeof(T) == 8 ? (const void*)c.w2 : (const void*)c.w2f), Vj, wv,
+                            static_cast<const T*>(sizeof(T) == 8 ? (const void*)c.w2 : (const void*)c.w2f), Vj, W,
                             T(1), c.nrhs, c.s);
         } else {
-            vcycle<T>(c, w, Vj, Z + 2 * vs * j, 3, wv, nullptr);        // z_j = M^-1 v_j, w = A z_j
+            vcycle<T>(c, w, Vj, Z + 2 * vs * j, 3, W, nullptr);         // Z'_j = M^-1 V'_j, w = A Z'_j
         }
-        launch_fg_dots<T>(V, vs, wv, j, 0, c.partials, c.pstride, c.st, f.dev, n, c.nrhs, c.s);
-        launch_fg_axpy<T>(V, vs, wv, j, 0, c.partials, c.pstride, c.st, f.dev, c.nactive, n, c.nrhs, c.s);
-        launch_fg_dots<T>(V, vs, wv, j, 1, c.partials, c.pstride, c.st, f.dev, n, c.nrhs, c.s);
-        launch_fg_axpy<T>(V, vs, wv, j, 1, c.partials, c.pstride, c.st, f.dev, c.nactive, n, c.nrhs, c.s);
-        if (j + 1 < m) launch_fg_scale<T>(wv, V + 2 * vs * (j + 1), c.st, f.dev, j, n, c.nrhs, c.s);
+        // first classical Gram-Schmidt pass; mode 0 leaves the column to the
+        // second pass, 1 finishes it, 2 decides per RHS
+        const int first = ro == HELM_REORTH_ALWAYS ? 0 : ro == HELM_REORTH_NEVER ? 1 : 2;
+        launch_fg_dots<T>(V, vs, W, j, 0, first == 2, 0, c.partials, c.pstride, c.st, f.dev, n, c.nrhs, c.s);
+        launch_fg_axpy<T>(V, vs, W, j, first, 0, c.partials, c.pstride, c.st, f.dev, c.nactive, n, c.nrhs, c.s);
+        if (ro != HELM_REORTH_NEVER) {
+            const int check = ro == HELM_REORTH_IFNEEDED;
+            launch_fg_dots<T>(V, vs, W, j, 1, 0, check, c.partials, c.pstride, c.st, f.dev, n, c.nrhs, c.s);
+            launch_fg_axpy<T>(V, vs, W, j, 1, check, c.partials, c.pstride, c.st, f.dev, c.nactive, n, c.nrhs, c.s);
+        }
     }
     launch_fg_backsolve(c.st, f.dev, c.nrhs, c.s);
     launch_fg_update<T>(Z, vs, w.x.template as<T>(), c.st, f.dev, n, c.nrhs, c.s);
@@ -385,7 +395,8 @@ static int fgmres_inner(const SolveCtx& c, Inner<T>& w, FgBufs<T>& f, const T* r
         fgmres_cycle<T>(c, w, f, rin);
     }
     const int m = f.dev.m;
-    count_launches(4 + (unsigned long long)m * ((c.o.precond == HELM_PRECOND_NONE ? 1 : mg_kernels_per_apply(c.m, sizeof(T) == 8, c.lf)) + 5));
+    count_launches(4 + (unsigned long long)m * ((c.o.precond == HELM_PRECOND_NONE ? 1 : mg_kernels_per_apply(c.m, sizeof(T) == 8, c.lf)) +
+                                                (c.o.reorth == HELM_REORTH_NEVER ? 2 : 4)));
     HELM_CUDA_TRY(cudaGetLastError());
     *iters_done += m;
     return HELM_OK;
@@ -446,7 +457,7 @@ static int solve_impl(const helm_model* m, cudaStream_t s, int nrhs, const doubl
     c.nrhs = nrhs;
     c.o = o;
     c.pstride = 3 * max_blocks_per_rhs(m);
-    if (o.krylov == HELM_KRYLOV_FGMRES) c.pstride = std::max(c.pstride, kFgPartials);
+    if (o.krylov == HELM_KRYLOV_FGMRES) c.pstride = std::max(c.pstride, fg_partials(m->n()));
     c.lf = fcycle_level(m, h_w2, nrhs);
     DBuf w2, w2f, st, part, nact, rin;
     TRY_ALLOC(w2, sizeof(double) * nrhs, s);

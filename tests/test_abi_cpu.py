@@ -77,3 +77,33 @@ def test_kernels_compile_for_sm103a_without_spills():
     assert r.returncode == 0, r.stderr
     spills = re.findall(r"(\d+) bytes spill stores", r.stderr)
     assert spills and all(int(s) == 0 for s in spills)
+
+
+def test_ctypes_structs_match_the_c_layout(tmp_path):
+    """Every struct the binding mirrors has the C compiler's size and field
+    offsets (include/helm.h compiled as plain C by gcc)."""
+    import shutil
+    import subprocess
+
+    from paper_1712_08743_gb300 import _lib
+
+    gcc = shutil.which("gcc") or shutil.which("cc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    structs = [_lib.helm_solve_opts, _lib.helm_solve_stats, _lib.helm_request, _lib.helm_result]
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "helm.h"', "int main(void) {"]
+    for st in structs:
+        lines.append(f'printf("{st.__name__} size %zu\\n", sizeof({st.__name__}));')
+        for name, _ in st._fields_:
+            lines.append(f'printf("{st.__name__} {name} %zu\\n", offsetof({st.__name__}, {name}));')
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run([gcc, "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {tuple(l.split()[:2]): int(l.split()[2]) for l in out if l.strip()}
+    for st in structs:
+        assert got[(st.__name__, "size")] == C.sizeof(st), st.__name__
+        for name, _ in st._fields_:
+            assert got[(st.__name__, name)] == getattr(st, name).offset, (st.__name__, name)

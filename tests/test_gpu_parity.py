@@ -112,13 +112,16 @@ def test_unpreconditioned_solve_matches_oracle(hg, ctx, krylov):
     model.close()
 
 
+@pytest.mark.parametrize("reorth", ["always", "never", "ifneeded"])
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
-def test_fgmres_matches_oracle_and_bicgstab(hg, ctx, precision):
-    """Flexible GMRES (restart 20) on the small case and a batched pair of the batched
-    case: same wavefields as the oracle, and as BiCGSTAB, within the solve tolerance."""
+def test_fgmres_matches_oracle_and_bicgstab(hg, ctx, precision, reorth):
+    """Flexible GMRES (restart 20) with each Gram-Schmidt variant on the small case and
+    a batched pair of the batched case: same wavefields as the oracle, and as BiCGSTAB,
+    within the solve tolerance."""
     mdl = models.c1_model()
     model = hg.helm_create_model(ctx, mdl.slowness, mdl.h, mdl.npml, mdl.alpha_max)
-    opts = dict(tol=1e-10, precision=precision, krylov=hg.HELM_KRYLOV_FGMRES, restart=20)
+    ro = {"always": hg.HELM_REORTH_ALWAYS, "never": hg.HELM_REORTH_NEVER, "ifneeded": hg.HELM_REORTH_IFNEEDED}[reorth]
+    opts = dict(tol=1e-10, precision=precision, krylov=hg.HELM_KRYLOV_FGMRES, restart=20, reorth=ro)
     u, stats, st = hg.helm_solve(model, mdl.omegas, mdl.sources, opts=opts)
     ref = oracle.solve_fields(mdl.slowness, mdl.h, mdl.omegas[0], mdl.sources, mdl.npml, mdl.alpha_max)
     assert st == hg.HELM_OK and stats[0]["converged"], stats
@@ -211,6 +214,8 @@ def test_invalid_arguments(hg, ctx):
         hg.helm_solve(model, [2 * np.pi * 5], [[30, 0]])
     with pytest.raises(hg.HelmError):
         hg.helm_solve(model, [-1.0], [[3, 0]])
+    with pytest.raises(hg.HelmError):
+        hg.helm_solve(model, [2 * np.pi * 5], [[3, 0]], opts=dict(krylov=hg.HELM_KRYLOV_FGMRES, reorth=3))
     model.close()
 
 
