@@ -209,7 +209,8 @@ def run_reference(args):
 
 
 # ---------------------------------------------------------------- our arm
-KERNELS = (("bicg_xr", "HELM_KERNEL_BICG_XR"), ("prolong_fine", "HELM_KERNEL_PROLONG"),
+KERNELS = (("fg_axpy", "HELM_KERNEL_FG_AXPY"), ("fg_dots", "HELM_KERNEL_FG_DOTS"),
+           ("bicg_xr", "HELM_KERNEL_BICG_XR"), ("prolong_fine", "HELM_KERNEL_PROLONG"),
            ("restrict_fine", "HELM_KERNEL_RESTRICT"), ("stencil_apply", "HELM_KERNEL_APPLY"),
            ("bicg_p", "HELM_KERNEL_BICG_P"), ("resid64", "HELM_KERNEL_RESID64"))
 
@@ -381,7 +382,9 @@ def run_ours(args):
     # roofline of the dominant kernel and of the stencil, each timed alone on inputs > L2
     peak, peak_kind = measured_peaks()
     kern = time_kernels(lib, api, _lib, model, float(om[0]))
-    dom = "bicg_xr"
+    # the largest bandwidth-bound kernel of the timed step: the Gram-Schmidt update of
+    # FGMRES (Arnoldi step 4 of 10), or the x/r update of BiCGSTAB
+    dom = "fg_axpy" if args.krylov == "fgmres" else "bicg_xr"
     traffic = None
     prof = os.path.join(ROOT, "profiles", "traffic.json")
     if os.path.exists(prof):

@@ -235,7 +235,9 @@ typedef enum {
     HELM_KERNEL_BICG_XR = 3,  /* BiCGSTAB x and r update with its two dots, complex64 */
     HELM_KERNEL_RESID64 = 4,  /* FP64 true residual r = f - A u */
     HELM_KERNEL_BICG_P = 5,   /* BiCGSTAB p update, complex64 */
-    HELM_KERNEL_APPLY64 = 6   /* y = A u, complex128 */
+    HELM_KERNEL_APPLY64 = 6,  /* y = A u, complex128 */
+    HELM_KERNEL_FG_DOTS = 7,  /* FGMRES Gram-Schmidt dot products at Arnoldi step 4 (5 basis vectors), complex64 */
+    HELM_KERNEL_FG_AXPY = 8   /* FGMRES Gram-Schmidt update + norm + Hessenberg column at step 4, complex64 */
 } helm_kernel_id;
 int helm_time_kernel(helm_model* model, int kernel, int nrhs, double omega, int reps, double* ms_per_launch,
                      double* bytes_per_launch);

@@ -34,6 +34,8 @@ HELM_KERNEL_BICG_XR = 3
 HELM_KERNEL_RESID64 = 4
 HELM_KERNEL_BICG_P = 5
 HELM_KERNEL_APPLY64 = 6
+HELM_KERNEL_FG_DOTS = 7
+HELM_KERNEL_FG_AXPY = 8
 HELM_KRYLOV_BICGSTAB = 0
 HELM_KRYLOV_FGMRES = 1
 

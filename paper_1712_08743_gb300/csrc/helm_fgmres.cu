@@ -4,7 +4,7 @@
 // One call of the inner solver runs one FGMRES cycle of at most m Arnoldi steps
 // from a zero guess; restarts happen through the FP64 outer refinement, which
 // recomputes the true residual. The basis is stored unnormalised: V'_i = s_i V_i
-// with V_i orthonormal and s_i kept in FP64 (s_0 = 1), so A Z'_j is written
+// with V_i orthonormal and 1/s_i kept in FP64 (s_0 = 1), so A Z'_j is written
 // straight into slot j+1 and orthogonalised there, and no scaling pass is
 // needed. With Z_j = Z'_j / s_j the Arnoldi relation A Z_j = sum_i h_ij V_i holds
 // for h_ij = <V'_i, A Z'_j> / (s_i s_j) and h_{j+1,j} = s_{j+1} / s_j; the
@@ -72,7 +72,7 @@ __global__ void __launch_bounds__(256) k_fg_norm(const T* __restrict__ rin, doub
             S.flag = FLAG_RUNNING;
             S.active = acc[0] > 0.0;
             fg.g[(size_t)b * (fg.m + 1)] = make_double2(sqrt(acc[0]), 0.0);
-            fg.s[(size_t)b * (fg.m + 1)] = 1.0;
+            fg.sinv[(size_t)b * (fg.m + 1)] = 1.0;
             if (S.active) atomicAdd(nactive, 1);
         }
     }
@@ -171,7 +171,7 @@ __global__ void __launch_bounds__(256) k_fg_dots(const T* __restrict__ V, size_t
     // deterministic)
     const int nx = gridDim.x;
     const size_t col = (size_t)b * (fg.m + 1);
-    const double* s = fg.s + col;
+    const double* sinv = fg.sinv + col;
     const int nsum = j + 1 + (wnorm ? 1 : 0);
     for (int i = warp; i < nsum; i += nw) {
         const bool isn = i > j;
@@ -200,7 +200,7 @@ __global__ void __launch_bounds__(256) k_fg_dots(const T* __restrict__ V, size_t
             if (isn) {
                 fg.wn2[b] = re;
             } else {
-                const double si = s[i], inv2 = 1.0 / (si * si), invh = 1.0 / (si * s[j]);
+                const double si = sinv[i], inv2 = si * si, invh = si * sinv[j];
                 fg.tmp[col + i] = make_double2(re * inv2, im * inv2);
                 double2& h = fg.H[(col + i) * fg.m + j];
                 if (add) { h.x += re * invh; h.y += im * invh; } else { h = make_double2(re * invh, im * invh); }
@@ -211,62 +211,77 @@ __global__ void __launch_bounds__(256) k_fg_dots(const T* __restrict__ V, size_t
 }
 
 // Column j of the Arnoldi relation is complete (||w'|| = hn2^(1/2) after the
-// last pass): s_{j+1}, h_{j+1,j} = s_{j+1} / s_j, the previous Givens rotations
-// on column j, the new rotation zeroing h_{j+1,j}, and the convergence test
-// |g_{j+1}| <= tol_rel * beta.
+// last pass): 1/s_{j+1}, h_{j+1,j} = s_{j+1} / s_j, the previous Givens
+// rotations on column j, the new rotation zeroing h_{j+1,j}, and the
+// convergence test |g_{j+1}| <= tol_rel * beta. Called by every thread of one
+// block: the column and the rotations are staged in shared memory, so the
+// serial FP64 chain of thread 0 waits on no global load; it takes three square
+// roots and two divisions.
 __device__ void fg_finish_column(RhsState& S, const FgDev& fg, int b, int j, double hn2, int* nactive) {
+    __shared__ double2 hc[kMaxRestart + 1];
+    __shared__ double2 sc[kMaxRestart];
+    __shared__ double cc[kMaxRestart];
     const int m = fg.m;
     const size_t col = (size_t)b * (m + 1);
     double2* H = fg.H + col * m;                   // H[i * m + j]
-    const double sn1 = sqrt(hn2);
-    fg.s[col + j + 1] = sn1;
-    const double hn = sn1 / fg.s[col + j];
-    // previous rotations on column j
-    for (int i = 0; i < j; ++i) {
-        const double c = fg.cs[(size_t)b * m + i];
-        const double2 s = fg.sn[(size_t)b * m + i];
-        const double2 a = H[(size_t)i * m + j], d = H[(size_t)(i + 1) * m + j];
-        // [a; d] <- [c a + s d; -conj(s) a + c d]
-        H[(size_t)i * m + j] = make_double2(c * a.x + s.x * d.x - s.y * d.y, c * a.y + s.x * d.y + s.y * d.x);
-        H[(size_t)(i + 1) * m + j] = make_double2(-(s.x * a.x + s.y * a.y) + c * d.x, -(s.x * a.y - s.y * a.x) + c * d.y);
+    for (int i = threadIdx.x; i <= j; i += blockDim.x) hc[i] = H[(size_t)i * m + j];
+    for (int i = threadIdx.x; i < j; i += blockDim.x) {
+        cc[i] = fg.cs[(size_t)b * m + i];
+        sc[i] = fg.sn[(size_t)b * m + i];
     }
-    // new rotation zeroing h_{j+1,j}
-    const double2 a = H[(size_t)j * m + j];
-    const double bb = hn;
-    const double an = sqrt(a.x * a.x + a.y * a.y);
-    double c;
-    double2 s;
-    if (an == 0.0) { c = 0.0; s = make_double2(1.0, 0.0); }
-    else {
-        const double t = sqrt(an * an + bb * bb);
-        c = an / t;
-        s = make_double2(a.x / an * bb / t, a.y / an * bb / t);   // (a/|a|) conj(b) / t, b real
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const double sn1 = sqrt(hn2);
+        fg.sinv[col + j + 1] = sn1 > 0.0 ? 1.0 / sn1 : 0.0;
+        const double hn = sn1 * fg.sinv[col + j];
+        // previous rotations on column j: [a; d] <- [c a + s d; -conj(s) a + c d]
+        double2 a = hc[0];
+        for (int i = 0; i < j; ++i) {
+            const double c = cc[i];
+            const double2 sv = sc[i], d = hc[i + 1];
+            hc[i] = make_double2(c * a.x + sv.x * d.x - sv.y * d.y, c * a.y + sv.x * d.y + sv.y * d.x);
+            a = make_double2(-(sv.x * a.x + sv.y * a.y) + c * d.x, -(sv.x * a.y - sv.y * a.x) + c * d.y);
+        }
+        // new rotation zeroing h_{j+1,j}: c = |a| / t, s = (a / |a|) h / t, t = (|a|^2 + h^2)^(1/2)
+        const double a2 = a.x * a.x + a.y * a.y, t2 = a2 + hn * hn;
+        double c;
+        double2 sv, hjj;
+        if (a2 == 0.0) { c = 0.0; sv = make_double2(1.0, 0.0); hjj = make_double2(hn, 0.0); }
+        else {
+            const double inv = 1.0 / (sqrt(a2) * sqrt(t2));   // 1 / (|a| t)
+            c = a2 * inv;
+            sv = make_double2(a.x * hn * inv, a.y * hn * inv);
+            hjj = make_double2(a.x * t2 * inv, a.y * t2 * inv);   // (a / |a|) t
+        }
+        hc[j] = hjj;
+        fg.cs[(size_t)b * m + j] = c;
+        fg.sn[(size_t)b * m + j] = sv;
+        double2* g = fg.g + col;
+        const double2 gj = g[j];
+        const double2 g1 = make_double2(-(sv.x * gj.x + sv.y * gj.y), -(sv.x * gj.y - sv.y * gj.x));   // -conj(s) g_j
+        g[j + 1] = g1;
+        g[j] = make_double2(c * gj.x, c * gj.y);
+        S.kfg = j + 1;
+        S.iters += 1;
+        const double res2 = g1.x * g1.x + g1.y * g1.y;
+        S.rnorm2 = res2;
+        int done = 0;
+        if (res2 <= S.tol_rel * S.tol_rel * S.bnorm2 || hn == 0.0) { done = 1; S.flag = FLAG_CONVERGED; }
+        else if (j + 1 >= m) { done = 1; S.flag = FLAG_MAXIT; }
+        else if (S.iters >= S.max_it) { done = 1; S.flag = FLAG_MAXIT; }
+        if (done) { S.active = 0; atomicSub(nactive, 1); }
     }
-    fg.cs[(size_t)b * m + j] = c;
-    fg.sn[(size_t)b * m + j] = s;
-    const double t2 = sqrt(an * an + bb * bb);
-    H[(size_t)j * m + j] = an == 0.0 ? make_double2(bb, 0.0) : make_double2(a.x / an * t2, a.y / an * t2);
-    H[(size_t)(j + 1) * m + j] = make_double2(0.0, 0.0);
-    double2* g = fg.g + col;
-    const double2 gj = g[j];
-    g[j + 1] = make_double2(-(s.x * gj.x + s.y * gj.y), -(s.x * gj.y - s.y * gj.x));   // -conj(s) g_j
-    g[j] = make_double2(c * gj.x, c * gj.y);
-    S.kfg = j + 1;
-    S.iters += 1;
-    const double res = sqrt(g[j + 1].x * g[j + 1].x + g[j + 1].y * g[j + 1].y);
-    S.rnorm2 = res * res;
-    int done = 0;
-    if (res <= S.tol_rel * sqrt(S.bnorm2) || hn == 0.0) { done = 1; S.flag = FLAG_CONVERGED; }
-    else if (j + 1 >= m) { done = 1; S.flag = FLAG_MAXIT; }
-    else if (S.iters >= S.max_it) { done = 1; S.flag = FLAG_MAXIT; }
-    if (done) { S.active = 0; atomicSub(nactive, 1); }
+    __syncthreads();
+    for (int i = threadIdx.x; i <= j; i += blockDim.x) H[(size_t)i * m + j] = hc[i];
+    if (threadIdx.x == 0) H[(size_t)(j + 1) * m + j] = make_double2(0.0, 0.0);
 }
 
 // w -= sum_{i <= j} tmp_i V'_i in place (w is basis slot j+1). mode 0: no norm
 // (a second pass follows); mode 1: ||w||^2 and the column is finished; mode 2:
 // ||w||^2, then a second pass is requested (S.reorth = 1) if ||w||^2 < wn2 / 2,
-// else the column is finished. With `check` an RHS whose first pass asked for
-// no second pass skips the kernel.
+// else the column is finished; mode 3: each block writes its part of ||w||^2
+// and k_fg_finish finishes the column (off the critical path). With `check` an
+// RHS whose first pass asked for no second pass skips the kernel.
 template <typename T, int NV>
 __global__ void __launch_bounds__(256) k_fg_axpy(const T* __restrict__ V, size_t vstride, T* __restrict__ w, int j,
                                                  int mode, int check, double* partials, int pstride, RhsState* st,
@@ -314,17 +329,42 @@ __global__ void __launch_bounds__(256) k_fg_axpy(const T* __restrict__ V, size_t
     if (mode == 0) return;
     const T vv[1] = {a0};
     double acc[1];
-    if (last_block_reduce_t<1, T>(vv, acc, sh, partials + (size_t)b * pstride, gridDim.x, blockIdx.x, &st[b].counter[0])) {
-        if (threadIdx.x == 0) {
-            RhsState& S = st[b];
-            if (mode == 2 && acc[0] < 0.5 * fg.wn2[b]) {
-                S.reorth = 1;
-            } else {
-                S.reorth = 0;
-                fg_finish_column(S, fg, b, j, acc[0], nactive);
-            }
-        }
+    if (mode == 3) {
+        block_sum_t<1, T>(vv, acc, sh);
+        if (threadIdx.x == 0) partials[(size_t)b * pstride + blockIdx.x] = acc[0];
+        return;
     }
+    if (last_block_reduce_t<1, T>(vv, acc, sh, partials + (size_t)b * pstride, gridDim.x, blockIdx.x, &st[b].counter[0])) {
+        __shared__ int s_finish;
+        __shared__ double s_hn2;
+        if (threadIdx.x == 0) {
+            const int second = mode == 2 && acc[0] < 0.5 * fg.wn2[b];
+            st[b].reorth = second;
+            s_finish = !second;
+            s_hn2 = acc[0];
+        }
+        __syncthreads();
+        if (s_finish) fg_finish_column(st[b], fg, b, j, s_hn2, nactive);
+    }
+}
+
+// Finishes column j from the per-block parts of ||w||^2 that k_fg_axpy (mode 3)
+// wrote: one block per RHS sums the nblk parts in a fixed order, then
+// fg_finish_column. Runs on a second stream, beside the next preconditioner
+// application, which reads only w.
+__global__ void __launch_bounds__(256) k_fg_finish(const double* partials, int pstride, int nblk, RhsState* st,
+                                                   FgDev fg, int j, int* nactive) {
+    __shared__ double sh[32];
+    __shared__ double s_hn2;
+    const int b = blockIdx.x;
+    if (!st[b].active) return;
+    const double* part = partials + (size_t)b * pstride;
+    double v[1] = {0.0};
+    for (int i = threadIdx.x; i < nblk; i += blockDim.x) v[0] += __ldcg(part + i);
+    block_sum<1>(v, sh);
+    if (threadIdx.x == 0) s_hn2 = v[0];
+    __syncthreads();
+    fg_finish_column(st[b], fg, b, j, s_hn2, nactive);
 }
 
 // y = R^{-1} g on the k = kfg leading rows (FP64), one warp per RHS: the warp
@@ -373,7 +413,7 @@ __global__ void k_fg_update(const T* __restrict__ Z, size_t zstride, T* __restri
     const int k = st[b].kfg;
     for (int i = threadIdx.x; i < k; i += blockDim.x) {
         const double2 y = fg.y[(size_t)b * fg.m + i];
-        const double inv = 1.0 / fg.s[(size_t)b * (fg.m + 1) + i];
+        const double inv = fg.sinv[(size_t)b * (fg.m + 1) + i];
         coef[i] = cx<T>((T)(y.x * inv), (T)(y.y * inv));
     }
     __syncthreads();
@@ -420,18 +460,24 @@ void launch_fg_dots(const T* V, size_t vstride, const T* w, int j, int add, int 
     else fg_dots_nv<T, kChunk>(V, vstride, w, j, add, wnorm, check, partials, pstride, st, fg, n, nrhs, s);
 }
 template <typename T, int NV>
-static void fg_axpy_nv(const T* V, size_t vstride, T* w, int j, int mode, int check, double* partials, int pstride,
-                       RhsState* st, const FgDev& fg, int* nactive, size_t n, int nrhs, cudaStream_t s) {
-    k_fg_axpy<T, NV><<<dim3(fg_grid<k_fg_axpy<T, NV>>(n), 1, nrhs), 256, 0, s>>>(V, vstride, w, j, mode, check,
-                                                                                partials, pstride, st, fg, nactive, n);
+static int fg_axpy_nv(const T* V, size_t vstride, T* w, int j, int mode, int check, double* partials, int pstride,
+                      RhsState* st, const FgDev& fg, int* nactive, size_t n, int nrhs, cudaStream_t s) {
+    const int grid = fg_grid<k_fg_axpy<T, NV>>(n);
+    k_fg_axpy<T, NV><<<dim3(grid, 1, nrhs), 256, 0, s>>>(V, vstride, w, j, mode, check, partials, pstride, st, fg,
+                                                          nactive, n);
+    return grid;
 }
 template <typename T>
-void launch_fg_axpy(const T* V, size_t vstride, T* w, int j, int mode, int check, double* partials, int pstride,
-                    RhsState* st, const FgDev& fg, int* nactive, size_t n, int nrhs, cudaStream_t s) {
-    if (j < 1) fg_axpy_nv<T, 1>(V, vstride, w, j, mode, check, partials, pstride, st, fg, nactive, n, nrhs, s);
-    else if (j < 2) fg_axpy_nv<T, 2>(V, vstride, w, j, mode, check, partials, pstride, st, fg, nactive, n, nrhs, s);
-    else if (j < 4) fg_axpy_nv<T, 4>(V, vstride, w, j, mode, check, partials, pstride, st, fg, nactive, n, nrhs, s);
-    else fg_axpy_nv<T, kChunk>(V, vstride, w, j, mode, check, partials, pstride, st, fg, nactive, n, nrhs, s);
+int launch_fg_axpy(const T* V, size_t vstride, T* w, int j, int mode, int check, double* partials, int pstride,
+                   RhsState* st, const FgDev& fg, int* nactive, size_t n, int nrhs, cudaStream_t s) {
+    if (j < 1) return fg_axpy_nv<T, 1>(V, vstride, w, j, mode, check, partials, pstride, st, fg, nactive, n, nrhs, s);
+    if (j < 2) return fg_axpy_nv<T, 2>(V, vstride, w, j, mode, check, partials, pstride, st, fg, nactive, n, nrhs, s);
+    if (j < 4) return fg_axpy_nv<T, 4>(V, vstride, w, j, mode, check, partials, pstride, st, fg, nactive, n, nrhs, s);
+    return fg_axpy_nv<T, kChunk>(V, vstride, w, j, mode, check, partials, pstride, st, fg, nactive, n, nrhs, s);
+}
+void launch_fg_finish(const double* partials, int pstride, int nblk, RhsState* st, const FgDev& fg, int j,
+                      int* nactive, int nrhs, cudaStream_t s) {
+    k_fg_finish<<<nrhs, 256, 0, s>>>(partials, pstride, nblk, st, fg, j, nactive);
 }
 void launch_fg_backsolve(const RhsState* st, const FgDev& fg, int nrhs, cudaStream_t s) {
     const size_t smem = sizeof(double2) * ((size_t)fg.m * fg.m + fg.m);
@@ -449,8 +495,8 @@ void launch_fg_update(const T* Z, size_t zstride, T* x, const RhsState* st, cons
     template void launch_fg_scale<T>(const T*, T*, const RhsState*, const FgDev&, size_t, int, cudaStream_t);       \
     template void launch_fg_dots<T>(const T*, size_t, const T*, int, int, int, int, double*, int, RhsState*,        \
                                     const FgDev&, size_t, int, cudaStream_t);                                       \
-    template void launch_fg_axpy<T>(const T*, size_t, T*, int, int, int, double*, int, RhsState*, const FgDev&,     \
-                                    int*, size_t, int, cudaStream_t);                                               \
+    template int launch_fg_axpy<T>(const T*, size_t, T*, int, int, int, double*, int, RhsState*, const FgDev&,      \
+                                   int*, size_t, int, cudaStream_t);                                                \
     template void launch_fg_update<T>(const T*, size_t, T*, const RhsState*, const FgDev&, size_t, int,             \
                                       cudaStream_t);
 HELM_FG_INST(float)

@@ -216,8 +216,8 @@ void launch_coarse_invert(const LevelDev& Lc, const double* w2_slots, const int*
 
 // FGMRES state on the device, per RHS: Hessenberg H [(m+1) x m], rotated
 // right-hand side g [m+1], Givens cosines cs / sines sn [m], solution y [m],
-// projection coefficients tmp [m+1], the norms s [m+1] of the unnormalised
-// basis vectors, and ||w||^2 before Gram-Schmidt wn2 [1].
+// projection coefficients tmp [m+1], the inverse norms sinv [m+1] of the
+// unnormalised basis vectors, and ||w||^2 before Gram-Schmidt wn2 [1].
 struct FgDev {
     int m;
     double2* H;
@@ -226,7 +226,7 @@ struct FgDev {
     double2* sn;
     double2* y;
     double2* tmp;
-    double* s;
+    double* sinv;
     double* wn2;
 };
 template <typename T>
@@ -237,11 +237,15 @@ void launch_fg_scale(const T* rin, T* v, const RhsState* st, const FgDev& fg, si
 template <typename T>
 void launch_fg_dots(const T* V, size_t vstride, const T* w, int j, int add, int wnorm, int check, double* partials,
                     int pstride, RhsState* st, const FgDev& fg, size_t n, int nrhs, cudaStream_t s);
+// returns the blocks per RHS it launched (the parts of ||w||^2 in mode 3)
 template <typename T>
-void launch_fg_axpy(const T* V, size_t vstride, T* w, int j, int mode, int check, double* partials, int pstride,
-                    RhsState* st, const FgDev& fg, int* nactive, size_t n, int nrhs, cudaStream_t s);
+int launch_fg_axpy(const T* V, size_t vstride, T* w, int j, int mode, int check, double* partials, int pstride,
+                   RhsState* st, const FgDev& fg, int* nactive, size_t n, int nrhs, cudaStream_t s);
+void launch_fg_finish(const double* partials, int pstride, int nblk, RhsState* st, const FgDev& fg, int j,
+                      int* nactive, int nrhs, cudaStream_t s);
 void launch_fg_backsolve(const RhsState* st, const FgDev& fg, int nrhs, cudaStream_t s);
 int fg_partials(size_t n);   // reduction partials per RHS the FGMRES kernels need on n points
+constexpr int kFgTimedStep = 4;   // Arnoldi step that helm_time_kernel times (the middle of FGMRES(10))
 template <typename T>
 void launch_fg_update(const T* Z, size_t zstride, T* x, const RhsState* st, const FgDev& fg, size_t n, int nrhs,
                       cudaStream_t s);

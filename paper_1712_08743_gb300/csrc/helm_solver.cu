@@ -91,6 +91,19 @@ struct SolveCtx {
     int ncoarse;
     const void* minv;       // float2* or double2* [nslots][n][n]
     int lf;                 // first level of the F-cycle for this batch
+    cudaStream_t side = nullptr;    // FGMRES: the Hessenberg column finish runs here
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+};
+
+// The second stream and events of an FGMRES solve.
+struct SideStream {
+    cudaStream_t s = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
+    ~SideStream() {
+        if (fork) cudaEventDestroy(fork);
+        if (join) cudaEventDestroy(join);
+        if (s) cudaStreamDestroy(s);
+    }
 };
 
 template <typename T>
@@ -334,7 +347,7 @@ static int alloc_fg(const SolveCtx& c, FgBufs<T>& f) {
     f.dev.sn = f.sn.template as<double2>();
     f.dev.y = f.y.template as<double2>();
     f.dev.tmp = f.tmp.template as<double2>();
-    f.dev.s = f.sc.template as<double>();
+    f.dev.sinv = f.sc.template as<double>();
     f.dev.wn2 = f.wn2.template as<double>();
     return HELM_OK;
 }
@@ -349,6 +362,7 @@ static void fgmres_cycle(const SolveCtx& c, Inner<T>& w, FgBufs<T>& f, const T* 
     T* Z = f.Z.template as<T>();
     launch_fg_norm<T>(rin, c.partials, c.pstride, c.st, f.dev, c.nactive, n, c.nrhs, c.s);
     launch_fg_scale<T>(rin, V, c.st, f.dev, n, c.nrhs, c.s);
+    bool pending = false;   // a column finish runs on the side stream
     for (int j = 0; j < m; ++j) {
         T* Vj = V + 2 * vs * j;
         T* W = V + 2 * vs * (j + 1);                                    // A Z'_j, orthogonalised in place
@@ -360,17 +374,33 @@ static void fgmres_cycle(const SolveCtx& c, Inner<T>& w, FgBufs<T>& f, const T* 
         } else {
             vcycle<T>(c, w, Vj, Z + 2 * vs * j, 3, W, nullptr);         // Z'_j = M^-1 V'_j, w = A Z'_j
         }
-        // first classical Gram-Schmidt pass; mode 0 leaves the column to the
-        // second pass, 1 finishes it, 2 decides per RHS
-        const int first = ro == HELM_REORTH_ALWAYS ? 0 : ro == HELM_REORTH_NEVER ? 1 : 2;
-        launch_fg_dots<T>(V, vs, W, j, 0, first == 2, 0, c.partials, c.pstride, c.st, f.dev, n, c.nrhs, c.s);
-        launch_fg_axpy<T>(V, vs, W, j, first, 0, c.partials, c.pstride, c.st, f.dev, c.nactive, n, c.nrhs, c.s);
-        if (ro != HELM_REORTH_NEVER) {
-            const int check = ro == HELM_REORTH_IFNEEDED;
-            launch_fg_dots<T>(V, vs, W, j, 1, 0, check, c.partials, c.pstride, c.st, f.dev, n, c.nrhs, c.s);
-            launch_fg_axpy<T>(V, vs, W, j, 1, check, c.partials, c.pstride, c.st, f.dev, c.nactive, n, c.nrhs, c.s);
+        // the dot products of this step need 1/s_j from the previous column's finish
+        if (pending) { cudaStreamWaitEvent(c.s, c.ev_join, 0); pending = false; }
+        int nblk = 0;
+        if (ro == HELM_REORTH_IFNEEDED) {
+            // first pass decides per RHS whether a second one follows; the column
+            // is finished by the last pass's last block
+            launch_fg_dots<T>(V, vs, W, j, 0, 1, 0, c.partials, c.pstride, c.st, f.dev, n, c.nrhs, c.s);
+            launch_fg_axpy<T>(V, vs, W, j, 2, 0, c.partials, c.pstride, c.st, f.dev, c.nactive, n, c.nrhs, c.s);
+            launch_fg_dots<T>(V, vs, W, j, 1, 0, 1, c.partials, c.pstride, c.st, f.dev, n, c.nrhs, c.s);
+            launch_fg_axpy<T>(V, vs, W, j, 1, 1, c.partials, c.pstride, c.st, f.dev, c.nactive, n, c.nrhs, c.s);
+            continue;
         }
+        launch_fg_dots<T>(V, vs, W, j, 0, 0, 0, c.partials, c.pstride, c.st, f.dev, n, c.nrhs, c.s);
+        if (ro == HELM_REORTH_ALWAYS) {
+            launch_fg_axpy<T>(V, vs, W, j, 0, 0, c.partials, c.pstride, c.st, f.dev, c.nactive, n, c.nrhs, c.s);
+            launch_fg_dots<T>(V, vs, W, j, 1, 0, 0, c.partials, c.pstride, c.st, f.dev, n, c.nrhs, c.s);
+        }
+        // last pass: per-block parts of ||w||^2; the column is finished on the side
+        // stream while the next preconditioner application (which reads only w) runs
+        nblk = launch_fg_axpy<T>(V, vs, W, j, 3, 0, c.partials, c.pstride, c.st, f.dev, c.nactive, n, c.nrhs, c.s);
+        cudaEventRecord(c.ev_fork, c.s);
+        cudaStreamWaitEvent(c.side, c.ev_fork, 0);
+        launch_fg_finish(c.partials, c.pstride, nblk, c.st, f.dev, j, c.nactive, c.nrhs, c.side);
+        cudaEventRecord(c.ev_join, c.side);
+        pending = true;
     }
+    if (pending) cudaStreamWaitEvent(c.s, c.ev_join, 0);
     launch_fg_backsolve(c.st, f.dev, c.nrhs, c.s);
     launch_fg_update<T>(Z, vs, w.x.template as<T>(), c.st, f.dev, n, c.nrhs, c.s);
 }
@@ -396,7 +426,7 @@ static int fgmres_inner(const SolveCtx& c, Inner<T>& w, FgBufs<T>& f, const T* r
     }
     const int m = f.dev.m;
     count_launches(4 + (unsigned long long)m * ((c.o.precond == HELM_PRECOND_NONE ? 1 : mg_kernels_per_apply(c.m, sizeof(T) == 8, c.lf)) +
-                                                (c.o.reorth == HELM_REORTH_NEVER ? 2 : 4)));
+                                                (c.o.reorth == HELM_REORTH_NEVER ? 3 : c.o.reorth == HELM_REORTH_ALWAYS ? 5 : 4)));
     HELM_CUDA_TRY(cudaGetLastError());
     *iters_done += m;
     return HELM_OK;
@@ -482,7 +512,14 @@ static int solve_impl(const helm_model* m, cudaStream_t s, int nrhs, const doubl
     if (rc != HELM_OK) return rc;
     const bool fgm = o.krylov == HELM_KRYLOV_FGMRES;
     FgBufs<T> fb;
+    SideStream side;
     if (fgm) {
+        HELM_CUDA_TRY(cudaStreamCreateWithFlags(&side.s, cudaStreamNonBlocking));
+        HELM_CUDA_TRY(cudaEventCreateWithFlags(&side.fork, cudaEventDisableTiming));
+        HELM_CUDA_TRY(cudaEventCreateWithFlags(&side.join, cudaEventDisableTiming));
+        c.side = side.s;
+        c.ev_fork = side.fork;
+        c.ev_join = side.join;
         rc = alloc_fg<T>(c, fb);
         if (rc != HELM_OK) return rc;
     }
@@ -620,8 +657,9 @@ int time_kernel(const helm_model* m, cudaStream_t s, int kernel, int nrhs, doubl
         // byte 0x3C gives small normal, non-zero values in both precisions
         HELM_CUDA_TRY(cudaMemsetAsync(v[k]->p, 0x3C, dbl ? v64 : v32, s));
     }
-    DBuf w2, w2f, st, part, nact, fc, rin;
-    const int pstride = 3 * max_blocks_per_rhs(m);
+    DBuf w2, w2f, st, part, nact, fc, rin, fgV, fgH, fgSmall;
+    FgDev fgd{};
+    const int pstride = std::max(3 * max_blocks_per_rhs(m), fg_partials(n));
     TRY_ALLOC(w2, sizeof(double) * nrhs, s);
     TRY_ALLOC(w2f, sizeof(float) * nrhs, s);
     TRY_ALLOC(st, sizeof(RhsState) * nrhs, s);
@@ -677,6 +715,45 @@ int time_kernel(const helm_model* m, cudaStream_t s, int kernel, int nrhs, doubl
             launch = [&] { launch_resid64<float>(level_dev(m, 0, true), m->npml, m->alpha_max, w2.as<double>(), D(0), D(1), rin.as<float>(), part.as<double>(), pstride, S, 0.0, 1e-4, 0.9, 0, nrhs, s); };
             *bytes = N * (40.0 * B + 8.0);
             break;
+        case HELM_KERNEL_FG_DOTS:
+        case HELM_KERNEL_FG_AXPY: {
+            // Arnoldi step j = kFgTimedStep of FGMRES(10): basis slots 0..j, w in slot j + 1
+            const int j = kFgTimedStep, mres = 10;
+            const size_t vs = n * nrhs;
+            TRY_ALLOC(fgV, sizeof(float) * 2 * vs * (j + 2), s);
+            HELM_CUDA_TRY(cudaMemsetAsync(fgV.p, 0x3C, sizeof(float) * 2 * vs * (j + 2), s));
+            const size_t nb = (size_t)nrhs;
+            TRY_ALLOC(fgH, sizeof(double2) * nb * (mres + 1) * mres, s);
+            TRY_ALLOC(fgSmall, sizeof(double2) * nb * 8 * (mres + 1), s);
+            HELM_CUDA_TRY(cudaMemsetAsync(fgH.p, 0, sizeof(double2) * nb * (mres + 1) * mres, s));
+            HELM_CUDA_TRY(cudaMemsetAsync(fgSmall.p, 0, sizeof(double2) * nb * 8 * (mres + 1), s));
+            // basis norms s_i = 1 and projection coefficients 1e-3 (w stays finite over the launches)
+            std::vector<double> ones(nb * (mres + 1), 1.0);
+            std::vector<double2> coef(nb * (mres + 1), make_double2(1e-3, 0.0));
+            double2* small = fgSmall.as<double2>();
+            fgd.m = mres;
+            fgd.H = fgH.as<double2>();
+            fgd.g = small;
+            fgd.sn = small + nb * (mres + 1);
+            fgd.y = small + 2 * nb * (mres + 1);
+            fgd.tmp = small + 3 * nb * (mres + 1);
+            fgd.cs = reinterpret_cast<double*>(small + 4 * nb * (mres + 1));
+            fgd.sinv = reinterpret_cast<double*>(small + 5 * nb * (mres + 1));
+            fgd.wn2 = reinterpret_cast<double*>(small + 6 * nb * (mres + 1));
+            HELM_CUDA_TRY(cudaMemcpyAsync(fgd.sinv, ones.data(), sizeof(double) * ones.size(), cudaMemcpyHostToDevice, s));
+            HELM_CUDA_TRY(cudaMemcpyAsync(fgd.tmp, coef.data(), sizeof(double2) * coef.size(), cudaMemcpyHostToDevice, s));
+            HELM_CUDA_TRY(cudaStreamSynchronize(s));   // the host vectors above are sources of async copies
+            float* Vb = fgV.as<float>();
+            float* Wb = Vb + 2 * vs * (j + 1);
+            if (kernel == HELM_KERNEL_FG_DOTS) {
+                launch = [&, j, vs, Vb, Wb] { launch_fg_dots<float>(Vb, vs, Wb, j, 0, 0, 0, part.as<double>(), pstride, S, fgd, n, nrhs, s); };
+                *bytes = N * B * 8.0 * (j + 2);
+            } else {
+                launch = [&, j, vs, Vb, Wb] { launch_fg_axpy<float>(Vb, vs, Wb, j, 1, 0, part.as<double>(), pstride, S, fgd, nact.as<int>(), n, nrhs, s); };
+                *bytes = N * B * 8.0 * (j + 3);
+            }
+            break;
+        }
         default:
             return HELM_E_INVALID;
     }
