@@ -56,14 +56,16 @@ def parse():
                     help="FGMRES Gram-Schmidt: second pass always (CGS2), never, or by the DGKS test")
     ap.add_argument("--inner-tol", type=float, default=5e-2, help="mixed precision: reduction per inner solve")
     ap.add_argument("--tune", action="store_true", help="autotune the multigrid tiles before timing")
-    ap.add_argument("--workload", default="single", choices=["single", "batched", "serving", "gn", "ablation"],
+    ap.add_argument("--workload", default="single", choices=["single", "batched", "serving", "gn", "ablation", "fwi"],
                     help="single: the single large case (the default line); batched: 64 shots x 5 "
                          "frequencies in one call; serving: a Poisson stream of requests; gn: one "
                          "Gauss-Newton iteration of the gradient case; ablation: preconditioner on/off")
     ap.add_argument("--kernels-only", action="store_true",
                     help="time only the hot kernels alone (the roofline legs), print one line per kernel")
     ap.add_argument("--requests", type=int, default=48, help="serving: number of requests")
-    ap.add_argument("--cg", type=int, default=5, help="gn: conjugate-gradient iterations per Gauss-Newton step")
+    ap.add_argument("--cg", type=int, default=5, help="gn, fwi: conjugate-gradient iterations per Gauss-Newton step")
+    ap.add_argument("--gn", type=int, default=2, help="fwi: Gauss-Newton iterations per frequency group")
+    ap.add_argument("--fwi-strategy", default="sequential", choices=["sequential", "simultaneous"])
     ap.add_argument("--rate", type=float, default=0.0, help="serving: arrivals per second (0: 0.8 x measured)")
     return ap.parse_args()
 
@@ -541,6 +543,57 @@ def run_gn(args):
     ctx.close()
 
 
+def run_fwi(args):
+    """The Gauss-Newton inversion loop on the gradient case (401 x 201, 32 shots,
+    201 receivers, 3..6 Hz, lambda = 1e-3, smoothed start): `--fwi-strategy`
+    sequential (one frequency at a time from the lowest, as in the paper's 2D
+    example) or simultaneous (all at once, as in its 1D example), `--gn` Gauss-Newton
+    iterations per group of `--cg` CG iterations each, with backtracking. Reports
+    accepted iterations per second, the misfit history and the model error."""
+    import torch
+
+    import oracle
+    from paper_1712_08743_gb300 import _lib, api, build
+    from synth import models
+
+    build.build()
+    _lib.load()
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    ctx = api.Context(0, stream)
+    true, start = models.c4_models()
+    om = true.omegas
+    d_obs = np.stack([oracle.sample_receivers(
+        oracle.solve_fields(true.slowness, true.h, w, true.sources, true.npml, true.alpha_max), true.receivers,
+        true.npml) for w in om])
+    opts = dict(tol=1e-6, precision="mixed")
+    lam = 1e-3
+    bounds = (1 / 4500.0, 1 / 1400.0)
+
+    def run(strategy, gn):
+        t0 = time.perf_counter()
+        m, hist, st = api.helm_fwi_run(ctx, start.slowness, start.h, om, start.sources, start.receivers, d_obs, lam,
+                                       strategy=strategy, gn_iters=gn, cg_iters=args.cg, max_halvings=4,
+                                       m_bounds=bounds, npml=start.npml, alpha_max=start.alpha_max, opts=opts)
+        return m, hist, st, time.perf_counter() - t0
+
+    for _ in range(max(args.warmup, 0)):
+        run("simultaneous", 1)
+    results = [run(args.fwi_strategy, args.gn) for _ in range(max(args.steps, 1))]
+    m, hist, st, _ = results[-1]
+    wall = float(np.mean([r[3] for r in results]))
+    ngroups = len(om) if args.fwi_strategy == "sequential" else 1
+    accepted = len(hist) - ngroups
+    err0 = float(np.linalg.norm(start.slowness - true.slowness))
+    print(json.dumps({"metric": "fwi_gauss_newton_iterations_per_s", "workload": "fwi_401x201_32shots_4f",
+                      "strategy": args.fwi_strategy, "value": accepted / wall, "unit": "iterations/s",
+                      "wall_s": wall, "accepted_iterations": accepted, "groups": ngroups, "gn_per_group": args.gn,
+                      "cg_iters": args.cg, "misfit_history": [float(x) for x in hist],
+                      "model_error_rel": float(np.linalg.norm(m - true.slowness)) / err0, "status": int(st)}),
+          flush=True)
+    ctx.close()
+
+
 def run_ablation(args):
     """Preconditioner ablation on the batched case's model (401 x 201 physical,
     h = 10 m), one surface source, 3, 5 and 7 Hz: Krylov iterations and time to
@@ -637,6 +690,8 @@ def main():
         run_batched(args)
     elif args.workload == "gn":
         run_gn(args)
+    elif args.workload == "fwi":
+        run_fwi(args)
     elif args.workload == "ablation":
         run_ablation(args)
     elif args.workload == "serving":

@@ -208,6 +208,48 @@ int helm_gn_hvp(helm_fwi_state* state, const double* dm, double* hdm_out, const 
 int helm_gn_step(helm_fwi_state* state, const double* grad, int cg_iters, double* dm_out, double* cg_rel_out,
                  const helm_solve_opts* opts);
 
+/* Gauss-Newton full-waveform inversion loop (Eq. 4-9 repeated, the way the
+ * paper's examples run it). The frequencies are inverted either all at once
+ * (HELM_FWI_SIMULTANEOUS, the paper's 1D example) or one at a time from the
+ * lowest up, each starting from the model the previous one ended with
+ * (HELM_FWI_SEQUENTIAL, the paper's 2D example). Every iteration of a group:
+ * forward solves and J at the current model, adjoint solves and the gradient
+ * (Eq. 7), the Gauss-Newton step dm = -H^{-1} grad by cg_iters CG iterations
+ * (Eq. 9, helm_gn_step), then a backtracking line search that the paper does
+ * not print: the trial m + t dm, clipped to [m_lo, m_hi], is accepted at the
+ * first t in 1, 1/2, ... (at most max_halvings halvings) whose J is below the
+ * current J; if none is, the group ends early. The accepted trial's forward
+ * solves serve the next iteration. */
+typedef enum { HELM_FWI_SIMULTANEOUS = 0, HELM_FWI_SEQUENTIAL = 1 } helm_fwi_strategy;
+typedef struct {
+    int strategy;       /* helm_fwi_strategy */
+    int gn_iters;       /* Gauss-Newton iterations per frequency group, >= 1 */
+    int cg_iters;       /* CG iterations per Gauss-Newton step, 1..1000 */
+    int max_halvings;   /* line-search halvings, 0..30 (0: the full step or nothing) */
+    double m_lo, m_hi;  /* slowness bounds of every trial model, 0 < m_lo <= m_hi */
+} helm_fwi_opts;
+/* Called after every accepted iteration (and once per group before its first):
+ * group index, iteration (0 = the group's starting model), the model m (host,
+ * float64 [Pz][Px], valid during the call) and its misfit J over the group's
+ * frequencies. */
+typedef void (*helm_fwi_checkpoint)(int group, int iter, const double* m, double J, void* user);
+/*  - m0: starting slowness, host float64 [Pz][Px]; m_out: host float64 [Pz][Px],
+ *    the final model (may alias m0).
+ *  - omega [nfreq], sources, receivers and lambda_reg as helm_adjoint_gradient;
+ *    d_obs: host c128 [nfreq][nshot][nrec].
+ *  - J_hist (nullable): host float64, room for ngroups * (gn_iters + 1) values
+ *    (ngroups = 1 or nfreq); gets each group's J at its start and after every
+ *    accepted iteration, in order; *n_hist (nullable) their count.
+ *  - checkpoint (nullable) with its user pointer.
+ *  - opts: the solves' options (device_ptrs must be 0; NULL = defaults).
+ * Returns HELM_E_INVALID for bad arguments, a solve's error status otherwise
+ * (m_out then holds the last accepted model). lambda_reg must be > 0. */
+int helm_fwi_run(helm_ctx* ctx, int Px, int Pz, double h, int npml, double alpha_max, const double* m0,
+                 int nfreq, const double* omega, int nshot, const int* src_ix, const int* src_iz, int nrec,
+                 const int* rec_ix, const int* rec_iz, const void* d_obs, double lambda_reg,
+                 const helm_fwi_opts* fwi_opts, const helm_solve_opts* opts, double* m_out, double* J_hist,
+                 int* n_hist, helm_fwi_checkpoint checkpoint, void* user);
+
 /* Operator application y = B(m, omega_k) u_k (Eq. 3) for parity checks and
  * bandwidth measurement. precision HELM_PREC_FP64: u, y c128; otherwise c64.
  * [nrhs][nz][nx] each, following device_ptrs. */
@@ -237,7 +279,7 @@ typedef enum {
     HELM_KERNEL_BICG_P = 5,   /* BiCGSTAB p update, complex64 */
     HELM_KERNEL_APPLY64 = 6,  /* y = A u, complex128 */
     HELM_KERNEL_FG_DOTS = 7,  /* FGMRES Gram-Schmidt dot products at Arnoldi step 4 (5 basis vectors), complex64 */
-    HELM_KERNEL_FG_AXPY = 8   /* FGMRES Gram-Schmidt update + norm + Hessenberg column at step 4, complex64 */
+    HELM_KERNEL_FG_AXPY = 8   /* FGMRES Gram-Schmidt update + per-block norm parts at step 4, complex64 */
 } helm_kernel_id;
 int helm_time_kernel(helm_model* model, int kernel, int nrhs, double omega, int reps, double* ms_per_launch,
                      double* bytes_per_launch);

@@ -23,4 +23,4 @@ from .helmholtz import (  # noqa: F401
     solve_fields,
     Factorised,
 )
-from .gauss_newton import gn_hvp, gn_step  # noqa: F401,E402
+from .gauss_newton import fwi_run, gn_hvp, gn_step  # noqa: F401,E402

@@ -73,3 +73,46 @@ def gn_step(m_phys, h, omegas, src_phys, rec_phys, lam, grad, iters, npml=20, al
         p = r + (rr_new / rr) * p
         rr = rr_new
     return dm, np.array(rel)
+
+
+def fwi_run(m0, h, omegas, src_phys, rec_phys, d_obs, lam, strategy="sequential", gn_iters=2, cg_iters=5,
+            max_halvings=4, m_bounds=(1 / 6000.0, 1 / 1000.0), npml=20, alpha_max=0.5):
+    """The Gauss-Newton inversion loop the paper's examples run (Section
+    "Examples"): all frequencies at once ("simultaneous", its 1D example) or one
+    at a time from the lowest, each starting from the previous model
+    ("sequential", its 2D example). Each iteration: the gradient of Eq. 7 at the
+    current model, the step dm of Eq. 9 by `cg_iters` CG iterations, then m + t dm
+    (clipped to m_bounds) for the first t in 1, 1/2, ... (at most `max_halvings`
+    halvings) whose misfit is below the current one; a group ends early when no
+    t lowers it (the paper prints no line search: this backtracking is a reading).
+    d_obs: [nf][ns][nrec]. Returns (m, J history): each group's J at its start and
+    after every accepted iteration."""
+    from .helmholtz import gradient, misfit
+
+    omegas = np.asarray(omegas, np.float64)
+    d_obs = np.asarray(d_obs, np.complex128)
+    m = np.asarray(m0, np.float64).copy()
+    if strategy == "simultaneous":
+        groups = [list(range(len(omegas)))]
+    else:
+        groups = [[f] for f in np.argsort(omegas, kind="stable")]
+    hist = []
+    for grp in groups:
+        om, d = omegas[grp], d_obs[grp]
+        J = misfit(m, h, om, src_phys, rec_phys, d, lam, npml, alpha_max)
+        hist.append(J)
+        for _ in range(gn_iters):
+            _, g = gradient(m, h, om, src_phys, rec_phys, d, lam, npml, alpha_max)
+            dm, _ = gn_step(m, h, om, src_phys, rec_phys, lam, g, cg_iters, npml, alpha_max)
+            t, accepted = 1.0, False
+            for _ in range(max_halvings + 1):
+                trial = np.clip(m + t * dm, m_bounds[0], m_bounds[1])
+                Jt = misfit(trial, h, om, src_phys, rec_phys, d, lam, npml, alpha_max)
+                if Jt < J:
+                    m, J, accepted = trial, Jt, True
+                    break
+                t *= 0.5
+            if not accepted:
+                break
+            hist.append(J)
+    return m, np.array(hist)

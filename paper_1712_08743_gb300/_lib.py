@@ -38,6 +38,8 @@ HELM_KERNEL_FG_DOTS = 7
 HELM_KERNEL_FG_AXPY = 8
 HELM_KRYLOV_BICGSTAB = 0
 HELM_KRYLOV_FGMRES = 1
+HELM_FWI_SIMULTANEOUS = 0
+HELM_FWI_SEQUENTIAL = 1
 
 
 class helm_solve_opts(C.Structure):
@@ -58,6 +60,21 @@ class helm_solve_opts(C.Structure):
         ("precond", C.c_int),
         ("reorth", C.c_int),
     ]
+
+
+class helm_fwi_opts(C.Structure):
+    _fields_ = [
+        ("strategy", C.c_int),
+        ("gn_iters", C.c_int),
+        ("cg_iters", C.c_int),
+        ("max_halvings", C.c_int),
+        ("m_lo", C.c_double),
+        ("m_hi", C.c_double),
+    ]
+
+
+# void (*)(int group, int iter, const double* m, double J, void* user)
+helm_fwi_checkpoint = C.CFUNCTYPE(None, C.c_int, C.c_int, C.POINTER(C.c_double), C.c_double, C.c_void_p)
 
 
 class helm_solve_stats(C.Structure):
@@ -123,6 +140,8 @@ SIGNATURES = {
     "helm_fwi_state_destroy": (None, [_P]),
     "helm_gn_hvp": (_I, [_P, _P, _P, _pOpts, _pStats]),
     "helm_gn_step": (_I, [_P, _P, _I, _P, _pD, _pOpts]),
+    "helm_fwi_run": (_I, [_P, _I, _I, _D, _I, _D, _pD, _I, _pD, _I, _pI, _pI, _I, _pI, _pI, _P, _D,
+                          C.POINTER(helm_fwi_opts), _pOpts, _pD, _pD, _pI, helm_fwi_checkpoint, _P]),
     "helm_apply": (_I, [_P, _I, _pD, _I, _P, _P, _I]),
     "helm_vcycle": (_I, [_P, _I, _pD, _D, _D, _D, _P, _P, _I]),
     "helm_vcycle_noalloc": (_I, [_P, _I, _pD, _D, _D, _D, _P, _P]),

@@ -348,6 +348,38 @@ def helm_gn_step(model: Model, state: FwiState, grad, cg_iters: int, opts=None):
     return dm, rel, st
 
 
+def helm_fwi_run(ctx: Context, m0, h: float, omegas, src, rec, d_obs, lam: float, strategy="sequential",
+                 gn_iters=2, cg_iters=5, max_halvings=4, m_bounds=(1 / 6000.0, 1 / 1000.0), npml=20,
+                 alpha_max=0.5, opts=None, checkpoint=None):
+    """Gauss-Newton FWI loop over frequency groups ("simultaneous": all at once;
+    "sequential": one at a time from the lowest). Returns (m [Pz][Px], J history,
+    status); `checkpoint(group, iter, m, J)` is called with a copy of every
+    accepted model."""
+    lib = ctx.lib
+    m = _np(m0, np.float64)
+    Pz, Px = m.shape
+    om, sx, sz, rx, rz = _geometry(omegas, src, rec)
+    nf, ns, nr = om.size, sx.size, rx.size
+    d = _np(d_obs, np.complex128).reshape(nf, ns, nr)
+    fo = _lib.helm_fwi_opts(_lib.HELM_FWI_SEQUENTIAL if strategy == "sequential" else _lib.HELM_FWI_SIMULTANEOUS,
+                            int(gn_iters), int(cg_iters), int(max_halvings), float(m_bounds[0]), float(m_bounds[1]))
+    o = _opts(opts, device_ptrs=0)
+    ngroups = nf if strategy == "sequential" else 1
+    hist = np.zeros(ngroups * (int(gn_iters) + 1), np.float64)
+    nh = C.c_int()
+    out = np.empty_like(m)
+
+    def _cb(group, it, mp, J, _user):
+        checkpoint(group, it, np.ctypeslib.as_array(mp, shape=(Pz, Px)).copy(), J)
+
+    cb = _lib.helm_fwi_checkpoint(_cb) if checkpoint else _lib.helm_fwi_checkpoint()
+    st = lib.helm_fwi_run(ctx.handle, Px, Pz, float(h), int(npml), float(alpha_max), _ptr_d(m), nf, _ptr_d(om), ns,
+                          _ptr_i(sx), _ptr_i(sz), nr, _ptr_i(rx), _ptr_i(rz), C.c_void_p(d.ctypes.data), float(lam),
+                          C.byref(fo), C.byref(o), _ptr_d(out), _ptr_d(hist), C.byref(nh), cb, None)
+    check(st, "helm_fwi_run", allow=(_lib.HELM_OK, _lib.HELM_E_NOT_CONVERGED))
+    return out, hist[: nh.value].copy(), st
+
+
 # ------------------------------------------------------------------ serving
 @dataclass
 class ServedResult:

@@ -155,10 +155,17 @@ __global__ void __launch_bounds__(256) k_fg_dots(const T* __restrict__ V, size_t
     const int nblk = gridDim.x * gridDim.y, blk = blockIdx.y * gridDim.x + blockIdx.x;
     double* part = partials + (size_t)b * pstride;
     if (threadIdx.x < NA) {
-        double v = 0.0;
-        for (int q = 0; q < nw; ++q) v += sh[threadIdx.x][q];
-        part[(size_t)threadIdx.x * nblk + blk] = v;
+        // the eight warp totals (256 threads) by a fixed pairwise tree
+        double w8[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) w8[q] = sh[threadIdx.x][q];
+#pragma unroll
+        for (int w = 4; w > 0; w >>= 1)
+#pragma unroll
+            for (int q = 0; q < w; ++q) w8[q] += w8[q + w];
+        part[(size_t)threadIdx.x * nblk + blk] = w8[0];
     }
+    (void)nw;
     __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) s_last = (atomicAdd(&st[b].counter[2], 1u) == (unsigned)(nblk - 1));
@@ -178,7 +185,8 @@ __global__ void __launch_bounds__(256) k_fg_dots(const T* __restrict__ V, size_t
         const int c = isn ? 0 : i / NV, k = isn ? NV : i % NV;
         const double* pre = part + (size_t)(2 * k) * nblk + (size_t)c * nx;
         const double* pim = part + (size_t)(2 * k + 1) * nblk + (size_t)c * nx;
-        // eight loads per lane in flight, then summed in a fixed order
+        // eight loads per lane in flight, summed by a fixed pairwise tree (three
+        // dependent FP64 additions per batch instead of eight)
         double re = 0.0, im = 0.0;
         for (int x0 = 0; x0 < nx; x0 += 256) {
             double vr[8], vi[8];
@@ -189,7 +197,11 @@ __global__ void __launch_bounds__(256) k_fg_dots(const T* __restrict__ V, size_t
                 vi[t] = (x < nx && !isn) ? __ldcg(pim + x) : 0.0;
             }
 #pragma unroll
-            for (int t = 0; t < 8; ++t) { re += vr[t]; im += vi[t]; }
+            for (int w = 4; w > 0; w >>= 1)
+#pragma unroll
+                for (int t = 0; t < w; ++t) { vr[t] += vr[t + w]; vi[t] += vi[t + w]; }
+            re += vr[0];
+            im += vi[0];
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {

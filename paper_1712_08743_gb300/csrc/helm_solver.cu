@@ -749,7 +749,8 @@ int time_kernel(const helm_model* m, cudaStream_t s, int kernel, int nrhs, doubl
                 launch = [&, j, vs, Vb, Wb] { launch_fg_dots<float>(Vb, vs, Wb, j, 0, 0, 0, part.as<double>(), pstride, S, fgd, n, nrhs, s); };
                 *bytes = N * B * 8.0 * (j + 2);
             } else {
-                launch = [&, j, vs, Vb, Wb] { launch_fg_axpy<float>(Vb, vs, Wb, j, 1, 0, part.as<double>(), pstride, S, fgd, nact.as<int>(), n, nrhs, s); };
+                // mode 3, as in the solve: per-block norm parts, the column finished elsewhere
+                launch = [&, j, vs, Vb, Wb] { launch_fg_axpy<float>(Vb, vs, Wb, j, 3, 0, part.as<double>(), pstride, S, fgd, nact.as<int>(), n, nrhs, s); };
                 *bytes = N * B * 8.0 * (j + 3);
             }
             break;

@@ -90,7 +90,7 @@ def test_ctypes_structs_match_the_c_layout(tmp_path):
     gcc = shutil.which("gcc") or shutil.which("cc")
     if gcc is None:
         pytest.skip("no C compiler")
-    structs = [_lib.helm_solve_opts, _lib.helm_solve_stats, _lib.helm_request, _lib.helm_result]
+    structs = [_lib.helm_solve_opts, _lib.helm_solve_stats, _lib.helm_request, _lib.helm_result, _lib.helm_fwi_opts]
     lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "helm.h"', "int main(void) {"]
     for st in structs:
         lines.append(f'printf("{st.__name__} size %zu\\n", sizeof({st.__name__}));')

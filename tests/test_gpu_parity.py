@@ -288,6 +288,29 @@ def test_gauss_newton_product_and_step_match_oracle(hg, ctx):
     model.close()
 
 
+@pytest.mark.parametrize("strategy", ["simultaneous", "sequential"])
+def test_fwi_loop_matches_oracle(hg, ctx, strategy):
+    """The Gauss-Newton inversion loop, all frequencies at once or lowest first: the
+    same accepted steps, misfit history and final model as the oracle's loop, and a
+    checkpoint for every accepted model."""
+    m0, h, npml, src, rec, om, d_obs = _small_fwi(2)
+    lam, bounds = 1e2, (1 / 4000.0, 1 / 1000.0)
+    seen = []
+    m, hist, st = hg.helm_fwi_run(ctx, m0, h, om, src, rec, d_obs, lam, strategy=strategy, gn_iters=2, cg_iters=4,
+                                  max_halvings=3, m_bounds=bounds, npml=npml, opts=dict(tol=1e-11),
+                                  checkpoint=lambda g, i, mm, J: seen.append((g, i, mm, J)))
+    m_ref, hist_ref = oracle.fwi_run(m0, h, om, src, rec, d_obs, lam, strategy=strategy, gn_iters=2, cg_iters=4,
+                                     max_halvings=3, m_bounds=bounds, npml=npml)
+    assert st == hg.HELM_OK
+    assert len(hist) == len(hist_ref) >= 3
+    np.testing.assert_allclose(hist, hist_ref, rtol=1e-5)
+    assert rel(m - m0, m_ref - m0) < 1e-4
+    assert len(seen) == len(hist) and np.array_equal(seen[-1][2], m)
+    assert [J for *_, J in seen] == list(hist)
+    with pytest.raises(hg.HelmError):
+        hg.helm_fwi_run(ctx, m0, h, om, src, rec, d_obs, 0.0, npml=npml)
+
+
 def test_autograd_backward_runs_adjoint(hg, ctx):
     import torch
 
