@@ -834,6 +834,18 @@ __global__ void __launch_bounds__(128) k_restrict_g(LevelDev Lf, LevelDev Lc, co
     if (!rhs_active(st, b)) return;
     const size_t nf = (size_t)Lf.nx * Lf.nz, nc = (size_t)Lc.nx * Lc.nz;
     const T* fb = f + 2 * nf * b;
+    // this thread's points of the fine region (blockDim.x == GRCX * GRCZ); their
+    // right-hand side is loaded before, and independently of, the coarse correction
+    constexpr int NT = GRCX * GRCZ, NF = GRFW * GRFH, NPT = (NF + NT - 1) / NT;
+    cx<T> fpre[NPT];
+#pragma unroll
+    for (int k = 0; k < NPT; ++k) {
+        const int idx = threadIdx.x + k * NT;
+        const int lz = idx / GRFW, lx = idx - lz * GRFW;
+        const int gx = gx0 + lx, gz = gz0 + lz;
+        fpre[k] = (idx < NF && gx >= 0 && gx < Lf.nx && gz >= 0 && gz < Lf.nz) ? ldc(fb, (size_t)gz * Lf.nx + gx)
+                                                                              : cx<T>(0, 0);
+    }
     if (CORRECT) {
         const T* eb = ec + 2 * nc * b;
         for (int idx = threadIdx.x; idx < CEW * CEH; idx += blockDim.x) {
@@ -845,12 +857,15 @@ __global__ void __launch_bounds__(128) k_restrict_g(LevelDev Lf, LevelDev Lc, co
         }
     }
     __syncthreads();
-    for (int idx = threadIdx.x; idx < GRFW * GRFH; idx += blockDim.x) {
+#pragma unroll
+    for (int k = 0; k < NPT; ++k) {
+        const int idx = threadIdx.x + k * NT;
+        if (idx >= NF) break;
         const int lz = idx / GRFW, lx = idx - lz * GRFW;
         const int gx = gx0 + lx, gz = gz0 + lz;
-        cx<T> fv(0, 0), uv(0, 0);
+        const cx<T> fv = fpre[k];
+        cx<T> uv(0, 0);
         if (gx >= 0 && gx < Lf.nx && gz >= 0 && gz < Lf.nz) {
-            fv = ldc(fb, (size_t)gz * Lf.nx + gx);
             uv = wj * cdiv(fv, C.c[0][lz][lx]);
             if (CORRECT) {
                 int ia, ib, ka, kb;
@@ -908,6 +923,25 @@ __global__ void __launch_bounds__(256) k_prolong_g(LevelDev Lf, LevelDev Lc, con
     const size_t nf = (size_t)Lf.nx * Lf.nz, nc = (size_t)Lc.nx * Lc.nz;
     const T* fb = f + 2 * nf * b;
     const T* eb = ec + 2 * nc * b;
+    // this thread's points of the fine region (blockDim.x == GPX * GPZ); their
+    // right-hand side is loaded before, and independently of, the coarse correction
+    constexpr int NT = GPX * GPZ, NF = RW * RH, NPT = (NF + NT - 1) / NT;
+    cx<T> fpre[NPT];
+#pragma unroll
+    for (int k = 0; k < NPT; ++k) {
+        const int idx = threadIdx.x + k * NT;
+        const int lz = idx / RW, lx = idx - lz * RW;
+        const int gx = gx0 + lx, gz = gz0 + lz;
+        fpre[k] = (idx < NF && gx >= 0 && gx < Lf.nx && gz >= 0 && gz < Lf.nz) ? ldc(fb, (size_t)gz * Lf.nx + gx)
+                                                                              : cx<T>(0, 0);
+    }
+    // the output point this thread accumulates into (one per thread), loaded with them
+    T* ob = out + 2 * nf * b;
+    cx<T> opre(0, 0);
+    {
+        const int tz = threadIdx.x / GPX, tx = threadIdx.x - tz * GPX;
+        if (accumulate && x0 + tx < Lf.nx && z0 + tz < Lf.nz) opre = ldcc(ob, (size_t)(z0 + tz) * Lf.nx + x0 + tx);
+    }
     for (int idx = threadIdx.x; idx < EW * EH; idx += blockDim.x) {
         const int lz = idx / EW, lx = idx - lz * EW;
         const int I = cx0 + lx, K = cz0 + lz;
@@ -916,12 +950,15 @@ __global__ void __launch_bounds__(256) k_prolong_g(LevelDev Lf, LevelDev Lc, con
         E[lz][lx] = e;
     }
     __syncthreads();
-    for (int idx = threadIdx.x; idx < RW * RH; idx += blockDim.x) {
+#pragma unroll
+    for (int k = 0; k < NPT; ++k) {
+        const int idx = threadIdx.x + k * NT;
+        if (idx >= NF) break;
         const int lz = idx / RW, lx = idx - lz * RW;
         const int gx = gx0 + lx, gz = gz0 + lz;
-        cx<T> fv(0, 0), u(0, 0);
+        const cx<T> fv = fpre[k];
+        cx<T> u(0, 0);
         if (gx >= 0 && gx < Lf.nx && gz >= 0 && gz < Lf.nz) {
-            fv = ldc(fb, (size_t)gz * Lf.nx + gx);
             u = wj * cdiv(fv, C.c[0][lz][lx]);
             int ia, ib, ka, kb;
             T wa, wb, va, vb;
@@ -934,17 +971,16 @@ __global__ void __launch_bounds__(256) k_prolong_g(LevelDev Lf, LevelDev Lc, con
         U2[lz][lx] = u;
     }
     __syncthreads();
-    T* ob = out + 2 * nf * b;
-    for (int idx = threadIdx.x; idx < GPX * GPZ; idx += blockDim.x) {
-        const int tz = idx / GPX, tx = idx - tz * GPX;
+    {
+        const int tz = threadIdx.x / GPX, tx = threadIdx.x - tz * GPX;   // one output point per thread
         const int gx = x0 + tx, gz = z0 + tz;
-        if (gx >= Lf.nx || gz >= Lf.nz) continue;
+        if (gx >= Lf.nx || gz >= Lf.nz) return;
         const int lx = tx + 1, lz = tz + 1;
         const size_t i = (size_t)gz * Lf.nx + gx;
         const cx<T> c = U2[lz][lx];
         const cx<T> mu = mop9_staged<T, RW, RH>(C, Lf.nx, Lf.nz, gx, gz, lx, lz, &U2[lz][lx]);
         const cx<T> v = c + wj * cdiv(F[lz][lx] - mu, C.c[0][lz][lx]);
-        stc(ob, i, accumulate ? ldcc(ob, i) + v : v);
+        stc(ob, i, accumulate ? opre + v : v);
     }
 }
 
@@ -1598,6 +1634,15 @@ __global__ void __launch_bounds__(1024, 1) k_tail(const __grid_constant__ TailAr
         for (int t = tid; t < nL * nL; t += nth) Ms[t] = ldc(Mg, t);
     pdl_wait();   // the coefficients above are model data; everything below depends on earlier kernels
     if (!rhs_active(st, b)) return;
+    // the output this block accumulates into (a second coarse correction), loaded
+    // now instead of after the cycle; the top tail level has at most 2 x 1024 nodes
+    static_assert(kTailMaxPoints32 <= 2 * 1024 && kTailMaxPoints64 <= 2 * 1024, "tail output preload");
+    cx<T> opre[2] = {cx<T>(0, 0), cx<T>(0, 0)};
+    if (a.accumulate) {
+        const int nt = a.lv[a.lt].nx * a.lv[a.lt].nz;
+        const T* o = static_cast<const T*>(a.out);
+        for (int k = 0, p = tid; k < 2 && p < nt; ++k, p += nth) opre[k] = ldcc(o, (size_t)nt * b + p);
+    }
     __syncthreads();
     for (int k = 0; k < a.nops; ++k) {
         const int op = a.ops[k], type = op & 255, l = op >> 8;
@@ -1706,8 +1751,8 @@ __global__ void __launch_bounds__(1024, 1) k_tail(const __grid_constant__ TailAr
             }
             case OP_OUTPUT: {
                 T* o = static_cast<T*>(a.out);
-                for (int p = tid; p < n; p += nth)
-                    stc(o, (size_t)n * b + p, a.accumulate ? ldcc(o, (size_t)n * b + p) + r[p] : r[p]);
+                for (int q = 0, p = tid; q < 2 && p < n; ++q, p += nth)
+                    stc(o, (size_t)n * b + p, a.accumulate ? opre[q] + r[p] : r[p]);
                 break;
             }
         }
