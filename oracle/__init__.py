@@ -13,6 +13,7 @@ misfit of Eq. 4 by the adjoint formula behind Eq. 7.
 """
 from .helmholtz import (  # noqa: F401
     damping_profile,
+    flux_laplacian,
     fold_pad,
     gradient,
     misfit,

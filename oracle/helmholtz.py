@@ -6,7 +6,10 @@ CPU-baseline leg; never by the product path.
 What it computes (Kazemi, "Application of shifted-Laplace preconditioners for
 heterogeneous Helmholtz equation - part 2: Full waveform inversion"):
 
-* Eq. 2:  -Laplace(u) - omega^2 m^2 (1 - j alpha) u = f, m = 1/c the real slowness.
+* Eq. 2:  -Laplace(u) - omega^2 m^2 (1 - j alpha) u = f, m = 1/c the real slowness;
+          with a density, Eq. 1:  -div(rho grad u) - omega^2 m^2 (1 - j alpha) u = f
+          (rho as the paper writes it, multiplying the gradient), in 5-point flux
+          form with harmonic-mean edge densities.
 * Eq. 3:  the finite-difference matrix form  B u = f.
 * Eq. 4:  J(m) = sum |u_obs - u_cal(m)|^2 + lambda |m|^2 over shots, receivers
           and frequencies (the paper's regulariser weight is also called alpha;
@@ -74,13 +77,54 @@ def _second_difference(n: int) -> sp.csr_matrix:
     return sp.diags([-e[:-1], 2.0 * e, -e[:-1]], [-1, 0, 1], format="csr")
 
 
-def operator(m_pad: np.ndarray, h: float, omega: float, alpha: np.ndarray) -> sp.csc_matrix:
+def flux_laplacian(rho_pad: np.ndarray) -> sp.csr_matrix:
+    """h^2 times -div(rho grad) of Eq. 1 in 5-point flux form on the padded grid:
+    row i holds sum_e rho_e on the diagonal and -rho_e for the neighbour across edge
+    e, with rho_e the harmonic mean 2 rho_i rho_j / (rho_i + rho_j) of the two nodes.
+    An edge to a node outside the grid (zero Dirichlet ghost) takes rho_i."""
+    rho = np.asarray(rho_pad, np.float64)
+    nz, nx = rho.shape
+    N = nz * nx
+    idx = np.arange(N).reshape(nz, nx)
+    diag = np.zeros((nz, nx))
+    rows, cols, vals = [], [], []
+    for axis in (0, 1):                                   # z edges, then x edges
+        a = rho[:-1, :] if axis == 0 else rho[:, :-1]
+        b = rho[1:, :] if axis == 0 else rho[:, 1:]
+        re = 2.0 * a * b / (a + b)
+        ia = idx[:-1, :] if axis == 0 else idx[:, :-1]
+        ib = idx[1:, :] if axis == 0 else idx[:, 1:]
+        rows += [ia.ravel(), ib.ravel()]
+        cols += [ib.ravel(), ia.ravel()]
+        vals += [-re.ravel(), -re.ravel()]
+        if axis == 0:
+            diag[:-1, :] += re
+            diag[1:, :] += re
+        else:
+            diag[:, :-1] += re
+            diag[:, 1:] += re
+    # edges to the ghost nodes around the grid
+    diag[0, :] += rho[0, :]
+    diag[-1, :] += rho[-1, :]
+    diag[:, 0] += rho[:, 0]
+    diag[:, -1] += rho[:, -1]
+    rows.append(idx.ravel())
+    cols.append(idx.ravel())
+    vals.append(diag.ravel())
+    return sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))), shape=(N, N))
+
+
+def operator(m_pad: np.ndarray, h: float, omega: float, alpha: np.ndarray, rho_pad=None) -> sp.csc_matrix:
     """B of Eq. 3 for Eq. 2 on the padded grid, unknowns ordered x fastest.
 
-    B = (I_z (x) L_x + L_z (x) I_x) / h^2 - diag(omega^2 m^2 (1 - j alpha)).
+    B = (I_z (x) L_x + L_z (x) I_x) / h^2 - diag(omega^2 m^2 (1 - j alpha)),
+    or, with a density (Eq. 1), flux_laplacian(rho) / h^2 - diag(...).
     """
     nz, nx = m_pad.shape
-    lap = sp.kron(sp.identity(nz), _second_difference(nx)) + sp.kron(_second_difference(nz), sp.identity(nx))
+    if rho_pad is None:
+        lap = sp.kron(sp.identity(nz), _second_difference(nx)) + sp.kron(_second_difference(nz), sp.identity(nx))
+    else:
+        lap = flux_laplacian(rho_pad)
     mass = (omega ** 2) * (m_pad ** 2) * (1.0 - 1j * alpha)
     B = lap.astype(np.complex128) / (h * h) - sp.diags(mass.ravel())
     return sp.csc_matrix(B)
@@ -100,9 +144,9 @@ class Factorised:
     """One sparse LU factorisation of B(m, omega), reused for every right-hand side
     of that frequency (the paper's direct "LU factorization" modelling)."""
 
-    def __init__(self, m_pad: np.ndarray, h: float, omega: float, alpha: np.ndarray):
+    def __init__(self, m_pad: np.ndarray, h: float, omega: float, alpha: np.ndarray, rho_pad=None):
         self.shape = m_pad.shape
-        self.B = operator(m_pad, h, omega, alpha)
+        self.B = operator(m_pad, h, omega, alpha, rho_pad)
         self.lu = spla.splu(self.B, permc_spec="MMD_AT_PLUS_A")
 
     def solve(self, F: np.ndarray) -> np.ndarray:
@@ -117,11 +161,12 @@ class Factorised:
 
 
 def solve_fields(m_phys: np.ndarray, h: float, omega: float, src_phys: np.ndarray,
-                 npml: int = 20, alpha_max: float = 0.5, F: np.ndarray | None = None) -> np.ndarray:
+                 npml: int = 20, alpha_max: float = 0.5, F: np.ndarray | None = None, rho_phys=None) -> np.ndarray:
     """Wavefields u = B^{-1} f (Eq. 3) on the padded grid, one per source: [ns][nz][nx].
 
     ``src_phys`` holds physical-grid (ix, iz) node indices; ``F`` (optional,
-    [k][nz*nx]) replaces the point sources by explicit right-hand sides.
+    [k][nz*nx]) replaces the point sources by explicit right-hand sides; ``rho_phys``
+    (optional, [Pz][Px]) is the density of Eq. 1, padded like the slowness.
     """
     Pz, Px = m_phys.shape
     m_pad = pad_slowness(m_phys, npml)
@@ -129,7 +174,8 @@ def solve_fields(m_phys: np.ndarray, h: float, omega: float, src_phys: np.ndarra
     nz, nx = m_pad.shape
     if F is None:
         F = point_sources(nx, nz, h, np.asarray(src_phys).reshape(-1, 2) + npml)
-    fac = Factorised(m_pad, h, omega, alpha)
+    rho_pad = None if rho_phys is None else pad_slowness(rho_phys, npml)
+    fac = Factorised(m_pad, h, omega, alpha, rho_pad)
     return fac.solve(F).reshape(-1, nz, nx)
 
 
@@ -152,23 +198,24 @@ def fold_pad(g_pad: np.ndarray, npml: int) -> np.ndarray:
     return g
 
 
-def misfit(m_phys, h, omegas, src_phys, rec_phys, d_obs, lam, npml=20, alpha_max=0.5) -> float:
+def misfit(m_phys, h, omegas, src_phys, rec_phys, d_obs, lam, npml=20, alpha_max=0.5, rho_phys=None) -> float:
     """J(m) of Eq. 4: sum over frequencies, shots and receivers of |d_cal - d_obs|^2
     plus lam * sum over physical cells of m^2. d_obs is [nf][ns][nrec]."""
     J = 0.0
     for f_i, om in enumerate(omegas):
-        U = solve_fields(m_phys, h, om, src_phys, npml, alpha_max)
+        U = solve_fields(m_phys, h, om, src_phys, npml, alpha_max, rho_phys=rho_phys)
         r = sample_receivers(U, rec_phys, npml) - d_obs[f_i]
         J += float(np.sum(np.abs(r) ** 2))
     return J + lam * float(np.sum(np.asarray(m_phys, float) ** 2))
 
 
-def gradient(m_phys, h, omegas, src_phys, rec_phys, d_obs, lam, npml=20, alpha_max=0.5):
+def gradient(m_phys, h, omegas, src_phys, rec_phys, d_obs, lam, npml=20, alpha_max=0.5, rho_phys=None):
     """(J, dJ/dm) for Eq. 4 by the adjoint method behind Eq. 7.
 
     Per frequency: u = B^{-1} f per shot; r_d = P u - d_obs; J += |r_d|^2;
     lambda = B^{-H} P^T r_d; g_pad += 4 omega^2 m Re[(1 - j alpha) u conj(lambda)].
     Then g = E^T g_pad + 2 lam m over physical cells. Returns (J, g [Pz][Px]).
+    A density (Eq. 1) enters B only: the slowness derivative is the same.
     """
     m_phys = np.asarray(m_phys, np.float64)
     Pz, Px = m_phys.shape
@@ -180,8 +227,9 @@ def gradient(m_phys, h, omegas, src_phys, rec_phys, d_obs, lam, npml=20, alpha_m
     rec_flat = rec_pad[:, 1] * nx + rec_pad[:, 0]
     J = 0.0
     g_pad = np.zeros(nz * nx)
+    rho_pad = None if rho_phys is None else pad_slowness(rho_phys, npml)
     for f_i, om in enumerate(omegas):
-        fac = Factorised(m_pad, h, om, alpha)
+        fac = Factorised(m_pad, h, om, alpha, rho_pad)
         U = fac.solve(point_sources(nx, nz, h, src_pad))          # [ns][N]
         r = U[:, rec_flat] - d_obs[f_i]                            # [ns][nrec]
         J += float(np.sum(np.abs(r) ** 2))

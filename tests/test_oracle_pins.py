@@ -10,6 +10,7 @@ catches each one.
 """
 import numpy as np
 import pytest
+import scipy.sparse as sp
 import scipy.special
 
 import oracle
@@ -220,17 +221,88 @@ def test_planted_mistakes_are_caught(monkeypatch):
     Green's-function and eigenpair pins must fail for each."""
     good = H.operator
 
-    def wrong_damping(m_pad, h, omega, alpha):
-        return good(m_pad, h, omega, -alpha)
+    def wrong_damping(m_pad, h, omega, alpha, rho_pad=None):
+        return good(m_pad, h, omega, -alpha, rho_pad)
 
     monkeypatch.setattr(H, "operator", wrong_damping)
     with pytest.raises(AssertionError):
         test_greens_function_far_from_source_and_layer()
 
-    def wrong_mass(m_pad, h, omega, alpha):
-        return good(m_pad, h, 1j * omega, alpha)   # flips the sign of omega^2
+    def wrong_mass(m_pad, h, omega, alpha, rho_pad=None):
+        return good(m_pad, h, 1j * omega, alpha, rho_pad)   # flips the sign of omega^2
 
     monkeypatch.setattr(H, "operator", wrong_mass)
     monkeypatch.setattr(oracle, "operator", wrong_mass)
     with pytest.raises(AssertionError):
         test_operator_discrete_eigenpair()
+
+
+# ------------------------------------------------ variable density (Eq. 1)
+def test_flux_laplacian_reduces_to_the_constant_density_operator():
+    """rho = 1 gives the 5-point Laplacian of Eq. 2 exactly; rho = c scales it by c."""
+    nz, nx = 7, 9
+    lap = (sp.kron(sp.identity(nz), sp.diags([-np.ones(nx - 1), 2 * np.ones(nx), -np.ones(nx - 1)], [-1, 0, 1]))
+           + sp.kron(sp.diags([-np.ones(nz - 1), 2 * np.ones(nz), -np.ones(nz - 1)], [-1, 0, 1]), sp.identity(nx)))
+    assert abs(oracle.flux_laplacian(np.ones((nz, nx))) - lap).max() == 0.0
+    assert abs(oracle.flux_laplacian(np.full((nz, nx), 2.5)) - 2.5 * lap).max() < 1e-14
+
+
+def test_flux_laplacian_energy_by_loops():
+    """u^T G u = sum over edges of rho_e |u_i - u_j|^2 (harmonic-mean rho_e) plus
+    rho_i |u_i|^2 for every edge to a ghost node outside the grid, summed here edge by
+    edge; G is symmetric."""
+    rng = _rng(21)
+    nz, nx = 5, 6
+    rho = rng.uniform(0.5, 3.0, (nz, nx))
+    u = rng.standard_normal((nz, nx))
+    G = oracle.flux_laplacian(rho)
+    assert abs(G - G.T).max() == 0.0
+    e = 0.0
+    for iz in range(nz):
+        for ix in range(nx):
+            for dz, dx in ((0, 1), (1, 0), (0, -1), (-1, 0)):
+                jz, jx = iz + dz, ix + dx
+                if 0 <= jz < nz and 0 <= jx < nx:
+                    if (dz, dx) in ((0, 1), (1, 0)):          # each interior edge once
+                        re = 2 * rho[iz, ix] * rho[jz, jx] / (rho[iz, ix] + rho[jz, jx])
+                        e += re * (u[iz, ix] - u[jz, jx]) ** 2
+                else:
+                    e += rho[iz, ix] * u[iz, ix] ** 2
+    assert float(u.ravel() @ (G @ u.ravel())) == pytest.approx(e, rel=1e-13)
+
+
+def test_flux_laplacian_exact_across_a_density_jump():
+    """With the density jump midway between two rows, -(rho u')' = 0 has the
+    piecewise-linear solution of constant flux; the harmonic-mean edge makes the
+    discrete operator vanish on it at every interior node (an arithmetic mean would
+    not)."""
+    nz, nx, k = 12, 5, 5                       # rows 0..k have rho1, rows k+1.. rho2
+    rho1, rho2, q = 1.0, 4.0, 0.7
+    z = np.arange(nz, dtype=float)
+    zi = k + 0.5
+    u_z = np.where(z <= zi, q * z / rho1, q * zi / rho1 + q * (z - zi) / rho2)
+    rho = np.where(z[:, None] <= zi, rho1, rho2) * np.ones((nz, nx))
+    u = np.repeat(u_z[:, None], nx, axis=1)
+    r = (oracle.flux_laplacian(rho) @ u.ravel()).reshape(nz, nx)
+    assert np.abs(r[1:-1, 1:-1]).max() < 1e-13
+    # the arithmetic mean across the jump would leave a residual on the row above it
+    ra = 0.5 * (rho1 + rho2)
+    r_arith = rho1 * (u_z[k] - u_z[k - 1]) + ra * (u_z[k] - u_z[k + 1])
+    assert abs(r_arith) > 0.5 * q
+
+
+def test_density_gradient_central_differences():
+    """With a density the slowness gradient keeps its form (rho enters B only) and
+    still equals central differences of J."""
+    p = _small_fwi()
+    rho = _rng(22).uniform(1.0, 2.5, p["m"].shape)
+    J, g = oracle.gradient(p["m"], p["h"], p["omegas"], p["src"], p["rec"], p["d_obs"], p["lam"], p["npml"],
+                           rho_phys=rho)
+    for (iz, ix) in [(0, 0), (7, 11), (15, 23)]:
+        e = 1e-4 * p["m"][iz, ix]
+        mp = p["m"].copy(); mp[iz, ix] += e
+        mm = p["m"].copy(); mm[iz, ix] -= e
+        fd = (oracle.misfit(mp, p["h"], p["omegas"], p["src"], p["rec"], p["d_obs"], p["lam"], p["npml"], rho_phys=rho)
+              - oracle.misfit(mm, p["h"], p["omegas"], p["src"], p["rec"], p["d_obs"], p["lam"], p["npml"],
+                              rho_phys=rho)) / (2 * e)
+        assert abs(fd - g[iz, ix]) / abs(g[iz, ix]) < 1e-6, ((iz, ix), fd, g[iz, ix])
