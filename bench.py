@@ -56,6 +56,8 @@ def parse():
                     help="FGMRES Gram-Schmidt: second pass always (CGS2), never, or by the DGKS test")
     ap.add_argument("--inner-tol", type=float, default=5e-2, help="mixed precision: reduction per inner solve")
     ap.add_argument("--tune", action="store_true", help="autotune the multigrid tiles before timing")
+    ap.add_argument("--density", action="store_true",
+                    help="single: the variable-density operator (Eq. 1) with a Gardner density on the same model")
     ap.add_argument("--workload", default="single", choices=["single", "batched", "serving", "gn", "ablation", "fwi"],
                     help="single: the single large case (the default line); batched: 64 shots x 5 "
                          "frequencies in one call; serving: a Poisson stream of requests; gn: one "
@@ -274,7 +276,9 @@ def run_ours(args):
     torch.cuda.set_stream(stream)
     ctx = api.Context(local, stream)
     mdl = models.c2_model()
-    model = api.helm_create_model(ctx, mdl.slowness, mdl.h, mdl.npml, mdl.alpha_max)
+    # --density: the variable-density operator of Eq. 1 on the same model, density by Gardner's relation
+    rho = models.gardner_density(mdl.velocity) if args.density else None
+    model = api.helm_create_model(ctx, mdl.slowness, mdl.h, mdl.npml, mdl.alpha_max, density=rho)
     n = model.n
     om = mdl.omegas
     kry = {"bicgstab": _lib.HELM_KRYLOV_BICGSTAB, "fgmres": _lib.HELM_KRYLOV_FGMRES}[args.krylov]
@@ -405,7 +409,7 @@ def run_ours(args):
             roof["time_shares"] = json.load(f)
 
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and not args.density:
         t_fac, ts = oracle_c2_timing(1)
         cpu = {"value": 1.0 / (t_fac + ts[0]), "unit": "solves/s", "cores": 1, "kind": "oracle",
                "sample": "one full solve of the same problem: SuperLU factorisation + triangular solve "
@@ -417,7 +421,7 @@ def run_ours(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_total / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c64+f64",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "grid": f"{model.nx}x{model.nz} padded ({mdl.Px}x{mdl.Pz} physical)",
+            "config": {"workload": WORKLOAD + ("_gardner_density" if args.density else ""), "grid": f"{model.nx}x{model.nz} padded ({mdl.Px}x{mdl.Pz} physical)",
                        "unknowns": n, "precision": "complex64 inner, FP64 residual/refinement",
                        "krylov": ("BiCGSTAB" if args.krylov == "bicgstab" else
                                   f"FGMRES({args.restart}, {GS_NAME[args.reorth]})") +

@@ -136,6 +136,19 @@ void helm_ctx_destroy(helm_ctx* ctx);
  * injection). h > 0 is the grid spacing in metres; 0 <= alpha_max. */
 int helm_create_model(helm_ctx* ctx, int Px, int Pz, double h, const double* slowness,
                       int npml, double alpha_max, helm_model** out);
+
+/* Model setup for the variable-density operator of Eq. 1,
+ * -div(rho grad u) - omega^2 m^2 (1 - j alpha) u = f, with rho as the paper
+ * writes it (multiplying the gradient; pass 1/density for the acoustic form).
+ * density: host float64 [Pz][Px], all > 0, padded into the layer like the
+ * slowness; the operator is the 5-point flux form with the harmonic mean of the
+ * two nodes' densities on each edge (an edge to a node outside the grid takes
+ * the node's own density), and the shifted-Laplace preconditioner and its
+ * Galerkin hierarchy are built from the same form. density = NULL is
+ * helm_create_model. Every call that takes a model accepts this one; serving
+ * requests carry no density. */
+int helm_create_model_rho(helm_ctx* ctx, int Px, int Pz, double h, const double* slowness,
+                          const double* density, int npml, double alpha_max, helm_model** out);
 void helm_destroy_model(helm_model* model);
 
 /* Padded grid size and number of multigrid levels of a model. */

@@ -10,7 +10,8 @@ the preconditioner is inverted. The reading used here, which the CUDA path
 implements, is one multigrid cycle per application:
 
 * Finest level: M_0 = 4 - (neighbours) - (h omega)^2 m^2 (beta1 - j beta2), the
-  grid-scaled 5-point shifted Laplacian (no damping term), zero Dirichlet ghosts.
+  grid-scaled 5-point shifted Laplacian (no damping term), zero Dirichlet ghosts;
+  with a density (Eq. 1) the 5-point flux form of -div(rho grad) in its place.
 * Level l + 1 has floor(n/2) nodes per axis; coarse node I sits on fine node
   2I+1. Coarsening stops once a level has at most 128 nodes or an axis has
   fewer than 4.
@@ -45,8 +46,12 @@ def level_shapes(nx: int, nz: int):
     return shapes
 
 
-def shifted_laplacian(m2: np.ndarray, hw2: float, beta: complex) -> sp.csr_matrix:
-    """Grid-scaled M on one level: diagonal 4 - hw2 m^2 beta, -1 to each existing neighbour."""
+def shifted_laplacian(m2: np.ndarray, hw2: float, beta: complex, rho=None) -> sp.csr_matrix:
+    """Grid-scaled M on one level: diagonal 4 - hw2 m^2 beta, -1 to each existing neighbour;
+    with a density (Eq. 1) the oracle's flux-form operator minus hw2 m^2 beta."""
+    if rho is not None:
+        from .helmholtz import flux_laplacian
+        return (flux_laplacian(rho).astype(complex) - sp.diags(hw2 * beta * np.asarray(m2, float).ravel())).tocsr()
     nz, nx = m2.shape
     rows, cols, vals = [], [], []
     for iz in range(nz):
@@ -120,13 +125,13 @@ def fcycle_level(shapes, hw2: float, m_max: float) -> int:
 class VCycle:
     """One preconditioner application approximating M^{-1} for grid-scaled (h omega)^2 = hw2."""
 
-    def __init__(self, m2_pad: np.ndarray, hw2: float, beta=(1.0, 0.5), omega_jacobi: float = 0.5):
+    def __init__(self, m2_pad: np.ndarray, hw2: float, beta=(1.0, 0.5), omega_jacobi: float = 0.5, rho_pad=None):
         nz, nx = m2_pad.shape
         self.wj = omega_jacobi
         bt = complex(beta[0], -beta[1])
         self.shapes = level_shapes(nx, nz)
         self.lt = fcycle_level(self.shapes, hw2, float(np.sqrt(np.max(m2_pad))))
-        self.M = [shifted_laplacian(np.asarray(m2_pad, float), hw2, bt)]
+        self.M = [shifted_laplacian(np.asarray(m2_pad, float), hw2, bt, rho_pad)]
         self.P = []
         for l, (lx, lz) in enumerate(self.shapes[:-1]):
             P = prolongation(lx, lz)

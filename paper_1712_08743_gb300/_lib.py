@@ -131,6 +131,7 @@ SIGNATURES = {
     "helm_ctx_create": (_I, [_I, _P, C.POINTER(_P)]),
     "helm_ctx_destroy": (None, [_P]),
     "helm_create_model": (_I, [_P, _I, _I, _D, _pD, _I, _D, C.POINTER(_P)]),
+    "helm_create_model_rho": (_I, [_P, _I, _I, _D, _pD, _pD, _I, _D, C.POINTER(_P)]),
     "helm_destroy_model": (None, [_P]),
     "helm_model_info": (_I, [_P, _pI, _pI, _pI]),
     "helm_solve": (_I, [_P, _I, _pD, _pI, _pI, _P, _P, _pOpts, _pStats]),

@@ -108,7 +108,7 @@ def helm_ctx_destroy(ctx: Context) -> None:
 class Model:
     """A helm_model: padded slowness and its multigrid hierarchy on the device."""
 
-    def __init__(self, ctx: Context, slowness, h: float, npml: int = 20, alpha_max: float = 0.5):
+    def __init__(self, ctx: Context, slowness, h: float, npml: int = 20, alpha_max: float = 0.5, density=None):
         m = _np(slowness, np.float64)
         if m.ndim != 2:
             raise ValueError("slowness must be [Pz][Px]")
@@ -117,8 +117,16 @@ class Model:
         self.Pz, self.Px = m.shape
         self.h, self.npml, self.alpha_max = float(h), int(npml), float(alpha_max)
         self.handle = C.c_void_p()
-        check(self.lib.helm_create_model(ctx.handle, self.Px, self.Pz, self.h, _ptr_d(m), self.npml,
-                                         self.alpha_max, C.byref(self.handle)), "helm_create_model")
+        if density is None:
+            check(self.lib.helm_create_model(ctx.handle, self.Px, self.Pz, self.h, _ptr_d(m), self.npml,
+                                             self.alpha_max, C.byref(self.handle)), "helm_create_model")
+        else:
+            rho = _np(density, np.float64)
+            if rho.shape != m.shape:
+                raise ValueError("density must have the slowness's shape")
+            check(self.lib.helm_create_model_rho(ctx.handle, self.Px, self.Pz, self.h, _ptr_d(m), _ptr_d(rho),
+                                                 self.npml, self.alpha_max, C.byref(self.handle)),
+                  "helm_create_model_rho")
         nx, nz, nl = C.c_int(), C.c_int(), C.c_int()
         check(self.lib.helm_model_info(self.handle, C.byref(nx), C.byref(nz), C.byref(nl)), "helm_model_info")
         self.nx, self.nz, self.nlevels = nx.value, nz.value, nl.value
@@ -139,8 +147,10 @@ class Model:
             pass
 
 
-def helm_create_model(ctx: Context, slowness, h: float, npml: int = 20, alpha_max: float = 0.5) -> Model:
-    return Model(ctx, slowness, h, npml, alpha_max)
+def helm_create_model(ctx: Context, slowness, h: float, npml: int = 20, alpha_max: float = 0.5,
+                      density=None) -> Model:
+    """A model of Eq. 2, or with `density` ([Pz][Px], > 0) of Eq. 1 (helm_create_model_rho)."""
+    return Model(ctx, slowness, h, npml, alpha_max, density)
 
 
 def helm_destroy_model(model: Model) -> None:

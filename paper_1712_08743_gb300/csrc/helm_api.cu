@@ -61,20 +61,25 @@ namespace helm {
 // Builds a model holding `nmodels` slowness fields of one grid shape (host
 // [nmodels][Pz][Px]); nmodels > 1 gives each right-hand side its own model.
 int create_model(helm_ctx* ctx, cudaStream_t s, int Px, int Pz, double h, const double* slowness, int nmodels,
-                 int npml, double alpha_max, helm_model** out) {
+                 int npml, double alpha_max, helm_model** out, const double* density) {
     if (!ctx || !out || !slowness || nmodels < 1) return HELM_E_INVALID;
     *out = nullptr;
     if (Px < 1 || Pz < 1 || npml < 0 || !finite_pos(h) || !std::isfinite(alpha_max) || alpha_max < 0.0)
         return HELM_E_INVALID;
+    if (density && nmodels != 1) return HELM_E_INVALID;
     const size_t np = (size_t)Px * Pz;
     for (size_t i = 0; i < np * nmodels; ++i)
         if (!finite_pos(slowness[i])) { set_last_error("slowness must be finite and > 0"); return HELM_E_INVALID; }
+    if (density)
+        for (size_t i = 0; i < np; ++i)
+            if (!finite_pos(density[i])) { set_last_error("density must be finite and > 0"); return HELM_E_INVALID; }
     DeviceGuard g(ctx->device);
     helm_model* m = new helm_model();
     m->ctx = ctx;
     m->Px = Px; m->Pz = Pz; m->npml = npml; m->h = h; m->alpha_max = alpha_max;
     m->nx = Px + 2 * npml; m->nz = Pz + 2 * npml;
     m->nmodels = nmodels;
+    m->vd = density != nullptr;
     for (int l = 0; l < kMaxLevels; ++l) { m->tile_restrict[l] = 1; m->tile_prolong[l] = 1; }
     // levels: halve per axis while the level is larger than the dense-coarse size
     Level L0; L0.nx = m->nx; L0.nz = m->nz; L0.h = h;
@@ -112,6 +117,13 @@ int create_model(helm_ctx* ctx, cudaStream_t s, int Px, int Pz, double h, const 
     if (e != cudaSuccess) return fail(e);
     if ((e = cudaMalloc(&m->lv[0].m2f, sizeof(float) * m->n() * nmodels)) != cudaSuccess) return fail(e);
     if ((e = cudaMalloc(&m->lv[0].m2d, sizeof(double) * m->n() * nmodels)) != cudaSuccess) return fail(e);
+    if (m->vd) {
+        Level& L0 = m->lv[0];
+        if ((e = cudaMalloc(&L0.rhof, sizeof(float) * 3 * L0.n())) != cudaSuccess) return fail(e);
+        if ((e = cudaMalloc(&L0.rhod, sizeof(double) * 3 * L0.n())) != cudaSuccess) return fail(e);
+        if ((e = cudaMalloc(&L0.gkf, sizeof(float) * kGalerkinCoefs * L0.n())) != cudaSuccess) return fail(e);
+        if ((e = cudaMalloc(&L0.gkd, sizeof(double) * kGalerkinCoefs * L0.n())) != cudaSuccess) return fail(e);
+    }
     for (int l = 1; l <= L; ++l) {
         Level& Lv = m->lv[l];
         if ((e = cudaMalloc(&Lv.gkf, sizeof(float) * kGalerkinCoefs * Lv.n() * nmodels)) != cudaSuccess) return fail(e);
@@ -140,6 +152,14 @@ int create_model(helm_ctx* ctx, cudaStream_t s, int Px, int Pz, double h, const 
             return fail(e);
     }
     launch_pad_model(static_cast<double*>(phys.p), Px, Pz, npml, nmodels, m->m_pad, m->lv[0].m2f, m->lv[0].m2d, s);
+    DevMem rho_phys;
+    if (m->vd) {
+        if ((e = cudaMalloc(&rho_phys.p, sizeof(double) * np)) != cudaSuccess) return fail(e);
+        if ((e = cudaMemcpyAsync(rho_phys.p, density, sizeof(double) * np, cudaMemcpyHostToDevice, s)) != cudaSuccess)
+            return fail(e);
+        Level& L0 = m->lv[0];
+        launch_rho_setup(static_cast<double*>(rho_phys.p), Px, Pz, npml, L0.m2d, L0.rhod, L0.rhof, L0.gkd, L0.gkf, s);
+    }
     for (int l = 1; l <= L; ++l) launch_galerkin(m, l, s);
     launch_sumsq(static_cast<double*>(phys.p), np, static_cast<double*>(msq.p), s);
     if ((e = cudaMemcpyAsync(&m->msq_sum, msq.p, sizeof(double), cudaMemcpyDeviceToHost, s)) != cudaSuccess) return fail(e);
@@ -223,7 +243,13 @@ void helm_ctx_destroy(helm_ctx* ctx) {
 int helm_create_model(helm_ctx* ctx, int Px, int Pz, double h, const double* slowness, int npml, double alpha_max,
                       helm_model** out) {
     if (!ctx) return HELM_E_INVALID;
-    return helm::create_model(ctx, ctx->stream, Px, Pz, h, slowness, 1, npml, alpha_max, out);
+    return helm::create_model(ctx, ctx->stream, Px, Pz, h, slowness, 1, npml, alpha_max, out, nullptr);
+}
+
+int helm_create_model_rho(helm_ctx* ctx, int Px, int Pz, double h, const double* slowness, const double* density,
+                          int npml, double alpha_max, helm_model** out) {
+    if (!ctx) return HELM_E_INVALID;
+    return helm::create_model(ctx, ctx->stream, Px, Pz, h, slowness, 1, npml, alpha_max, out, density);
 }
 
 void helm_destroy_model(helm_model* m) {
@@ -239,6 +265,8 @@ void helm_destroy_model(helm_model* m) {
         if (L.m2d) cudaFree(L.m2d);
         if (L.gkf) cudaFree(L.gkf);
         if (L.gkd) cudaFree(L.gkd);
+        if (L.rhof) cudaFree(L.rhof);
+        if (L.rhod) cudaFree(L.rhod);
     }
     delete m;
 }

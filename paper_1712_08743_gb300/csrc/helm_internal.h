@@ -43,6 +43,8 @@ struct LevelDev {
     size_t mstride;
     const void* gk;     // Galerkin levels: float* or double* [nmodels][10][n]
     size_t gkstride;
+    const void* rho;    // finest level with a density (Eq. 1): [3][n] east-edge, north-edge and diagonal
+                        // coefficients of the flux-form operator; nullptr for constant density
 };
 
 struct Level {
@@ -50,8 +52,10 @@ struct Level {
     double h = 0;
     float* m2f = nullptr;    // finest level only
     double* m2d = nullptr;
-    float* gkf = nullptr;    // Galerkin levels (l >= 1)
+    float* gkf = nullptr;    // Galerkin levels (l >= 1), and the finest level with a density
     double* gkd = nullptr;
+    float* rhof = nullptr;   // finest level with a density: [3][n] (see LevelDev::rho)
+    double* rhod = nullptr;
     size_t n() const { return (size_t)nx * nz; }
 };
 
@@ -73,6 +77,7 @@ struct helm_model {
     int Px = 0, Pz = 0, npml = 0, nx = 0, nz = 0;
     double h = 0, alpha_max = 0;
     int nmodels = 1;                      // > 1: one slowness model per right-hand side (serving batches)
+    bool vd = false;                      // variable density (Eq. 1): the finest level is a stored 9-point level
     int lf = 1;                           // first level with at most kFcycleMaxPoints nodes (latest F-cycle start)
     double m_max = 0;                     // largest slowness of the model(s): the shortest wavelength
     // Per precision (0: complex64, 1: complex128): first level handled by the
@@ -118,6 +123,7 @@ inline LevelDev level_dev(const helm_model* m, int l, bool dbl) {
     d.mstride = m->nmodels > 1 ? L.n() : 0;
     d.gk = dbl ? (const void*)L.gkd : (const void*)L.gkf;
     d.gkstride = m->nmodels > 1 ? kGalerkinCoefs * L.n() : 0;
+    d.rho = dbl ? (const void*)L.rhod : (const void*)L.rhof;
     return d;
 }
 
@@ -154,6 +160,8 @@ struct TailArgs {
 void launch_pad_model(const double* m_phys, int Px, int Pz, int npml, int nmodels, double* m_pad, float* m2f,
                       double* m2d, cudaStream_t s);
 void launch_galerkin(const helm_model* m, int l, cudaStream_t s);   // builds level l >= 1 from level l - 1
+void launch_rho_setup(const double* rho_phys, int Px, int Pz, int npml, const double* m2d, double* rhod, float* rhof,
+                      double* gkd, float* gkf, cudaStream_t s);
 void launch_sumsq(const double* a, size_t count, double* out, cudaStream_t s);
 
 // hw: per-RHS (h omega)^2 in the kernel's precision

@@ -76,6 +76,52 @@ void launch_pad_model(const double* m_phys, int Px, int Pz, int npml, int nmodel
     k_pad_model<<<dim3(grid1d(n), nmodels), 256, 0, s>>>(m_phys, Px, Pz, npml, m_pad, m2f, m2d);
 }
 
+// Finest-level coefficients of the flux-form operator of Eq. 1 (h^2 times
+// -div(rho grad)): the density is padded like the slowness (nearest physical
+// cell); an edge between nodes i and j takes the harmonic mean
+// 2 rho_i rho_j / (rho_i + rho_j), an edge to a ghost node outside the grid
+// takes rho_i. rho[0][i] / rho[1][i]: east / north edge of node i, rho[2][i]: the
+// sum of the node's four edges. gk: the same operator as a stored level for the
+// Galerkin kernels (G: centre = the sum, east and north = minus the edge, the
+// diagonal couplings 0; K: centre m^2, the rest 0).
+__device__ __forceinline__ double pad_at(const double* phys, int Px, int Pz, int npml, int ix, int iz) {
+    const int px = min(max(ix - npml, 0), Px - 1), pz = min(max(iz - npml, 0), Pz - 1);
+    return phys[(size_t)pz * Px + px];
+}
+__device__ __forceinline__ double harmonic(double a, double b) { return 2.0 * a * b / (a + b); }
+
+__global__ void k_rho_setup(const double* __restrict__ rho_phys, int Px, int Pz, int npml,
+                            const double* __restrict__ m2d, double* __restrict__ rhod, float* __restrict__ rhof,
+                            double* __restrict__ gkd, float* __restrict__ gkf) {
+    const int nx = Px + 2 * npml, nz = Pz + 2 * npml;
+    const size_t n = (size_t)nx * nz;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const int ix = (int)(i % nx), iz = (int)(i / nx);
+        const double r = pad_at(rho_phys, Px, Pz, npml, ix, iz);
+        const double re = ix + 1 < nx ? harmonic(r, pad_at(rho_phys, Px, Pz, npml, ix + 1, iz)) : r;
+        const double rw = ix > 0 ? harmonic(r, pad_at(rho_phys, Px, Pz, npml, ix - 1, iz)) : r;
+        const double rn = iz + 1 < nz ? harmonic(r, pad_at(rho_phys, Px, Pz, npml, ix, iz + 1)) : r;
+        const double rs = iz > 0 ? harmonic(r, pad_at(rho_phys, Px, Pz, npml, ix, iz - 1)) : r;
+        const double dg = re + rw + rn + rs;
+        const double v[3] = {re, rn, dg};
+        for (int k = 0; k < 3; ++k) {
+            rhod[(size_t)k * n + i] = v[k];
+            rhof[(size_t)k * n + i] = (float)v[k];
+        }
+        const double g[10] = {dg, -re, -rn, 0.0, 0.0, m2d[i], 0.0, 0.0, 0.0, 0.0};
+        for (int k = 0; k < 10; ++k) {
+            gkd[(size_t)k * n + i] = g[k];
+            gkf[(size_t)k * n + i] = (float)g[k];
+        }
+    }
+}
+
+void launch_rho_setup(const double* rho_phys, int Px, int Pz, int npml, const double* m2d, double* rhod, float* rhof,
+                      double* gkd, float* gkf, cudaStream_t s) {
+    const size_t n = (size_t)(Px + 2 * npml) * (Pz + 2 * npml);
+    k_rho_setup<<<grid1d(n), 256, 0, s>>>(rho_phys, Px, Pz, npml, m2d, rhod, rhof, gkd, gkf);
+}
+
 // sum of squares of a real array (one block; model setup only)
 __global__ void k_sumsq(const double* __restrict__ a, size_t count, double* out) {
     __shared__ double sh[32];
@@ -179,23 +225,64 @@ __global__ void __launch_bounds__(AP_X * AP_Y) k_apply(LevelDev L, int npml, T a
     }
 }
 
+template <typename T, int MODE, bool VD>
+__global__ void __launch_bounds__(256) k_apply_dots(LevelDev L, int npml, T acoef, const T* __restrict__ hwv,
+                                                    const T* __restrict__ u, T* __restrict__ y,
+                                                    const T* __restrict__ aux, double* partials, int pstride,
+                                                    RhsState* st, T scale);
+
 template <typename T>
 void launch_apply(const LevelDev& L0, int npml, double amax, const T* hw, const T* u, T* y, T scale,
                   int nrhs, cudaStream_t s) {
+    if (L0.rho) {   // variable density: the flux-form operator, one node per thread
+        dim3 blk(32, 8), grd((L0.nx + 31) / 32, (L0.nz + 7) / 8, nrhs);
+        k_apply_dots<T, 0, true><<<grd, blk, 0, s>>>(L0, npml, (T)layer_coef(npml, amax), hw, u, y,
+                                                     (const T*)nullptr, nullptr, 0, nullptr, scale);
+        return;
+    }
     dim3 blk(AP_X, AP_Y), grd((L0.nx + AP_X - 1) / AP_X, (L0.nz + AP_Y * AP_R - 1) / (AP_Y * AP_R), nrhs);
     k_apply<T><<<grd, blk, 0, s>>>(L0, npml, (T)layer_coef(npml, amax), hw, u, y, scale);
 }
 template void launch_apply<float>(const LevelDev&, int, double, const float*, const float*, float*, float, int, cudaStream_t);
 template void launch_apply<double>(const LevelDev&, int, double, const double*, const double*, double*, double, int, cudaStream_t);
 
+// (A u)_i on the finest level, one node: the 5-point operator of Eq. 2,
+// 4 u_i - sum of the four neighbours, or with a density (VD, Eq. 1) the flux form
+// d_i u_i - sum_e rho_e u_j from the stored coefficients; minus s (1 - j a) u_i;
+// neighbours outside the grid are zero. c = u_i. The two forms are separate
+// instances so that the constant-density arithmetic is not reshaped by the other.
+template <typename T, bool VD>
+__device__ __forceinline__ cx<T> fine_apply_point(const LevelDev& L, const T* __restrict__ ub, size_t i, int ix,
+                                                  int iz, T s, T a, cx<T> c) {
+    if constexpr (!VD) {
+        cx<T> yv((T(4) - s) * c.re - s * a * c.im, (T(4) - s) * c.im + s * a * c.re);
+        if (ix > 0) yv = yv - ldc(ub, i - 1);
+        if (ix + 1 < L.nx) yv = yv - ldc(ub, i + 1);
+        if (iz > 0) yv = yv - ldc(ub, i - L.nx);
+        if (iz + 1 < L.nz) yv = yv - ldc(ub, i + L.nx);
+        return yv;
+    } else {
+        const T* R = static_cast<const T*>(L.rho);
+        const size_t n = (size_t)L.nx * L.nz;
+        const T dg = R[2 * n + i];
+        cx<T> yv((dg - s) * c.re - s * a * c.im, (dg - s) * c.im + s * a * c.re);
+        if (ix > 0) yv = yv - R[i - 1] * ldc(ub, i - 1);
+        if (ix + 1 < L.nx) yv = yv - R[i] * ldc(ub, i + 1);
+        if (iz > 0) yv = yv - R[n + i - L.nx] * ldc(ub, i - L.nx);
+        if (iz + 1 < L.nz) yv = yv - R[n + i] * ldc(ub, i + L.nx);
+        return yv;
+    }
+}
+
 // y = A u with the dot products of the unpreconditioned BiCGSTAB (the
-// preconditioner-free path of the ablation): mode 1 <aux, y> -> alpha, mode 2
-// <y, u>, <y, y> -> omega, as the fused prolongation does after a cycle.
-template <typename T, int MODE>
+// preconditioner-free path of the ablation, and the variable-density path):
+// mode 1 <aux, y> -> alpha, mode 2 <y, aux or u>, <y, y> -> omega, as the fused
+// prolongation does after a cycle; mode 0 only y = scale A u.
+template <typename T, int MODE, bool VD>
 __global__ void __launch_bounds__(256) k_apply_dots(LevelDev L, int npml, T acoef, const T* __restrict__ hwv,
                                                     const T* __restrict__ u, T* __restrict__ y,
                                                     const T* __restrict__ aux, double* partials, int pstride,
-                                                    RhsState* st) {
+                                                    RhsState* st, T scale) {
     __shared__ double shred[96];
     pdl_trigger();
     pdl_wait();
@@ -210,22 +297,40 @@ __global__ void __launch_bounds__(256) k_apply_dots(LevelDev L, int npml, T acoe
         const T s = hwv[b] * (m2ptr<T>(L) + (size_t)b * L.mstride)[i];
         const T a = layer_alpha_t<T>(ix, iz, L.nx, L.nz, npml, acoef);
         const cx<T> c = ldc(ub, i);
-        cx<T> yv((T(4) - s) * c.re - s * a * c.im, (T(4) - s) * c.im + s * a * c.re);
-        if (ix > 0) yv = yv - ldc(ub, i - 1);
-        if (ix + 1 < L.nx) yv = yv - ldc(ub, i + 1);
-        if (iz > 0) yv = yv - ldc(ub, i - L.nx);
-        if (iz + 1 < L.nz) yv = yv - ldc(ub, i + L.nx);
-        stc(y + 2 * n * b, i, yv);
-        if (MODE == 1) {
-            const cx<T> q = ldc(aux + 2 * n * b, i);
-            d0 = q.re * yv.re + q.im * yv.im;
-            d1 = q.re * yv.im - q.im * yv.re;
+        if constexpr (!VD) {
+            cx<T> yv((T(4) - s) * c.re - s * a * c.im, (T(4) - s) * c.im + s * a * c.re);
+            if (ix > 0) yv = yv - ldc(ub, i - 1);
+            if (ix + 1 < L.nx) yv = yv - ldc(ub, i + 1);
+            if (iz > 0) yv = yv - ldc(ub, i - L.nx);
+            if (iz + 1 < L.nz) yv = yv - ldc(ub, i + L.nx);
+            stc(y + 2 * n * b, i, MODE == 0 ? scale * yv : yv);
+            if (MODE == 1) {
+                const cx<T> q = ldc(aux + 2 * n * b, i);
+                d0 = q.re * yv.re + q.im * yv.im;
+                d1 = q.re * yv.im - q.im * yv.re;
+            } else if (MODE == 2) {
+                d0 = yv.re * c.re + yv.im * c.im;
+                d1 = yv.re * c.im - yv.im * c.re;
+                d2 = yv.re * yv.re + yv.im * yv.im;
+            }
         } else {
-            d0 = yv.re * c.re + yv.im * c.im;
-            d1 = yv.re * c.im - yv.im * c.re;
-            d2 = yv.re * yv.re + yv.im * yv.im;
+            const cx<T> yv = fine_apply_point<T, true>(L, ub, i, ix, iz, s, a, c);
+            stc(y + 2 * n * b, i, MODE == 0 ? scale * yv : yv);
+            if (MODE == 1) {
+                const cx<T> q = ldc(aux + 2 * n * b, i);
+                d0 = q.re * yv.re + q.im * yv.im;
+                d1 = q.re * yv.im - q.im * yv.re;
+            } else if (MODE == 2) {
+                // BiCGSTAB's omega takes <t, s> with s the preconditioner's input: aux when
+                // given (after a separate cycle), else u itself (no preconditioner)
+                const cx<T> q = aux ? ldc(aux + 2 * n * b, i) : c;
+                d0 = yv.re * q.re + yv.im * q.im;
+                d1 = yv.re * q.im - yv.im * q.re;
+                d2 = yv.re * yv.re + yv.im * yv.im;
+            }
         }
     }
+    if (MODE == 0) return;
     const T vv[3] = {d0, d1, d2};
     double acc[3];
     const int nblk = gridDim.x * gridDim.y, blk = blockIdx.y * gridDim.x + blockIdx.x;
@@ -254,10 +359,15 @@ void launch_apply_dots(int mode, const LevelDev& L0, int npml, double amax, cons
                        const T* aux, double* partials, int pstride, RhsState* st, int nrhs, cudaStream_t s) {
     dim3 blk(32, 8), grd((L0.nx + 31) / 32, (L0.nz + 7) / 8, nrhs);
     const T ac = (T)layer_coef(npml, amax);
-    if (mode == 1)
-        launch_pdl(k_apply_dots<T, 1>, grd, blk, 0, s, L0, npml, ac, hw, u, y, aux, partials, pstride, st);
+    const bool vd = L0.rho != nullptr;
+    if (mode == 1 && vd)
+        launch_pdl(k_apply_dots<T, 1, true>, grd, blk, 0, s, L0, npml, ac, hw, u, y, aux, partials, pstride, st, T(1));
+    else if (mode == 1)
+        launch_pdl(k_apply_dots<T, 1, false>, grd, blk, 0, s, L0, npml, ac, hw, u, y, aux, partials, pstride, st, T(1));
+    else if (vd)
+        launch_pdl(k_apply_dots<T, 2, true>, grd, blk, 0, s, L0, npml, ac, hw, u, y, aux, partials, pstride, st, T(1));
     else
-        launch_pdl(k_apply_dots<T, 2>, grd, blk, 0, s, L0, npml, ac, hw, u, y, aux, partials, pstride, st);
+        launch_pdl(k_apply_dots<T, 2, false>, grd, blk, 0, s, L0, npml, ac, hw, u, y, aux, partials, pstride, st, T(1));
 }
 template void launch_apply_dots<float>(int, const LevelDev&, int, double, const float*, const float*, float*,
                                        const float*, double*, int, RhsState*, int, cudaStream_t);
@@ -267,7 +377,7 @@ template void launch_apply_dots<double>(int, const LevelDev&, int, double, const
 // ======================================================= FP64 outer residual
 // r = f - A u in FP64; writes the inner right-hand side rin = r in precision TI
 // and decides, per right-hand side, whether refinement continues.
-template <typename TI>
+template <typename TI, bool VD>
 __global__ void __launch_bounds__(256) k_resid64(LevelDev L, int npml, double acoef, const double* __restrict__ w2,
                                                  const double* __restrict__ f, const double* __restrict__ u,
                                                  TI* __restrict__ rin, double* partials, int pstride, RhsState* st,
@@ -284,12 +394,8 @@ __global__ void __launch_bounds__(256) k_resid64(LevelDev L, int npml, double ac
         const size_t i = (size_t)iz * L.nx + ix;
         const double s = L.h2 * w2[b] * (static_cast<const double*>(L.m2) + (size_t)b * L.mstride)[i];
         const double a = layer_alpha_t<double>(ix, iz, L.nx, L.nz, npml, acoef);
-        cx<double> c = ldc(ub, i);
-        cx<double> acc((4.0 - s) * c.re - s * a * c.im, (4.0 - s) * c.im + s * a * c.re);
-        if (ix > 0) acc = acc - ldc(ub, i - 1);
-        if (ix + 1 < L.nx) acc = acc - ldc(ub, i + 1);
-        if (iz > 0) acc = acc - ldc(ub, i - L.nx);
-        if (iz + 1 < L.nz) acc = acc - ldc(ub, i + L.nx);
+        const cx<double> c = ldc(ub, i);
+        const cx<double> acc = fine_apply_point<double, VD>(L, ub, i, ix, iz, s, a, c);
         cx<double> fv = ldc(f + 2 * n * b, i);
         cx<double> r = fv - acc;
         v[0] = r.re * r.re + r.im * r.im;
@@ -318,8 +424,12 @@ void launch_resid64(const LevelDev& L0, int npml, double amax, const double* w2,
                     TI* rin, double* partials, int pstride, RhsState* st, double tol, double inner_floor,
                     double inner_fac, int first, int nrhs, cudaStream_t s) {
     dim3 blk(32, 8), grd((L0.nx + 31) / 32, (L0.nz + 7) / 8, nrhs);
-    k_resid64<TI><<<grd, blk, 0, s>>>(L0, npml, layer_coef(npml, amax), w2, f, u, rin, partials, pstride, st, tol,
-                                      inner_floor, inner_fac, first);
+    if (L0.rho)
+        k_resid64<TI, true><<<grd, blk, 0, s>>>(L0, npml, layer_coef(npml, amax), w2, f, u, rin, partials, pstride,
+                                                st, tol, inner_floor, inner_fac, first);
+    else
+        k_resid64<TI, false><<<grd, blk, 0, s>>>(L0, npml, layer_coef(npml, amax), w2, f, u, rin, partials, pstride,
+                                                 st, tol, inner_floor, inner_fac, first);
 }
 template void launch_resid64<float>(const LevelDev&, int, double, const double*, const double*, const double*, float*, double*, int, RhsState*, double, double, double, int, int, cudaStream_t);
 template void launch_resid64<double>(const LevelDev&, int, double, const double*, const double*, const double*, double*, double*, int, RhsState*, double, double, double, int, int, cudaStream_t);
@@ -747,7 +857,7 @@ __global__ void k_galerkin(int fine0, const double* __restrict__ m2f, const doub
 void launch_galerkin(const helm_model* m, int l, cudaStream_t s) {
     const Level& F = m->lv[l - 1];
     const Level& C = m->lv[l];
-    const int fine0 = (l == 1);
+    const int fine0 = (l == 1) && !m->vd;   // with a density the finest level is stored like a coarse one
     k_galerkin<<<dim3(grid1d(C.n()), m->nmodels), 256, 0, s>>>(fine0, F.m2d, F.gkd, F.nx, F.nz, F.n(),
                                                               kGalerkinCoefs * F.n(), C.gkd, C.gkf, C.nx, C.nz);
 }
@@ -1119,7 +1229,7 @@ inline int march_rows(int col_warps, int rows, int nrhs, int longest) {
 template <typename T>
 void launch_restrict(const LevelDev& Lf, const LevelDev& Lc, const T* w2, double b1, double b2, double wj,
                      const T* f, T* fc, const RhsState* st, int nrhs, cudaStream_t s, int tile) {
-    if (Lf.m2) {
+    if (Lf.m2 && !Lf.rho) {   // finest constant-density level; a density level is stored like a coarse one
         const int cw = (Lc.nx + RM_COLS - 1) / RM_COLS;
         const int ks = march_rows(cw, Lc.nz, nrhs, 16);
         dim3 grd((cw + 7) / 8, (Lc.nz + ks - 1) / ks, nrhs);
@@ -1381,7 +1491,9 @@ void launch_prolong(int mode, const LevelDev& Lf, const LevelDev& Lc, int npml, 
                     double* partials, int pstride, RhsState* st, int nrhs, cudaStream_t s, int accumulate, int tile) {
     const T ac = (T)layer_coef(npml, amax);
     const bool small = sizeof(T) == 4 && tile == 0;
-    if (mode == 0 && !Lf.m2) {
+    // a density level is stored like a coarse one: only mode 0 exists there (the
+    // caller applies A and forms the dots with launch_apply_dots)
+    if (mode == 0 && (!Lf.m2 || Lf.rho)) {
         constexpr int GPZ = GTile<T>::PZ;
         if (small) {
             constexpr int GPX = 16;
@@ -1887,7 +1999,7 @@ template <typename T>
 void launch_correct_restrict(const LevelDev& Lf, const LevelDev& Lc, const T* w2, double b1, double b2,
                              double wj, const T* f, const T* ec, T* fc, const RhsState* st, int nrhs, cudaStream_t s,
                              int tile) {
-    if (Lf.m2) {
+    if (Lf.m2 && !Lf.rho) {
         dim3 grd((Lc.nx + RCX - 1) / RCX, (Lc.nz + RCZ - 1) / RCZ, nrhs);
         k_correct_restrict<T, false><<<grd, RCX * RCZ, 0, s>>>(Lf, Lc, w2, (T)b1, (T)b2, (T)wj, f, ec, fc, st);
     } else if (sizeof(T) == 4 && tile == 0) {

@@ -160,6 +160,18 @@ void mg_apply(const helm_model* m, const MgCall& c, const MgLevels<T>& B, const 
     const LevelDev L0 = level_dev(m, 0, dbl), L1 = level_dev(m, 1, dbl);
     launch_restrict<T>(L0, L1, hw, c.b1, c.b2, c.wj, in, B.f[1], c.st, c.nrhs, c.s);
     mg_cycle<T>(m, c, B, 1, c.lf == 1, 0);
+    if (m->vd && mode != 0) {
+        // variable density: the stored-level prolongation, then y = A out (with the
+        // dots of modes 1 and 2) in a separate kernel
+        launch_prolong<T>(0, L0, L1, m->npml, m->alpha_max, hw, c.b1, c.b2, c.wj, in, B.e[1], out, nullptr, nullptr,
+                          c.partials, c.pstride, c.st, c.nrhs, c.s, 0, m->tile_prolong[0]);
+        if (mode == 3)
+            launch_apply<T>(L0, m->npml, m->alpha_max, hw, out, y, T(1), c.nrhs, c.s);
+        else   // mode 2 dots A out with the cycle's input, as the fused kernel does
+            launch_apply_dots<T>(mode, L0, m->npml, m->alpha_max, hw, out, y, mode == 2 ? in : aux, c.partials,
+                                 c.pstride, c.st, c.nrhs, c.s);
+        return;
+    }
     launch_prolong<T>(mode, L0, L1, m->npml, m->alpha_max, hw, c.b1, c.b2, c.wj, in, B.e[1], out, y, aux,
                       c.partials, c.pstride, c.st, c.nrhs, c.s, 0, m->tile_prolong[0]);
 }
@@ -175,7 +187,7 @@ static int count_cycle(const helm_model* m, int lt, int l, bool F, int lf) {
     return k;
 }
 int mg_kernels_per_apply(const helm_model* m, bool dbl, int lf) {
-    return 2 + count_cycle(m, m->tail_level(dbl), 1, lf == 1, lf);
+    return 2 + (m->vd ? 1 : 0) + count_cycle(m, m->tail_level(dbl), 1, lf == 1, lf);
 }
 
 int fcycle_level(const helm_model* m, const double* h_w2, int nrhs) {
@@ -827,7 +839,7 @@ int autotune(helm_model* m, cudaStream_t s, int nrhs, double hw2, int reps, int*
         float tp[2], tr[2] = {0.f, 0.f};
         for (int t = 0; t < 2; ++t) {
             tp[t] = time_it([&] {
-                launch_prolong<float>(l == 0 ? 1 : 0, Lf, Lc, m->npml, m->alpha_max, w2f.as<float>(), 1.0, 0.5, 0.5,
+                launch_prolong<float>(l == 0 && !m->vd ? 1 : 0, Lf, Lc, m->npml, m->alpha_max, w2f.as<float>(), 1.0, 0.5, 0.5,
                                       F(0), F(1), F(2), F(3), F(0), part.as<double>(), pstride, S, nrhs, s, 0, t);
             });
             if (l > 0)

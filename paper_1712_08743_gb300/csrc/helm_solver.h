@@ -87,7 +87,8 @@ int autotune(helm_model* m, cudaStream_t s, int nrhs, double hw2, int reps, int*
 int time_kernel(const helm_model* m, cudaStream_t s, int kernel, int nrhs, double hw2, int reps, double* ms,
                 double* bytes);
 
+// density (nullable, host [Pz][Px], nmodels == 1 only): the variable-density operator of Eq. 1
 int create_model(helm_ctx* ctx, cudaStream_t s, int Px, int Pz, double h, const double* slowness, int nmodels,
-                 int npml, double alpha_max, helm_model** out);
+                 int npml, double alpha_max, helm_model** out, const double* density = nullptr);
 
 }  // namespace helm

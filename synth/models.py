@@ -184,6 +184,13 @@ def c5_request(i: int, sizes=(128, 256, 512, 1024)) -> Model:
     return Model(f"c5_req{i}_{n}", c, h, src, np.array([f]), seed=5 + i)
 
 
+def gardner_density(velocity: np.ndarray) -> np.ndarray:
+    """Density (g/cm^3) from velocity (m/s) by Gardner's empirical relation
+    0.31 c^0.25: a layered density that follows the velocity model, as input for
+    the variable-density operator."""
+    return 0.31 * np.asarray(velocity, np.float64) ** 0.25
+
+
 def random_complex(rng, shape, dtype=np.complex128) -> np.ndarray:
     """Standard complex normal samples (real and imaginary parts N(0, 1/2))."""
     a = rng.standard_normal(shape) + 1j * rng.standard_normal(shape)
