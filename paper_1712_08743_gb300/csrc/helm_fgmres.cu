@@ -295,7 +295,7 @@ __device__ void fg_finish_column(RhsState& S, const FgDev& fg, int b, int j, dou
 // and k_fg_finish finishes the column (off the critical path). With `check` an
 // RHS whose first pass asked for no second pass skips the kernel.
 template <typename T, int NV>
-__global__ void __launch_bounds__(256) k_fg_axpy(const T* __restrict__ V, size_t vstride, T* __restrict__ w, int j,
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_fg_axpy(const T* __restrict__ V, size_t vstride, T* __restrict__ w, int j,
                                                  int mode, int check, double* partials, int pstride, RhsState* st,
                                                  FgDev fg, int* nactive, size_t n) {
     __shared__ double sh[32];
