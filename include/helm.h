@@ -292,7 +292,10 @@ typedef enum {
     HELM_KERNEL_BICG_P = 5,   /* BiCGSTAB p update, complex64 */
     HELM_KERNEL_APPLY64 = 6,  /* y = A u, complex128 */
     HELM_KERNEL_FG_DOTS = 7,  /* FGMRES Gram-Schmidt dot products at Arnoldi step 4 (5 basis vectors), complex64 */
-    HELM_KERNEL_FG_AXPY = 8   /* FGMRES Gram-Schmidt update + per-block norm parts at step 4, complex64 */
+    HELM_KERNEL_FG_AXPY = 8,  /* FGMRES Gram-Schmidt update + per-block norm parts at step 4, complex64 */
+    HELM_KERNEL_TAIL = 9      /* coarse-level tail: one F-cycle over the levels from the first of at most
+                                 2048 nodes down to the coarsest, one block per right-hand side, complex64;
+                                 bytes = its input and output on the tail's top level */
 } helm_kernel_id;
 int helm_time_kernel(helm_model* model, int kernel, int nrhs, double omega, int reps, double* ms_per_launch,
                      double* bytes_per_launch);

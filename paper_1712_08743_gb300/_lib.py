@@ -36,6 +36,7 @@ HELM_KERNEL_BICG_P = 5
 HELM_KERNEL_APPLY64 = 6
 HELM_KERNEL_FG_DOTS = 7
 HELM_KERNEL_FG_AXPY = 8
+HELM_KERNEL_TAIL = 9
 HELM_KRYLOV_BICGSTAB = 0
 HELM_KRYLOV_FGMRES = 1
 HELM_FWI_SIMULTANEOUS = 0

@@ -111,32 +111,42 @@ static const T* hw_of(const MgCall& c) {
     return static_cast<const T*>(sizeof(T) == 8 ? (const void*)c.w2 : (const void*)c.w2f);
 }
 
+// Arguments of one tail launch (an F- or V-cycle over levels lt..L) from the
+// level-lt right-hand side `in` into `out`.
+template <typename T>
+static TailArgs tail_args(const helm_model* m, bool F, const void* in, void* out, int acc, const void* minv,
+                          const int* slot, const double* w2, double b1, double b2, double wj) {
+    const bool dbl = sizeof(T) == 8;
+    TailArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.lt = m->tail_level(dbl);
+    a.L = (int)m->lv.size() - 1;
+    for (int q = 0; q <= a.L; ++q) a.lv[q] = level_dev(m, q, dbl);
+    a.in = in;
+    a.out = out;
+    a.accumulate = acc;
+    a.minv = minv;
+    a.slot = slot;
+    a.ops = F ? m->ops_f[dbl] : m->ops_v[dbl];
+    a.nops = F ? m->nops_f[dbl] : m->nops_v[dbl];
+    bool ms = false;
+    tail_smem_bytes(m, a.lt, sizeof(T), &ms, &a.minv_off);
+    a.minv_smem = ms ? 1 : 0;
+    for (int q = a.lt, o = 0; q <= a.L; ++q) { a.off[q] = o; o += 8 * (int)m->lv[q].n(); }
+    a.w2 = w2;
+    a.b1 = b1;
+    a.b2 = b2;
+    a.wj = wj;
+    return a;
+}
+
 template <typename T>
 static void mg_cycle(const helm_model* m, const MgCall& c, const MgLevels<T>& B, int l, bool F, int acc) {
     const bool dbl = sizeof(T) == 8;
     const T* hw = hw_of<T>(c);
     const int lt = m->tail_level(dbl);
     if (l >= lt) {
-        TailArgs a;
-        std::memset(&a, 0, sizeof(a));
-        a.lt = lt;
-        a.L = (int)m->lv.size() - 1;
-        for (int q = 0; q <= a.L; ++q) a.lv[q] = level_dev(m, q, dbl);
-        a.in = B.f[l];
-        a.out = B.e[l];
-        a.accumulate = acc;
-        a.minv = c.minv;
-        a.slot = c.slot;
-        a.ops = F ? m->ops_f[dbl] : m->ops_v[dbl];
-        a.nops = F ? m->nops_f[dbl] : m->nops_v[dbl];
-        bool ms = false;
-        tail_smem_bytes(m, lt, sizeof(T), &ms, &a.minv_off);
-        a.minv_smem = ms ? 1 : 0;
-        for (int q = lt, o = 0; q <= a.L; ++q) { a.off[q] = o; o += 8 * (int)m->lv[q].n(); }
-        a.w2 = c.w2;
-        a.b1 = c.b1;
-        a.b2 = c.b2;
-        a.wj = c.wj;
+        const TailArgs a = tail_args<T>(m, F, B.f[l], B.e[l], acc, c.minv, c.slot, c.w2, c.b1, c.b2, c.wj);
         launch_tail<T>(a, m->tail_smem[dbl], c.nrhs, c.st, c.s);
         return;
     }
@@ -765,6 +775,21 @@ int time_kernel(const helm_model* m, cudaStream_t s, int kernel, int nrhs, doubl
                 launch = [&, j, vs, Vb, Wb] { launch_fg_axpy<float>(Vb, vs, Wb, j, 3, 0, part.as<double>(), pstride, S, fgd, nact.as<int>(), n, nrhs, s); };
                 *bytes = N * B * 8.0 * (j + 3);
             }
+            break;
+        }
+        case HELM_KERNEL_TAIL: {
+            // one F-cycle over the tail levels; the coarsest inverse is filler of the
+            // right size (the launch's cost does not depend on its values)
+            const int lt = m->tail_level(false);
+            const size_t nL = m->lv.back().n(), nt = m->lv[lt].n();
+            TRY_ALLOC(fgV, sizeof(float) * 2 * nL * nL, s);
+            HELM_CUDA_TRY(cudaMemsetAsync(fgV.p, 0x3C, sizeof(float) * 2 * nL * nL, s));
+            TRY_ALLOC(fgSmall, sizeof(int) * nrhs, s);
+            HELM_CUDA_TRY(cudaMemsetAsync(fgSmall.p, 0, sizeof(int) * nrhs, s));
+            const TailArgs a = tail_args<float>(m, true, F(0), F(1), 0, fgV.p, fgSmall.as<int>(), w2.as<double>(),
+                                                1.0, 0.5, 0.8);
+            launch = [&, a] { launch_tail<float>(a, m->tail_smem[0], nrhs, S, s); };
+            *bytes = 16.0 * B * (double)nt;
             break;
         }
         default:

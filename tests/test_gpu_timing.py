@@ -35,15 +35,21 @@ def test_time_kernel_bytes_and_times(hg):
         _lib.HELM_KERNEL_FG_DOTS: n * nrhs * 8.0 * 6,
         _lib.HELM_KERNEL_FG_AXPY: n * nrhs * 8.0 * 7,
     }
-    for kid in range(9):
+    for kid in range(10):
         ms, byt = C.c_double(), C.c_double()
         api.check(lib.helm_time_kernel(model.handle, kid, nrhs, 2 * np.pi * 5.0, 3, C.byref(ms), C.byref(byt)),
                   "helm_time_kernel")
         assert ms.value > 0.0 and byt.value > 0.0, kid
         if kid in expect:
             assert byt.value == pytest.approx(expect[kid], rel=1e-12), kid
+    # the tail moves its top level's input and output: a whole number of complex64
+    # nodes per right-hand side, at most the 2048 of a complex64 tail level
     ms, byt = C.c_double(), C.c_double()
-    assert lib.helm_time_kernel(model.handle, 9, nrhs, 2 * np.pi * 5.0, 3, C.byref(ms), C.byref(byt)) == \
+    api.check(lib.helm_time_kernel(model.handle, _lib.HELM_KERNEL_TAIL, nrhs, 2 * np.pi * 5.0, 3, C.byref(ms),
+                                   C.byref(byt)), "helm_time_kernel")
+    nodes = byt.value / (16.0 * nrhs)
+    assert nodes == int(nodes) and 1 <= nodes <= 2048
+    assert lib.helm_time_kernel(model.handle, 10, nrhs, 2 * np.pi * 5.0, 3, C.byref(ms), C.byref(byt)) == \
         _lib.HELM_E_INVALID
     model.close()
     ctx.close()
