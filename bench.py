@@ -65,6 +65,8 @@ def parse():
     ap.add_argument("--kernels-only", action="store_true",
                     help="time only the hot kernels alone (the roofline legs), print one line per kernel")
     ap.add_argument("--requests", type=int, default=48, help="serving: number of requests")
+    ap.add_argument("--serve-sizes", default="128,256,512,1024",
+                    help="serving: physical grid sizes N (N x N) the requests draw from")
     ap.add_argument("--cg", type=int, default=5, help="gn, fwi: conjugate-gradient iterations per Gauss-Newton step")
     ap.add_argument("--gn", type=int, default=2, help="fwi: Gauss-Newton iterations per frequency group")
     ap.add_argument("--fwi-strategy", default="sequential", choices=["sequential", "simultaneous"])
@@ -649,8 +651,10 @@ def run_serving(args):
 
     build.build()
     ctx = api.Context(0)
-    reqs = [models.c5_request(i, sizes=(128, 256, 512)) for i in range(args.requests)]
-    opts = dict(tol=1e-6, precision="mixed", krylov=_lib.HELM_KRYLOV_FGMRES, max_it=20000, reorth=REORTH[args.reorth])
+    sizes = tuple(int(x) for x in args.serve_sizes.split(","))
+    reqs = [models.c5_request(i, sizes=sizes) for i in range(args.requests)]
+    kry = _lib.HELM_KRYLOV_FGMRES if args.krylov == "fgmres" else _lib.HELM_KRYLOV_BICGSTAB
+    opts = dict(tol=1e-6, precision="mixed", krylov=kry, max_it=20000, reorth=REORTH[args.reorth])
     # sequential plain FP64 on a subset
     o64 = dict(tol=1e-6, precision="fp64", max_it=20000)
     t_seq = []
@@ -673,11 +677,15 @@ def run_serving(args):
     res = [api.helm_poll(ctx, t, -1) for t in tickets]
     t_total = time.perf_counter() - t_start
     lat = [x.latency_ms for x in res]
-    print(json.dumps({"metric": "helmholtz_solves_per_s", "workload": f"serving_{len(reqs)}req_128-512",
+    print(json.dumps({"metric": "helmholtz_solves_per_s", "workload": f"serving_{len(reqs)}req_{min(sizes)}-{max(sizes)}",
+                      "krylov": args.krylov,
                       "value": len(reqs) / t_total, "unit": "solves/s", "p50_ms": float(np.percentile(lat, 50)),
                       "p99_ms": float(np.percentile(lat, 99)), "arrival_rate": rate,
                       "sequential_fp64_solves_per_s": seq_rate,
-                      "ok": sum(x.status == 0 for x in res), "mean_batch": float(np.mean([x.batch_size for x in res]))}),
+                      "ok": sum(x.status == 0 for x in res), "mean_batch": float(np.mean([x.batch_size for x in res])),
+                      "sizes": {str(n): sum(r.slowness.shape[0] == n for r in reqs) for n in sizes},
+                      "not_ok": [{"N": int(r.slowness.shape[0]), "f_hz": float(r.omegas[0] / (2 * np.pi)),
+                                  "status": int(x.status), **x.stats} for r, x in zip(reqs, res) if x.status != 0]}),
           flush=True)
     for t in tickets:
         api.helm_release(ctx, t)
@@ -687,7 +695,7 @@ def run_serving(args):
 def main():
     args = parse()
     if args.krylov is None:
-        args.krylov = "fgmres" if args.workload == "single" and not args.kernels_only else "bicgstab"
+        args.krylov = "fgmres" if args.workload in ("single", "serving") and not args.kernels_only else "bicgstab"
     if args.impl == "reference":
         run_reference(args)
     elif args.kernels_only:
