@@ -43,6 +43,18 @@ def test_binding_covers_every_declared_symbol():
     assert set(declared_functions()) <= set(_lib.SIGNATURES)
 
 
+def test_binding_constants_match_the_header():
+    """Every enumerator of include/helm.h (status codes, options, kernel ids) has
+    the same value in the binding."""
+    from paper_1712_08743_gb300 import _lib
+
+    src = re.sub(r"/\*.*?\*/", "", open(os.path.join(ROOT, "include", "helm.h")).read(), flags=re.S)
+    enums = {k: int(v) for k, v in re.findall(r"\b(HELM_[A-Z0-9_]+)\s*=\s*(-?\d+)", src)}
+    assert len(enums) >= 30
+    for name, value in enums.items():
+        assert getattr(_lib, name) == value, name
+
+
 def test_calls_without_gpu(built_lib):
     from paper_1712_08743_gb300 import _lib
 
