@@ -153,6 +153,27 @@ def test_ragged_grid_general_rhs(hg, ctx):
     model.close()
 
 
+def test_degenerate_inputs(hg, ctx):
+    """Degenerate cases of Eq. 3: a zero right-hand side gives u = 0 at once, also
+    beside a non-zero one in the same batch; a frequency near zero (almost the
+    Dirichlet Poisson problem) still matches the oracle; an empty batch is refused."""
+    mdl = GRIDS[1][1]()
+    model = hg.helm_create_model(ctx, mdl.slowness, mdl.h, mdl.npml, mdl.alpha_max)
+    F = np.zeros((2, model.nz, model.nx), np.complex128)
+    F[1] = models.random_complex(np.random.default_rng(7), (model.nz, model.nx))
+    om = 2 * np.pi * np.array([5.0, 0.05])
+    for precision in ("fp64", "mixed"):
+        u, stats, st = hg.helm_solve(model, om, f=F, opts=dict(tol=1e-10, precision=precision))
+        assert st == hg.HELM_OK, stats
+        assert np.all(u[0] == 0) and stats[0]["converged"] and stats[0]["relres"] == 0.0
+        ref = oracle.solve_fields(mdl.slowness, mdl.h, om[1], None, mdl.npml, mdl.alpha_max,
+                                  F=F[1].reshape(1, -1))[0]
+        assert rel(u[1], ref) < 1e-6, (precision, rel(u[1], ref))
+    with pytest.raises(hg.HelmError):
+        hg.helm_solve(model, np.zeros(0), np.zeros((0, 2), np.int32))
+    model.close()
+
+
 def test_batch_equals_each_alone_and_oracle(hg, ctx):
     mdl = models.c3_model()
     model = hg.helm_create_model(ctx, mdl.slowness, mdl.h, mdl.npml, mdl.alpha_max)
