@@ -65,6 +65,8 @@ def parse():
     ap.add_argument("--kernels-only", action="store_true",
                     help="time only the hot kernels alone (the roofline legs), print one line per kernel")
     ap.add_argument("--requests", type=int, default=48, help="serving: number of requests")
+    ap.add_argument("--serve-beta2", type=float, default=1.0,
+                    help="serving: imaginary shift beta2 of the preconditioner (1: the paper's (1, 1) shift)")
     ap.add_argument("--serve-sizes", default="128,256,512,1024",
                     help="serving: physical grid sizes N (N x N) the requests draw from")
     ap.add_argument("--cg", type=int, default=5, help="gn, fwi: conjugate-gradient iterations per Gauss-Newton step")
@@ -638,7 +640,7 @@ def run_ablation(args):
             rows.append({"f_hz": f_hz, "preconditioner": name, "iters": st[0]["iters"], "ms": 1e3 * dt,
                          "converged": bool(st[0]["converged"]), "relres": st[0]["relres"]})
     print(json.dumps({"metric": "krylov_iterations", "workload": "ablation_401x201_1src_3-7Hz",
-                      "krylov": args.krylov, "rows": rows}), flush=True)
+                      "krylov": args.krylov, "shift": [1.0, args.serve_beta2], "rows": rows}), flush=True)
     model.close()
     ctx.close()
 
@@ -657,9 +659,10 @@ def run_serving(args):
     sizes = tuple(int(x) for x in args.serve_sizes.split(","))
     reqs = [models.c5_request(i, sizes=sizes) for i in range(args.requests)]
     kry = _lib.HELM_KRYLOV_FGMRES if args.krylov == "fgmres" else _lib.HELM_KRYLOV_BICGSTAB
-    opts = dict(tol=1e-6, precision="mixed", krylov=kry, max_it=20000, reorth=REORTH[args.reorth])
+    opts = dict(tol=1e-6, precision="mixed", krylov=kry, max_it=20000, reorth=REORTH[args.reorth],
+                beta2=args.serve_beta2)
     # sequential plain FP64 on a subset
-    o64 = dict(tol=1e-6, precision="fp64", max_it=20000)
+    o64 = dict(tol=1e-6, precision="fp64", max_it=20000, beta2=args.serve_beta2)
     t_seq = []
     for r in reqs[: min(8, len(reqs))]:
         mm = api.helm_create_model(ctx, r.slowness, r.h)
@@ -681,7 +684,7 @@ def run_serving(args):
     t_total = time.perf_counter() - t_start
     lat = [x.latency_ms for x in res]
     print(json.dumps({"metric": "helmholtz_solves_per_s", "workload": f"serving_{len(reqs)}req_{min(sizes)}-{max(sizes)}",
-                      "krylov": args.krylov,
+                      "krylov": args.krylov, "shift": [1.0, args.serve_beta2],
                       "value": len(reqs) / t_total, "unit": "solves/s", "p50_ms": float(np.percentile(lat, 50)),
                       "p99_ms": float(np.percentile(lat, 99)), "arrival_rate": rate,
                       "sequential_fp64_solves_per_s": seq_rate,
