@@ -65,8 +65,9 @@ def parse():
     ap.add_argument("--kernels-only", action="store_true",
                     help="time only the hot kernels alone (the roofline legs), print one line per kernel")
     ap.add_argument("--requests", type=int, default=48, help="serving: number of requests")
-    ap.add_argument("--serve-beta2", type=float, default=1.0,
-                    help="serving: imaginary shift beta2 of the preconditioner (1: the paper's (1, 1) shift)")
+    ap.add_argument("--serve-beta2", type=float, default=None,
+                    help="serving: imaginary shift beta2 of the preconditioner (default: the library's (1, 0.5), "
+                         "whose stall guard switches a stalled solve to the paper's (1, 1))")
     ap.add_argument("--serve-sizes", default="128,256,512,1024",
                     help="serving: physical grid sizes N (N x N) the requests draw from")
     ap.add_argument("--cg", type=int, default=5, help="gn, fwi: conjugate-gradient iterations per Gauss-Newton step")
@@ -146,10 +147,11 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------ CPU oracle arm
-def oracle_c2_timing(nsolves: int):
+def oracle_c2_timing(nsolves: int, want_field: bool = False):
     """Sparse-LU oracle on the same problem: assembly and factorisation once
     (timed together from the padded model), then nsolves triangular solves of
-    the point-source right-hand side. Returns (setup seconds, [solve seconds])."""
+    the point-source right-hand side. Returns (setup seconds, [solve seconds]),
+    and the oracle wavefield [1][nz][nx] as a third item when want_field."""
     import oracle
     from synth import models
 
@@ -161,11 +163,12 @@ def oracle_c2_timing(nsolves: int):
     t_fac = time.perf_counter() - t0
     F = oracle.point_sources(m_pad.shape[1], m_pad.shape[0], mdl.h, mdl.sources + mdl.npml)
     ts = []
+    U = None
     for _ in range(nsolves):
         t0 = time.perf_counter()
-        fac.solve(F)
+        U = fac.solve(F)
         ts.append(time.perf_counter() - t0)
-    return t_fac, ts
+    return (t_fac, ts, U) if want_field else (t_fac, ts)
 
 
 def oracle_c2_full_solve() -> tuple[float, float]:
@@ -244,6 +247,52 @@ def time_kernels(lib, api, _lib, model, omega, reps=20):
             continue
         out[name] = {"ms": tms.value, "bytes": byt.value, "gbs": byt.value / tms.value / 1e6, "nrhs": nb}
     return out
+
+
+def profile_solve(lib, _lib, step_fn):
+    """One solve of the bench workload with every launch of the library timed by
+    CUDA events on its stream (helm_profile_begin/end, no graphs, launches
+    serialised); returns per-kernel totals summed over the grids each ran on."""
+    import ctypes as C
+
+    lib.helm_profile_begin()
+    step_fn()
+    cap = 512
+    buf = (_lib.helm_profile_entry * cap)()
+    n = C.c_int()
+    lib.helm_profile_end(buf, cap, C.byref(n))
+    per = {}
+    grids = []
+    for e in buf[: min(n.value, cap)]:
+        name = e.name.decode()
+        d = per.setdefault(name, {"launches": 0, "ms": 0.0, "bytes": 0.0})
+        d["launches"] += int(e.launches)
+        d["ms"] += e.ms
+        d["bytes"] += e.bytes
+        grids.append({"kernel": name, "grid": f"{e.nx}x{e.nz}", "launches": int(e.launches), "ms": e.ms,
+                      "bytes": e.bytes})
+    return per, grids
+
+
+def traffic_for(kernel: str, grid: str):
+    """DRAM bytes per launch of `kernel` on `grid` from the committed ncu summary,
+    when the summary was taken of the kernel's current source (else None)."""
+    import hashlib
+
+    prof = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(prof):
+        return None
+    with open(prof) as f:
+        tr = json.load(f)
+    e = tr.get(kernel)
+    if not isinstance(e, dict) or e.get("grid") != grid:
+        return None
+    src = os.path.join(ROOT, "paper_1712_08743_gb300", "csrc", e.get("file", ""))
+    if not os.path.exists(src):
+        return None
+    with open(src, "rb") as f:
+        sha = hashlib.sha1(f.read()).hexdigest()
+    return e.get("traffic") if e.get("src_sha1") == sha else None
 
 
 def run_kernels_only(args):
@@ -394,35 +443,58 @@ def run_ours(args):
         alt = {"krylov": alt_name, "solves_per_s": 1e3 / float(np.mean(talt)), "ms": float(np.mean(talt)),
                "iters": stalt[0]["iters"], "relres": stalt[0]["relres"], "converged": bool(stalt[0]["converged"])}
 
-    # roofline of the dominant kernel and of the stencil, each timed alone on inputs > L2
+    # roofline: per-kernel times of one solve of this workload, measured here with CUDA events
+    # around every launch (helm_profile_*: serialised launches, so shares are the figure), the
+    # dominant kernel by its share of the solve, and each hot kernel timed alone on inputs > L2
     peak, peak_kind = measured_peaks()
+    per, grids = profile_solve(lib, _lib, lambda: step(opts))
+    total_ms = sum(d["ms"] for d in per.values())
+    total_bytes = sum(d["bytes"] for d in per.values())
+    dom = max(per, key=lambda k: per[k]["ms"])
+    dgrid = max((g for g in grids if g["kernel"] == dom), key=lambda g: g["ms"])
+    achieved = per[dom]["bytes"] / (per[dom]["ms"] * 1e-3) / 1e9
     kern = time_kernels(lib, api, _lib, model, float(om[0]))
-    # the largest bandwidth-bound kernel of the timed step: the Gram-Schmidt update of
-    # FGMRES (Arnoldi step 4 of 10), or the x/r update of BiCGSTAB
-    dom = "fg_axpy" if args.krylov == "fgmres" else "bicg_xr"
-    traffic = None
-    prof = os.path.join(ROOT, "profiles", "traffic.json")
-    if os.path.exists(prof):
-        with open(prof) as f:
-            tr = json.load(f).get(dom)
-        # counters taken at the same batch size as this launch configuration
-        if tr and tr.get("nrhs") == kern[dom]["nrhs"]:
-            traffic = tr["traffic"]
-    roof = {"bound": "hbm", "kernel": dom, "achieved": kern[dom]["gbs"], "peak": peak, "unit": "GB/s",
-            "frac": kern[dom]["gbs"] / peak, "traffic": traffic, "peak_kind": f"{peak_kind} burst copy",
-            "bytes_per_launch": kern[dom]["bytes"], "kernels": kern}
-    # shares of the step's device time per kernel, from the committed ncu launch list of this workload
-    shares = os.path.join(ROOT, "profiles", "launch_shares.json")
-    if os.path.exists(shares):
-        with open(shares) as f:
-            roof["time_shares"] = json.load(f)
+    roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "traffic": traffic_for(dom, dgrid["grid"]),
+            "peak_kind": f"{peak_kind} burst copy",
+            "bytes_per_launch": per[dom]["bytes"] / per[dom]["launches"],
+            "ms_per_launch": per[dom]["ms"] / per[dom]["launches"], "launches": per[dom]["launches"],
+            "share": per[dom]["ms"] / total_ms,
+            "how": "one solve of this workload with a CUDA event pair around every launch (helm_profile_*; "
+                   "no graphs, launches serialised); achieved = the kernel's summed algorithmic bytes / summed "
+                   "event time",
+            # the whole solve: algorithmic bytes of every launch over the timed step time
+            "solve_frac": total_bytes / (t_total / args.steps) / 1e9 / peak,
+            "solve_bytes": total_bytes,
+            "shares": {k: {"share": d["ms"] / total_ms, "launches": d["launches"],
+                           "gbs": d["bytes"] / (d["ms"] * 1e-3) / 1e9 if d["ms"] > 0 else None}
+                       for k, d in sorted(per.items(), key=lambda kv: -kv[1]["ms"])},
+            "profiled_ms": total_ms, "kernels_alone": kern}
 
     cpu = None
+    err = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline and not args.density:
-        t_fac, ts = oracle_c2_timing(1)
+        t_fac, ts, U = oracle_c2_timing(1, want_field=True)
+        U = np.asarray(U).reshape(u_host.shape)
         cpu = {"value": 1.0 / (t_fac + ts[0]), "unit": "solves/s", "cores": 1, "kind": "oracle",
                "sample": "one full solve of the same problem: SuperLU factorisation + triangular solve "
                          "(single-threaded)", "factor_s": t_fac, "solve_s": ts[0]}
+        # each result's error against the FP64 oracle: the timed configuration's wavefield (the e2e
+        # leg's output, the same solve) and a complex64-only solve of the same problem
+        p = slice(mdl.npml, -mdl.npml)
+
+        def rel(a, b):
+            return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+        # complex64 only: one BiCGSTAB solve with no FP64 refinement (FGMRES restarts through the
+        # FP64 residual, so it has no complex64-only mode)
+        o32 = api.helm_default_opts(tol=1e-6, precision="fp32", krylov=_lib.HELM_KRYLOV_BICGSTAB, max_it=20000)
+        u32, st32, status32 = api.helm_solve(model, om, f=f_host, opts=o32)
+        err = {"rel_l2": rel(u_host, U), "rel_l2_physical": rel(u_host[0][p, p], U[0][p, p]),
+               "complex64_only": {"krylov": "BiCGSTAB", "rel_l2": rel(u32, U), "relres": st32[0]["relres"], "iters": st32[0]["iters"],
+                                  "converged": bool(st32[0]["converged"]), "bar": 1e-4},
+               "note": "the timed solve stops at relres 1e-6, so its error is about cond(B) x 1e-6; the parity "
+                       "tests solve to 1e-10 and meet 1e-6"}
 
     if rank == 0:
         line = {
@@ -435,18 +507,21 @@ def run_ours(args):
                        "krylov": ("BiCGSTAB" if args.krylov == "bicgstab" else
                                   f"FGMRES({args.restart}, {GS_NAME[args.reorth]})") +
                                  " + shifted-Laplace Galerkin MG (V-cycle above the first level where k h of the "
-                                 "shortest wavelength reaches 0.7, F-cycle from there), beta=(1,0.5)",
+                                 "shortest wavelength reaches 0.7, F-cycle from there; the first level with at most "
+                                 "1200 nodes solved by its dense inverse), beta=(1,0.5)",
                        "inner_tol": args.inner_tol, "restart": args.restart if args.krylov == "fgmres" else None,
                        "levels": model.nlevels, "l2": "flushed between timed steps (258 MB write)",
                        "parallelism": f"replicas x{world}"},
             "p50_ms": float(np.percentile(ms, 50)), "p99_ms": float(np.percentile(ms, 99)),
             "iters": stats_all[-1]["iters"], "outer_its": stats_all[-1]["outer_its"],
+            "dense_level": stats_all[-1]["dense_level"],
             "relres": stats_all[-1]["relres"], "converged": conv,
             "fp64_plain": fp64, "other_krylov": alt,
             "speedup_vs_fp64": (value / world) / fp64["solves_per_s"] if fp64 else None,
             "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": int(f_host.nbytes),
                     "d2h_bytes_per_step": int(u_host.nbytes), "ms": float(np.mean(e2e_ms))},
             "roofline": roof, "clocks": clocks, "gpu_launches": int(launches), "cpu_baseline": cpu,
+            "err_vs_oracle": err,
         }
         print(json.dumps(line), flush=True)
     model.close()
@@ -640,7 +715,7 @@ def run_ablation(args):
             rows.append({"f_hz": f_hz, "preconditioner": name, "iters": st[0]["iters"], "ms": 1e3 * dt,
                          "converged": bool(st[0]["converged"]), "relres": st[0]["relres"]})
     print(json.dumps({"metric": "krylov_iterations", "workload": "ablation_401x201_1src_3-7Hz",
-                      "krylov": args.krylov, "shift": [1.0, args.serve_beta2], "rows": rows}), flush=True)
+                      "krylov": args.krylov, "rows": rows}), flush=True)
     model.close()
     ctx.close()
 
@@ -659,10 +734,10 @@ def run_serving(args):
     sizes = tuple(int(x) for x in args.serve_sizes.split(","))
     reqs = [models.c5_request(i, sizes=sizes) for i in range(args.requests)]
     kry = _lib.HELM_KRYLOV_FGMRES if args.krylov == "fgmres" else _lib.HELM_KRYLOV_BICGSTAB
-    opts = dict(tol=1e-6, precision="mixed", krylov=kry, max_it=20000, reorth=REORTH[args.reorth],
-                beta2=args.serve_beta2)
+    shift = {} if args.serve_beta2 is None else dict(beta2=args.serve_beta2)
+    opts = dict(tol=1e-6, precision="mixed", krylov=kry, max_it=20000, reorth=REORTH[args.reorth], **shift)
     # sequential plain FP64 on a subset
-    o64 = dict(tol=1e-6, precision="fp64", max_it=20000, beta2=args.serve_beta2)
+    o64 = dict(tol=1e-6, precision="fp64", max_it=20000, **shift)
     t_seq = []
     for r in reqs[: min(8, len(reqs))]:
         mm = api.helm_create_model(ctx, r.slowness, r.h)
@@ -684,7 +759,7 @@ def run_serving(args):
     t_total = time.perf_counter() - t_start
     lat = [x.latency_ms for x in res]
     print(json.dumps({"metric": "helmholtz_solves_per_s", "workload": f"serving_{len(reqs)}req_{min(sizes)}-{max(sizes)}",
-                      "krylov": args.krylov, "shift": [1.0, args.serve_beta2],
+                      "krylov": args.krylov, "shift": [1.0, args.serve_beta2 if args.serve_beta2 is not None else 0.5],
                       "value": len(reqs) / t_total, "unit": "solves/s", "p50_ms": float(np.percentile(lat, 50)),
                       "p99_ms": float(np.percentile(lat, 99)), "arrival_rate": rate,
                       "sequential_fp64_solves_per_s": seq_rate,

@@ -84,6 +84,18 @@ typedef enum { HELM_PRECOND_MG = 0, HELM_PRECOND_NONE = 1 } helm_precond;
  * where the basis loses orthogonality within a cycle. */
 typedef enum { HELM_REORTH_ALWAYS = 0, HELM_REORTH_NEVER = 1, HELM_REORTH_IFNEEDED = 2 } helm_reorth;
 
+/* Coarse end of the multigrid cycle. HELM_COARSE_AUTO solves the first level
+ * with at most 1200 nodes exactly, by its dense inverse (computed once per solve
+ * for each distinct model and frequency by block Gauss-Jordan, then applied by a
+ * matrix-vector kernel); it needs beta2 != 0, which keeps every pivot away from
+ * zero, and falls back to HELM_COARSE_TAIL otherwise. HELM_COARSE_TAIL runs the
+ * levels from the first with at most 2048 (complex64) or 1024 (complex128) nodes
+ * down to the coarsest as an F- or V-cycle in one block per right-hand side, in
+ * shared memory, with a dense solve of the coarsest level only. Both are one
+ * reading of "approximately invert the shifted Laplacian" (the paragraph after
+ * Eq. 9); they change the iteration count, not the answer. */
+typedef enum { HELM_COARSE_AUTO = 0, HELM_COARSE_TAIL = 1 } helm_coarse;
+
 typedef struct {
     double tol;          /* stop at ||f - B u||_2 / ||f||_2 <= tol, residual formed in FP64 */
     int max_it;          /* cap on preconditioned Krylov iterations per right-hand side */
@@ -100,6 +112,7 @@ typedef struct {
     int use_graphs;      /* 1: replay the iteration body as a CUDA graph */
     int precond;         /* helm_precond: the shifted-Laplace multigrid (default) or none (ablation) */
     int reorth;          /* helm_reorth: FGMRES Gram-Schmidt passes (default HELM_REORTH_ALWAYS) */
+    int coarse;          /* helm_coarse: coarse end of the multigrid cycle (default HELM_COARSE_AUTO) */
 } helm_solve_opts;
 
 typedef struct {
@@ -107,12 +120,14 @@ typedef struct {
     int outer_its;    /* FP64 refinement steps */
     int converged;    /* 1 if relres <= tol */
     double relres;    /* final ||f - B u|| / ||f||, computed in FP64 */
+    int dense_level;  /* multigrid level solved by its dense inverse (0: the shared-memory tail ran) */
+    int shift_switched; /* 1 if the solve stalled and continued with the shift (1, 1) (see helm_solve) */
 } helm_solve_stats;
 
 /* Fills *opts with the defaults: tol 1e-6, max_it 5000, BiCGSTAB, restart 30,
  * mixed precision, beta = (1, 0.5), omega_jacobi 0.5, inner_tol 1e-2,
  * max_outer 20, check_every 10, host pointers, graphs on, multigrid preconditioner,
- * two Gram-Schmidt passes. */
+ * two Gram-Schmidt passes, HELM_COARSE_AUTO. */
 void helm_default_opts(helm_solve_opts* opts);
 
 const char* helm_strerror(int status);
@@ -160,7 +175,12 @@ int helm_model_info(const helm_model* model, int* nx, int* nz, int* nlevels);
  * (src_ix[k], src_iz[k]); otherwise f is c128 [nrhs][nz][nx] (src_* ignored).
  * u_out: c128 [nrhs][nz][nx] on the padded grid. opts NULL = defaults.
  * stats (nullable): [nrhs]. Returns HELM_E_NOT_CONVERGED if any right-hand side
- * missed tol (u_out then holds the best iterate). */
+ * missed tol (u_out then holds the best iterate).
+ * Stall guard: with the multigrid preconditioner and a shift other than (1, 1),
+ * a right-hand side whose FP64 residual has not halved within 300 Krylov
+ * iterations (while above tol) makes the whole batch continue with the
+ * paper's shift (1, 1) (stats[k].shift_switched = 1); BiCGSTAB applies the same
+ * test to its recursive residual within each inner solve. */
 int helm_solve(helm_model* model, int nrhs, const double* omega, const int* src_ix,
                const int* src_iz, const void* f, void* u_out, const helm_solve_opts* opts,
                helm_solve_stats* stats);
@@ -276,6 +296,12 @@ int helm_apply(helm_model* model, int nrhs, const double* omega, int precision, 
 int helm_vcycle(helm_model* model, int nrhs, const double* omega, double beta1, double beta2,
                 double omega_jacobi, const void* r, void* z, int device_ptrs);
 
+/* helm_vcycle with the preconditioner options of a solve: beta1, beta2,
+ * omega_jacobi, coarse and device_ptrs are taken from *opts (NULL = defaults);
+ * helm_vcycle is this call with the defaults' coarse setting. */
+int helm_vcycle_ex(helm_model* model, int nrhs, const double* omega, const helm_solve_opts* opts, const void* r,
+                   void* z);
+
 /* Bandwidth measurement of one hot-path kernel (no counterpart in the paper;
  * it feeds the roofline report). Launches `kernel` (helm_kernel_id) `reps`
  * times on library-owned zero-filled vectors of nrhs right-hand sides of this
@@ -299,6 +325,27 @@ typedef enum {
 } helm_kernel_id;
 int helm_time_kernel(helm_model* model, int kernel, int nrhs, double omega, int reps, double* ms_per_launch,
                      double* bytes_per_launch);
+
+/* Per-kernel profile of this library's launches (no counterpart in the paper;
+ * it feeds the roofline report). Between helm_profile_begin() and
+ * helm_profile_end() every kernel the library launches, from any thread, is
+ * timed with a CUDA event pair on its stream, and solves run without CUDA
+ * graphs; the events also keep consecutive launches from overlapping, so the
+ * durations are those of serialised launches. helm_profile_end synchronises on
+ * the recorded events and writes one entry per (kernel, grid) to out (at most
+ * cap; *n_out = the number of entries there are): launches, total ms and the
+ * total algorithmic bytes (each operand read or written once, model data
+ * shared by a batch counted once). Profiling adds host work per launch; do not
+ * time a workload while a session is open. */
+typedef struct {
+    char name[32];       /* kernel, e.g. "k_restrict_g" */
+    int nx, nz;          /* the grid it works on (fine grid of a level transfer; n x 1 for vectors) */
+    uint64_t launches;
+    double ms;           /* summed event time */
+    double bytes;        /* summed algorithmic bytes */
+} helm_profile_entry;
+int helm_profile_begin(void);
+int helm_profile_end(helm_profile_entry* out, int cap, int* n_out);
 
 /* helm_vcycle for callers that cannot allocate device memory (no counterpart in
  * the paper). helm_vcycle allocates its level vectors and the coarsest-level
@@ -360,7 +407,10 @@ typedef struct {
 
 /* Starts the scheduler (first call) and enqueues a request; *ticket names it. */
 int helm_submit(helm_ctx* ctx, const helm_request* req, uint64_t* ticket);
-/* Waits up to timeout_ms (0 = just look, < 0 = forever) for a request.
+/* Waits up to timeout_ms (0 = just look) for a request. A negative timeout waits
+ * on the host (a condition variable; no GPU work waits) until the request has
+ * finished, which every request does: its solve is bounded by max_it and
+ * max_outer, and an admission refusal finishes it with HELM_E_NOMEM.
  * HELM_OK fills *result; HELM_PENDING / HELM_E_TIMEOUT leave it untouched. */
 int helm_poll(helm_ctx* ctx, uint64_t ticket, int timeout_ms, helm_result* result);
 /* Frees a finished request's result. */

@@ -21,6 +21,9 @@ implements, is one multigrid cycle per application:
   guess) and one after each coarse correction.
 * Cycle: a V-cycle on the levels above lf; from lf down, an F-cycle whose
   second coarse correction is a V-cycle; the coarsest level is solved exactly.
+  With coarse="dense" (the library's default when beta2 != 0) the first level
+  l >= 1 with at most 1200 nodes is solved exactly instead, and the cycle does
+  not descend below it; coarse="tail" keeps the full hierarchy.
   lf (>= 1) is the first level whose spacing 2^l h gives k h >= 0.7 for the
   shortest wavelength (h omega 2^l m_max >= 0.7: fewer than about 9 nodes per
   wavelength), and no later than the first level with at most 24576 nodes.
@@ -37,6 +40,7 @@ import scipy.sparse.linalg as spla
 
 COARSE_MAX = 128
 TAIL_MAX = 24576
+DENSE_MAX = 1200
 
 
 def level_shapes(nx: int, nz: int):
@@ -125,7 +129,8 @@ def fcycle_level(shapes, hw2: float, m_max: float) -> int:
 class VCycle:
     """One preconditioner application approximating M^{-1} for grid-scaled (h omega)^2 = hw2."""
 
-    def __init__(self, m2_pad: np.ndarray, hw2: float, beta=(1.0, 0.5), omega_jacobi: float = 0.5, rho_pad=None):
+    def __init__(self, m2_pad: np.ndarray, hw2: float, beta=(1.0, 0.5), omega_jacobi: float = 0.5, rho_pad=None,
+                 coarse: str = "dense"):
         nz, nx = m2_pad.shape
         self.wj = omega_jacobi
         bt = complex(beta[0], -beta[1])
@@ -137,11 +142,18 @@ class VCycle:
             P = prolongation(lx, lz)
             self.P.append(P)
             self.M.append((P.T @ self.M[-1] @ P).tocsr())
-        self.coarse = spla.splu(sp.csc_matrix(self.M[-1]))
+        # the level solved exactly: the coarsest, or (coarse="dense", beta2 != 0) the first
+        # level l >= 1 with at most DENSE_MAX nodes
+        self.exact = len(self.M) - 1
+        if coarse == "dense" and beta[1] != 0:
+            self.exact = next(l for l in range(1, len(self.shapes)) if self.shapes[l][0] * self.shapes[l][1] <= DENSE_MAX)
+        elif coarse not in ("dense", "tail"):
+            raise ValueError(coarse)
+        self.coarse = spla.splu(sp.csc_matrix(self.M[self.exact]))
 
     def cycle(self, f: np.ndarray, level: int, kind: str) -> np.ndarray:
         """kind 'V' or 'F' from `level` with a zero initial guess."""
-        if level == len(self.M) - 1:
+        if level == self.exact:
             return self.coarse.solve(f)
         M, P = self.M[level], self.P[level]
         D = M.diagonal()

@@ -27,6 +27,8 @@ HELM_PRECOND_NONE = 1
 HELM_REORTH_ALWAYS = 0
 HELM_REORTH_NEVER = 1
 HELM_REORTH_IFNEEDED = 2
+HELM_COARSE_AUTO = 0
+HELM_COARSE_TAIL = 1
 HELM_KERNEL_APPLY = 0
 HELM_KERNEL_RESTRICT = 1
 HELM_KERNEL_PROLONG = 2
@@ -60,6 +62,7 @@ class helm_solve_opts(C.Structure):
         ("use_graphs", C.c_int),
         ("precond", C.c_int),
         ("reorth", C.c_int),
+        ("coarse", C.c_int),
     ]
 
 
@@ -84,6 +87,8 @@ class helm_solve_stats(C.Structure):
         ("outer_its", C.c_int),
         ("converged", C.c_int),
         ("relres", C.c_double),
+        ("dense_level", C.c_int),
+        ("shift_switched", C.c_int),
     ]
 
 
@@ -112,6 +117,17 @@ class helm_result(C.Structure):
         ("latency_ms", C.c_double),
         ("queue_ms", C.c_double),
         ("batch_size", C.c_int),
+    ]
+
+
+class helm_profile_entry(C.Structure):
+    _fields_ = [
+        ("name", C.c_char * 32),
+        ("nx", C.c_int),
+        ("nz", C.c_int),
+        ("launches", C.c_uint64),
+        ("ms", C.c_double),
+        ("bytes", C.c_double),
     ]
 
 
@@ -147,6 +163,9 @@ SIGNATURES = {
     "helm_apply": (_I, [_P, _I, _pD, _I, _P, _P, _I]),
     "helm_vcycle": (_I, [_P, _I, _pD, _D, _D, _D, _P, _P, _I]),
     "helm_vcycle_noalloc": (_I, [_P, _I, _pD, _D, _D, _D, _P, _P]),
+    "helm_vcycle_ex": (_I, [_P, _I, _pD, _pOpts, _P, _P]),
+    "helm_profile_begin": (_I, []),
+    "helm_profile_end": (_I, [C.POINTER(helm_profile_entry), _I, _pI]),
     "helm_autotune": (_I, [_P, _I, _D, _pI]),
     "helm_set_tiles": (_I, [_P, _pI]),
     "helm_time_kernel": (_I, [_P, _I, _I, _D, _I, _pD, _pD]),

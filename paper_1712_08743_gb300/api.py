@@ -69,7 +69,8 @@ def _opts(opts, **extra) -> _lib.helm_solve_opts:
 
 def stats_list(arr, n):
     return [dict(iters=arr[i].iters, outer_its=arr[i].outer_its, converged=bool(arr[i].converged),
-                 relres=arr[i].relres) for i in range(n)]
+                 relres=arr[i].relres, dense_level=arr[i].dense_level, shift_switched=bool(arr[i].shift_switched))
+            for i in range(n)]
 
 
 # ------------------------------------------------------------------ context
@@ -222,21 +223,30 @@ def helm_apply(model: Model, omega, u, precision: int = _lib.HELM_PREC_FP64, y=N
     return y
 
 
-def helm_vcycle(model: Model, omega, r, beta=(1.0, 0.5), omega_jacobi: float = 0.8):
-    """One V-cycle z ~ M^{-1} r of the shifted-Laplace preconditioner, complex64."""
+def helm_vcycle(model: Model, omega, r, beta=(1.0, 0.5), omega_jacobi: float = 0.8, coarse=None):
+    """One cycle z ~ M^{-1} r of the shifted-Laplace preconditioner, complex64.
+
+    coarse=None calls helm_vcycle (the default coarse end); otherwise helm_vcycle_ex
+    with opts.coarse = coarse (HELM_COARSE_AUTO or HELM_COARSE_TAIL)."""
     lib = model.lib
     om = _np(omega, np.float64).reshape(-1)
     nrhs = om.size
-    if _is_cuda_tensor(r):
+    dev = _is_cuda_tensor(r)
+    if dev:
         z = torch.empty_like(r)
         torch.cuda.synchronize()
-        st = lib.helm_vcycle(model.handle, nrhs, _ptr_d(om), float(beta[0]), float(beta[1]), float(omega_jacobi),
-                             C.c_void_p(r.data_ptr()), C.c_void_p(z.data_ptr()), 1)
+        rp, zp = C.c_void_p(r.data_ptr()), C.c_void_p(z.data_ptr())
     else:
         ra = _np(r, np.complex64)
         z = np.empty_like(ra)
+        rp, zp = C.c_void_p(ra.ctypes.data), C.c_void_p(z.ctypes.data)
+    if coarse is None:
         st = lib.helm_vcycle(model.handle, nrhs, _ptr_d(om), float(beta[0]), float(beta[1]), float(omega_jacobi),
-                             C.c_void_p(ra.ctypes.data), C.c_void_p(z.ctypes.data), 0)
+                             rp, zp, 1 if dev else 0)
+    else:
+        o = helm_default_opts(beta=beta, omega_jacobi=float(omega_jacobi), coarse=int(coarse),
+                              device_ptrs=1 if dev else 0)
+        st = lib.helm_vcycle_ex(model.handle, nrhs, _ptr_d(om), C.byref(o), rp, zp)
     check(st, "helm_vcycle")
     return z
 
@@ -436,7 +446,8 @@ def helm_poll(ctx: Context, ticket: int, timeout_ms: int = -1):
         u = np.frombuffer(buf, dtype=np.complex128, count=n).reshape(res.nz, res.nx).copy()
     s = res.stats
     return ServedResult(u, res.status, dict(iters=s.iters, outer_its=s.outer_its, converged=bool(s.converged),
-                                            relres=s.relres), res.latency_ms, res.queue_ms, res.batch_size)
+                                            relres=s.relres, dense_level=s.dense_level,
+                                            shift_switched=bool(s.shift_switched)), res.latency_ms, res.queue_ms, res.batch_size)
 
 
 def helm_release(ctx: Context, ticket: int) -> int:

@@ -11,6 +11,7 @@ from dataclasses import dataclass, field
 
 import numpy as np
 import torch
+from torch.autograd.function import once_differentiable
 
 from . import api
 
@@ -30,8 +31,16 @@ class FWIProblem:
 
 
 class HelmFWI(torch.autograd.Function):
+    """J(m) with one backward: the forward keeps the wavefields and data residuals on
+    the device (a library FwiState), the backward consumes them with the adjoint
+    solves and releases them. A second backward through the same graph raises; a
+    forward whose graph is dropped without a backward frees its state when the
+    autograd context is collected (FwiState and Model close themselves)."""
+
     @staticmethod
     def forward(ctx, m: torch.Tensor, problem: FWIProblem):
+        # the model build (padding, multigrid hierarchy, Galerkin operators) runs on the device
+        # from a host copy of the physical slowness, which helm_create_model validates
         slow = m.detach().to("cpu", torch.float64).contiguous().numpy()
         model = api.helm_create_model(problem.ctx, slow, problem.h, problem.npml, problem.alpha_max)
         J, d_cal, state, stats, status = api.helm_fwi_forward(model, problem.omegas, problem.src, problem.rec,
@@ -41,9 +50,18 @@ class HelmFWI(torch.autograd.Function):
         return torch.tensor(J, dtype=torch.float64, device=m.device)
 
     @staticmethod
+    @once_differentiable
     def backward(ctx, grad_J):
-        g, status = api.helm_fwi_backward(ctx.model, ctx.state, ctx.problem.opts)
+        if ctx.state is None:
+            raise RuntimeError("HelmFWI: backward ran already; its device state was released "
+                               "(call forward again for another gradient)")
+        if grad_J.is_cuda:
+            # the library writes the gradient straight into a device tensor (device_ptrs)
+            g = torch.empty((ctx.model.Pz, ctx.model.Px), dtype=torch.float64, device=grad_J.device)
+            api.helm_fwi_backward(ctx.model, ctx.state, ctx.problem.opts, grad_out=g)
+        else:
+            g = torch.from_numpy(api.helm_fwi_backward(ctx.model, ctx.state, ctx.problem.opts)[0])
         ctx.state.close()
         ctx.model.close()
-        grad = torch.from_numpy(g).to(grad_J.device)
-        return grad_J * grad, None
+        ctx.state = None
+        return grad_J * g, None

@@ -46,6 +46,7 @@ int check_opts(const helm_solve_opts& o) {
     if (!(o.inner_tol > 0.0) || o.inner_tol >= 1.0) return HELM_E_INVALID;
     if (o.precond != HELM_PRECOND_MG && o.precond != HELM_PRECOND_NONE) return HELM_E_INVALID;
     if (o.reorth < HELM_REORTH_ALWAYS || o.reorth > HELM_REORTH_IFNEEDED) return HELM_E_INVALID;
+    if (o.coarse != HELM_COARSE_AUTO && o.coarse != HELM_COARSE_TAIL) return HELM_E_INVALID;
     return HELM_OK;
 }
 
@@ -97,6 +98,8 @@ int create_model(helm_ctx* ctx, cudaStream_t s, int Px, int Pz, double h, const 
     m->lf = L;
     for (int l = 1; l <= L; ++l)
         if (m->lv[l].n() <= (size_t)kFcycleMaxPoints) { m->lf = l; break; }
+    for (int l = 1; l <= L; ++l)
+        if (m->lv[l].n() <= (size_t)kDenseMaxPoints) { m->ld = l; break; }
     for (size_t i = 0; i < np * (size_t)nmodels; ++i) m->m_max = std::max(m->m_max, slowness[i]);
     for (int d = 0; d < 2; ++d) {
         const size_t cap = d ? (size_t)kTailMaxPoints64 : (size_t)kTailMaxPoints32;
@@ -189,6 +192,7 @@ void helm_default_opts(helm_solve_opts* o) {
     o->check_every = 10;
     o->device_ptrs = 0;
     o->use_graphs = 1;
+    o->coarse = HELM_COARSE_AUTO;
 }
 
 const char* helm_strerror(int st) {
@@ -404,10 +408,12 @@ int helm_set_tiles(helm_model* m, const int* tiles) {
     return HELM_OK;
 }
 
-int helm_vcycle(helm_model* m, int nrhs, const double* omega, double beta1, double beta2, double omega_jacobi,
-                const void* r, void* z, int device_ptrs) {
+namespace {
+int vcycle_call(helm_model* m, int nrhs, const double* omega, double beta1, double beta2, double omega_jacobi,
+                int coarse, const void* r, void* z, int device_ptrs) {
     if (!m || nrhs < 1 || !omega || !r || !z) return HELM_E_INVALID;
     if (!std::isfinite(beta1) || !std::isfinite(beta2) || !(omega_jacobi > 0.0)) return HELM_E_INVALID;
+    if (coarse != HELM_COARSE_AUTO && coarse != HELM_COARSE_TAIL) return HELM_E_INVALID;
     std::vector<double> w2(nrhs);
     for (int b = 0; b < nrhs; ++b) {
         if (!finite_pos(omega[b])) return HELM_E_INVALID;
@@ -428,12 +434,27 @@ int helm_vcycle(helm_model* m, int nrhs, const double* omega, double beta1, doub
         rp = dr.p;
         zp = dz.p;
     }
-    int rc = vcycle_once(m, s, nrhs, w2.data(), beta1, beta2, omega_jacobi, static_cast<const float*>(rp),
+    int rc = vcycle_once(m, s, nrhs, w2.data(), beta1, beta2, omega_jacobi, coarse, static_cast<const float*>(rp),
                          static_cast<float*>(zp));
     if (rc != HELM_OK) return rc;
     if (!device_ptrs) HELM_CUDA_TRY(cudaMemcpyAsync(z, zp, bytes, cudaMemcpyDeviceToHost, s));
     HELM_CUDA_TRY(cudaStreamSynchronize(s));
     return HELM_OK;
+}
+}  // namespace
+
+int helm_vcycle(helm_model* m, int nrhs, const double* omega, double beta1, double beta2, double omega_jacobi,
+                const void* r, void* z, int device_ptrs) {
+    helm_solve_opts d;
+    helm_default_opts(&d);
+    return vcycle_call(m, nrhs, omega, beta1, beta2, omega_jacobi, d.coarse, r, z, device_ptrs);
+}
+
+int helm_vcycle_ex(helm_model* m, int nrhs, const double* omega, const helm_solve_opts* opts, const void* r,
+                   void* z) {
+    helm_solve_opts o;
+    if (opts) o = *opts; else helm_default_opts(&o);
+    return vcycle_call(m, nrhs, omega, o.beta1, o.beta2, o.omega_jacobi, o.coarse, r, z, o.device_ptrs);
 }
 
 int helm_fwi_forward(helm_model* m, int nfreq, const double* omega, int nshot, const int* src_ix, const int* src_iz,

@@ -98,6 +98,9 @@ struct RhsState {
     unsigned int counter[4];  // last-block election counters, one per reduction site
 };
 
+// A right-hand side takes part in a kernel while its state says so (no state: always).
+__device__ __forceinline__ bool rhs_active(const RhsState* st, int b) { return st == nullptr || st[b].active; }
+
 // ------------------------------------------------ programmatic dependent launch
 // Kernels of the iteration chain let the next kernel start launching at once
 // (its blocks then wait in pdl_wait until this grid has completed and its

@@ -27,12 +27,13 @@ constexpr int kFgMaxBlocks = 1024;                                 // blocks per
 // one wave of the kernel's resident blocks on every SM.
 template <auto Kernel>
 int fg_grid(size_t n) {
-    static int per_sm = 0;
-    if (per_sm == 0) {
+    // resident blocks per SM of this kernel, looked up once (a function-local static is
+    // initialised exactly once even when serving threads get here together)
+    static const int per_sm = [] {
         int nb = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, Kernel, 256, 0);
-        per_sm = nb > 0 ? nb : 1;
-    }
+        return nb > 0 ? nb : 1;
+    }();
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -450,10 +451,12 @@ __global__ void k_fg_update(const T* __restrict__ Z, size_t zstride, T* __restri
 template <typename T>
 void launch_fg_norm(const T* rin, double* partials, int pstride, RhsState* st, const FgDev& fg, int* nactive,
                     size_t n, int nrhs, cudaStream_t s) {
+    ProfScope prof(PK_FG_NORM, (int)n, 1, (double)n * nrhs * 2.0 * sizeof(T), s);
     k_fg_norm<T><<<dim3(fg_grid<k_fg_norm<T>>(n), 1, nrhs), 256, 0, s>>>(rin, partials, pstride, st, fg, nactive, n);
 }
 template <typename T>
 void launch_fg_scale(const T* rin, T* v, const RhsState* st, const FgDev& fg, size_t n, int nrhs, cudaStream_t s) {
+    ProfScope prof(PK_FG_SCALE, (int)n, 1, (double)n * nrhs * 4.0 * sizeof(T), s);
     k_fg_scale<T><<<dim3(fg_grid<k_fg_scale<T>>(n), 1, nrhs), 256, 0, s>>>(rin, v, st, fg, n);
 }
 template <typename T, int NV>
@@ -466,6 +469,8 @@ static void fg_dots_nv(const T* V, size_t vstride, const T* w, int j, int add, i
 template <typename T>
 void launch_fg_dots(const T* V, size_t vstride, const T* w, int j, int add, int wnorm, int check, double* partials,
                     int pstride, RhsState* st, const FgDev& fg, size_t n, int nrhs, cudaStream_t s) {
+    // reads w and the basis vectors V'_0 .. V'_j
+    ProfScope prof(PK_FG_DOTS, (int)n, 1, (double)n * nrhs * 2.0 * sizeof(T) * (j + 2), s);
     if (j < 1) fg_dots_nv<T, 1>(V, vstride, w, j, add, wnorm, check, partials, pstride, st, fg, n, nrhs, s);
     else if (j < 2) fg_dots_nv<T, 2>(V, vstride, w, j, add, wnorm, check, partials, pstride, st, fg, n, nrhs, s);
     else if (j < 4) fg_dots_nv<T, 4>(V, vstride, w, j, add, wnorm, check, partials, pstride, st, fg, n, nrhs, s);
@@ -482,6 +487,8 @@ static int fg_axpy_nv(const T* V, size_t vstride, T* w, int j, int mode, int che
 template <typename T>
 int launch_fg_axpy(const T* V, size_t vstride, T* w, int j, int mode, int check, double* partials, int pstride,
                    RhsState* st, const FgDev& fg, int* nactive, size_t n, int nrhs, cudaStream_t s) {
+    // reads V'_0 .. V'_j and w, writes w
+    ProfScope prof(PK_FG_AXPY, (int)n, 1, (double)n * nrhs * 2.0 * sizeof(T) * (j + 3), s);
     if (j < 1) return fg_axpy_nv<T, 1>(V, vstride, w, j, mode, check, partials, pstride, st, fg, nactive, n, nrhs, s);
     if (j < 2) return fg_axpy_nv<T, 2>(V, vstride, w, j, mode, check, partials, pstride, st, fg, nactive, n, nrhs, s);
     if (j < 4) return fg_axpy_nv<T, 4>(V, vstride, w, j, mode, check, partials, pstride, st, fg, nactive, n, nrhs, s);
@@ -489,15 +496,19 @@ int launch_fg_axpy(const T* V, size_t vstride, T* w, int j, int mode, int check,
 }
 void launch_fg_finish(const double* partials, int pstride, int nblk, RhsState* st, const FgDev& fg, int j,
                       int* nactive, int nrhs, cudaStream_t s) {
+    ProfScope prof(PK_FG_FINISH, nblk, 1, (double)nblk * nrhs * 8.0 * 2, s);
     k_fg_finish<<<nrhs, 256, 0, s>>>(partials, pstride, nblk, st, fg, j, nactive);
 }
 void launch_fg_backsolve(const RhsState* st, const FgDev& fg, int nrhs, cudaStream_t s) {
+    ProfScope prof(PK_FG_BACKSOLVE, fg.m, 1, (double)fg.m * fg.m * nrhs * 16.0, s);
     const size_t smem = sizeof(double2) * ((size_t)fg.m * fg.m + fg.m);
     k_fg_backsolve<<<nrhs, 32, smem, s>>>(st, fg);
 }
 template <typename T>
 void launch_fg_update(const T* Z, size_t zstride, T* x, const RhsState* st, const FgDev& fg, size_t n, int nrhs,
                       cudaStream_t s) {
+    // reads Z'_0 .. Z'_{m-1}, reads and writes x
+    ProfScope prof(PK_FG_UPDATE, (int)n, 1, (double)n * nrhs * 2.0 * sizeof(T) * (fg.m + 2), s);
     k_fg_update<T><<<dim3(fg_grid<k_fg_update<T>>(n), 1, nrhs), 256, 0, s>>>(Z, zstride, x, st, fg, n);
 }
 

@@ -10,6 +10,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "helm.h"
 #include "helm_common.cuh"
 
@@ -24,7 +26,10 @@ constexpr int kTailMaxPoints32 = 2048;
 constexpr int kTailMaxPoints64 = 1024;
 constexpr int kMaxLevels = 24;
 constexpr int kMaxRestart = 32;
-constexpr int kGalerkinCoefs = 10;      // per coarse node: G (c, e, n, ne, nw) then K (c, e, n, ne, nw)
+constexpr int kGalerkinCoefs = 10;
+// the first level with at most this many nodes is solved exactly by its dense inverse
+// (few right-hand sides; see helm_dense.cu)
+constexpr int kDenseMaxPoints = 1200;      // per coarse node: G (c, e, n, ne, nw) then K (c, e, n, ne, nw)
 
 // One multigrid level as the kernels see it. The finest level carries the
 // squared slowness m2 and the 5-point operator; every coarser level carries
@@ -79,6 +84,7 @@ struct helm_model {
     int nmodels = 1;                      // > 1: one slowness model per right-hand side (serving batches)
     bool vd = false;                      // variable density (Eq. 1): the finest level is a stored 9-point level
     int lf = 1;                           // first level with at most kFcycleMaxPoints nodes (latest F-cycle start)
+    int ld = 0;                           // first level (>= 1) with at most kDenseMaxPoints nodes (0: none)
     double m_max = 0;                     // largest slowness of the model(s): the shortest wavelength
     // Per precision (0: complex64, 1: complex128): first level handled by the
     // shared-memory tail kernel (>= lf), its F- and V-cycle schedules on the
@@ -100,6 +106,56 @@ struct helm_model {
 };
 
 namespace helm {
+
+// Launch with programmatic stream serialization (the kernel must call pdl_wait
+// before reading anything an earlier kernel of the stream writes).
+template <typename... KArgs, typename... Args>
+void launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
+// NVTX range over a scope (a named span on a profiler's host timeline: a solve,
+// a refinement step, an iteration chunk, a multigrid level visit); free when no
+// profiler is attached.
+class NvtxRange {
+  public:
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
+
+// Per-kernel timing of this library's launches (helm_profile.cu): while a
+// profiling session runs, a ProfScope records CUDA events around the launch in
+// its scope, with the kernel class, the grid and the launch's algorithmic bytes.
+enum ProfKernel : int {
+    PK_APPLY, PK_APPLY_DOTS, PK_RESID64, PK_REFINE, PK_BICG_INIT, PK_BICG_RESUME, PK_BICG_P, PK_BICG_S, PK_BICG_XR,
+    PK_RESTRICT, PK_PROLONG, PK_RESTRICT_G, PK_CORRECT_RESTRICT, PK_PROLONG_G, PK_TAIL, PK_COARSE_DENSE,
+    PK_DENSE_INVERT, PK_COARSE_INVERT, PK_FG_NORM, PK_FG_SCALE, PK_FG_DOTS, PK_FG_AXPY, PK_FG_FINISH,
+    PK_FG_BACKSOLVE, PK_FG_UPDATE, PK_OTHER, PK_COUNT
+};
+bool prof_on();
+class ProfScope {
+  public:
+    ProfScope(int kid, int nx, int nz, double bytes, cudaStream_t s);
+    ~ProfScope();
+    ProfScope(const ProfScope&) = delete;
+    ProfScope& operator=(const ProfScope&) = delete;
+
+  private:
+    cudaStream_t s_ = nullptr;
+    int idx_ = -1;
+};
 
 // Error helpers -----------------------------------------------------------
 #define HELM_CUDA_TRY(expr)                                   \
@@ -219,6 +275,19 @@ void launch_prolong(int mode, const LevelDev& Lf, const LevelDev& Lc, int npml, 
 template <typename T>
 void launch_coarse(int n, const T* minv, const int* slot, const T* fL, T* eL, const RhsState* st,
                    int nrhs, cudaStream_t s);
+// Dense exact solve of one coarse level (helm_dense.cu). dense_invert_plan
+// returns 1 and the strip width / slots per cooperative launch when an n-node
+// level can be inverted, 0 otherwise.
+int dense_invert_plan(int n, bool dbl, int* W, int* per_launch_slots);
+template <typename T>
+cudaError_t launch_dense_invert(const LevelDev& Ld, const double* w2s, const int* mods, int nslots, double b1,
+                                double b2, int W, int per_launch, T* minv, T* panel, T* dinv, unsigned* bar,
+                                int* err, cudaStream_t s);
+// e (+)= M_d^-1 f per right-hand side; grp: [ngroups + 1] boundaries of groups of
+// at most maxg (<= 8) consecutive right-hand sides sharing a slot.
+template <typename T>
+void launch_coarse_dense(int n, const T* minv, const int* slot, const int* grp, int ngroups, int maxg, const T* f,
+                         T* e, int accumulate, const RhsState* st, cudaStream_t s);
 void launch_coarse_invert(const LevelDev& Lc, const double* w2_slots, const int* mod_slots, int nslots,
                           double b1, double b2, double2* work, float2* minv_f, double2* minv_d, cudaStream_t s);
 

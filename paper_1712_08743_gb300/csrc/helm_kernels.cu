@@ -20,31 +20,12 @@ namespace {
 template <typename T>
 __device__ __forceinline__ const T* m2ptr(const LevelDev& L) { return static_cast<const T*>(L.m2); }
 
-__device__ __forceinline__ bool rhs_active(const RhsState* st, int b) { return st == nullptr || st[b].active; }
-
 // Grid-stride extent for 1D vector kernels.
 inline int grid1d(size_t n) {
     size_t g = (n + 1023) / 1024;
     if (g < 1) g = 1;
     if (g > 2048) g = 2048;
     return (int)g;
-}
-
-// Launch with programmatic stream serialization (the kernel must call pdl_wait
-// before reading anything an earlier kernel of the stream writes).
-template <typename... KArgs, typename... Args>
-void launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, Args... args) {
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = grid;
-    cfg.blockDim = block;
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = s;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    attr[0].val.programmaticStreamSerializationAllowed = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
 }
 
 }  // namespace
@@ -234,6 +215,9 @@ __global__ void __launch_bounds__(256) k_apply_dots(LevelDev L, int npml, T acoe
 template <typename T>
 void launch_apply(const LevelDev& L0, int npml, double amax, const T* hw, const T* u, T* y, T scale,
                   int nrhs, cudaStream_t s) {
+    const double n0 = (double)L0.nx * L0.nz, es = 2.0 * sizeof(T);
+    ProfScope prof(PK_APPLY, L0.nx, L0.nz, n0 * (2 * es * nrhs + sizeof(T) * (L0.mstride ? nrhs : 1) * (L0.rho ? 4 : 1)),
+                   s);
     if (L0.rho) {   // variable density: the flux-form operator, one node per thread
         dim3 blk(32, 8), grd((L0.nx + 31) / 32, (L0.nz + 7) / 8, nrhs);
         k_apply_dots<T, 0, true><<<grd, blk, 0, s>>>(L0, npml, (T)layer_coef(npml, amax), hw, u, y,
@@ -357,6 +341,9 @@ __global__ void __launch_bounds__(256) k_apply_dots(LevelDev L, int npml, T acoe
 template <typename T>
 void launch_apply_dots(int mode, const LevelDev& L0, int npml, double amax, const T* hw, const T* u, T* y,
                        const T* aux, double* partials, int pstride, RhsState* st, int nrhs, cudaStream_t s) {
+    const double n0 = (double)L0.nx * L0.nz, es = 2.0 * sizeof(T);
+    ProfScope prof(PK_APPLY_DOTS, L0.nx, L0.nz,
+                   n0 * (3 * es * nrhs + sizeof(T) * (L0.mstride ? nrhs : 1) * (L0.rho ? 4 : 1)), s);
     dim3 blk(32, 8), grd((L0.nx + 31) / 32, (L0.nz + 7) / 8, nrhs);
     const T ac = (T)layer_coef(npml, amax);
     const bool vd = L0.rho != nullptr;
@@ -423,6 +410,9 @@ template <typename TI>
 void launch_resid64(const LevelDev& L0, int npml, double amax, const double* w2, const double* f, const double* u,
                     TI* rin, double* partials, int pstride, RhsState* st, double tol, double inner_floor,
                     double inner_fac, int first, int nrhs, cudaStream_t s) {
+    const double n0 = (double)L0.nx * L0.nz;
+    ProfScope prof(PK_RESID64, L0.nx, L0.nz,
+                   n0 * ((32.0 + 2 * sizeof(TI)) * nrhs + 8.0 * (L0.mstride ? nrhs : 1) * (L0.rho ? 4 : 1)), s);
     dim3 blk(32, 8), grd((L0.nx + 31) / 32, (L0.nz + 7) / 8, nrhs);
     if (L0.rho)
         k_resid64<TI, true><<<grd, blk, 0, s>>>(L0, npml, layer_coef(npml, amax), w2, f, u, rin, partials, pstride,
@@ -452,6 +442,7 @@ __global__ void k_refine(const TI* __restrict__ x, double* __restrict__ u, const
 
 template <typename TI>
 void launch_refine(const TI* x, double* u, const RhsState* st, size_t n, int nrhs, cudaStream_t s) {
+    ProfScope prof(PK_REFINE, (int)n, 1, (double)n * nrhs * (32.0 + 2 * sizeof(TI)), s);
     k_refine<TI><<<dim3(grid1d(n), 1, nrhs), 256, 0, s>>>(x, u, st, n);
 }
 template void launch_refine<float>(const float*, double*, const RhsState*, size_t, int, cudaStream_t);
@@ -499,6 +490,7 @@ __global__ void __launch_bounds__(256) k_bicg_init(const T* __restrict__ bv, T* 
 template <typename T>
 void launch_bicg_init(const T* b, T* x, T* r, T* rh, T* p, T* v, double* partials, int pstride, RhsState* st,
                       int* nactive, size_t n, int nrhs, cudaStream_t s) {
+    ProfScope prof(PK_BICG_INIT, (int)n, 1, (double)n * nrhs * 12.0 * sizeof(T), s);
     k_bicg_init<T><<<dim3(grid1d(n), 1, nrhs), 256, 0, s>>>(b, x, r, rh, p, v, partials, pstride, st, nactive, n);
 }
 
@@ -574,6 +566,7 @@ __global__ void __launch_bounds__(256) k_bicg_resume(const T* __restrict__ rin, 
 template <typename T>
 void launch_bicg_resume(const T* rin, T* x, T* r, T* rh, T* p, T* v, double* partials, int pstride, RhsState* st,
                         int* nactive, size_t n, int nrhs, cudaStream_t s) {
+    ProfScope prof(PK_BICG_RESUME, (int)n, 1, (double)n * nrhs * 12.0 * sizeof(T), s);
     k_bicg_resume<T><<<dim3(grid1d(n), 1, nrhs), 256, 0, s>>>(rin, x, r, rh, p, v, partials, pstride, st, nactive, n);
 }
 template void launch_bicg_resume<float>(const float*, float*, float*, float*, float*, float*, double*, int, RhsState*,
@@ -604,6 +597,7 @@ __global__ void k_bicg_p(const T* __restrict__ r, T* __restrict__ p, const T* __
 
 template <typename T>
 void launch_bicg_p(const T* r, T* p, const T* v, const RhsState* st, size_t n, int nrhs, cudaStream_t s) {
+    ProfScope prof(PK_BICG_P, (int)n, 1, (double)n * nrhs * 8.0 * sizeof(T), s);
     launch_pdl(k_bicg_p<T>, dim3(grid1d(n), 1, nrhs), dim3(256), 0, s, r, p, v, st, n);
 }
 
@@ -625,6 +619,7 @@ __global__ void k_bicg_s(const T* __restrict__ r, const T* __restrict__ v, T* __
 
 template <typename T>
 void launch_bicg_s(const T* r, const T* v, T* sv, const RhsState* st, size_t n, int nrhs, cudaStream_t s) {
+    ProfScope prof(PK_BICG_S, (int)n, 1, (double)n * nrhs * 6.0 * sizeof(T), s);
     launch_pdl(k_bicg_s<T>, dim3(grid1d(n), 1, nrhs), dim3(256), 0, s, r, v, sv, st, n);
 }
 
@@ -694,6 +689,7 @@ __global__ void __launch_bounds__(256) k_bicg_xr(T* x, const T* __restrict__ ph,
 template <typename T>
 void launch_bicg_xr(T* x, const T* ph, const T* shv, const T* sv, const T* t, const T* rh, T* r, double* partials,
                     int pstride, RhsState* st, int* nactive, size_t n, int nrhs, cudaStream_t s) {
+    ProfScope prof(PK_BICG_XR, (int)n, 1, (double)n * nrhs * 16.0 * sizeof(T), s);
     launch_pdl(k_bicg_xr<T>, dim3(grid1d(n), 1, nrhs), dim3(256), 0, s, x, ph, shv, sv, t, rh, r, partials, pstride, st,
                nactive, n);
 }
@@ -1229,6 +1225,13 @@ inline int march_rows(int col_warps, int rows, int nrhs, int longest) {
 template <typename T>
 void launch_restrict(const LevelDev& Lf, const LevelDev& Lc, const T* w2, double b1, double b2, double wj,
                      const T* f, T* fc, const RhsState* st, int nrhs, cudaStream_t s, int tile) {
+    const bool fine = Lf.m2 && !Lf.rho;
+    const double nf = (double)Lf.nx * Lf.nz, nc = (double)Lc.nx * Lc.nz, es = 2.0 * sizeof(T);
+    // f and fc per RHS; m^2 (finest) or the ten Galerkin coefficients per node, per model
+    ProfScope prof(fine ? PK_RESTRICT : PK_RESTRICT_G, Lf.nx, Lf.nz,
+                   (nf + nc) * es * nrhs +
+                       nf * sizeof(T) * (fine ? 1 : kGalerkinCoefs) * ((fine ? Lf.mstride : Lf.gkstride) ? nrhs : 1),
+                   s);
     if (Lf.m2 && !Lf.rho) {   // finest constant-density level; a density level is stored like a coarse one
         const int cw = (Lc.nx + RM_COLS - 1) / RM_COLS;
         const int ks = march_rows(cw, Lc.nz, nrhs, 16);
@@ -1489,6 +1492,15 @@ template <typename T>
 void launch_prolong(int mode, const LevelDev& Lf, const LevelDev& Lc, int npml, double amax, const T* w2,
                     double b1, double b2, double wj, const T* f, const T* ec, T* out, T* y, const T* aux,
                     double* partials, int pstride, RhsState* st, int nrhs, cudaStream_t s, int accumulate, int tile) {
+    const bool galk = mode == 0 && (!Lf.m2 || Lf.rho);
+    const double nf = (double)Lf.nx * Lf.nz, nc = (double)Lc.nx * Lc.nz, es = 2.0 * sizeof(T);
+    // f, the coarse correction and the output (read too when accumulating); finest modes also
+    // write y = A out and mode 1 reads the shadow residual; model data per model
+    const double vec = galk ? nf * (2 + accumulate) + nc : nf * (3 + (mode == 1 ? 1 : 0)) + nc;
+    ProfScope prof(galk ? PK_PROLONG_G : PK_PROLONG, Lf.nx, Lf.nz,
+                   vec * es * nrhs +
+                       nf * sizeof(T) * (galk ? kGalerkinCoefs : 1) * ((galk ? Lf.gkstride : Lf.mstride) ? nrhs : 1),
+                   s);
     const T ac = (T)layer_coef(npml, amax);
     const bool small = sizeof(T) == 4 && tile == 0;
     // a density level is stored like a coarse one: only mode 0 exists there (the
@@ -1669,6 +1681,8 @@ __global__ void __launch_bounds__(1024) k_coarse_invert(int nx, int nz, const do
 
 void launch_coarse_invert(const LevelDev& Lc, const double* w2_slots, const int* mod_slots, int nslots, double b1,
                           double b2, double2* work, float2* minv_f, double2* minv_d, cudaStream_t s) {
+    const double nn = (double)Lc.nx * Lc.nz * Lc.nx * Lc.nz;
+    ProfScope prof(PK_COARSE_INVERT, Lc.nx, Lc.nz, nn * nslots * 24.0, s);
     k_coarse_invert<<<nslots, 1024, 0, s>>>(Lc.nx, Lc.nz, static_cast<const double*>(Lc.gk),
                                             kGalerkinCoefs * (size_t)Lc.nx * Lc.nz, w2_slots, mod_slots, b1, b2,
                                             work, minv_f, minv_d);
@@ -1887,11 +1901,19 @@ size_t tail_smem_bytes(const helm_model* m, int lt, size_t elem, bool* minv_smem
 
 template <typename T>
 void launch_tail(const TailArgs& a, size_t smem, int nrhs, const RhsState* st, cudaStream_t s) {
-    static bool attr_set = false;   // one-time opt-in to more than 48 KB of dynamic shared memory
-    if (!attr_set) {
+    double coef = 0;
+    for (int l = a.lt; l <= a.L; ++l) coef += (double)a.lv[l].nx * a.lv[l].nz;
+    const double ntop = (double)a.lv[a.lt].nx * a.lv[a.lt].nz;
+    ProfScope prof(PK_TAIL, a.lv[a.lt].nx, a.lv[a.lt].nz,
+                   ntop * 2.0 * sizeof(T) * nrhs * (2 + a.accumulate) +
+                       coef * kGalerkinCoefs * sizeof(T) * (a.lv[a.lt].gkstride ? nrhs : 1),
+                   s);
+    // one-time opt-in to more than 48 KB of dynamic shared memory (initialised once, thread-safe)
+    static const bool attr_set = [] {
         cudaFuncSetAttribute(k_tail<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-        attr_set = true;
-    }
+        return true;
+    }();
+    (void)attr_set;
     launch_pdl(k_tail<T>, dim3(nrhs), dim3(1024), smem, s, a, st);
 }
 template void launch_tail<float>(const TailArgs&, size_t, int, const RhsState*, cudaStream_t);
@@ -1999,6 +2021,12 @@ template <typename T>
 void launch_correct_restrict(const LevelDev& Lf, const LevelDev& Lc, const T* w2, double b1, double b2,
                              double wj, const T* f, const T* ec, T* fc, const RhsState* st, int nrhs, cudaStream_t s,
                              int tile) {
+    const bool fine = Lf.m2 && !Lf.rho;
+    const double nf = (double)Lf.nx * Lf.nz, nc = (double)Lc.nx * Lc.nz, es = 2.0 * sizeof(T);
+    ProfScope prof(PK_CORRECT_RESTRICT, Lf.nx, Lf.nz,
+                   (nf + 2 * nc) * es * nrhs +
+                       nf * sizeof(T) * (fine ? 1 : kGalerkinCoefs) * ((fine ? Lf.mstride : Lf.gkstride) ? nrhs : 1),
+                   s);
     if (Lf.m2 && !Lf.rho) {
         dim3 grd((Lc.nx + RCX - 1) / RCX, (Lc.nz + RCZ - 1) / RCZ, nrhs);
         k_correct_restrict<T, false><<<grd, RCX * RCZ, 0, s>>>(Lf, Lc, w2, (T)b1, (T)b2, (T)wj, f, ec, fc, st);

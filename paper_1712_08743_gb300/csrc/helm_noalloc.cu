@@ -9,6 +9,7 @@
 // fixed scratch area that is part of the library image instead: a file-scope
 // __device__ array of kNoAllocScratchBytes, present on every GPU that loads the
 // library until the process exits.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <mutex>
@@ -79,9 +80,21 @@ extern "C" int helm_vcycle_noalloc(helm_model* m, int nrhs, const double* omega,
         if (k == nslots) { w2s[k] = hw2[b]; mods[k] = mod; ++nslots; }
         slot[b] = k;
     }
+    // the coarse end of the cycle helm_vcycle would use: the dense inverse of level m->ld where it
+    // applies (beta2 != 0 and the inversion fits the GPU), else the shared-memory tail
+    int W = 0, per = 0;
+    const bool dense = beta2 != 0.0 && m->ld > 0 && dense_invert_plan((int)m->lv[m->ld].n(), false, &W, &per);
+    // groups of consecutive right-hand sides sharing a slot, at most 8 each
+    int grp[kNoAllocMaxRhs + 1];
+    int ngroups = 0, maxg = 0;
+    grp[0] = 0;
+    for (int b = 1; b <= nrhs; ++b)
+        if (b == nrhs || slot[b] != slot[grp[ngroups]] || b - grp[ngroups] >= 8) {
+            maxg = std::max(maxg, b - grp[ngroups]);
+            grp[++ngroups] = b;
+        }
     const int L = (int)m->lv.size() - 1;
-    const size_t nc = m->lv[L].n();
-    // carve the scratch area
+    // carve the scratch area: the arrays every path uses, then those of the path
     size_t off = 0;
     auto take = [&](size_t bytes) { size_t o = off; off = align256(off + bytes); return o; };
     const size_t o_w2 = take(sizeof(double) * nrhs);
@@ -89,16 +102,42 @@ extern "C" int helm_vcycle_noalloc(helm_model* m, int nrhs, const double* omega,
     const size_t o_slot = take(sizeof(int) * nrhs);
     const size_t o_w2s = take(sizeof(double) * nslots);
     const size_t o_mods = take(sizeof(int) * nslots);
-    const size_t o_work = take(sizeof(double2) * nc * nc * 2 * nslots);
-    const size_t o_mf = take(sizeof(float2) * nc * nc * nslots);
-    const size_t o_md = take(sizeof(double2) * nc * nc * nslots);
-    size_t o_f[kMaxLevels], o_e[kMaxLevels];
-    for (int l = 1; l <= m->lt[0]; ++l) {
-        o_f[l] = take(sizeof(float) * 2 * m->lv[l].n() * nrhs);
-        o_e[l] = take(sizeof(float) * 2 * m->lv[l].n() * nrhs);
-    }
-    if (off > kNoAllocScratchBytes) {
-        set_last_error("helm_vcycle_noalloc: this model and batch need " + std::to_string(off) +
+    const size_t o_grp = take(sizeof(int) * (ngroups + 1));
+    const size_t common = off;
+    struct Plan {
+        size_t minv = 0, work = 0, md = 0, panel = 0, dinv = 0, bar = 0, err = 0, f[kMaxLevels] = {}, e[kMaxLevels] = {};
+        int top = 0;
+        size_t end = 0;
+    };
+    auto carve = [&](bool dn) {
+        Plan p;
+        off = common;
+        if (dn) {
+            const size_t nd = m->lv[m->ld].n();
+            const int nl = std::min(per, nslots);
+            p.minv = take(sizeof(float2) * nd * nd * nslots);
+            p.panel = take(sizeof(float2) * 2 * nd * W * nl);
+            p.dinv = take(sizeof(float2) * 2 * (size_t)W * W * nl);
+            p.bar = take(sizeof(unsigned) * nl);
+            p.err = take(sizeof(int));
+            p.top = m->ld;
+        } else {
+            const size_t nc = m->lv[L].n();
+            p.work = take(sizeof(double2) * nc * nc * 2 * nslots);
+            p.minv = take(sizeof(float2) * nc * nc * nslots);
+            p.md = take(sizeof(double2) * nc * nc * nslots);
+            p.top = m->lt[0];
+        }
+        for (int l = 1; l <= p.top; ++l) {
+            p.f[l] = take(sizeof(float) * 2 * m->lv[l].n() * nrhs);
+            p.e[l] = take(sizeof(float) * 2 * m->lv[l].n() * nrhs);
+        }
+        p.end = off;
+        return p;
+    };
+    Plan plan = carve(dense);
+    if (plan.end > kNoAllocScratchBytes) {
+        set_last_error("helm_vcycle_noalloc: this model and batch need " + std::to_string(plan.end) +
                        " bytes of scratch; the static area holds 67108864 (64 MiB)");
         return HELM_E_INVALID;
     }
@@ -114,13 +153,42 @@ extern "C" int helm_vcycle_noalloc(helm_model* m, int nrhs, const double* omega,
     if (e == cudaSuccess) e = cudaMemcpyAsync(base + o_slot, slot, sizeof(int) * nrhs, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(base + o_w2s, w2s, sizeof(double) * nslots, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(base + o_mods, mods, sizeof(int) * nslots, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(base + o_grp, grp, sizeof(int) * (ngroups + 1), cudaMemcpyHostToDevice, s);
+    bool use_dense = dense;
+    if (e == cudaSuccess && use_dense) {
+        // every byte the inversion reads is written earlier in this call (the counters and the
+        // error flag are cleared by the launcher), so stale contents do not matter
+        e = launch_dense_invert<float>(level_dev(m, m->ld, true), reinterpret_cast<const double*>(base + o_w2s),
+                                       reinterpret_cast<const int*>(base + o_mods), nslots, beta1, beta2, W, per,
+                                       reinterpret_cast<float*>(base + plan.minv),
+                                       reinterpret_cast<float*>(base + plan.panel),
+                                       reinterpret_cast<float*>(base + plan.dinv),
+                                       reinterpret_cast<unsigned*>(base + plan.bar),
+                                       reinterpret_cast<int*>(base + plan.err), s);
+        int herr = -1;
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, base + plan.err, sizeof(int), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess || herr != 0) {
+            // as helm_vcycle: without the dense inverse the tail path runs
+            cudaGetLastError();
+            e = cudaSuccess;
+            use_dense = false;
+            plan = carve(false);
+            if (plan.end > kNoAllocScratchBytes) {
+                if (cur != dev) cudaSetDevice(cur);
+                set_last_error("helm_vcycle_noalloc: this model and batch need " + std::to_string(plan.end) +
+                               " bytes of scratch; the static area holds 67108864 (64 MiB)");
+                return HELM_E_INVALID;
+            }
+        }
+    }
     if (e == cudaSuccess) {
-        // every byte read below is written earlier in this call, so nothing needs clearing
         const double* dw2 = reinterpret_cast<const double*>(base + o_w2);
-        launch_coarse_invert(level_dev(m, L, true), reinterpret_cast<const double*>(base + o_w2s),
-                             reinterpret_cast<const int*>(base + o_mods), nslots, beta1, beta2,
-                             reinterpret_cast<double2*>(base + o_work), reinterpret_cast<float2*>(base + o_mf),
-                             reinterpret_cast<double2*>(base + o_md), s);
+        if (!use_dense)
+            launch_coarse_invert(level_dev(m, L, true), reinterpret_cast<const double*>(base + o_w2s),
+                                 reinterpret_cast<const int*>(base + o_mods), nslots, beta1, beta2,
+                                 reinterpret_cast<double2*>(base + plan.work), reinterpret_cast<float2*>(base + plan.minv),
+                                 reinterpret_cast<double2*>(base + plan.md), s);
         MgCall mc;
         mc.w2 = dw2;
         mc.w2f = reinterpret_cast<const float*>(base + o_w2f);
@@ -131,15 +199,19 @@ extern "C" int helm_vcycle_noalloc(helm_model* m, int nrhs, const double* omega,
         mc.nrhs = nrhs;
         mc.lf = fcycle_level(m, hw2, nrhs);
         mc.s = s;
-        mc.minv = base + o_mf;
+        mc.minv = base + plan.minv;
         mc.slot = reinterpret_cast<const int*>(base + o_slot);
         mc.partials = nullptr;
         mc.pstride = 0;
+        mc.ld = use_dense ? m->ld : 0;
+        mc.grp = reinterpret_cast<const int*>(base + o_grp);
+        mc.ngroups = ngroups;
+        mc.maxg = maxg;
         MgLevels<float> B;
         std::memset(&B, 0, sizeof(B));
-        for (int l = 1; l <= m->lt[0]; ++l) {
-            B.f[l] = reinterpret_cast<float*>(base + o_f[l]);
-            B.e[l] = reinterpret_cast<float*>(base + o_e[l]);
+        for (int l = 1; l <= plan.top; ++l) {
+            B.f[l] = reinterpret_cast<float*>(base + plan.f[l]);
+            B.e[l] = reinterpret_cast<float*>(base + plan.e[l]);
         }
         mg_apply<float>(m, mc, B, static_cast<const float*>(r), static_cast<float*>(z), 0, nullptr, nullptr);
         e = cudaGetLastError();

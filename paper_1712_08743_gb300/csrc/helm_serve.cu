@@ -7,8 +7,11 @@
 // simulated budget) minus a reserve and minus what running slots hold, and run
 // it as one batched solve with one slowness model per right-hand side. A
 // request that arrives while others are on the GPU is admitted as soon as a
-// slot and the memory free up; slots run concurrently on the device. Every wait
-// is bounded by the caller's timeout; nothing spins.
+// slot and the memory free up; slots run concurrently on the device. Nothing
+// spins: host threads wait on a condition variable, and every request ends
+// because each solve is bounded by its max_it and max_outer. helm_poll waits at
+// most timeout_ms, or, for a negative timeout, on the host until its request
+// has finished.
 #include <algorithm>
 #include <chrono>
 #include <cmath>

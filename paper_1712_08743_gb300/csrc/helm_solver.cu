@@ -91,6 +91,9 @@ struct SolveCtx {
     int ncoarse;
     const void* minv;       // float2* or double2* [nslots][n][n]
     int lf;                 // first level of the F-cycle for this batch
+    int ld = 0;             // > 0: level solved exactly by its dense inverse (minv); 0: the tail path
+    const int* grp = nullptr;
+    int ngroups = 0, maxg = 0;
     cudaStream_t side = nullptr;    // FGMRES: the Hessenberg column finish runs here
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 };
@@ -140,12 +143,24 @@ static TailArgs tail_args(const helm_model* m, bool F, const void* in, void* out
     return a;
 }
 
+static const char* const kLevelNames[kMaxLevels] = {
+    "mg level 0", "mg level 1", "mg level 2", "mg level 3", "mg level 4", "mg level 5", "mg level 6", "mg level 7",
+    "mg level 8", "mg level 9", "mg level 10", "mg level 11", "mg level 12", "mg level 13", "mg level 14",
+    "mg level 15", "mg level 16", "mg level 17", "mg level 18", "mg level 19", "mg level 20", "mg level 21",
+    "mg level 22", "mg level 23"};
+
 template <typename T>
 static void mg_cycle(const helm_model* m, const MgCall& c, const MgLevels<T>& B, int l, bool F, int acc) {
+    NvtxRange nv(kLevelNames[l]);
     const bool dbl = sizeof(T) == 8;
     const T* hw = hw_of<T>(c);
+    if (c.ld > 0 && l == c.ld) {   // exact solve of this level by its dense inverse
+        launch_coarse_dense<T>((int)m->lv[l].n(), static_cast<const T*>(c.minv), c.slot, c.grp, c.ngroups, c.maxg,
+                               B.f[l], B.e[l], acc, c.st, c.s);
+        return;
+    }
     const int lt = m->tail_level(dbl);
-    if (l >= lt) {
+    if (c.ld <= 0 && l >= lt) {
         const TailArgs a = tail_args<T>(m, F, B.f[l], B.e[l], acc, c.minv, c.slot, c.w2, c.b1, c.b2, c.wj);
         launch_tail<T>(a, m->tail_smem[dbl], c.nrhs, c.st, c.s);
         return;
@@ -190,14 +205,14 @@ template void mg_apply<float>(const helm_model*, const MgCall&, const MgLevels<f
 template void mg_apply<double>(const helm_model*, const MgCall&, const MgLevels<double>&, const double*, double*, int,
                                double*, const double*);
 
-static int count_cycle(const helm_model* m, int lt, int l, bool F, int lf) {
-    if (l >= lt) return 1;
-    int k = 2 + count_cycle(m, lt, l + 1, F || (l + 1 == lf), lf);
-    if (F) k += 1 + count_cycle(m, lt, l + 1, false, lf);
+static int count_cycle(const helm_model* m, int lt, int l, bool F, int lf, int ld) {
+    if (ld > 0 ? l == ld : l >= lt) return 1;
+    int k = 2 + count_cycle(m, lt, l + 1, F || (l + 1 == lf), lf, ld);
+    if (F) k += 1 + count_cycle(m, lt, l + 1, false, lf, ld);
     return k;
 }
-int mg_kernels_per_apply(const helm_model* m, bool dbl, int lf) {
-    return 2 + (m->vd ? 1 : 0) + count_cycle(m, m->tail_level(dbl), 1, lf == 1, lf);
+int mg_kernels_per_apply(const helm_model* m, bool dbl, int lf, int ld) {
+    return 2 + (m->vd ? 1 : 0) + count_cycle(m, m->tail_level(dbl), 1, lf == 1, lf, ld);
 }
 
 int fcycle_level(const helm_model* m, const double* h_w2, int nrhs) {
@@ -225,21 +240,27 @@ static void vcycle(const SolveCtx& c, Inner<T>& w, const T* in, T* out, int mode
     mc.slot = c.slot;
     mc.partials = c.partials;
     mc.pstride = c.pstride;
+    mc.ld = c.ld;
+    mc.grp = c.grp;
+    mc.ngroups = c.ngroups;
+    mc.maxg = c.maxg;
     MgLevels<T> B;
     std::memset(&B, 0, sizeof(B));
-    for (int l = 1; l <= c.m->tail_level(sizeof(T) == 8); ++l) {
+    const int top = c.ld > 0 ? c.ld : c.m->tail_level(sizeof(T) == 8);
+    for (int l = 1; l <= top; ++l) {
         B.f[l] = w.fl[l]->template as<T>();
         B.e[l] = w.el[l]->template as<T>();
     }
     mg_apply<T>(c.m, mc, B, in, out, mode, y, aux);
 }
 
+// level vectors of levels 1..top (top: the dense level, or the tail's first level)
 template <typename T>
-static int alloc_levels(const helm_model* m, cudaStream_t s, int nrhs, Inner<T>& w) {
+static int alloc_levels(const helm_model* m, cudaStream_t s, int nrhs, Inner<T>& w, int top) {
     const int nl = (int)m->lv.size();
     w.fl.resize(nl);
     w.el.resize(nl);
-    for (int l = 1; l < nl && l <= m->tail_level(sizeof(T) == 8); ++l) {
+    for (int l = 1; l < nl && l <= top; ++l) {
         const size_t b = sizeof(T) * 2 * m->lv[l].n() * nrhs;
         w.fl[l].reset(new DBuf());
         w.el[l].reset(new DBuf());
@@ -258,13 +279,13 @@ static int alloc_inner(const SolveCtx& c, Inner<T>& w) {
         TRY_ALLOC(w.p, vb, c.s); TRY_ALLOC(w.v, vb, c.s); TRY_ALLOC(w.sv, vb, c.s);
         TRY_ALLOC(w.t, vb, c.s); TRY_ALLOC(w.ph, vb, c.s); TRY_ALLOC(w.shv, vb, c.s);
     }
-    return alloc_levels<T>(c.m, c.s, c.nrhs, w);
+    return alloc_levels<T>(c.m, c.s, c.nrhs, w, c.ld > 0 ? c.ld : c.m->tail_level(sizeof(T) == 8));
 }
 
 // kernels one BiCGSTAB iteration launches: p, s and x/r updates plus two
 // preconditioner applications
-static int kernels_per_iteration(const helm_model* m, bool dbl, int precond, int lf) {
-    return precond == HELM_PRECOND_NONE ? 5 : 3 + 2 * mg_kernels_per_apply(m, dbl, lf);
+static int kernels_per_iteration(const helm_model* m, bool dbl, int precond, int lf, int ld) {
+    return precond == HELM_PRECOND_NONE ? 5 : 3 + 2 * mg_kernels_per_apply(m, dbl, lf, ld);
 }
 
 template <typename T>
@@ -296,7 +317,7 @@ static void bicg_iteration(const SolveCtx& c, Inner<T>& w) {
 // Leaves the correction in w.x. `graph` caches the captured iteration chunk.
 template <typename T>
 static int inner_solve(const SolveCtx& c, Inner<T>& w, const T* rin, cudaGraphExec_t* graph, int* iters_done,
-                       bool resume) {
+                       bool resume, int guard_iters, bool* stalled) {
     const size_t n = c.m->n();
     HELM_CUDA_TRY(cudaMemsetAsync(c.nactive, 0, sizeof(int), c.s));
     count_launches(1);
@@ -308,6 +329,7 @@ static int inner_solve(const SolveCtx& c, Inner<T>& w, const T* rin, cudaGraphEx
         launch_bicg_init<T>(rin, w.x.template as<T>(), w.r.template as<T>(), w.rh.template as<T>(),
                             w.p.template as<T>(), w.v.template as<T>(), c.partials, c.pstride, c.st, c.nactive, n,
                             c.nrhs, c.s);
+    NvtxRange nv("bicgstab inner solve");
     const int chunk = std::max(1, c.o.check_every);
     if (c.o.use_graphs && *graph == nullptr) {
         cudaGraph_t g;
@@ -323,17 +345,36 @@ static int inner_solve(const SolveCtx& c, Inner<T>& w, const T* rin, cudaGraphEx
     int done = 0;
     // every right-hand side stops by itself at max_it; the extra chunk bounds the loop
     const int limit = c.o.max_it + chunk;
+    // stall guard (guard_iters > 0): a right-hand side whose recursive residual has not halved
+    // within guard_iters iterations ends the inner solve early with *stalled set (its next inner
+    // solve restarts the recurrence from the true residual)
+    std::vector<RhsState> hs;
+    std::vector<double> best(c.nrhs, -1.0);
+    std::vector<int> best_it(c.nrhs, 0);
+    if (guard_iters > 0) hs.resize(c.nrhs);
     while (done < limit) {
         if (c.o.use_graphs) {
             HELM_CUDA_TRY(cudaGraphLaunch(*graph, c.s));
         } else {
             for (int k = 0; k < chunk; ++k) bicg_iteration<T>(c, w);
         }
-        count_launches((unsigned long long)chunk * kernels_per_iteration(c.m, sizeof(T) == 8, c.o.precond, c.lf));
+        count_launches((unsigned long long)chunk * kernels_per_iteration(c.m, sizeof(T) == 8, c.o.precond, c.lf, c.ld));
         done += chunk;
         HELM_CUDA_TRY(cudaMemcpyAsync(&h_active, c.nactive, sizeof(int), cudaMemcpyDeviceToHost, c.s));
+        if (guard_iters > 0)
+            HELM_CUDA_TRY(cudaMemcpyAsync(hs.data(), c.st, sizeof(RhsState) * c.nrhs, cudaMemcpyDeviceToHost, c.s));
         HELM_CUDA_TRY(cudaStreamSynchronize(c.s));
         if (h_active <= 0) break;
+        if (guard_iters > 0) {
+            bool stall = false;
+            for (int b = 0; b < c.nrhs; ++b) {
+                if (!hs[b].active || !(hs[b].bnorm2 > 0.0)) continue;
+                const double rr = std::sqrt(hs[b].rnorm2 / hs[b].bnorm2);
+                if (best[b] < 0.0 || rr <= 0.5 * best[b]) { best[b] = rr; best_it[b] = hs[b].iters; }
+                else if (hs[b].iters - best_it[b] >= guard_iters) stall = true;
+            }
+            if (stall) { *stalled = true; break; }
+        }
     }
     HELM_CUDA_TRY(cudaGetLastError());
     *iters_done += done;
@@ -430,6 +471,7 @@ static void fgmres_cycle(const SolveCtx& c, Inner<T>& w, FgBufs<T>& f, const T* 
 template <typename T>
 static int fgmres_inner(const SolveCtx& c, Inner<T>& w, FgBufs<T>& f, const T* rin, cudaGraphExec_t* graph,
                         int* iters_done) {
+    NvtxRange nv("fgmres cycle");
     HELM_CUDA_TRY(cudaMemsetAsync(c.nactive, 0, sizeof(int), c.s));
     if (c.o.use_graphs) {
         if (*graph == nullptr) {
@@ -447,22 +489,33 @@ static int fgmres_inner(const SolveCtx& c, Inner<T>& w, FgBufs<T>& f, const T* r
         fgmres_cycle<T>(c, w, f, rin);
     }
     const int m = f.dev.m;
-    count_launches(4 + (unsigned long long)m * ((c.o.precond == HELM_PRECOND_NONE ? 1 : mg_kernels_per_apply(c.m, sizeof(T) == 8, c.lf)) +
+    count_launches(4 + (unsigned long long)m * ((c.o.precond == HELM_PRECOND_NONE ? 1 : mg_kernels_per_apply(c.m, sizeof(T) == 8, c.lf, c.ld)) +
                                                 (c.o.reorth == HELM_REORTH_NEVER ? 3 : c.o.reorth == HELM_REORTH_ALWAYS ? 5 : 4)));
     HELM_CUDA_TRY(cudaGetLastError());
     *iters_done += m;
     return HELM_OK;
 }
 
-// Dense inverses of the coarsest level, one per distinct frequency.
+// The coarse end of the cycle for one batch: either the dense inverse of level
+// ld (HELM_COARSE_AUTO where it applies), in the solve's precision, or the dense
+// inverse of the coarsest level that the shared-memory tail uses (FP32 and FP64
+// copies). One inverse per distinct (model, frequency) pair: slot[b].
 struct CoarseSet {
     DBuf work, mf, md, slot, w2s, mods;
+    DBuf grp, panel, dinv, bar, err;   // dense path
     int n = 0, nslots = 0;
+    int ld = 0;                        // > 0: the dense path, level ld
+    int ngroups = 0, maxg = 0;
+    const void* minv(bool dbl) const { return dbl ? md.p : mf.p; }
 };
 
+constexpr int kDenseGroup = 8;   // right-hand sides per group of the dense coarse kernel
+constexpr int kStallIters = 300; // Krylov iterations without the residual halving that count as a stall
+
 static int build_coarse(const helm_model* m, cudaStream_t s, int nrhs, const double* h_w2, double b1, double b2,
-                        CoarseSet& cs) {
-    // one dense inverse per distinct (model, frequency) pair
+                        bool dbl, int coarse, CoarseSet& cs) {
+    NvtxRange nv("coarse set-up");
+    // one inverse per distinct (model, frequency) pair
     std::map<std::pair<int, double>, int> uniq;
     std::vector<int> slot(nrhs), mods;
     std::vector<double> w2s;
@@ -477,19 +530,64 @@ static int build_coarse(const helm_model* m, cudaStream_t s, int nrhs, const dou
         }
         slot[b] = it->second;
     }
-    const Level& Lc = m->lv.back();
-    cs.n = (int)Lc.n();
     cs.nslots = (int)w2s.size();
-    const size_t nn = (size_t)cs.n * cs.n;
-    TRY_ALLOC(cs.work, sizeof(double2) * nn * 2 * cs.nslots, s);
-    TRY_ALLOC(cs.mf, sizeof(float2) * nn * cs.nslots, s);
-    TRY_ALLOC(cs.md, sizeof(double2) * nn * cs.nslots, s);
     TRY_ALLOC(cs.slot, sizeof(int) * nrhs, s);
     TRY_ALLOC(cs.w2s, sizeof(double) * cs.nslots, s);
     TRY_ALLOC(cs.mods, sizeof(int) * cs.nslots, s);
     HELM_CUDA_TRY(cudaMemcpyAsync(cs.slot.p, slot.data(), sizeof(int) * nrhs, cudaMemcpyHostToDevice, s));
     HELM_CUDA_TRY(cudaMemcpyAsync(cs.w2s.p, w2s.data(), sizeof(double) * cs.nslots, cudaMemcpyHostToDevice, s));
     HELM_CUDA_TRY(cudaMemcpyAsync(cs.mods.p, mods.data(), sizeof(int) * cs.nslots, cudaMemcpyHostToDevice, s));
+
+    int W = 0, per = 0;
+    if (coarse == HELM_COARSE_AUTO && b2 != 0.0 && m->ld > 0 && dense_invert_plan((int)m->lv[m->ld].n(), dbl, &W, &per)) {
+        const int ld = m->ld, n = (int)m->lv[ld].n();
+        const size_t es = dbl ? sizeof(double2) : sizeof(float2);
+        const int nl = std::min(per, cs.nslots);
+        // groups of at most kDenseGroup consecutive right-hand sides of one slot
+        std::vector<int> grp{0};
+        int maxg = 0;
+        for (int b = 1; b <= nrhs; ++b)
+            if (b == nrhs || slot[b] != slot[grp.back()] || b - grp.back() >= kDenseGroup) {
+                maxg = std::max(maxg, b - grp.back());
+                grp.push_back(b);
+            }
+        DBuf& mi = dbl ? cs.md : cs.mf;
+        TRY_ALLOC(mi, es * (size_t)n * n * cs.nslots, s);
+        TRY_ALLOC(cs.panel, es * 2 * (size_t)n * W * nl, s);
+        TRY_ALLOC(cs.dinv, es * 2 * (size_t)W * W * nl, s);
+        TRY_ALLOC(cs.bar, sizeof(unsigned) * nl, s);
+        TRY_ALLOC(cs.err, sizeof(int), s);
+        TRY_ALLOC(cs.grp, sizeof(int) * grp.size(), s);
+        HELM_CUDA_TRY(cudaMemcpyAsync(cs.grp.p, grp.data(), sizeof(int) * grp.size(), cudaMemcpyHostToDevice, s));
+        const LevelDev Ld = level_dev(m, ld, true);
+        cudaError_t e = dbl ? launch_dense_invert<double>(Ld, cs.w2s.as<double>(), cs.mods.as<int>(), cs.nslots, b1, b2, W,
+                                                          per, cs.md.as<double>(), cs.panel.as<double>(),
+                                                          cs.dinv.as<double>(), cs.bar.as<unsigned>(), cs.err.as<int>(), s)
+                            : launch_dense_invert<float>(Ld, cs.w2s.as<double>(), cs.mods.as<int>(), cs.nslots, b1, b2, W,
+                                                         per, cs.mf.as<float>(), cs.panel.as<float>(),
+                                                         cs.dinv.as<float>(), cs.bar.as<unsigned>(), cs.err.as<int>(), s);
+        int herr = -1;
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, cs.err.p, sizeof(int), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e == cudaSuccess && herr == 0) {
+            cs.ld = ld;
+            cs.n = n;
+            cs.ngroups = (int)grp.size() - 1;
+            cs.maxg = maxg;
+            return HELM_OK;
+        }
+        // the dense inverse could not be formed (a launch that does not fit, or a
+        // vanishing pivot): fall back to the multigrid tail below
+        cudaGetLastError();
+    }
+
+    const Level& Lc = m->lv.back();
+    cs.n = (int)Lc.n();
+    cs.ld = 0;
+    const size_t nn = (size_t)cs.n * cs.n;
+    TRY_ALLOC(cs.work, sizeof(double2) * nn * 2 * cs.nslots, s);
+    TRY_ALLOC(cs.mf, sizeof(float2) * nn * cs.nslots, s);
+    TRY_ALLOC(cs.md, sizeof(double2) * nn * cs.nslots, s);
     count_launches(1);
     launch_coarse_invert(level_dev(m, (int)m->lv.size() - 1, true), cs.w2s.as<double>(), cs.mods.as<int>(), cs.nslots,
                          b1, b2, cs.work.as<double2>(), cs.mf.as<float2>(), cs.md.as<double2>(), s);
@@ -502,12 +600,14 @@ static int build_coarse(const helm_model* m, cudaStream_t s, int nrhs, const dou
 template <typename T>
 static int solve_impl(const helm_model* m, cudaStream_t s, int nrhs, const double* h_w2, const double* f64,
                       double* u64, const helm_solve_opts& o, helm_solve_stats* stats) {
+    NvtxRange nv("helm solve");
     const size_t n = m->n();
     SolveCtx c;
     c.m = m;
     c.s = s;
     c.nrhs = nrhs;
     c.o = o;
+    if (prof_on()) c.o.use_graphs = 0;   // every launch is timed on its own while profiling
     c.pstride = 3 * max_blocks_per_rhs(m);
     if (o.krylov == HELM_KRYLOV_FGMRES) c.pstride = std::max(c.pstride, fg_partials(m->n()));
     c.lf = fcycle_level(m, h_w2, nrhs);
@@ -518,17 +618,25 @@ static int solve_impl(const helm_model* m, cudaStream_t s, int nrhs, const doubl
     TRY_ALLOC(part, sizeof(double) * (size_t)c.pstride * nrhs, s);
     TRY_ALLOC(nact, sizeof(int), s);
     TRY_ALLOC(rin, sizeof(T) * 2 * n * nrhs, s);
-    CoarseSet cs;
-    int rc = build_coarse(m, s, nrhs, h_w2, o.beta1, o.beta2, cs);
+    const int coarse = o.precond == HELM_PRECOND_NONE ? HELM_COARSE_TAIL : o.coarse;
+    std::unique_ptr<CoarseSet> cs(new CoarseSet());
+    int rc = build_coarse(m, s, nrhs, h_w2, o.beta1, o.beta2, sizeof(T) == 8, coarse, *cs);
     if (rc != HELM_OK) return rc;
     c.w2 = w2.as<double>();
     c.w2f = w2f.as<float>();
     c.st = st.as<RhsState>();
     c.partials = part.as<double>();
     c.nactive = nact.as<int>();
-    c.slot = cs.slot.as<int>();
-    c.ncoarse = cs.n;
-    c.minv = sizeof(T) == 8 ? (const void*)cs.md.p : (const void*)cs.mf.p;
+    auto use_coarse = [&](const CoarseSet& q) {
+        c.slot = q.slot.as<int>();
+        c.ncoarse = q.n;
+        c.minv = q.minv(sizeof(T) == 8);
+        c.ld = q.ld;
+        c.grp = q.grp.as<int>();
+        c.ngroups = q.ngroups;
+        c.maxg = q.maxg;
+    };
+    use_coarse(*cs);
     Inner<T> w;
     rc = alloc_inner<T>(c, w);
     if (rc != HELM_OK) return rc;
@@ -570,7 +678,18 @@ static int solve_impl(const helm_model* m, cudaStream_t s, int nrhs, const doubl
     cudaGraphExec_t graph = nullptr;
     int iters_done = 0;
     const LevelDev L0 = level_dev(m, 0, true);
+    // Stall guard: while the preconditioner's shift is not the paper's (1, 1), a right-hand side
+    // whose FP64 residual has not halved within kStallIters Krylov iterations (while above tol)
+    // switches the batch to (1, 1): with (1, 0.5) and Jacobi weight 0.5 the cycle is not a stable
+    // approximate inverse on some layered models (slow layers between fast ones), and the solve
+    // then stalls at any tolerance. BiCGSTAB also checks its recursive residual within the inner
+    // solve (it can run up to max_it there) and ends that inner solve early on a stall.
+    const bool guard = o.precond != HELM_PRECOND_NONE && !(o.beta1 == 1.0 && o.beta2 == 1.0);
+    bool switched = false, restart_inner = false, force_switch = false;
+    std::vector<int> ref_it(nrhs, 0);
+    std::vector<double> ref_res(nrhs, -1.0);
     for (int outer = 0;; ++outer) {
+        NvtxRange nv_outer("refinement step");
         launch_resid64<T>(L0, m->npml, m->alpha_max, c.w2, f64, u64, rin.as<T>(), c.partials, c.pstride, c.st, o.tol,
                           floor_tol, inner_fac, outer == 0, nrhs, s);
         count_launches(1);
@@ -581,10 +700,38 @@ static int solve_impl(const helm_model* m, cudaStream_t s, int nrhs, const doubl
         for (int b = 0; b < nrhs; ++b)
             if (hs[b].outer_active) { any = 1; }
         if (!any || outer >= max_outer) break;
+        if (guard && !switched) {
+            bool stall = force_switch;
+            for (int b = 0; b < nrhs; ++b) {
+                if (!hs[b].outer_active) continue;
+                if (ref_res[b] < 0.0 || hs[b].relres <= 0.5 * ref_res[b]) {
+                    ref_res[b] = hs[b].relres;
+                    ref_it[b] = hs[b].iters;
+                } else if (hs[b].iters - ref_it[b] >= kStallIters) {
+                    stall = true;
+                }
+            }
+            if (stall) {
+                c.o.beta1 = 1.0;
+                c.o.beta2 = 1.0;
+                std::unique_ptr<CoarseSet> cs2(new CoarseSet());
+                rc = build_coarse(m, s, nrhs, h_w2, 1.0, 1.0, sizeof(T) == 8, coarse, *cs2);
+                if (rc != HELM_OK) break;
+                cs.swap(cs2);
+                use_coarse(*cs);
+                if (graph) { cudaGraphExecDestroy(graph); graph = nullptr; }   // captured with the old inverse
+                switched = true;
+                restart_inner = true;
+            }
+        }
         for (int b = 0; b < nrhs; ++b) outer_count[b] += hs[b].outer_active;
         // BiCGSTAB keeps its recurrence across refinement steps (residual replacement)
+        bool inner_stall = false;
         rc = fgm ? fgmres_inner<T>(c, w, fb, rin.as<T>(), &graph, &iters_done)
-                 : inner_solve<T>(c, w, rin.as<T>(), &graph, &iters_done, outer > 0);
+                 : inner_solve<T>(c, w, rin.as<T>(), &graph, &iters_done, outer > 0 && !restart_inner,
+                                  guard && !switched ? kStallIters : 0, &inner_stall);
+        restart_inner = false;
+        if (inner_stall) force_switch = true;
         if (rc != HELM_OK) break;
         launch_refine<T>(w.x.template as<T>(), u64, c.st, n, nrhs, s);
         count_launches(1);
@@ -601,6 +748,8 @@ static int solve_impl(const helm_model* m, cudaStream_t s, int nrhs, const doubl
             stats[b].outer_its = outer_count[b];
             stats[b].converged = conv ? 1 : 0;
             stats[b].relres = hs[b].relres;
+            stats[b].dense_level = cs->ld;
+            stats[b].shift_switched = switched ? 1 : 0;
         }
     }
     return status;
@@ -621,9 +770,9 @@ size_t solve_bytes(int nx, int nz, int nlev_n_sum_extra, int nrhs, int precision
     return b + (64u << 20);
 }
 
-// One standalone V-cycle z = V(r) on the fine level, complex64, for checks.
+// One standalone preconditioner cycle z = V(r) on the fine level, complex64, for checks.
 int vcycle_once(const helm_model* m, cudaStream_t s, int nrhs, const double* h_w2, double b1, double b2, double wj,
-                const float* r, float* z) {
+                int coarse, const float* r, float* z) {
     SolveCtx c;
     c.m = m;
     c.s = s;
@@ -641,7 +790,7 @@ int vcycle_once(const helm_model* m, cudaStream_t s, int nrhs, const double* h_w
     std::vector<float> h_w2f(h_w2, h_w2 + nrhs);
     HELM_CUDA_TRY(cudaMemcpyAsync(w2f.p, h_w2f.data(), sizeof(float) * nrhs, cudaMemcpyHostToDevice, s));
     CoarseSet cs;
-    int rc = build_coarse(m, s, nrhs, h_w2, b1, b2, cs);
+    int rc = build_coarse(m, s, nrhs, h_w2, b1, b2, false, coarse, cs);
     if (rc != HELM_OK) return rc;
     c.w2 = w2.as<double>();
     c.w2f = w2f.as<float>();
@@ -651,8 +800,12 @@ int vcycle_once(const helm_model* m, cudaStream_t s, int nrhs, const double* h_w
     c.slot = cs.slot.as<int>();
     c.ncoarse = cs.n;
     c.minv = cs.mf.p;
+    c.ld = cs.ld;
+    c.grp = cs.grp.as<int>();
+    c.ngroups = cs.ngroups;
+    c.maxg = cs.maxg;
     Inner<float> w;
-    rc = alloc_levels<float>(m, s, nrhs, w);
+    rc = alloc_levels<float>(m, s, nrhs, w, c.ld > 0 ? c.ld : m->tail_level(false));
     if (rc != HELM_OK) return rc;
     vcycle<float>(c, w, r, z, 0, nullptr, nullptr);
     HELM_CUDA_TRY(cudaGetLastError());

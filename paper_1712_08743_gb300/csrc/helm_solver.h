@@ -21,7 +21,7 @@ int solve_batch(const helm_model* m, cudaStream_t s, int nrhs, const double* h_w
 size_t solve_bytes(int nx, int nz, int extra, int nrhs, int precision);
 
 int vcycle_once(const helm_model* m, cudaStream_t s, int nrhs, const double* h_w2, double b1, double b2, double wj,
-                const float* r, float* z);
+                int coarse, const float* r, float* z);
 
 // Misfit (Eq. 4) and its gradient (Eq. 7), split so that an autograd backward
 // runs the adjoint solves: fwi_forward keeps the wavefields and data residuals
@@ -66,6 +66,9 @@ struct MgCall {
     double* partials;       // finest-level dot reductions (modes 1, 2)
     int pstride;
     int lf;                 // first level of the F-cycle (fcycle_level)
+    int ld = 0;             // > 0: this level is solved exactly by its dense inverse (minv), 0: the tail path
+    const int* grp = nullptr;   // dense path: groups of consecutive right-hand sides sharing a slot
+    int ngroups = 0, maxg = 0;
 };
 // First level of the F-cycle for a batch with grid-scaled (h omega_b)^2 = h_w2[b]:
 // the first level l >= 1 whose spacing 2^l h gives k h >= kFcycleKh for the
@@ -81,7 +84,7 @@ struct MgLevels {
 template <typename T>
 void mg_apply(const helm_model* m, const MgCall& c, const MgLevels<T>& B, const T* in, T* out, int mode, T* y,
               const T* aux);
-int mg_kernels_per_apply(const helm_model* m, bool dbl, int lf);
+int mg_kernels_per_apply(const helm_model* m, bool dbl, int lf, int ld);
 
 int autotune(helm_model* m, cudaStream_t s, int nrhs, double hw2, int reps, int* out);
 int time_kernel(const helm_model* m, cudaStream_t s, int kernel, int nrhs, double hw2, int reps, double* ms,

@@ -70,14 +70,17 @@ def test_vcycle_matches_restatement(hg, ctx, name, make):
     rng = np.random.default_rng(2)
     om = 2 * np.pi * np.array([4.0, 6.0])
     r = models.random_complex(rng, (2, model.nz, model.nx), np.complex64)
-    for beta, wj in [((1.0, 0.5), 0.8), ((1.0, 1.0), 0.6)]:
-        z = hg.helm_vcycle(model, om, r, beta, wj)
-        m2 = oracle.pad_slowness(mdl.slowness, mdl.npml) ** 2
-        assert len(mg.level_shapes(model.nx, model.nz)) == model.nlevels
-        for k in range(2):
-            V = mg.VCycle(m2, (mdl.h * om[k]) ** 2, beta, wj)
-            ref = V.apply(r[k].astype(np.complex128).ravel()).reshape(model.nz, model.nx)
-            assert rel(z[k], ref) < 2e-5, (name, beta, k, rel(z[k], ref))
+    # default coarse end (the first level with at most 1200 nodes solved by its dense inverse)
+    # and the shared-memory tail over the whole hierarchy
+    for coarse, kind in [(None, "dense"), (hg.HELM_COARSE_TAIL, "tail")]:
+        for beta, wj in [((1.0, 0.5), 0.8), ((1.0, 1.0), 0.6)]:
+            z = hg.helm_vcycle(model, om, r, beta, wj, coarse=coarse)
+            m2 = oracle.pad_slowness(mdl.slowness, mdl.npml) ** 2
+            assert len(mg.level_shapes(model.nx, model.nz)) == model.nlevels
+            for k in range(2):
+                V = mg.VCycle(m2, (mdl.h * om[k]) ** 2, beta, wj, coarse=kind)
+                ref = V.apply(r[k].astype(np.complex128).ravel()).reshape(model.nz, model.nx)
+                assert rel(z[k], ref) < 2e-5, (name, kind, beta, k, rel(z[k], ref))
     model.close()
 
 
@@ -347,10 +350,13 @@ def test_autograd_backward_runs_adjoint(hg, ctx):
     prob = FWIProblem(ctx, h, om, src, rec, d_obs, 1e-3, npml, 0.5, dict(tol=1e-12))
     m = torch.tensor(m0, dtype=torch.float64, device="cuda", requires_grad=True)
     J = HelmFWI.apply(m, prob)
-    J.backward()
+    J.backward(retain_graph=True)
     Jr, gr = oracle.gradient(m0, h, om, src, rec, d_obs, 1e-3, npml)
     assert abs(J.item() - Jr) / Jr < 1e-8
     assert rel(m.grad.cpu().numpy(), gr) < 1e-5
+    # the forward's device state serves one backward: a second one through the same graph raises
+    with pytest.raises(RuntimeError, match="backward ran already"):
+        J.backward()
 
 
 def test_served_results_equal_lone_solves(hg):
@@ -375,6 +381,29 @@ def test_served_results_equal_lone_solves(hg):
         model.close()
         hg.helm_release(ctx, t)
     assert max(r.batch_size for r in served) >= 2
+    ctx.close()
+
+
+def test_served_requests_match_the_oracle(hg):
+    """Requests of the serving workload's kind (a 128^2 and a 256^2 grid, layered models,
+    ten points per wavelength) served together with a smaller one: each served wavefield
+    matches the oracle's sparse-LU wavefield to 1e-6 (tol 1e-10)."""
+    ctx = hg.Context(0)
+    hg.helm_serve_config(ctx, max_batch=4, max_slots=2)
+    reqs = [models.c5_request(i) for i in (6, 1)]          # 128^2 at 13.5 Hz, 256^2 at 9.9 Hz
+    rng = np.random.default_rng(11)
+    c = models.layered_model(rng, 64, 64, 20.0, 4)
+    opts = dict(tol=1e-10, krylov=hg.HELM_KRYLOV_FGMRES, max_it=20000)
+    tickets = [hg.helm_submit(ctx, r.slowness, r.h, r.omegas[0], r.sources[0], opts=opts) for r in reqs]
+    tickets.append(hg.helm_submit(ctx, 1 / c, 20.0, 2 * np.pi * 5.0, (32, 2), opts=opts))
+    served = [hg.helm_poll(ctx, t, 300000) for t in tickets]
+    for r, res in zip(reqs, served):
+        assert res is not None and res.status == hg.HELM_OK, (r.name, res and res.stats)
+        ref = oracle.solve_fields(r.slowness, r.h, r.omegas[0], r.sources, 20, 0.5)[0]
+        assert rel(res.u, ref) < 1e-6, (r.name, rel(res.u, ref))
+    assert served[2] is not None and served[2].status == hg.HELM_OK
+    for t in tickets:
+        hg.helm_release(ctx, t)
     ctx.close()
 
 
