@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-alt", action="store_true", help="skip the other Krylov method's leg of the single-case line")
+    ap.add_argument("--no-legs", action="store_true",
+                    help="skip the batched and Gauss-Newton legs of the single-case line")
     ap.add_argument("--krylov", default=None, choices=["bicgstab", "fgmres"],
                     help="Krylov method (default: FGMRES(10) for the single case, the paper's engine, with "
                          "BiCGSTAB timed beside it; BiCGSTAB for the batched and ablation workloads)")
@@ -64,7 +66,12 @@ def parse():
                          "Gauss-Newton iteration of the gradient case; ablation: preconditioner on/off")
     ap.add_argument("--kernels-only", action="store_true",
                     help="time only the hot kernels alone (the roofline legs), print one line per kernel")
-    ap.add_argument("--requests", type=int, default=48, help="serving: number of requests")
+    ap.add_argument("--requests", type=int, default=48, help="serving: number of requests per stream")
+    ap.add_argument("--rates", default="0.8", help="serving: arrival rates as fractions of the saturated throughput")
+    ap.add_argument("--sat-requests", type=int, default=200,
+                    help="serving: requests of the saturated-throughput run (all queued at once)")
+    ap.add_argument("--seq-requests", type=int, default=16,
+                    help="serving: requests solved one after another in plain FP64 for the baseline")
     ap.add_argument("--serve-beta2", type=float, default=None,
                     help="serving: imaginary shift beta2 of the preconditioner (default: the library's (1, 0.5), "
                          "whose stall guard switches a stalled solve to the paper's (1, 1))")
@@ -316,6 +323,103 @@ def run_kernels_only(args):
     ctx.close()
 
 
+def batched_leg(api, _lib, ctx, stream, steps: int, tune: bool = True, inner_tol: float = 1e-2,
+                krylov: str = "bicgstab"):
+    """64 surface shots x 5 frequencies (3..7 Hz) on the 401 x 201 layered model with a dipping
+    interface, 320 right-hand sides in one helm_solve, mixed precision to relres 1e-6, the tiles
+    of the multigrid kernels chosen by the autotuner first. Timed with CUDA events on the
+    library's stream, one warm-up batch."""
+    import torch
+
+    from synth import models
+
+    mdl = models.c3_model()
+    model = api.helm_create_model(ctx, mdl.slowness, mdl.h, mdl.npml, mdl.alpha_max)
+    om = np.repeat(mdl.omegas, len(mdl.sources))
+    src = np.tile(mdl.sources, (len(mdl.omegas), 1))
+    kry = {"bicgstab": _lib.HELM_KRYLOV_BICGSTAB, "fgmres": _lib.HELM_KRYLOV_FGMRES}[krylov]
+    opts = api.helm_default_opts(tol=1e-6, precision="mixed", krylov=kry, inner_tol=inner_tol)
+    tiles = None
+    if tune:
+        from paper_1712_08743_gb300 import autotune
+        tiles = autotune.autotune(model, len(om), float(om[0]))
+    F = np.zeros((len(om), model.nz, model.nx), np.complex128)
+    for k, (sx, sz) in enumerate(src):
+        F[k, sz + mdl.npml, sx + mdl.npml] = 1.0 / mdl.h ** 2
+    f_dev = torch.from_numpy(F).cuda()
+    u_dev = torch.empty_like(f_dev)
+    api.helm_solve(model, om, f=f_dev, opts=opts, out=u_dev)
+    ms = []
+    st = None
+    for _ in range(max(steps, 1)):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        _, st, _ = api.helm_solve(model, om, f=f_dev, opts=opts, out=u_dev)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms.append(a.elapsed_time(b))
+    model.close()
+    its = [x["iters"] for x in st]
+    return {"workload": "batched_401x201_64src_5f_tol1e-6", "solves_per_s": len(om) * 1e3 / float(np.mean(ms)),
+            "ms_per_batch": float(np.mean(ms)), "nrhs": len(om), "krylov": krylov, "inner_tol": inner_tol,
+            "iters_min": min(its), "iters_max": max(its), "converged": all(x["converged"] for x in st),
+            "autotuned_tiles": tiles, "steps": len(ms)}
+
+
+def observed_data(api, ctx, true):
+    """Observed data of the gradient case: the library's modelled data P u of the true model at
+    every frequency and shot (the paper likewise makes its data with the same discretisation)."""
+    om = true.omegas
+    mt = api.helm_create_model(ctx, true.slowness, true.h, true.npml, true.alpha_max)
+    zero = np.zeros((len(om), len(true.sources), len(true.receivers)), np.complex128)
+    _, d_obs, st0, _, _ = api.helm_fwi_forward(mt, om, true.sources, true.receivers, zero, 0.0,
+                                               dict(tol=1e-10, precision="mixed"))
+    st0.close()
+    mt.close()
+    return d_obs
+
+
+def gn_leg(api, ctx, steps: int, cg: int = 5):
+    """One Gauss-Newton iteration (Eq. 9) of the gradient case: 401 x 201 smoothed start model,
+    32 shots x 4 frequencies (3..6 Hz), 201 receivers, lambda = 1e-3: forward solves and misfit,
+    adjoint solves and gradient, then `cg` CG iterations (a Born and an adjoint solve per shot
+    and frequency each). The observed data are the library's own modelled data of the true
+    model. Wall time per iteration (each call synchronises), one warm-up iteration."""
+    from synth import models
+
+    true, start = models.c4_models()
+    om = true.omegas
+    opts = dict(tol=1e-6, precision="mixed")
+    lam = 1e-3
+    d_obs = observed_data(api, ctx, true)
+    model = api.helm_create_model(ctx, start.slowness, start.h, start.npml, start.alpha_max)
+
+    def iteration():
+        t0 = time.perf_counter()
+        J, _, state, _, _ = api.helm_fwi_forward(model, om, start.sources, start.receivers, d_obs, lam, opts)
+        t1 = time.perf_counter()
+        g, _ = api.helm_fwi_backward(model, state, opts)
+        t2 = time.perf_counter()
+        dm, rel, _ = api.helm_gn_step(model, state, g, cg, opts)
+        t3 = time.perf_counter()
+        state.close()
+        return J, rel, (t1 - t0, t2 - t1, t3 - t2)
+
+    iteration()
+    times = []
+    J = rel = None
+    for _ in range(max(steps, 1)):
+        J, rel, t = iteration()
+        times.append(t)
+    model.close()
+    tf, tb, tg = (float(np.mean([t[k] for t in times])) for k in range(3))
+    nrhs = len(om) * len(start.sources)
+    solves = nrhs * (2 + 2 * cg)
+    return {"workload": "gradient_401x201_32shots_4f_gn", "iters_per_s": 1.0 / (tf + tb + tg), "cg_iters": cg,
+            "solves_per_iteration": solves, "solves_per_s": solves / (tf + tb + tg), "forward_s": tf,
+            "gradient_s": tb, "cg_s": tg, "misfit": J, "cg_relres": [float(x) for x in rel], "steps": len(times)}
+
+
 def run_ours(args):
     import torch
 
@@ -471,6 +575,12 @@ def run_ours(args):
                        for k, d in sorted(per.items(), key=lambda kv: -kv[1]["ms"])},
             "profiled_ms": total_ms, "kernels_alone": kern}
 
+    # the batched and Gauss-Newton configurations, each timed on its own (not part of `value`)
+    legs = {}
+    if not args.no_legs and not args.density:
+        legs["batched"] = batched_leg(api, _lib, ctx, stream, steps=3)
+        legs["gauss_newton"] = gn_leg(api, ctx, steps=2)
+
     cpu = None
     err = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline and not args.density:
@@ -522,6 +632,9 @@ def run_ours(args):
                     "d2h_bytes_per_step": int(u_host.nbytes), "ms": float(np.mean(e2e_ms))},
             "roofline": roof, "clocks": clocks, "gpu_launches": int(launches), "cpu_baseline": cpu,
             "err_vs_oracle": err,
+            "batched_solves_per_s": legs["batched"]["solves_per_s"] if "batched" in legs else None,
+            "gn_iters_per_s": legs["gauss_newton"]["iters_per_s"] if "gauss_newton" in legs else None,
+            "legs": legs,
         }
         print(json.dumps(line), flush=True)
     model.close()
@@ -533,101 +646,37 @@ def run_ours(args):
 
 
 def run_batched(args):
-    """64 surface shots x 5 frequencies (3..7 Hz) on the 401 x 201 layered model, one call."""
+    """64 shots x 5 frequencies (3..7 Hz) on the 401 x 201 layered model, one call (--tune: autotuned tiles)."""
     import torch
 
     from paper_1712_08743_gb300 import _lib, api, build
-    from synth import models
-
-    build.build()
-    lib = _lib.load()
-    stream = torch.cuda.Stream()
-    torch.cuda.set_stream(stream)
-    ctx = api.Context(0, stream)
-    mdl = models.c3_model()
-    model = api.helm_create_model(ctx, mdl.slowness, mdl.h, mdl.npml, mdl.alpha_max)
-    om = np.repeat(mdl.omegas, len(mdl.sources))
-    src = np.tile(mdl.sources, (len(mdl.omegas), 1))
-    kry = {"bicgstab": _lib.HELM_KRYLOV_BICGSTAB, "fgmres": _lib.HELM_KRYLOV_FGMRES}[args.krylov]
-    opts = api.helm_default_opts(tol=1e-6, precision="mixed", krylov=kry, restart=args.restart,
-                                 inner_tol=args.inner_tol)
-    if args.tune:
-        from paper_1712_08743_gb300 import autotune
-        autotune.autotune(model, len(om), float(om[0]))
-    F = np.zeros((len(om), model.nz, model.nx), np.complex128)
-    for k, (sx, sz) in enumerate(src):
-        F[k, sz + mdl.npml, sx + mdl.npml] = 1.0 / mdl.h ** 2
-    f_dev = torch.from_numpy(F).cuda()
-    u_dev = torch.empty_like(f_dev)
-    for _ in range(max(args.warmup, 1)):
-        api.helm_solve(model, om, f=f_dev, opts=opts, out=u_dev)
-    ms = []
-    for _ in range(args.steps):
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        _, st, _ = api.helm_solve(model, om, f=f_dev, opts=opts, out=u_dev)
-        b.record(stream)
-        torch.cuda.synchronize()
-        ms.append(a.elapsed_time(b))
-    its = [s["iters"] for s in st]
-    print(json.dumps({"metric": "helmholtz_solves_per_s", "workload": "batched_401x201_64src_5f",
-                      "value": len(om) * 1e3 / float(np.mean(ms)), "unit": "solves/s", "ms_per_batch": float(np.mean(ms)),
-                      "nrhs": len(om), "krylov": args.krylov, "iters_min": min(its), "iters_max": max(its),
-                      "converged": all(s["converged"] for s in st)}), flush=True)
-
-
-def run_gn(args):
-    """One Gauss-Newton iteration (Eq. 9) of the gradient case: 401 x 201 smoothed
-    start model, 32 shots x 4 frequencies (3..6 Hz), 201 receivers, lambda = 1e-3;
-    forward solves and misfit, adjoint solves and gradient, then `--cg` CG
-    iterations, each one Born and one adjoint solve per shot and frequency."""
-    import torch
-
-    import oracle
-    from paper_1712_08743_gb300 import _lib, api, build
-    from synth import models
 
     build.build()
     _lib.load()
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
     ctx = api.Context(0, stream)
-    true, start = models.c4_models()
-    om = true.omegas
-    # observed data from the true model (oracle solves; input preparation, not timed)
-    d_obs = np.stack([oracle.sample_receivers(
-        oracle.solve_fields(true.slowness, true.h, w, true.sources, true.npml, true.alpha_max), true.receivers,
-        true.npml) for w in om])
-    model = api.helm_create_model(ctx, start.slowness, start.h, start.npml, start.alpha_max)
-    opts = dict(tol=1e-6, precision="mixed")
-    lam = 1e-3
-    nrhs = len(om) * len(start.sources)
+    r = batched_leg(api, _lib, ctx, stream, steps=args.steps, tune=args.tune, inner_tol=args.inner_tol,
+                    krylov=args.krylov)
+    print(json.dumps({"metric": "helmholtz_solves_per_s", "value": r["solves_per_s"], "unit": "solves/s", **r}),
+          flush=True)
+    ctx.close()
 
-    def iteration():
-        t0 = time.perf_counter()
-        J, _, state, _, _ = api.helm_fwi_forward(model, om, start.sources, start.receivers, d_obs, lam, opts)
-        t1 = time.perf_counter()
-        g, _ = api.helm_fwi_backward(model, state, opts)
-        t2 = time.perf_counter()
-        dm, rel, _ = api.helm_gn_step(model, state, g, args.cg, opts)
-        t3 = time.perf_counter()
-        state.close()
-        return J, rel, (t1 - t0, t2 - t1, t3 - t2)
 
-    for _ in range(max(args.warmup, 1)):
-        iteration()
-    times = []
-    for _ in range(max(args.steps, 1)):
-        J, rel, t = iteration()
-        times.append(t)
-    tf, tb, tg = (float(np.mean([t[k] for t in times])) for k in range(3))
-    solves = nrhs * (2 + 2 * args.cg)
-    print(json.dumps({"metric": "gauss_newton_iterations_per_s", "workload": "gradient_401x201_32shots_4f_gn",
-                      "value": 1.0 / (tf + tb + tg), "unit": "iterations/s", "steps": len(times),
-                      "cg_iters": args.cg, "solves_per_iteration": solves,
-                      "solves_per_s": solves / (tf + tb + tg), "forward_s": tf, "gradient_s": tb, "cg_s": tg,
-                      "misfit": J, "cg_relres": [float(x) for x in rel]}), flush=True)
-    model.close()
+def run_gn(args):
+    """One Gauss-Newton iteration of the gradient case (see gn_leg)."""
+    import torch
+
+    from paper_1712_08743_gb300 import _lib, api, build
+
+    build.build()
+    _lib.load()
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    ctx = api.Context(0, stream)
+    r = gn_leg(api, ctx, steps=args.steps, cg=args.cg)
+    print(json.dumps({"metric": "gauss_newton_iterations_per_s", "value": r["iters_per_s"], "unit": "iterations/s",
+                      **r}), flush=True)
     ctx.close()
 
 
@@ -640,7 +689,6 @@ def run_fwi(args):
     accepted iterations per second, the misfit history and the model error."""
     import torch
 
-    import oracle
     from paper_1712_08743_gb300 import _lib, api, build
     from synth import models
 
@@ -651,9 +699,7 @@ def run_fwi(args):
     ctx = api.Context(0, stream)
     true, start = models.c4_models()
     om = true.omegas
-    d_obs = np.stack([oracle.sample_receivers(
-        oracle.solve_fields(true.slowness, true.h, w, true.sources, true.npml, true.alpha_max), true.receivers,
-        true.npml) for w in om])
+    d_obs = observed_data(api, ctx, true)
     opts = dict(tol=1e-6, precision="mixed")
     lam = 1e-3
     bounds = (1 / 4500.0, 1 / 1400.0)
@@ -720,11 +766,65 @@ def run_ablation(args):
     ctx.close()
 
 
-def run_serving(args):
-    """A Poisson stream of requests of mixed grid sizes and frequencies (ten points per
-    wavelength at 1500 m/s), served with continuous batching; p50/p99 latency and
-    solves/s, beside the same requests solved one at a time in plain FP64."""
+def serve_stream(api, ctx, n: int, sizes, opts, rate: float, seed: int = 5):
+    """Submits serving requests 0..n-1 (each generated just before it is due) at Poisson
+    arrivals of `rate` per second (rate <= 0: all at once) through helm_submit; a poller
+    thread collects every result in submission order (helm_poll) and releases it. Returns
+    per-request records and the wall time from the first submission to the last completion."""
+    import queue
     import threading as th
+
+    from synth import models
+
+    q = queue.Queue()
+    recs = [None] * n
+    t_sub = [0.0] * n
+
+    def poller():
+        for _ in range(n):
+            i, t, N, f = q.get()
+            res = api.helm_poll(ctx, t, -1, copy_u=False)
+            recs[i] = {"N": N, "f_hz": f, "status": int(res.status), "latency_ms": res.latency_ms,
+                       "queue_ms": res.queue_ms, "batch": res.batch_size, "iters": res.stats["iters"],
+                       "relres": res.stats["relres"], "shift_switched": res.stats["shift_switched"]}
+            api.helm_release(ctx, t)
+
+    pt = th.Thread(target=poller)
+    pt.start()
+    rng = np.random.default_rng(seed)
+    t0 = time.perf_counter()
+    due = t0
+    for i in range(n):
+        r = models.c5_request(i, sizes=sizes)
+        if rate > 0:
+            due += rng.exponential(1.0 / rate)
+            time.sleep(max(0.0, due - time.perf_counter()))
+        t_sub[i] = time.perf_counter()
+        t = api.helm_submit(ctx, r.slowness, r.h, r.omegas[0], r.sources[0], opts=opts)
+        q.put((i, t, int(r.Px), float(r.omegas[0] / (2 * np.pi))))
+    pt.join()
+    t_end = max(t_sub[i] + 1e-3 * recs[i]["latency_ms"] for i in range(n))
+    return recs, t_end - t0
+
+
+def serve_summary(recs, wall):
+    lat = [r["latency_ms"] for r in recs]
+    return {"requests": len(recs), "solves_per_s": len(recs) / wall, "wall_s": wall,
+            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "converged": sum(r["status"] == 0 for r in recs),
+            "shift_switched": sum(bool(r["shift_switched"]) for r in recs),
+            "mean_batch": float(np.mean([r["batch"] for r in recs])),
+            "not_ok": [r for r in recs if r["status"] != 0]}
+
+
+def run_serving(args):
+    """The serving workload: a Poisson stream of solve requests of mixed grid sizes (128^2 ..
+    1024^2) and frequencies (2..25 Hz, ten points per wavelength at 1500 m/s) on random layered
+    models, served with continuous batching. First the saturated throughput (requests submitted
+    all at once), then one stream per arrival rate rho x saturated (--rates), each reporting
+    solves/s and p50/p99 latency; beside them the same kind of requests solved one after another
+    in plain FP64 (--seq-requests of them)."""
+    import torch
 
     from paper_1712_08743_gb300 import _lib, api, build
     from synth import models
@@ -732,44 +832,46 @@ def run_serving(args):
     build.build()
     ctx = api.Context(0)
     sizes = tuple(int(x) for x in args.serve_sizes.split(","))
-    reqs = [models.c5_request(i, sizes=sizes) for i in range(args.requests)]
     kry = _lib.HELM_KRYLOV_FGMRES if args.krylov == "fgmres" else _lib.HELM_KRYLOV_BICGSTAB
     shift = {} if args.serve_beta2 is None else dict(beta2=args.serve_beta2)
     opts = dict(tol=1e-6, precision="mixed", krylov=kry, max_it=20000, reorth=REORTH[args.reorth], **shift)
-    # sequential plain FP64 on a subset
-    o64 = dict(tol=1e-6, precision="fp64", max_it=20000, **shift)
+    api.helm_serve_config(ctx, max_batch=16, max_slots=4)
+    # warm-up: one request of each size through the server
+    for N in sizes:
+        warm = models.c5_request(0, sizes=(N,))
+        t = api.helm_submit(ctx, warm.slowness, warm.h, warm.omegas[0], warm.sources[0], opts=opts)
+        api.helm_poll(ctx, t, -1, copy_u=False)
+        api.helm_release(ctx, t)
+    # saturated throughput: every request queued at once
+    nsat = min(args.requests, args.sat_requests)
+    recs, wall = serve_stream(api, ctx, nsat, sizes, opts, rate=0.0)
+    sat = serve_summary(recs, wall)
+    rows = []
+    for rho in (float(x) for x in args.rates.split(",")):
+        rate = rho * sat["solves_per_s"] if args.rate <= 0 else args.rate
+        with ClockSampler(0) as clk:
+            recs, wall = serve_stream(api, ctx, args.requests, sizes, opts, rate=rate)
+        row = {"rho": rho, "arrival_rate": rate, **serve_summary(recs, wall), "clocks": clk.summary()}
+        rows.append(row)
+    # sequential plain FP64 of the first requests of the same stream
+    o64 = dict(tol=1e-6, precision="fp64", krylov=kry, max_it=20000, reorth=REORTH[args.reorth], **shift)
     t_seq = []
-    for r in reqs[: min(8, len(reqs))]:
+    for i in range(min(args.seq_requests, args.requests)):
+        r = models.c5_request(i, sizes=sizes)
         mm = api.helm_create_model(ctx, r.slowness, r.h)
+        torch.cuda.synchronize()
         t0 = time.perf_counter()
         api.helm_solve(mm, r.omegas, r.sources, opts=o64)
         t_seq.append(time.perf_counter() - t0)
         mm.close()
-    seq_rate = 1.0 / float(np.mean(t_seq))
-    rate = args.rate if args.rate > 0 else 0.8 * 4 * seq_rate
-    api.helm_serve_config(ctx, max_batch=16, max_slots=4)
-    rng = np.random.default_rng(5)
-    gaps = rng.exponential(1.0 / rate, len(reqs))
-    tickets = []
-    t_start = time.perf_counter()
-    for r, g in zip(reqs, gaps):
-        time.sleep(g)
-        tickets.append(api.helm_submit(ctx, r.slowness, r.h, r.omegas[0], r.sources[0], opts=opts))
-    res = [api.helm_poll(ctx, t, -1) for t in tickets]
-    t_total = time.perf_counter() - t_start
-    lat = [x.latency_ms for x in res]
-    print(json.dumps({"metric": "helmholtz_solves_per_s", "workload": f"serving_{len(reqs)}req_{min(sizes)}-{max(sizes)}",
+    seq = {"requests": len(t_seq), "solves_per_s": len(t_seq) / float(np.sum(t_seq)),
+           "p50_ms": 1e3 * float(np.percentile(t_seq, 50)), "p99_ms": 1e3 * float(np.percentile(t_seq, 99))}
+    print(json.dumps({"metric": "helmholtz_solves_per_s",
+                      "workload": f"serving_{args.requests}req_{min(sizes)}-{max(sizes)}",
                       "krylov": args.krylov, "shift": [1.0, args.serve_beta2 if args.serve_beta2 is not None else 0.5],
-                      "value": len(reqs) / t_total, "unit": "solves/s", "p50_ms": float(np.percentile(lat, 50)),
-                      "p99_ms": float(np.percentile(lat, 99)), "arrival_rate": rate,
-                      "sequential_fp64_solves_per_s": seq_rate,
-                      "ok": sum(x.status == 0 for x in res), "mean_batch": float(np.mean([x.batch_size for x in res])),
-                      "sizes": {str(n): sum(r.slowness.shape[0] == n for r in reqs) for n in sizes},
-                      "not_ok": [{"N": int(r.slowness.shape[0]), "f_hz": float(r.omegas[0] / (2 * np.pi)),
-                                  "status": int(x.status), **x.stats} for r, x in zip(reqs, res) if x.status != 0]}),
-          flush=True)
-    for t in tickets:
-        api.helm_release(ctx, t)
+                      "unit": "solves/s", "saturated": sat, "rates": rows, "sequential_fp64": seq,
+                      "sizes": {str(n): sum(models.c5_request(i, sizes=sizes).Px == n for i in range(args.requests))
+                                for n in sizes} if args.requests <= 200 else None}), flush=True)
     ctx.close()
 
 

@@ -88,13 +88,17 @@ typedef enum { HELM_REORTH_ALWAYS = 0, HELM_REORTH_NEVER = 1, HELM_REORTH_IFNEED
  * with at most 1200 nodes exactly, by its dense inverse (computed once per solve
  * for each distinct model and frequency by block Gauss-Jordan, then applied by a
  * matrix-vector kernel); it needs beta2 != 0, which keeps every pivot away from
- * zero, and falls back to HELM_COARSE_TAIL otherwise. HELM_COARSE_TAIL runs the
- * levels from the first with at most 2048 (complex64) or 1024 (complex128) nodes
- * down to the coarsest as an F- or V-cycle in one block per right-hand side, in
- * shared memory, with a dense solve of the coarsest level only. Both are one
- * reading of "approximately invert the shifted Laplacian" (the paragraph after
- * Eq. 9); they change the iteration count, not the answer. */
-typedef enum { HELM_COARSE_AUTO = 0, HELM_COARSE_TAIL = 1 } helm_coarse;
+ * zero, and falls back to HELM_COARSE_TAIL otherwise. For complex64 batches of at
+ * most 8 right-hand sides it runs the F-cycle part of the cycle (from its start
+ * level down to the dense level) as one persistent cooperative kernel with a
+ * grid barrier between steps. HELM_COARSE_DENSE is the same cycle with one
+ * kernel launch per step. HELM_COARSE_TAIL runs the levels from the first with
+ * at most 2048 (complex64) or 1024 (complex128) nodes down to the coarsest as an
+ * F- or V-cycle in one block per right-hand side, in shared memory, with a dense
+ * solve of the coarsest level only. All are readings of "approximately invert
+ * the shifted Laplacian" (the paragraph after Eq. 9); they change the iteration
+ * count, not the answer, and AUTO and DENSE give the same numbers. */
+typedef enum { HELM_COARSE_AUTO = 0, HELM_COARSE_TAIL = 1, HELM_COARSE_DENSE = 2 } helm_coarse;
 
 typedef struct {
     double tol;          /* stop at ||f - B u||_2 / ||f||_2 <= tol, residual formed in FP64 */
@@ -367,14 +371,16 @@ int helm_profile_end(helm_profile_entry* out, int cap, int* n_out);
 int helm_vcycle_noalloc(helm_model* model, int nrhs, const double* omega, double beta1, double beta2,
                         double omega_jacobi, const void* r, void* z);
 
-/* Autotuner (no counterpart in the paper): times the two tile shapes of each
- * complex64 multigrid kernel on the grid levels of this model (finest-level
- * prolongation; Galerkin restriction and prolongation) for nrhs right-hand
- * sides at angular frequency omega, keeps the faster in the model, and writes
- * the choices to tiles_out (nullable): int[48], restriction tiles per level
- * then prolongation tiles per level, each 0 (smaller) or 1 (larger, the
- * default). helm_set_tiles applies a stored choice. Tile shapes change the
- * speed, not the arithmetic of a node (dot products may sum in another order). */
+/* Autotuner (no counterpart in the paper): times the tile shapes of each complex64
+ * multigrid kernel on the grid levels of this model for nrhs right-hand sides at
+ * angular frequency omega, keeps the fastest in the model, and writes the choices
+ * to tiles_out (nullable): int[48], restriction tiles per level then prolongation
+ * tiles per level. Galerkin levels: restriction 0..3 (coarse tiles 8x8, 16x8,
+ * 32x4, 8x16), prolongation 0..4 (fine tiles 16x8, 32x8, 64x4, 32x16, 128x2);
+ * the finest level's prolongation 0..1 (row segments of 16 or 32 rows); 1 is
+ * the default everywhere. helm_set_tiles applies a stored choice. Tile shapes
+ * change the speed, not the arithmetic of a node (dot products may sum in
+ * another order). */
 int helm_autotune(helm_model* model, int nrhs, double omega, int* tiles_out);
 int helm_set_tiles(helm_model* model, const int* tiles);
 

@@ -29,6 +29,7 @@ HELM_REORTH_NEVER = 1
 HELM_REORTH_IFNEEDED = 2
 HELM_COARSE_AUTO = 0
 HELM_COARSE_TAIL = 1
+HELM_COARSE_DENSE = 2
 HELM_KERNEL_APPLY = 0
 HELM_KERNEL_RESTRICT = 1
 HELM_KERNEL_PROLONG = 2

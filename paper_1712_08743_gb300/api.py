@@ -432,15 +432,16 @@ def helm_submit(ctx: Context, slowness, h, omega, src, npml=20, alpha_max=0.5, o
     return t.value
 
 
-def helm_poll(ctx: Context, ticket: int, timeout_ms: int = -1):
-    """ServedResult when done (the field array is copied out), None if still pending."""
+def helm_poll(ctx: Context, ticket: int, timeout_ms: int = -1, copy_u: bool = True):
+    """ServedResult when done (the field array is copied out unless copy_u is False), None if
+    still pending."""
     res = _lib.helm_result()
     st = ctx.lib.helm_poll(ctx.handle, C.c_uint64(ticket), int(timeout_ms), C.byref(res))
     if st in (_lib.HELM_PENDING, _lib.HELM_E_TIMEOUT):
         return None
     check(st, "helm_poll")
     u = None
-    if res.u:
+    if res.u and copy_u:
         n = res.nx * res.nz
         buf = (C.c_double * (2 * n)).from_address(res.u)
         u = np.frombuffer(buf, dtype=np.complex128, count=n).reshape(res.nz, res.nx).copy()

@@ -25,7 +25,7 @@ def default_cache_path() -> str:
 
 
 def cache_key(nx: int, nz: int, nrhs: int) -> str:
-    return f"{nx}x{nz}:b{nrhs}:c64"
+    return f"{nx}x{nz}:b{nrhs}:c64:shapes5"
 
 
 def load_cache(path: str) -> dict:

@@ -46,7 +46,7 @@ int check_opts(const helm_solve_opts& o) {
     if (!(o.inner_tol > 0.0) || o.inner_tol >= 1.0) return HELM_E_INVALID;
     if (o.precond != HELM_PRECOND_MG && o.precond != HELM_PRECOND_NONE) return HELM_E_INVALID;
     if (o.reorth < HELM_REORTH_ALWAYS || o.reorth > HELM_REORTH_IFNEEDED) return HELM_E_INVALID;
-    if (o.coarse != HELM_COARSE_AUTO && o.coarse != HELM_COARSE_TAIL) return HELM_E_INVALID;
+    if (o.coarse < HELM_COARSE_AUTO || o.coarse > HELM_COARSE_DENSE) return HELM_E_INVALID;
     return HELM_OK;
 }
 
@@ -399,8 +399,10 @@ int helm_autotune(helm_model* m, int nrhs, double omega, int* tiles_out) {
 
 int helm_set_tiles(helm_model* m, const int* tiles) {
     if (!m || !tiles) return HELM_E_INVALID;
-    for (int k = 0; k < 2 * kMaxLevels; ++k)
-        if (tiles[k] != 0 && tiles[k] != 1) return HELM_E_INVALID;
+    for (int k = 0; k < kMaxLevels; ++k)
+        if (tiles[k] < 0 || tiles[k] >= kRestrictTiles || tiles[kMaxLevels + k] < 0 ||
+            tiles[kMaxLevels + k] >= kProlongTiles || (k == 0 && tiles[kMaxLevels] > 1))
+            return HELM_E_INVALID;
     for (int l = 0; l < kMaxLevels; ++l) {
         m->tile_restrict[l] = tiles[l];
         m->tile_prolong[l] = tiles[kMaxLevels + l];
@@ -413,7 +415,7 @@ int vcycle_call(helm_model* m, int nrhs, const double* omega, double beta1, doub
                 int coarse, const void* r, void* z, int device_ptrs) {
     if (!m || nrhs < 1 || !omega || !r || !z) return HELM_E_INVALID;
     if (!std::isfinite(beta1) || !std::isfinite(beta2) || !(omega_jacobi > 0.0)) return HELM_E_INVALID;
-    if (coarse != HELM_COARSE_AUTO && coarse != HELM_COARSE_TAIL) return HELM_E_INVALID;
+    if (coarse < HELM_COARSE_AUTO || coarse > HELM_COARSE_DENSE) return HELM_E_INVALID;
     std::vector<double> w2(nrhs);
     for (int b = 0; b < nrhs; ++b) {
         if (!finite_pos(omega[b])) return HELM_E_INVALID;

@@ -110,6 +110,37 @@ __device__ __forceinline__ bool rhs_active(const RhsState* st, int b) { return s
 __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
+// ------------------------------------------------ barrier of co-resident blocks
+// For kernels launched cooperatively (every block resident at once). Thread 0 of
+// each block makes the block's writes visible, counts the block in on *bar and
+// waits until *bar reaches `target` (the monotone count of arrivals: phase *
+// number of blocks). The wait is bounded: it gives up when another block has
+// reported a failure in *err, or after `spins` naps of 32 ns, setting *err = 1.
+// Returns false in every thread of the block when the kernel must stop.
+__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ bool coop_barrier(unsigned* bar, unsigned target, int* err, unsigned spins) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        atomicAdd(bar, 1u);
+        int ok = 1;
+        for (unsigned k = 0;; ++k) {
+            if (ld_acquire_gpu(bar) >= target) break;
+            if (*reinterpret_cast<const volatile int*>(err) != 0) { ok = 0; break; }
+            if (k >= spins) { atomicExch(err, 1); ok = 0; break; }
+            __nanosleep(32);
+        }
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
 // -------------------------------------------------------------- reductions
 __device__ __forceinline__ int lin_tid() { return threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z); }
 __device__ __forceinline__ int lin_nthreads() { return blockDim.x * blockDim.y * blockDim.z; }

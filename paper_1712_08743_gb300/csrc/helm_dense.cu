@@ -29,14 +29,8 @@ namespace {
 
 constexpr int kDenseThreads = 256;
 constexpr int kDenseMaxW = 16;                 // widest column strip (panel) a block owns
-constexpr unsigned kBarrierSpins = 4000000u;   // bounded wait of one strip barrier (with 64 ns naps)
+constexpr unsigned kBarrierSpins = 8000000u;   // bounded wait of one strip barrier (32 ns naps)
 
-__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
-    unsigned v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-__device__ __forceinline__ int ld_volatile_i32(const int* p) { return *reinterpret_cast<const volatile int*>(p); }
 
 // Coherent (L2) loads of values another block wrote in this launch.
 __device__ __forceinline__ cx<float> ldcg_c(const float* p, size_t i) {
@@ -46,30 +40,6 @@ __device__ __forceinline__ cx<float> ldcg_c(const float* p, size_t i) {
 __device__ __forceinline__ cx<double> ldcg_c(const double* p, size_t i) {
     const double2 v = __ldcg(reinterpret_cast<const double2*>(p) + i);
     return {v.x, v.y};
-}
-
-// Barrier of the S blocks that invert one matrix. Thread 0 makes the block's
-// writes visible, counts the block in and waits (bounded) until `target`
-// blocks have arrived; it gives up when another block reported a failure in
-// *err or after kBarrierSpins naps (then it sets *err = 1). Returns false in
-// every thread of the block when the inversion must stop.
-__device__ bool strip_barrier(unsigned* bar, unsigned target, int* err) {
-    __shared__ int s_ok;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        __threadfence();
-        atomicAdd(bar, 1u);
-        int ok = 1;
-        for (unsigned spin = 0;; ++spin) {
-            if (ld_acquire_u32(bar) >= target) break;
-            if (ld_volatile_i32(err) != 0) { ok = 0; break; }
-            if (spin >= kBarrierSpins) { atomicExch(err, 1); ok = 0; break; }
-            __nanosleep(64);
-        }
-        s_ok = ok;
-    }
-    __syncthreads();
-    return s_ok != 0;
 }
 
 // Entry (i, j) of the level's shifted-Laplace matrix: the coefficient of u_j in
@@ -185,7 +155,7 @@ __global__ void __launch_bounds__(kDenseThreads) k_dense_invert(int nx, int nz, 
                 stc(dv, (size_t)buf * W * W + p * W + q, Ds[p * W + q]);
             }
         }
-        if (!strip_barrier(sbar, (unsigned)((k + 1) * S), err)) return;
+        if (!coop_barrier(sbar, (unsigned)((k + 1) * S), err, kBarrierSpins)) return;
         const T* C = pan + 2 * ((size_t)buf * n * W);
         if (s != k) {
             for (int idx = tid; idx < wk * wk; idx += nth) {

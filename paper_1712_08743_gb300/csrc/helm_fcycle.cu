@@ -1,0 +1,199 @@
+// helm_fcycle.cu - the F-cycle part of the multigrid preconditioner in one
+// persistent kernel.
+//
+// From the F-cycle start level ls down to the level ld that the dense inverse
+// solves, a preconditioner application is a chain of about twenty dependent
+// steps on small grids (restriction, F-cycle correction + restriction,
+// prolongation + smoothing, dense coarse solve). Launched one kernel per step,
+// each step pays a kernel launch and completion on the critical path; here the
+// whole chain runs in one cooperative launch whose blocks stay resident and
+// separate the steps with a grid barrier. Each block holds two groups of 128
+// threads; a group works on one tile of a step at a time (the tile bodies of
+// helm_gal_tiles.cuh, with named-barrier synchronisation), and all of a
+// block's warps share the rows of the dense solve. Vectors written within the
+// launch are read through L2. The arithmetic of every node is that of the
+// one-launch-per-level kernels, so the results are the same.
+#include <algorithm>
+#include <functional>
+
+#include "helm_gal_tiles.cuh"
+#include "helm_internal.h"
+#include "helm_solver.h"
+
+namespace helm {
+
+namespace {
+
+constexpr int kFcThreads = 256;                 // two tile groups of 128 threads
+constexpr int kFcGroup = 128;
+constexpr int kFcRCX = 16;                      // restriction: 16 x 8 coarse nodes per tile
+constexpr int kFcPX = 16;                       // prolongation: 16 x 8 fine nodes per tile (128 threads each)
+constexpr unsigned kFcSpins = 2000000u;         // bounded wait of one step barrier (32 ns naps)
+
+constexpr int kFcRCZ = 8, kFcPZ = 8;
+
+template <typename T>
+union FcGroupSmem {
+    RestrictTile<T, kFcRCX, kFcRCZ> r;
+    ProlongTile<T, kFcPX, kFcPZ> p;
+};
+
+template <typename T>
+__global__ void __launch_bounds__(kFcThreads, 2) k_fcycle(const __grid_constant__ FcArgs a, const RhsState* st) {
+    extern __shared__ __align__(16) unsigned char fc_smem[];
+    const int g = threadIdx.x / kFcGroup, gtid = threadIdx.x - g * kFcGroup;
+    FcGroupSmem<T>& sm = reinterpret_cast<FcGroupSmem<T>*>(fc_smem)[g];
+    const GroupSync gsync{1 + g, kFcGroup};
+    const int gid = blockIdx.x * 2 + g, ngr = gridDim.x * 2;
+    const T* hw = static_cast<const T*>(a.hw);
+    const T b1 = (T)a.b1, b2 = (T)a.b2, wj = (T)a.wj;
+    for (int k = 0; k < a.nops; ++k) {
+        const int op = a.ops[k], type = op & 15, acc = (op & FC_ACC) ? 1 : 0, l = op >> 8;
+        if (type == FC_RESTRICT || type == FC_CORRECT_RESTRICT) {
+            const LevelDev& Lf = a.lv[l];
+            const LevelDev& Lc = a.lv[l + 1];
+            const int tx = (Lc.nx + kFcRCX - 1) / kFcRCX, tz = (Lc.nz + kFcRCZ - 1) / kFcRCZ;
+            const int per = tx * tz, nt = per * a.nrhs;
+            const T* f = static_cast<const T*>(a.f[l]);
+            const T* ec = static_cast<const T*>(a.e[l + 1]);
+            T* fc = static_cast<T*>(a.f[l + 1]);
+            for (int t = gid; t < nt; t += ngr) {
+                const int b = t / per, r = t - b * per, by = r / tx, bx = r - by * tx;
+                if (!rhs_active(st, b)) continue;
+                restrict_tile_stage<T, kFcRCX, kFcRCZ>(sm.r, Lf, bx, by, b, hw[b], b1, b2, gtid);
+                if (type == FC_CORRECT_RESTRICT)
+                    restrict_tile_work<T, true, kFcRCX, kFcRCZ, true>(sm.r, Lf, Lc, wj, f, ec, fc, bx, by, b, gtid,
+                                                                      gsync);
+                else
+                    restrict_tile_work<T, false, kFcRCX, kFcRCZ, true>(sm.r, Lf, Lc, wj, f, ec, fc, bx, by, b, gtid,
+                                                                       gsync);
+                gsync();   // the next tile's staging overwrites this tile's shared memory
+            }
+        } else if (type == FC_PROLONG) {
+            const LevelDev& Lf = a.lv[l];
+            const LevelDev& Lc = a.lv[l + 1];
+            const int tx = (Lf.nx + kFcPX - 1) / kFcPX, tz = (Lf.nz + kFcPZ - 1) / kFcPZ;
+            const int per = tx * tz, nt = per * a.nrhs;
+            const T* f = static_cast<const T*>(a.f[l]);
+            const T* ec = static_cast<const T*>(a.e[l + 1]);
+            T* out = static_cast<T*>(a.e[l]);
+            for (int t = gid; t < nt; t += ngr) {
+                const int b = t / per, r = t - b * per, by = r / tx, bx = r - by * tx;
+                if (!rhs_active(st, b)) continue;
+                prolong_tile_stage<T, kFcPX, kFcPZ>(sm.p, Lf, bx, by, b, hw[b], b1, b2, gtid);
+                prolong_tile_work<T, kFcPX, kFcPZ, true>(sm.p, Lf, Lc, wj, f, ec, out, acc, bx, by, b, gtid, gsync);
+                gsync();
+            }
+        } else if (type == FC_DENSE) {
+            // e (+)= M_d^-1 f, one warp per row; each block stages the group's right-hand sides
+            const int n = a.lv[l].nx * a.lv[l].nz;
+            const T* fl = static_cast<const T*>(a.f[l]);
+            T* el = static_cast<T*>(a.e[l]);
+            cx<T>* fs = reinterpret_cast<cx<T>*>(fc_smem);
+            const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+            for (int gg = 0; gg < a.ngroups; ++gg) {
+                const int r0 = a.grp[gg], nb = a.grp[gg + 1] - r0;
+                __syncthreads();
+                for (int idx = threadIdx.x; idx < nb * n; idx += blockDim.x)
+                    fs[idx] = ldv<true>(fl, (size_t)r0 * n + idx);
+                __syncthreads();
+                const T* Mb = static_cast<const T*>(a.minv) + 2 * (size_t)a.slot[r0] * n * n;
+                for (int row = blockIdx.x * 8 + warp; row < n; row += gridDim.x * 8) {
+                    T are[8], aim[8];
+#pragma unroll
+                    for (int r = 0; r < 8; ++r) { are[r] = T(0); aim[r] = T(0); }
+                    for (int j = lane; j < n; j += 32) {
+                        const cx<T> m = ldc(Mb, (size_t)row * n + j);
+#pragma unroll
+                        for (int r = 0; r < 8; ++r) {
+                            if (r >= nb) break;
+                            const cx<T> v = fs[(size_t)r * n + j];
+                            are[r] += m.re * v.re - m.im * v.im;
+                            aim[r] += m.re * v.im + m.im * v.re;
+                        }
+                    }
+#pragma unroll
+                    for (int r = 0; r < 8; ++r) {
+                        if (r >= nb) break;
+#pragma unroll
+                        for (int o = 16; o > 0; o >>= 1) {
+                            are[r] += __shfl_xor_sync(0xffffffffu, are[r], o);
+                            aim[r] += __shfl_xor_sync(0xffffffffu, aim[r], o);
+                        }
+                        const int b = r0 + r;
+                        if (lane == 0 && rhs_active(st, b)) {
+                            cx<T> v(are[r], aim[r]);
+                            if (acc) v = v + ldv<true>(el, (size_t)b * n + row);
+                            stc(el, (size_t)b * n + row, v);
+                        }
+                    }
+                }
+            }
+        }
+        // the next step reads what this one wrote anywhere on the grid
+        if (k + 1 < a.nops && !coop_barrier(a.bar, (unsigned)((k + 1) * gridDim.x), a.err, kFcSpins)) return;
+    }
+}
+
+size_t fc_smem_bytes() { return 2 * sizeof(FcGroupSmem<float>); }
+
+}  // namespace
+
+// Schedule of one cycle at level l (F or V) down to the dense level ld, with the
+// F-cycle from level lf: the order of mg_cycle's launches.
+std::vector<int> fcycle_schedule(int l, int lf, int ld, bool F, int acc) {
+    std::vector<int> ops;
+    std::function<void(int, bool, int)> cyc = [&](int q, bool f, int a) {
+        if (q == ld) { ops.push_back(FC_DENSE | (a ? FC_ACC : 0) | (q << 8)); return; }
+        ops.push_back(FC_RESTRICT | (q << 8));
+        cyc(q + 1, f || (q + 1 == lf), 0);
+        if (f) {
+            ops.push_back(FC_CORRECT_RESTRICT | (q << 8));
+            cyc(q + 1, false, 1);
+        }
+        ops.push_back(FC_PROLONG | (a ? FC_ACC : 0) | (q << 8));
+    };
+    cyc(l, F, acc);
+    return ops;
+}
+
+// Blocks of the cooperative launch: two per SM when they fit, else what the
+// occupancy allows (0: the kernel cannot run cooperatively here).
+int fcycle_grid(int dense_n, int maxg) {
+    static const int per_sm = [] {
+        cudaFuncSetAttribute(k_fcycle<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fc_smem_bytes());
+        int nb = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_fcycle<float>, kFcThreads, fc_smem_bytes()) !=
+            cudaSuccess) {
+            cudaGetLastError();
+            return 0;
+        }
+        return nb;
+    }();
+    // the dense step stages the group's right-hand sides in the same shared memory
+    if ((size_t)dense_n * maxg * sizeof(float2) > fc_smem_bytes()) return 0;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return std::min(per_sm, 2) * sms;
+}
+
+cudaError_t launch_fcycle(const FcArgs& a, int grid, const RhsState* st, cudaStream_t s) {
+    ProfScope prof(PK_FCYCLE, a.lv[a.ops[0] >> 8].nx, a.lv[a.ops[0] >> 8].nz, a.bytes, s);
+    cudaError_t e = cudaMemsetAsync(a.bar, 0, sizeof(unsigned), s);
+    if (e != cudaSuccess) return e;
+    // a cooperative launch (all blocks resident together), in a form that stream capture accepts
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(kFcThreads);
+    cfg.dynamicSmemBytes = fc_smem_bytes();
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_fcycle<float>, a, st);
+}
+
+}  // namespace helm

@@ -1,0 +1,326 @@
+// helm_gal_tiles.cuh - tile bodies of the Galerkin multigrid levels, shared by
+// the one-launch-per-level kernels (k_restrict_g, k_prolong_g in
+// helm_kernels.cu) and the persistent F-cycle kernel (helm_fcycle.cu).
+//
+// A tile is worked on by a group of threads (a whole block, or a fixed part of
+// one) that synchronises with a Sync policy: BlockSync (__syncthreads) or
+// GroupSync (a named barrier of the group's threads). Each tile body has two
+// halves: stage, which reads only model data (the Galerkin coefficients) and
+// may run before the data of the previous step is ready, and work, which reads
+// the level vectors. Vectors written earlier in the same kernel launch (the
+// persistent kernel) must be read through L2 (COH = true, ld.global.cg); the
+// one-launch kernels read them through the non-coherent path.
+#pragma once
+
+#include "helm_internal.h"
+
+namespace helm {
+
+struct BlockSync {
+    __device__ __forceinline__ void operator()() const { __syncthreads(); }
+};
+// named barrier `id` (1..15) of `nthreads` threads (a multiple of 32)
+struct GroupSync {
+    int id, nthreads;
+    __device__ __forceinline__ void operator()() const {
+        asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+    }
+};
+
+template <bool COH>
+__device__ __forceinline__ cx<float> ldv(const float* p, size_t i) {
+    if constexpr (COH) {
+        const float2 v = __ldcg(reinterpret_cast<const float2*>(p) + i);
+        return {v.x, v.y};
+    } else {
+        return ldc(p, i);
+    }
+}
+template <bool COH>
+__device__ __forceinline__ cx<double> ldv(const double* p, size_t i) {
+    if constexpr (COH) {
+        const double2 v = __ldcg(reinterpret_cast<const double2*>(p) + i);
+        return {v.x, v.y};
+    } else {
+        return ldc(p, i);
+    }
+}
+
+// Bilinear prolongation along one axis at fine index g (coarse node I sits on
+// fine 2I+1): odd g takes coarse (g-1)/2 with weight 1, even g takes g/2-1 and
+// g/2 with weight 1/2 each. Branch-free: a = (g-1)>>1, b = g>>1 (arithmetic
+// shift, so g = 0 gives a = -1).
+template <typename T>
+__device__ __forceinline__ void bil_axis(int g, int& a, int& b, T& wa, T& wb) {
+    const bool odd = g & 1;
+    a = (g - 1) >> 1;
+    b = g >> 1;
+    wa = odd ? T(1) : T(0.5);
+    wb = odd ? T(0) : T(0.5);
+}
+
+// ================================ Galerkin grid levels: staged coefficients
+// On the coarse grid levels the 9-point coefficients would otherwise be read
+// one by one per stencil evaluation, serialising each tile on memory latency.
+// The tiles first stage, cooperatively and coalesced, the per-RHS complex
+// coefficients M_k = G_k - hw (b1 - j b2) K_k of their region into shared
+// memory, then work from there.
+template <typename T, int W, int H>
+struct GalTile {
+    cx<T> c[5][H][W];   // centre, east, north, north-east, north-west
+};
+
+template <typename T, int W, int H>
+__device__ __forceinline__ void stage_gal(GalTile<T, W, H>& t, const LevelDev& L, int b, T hb1, T hb2, int gx0,
+                                          int gz0, int tid, int nt) {
+    const T* gk = static_cast<const T*>(L.gk) + (size_t)b * L.gkstride;
+    const size_t n = (size_t)L.nx * L.nz;
+    // one node per iteration, its ten coefficients loaded independently
+    for (int idx = tid; idx < W * H; idx += nt) {
+        const int lz = idx / W, lx = idx - lz * W;
+        const int gx = gx0 + lx, gz = gz0 + lz;
+        T g[5], q[5];
+        const bool in = gx >= 0 && gx < L.nx && gz >= 0 && gz < L.nz;
+        const size_t i = in ? (size_t)gz * L.nx + gx : 0;
+#pragma unroll
+        for (int k = 0; k < 5; ++k) {
+            g[k] = in ? __ldg(gk + (size_t)k * n + i) : T(0);
+            q[k] = in ? __ldg(gk + (size_t)(5 + k) * n + i) : T(0);
+        }
+#pragma unroll
+        for (int k = 0; k < 5; ++k) t.c[k][lz][lx] = cx<T>(g[k] - hb1 * q[k], hb2 * q[k]);
+    }
+}
+
+// M u at tile point (lx, lz) (global (gx, gz)); U row pitch W; coefficients of
+// the neighbours come from the staged tile (the point must not lie on the
+// tile border).
+template <typename T, int W, int H>
+__device__ __forceinline__ cx<T> mop9_staged(const GalTile<T, W, H>& t, int nx, int nz, int gx, int gz, int lx, int lz,
+                                             const cx<T>* U) {
+    cx<T> acc = t.c[0][lz][lx] * U[0];
+    const bool e = gx + 1 < nx, w = gx > 0, no = gz + 1 < nz, so = gz > 0;
+    if (e) acc = acc + t.c[1][lz][lx] * U[1];
+    if (w) acc = acc + t.c[1][lz][lx - 1] * U[-1];
+    if (no) acc = acc + t.c[2][lz][lx] * U[W];
+    if (so) acc = acc + t.c[2][lz - 1][lx] * U[-W];
+    if (no && e) acc = acc + t.c[3][lz][lx] * U[W + 1];
+    if (so && w) acc = acc + t.c[3][lz - 1][lx - 1] * U[-W - 1];
+    if (no && w) acc = acc + t.c[4][lz][lx] * U[W - 1];
+    if (so && e) acc = acc + t.c[4][lz - 1][lx + 1] * U[-W + 1];
+    return acc;
+}
+
+// Default tiles of the Galerkin kernels: restriction coarse tile RCX x RCZ,
+// prolongation fine tile PX x PZ; halved in x for complex128 to stay within 48 KB
+// of static shared memory. The complex64 kernels also come in the other shapes of
+// kGalTiles (helm_kernels.cu), among which the autotuner chooses per level.
+template <typename T> struct GTile {
+    static constexpr int RCX = sizeof(T) == 4 ? 16 : 8, RCZ = 8;
+    static constexpr int PX = sizeof(T) == 4 ? 32 : 16, PZ = 8;
+};
+
+// ------------------------------------------------------------ restriction
+// Coarse tile (I0, K0) of GRCX x GRCZ nodes, GRCX * GRCZ threads: from the fine
+// level's right-hand side f (zero initial guess), one damped-Jacobi sweep
+// u1 = wj D^-1 f (CORRECT: u2 = wj D^-1 f + P e, e the first coarse correction of
+// an F-cycle), the residual r = f - M u on the fine region, and its restriction
+// P^T r (full weighting times 4) to the coarse tile.
+template <typename T, int GRCX, int GRCZ_ = GTile<T>::RCZ>
+struct RestrictTile {
+    static constexpr int GRCZ = GRCZ_;
+    static constexpr int GRFW = 2 * GRCX + 3, GRFH = 2 * GRCZ + 3;
+    static constexpr int CEW = GRCX + 2, CEH = GRCZ + 2;
+    static constexpr int NT = GRCX * GRCZ;
+    GalTile<T, GRFW, GRFH> C;
+    cx<T> F[GRFH][GRFW];
+    cx<T> U[GRFH][GRFW];
+    cx<T> E[CEH][CEW];
+};
+
+template <typename T, int GRCX, int GRCZ>
+__device__ __forceinline__ void restrict_tile_stage(RestrictTile<T, GRCX, GRCZ>& sm, const LevelDev& Lf, int bx,
+                                                    int by, int b, T hw, T b1, T b2, int tid) {
+    using RT = RestrictTile<T, GRCX, GRCZ>;
+    const int I0 = bx * GRCX, K0 = by * RT::GRCZ;
+    stage_gal<T, RT::GRFW, RT::GRFH>(sm.C, Lf, b, hw * b1, hw * b2, 2 * I0 - 1, 2 * K0 - 1, tid, RT::NT);
+}
+
+template <typename T, bool CORRECT, int GRCX, int GRCZ, bool COH, class Sync>
+__device__ __forceinline__ void restrict_tile_work(RestrictTile<T, GRCX, GRCZ>& sm, const LevelDev& Lf,
+                                                   const LevelDev& Lc, T wj, const T* f, const T* ec, T* fc, int bx,
+                                                   int by, int b, int tid, Sync sync) {
+    using RT = RestrictTile<T, GRCX, GRCZ>;
+    constexpr int GRFW = RT::GRFW, GRFH = RT::GRFH, CEW = RT::CEW, CEH = RT::CEH;
+    const int I0 = bx * GRCX, K0 = by * GRCZ;
+    const int gx0 = 2 * I0 - 1, gz0 = 2 * K0 - 1;
+    const size_t nf = (size_t)Lf.nx * Lf.nz, nc = (size_t)Lc.nx * Lc.nz;
+    const T* fb = f + 2 * nf * b;
+    // this thread's points of the fine region; their right-hand side is loaded
+    // before, and independently of, the coarse correction
+    constexpr int NT = RT::NT, NF = GRFW * GRFH, NPT = (NF + NT - 1) / NT;
+    cx<T> fpre[NPT];
+#pragma unroll
+    for (int k = 0; k < NPT; ++k) {
+        const int idx = tid + k * NT;
+        const int lz = idx / GRFW, lx = idx - lz * GRFW;
+        const int gx = gx0 + lx, gz = gz0 + lz;
+        fpre[k] = (idx < NF && gx >= 0 && gx < Lf.nx && gz >= 0 && gz < Lf.nz)
+                      ? ldv<COH>(fb, (size_t)gz * Lf.nx + gx) : cx<T>(0, 0);
+    }
+    if (CORRECT) {
+        const T* eb = ec + 2 * nc * b;
+        for (int idx = tid; idx < CEW * CEH; idx += NT) {
+            const int lz = idx / CEW, lx = idx - lz * CEW;
+            const int I = I0 - 1 + lx, K = K0 - 1 + lz;
+            cx<T> e(0, 0);
+            if (I >= 0 && I < Lc.nx && K >= 0 && K < Lc.nz) e = ldv<COH>(eb, (size_t)K * Lc.nx + I);
+            sm.E[lz][lx] = e;
+        }
+    }
+    sync();
+#pragma unroll
+    for (int k = 0; k < NPT; ++k) {
+        const int idx = tid + k * NT;
+        if (idx >= NF) break;
+        const int lz = idx / GRFW, lx = idx - lz * GRFW;
+        const int gx = gx0 + lx, gz = gz0 + lz;
+        const cx<T> fv = fpre[k];
+        cx<T> uv(0, 0);
+        if (gx >= 0 && gx < Lf.nx && gz >= 0 && gz < Lf.nz) {
+            uv = wj * cdiv(fv, sm.C.c[0][lz][lx]);
+            if (CORRECT) {
+                int ia, ib, ka, kb;
+                T wa, wb, va, vb;
+                bil_axis<T>(gx, ia, ib, wa, wb);
+                bil_axis<T>(gz, ka, kb, va, vb);
+                ia -= I0 - 1; ib -= I0 - 1; ka -= K0 - 1; kb -= K0 - 1;
+                uv = uv + (va * wa) * sm.E[ka][ia] + (va * wb) * sm.E[ka][ib] + (vb * wa) * sm.E[kb][ia] +
+                     (vb * wb) * sm.E[kb][ib];
+            }
+        }
+        sm.F[lz][lx] = fv;
+        sm.U[lz][lx] = uv;
+    }
+    sync();
+    constexpr int W2 = GRFW - 2, H2 = GRFH - 2;
+    for (int idx = tid; idx < W2 * H2; idx += NT) {
+        const int lz = 1 + idx / W2, lx = 1 + idx % W2;
+        const int gx = gx0 + lx, gz = gz0 + lz;
+        cx<T> r(0, 0);
+        if (gx < Lf.nx && gz < Lf.nz)
+            r = sm.F[lz][lx] - mop9_staged<T, GRFW, GRFH>(sm.C, Lf.nx, Lf.nz, gx, gz, lx, lz, &sm.U[lz][lx]);
+        sm.F[lz][lx] = r;
+    }
+    sync();
+    const int cxl = tid % GRCX, czl = tid / GRCX;
+    const int I = I0 + cxl, K = K0 + czl;
+    if (I < Lc.nx && K < Lc.nz) {
+        const int lx = 2 * cxl + 2, lz = 2 * czl + 2;
+        cx<T> a = T(4) * sm.F[lz][lx];
+        a = a + T(2) * (sm.F[lz][lx - 1] + sm.F[lz][lx + 1] + sm.F[lz - 1][lx] + sm.F[lz + 1][lx]);
+        a = a + sm.F[lz - 1][lx - 1] + sm.F[lz - 1][lx + 1] + sm.F[lz + 1][lx - 1] + sm.F[lz + 1][lx + 1];
+        stc(fc + 2 * nc * b, (size_t)K * Lc.nx + I, T(0.25) * a);
+    }
+}
+
+// ----------------------------------------------------------- prolongation
+// Fine tile (x0, z0) of GPX x GPZ nodes, GPX * GPZ threads: u = wj D^-1 f + P e
+// on the tile and its halo, then the post-smoothing sweep u + wj D^-1 (f - M u),
+// written to out (added to it when accumulating).
+template <typename T, int GPX, int GPZ_ = GTile<T>::PZ>
+struct ProlongTile {
+    static constexpr int GPZ = GPZ_;
+    static constexpr int RW = GPX + 2, RH = GPZ + 2;
+    static constexpr int EW = GPX / 2 + 2, EH = GPZ / 2 + 2;
+    static constexpr int NT = GPX * GPZ;
+    GalTile<T, RW, RH> C;
+    cx<T> F[RH][RW];
+    cx<T> U2[RH][RW];
+    cx<T> E[EH][EW];
+};
+
+template <typename T, int GPX, int GPZ>
+__device__ __forceinline__ void prolong_tile_stage(ProlongTile<T, GPX, GPZ>& sm, const LevelDev& Lf, int bx, int by,
+                                                   int b, T hw, T b1, T b2, int tid) {
+    using PT = ProlongTile<T, GPX, GPZ>;
+    stage_gal<T, PT::RW, PT::RH>(sm.C, Lf, b, hw * b1, hw * b2, bx * GPX - 1, by * PT::GPZ - 1, tid, PT::NT);
+}
+
+template <typename T, int GPX, int GPZ, bool COH, class Sync>
+__device__ __forceinline__ void prolong_tile_work(ProlongTile<T, GPX, GPZ>& sm, const LevelDev& Lf, const LevelDev& Lc,
+                                                  T wj, const T* f, const T* ec, T* out, int accumulate, int bx,
+                                                  int by, int b, int tid, Sync sync) {
+    using PT = ProlongTile<T, GPX, GPZ>;
+    constexpr int RW = PT::RW, RH = PT::RH, EW = PT::EW, EH = PT::EH;
+    const int x0 = bx * GPX, z0 = by * GPZ;
+    const int gx0 = x0 - 1, gz0 = z0 - 1;
+    const int cx0 = x0 / 2 - 1, cz0 = z0 / 2 - 1;
+    const size_t nf = (size_t)Lf.nx * Lf.nz, nc = (size_t)Lc.nx * Lc.nz;
+    const T* fb = f + 2 * nf * b;
+    const T* eb = ec + 2 * nc * b;
+    // this thread's points of the fine region; their right-hand side is loaded
+    // before, and independently of, the coarse correction
+    constexpr int NT = PT::NT, NF = RW * RH, NPT = (NF + NT - 1) / NT;
+    cx<T> fpre[NPT];
+#pragma unroll
+    for (int k = 0; k < NPT; ++k) {
+        const int idx = tid + k * NT;
+        const int lz = idx / RW, lx = idx - lz * RW;
+        const int gx = gx0 + lx, gz = gz0 + lz;
+        fpre[k] = (idx < NF && gx >= 0 && gx < Lf.nx && gz >= 0 && gz < Lf.nz)
+                      ? ldv<COH>(fb, (size_t)gz * Lf.nx + gx) : cx<T>(0, 0);
+    }
+    // the output point this thread accumulates into (one per thread), loaded with them
+    T* ob = out + 2 * nf * b;
+    cx<T> opre(0, 0);
+    {
+        const int tz = tid / GPX, tx = tid - tz * GPX;
+        if (accumulate && x0 + tx < Lf.nx && z0 + tz < Lf.nz) {
+            const size_t i = (size_t)(z0 + tz) * Lf.nx + x0 + tx;
+            opre = COH ? ldv<true>(ob, i) : ldcc(ob, i);
+        }
+    }
+    for (int idx = tid; idx < EW * EH; idx += NT) {
+        const int lz = idx / EW, lx = idx - lz * EW;
+        const int I = cx0 + lx, K = cz0 + lz;
+        cx<T> e(0, 0);
+        if (I >= 0 && I < Lc.nx && K >= 0 && K < Lc.nz) e = ldv<COH>(eb, (size_t)K * Lc.nx + I);
+        sm.E[lz][lx] = e;
+    }
+    sync();
+#pragma unroll
+    for (int k = 0; k < NPT; ++k) {
+        const int idx = tid + k * NT;
+        if (idx >= NF) break;
+        const int lz = idx / RW, lx = idx - lz * RW;
+        const int gx = gx0 + lx, gz = gz0 + lz;
+        const cx<T> fv = fpre[k];
+        cx<T> u(0, 0);
+        if (gx >= 0 && gx < Lf.nx && gz >= 0 && gz < Lf.nz) {
+            u = wj * cdiv(fv, sm.C.c[0][lz][lx]);
+            int ia, ib, ka, kb;
+            T wa, wb, va, vb;
+            bil_axis<T>(gx, ia, ib, wa, wb);
+            bil_axis<T>(gz, ka, kb, va, vb);
+            ia -= cx0; ib -= cx0; ka -= cz0; kb -= cz0;
+            u = u + (va * wa) * sm.E[ka][ia] + (va * wb) * sm.E[ka][ib] + (vb * wa) * sm.E[kb][ia] +
+                (vb * wb) * sm.E[kb][ib];
+        }
+        sm.F[lz][lx] = fv;
+        sm.U2[lz][lx] = u;
+    }
+    sync();
+    const int tz = tid / GPX, tx = tid - tz * GPX;   // one output point per thread
+    const int gx = x0 + tx, gz = z0 + tz;
+    if (gx < Lf.nx && gz < Lf.nz) {
+        const int lx = tx + 1, lz = tz + 1;
+        const size_t i = (size_t)gz * Lf.nx + gx;
+        const cx<T> c = sm.U2[lz][lx];
+        const cx<T> mu = mop9_staged<T, RW, RH>(sm.C, Lf.nx, Lf.nz, gx, gz, lx, lz, &sm.U2[lz][lx]);
+        const cx<T> v = c + wj * cdiv(sm.F[lz][lx] - mu, sm.C.c[0][lz][lx]);
+        stc(ob, i, accumulate ? opre + v : v);
+    }
+}
+
+}  // namespace helm

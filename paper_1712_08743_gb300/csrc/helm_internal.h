@@ -26,6 +26,10 @@ constexpr int kTailMaxPoints32 = 2048;
 constexpr int kTailMaxPoints64 = 1024;
 constexpr int kMaxLevels = 24;
 constexpr int kMaxRestart = 32;
+// tile-shape choices of the complex64 Galerkin kernels (launch_prolong_g / launch_restrict_g);
+// 1 is the default shape
+constexpr int kProlongTiles = 5;
+constexpr int kRestrictTiles = 4;
 constexpr int kGalerkinCoefs = 10;
 // the first level with at most this many nodes is solved exactly by its dense inverse
 // (few right-hand sides; see helm_dense.cu)
@@ -142,7 +146,7 @@ enum ProfKernel : int {
     PK_APPLY, PK_APPLY_DOTS, PK_RESID64, PK_REFINE, PK_BICG_INIT, PK_BICG_RESUME, PK_BICG_P, PK_BICG_S, PK_BICG_XR,
     PK_RESTRICT, PK_PROLONG, PK_RESTRICT_G, PK_CORRECT_RESTRICT, PK_PROLONG_G, PK_TAIL, PK_COARSE_DENSE,
     PK_DENSE_INVERT, PK_COARSE_INVERT, PK_FG_NORM, PK_FG_SCALE, PK_FG_DOTS, PK_FG_AXPY, PK_FG_FINISH,
-    PK_FG_BACKSOLVE, PK_FG_UPDATE, PK_OTHER, PK_COUNT
+    PK_FG_BACKSOLVE, PK_FG_UPDATE, PK_FCYCLE, PK_OTHER, PK_COUNT
 };
 bool prof_on();
 class ProfScope {
@@ -290,6 +294,32 @@ void launch_coarse_dense(int n, const T* minv, const int* slot, const int* grp, 
                          T* e, int accumulate, const RhsState* st, cudaStream_t s);
 void launch_coarse_invert(const LevelDev& Lc, const double* w2_slots, const int* mod_slots, int nslots,
                           double b1, double b2, double2* work, float2* minv_f, double2* minv_d, cudaStream_t s);
+
+// Persistent F-cycle (helm_fcycle.cu): the steps of one cycle from level ls down
+// to the dense level, in one cooperative launch. Step: type | FC_ACC (add to the
+// output) | level << 8.
+constexpr int kFcMaxOps = 96;
+constexpr int kFcMaxRhs = 8;      // right-hand sides a batch may have for the persistent path
+enum FcOpType : int { FC_RESTRICT = 1, FC_CORRECT_RESTRICT = 2, FC_PROLONG = 3, FC_DENSE = 4, FC_ACC = 16 };
+struct FcArgs {
+    int nops, nrhs;
+    int ops[kFcMaxOps];
+    LevelDev lv[kMaxLevels];
+    void* f[kMaxLevels];      // per level: right-hand side and correction [nrhs][n_l] (complex64)
+    void* e[kMaxLevels];
+    const void* hw;           // (h_0 omega_b)^2 per RHS, FP32
+    double b1, b2, wj;
+    const void* minv;         // dense inverses of level ld, [nslots][n][n]
+    const int* slot;
+    const int* grp;           // groups of consecutive right-hand sides sharing a slot
+    int ngroups, maxg;
+    unsigned* bar;            // step barrier counter (cleared before each launch)
+    int* err;                 // set to 1 when a barrier wait gave up
+    double bytes;             // algorithmic bytes of one launch (profiling)
+};
+std::vector<int> fcycle_schedule(int l, int lf, int ld, bool F, int acc);
+int fcycle_grid(int dense_n, int maxg);
+cudaError_t launch_fcycle(const FcArgs& a, int grid, const RhsState* st, cudaStream_t s);
 
 // FGMRES state on the device, per RHS: Hessenberg H [(m+1) x m], rotated
 // right-hand side g [m+1], Givens cosines cs / sines sn [m], solution y [m],

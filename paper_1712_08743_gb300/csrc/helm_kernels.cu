@@ -11,6 +11,7 @@
 #include <functional>
 #include <vector>
 
+#include "helm_gal_tiles.cuh"
 #include "helm_internal.h"
 
 namespace helm {
@@ -694,19 +695,6 @@ void launch_bicg_xr(T* x, const T* ph, const T* shv, const T* sv, const T* t, co
                nactive, n);
 }
 
-// Bilinear prolongation along one axis at fine index g (coarse node I sits on
-// fine 2I+1): odd g takes coarse (g-1)/2 with weight 1, even g takes g/2-1 and
-// g/2 with weight 1/2 each. Branch-free: a = (g-1)>>1, b = g>>1 (arithmetic
-// shift, so g = 0 gives a = -1).
-template <typename T>
-__device__ __forceinline__ void bil_axis(int g, int& a, int& b, T& wa, T& wb) {
-    const bool odd = g & 1;
-    a = (g - 1) >> 1;
-    b = g >> 1;
-    wa = odd ? T(1) : T(0.5);
-    wb = odd ? T(0) : T(0.5);
-}
-
 // ===================================================== Galerkin operators
 // Complex coefficient of stored stencil entry k (0 centre, 1 east, 2 north,
 // 3 north-east, 4 north-west) at node i: G_k - hw (b1 - j b2) K_k.
@@ -858,236 +846,87 @@ void launch_galerkin(const helm_model* m, int l, cudaStream_t s) {
                                                               kGalerkinCoefs * F.n(), C.gkd, C.gkf, C.nx, C.nz);
 }
 
-// ================================ Galerkin grid levels: staged coefficients
-// On the coarse grid levels the 9-point coefficients would otherwise be read
-// one by one per stencil evaluation, serialising each block on memory latency.
-// These kernels first stage, cooperatively and coalesced, the per-RHS complex
-// coefficients M_k = G_k - hw (b1 - j b2) K_k of their tile region into shared
-// memory, then work from there. Smaller tiles give the small grids more blocks.
-template <typename T, int W, int H>
-struct GalTile {
-    cx<T> c[5][H][W];   // centre, east, north, north-east, north-west
-};
-
-template <typename T, int W, int H>
-__device__ __forceinline__ void stage_gal(GalTile<T, W, H>& t, const LevelDev& L, int b, T hb1, T hb2, int gx0,
-                                          int gz0) {
-    const T* gk = static_cast<const T*>(L.gk) + (size_t)b * L.gkstride;
-    const size_t n = (size_t)L.nx * L.nz;
-    // one node per iteration, its ten coefficients loaded independently
-    for (int idx = threadIdx.x; idx < W * H; idx += blockDim.x) {
-        const int lz = idx / W, lx = idx - lz * W;
-        const int gx = gx0 + lx, gz = gz0 + lz;
-        T g[5], q[5];
-        const bool in = gx >= 0 && gx < L.nx && gz >= 0 && gz < L.nz;
-        const size_t i = in ? (size_t)gz * L.nx + gx : 0;
-#pragma unroll
-        for (int k = 0; k < 5; ++k) {
-            g[k] = in ? __ldg(gk + (size_t)k * n + i) : T(0);
-            q[k] = in ? __ldg(gk + (size_t)(5 + k) * n + i) : T(0);
-        }
-#pragma unroll
-        for (int k = 0; k < 5; ++k) t.c[k][lz][lx] = cx<T>(g[k] - hb1 * q[k], hb2 * q[k]);
-    }
-}
-
-// M u at tile point (lx, lz) (global (gx, gz)); U row pitch W; coefficients of
-// the neighbours come from the staged tile (the point must not lie on the
-// tile border).
-template <typename T, int W, int H>
-__device__ __forceinline__ cx<T> mop9_staged(const GalTile<T, W, H>& t, int nx, int nz, int gx, int gz, int lx, int lz,
-                                             const cx<T>* U) {
-    cx<T> acc = t.c[0][lz][lx] * U[0];
-    const bool e = gx + 1 < nx, w = gx > 0, no = gz + 1 < nz, so = gz > 0;
-    if (e) acc = acc + t.c[1][lz][lx] * U[1];
-    if (w) acc = acc + t.c[1][lz][lx - 1] * U[-1];
-    if (no) acc = acc + t.c[2][lz][lx] * U[W];
-    if (so) acc = acc + t.c[2][lz - 1][lx] * U[-W];
-    if (no && e) acc = acc + t.c[3][lz][lx] * U[W + 1];
-    if (so && w) acc = acc + t.c[3][lz - 1][lx - 1] * U[-W - 1];
-    if (no && w) acc = acc + t.c[4][lz][lx] * U[W - 1];
-    if (so && e) acc = acc + t.c[4][lz - 1][lx + 1] * U[-W + 1];
-    return acc;
-}
-
-// Tiles of the Galerkin kernels: restriction coarse tile GRCX x GRCZ, prolongation
-// fine tile GPX x GPZ; halved in x for complex128 to stay within 48 KB of static
-// shared memory.
-template <typename T> struct GTile {
-    static constexpr int RCX = sizeof(T) == 4 ? 16 : 8, RCZ = 8;
-    static constexpr int PX = sizeof(T) == 4 ? 32 : 16, PZ = 8;
-};
+// ================================ Galerkin grid levels: one launch per level
+// Tile bodies in helm_gal_tiles.cuh; each block is one tile of one right-hand
+// side. The coefficient staging reads only model data, so it runs before the
+// wait on the previous kernel (programmatic dependent launch).
 
 // restriction (CORRECT = false: zero-guess smoothing; true: u2 = wj D^-1 f + P e)
-template <typename T, bool CORRECT, int GRCX>
-__global__ void __launch_bounds__(128) k_restrict_g(LevelDev Lf, LevelDev Lc, const T* __restrict__ hwv, T b1, T b2,
-                                                    T wj, const T* __restrict__ f, const T* __restrict__ ec,
-                                                    T* __restrict__ fc, const RhsState* st) {
-    constexpr int GRCZ = GTile<T>::RCZ;
-    constexpr int GRFW = 2 * GRCX + 3, GRFH = 2 * GRCZ + 3;
-    constexpr int CEW = GRCX + 2, CEH = GRCZ + 2;
-    __shared__ GalTile<T, GRFW, GRFH> C;
-    __shared__ cx<T> F[GRFH][GRFW];
-    __shared__ cx<T> U[GRFH][GRFW];
-    __shared__ cx<T> E[CORRECT ? CEH : 1][CORRECT ? CEW : 1];
+template <typename T, bool CORRECT, int GRCX, int GRCZ>
+__global__ void __launch_bounds__(GRCX * GRCZ) k_restrict_g(LevelDev Lf, LevelDev Lc, const T* __restrict__ hwv, T b1,
+                                                            T b2, T wj, const T* __restrict__ f,
+                                                            const T* __restrict__ ec, T* __restrict__ fc,
+                                                            const RhsState* st) {
+    __shared__ RestrictTile<T, GRCX, GRCZ> sm;
     pdl_trigger();
     const int b = blockIdx.z;
-    const int I0 = blockIdx.x * GRCX, K0 = blockIdx.y * GRCZ;
-    const int gx0 = 2 * I0 - 1, gz0 = 2 * K0 - 1;
-    const T hw = hwv[b];
-    stage_gal<T, GRFW, GRFH>(C, Lf, b, hw * b1, hw * b2, gx0, gz0);   // model data only
+    restrict_tile_stage<T, GRCX, GRCZ>(sm, Lf, blockIdx.x, blockIdx.y, b, hwv[b], b1, b2, threadIdx.x);   // model data
     pdl_wait();
     if (!rhs_active(st, b)) return;
-    const size_t nf = (size_t)Lf.nx * Lf.nz, nc = (size_t)Lc.nx * Lc.nz;
-    const T* fb = f + 2 * nf * b;
-    // this thread's points of the fine region (blockDim.x == GRCX * GRCZ); their
-    // right-hand side is loaded before, and independently of, the coarse correction
-    constexpr int NT = GRCX * GRCZ, NF = GRFW * GRFH, NPT = (NF + NT - 1) / NT;
-    cx<T> fpre[NPT];
-#pragma unroll
-    for (int k = 0; k < NPT; ++k) {
-        const int idx = threadIdx.x + k * NT;
-        const int lz = idx / GRFW, lx = idx - lz * GRFW;
-        const int gx = gx0 + lx, gz = gz0 + lz;
-        fpre[k] = (idx < NF && gx >= 0 && gx < Lf.nx && gz >= 0 && gz < Lf.nz) ? ldc(fb, (size_t)gz * Lf.nx + gx)
-                                                                              : cx<T>(0, 0);
-    }
-    if (CORRECT) {
-        const T* eb = ec + 2 * nc * b;
-        for (int idx = threadIdx.x; idx < CEW * CEH; idx += blockDim.x) {
-            const int lz = idx / CEW, lx = idx - lz * CEW;
-            const int I = I0 - 1 + lx, K = K0 - 1 + lz;
-            cx<T> e(0, 0);
-            if (I >= 0 && I < Lc.nx && K >= 0 && K < Lc.nz) e = ldc(eb, (size_t)K * Lc.nx + I);
-            E[lz][lx] = e;
-        }
-    }
-    __syncthreads();
-#pragma unroll
-    for (int k = 0; k < NPT; ++k) {
-        const int idx = threadIdx.x + k * NT;
-        if (idx >= NF) break;
-        const int lz = idx / GRFW, lx = idx - lz * GRFW;
-        const int gx = gx0 + lx, gz = gz0 + lz;
-        const cx<T> fv = fpre[k];
-        cx<T> uv(0, 0);
-        if (gx >= 0 && gx < Lf.nx && gz >= 0 && gz < Lf.nz) {
-            uv = wj * cdiv(fv, C.c[0][lz][lx]);
-            if (CORRECT) {
-                int ia, ib, ka, kb;
-                T wa, wb, va, vb;
-                bil_axis<T>(gx, ia, ib, wa, wb);
-                bil_axis<T>(gz, ka, kb, va, vb);
-                ia -= I0 - 1; ib -= I0 - 1; ka -= K0 - 1; kb -= K0 - 1;
-                uv = uv + (va * wa) * E[ka][ia] + (va * wb) * E[ka][ib] + (vb * wa) * E[kb][ia] + (vb * wb) * E[kb][ib];
-            }
-        }
-        F[lz][lx] = fv;
-        U[lz][lx] = uv;
-    }
-    __syncthreads();
-    constexpr int W2 = GRFW - 2, H2 = GRFH - 2;
-    for (int idx = threadIdx.x; idx < W2 * H2; idx += blockDim.x) {
-        const int lz = 1 + idx / W2, lx = 1 + idx % W2;
-        const int gx = gx0 + lx, gz = gz0 + lz;
-        cx<T> r(0, 0);
-        if (gx < Lf.nx && gz < Lf.nz) r = F[lz][lx] - mop9_staged<T, GRFW, GRFH>(C, Lf.nx, Lf.nz, gx, gz, lx, lz, &U[lz][lx]);
-        F[lz][lx] = r;
-    }
-    __syncthreads();
-    const int cxl = threadIdx.x % GRCX, czl = threadIdx.x / GRCX;
-    const int I = I0 + cxl, K = K0 + czl;
-    if (I < Lc.nx && K < Lc.nz) {
-        const int lx = 2 * cxl + 2, lz = 2 * czl + 2;
-        cx<T> a = T(4) * F[lz][lx];
-        a = a + T(2) * (F[lz][lx - 1] + F[lz][lx + 1] + F[lz - 1][lx] + F[lz + 1][lx]);
-        a = a + F[lz - 1][lx - 1] + F[lz - 1][lx + 1] + F[lz + 1][lx - 1] + F[lz + 1][lx + 1];
-        stc(fc + 2 * nc * b, (size_t)K * Lc.nx + I, T(0.25) * a);
-    }
+    restrict_tile_work<T, CORRECT, GRCX, GRCZ, false>(sm, Lf, Lc, wj, f, ec, fc, blockIdx.x, blockIdx.y, b,
+                                                      threadIdx.x, BlockSync{});
 }
 
-template <typename T, int GPX>
-__global__ void __launch_bounds__(256) k_prolong_g(LevelDev Lf, LevelDev Lc, const T* __restrict__ hwv, T b1, T b2,
-                                                   T wj, const T* __restrict__ f, const T* __restrict__ ec,
-                                                   T* __restrict__ out, const RhsState* st, int accumulate) {
-    constexpr int GPZ = GTile<T>::PZ;
-    constexpr int RW = GPX + 2, RH = GPZ + 2;
-    constexpr int EW = GPX / 2 + 2, EH = GPZ / 2 + 2;
-    __shared__ GalTile<T, RW, RH> C;
-    __shared__ cx<T> F[RH][RW];
-    __shared__ cx<T> U2[RH][RW];
-    __shared__ cx<T> E[EH][EW];
+template <typename T, int GPX, int GPZ>
+__global__ void __launch_bounds__(GPX * GPZ) k_prolong_g(LevelDev Lf, LevelDev Lc, const T* __restrict__ hwv, T b1,
+                                                         T b2, T wj, const T* __restrict__ f, const T* __restrict__ ec,
+                                                         T* __restrict__ out, const RhsState* st, int accumulate) {
+    __shared__ ProlongTile<T, GPX, GPZ> sm;
     pdl_trigger();
     const int b = blockIdx.z;
-    const int x0 = blockIdx.x * GPX, z0 = blockIdx.y * GPZ;
-    const int gx0 = x0 - 1, gz0 = z0 - 1;
-    const int cx0 = x0 / 2 - 1, cz0 = z0 / 2 - 1;
-    const T hw = hwv[b];
-    stage_gal<T, RW, RH>(C, Lf, b, hw * b1, hw * b2, gx0, gz0);   // model data only
+    prolong_tile_stage<T, GPX, GPZ>(sm, Lf, blockIdx.x, blockIdx.y, b, hwv[b], b1, b2, threadIdx.x);   // model data
     pdl_wait();
     if (!rhs_active(st, b)) return;
-    const size_t nf = (size_t)Lf.nx * Lf.nz, nc = (size_t)Lc.nx * Lc.nz;
-    const T* fb = f + 2 * nf * b;
-    const T* eb = ec + 2 * nc * b;
-    // this thread's points of the fine region (blockDim.x == GPX * GPZ); their
-    // right-hand side is loaded before, and independently of, the coarse correction
-    constexpr int NT = GPX * GPZ, NF = RW * RH, NPT = (NF + NT - 1) / NT;
-    cx<T> fpre[NPT];
-#pragma unroll
-    for (int k = 0; k < NPT; ++k) {
-        const int idx = threadIdx.x + k * NT;
-        const int lz = idx / RW, lx = idx - lz * RW;
-        const int gx = gx0 + lx, gz = gz0 + lz;
-        fpre[k] = (idx < NF && gx >= 0 && gx < Lf.nx && gz >= 0 && gz < Lf.nz) ? ldc(fb, (size_t)gz * Lf.nx + gx)
-                                                                              : cx<T>(0, 0);
-    }
-    // the output point this thread accumulates into (one per thread), loaded with them
-    T* ob = out + 2 * nf * b;
-    cx<T> opre(0, 0);
-    {
-        const int tz = threadIdx.x / GPX, tx = threadIdx.x - tz * GPX;
-        if (accumulate && x0 + tx < Lf.nx && z0 + tz < Lf.nz) opre = ldcc(ob, (size_t)(z0 + tz) * Lf.nx + x0 + tx);
-    }
-    for (int idx = threadIdx.x; idx < EW * EH; idx += blockDim.x) {
-        const int lz = idx / EW, lx = idx - lz * EW;
-        const int I = cx0 + lx, K = cz0 + lz;
-        cx<T> e(0, 0);
-        if (I >= 0 && I < Lc.nx && K >= 0 && K < Lc.nz) e = ldc(eb, (size_t)K * Lc.nx + I);
-        E[lz][lx] = e;
-    }
-    __syncthreads();
-#pragma unroll
-    for (int k = 0; k < NPT; ++k) {
-        const int idx = threadIdx.x + k * NT;
-        if (idx >= NF) break;
-        const int lz = idx / RW, lx = idx - lz * RW;
-        const int gx = gx0 + lx, gz = gz0 + lz;
-        const cx<T> fv = fpre[k];
-        cx<T> u(0, 0);
-        if (gx >= 0 && gx < Lf.nx && gz >= 0 && gz < Lf.nz) {
-            u = wj * cdiv(fv, C.c[0][lz][lx]);
-            int ia, ib, ka, kb;
-            T wa, wb, va, vb;
-            bil_axis<T>(gx, ia, ib, wa, wb);
-            bil_axis<T>(gz, ka, kb, va, vb);
-            ia -= cx0; ib -= cx0; ka -= cz0; kb -= cz0;
-            u = u + (va * wa) * E[ka][ia] + (va * wb) * E[ka][ib] + (vb * wa) * E[kb][ia] + (vb * wb) * E[kb][ib];
+    prolong_tile_work<T, GPX, GPZ, false>(sm, Lf, Lc, wj, f, ec, out, accumulate, blockIdx.x, blockIdx.y, b,
+                                          threadIdx.x, BlockSync{});
+}
+
+// Tile shapes of the complex64 Galerkin kernels, by the code the autotuner stores
+// per level (kGalTiles choices; 1 is the default): restriction coarse tile
+// (x, z) and prolongation fine tile (x, z), one thread per node of the tile. The
+// shapes keep each block's shared memory within 48 KB.
+//   0: 8 x 8 / 16 x 8,  1: 16 x 8 / 32 x 8,  2: 32 x 4 / 64 x 4,  3: 8 x 16 / 32 x 16,  4: 16 x 8 / 128 x 2
+template <typename T, bool CORRECT, int GRCX, int GRCZ>
+void launch_restrict_g_shape(const LevelDev& Lf, const LevelDev& Lc, const T* w2, double b1, double b2, double wj,
+                             const T* f, const T* ec, T* fc, const RhsState* st, int nrhs, cudaStream_t s) {
+    dim3 grd((Lc.nx + GRCX - 1) / GRCX, (Lc.nz + GRCZ - 1) / GRCZ, nrhs);
+    launch_pdl(k_restrict_g<T, CORRECT, GRCX, GRCZ>, grd, dim3(GRCX * GRCZ), 0, s, Lf, Lc, w2, (T)b1, (T)b2, (T)wj,
+               f, ec, fc, st);
+}
+template <typename T, bool CORRECT>
+void launch_restrict_g(int tile, const LevelDev& Lf, const LevelDev& Lc, const T* w2, double b1, double b2, double wj,
+                       const T* f, const T* ec, T* fc, const RhsState* st, int nrhs, cudaStream_t s) {
+    if constexpr (sizeof(T) == 4) {
+        switch (tile) {
+            case 0: launch_restrict_g_shape<T, CORRECT, 8, 8>(Lf, Lc, w2, b1, b2, wj, f, ec, fc, st, nrhs, s); return;
+            case 2: launch_restrict_g_shape<T, CORRECT, 32, 4>(Lf, Lc, w2, b1, b2, wj, f, ec, fc, st, nrhs, s); return;
+            case 3: launch_restrict_g_shape<T, CORRECT, 8, 16>(Lf, Lc, w2, b1, b2, wj, f, ec, fc, st, nrhs, s); return;
+            default: break;
         }
-        F[lz][lx] = fv;
-        U2[lz][lx] = u;
     }
-    __syncthreads();
-    {
-        const int tz = threadIdx.x / GPX, tx = threadIdx.x - tz * GPX;   // one output point per thread
-        const int gx = x0 + tx, gz = z0 + tz;
-        if (gx >= Lf.nx || gz >= Lf.nz) return;
-        const int lx = tx + 1, lz = tz + 1;
-        const size_t i = (size_t)gz * Lf.nx + gx;
-        const cx<T> c = U2[lz][lx];
-        const cx<T> mu = mop9_staged<T, RW, RH>(C, Lf.nx, Lf.nz, gx, gz, lx, lz, &U2[lz][lx]);
-        const cx<T> v = c + wj * cdiv(F[lz][lx] - mu, C.c[0][lz][lx]);
-        stc(ob, i, accumulate ? opre + v : v);
+    launch_restrict_g_shape<T, CORRECT, GTile<T>::RCX, GTile<T>::RCZ>(Lf, Lc, w2, b1, b2, wj, f, ec, fc, st, nrhs, s);
+}
+template <typename T, int GPX, int GPZ>
+void launch_prolong_g_shape(const LevelDev& Lf, const LevelDev& Lc, const T* w2, double b1, double b2, double wj,
+                            const T* f, const T* ec, T* out, const RhsState* st, int nrhs, cudaStream_t s,
+                            int accumulate) {
+    dim3 grd((Lf.nx + GPX - 1) / GPX, (Lf.nz + GPZ - 1) / GPZ, nrhs);
+    launch_pdl(k_prolong_g<T, GPX, GPZ>, grd, dim3(GPX * GPZ), 0, s, Lf, Lc, w2, (T)b1, (T)b2, (T)wj, f, ec, out, st,
+               accumulate);
+}
+template <typename T>
+void launch_prolong_g(int tile, const LevelDev& Lf, const LevelDev& Lc, const T* w2, double b1, double b2, double wj,
+                      const T* f, const T* ec, T* out, const RhsState* st, int nrhs, cudaStream_t s, int accumulate) {
+    if constexpr (sizeof(T) == 4) {
+        switch (tile) {
+            case 0: launch_prolong_g_shape<T, 16, 8>(Lf, Lc, w2, b1, b2, wj, f, ec, out, st, nrhs, s, accumulate); return;
+            case 2: launch_prolong_g_shape<T, 64, 4>(Lf, Lc, w2, b1, b2, wj, f, ec, out, st, nrhs, s, accumulate); return;
+            case 3: launch_prolong_g_shape<T, 32, 16>(Lf, Lc, w2, b1, b2, wj, f, ec, out, st, nrhs, s, accumulate); return;
+            case 4: launch_prolong_g_shape<T, 128, 2>(Lf, Lc, w2, b1, b2, wj, f, ec, out, st, nrhs, s, accumulate); return;
+            default: break;
+        }
     }
+    launch_prolong_g_shape<T, GTile<T>::PX, GTile<T>::PZ>(Lf, Lc, w2, b1, b2, wj, f, ec, out, st, nrhs, s, accumulate);
 }
 
 // ======================================================== V-cycle: restrict
@@ -1237,16 +1076,8 @@ void launch_restrict(const LevelDev& Lf, const LevelDev& Lc, const T* w2, double
         const int ks = march_rows(cw, Lc.nz, nrhs, 16);
         dim3 grd((cw + 7) / 8, (Lc.nz + ks - 1) / ks, nrhs);
         launch_pdl(k_restrict<T>, grd, dim3(256), 0, s, Lf, Lc, w2, (T)b1, (T)b2, (T)wj, f, fc, st, ks);
-    } else if (sizeof(T) == 4 && tile == 0) {
-        constexpr int GRCX = 8, GRCZ = GTile<T>::RCZ;
-        dim3 grd((Lc.nx + GRCX - 1) / GRCX, (Lc.nz + GRCZ - 1) / GRCZ, nrhs);
-        launch_pdl(k_restrict_g<T, false, GRCX>, grd, dim3(GRCX * GRCZ), 0, s, Lf, Lc, w2, (T)b1, (T)b2, (T)wj, f,
-                   (const T*)nullptr, fc, st);
     } else {
-        constexpr int GRCX = GTile<T>::RCX, GRCZ = GTile<T>::RCZ;
-        dim3 grd((Lc.nx + GRCX - 1) / GRCX, (Lc.nz + GRCZ - 1) / GRCZ, nrhs);
-        launch_pdl(k_restrict_g<T, false, GRCX>, grd, dim3(GRCX * GRCZ), 0, s, Lf, Lc, w2, (T)b1, (T)b2, (T)wj, f,
-                   (const T*)nullptr, fc, st);
+        launch_restrict_g<T, false>(tile, Lf, Lc, w2, b1, b2, wj, f, (const T*)nullptr, fc, st, nrhs, s);
     }
 }
 
@@ -1502,22 +1333,10 @@ void launch_prolong(int mode, const LevelDev& Lf, const LevelDev& Lc, int npml, 
                        nf * sizeof(T) * (galk ? kGalerkinCoefs : 1) * ((galk ? Lf.gkstride : Lf.mstride) ? nrhs : 1),
                    s);
     const T ac = (T)layer_coef(npml, amax);
-    const bool small = sizeof(T) == 4 && tile == 0;
     // a density level is stored like a coarse one: only mode 0 exists there (the
     // caller applies A and forms the dots with launch_apply_dots)
     if (mode == 0 && (!Lf.m2 || Lf.rho)) {
-        constexpr int GPZ = GTile<T>::PZ;
-        if (small) {
-            constexpr int GPX = 16;
-            dim3 gg((Lf.nx + GPX - 1) / GPX, (Lf.nz + GPZ - 1) / GPZ, nrhs);
-            launch_pdl(k_prolong_g<T, GPX>, gg, dim3(GPX * GPZ), 0, s, Lf, Lc, w2, (T)b1, (T)b2, (T)wj, f, ec, out, st,
-                       accumulate);
-        } else {
-            constexpr int GPX = GTile<T>::PX;
-            dim3 gg((Lf.nx + GPX - 1) / GPX, (Lf.nz + GPZ - 1) / GPZ, nrhs);
-            launch_pdl(k_prolong_g<T, GPX>, gg, dim3(GPX * GPZ), 0, s, Lf, Lc, w2, (T)b1, (T)b2, (T)wj, f, ec, out, st,
-                       accumulate);
-        }
+        launch_prolong_g<T>(tile, Lf, Lc, w2, b1, b2, wj, f, ec, out, st, nrhs, s, accumulate);
         return;
     }
     // finest level: the tile choice is the longest row segment (16 or 32 rows)
@@ -2030,16 +1849,8 @@ void launch_correct_restrict(const LevelDev& Lf, const LevelDev& Lc, const T* w2
     if (Lf.m2 && !Lf.rho) {
         dim3 grd((Lc.nx + RCX - 1) / RCX, (Lc.nz + RCZ - 1) / RCZ, nrhs);
         k_correct_restrict<T, false><<<grd, RCX * RCZ, 0, s>>>(Lf, Lc, w2, (T)b1, (T)b2, (T)wj, f, ec, fc, st);
-    } else if (sizeof(T) == 4 && tile == 0) {
-        constexpr int GRCX = 8, GRCZ = GTile<T>::RCZ;
-        dim3 grd((Lc.nx + GRCX - 1) / GRCX, (Lc.nz + GRCZ - 1) / GRCZ, nrhs);
-        launch_pdl(k_restrict_g<T, true, GRCX>, grd, dim3(GRCX * GRCZ), 0, s, Lf, Lc, w2, (T)b1, (T)b2, (T)wj, f, ec, fc,
-                   st);
     } else {
-        constexpr int GRCX = GTile<T>::RCX, GRCZ = GTile<T>::RCZ;
-        dim3 grd((Lc.nx + GRCX - 1) / GRCX, (Lc.nz + GRCZ - 1) / GRCZ, nrhs);
-        launch_pdl(k_restrict_g<T, true, GRCX>, grd, dim3(GRCX * GRCZ), 0, s, Lf, Lc, w2, (T)b1, (T)b2, (T)wj, f, ec, fc,
-                   st);
+        launch_restrict_g<T, true>(tile, Lf, Lc, w2, b1, b2, wj, f, ec, fc, st, nrhs, s);
     }
 }
 template void launch_correct_restrict<float>(const LevelDev&, const LevelDev&, const float*, double, double, double,

@@ -105,7 +105,8 @@ extern "C" int helm_vcycle_noalloc(helm_model* m, int nrhs, const double* omega,
     const size_t o_grp = take(sizeof(int) * (ngroups + 1));
     const size_t common = off;
     struct Plan {
-        size_t minv = 0, work = 0, md = 0, panel = 0, dinv = 0, bar = 0, err = 0, f[kMaxLevels] = {}, e[kMaxLevels] = {};
+        size_t minv = 0, work = 0, md = 0, panel = 0, dinv = 0, bar = 0, err = 0, fbar = 0, ferr = 0;
+        size_t f[kMaxLevels] = {}, e[kMaxLevels] = {};
         int top = 0;
         size_t end = 0;
     };
@@ -120,6 +121,8 @@ extern "C" int helm_vcycle_noalloc(helm_model* m, int nrhs, const double* omega,
             p.dinv = take(sizeof(float2) * 2 * (size_t)W * W * nl);
             p.bar = take(sizeof(unsigned) * nl);
             p.err = take(sizeof(int));
+            p.fbar = take(sizeof(unsigned));   // the persistent F-cycle's barrier counter and error flag
+            p.ferr = take(sizeof(int));
             p.top = m->ld;
         } else {
             const size_t nc = m->lv[L].n();
@@ -213,8 +216,33 @@ extern "C" int helm_vcycle_noalloc(helm_model* m, int nrhs, const double* omega,
             B.f[l] = reinterpret_cast<float*>(base + plan.f[l]);
             B.e[l] = reinterpret_cast<float*>(base + plan.e[l]);
         }
-        mg_apply<float>(m, mc, B, static_cast<const float*>(r), static_cast<float*>(z), 0, nullptr, nullptr);
-        e = cudaGetLastError();
+        // as helm_vcycle: the F-cycle part as one persistent kernel where it applies
+        FcArgs fa;
+        if (use_dense) {
+            int* ferr = reinterpret_cast<int*>(base + plan.ferr);
+            e = cudaMemsetAsync(ferr, 0, sizeof(int), s);
+            const int grid = e == cudaSuccess ? fcycle_setup(m, mc, HELM_COARSE_AUTO, B.f, B.e,
+                                                             reinterpret_cast<unsigned*>(base + plan.fbar), ferr, &fa)
+                                              : 0;
+            if (grid > 0) {
+                mc.fca = &fa;
+                mc.fca_level = mc.lf;
+                mc.fca_grid = grid;
+            }
+        }
+        if (e == cudaSuccess)
+            mg_apply<float>(m, mc, B, static_cast<const float*>(r), static_cast<float*>(z), 0, nullptr, nullptr);
+        if (e == cudaSuccess) e = cudaGetLastError();
+        if (e == cudaSuccess && mc.fca) {
+            int herr = 0;
+            e = cudaMemcpyAsync(&herr, base + plan.ferr, sizeof(int), cudaMemcpyDeviceToHost, s);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+            if (e == cudaSuccess && herr != 0) {
+                if (cur != dev) cudaSetDevice(cur);
+                set_last_error("helm_vcycle_noalloc: a grid barrier wait of the persistent cycle gave up");
+                return HELM_E_CUDA;
+            }
+        }
     }
     // the host arrays above are the sources of the copies: wait before returning
     cudaError_t e2 = cudaStreamSynchronize(s);

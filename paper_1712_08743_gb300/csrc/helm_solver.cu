@@ -94,6 +94,8 @@ struct SolveCtx {
     int ld = 0;             // > 0: level solved exactly by its dense inverse (minv); 0: the tail path
     const int* grp = nullptr;
     int ngroups = 0, maxg = 0;
+    const FcArgs* fca = nullptr;    // persistent F-cycle kernel (complex64, few right-hand sides)
+    int fca_level = 0, fca_grid = 0;
     cudaStream_t side = nullptr;    // FGMRES: the Hessenberg column finish runs here
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 };
@@ -154,6 +156,10 @@ static void mg_cycle(const helm_model* m, const MgCall& c, const MgLevels<T>& B,
     NvtxRange nv(kLevelNames[l]);
     const bool dbl = sizeof(T) == 8;
     const T* hw = hw_of<T>(c);
+    if (c.fca && l == c.fca_level) {   // the whole cycle from here down in one persistent launch
+        launch_fcycle(*c.fca, c.fca_grid, c.st, c.s);
+        return;
+    }
     if (c.ld > 0 && l == c.ld) {   // exact solve of this level by its dense inverse
         launch_coarse_dense<T>((int)m->lv[l].n(), static_cast<const T*>(c.minv), c.slot, c.grp, c.ngroups, c.maxg,
                                B.f[l], B.e[l], acc, c.st, c.s);
@@ -205,14 +211,54 @@ template void mg_apply<float>(const helm_model*, const MgCall&, const MgLevels<f
 template void mg_apply<double>(const helm_model*, const MgCall&, const MgLevels<double>&, const double*, double*, int,
                                double*, const double*);
 
-static int count_cycle(const helm_model* m, int lt, int l, bool F, int lf, int ld) {
+static int count_cycle(const helm_model* m, int lt, int l, bool F, int lf, int ld, int fl = 0) {
+    if (fl > 0 && l == fl) return 1;
     if (ld > 0 ? l == ld : l >= lt) return 1;
-    int k = 2 + count_cycle(m, lt, l + 1, F || (l + 1 == lf), lf, ld);
-    if (F) k += 1 + count_cycle(m, lt, l + 1, false, lf, ld);
+    int k = 2 + count_cycle(m, lt, l + 1, F || (l + 1 == lf), lf, ld, fl);
+    if (F) k += 1 + count_cycle(m, lt, l + 1, false, lf, ld, fl);
     return k;
 }
-int mg_kernels_per_apply(const helm_model* m, bool dbl, int lf, int ld) {
-    return 2 + (m->vd ? 1 : 0) + count_cycle(m, m->tail_level(dbl), 1, lf == 1, lf, ld);
+int mg_kernels_per_apply(const helm_model* m, bool dbl, int lf, int ld, int fl) {
+    return 2 + (m->vd ? 1 : 0) + count_cycle(m, m->tail_level(dbl), 1, lf == 1, lf, ld, fl);
+}
+
+int fcycle_setup(const helm_model* m, const MgCall& c, int coarse, float* const* f, float* const* e, unsigned* bar,
+                 int* err, FcArgs* fa) {
+    if (coarse != HELM_COARSE_AUTO || c.ld <= 0 || c.nrhs > kFcMaxRhs || c.lf >= c.ld || !bar || !err) return 0;
+    const int nd = (int)m->lv[c.ld].n();
+    const int grid = fcycle_grid(nd, c.maxg);
+    if (grid <= 0) return 0;
+    const std::vector<int> ops = fcycle_schedule(c.lf, c.lf, c.ld, true, 0);
+    if ((int)ops.size() > kFcMaxOps) return 0;
+    std::memset(fa, 0, sizeof(*fa));
+    fa->nops = (int)ops.size();
+    fa->nrhs = c.nrhs;
+    double bytes = 0;
+    for (size_t k = 0; k < ops.size(); ++k) {
+        fa->ops[k] = ops[k];
+        const int type = ops[k] & 15, l = ops[k] >> 8, acc = (ops[k] & FC_ACC) ? 1 : 0;
+        const double n = (double)m->lv[l].n(), nc = l + 1 < (int)m->lv.size() ? (double)m->lv[l + 1].n() : 0.0;
+        const double coef = n * sizeof(float) * kGalerkinCoefs * (m->nmodels > 1 ? c.nrhs : 1);
+        if (type == FC_RESTRICT) bytes += (n + nc) * 8.0 * c.nrhs + coef;
+        else if (type == FC_CORRECT_RESTRICT) bytes += (n + 2 * nc) * 8.0 * c.nrhs + coef;
+        else if (type == FC_PROLONG) bytes += (n * (2 + acc) + nc) * 8.0 * c.nrhs + coef;
+        else bytes += n * n * 8.0 * c.ngroups + n * (2 + acc) * 8.0 * c.nrhs;
+    }
+    for (int l = 0; l < (int)m->lv.size(); ++l) fa->lv[l] = level_dev(m, l, false);
+    for (int l = 1; l <= c.ld; ++l) { fa->f[l] = f[l]; fa->e[l] = e[l]; }
+    fa->hw = c.w2f;
+    fa->b1 = c.b1;
+    fa->b2 = c.b2;
+    fa->wj = c.wj;
+    fa->minv = c.minv;
+    fa->slot = c.slot;
+    fa->grp = c.grp;
+    fa->ngroups = c.ngroups;
+    fa->maxg = c.maxg;
+    fa->bar = bar;
+    fa->err = err;
+    fa->bytes = bytes;
+    return grid;
 }
 
 int fcycle_level(const helm_model* m, const double* h_w2, int nrhs) {
@@ -224,8 +270,7 @@ int fcycle_level(const helm_model* m, const double* h_w2, int nrhs) {
     return m->lf;
 }
 
-template <typename T>
-static void vcycle(const SolveCtx& c, Inner<T>& w, const T* in, T* out, int mode, T* y, const T* aux) {
+static MgCall mgcall_of(const SolveCtx& c) {
     MgCall mc;
     mc.w2 = c.w2;
     mc.w2f = c.w2f;
@@ -244,6 +289,15 @@ static void vcycle(const SolveCtx& c, Inner<T>& w, const T* in, T* out, int mode
     mc.grp = c.grp;
     mc.ngroups = c.ngroups;
     mc.maxg = c.maxg;
+    mc.fca = c.fca;
+    mc.fca_level = c.fca_level;
+    mc.fca_grid = c.fca_grid;
+    return mc;
+}
+
+template <typename T>
+static void vcycle(const SolveCtx& c, Inner<T>& w, const T* in, T* out, int mode, T* y, const T* aux) {
+    MgCall mc = mgcall_of(c);
     MgLevels<T> B;
     std::memset(&B, 0, sizeof(B));
     const int top = c.ld > 0 ? c.ld : c.m->tail_level(sizeof(T) == 8);
@@ -252,6 +306,47 @@ static void vcycle(const SolveCtx& c, Inner<T>& w, const T* in, T* out, int mode
         B.e[l] = w.el[l]->template as<T>();
     }
     mg_apply<T>(c.m, mc, B, in, out, mode, y, aux);
+}
+
+// The persistent F-cycle of a complex64 batch, when it applies (see fcycle_setup):
+// fills fa, its barrier counter and error flag, and points c at it.
+template <typename T>
+static int setup_fcycle(SolveCtx& c, Inner<T>& w, int coarse, DBuf& bar, DBuf& err, FcArgs* fa) {
+    c.fca = nullptr;
+    if constexpr (sizeof(T) == 4) {
+        if (coarse != HELM_COARSE_AUTO || c.ld <= 0) return HELM_OK;
+        if (!bar.p) {
+            TRY_ALLOC(bar, sizeof(unsigned), c.s);
+            TRY_ALLOC(err, sizeof(int), c.s);
+            HELM_CUDA_TRY(cudaMemsetAsync(err.p, 0, sizeof(int), c.s));
+        }
+        float* f[kMaxLevels] = {};
+        float* e[kMaxLevels] = {};
+        for (int l = 1; l <= c.ld; ++l) {
+            f[l] = w.fl[l]->template as<float>();
+            e[l] = w.el[l]->template as<float>();
+        }
+        const int grid = fcycle_setup(c.m, mgcall_of(c), coarse, f, e, bar.as<unsigned>(), err.as<int>(), fa);
+        if (grid > 0) {
+            c.fca = fa;
+            c.fca_level = c.lf;
+            c.fca_grid = grid;
+        }
+    }
+    return HELM_OK;
+}
+
+// After a solve that used the persistent F-cycle: HELM_E_CUDA if one of its barrier waits gave up.
+static int check_fcycle(const SolveCtx& c, const DBuf& err) {
+    if (!c.fca || !err.p) return HELM_OK;
+    int h = 0;
+    HELM_CUDA_TRY(cudaMemcpyAsync(&h, err.p, sizeof(int), cudaMemcpyDeviceToHost, c.s));
+    HELM_CUDA_TRY(cudaStreamSynchronize(c.s));
+    if (h != 0) {
+        set_last_error("persistent multigrid cycle: a grid barrier wait gave up");
+        return HELM_E_CUDA;
+    }
+    return HELM_OK;
 }
 
 // level vectors of levels 1..top (top: the dense level, or the tail's first level)
@@ -284,8 +379,8 @@ static int alloc_inner(const SolveCtx& c, Inner<T>& w) {
 
 // kernels one BiCGSTAB iteration launches: p, s and x/r updates plus two
 // preconditioner applications
-static int kernels_per_iteration(const helm_model* m, bool dbl, int precond, int lf, int ld) {
-    return precond == HELM_PRECOND_NONE ? 5 : 3 + 2 * mg_kernels_per_apply(m, dbl, lf, ld);
+static int kernels_per_iteration(const helm_model* m, bool dbl, int precond, int lf, int ld, int fl) {
+    return precond == HELM_PRECOND_NONE ? 5 : 3 + 2 * mg_kernels_per_apply(m, dbl, lf, ld, fl);
 }
 
 template <typename T>
@@ -358,7 +453,7 @@ static int inner_solve(const SolveCtx& c, Inner<T>& w, const T* rin, cudaGraphEx
         } else {
             for (int k = 0; k < chunk; ++k) bicg_iteration<T>(c, w);
         }
-        count_launches((unsigned long long)chunk * kernels_per_iteration(c.m, sizeof(T) == 8, c.o.precond, c.lf, c.ld));
+        count_launches((unsigned long long)chunk * kernels_per_iteration(c.m, sizeof(T) == 8, c.o.precond, c.lf, c.ld, c.fca ? c.fca_level : 0));
         done += chunk;
         HELM_CUDA_TRY(cudaMemcpyAsync(&h_active, c.nactive, sizeof(int), cudaMemcpyDeviceToHost, c.s));
         if (guard_iters > 0)
@@ -489,7 +584,7 @@ static int fgmres_inner(const SolveCtx& c, Inner<T>& w, FgBufs<T>& f, const T* r
         fgmres_cycle<T>(c, w, f, rin);
     }
     const int m = f.dev.m;
-    count_launches(4 + (unsigned long long)m * ((c.o.precond == HELM_PRECOND_NONE ? 1 : mg_kernels_per_apply(c.m, sizeof(T) == 8, c.lf, c.ld)) +
+    count_launches(4 + (unsigned long long)m * ((c.o.precond == HELM_PRECOND_NONE ? 1 : mg_kernels_per_apply(c.m, sizeof(T) == 8, c.lf, c.ld, c.fca ? c.fca_level : 0)) +
                                                 (c.o.reorth == HELM_REORTH_NEVER ? 3 : c.o.reorth == HELM_REORTH_ALWAYS ? 5 : 4)));
     HELM_CUDA_TRY(cudaGetLastError());
     *iters_done += m;
@@ -539,7 +634,7 @@ static int build_coarse(const helm_model* m, cudaStream_t s, int nrhs, const dou
     HELM_CUDA_TRY(cudaMemcpyAsync(cs.mods.p, mods.data(), sizeof(int) * cs.nslots, cudaMemcpyHostToDevice, s));
 
     int W = 0, per = 0;
-    if (coarse == HELM_COARSE_AUTO && b2 != 0.0 && m->ld > 0 && dense_invert_plan((int)m->lv[m->ld].n(), dbl, &W, &per)) {
+    if (coarse != HELM_COARSE_TAIL && b2 != 0.0 && m->ld > 0 && dense_invert_plan((int)m->lv[m->ld].n(), dbl, &W, &per)) {
         const int ld = m->ld, n = (int)m->lv[ld].n();
         const size_t es = dbl ? sizeof(double2) : sizeof(float2);
         const int nl = std::min(per, cs.nslots);
@@ -640,6 +735,10 @@ static int solve_impl(const helm_model* m, cudaStream_t s, int nrhs, const doubl
     Inner<T> w;
     rc = alloc_inner<T>(c, w);
     if (rc != HELM_OK) return rc;
+    DBuf fcbar, fcerr;
+    std::unique_ptr<FcArgs> fca(new FcArgs());
+    rc = setup_fcycle<T>(c, w, coarse, fcbar, fcerr, fca.get());
+    if (rc != HELM_OK) return rc;
     const bool fgm = o.krylov == HELM_KRYLOV_FGMRES;
     FgBufs<T> fb;
     SideStream side;
@@ -719,6 +818,8 @@ static int solve_impl(const helm_model* m, cudaStream_t s, int nrhs, const doubl
                 if (rc != HELM_OK) break;
                 cs.swap(cs2);
                 use_coarse(*cs);
+                rc = setup_fcycle<T>(c, w, coarse, fcbar, fcerr, fca.get());
+                if (rc != HELM_OK) break;
                 if (graph) { cudaGraphExecDestroy(graph); graph = nullptr; }   // captured with the old inverse
                 switched = true;
                 restart_inner = true;
@@ -733,12 +834,16 @@ static int solve_impl(const helm_model* m, cudaStream_t s, int nrhs, const doubl
         restart_inner = false;
         if (inner_stall) force_switch = true;
         if (rc != HELM_OK) break;
+        rc = check_fcycle(c, fcerr);   // a persistent cycle that gave up a barrier ends the solve
+        if (rc != HELM_OK) break;
         launch_refine<T>(w.x.template as<T>(), u64, c.st, n, nrhs, s);
         count_launches(1);
     }
     if (graph) cudaGraphExecDestroy(graph);
     if (rc != HELM_OK) return rc;
     HELM_CUDA_TRY(cudaGetLastError());
+    rc = check_fcycle(c, fcerr);
+    if (rc != HELM_OK) return rc;
     int status = HELM_OK;
     for (int b = 0; b < nrhs; ++b) {
         const bool conv = hs[b].relres <= o.tol;
@@ -807,10 +912,14 @@ int vcycle_once(const helm_model* m, cudaStream_t s, int nrhs, const double* h_w
     Inner<float> w;
     rc = alloc_levels<float>(m, s, nrhs, w, c.ld > 0 ? c.ld : m->tail_level(false));
     if (rc != HELM_OK) return rc;
+    DBuf fcbar, fcerr;
+    FcArgs fa;
+    rc = setup_fcycle<float>(c, w, coarse, fcbar, fcerr, &fa);
+    if (rc != HELM_OK) return rc;
     vcycle<float>(c, w, r, z, 0, nullptr, nullptr);
     HELM_CUDA_TRY(cudaGetLastError());
     HELM_CUDA_TRY(cudaStreamSynchronize(s));
-    return HELM_OK;
+    return check_fcycle(c, fcerr);
 }
 
 // ------------------------------------------------------- kernel timing
@@ -1012,21 +1121,31 @@ int autotune(helm_model* m, cudaStream_t s, int nrhs, double hw2, int reps, int*
         return t;
     };
     for (int l = 0; l < kMaxLevels; ++l) { out[l] = m->tile_restrict[l]; out[kMaxLevels + l] = m->tile_prolong[l]; }
-    for (int l = 0; l < lt; ++l) {
+    // every grid level a cycle launches kernels on: above the tail, or above the dense level
+    const int top = std::max(lt, m->ld);
+    for (int l = 0; l < top && l + 1 < (int)m->lv.size(); ++l) {
         const LevelDev Lf = level_dev(m, l, false), Lc = level_dev(m, l + 1, false);
-        float tp[2], tr[2] = {0.f, 0.f};
-        for (int t = 0; t < 2; ++t) {
-            tp[t] = time_it([&] {
-                launch_prolong<float>(l == 0 && !m->vd ? 1 : 0, Lf, Lc, m->npml, m->alpha_max, w2f.as<float>(), 1.0, 0.5, 0.5,
+        // the finest level's marching prolongation has two row-segment choices; the Galerkin
+        // levels the tile shapes of launch_prolong_g / launch_restrict_g
+        const bool fine = l == 0 && !m->vd;
+        const int np = fine ? 2 : kProlongTiles, nr = l > 0 ? kRestrictTiles : 0;
+        int bp = m->tile_prolong[l], br = m->tile_restrict[l];
+        float best_p = 0.f, best_r = 0.f;
+        for (int t = 0; t < np; ++t) {
+            const float tp = time_it([&] {
+                launch_prolong<float>(fine ? 1 : 0, Lf, Lc, m->npml, m->alpha_max, w2f.as<float>(), 1.0, 0.5, 0.5,
                                       F(0), F(1), F(2), F(3), F(0), part.as<double>(), pstride, S, nrhs, s, 0, t);
             });
-            if (l > 0)
-                tr[t] = time_it([&] {
-                    launch_restrict<float>(Lf, Lc, w2f.as<float>(), 1.0, 0.5, 0.5, F(0), F(1), S, nrhs, s, t);
-                });
+            if (t == 0 || tp < best_p) { best_p = tp; bp = t; }
         }
-        m->tile_prolong[l] = tp[0] < tp[1] ? 0 : 1;
-        if (l > 0) m->tile_restrict[l] = tr[0] < tr[1] ? 0 : 1;
+        for (int t = 0; t < nr; ++t) {
+            const float tr = time_it([&] {
+                launch_restrict<float>(Lf, Lc, w2f.as<float>(), 1.0, 0.5, 0.5, F(0), F(1), S, nrhs, s, t);
+            });
+            if (t == 0 || tr < best_r) { best_r = tr; br = t; }
+        }
+        m->tile_prolong[l] = bp;
+        if (l > 0) m->tile_restrict[l] = br;
         out[l] = m->tile_restrict[l];
         out[kMaxLevels + l] = m->tile_prolong[l];
     }

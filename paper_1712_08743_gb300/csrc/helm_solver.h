@@ -69,7 +69,15 @@ struct MgCall {
     int ld = 0;             // > 0: this level is solved exactly by its dense inverse (minv), 0: the tail path
     const int* grp = nullptr;   // dense path: groups of consecutive right-hand sides sharing a slot
     int ngroups = 0, maxg = 0;
+    const FcArgs* fca = nullptr;   // non-null: the cycle at level fca_level runs as the persistent kernel
+    int fca_level = 0, fca_grid = 0;
 };
+// Fills *fa for the persistent F-cycle kernel of a complex64 batch (levels
+// c.lf .. c.ld) when it applies: the dense path is on, coarse is HELM_COARSE_AUTO,
+// nrhs <= kFcMaxRhs and the cooperative grid fits; returns its grid size, or 0.
+// f, e: the batch's level vectors; bar, err: one device counter and flag.
+int fcycle_setup(const helm_model* m, const MgCall& c, int coarse, float* const* f, float* const* e, unsigned* bar,
+                 int* err, FcArgs* fa);
 // First level of the F-cycle for a batch with grid-scaled (h omega_b)^2 = h_w2[b]:
 // the first level l >= 1 whose spacing 2^l h gives k h >= kFcycleKh for the
 // shortest wavelength of the lowest frequency (omega_min 2^l h m_max >= 0.7,
@@ -84,7 +92,7 @@ struct MgLevels {
 template <typename T>
 void mg_apply(const helm_model* m, const MgCall& c, const MgLevels<T>& B, const T* in, T* out, int mode, T* y,
               const T* aux);
-int mg_kernels_per_apply(const helm_model* m, bool dbl, int lf, int ld);
+int mg_kernels_per_apply(const helm_model* m, bool dbl, int lf, int ld, int fl = 0);
 
 int autotune(helm_model* m, cudaStream_t s, int nrhs, double hw2, int reps, int* out);
 int time_kernel(const helm_model* m, cudaStream_t s, int kernel, int nrhs, double hw2, int reps, double* ms,

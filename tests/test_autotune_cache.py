@@ -36,7 +36,7 @@ def test_measure_once_then_apply(tmp_path):
     assert lib.tuned == 1 and lib.applied == first == second
     autotune.autotune(FakeModel(lib), 16, 30.0, path)          # another batch size: another key
     assert lib.tuned == 2
-    assert set(autotune.load_cache(path)) == {"441x241:b8:c64", "441x241:b16:c64"}
+    assert set(autotune.load_cache(path)) == {"441x241:b8:c64:shapes5", "441x241:b16:c64:shapes5"}
 
 
 def test_corrupt_cache_is_ignored(tmp_path):
