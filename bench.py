@@ -57,7 +57,11 @@ def parse():
     ap.add_argument("--reorth", default="never", choices=["always", "never", "ifneeded"],
                     help="FGMRES Gram-Schmidt: second pass always (CGS2), never, or by the DGKS test")
     ap.add_argument("--inner-tol", type=float, default=5e-2, help="mixed precision: reduction per inner solve")
-    ap.add_argument("--tune", action="store_true", help="autotune the multigrid tiles before timing")
+    ap.add_argument("--no-tune", dest="tune", action="store_false",
+                    help="skip the autotuner (default: the multigrid tile shapes are chosen by helm_autotune for "
+                         "the workload's grid and batch size before timing; the choice is cached per shape)")
+    ap.add_argument("--coarse", default="auto", choices=["auto", "dense", "fused", "tail"],
+                    help="coarse end of the multigrid cycle (helm_coarse) of the single-case solves")
     ap.add_argument("--density", action="store_true",
                     help="single: the variable-density operator (Eq. 1) with a Gardner density on the same model")
     ap.add_argument("--workload", default="single", choices=["single", "batched", "serving", "gn", "ablation", "fwi"],
@@ -253,6 +257,17 @@ def time_kernels(lib, api, _lib, model, omega, reps=20):
             out[name] = {"ms": tms.value, "nrhs": nb, "bound": "latency (one block on one SM)"}
             continue
         out[name] = {"ms": tms.value, "bytes": byt.value, "gbs": byt.value / tms.value / 1e6, "nrhs": nb}
+    # FP64 peak measured here (independent fused multiply-add chains) and the FP64 residual's rate
+    # against it: 27 FP64 operations per node and right-hand side (scale 3, damped diagonal
+    # product 8, neighbours 8, residual 2, the two squared norms 6)
+    api.check(lib.helm_time_kernel(model.handle, _lib.HELM_KERNEL_FMA64, 1, omega, reps, api.C.byref(tms),
+                                   api.C.byref(byt)), "helm_time_kernel")
+    peak64 = byt.value / tms.value / 1e9
+    out["fma64"] = {"ms": tms.value, "flops": byt.value, "tflops": peak64, "bound": "fp64 alu"}
+    r = out["resid64"]
+    flops = 27.0 * model.n * r["nrhs"]
+    r["fp64_tflops"] = flops / r["ms"] / 1e9
+    r["fp64_frac"] = r["fp64_tflops"] / peak64
     return out
 
 
@@ -445,11 +460,14 @@ def run_ours(args):
     om = mdl.omegas
     kry = {"bicgstab": _lib.HELM_KRYLOV_BICGSTAB, "fgmres": _lib.HELM_KRYLOV_FGMRES}[args.krylov]
     ro = REORTH[args.reorth]
+    coarse = {"auto": _lib.HELM_COARSE_AUTO, "dense": _lib.HELM_COARSE_DENSE, "fused": _lib.HELM_COARSE_FUSED,
+              "tail": _lib.HELM_COARSE_TAIL}[args.coarse]
     opts = api.helm_default_opts(tol=1e-6, precision="mixed", krylov=kry, restart=args.restart,
-                                 inner_tol=args.inner_tol, max_it=20000, reorth=ro)
+                                 inner_tol=args.inner_tol, max_it=20000, reorth=ro, coarse=coarse)
+    tiles = None
     if args.tune:
         from paper_1712_08743_gb300 import autotune
-        autotune.autotune(model, 1, float(om[0]))
+        tiles = autotune.autotune(model, 1, float(om[0]))
     # device-resident input (point source, grid-scaled form is built by the library from f)
     f_host = np.zeros((1, model.nz, model.nx), np.complex128)
     sx, sz = mdl.sources[0]
@@ -506,7 +524,7 @@ def run_ours(args):
     fp64 = None
     if not args.no_fp64:
         o64 = api.helm_default_opts(tol=1e-6, precision="fp64", krylov=kry, restart=args.restart, max_it=20000,
-                                    reorth=ro)
+                                    reorth=ro, coarse=coarse)
         step(o64)
         t64 = []
         its64 = None
@@ -527,7 +545,7 @@ def run_ours(args):
     if not args.no_alt:
         if args.krylov == "fgmres":
             oalt = api.helm_default_opts(tol=1e-6, precision="mixed", krylov=_lib.HELM_KRYLOV_BICGSTAB,
-                                         inner_tol=args.inner_tol)
+                                         inner_tol=args.inner_tol, coarse=coarse)
             alt_name = f"BiCGSTAB (inner reduction {args.inner_tol:g})"
         else:
             oalt = api.helm_default_opts(tol=1e-6, precision="mixed", krylov=_lib.HELM_KRYLOV_FGMRES, restart=10,
@@ -620,6 +638,9 @@ def run_ours(args):
                                  "shortest wavelength reaches 0.7, F-cycle from there; the first level with at most "
                                  "1200 nodes solved by its dense inverse), beta=(1,0.5)",
                        "inner_tol": args.inner_tol, "restart": args.restart if args.krylov == "fgmres" else None,
+                       "coarse": args.coarse,
+                       "tiles": {"restrict": tiles[:model.nlevels], "prolong": tiles[24:24 + model.nlevels],
+                                 "by": "helm_autotune at 1 right-hand side"} if tiles else "library defaults",
                        "levels": model.nlevels, "l2": "flushed between timed steps (258 MB write)",
                        "parallelism": f"replicas x{world}"},
             "p50_ms": float(np.percentile(ms, 50)), "p99_ms": float(np.percentile(ms, 99)),

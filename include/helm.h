@@ -84,21 +84,27 @@ typedef enum { HELM_PRECOND_MG = 0, HELM_PRECOND_NONE = 1 } helm_precond;
  * where the basis loses orthogonality within a cycle. */
 typedef enum { HELM_REORTH_ALWAYS = 0, HELM_REORTH_NEVER = 1, HELM_REORTH_IFNEEDED = 2 } helm_reorth;
 
-/* Coarse end of the multigrid cycle. HELM_COARSE_AUTO solves the first level
- * with at most 1200 nodes exactly, by its dense inverse (computed once per solve
- * for each distinct model and frequency by block Gauss-Jordan, then applied by a
- * matrix-vector kernel); it needs beta2 != 0, which keeps every pivot away from
- * zero, and falls back to HELM_COARSE_TAIL otherwise. For complex64 batches of at
- * most 8 right-hand sides it runs the F-cycle part of the cycle (from its start
- * level down to the dense level) as one persistent cooperative kernel with a
- * grid barrier between steps. HELM_COARSE_DENSE is the same cycle with one
- * kernel launch per step. HELM_COARSE_TAIL runs the levels from the first with
- * at most 2048 (complex64) or 1024 (complex128) nodes down to the coarsest as an
- * F- or V-cycle in one block per right-hand side, in shared memory, with a dense
- * solve of the coarsest level only. All are readings of "approximately invert
- * the shifted Laplacian" (the paragraph after Eq. 9); they change the iteration
- * count, not the answer, and AUTO and DENSE give the same numbers. */
-typedef enum { HELM_COARSE_AUTO = 0, HELM_COARSE_TAIL = 1, HELM_COARSE_DENSE = 2 } helm_coarse;
+/* Coarse end of the multigrid cycle; all are readings of "approximately invert
+ * the shifted Laplacian" (the paragraph after Eq. 9) and change the iteration
+ * count, not the answer.
+ *  - HELM_COARSE_DENSE: the first level with at most 1200 nodes is solved
+ *    exactly by its dense inverse (computed once per solve for each distinct
+ *    model and frequency by block Gauss-Jordan, applied by a matrix-vector
+ *    kernel); the cycle above it runs one kernel launch per step. It needs
+ *    beta2 != 0, which keeps every pivot away from zero, and falls back to the
+ *    tail otherwise.
+ *  - HELM_COARSE_TAIL: the levels from the first with at most 2048 (complex64)
+ *    or 1024 (complex128) nodes down to the coarsest run as an F- or V-cycle in
+ *    one block per right-hand side, in shared memory, with a dense solve of the
+ *    coarsest level only.
+ *  - HELM_COARSE_FUSED: as DENSE, with the F-cycle part (from its start level
+ *    down to the dense level) in one persistent cooperative kernel with a grid
+ *    barrier between steps (complex64 batches of at most 8 right-hand sides;
+ *    otherwise as DENSE). Same numbers as DENSE to rounding.
+ *  - HELM_COARSE_AUTO (default): DENSE for batches of at most 16 right-hand
+ *    sides, TAIL for larger ones (there the tail's one launch per cycle does the
+ *    coarse levels of every right-hand side at once). */
+typedef enum { HELM_COARSE_AUTO = 0, HELM_COARSE_TAIL = 1, HELM_COARSE_DENSE = 2, HELM_COARSE_FUSED = 3 } helm_coarse;
 
 typedef struct {
     double tol;          /* stop at ||f - B u||_2 / ||f||_2 <= tol, residual formed in FP64 */
@@ -323,9 +329,12 @@ typedef enum {
     HELM_KERNEL_APPLY64 = 6,  /* y = A u, complex128 */
     HELM_KERNEL_FG_DOTS = 7,  /* FGMRES Gram-Schmidt dot products at Arnoldi step 4 (5 basis vectors), complex64 */
     HELM_KERNEL_FG_AXPY = 8,  /* FGMRES Gram-Schmidt update + per-block norm parts at step 4, complex64 */
-    HELM_KERNEL_TAIL = 9      /* coarse-level tail: one F-cycle over the levels from the first of at most
+    HELM_KERNEL_TAIL = 9,     /* coarse-level tail: one F-cycle over the levels from the first of at most
                                  2048 nodes down to the coarsest, one block per right-hand side, complex64;
                                  bytes = its input and output on the tail's top level */
+    HELM_KERNEL_FMA64 = 10    /* FP64 throughput probe (8 independent chains of fused multiply-adds per
+                                 thread, 8 blocks of 256 threads per SM); nrhs and omega are ignored and
+                                 bytes_per_launch holds the launch's FP64 operations (2 per multiply-add) */
 } helm_kernel_id;
 int helm_time_kernel(helm_model* model, int kernel, int nrhs, double omega, int reps, double* ms_per_launch,
                      double* bytes_per_launch);
@@ -375,8 +384,9 @@ int helm_vcycle_noalloc(helm_model* model, int nrhs, const double* omega, double
  * multigrid kernel on the grid levels of this model for nrhs right-hand sides at
  * angular frequency omega, keeps the fastest in the model, and writes the choices
  * to tiles_out (nullable): int[48], restriction tiles per level then prolongation
- * tiles per level. Galerkin levels: restriction 0..3 (coarse tiles 8x8, 16x8,
- * 32x4, 8x16), prolongation 0..4 (fine tiles 16x8, 32x8, 64x4, 32x16, 128x2);
+ * tiles per level. Galerkin levels: restriction 0..4 (coarse tiles 8x8, 16x8,
+ * 32x4, 8x16, and 8x8 on two threads per node), prolongation 0..4 (fine tiles
+ * 16x8, 32x8, 64x4, 32x16, 128x2);
  * the finest level's prolongation 0..1 (row segments of 16 or 32 rows); 1 is
  * the default everywhere. helm_set_tiles applies a stored choice. Tile shapes
  * change the speed, not the arithmetic of a node (dot products may sum in

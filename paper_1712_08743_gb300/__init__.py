@@ -7,7 +7,7 @@ from ._lib import (  # noqa: F401
     HELM_E_BUSY, HELM_E_CUDA, HELM_E_INVALID, HELM_E_NOMEM, HELM_E_NOT_CONVERGED, HELM_E_TIMEOUT, HELM_OK,
     HELM_PENDING, HELM_KRYLOV_BICGSTAB, HELM_KRYLOV_FGMRES, HELM_PREC_FP32, HELM_PREC_FP64, HELM_PREC_MIXED,
     HELM_FWI_SEQUENTIAL, HELM_FWI_SIMULTANEOUS, HELM_PRECOND_MG, HELM_PRECOND_NONE, HELM_REORTH_ALWAYS,
-    HELM_REORTH_IFNEEDED, HELM_REORTH_NEVER, HELM_COARSE_AUTO, HELM_COARSE_DENSE, HELM_COARSE_TAIL, HelmError, load,
+    HELM_REORTH_IFNEEDED, HELM_REORTH_NEVER, HELM_COARSE_AUTO, HELM_COARSE_DENSE, HELM_COARSE_FUSED, HELM_COARSE_TAIL, HelmError, load,
 )
 from .api import (  # noqa: F401
     Context, Model, helm_adjoint_gradient, helm_apply, helm_create_model, helm_ctx_create, helm_ctx_destroy,

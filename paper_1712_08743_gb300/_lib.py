@@ -30,6 +30,7 @@ HELM_REORTH_IFNEEDED = 2
 HELM_COARSE_AUTO = 0
 HELM_COARSE_TAIL = 1
 HELM_COARSE_DENSE = 2
+HELM_COARSE_FUSED = 3
 HELM_KERNEL_APPLY = 0
 HELM_KERNEL_RESTRICT = 1
 HELM_KERNEL_PROLONG = 2
@@ -40,6 +41,7 @@ HELM_KERNEL_APPLY64 = 6
 HELM_KERNEL_FG_DOTS = 7
 HELM_KERNEL_FG_AXPY = 8
 HELM_KERNEL_TAIL = 9
+HELM_KERNEL_FMA64 = 10
 HELM_KRYLOV_BICGSTAB = 0
 HELM_KRYLOV_FGMRES = 1
 HELM_FWI_SIMULTANEOUS = 0

@@ -46,7 +46,7 @@ int check_opts(const helm_solve_opts& o) {
     if (!(o.inner_tol > 0.0) || o.inner_tol >= 1.0) return HELM_E_INVALID;
     if (o.precond != HELM_PRECOND_MG && o.precond != HELM_PRECOND_NONE) return HELM_E_INVALID;
     if (o.reorth < HELM_REORTH_ALWAYS || o.reorth > HELM_REORTH_IFNEEDED) return HELM_E_INVALID;
-    if (o.coarse < HELM_COARSE_AUTO || o.coarse > HELM_COARSE_DENSE) return HELM_E_INVALID;
+    if (o.coarse < HELM_COARSE_AUTO || o.coarse > HELM_COARSE_FUSED) return HELM_E_INVALID;
     return HELM_OK;
 }
 
@@ -415,7 +415,7 @@ int vcycle_call(helm_model* m, int nrhs, const double* omega, double beta1, doub
                 int coarse, const void* r, void* z, int device_ptrs) {
     if (!m || nrhs < 1 || !omega || !r || !z) return HELM_E_INVALID;
     if (!std::isfinite(beta1) || !std::isfinite(beta2) || !(omega_jacobi > 0.0)) return HELM_E_INVALID;
-    if (coarse < HELM_COARSE_AUTO || coarse > HELM_COARSE_DENSE) return HELM_E_INVALID;
+    if (coarse < HELM_COARSE_AUTO || coarse > HELM_COARSE_FUSED) return HELM_E_INVALID;
     std::vector<double> w2(nrhs);
     for (int b = 0; b < nrhs; ++b) {
         if (!finite_pos(omega[b])) return HELM_E_INVALID;

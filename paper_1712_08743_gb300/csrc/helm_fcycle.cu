@@ -7,8 +7,8 @@
 // prolongation + smoothing, dense coarse solve). Launched one kernel per step,
 // each step pays a kernel launch and completion on the critical path; here the
 // whole chain runs in one cooperative launch whose blocks stay resident and
-// separate the steps with a grid barrier. Each block holds two groups of 128
-// threads; a group works on one tile of a step at a time (the tile bodies of
+// separate the steps with a grid barrier. One block per SM holds four groups of 128
+// threads each; a group works on one tile of a step at a time (the tile bodies of
 // helm_gal_tiles.cuh, with named-barrier synchronisation), and all of a
 // block's warps share the rows of the dense solve. Vectors written within the
 // launch are read through L2. The arithmetic of every node is that of the
@@ -24,29 +24,94 @@ namespace helm {
 
 namespace {
 
-constexpr int kFcThreads = 256;                 // two tile groups of 128 threads
+constexpr int kFcGroups = 4;                    // tile groups of 128 threads per block, one block per SM
 constexpr int kFcGroup = 128;
-constexpr int kFcRCX = 16;                      // restriction: 16 x 8 coarse nodes per tile
+constexpr int kFcThreads = kFcGroups * kFcGroup;
+constexpr int kFcRCX = 8;                       // restriction: 8 x 8 coarse nodes per tile (128 threads)
 constexpr int kFcPX = 16;                       // prolongation: 16 x 8 fine nodes per tile (128 threads each)
-constexpr unsigned kFcSpins = 2000000u;         // bounded wait of one step barrier (32 ns naps)
+constexpr unsigned kFcSpins = 2000000u;         // bounded wait of one step barrier (polls, about 1 s)
 
 constexpr int kFcRCZ = 8, kFcPZ = 8;
+constexpr int kFcRNT = kFcGroup;
 
 template <typename T>
 union FcGroupSmem {
-    RestrictTile<T, kFcRCX, kFcRCZ> r;
+    RestrictTile<T, kFcRCX, kFcRCZ, kFcRNT> r;
     ProlongTile<T, kFcPX, kFcPZ> p;
 };
 
+// Split grid barrier of the persistent launch: arrive (make this block's writes
+// visible and count it in on one counter) and wait (bounded poll until every
+// block has arrived for this step, then a fence before the step's loads).
+// Between the two a block may do work that does not read what other blocks
+// wrote in the step (here: stage the next step's Galerkin coefficients).
+struct FcBarrier {
+    unsigned* count;
+    int* err;
+    __device__ __forceinline__ void arrive() const {
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();
+            atomicAdd(count, 1u);
+        }
+    }
+    __device__ __forceinline__ bool wait(unsigned step) const {
+        __shared__ int s_ok;
+        if (threadIdx.x == 0) {
+            const unsigned target = step * gridDim.x;
+            int ok = 1;
+            for (unsigned k = 0;; ++k) {
+                if (*reinterpret_cast<const volatile unsigned*>(count) >= target) break;
+                if (*reinterpret_cast<const volatile int*>(err) != 0) { ok = 0; break; }
+                if (k >= kFcSpins) { atomicExch(err, 1); ok = 0; break; }
+            }
+            __threadfence();
+            s_ok = ok;
+        }
+        __syncthreads();
+        return s_ok != 0;
+    }
+};
+
+// Stages the Galerkin coefficients of this group's first tile of step `op`
+// (model data only); returns whether it did.
 template <typename T>
-__global__ void __launch_bounds__(kFcThreads, 2) k_fcycle(const __grid_constant__ FcArgs a, const RhsState* st) {
+__device__ __forceinline__ bool fc_stage_first(const FcArgs& a, FcGroupSmem<T>& sm, int op, int gid, int gtid,
+                                               const RhsState* st) {
+    const int type = op & 15, l = op >> 8;
+    const T* hw = static_cast<const T*>(a.hw);
+    if (type == FC_RESTRICT || type == FC_CORRECT_RESTRICT) {
+        const LevelDev& Lc = a.lv[l + 1];
+        const int tx = (Lc.nx + kFcRCX - 1) / kFcRCX, tz = (Lc.nz + kFcRCZ - 1) / kFcRCZ, per = tx * tz;
+        if (gid >= per * a.nrhs) return false;
+        const int b = gid / per, r = gid - b * per, by = r / tx, bx = r - by * tx;
+        if (!rhs_active(st, b)) return false;
+        restrict_tile_stage<T, kFcRCX, kFcRCZ, kFcRNT>(sm.r, a.lv[l], bx, by, b, hw[b], (T)a.b1, (T)a.b2, gtid);
+        return true;
+    }
+    if (type == FC_PROLONG) {
+        const LevelDev& Lf = a.lv[l];
+        const int tx = (Lf.nx + kFcPX - 1) / kFcPX, tz = (Lf.nz + kFcPZ - 1) / kFcPZ, per = tx * tz;
+        if (gid >= per * a.nrhs) return false;
+        const int b = gid / per, r = gid - b * per, by = r / tx, bx = r - by * tx;
+        if (!rhs_active(st, b)) return false;
+        prolong_tile_stage<T, kFcPX, kFcPZ>(sm.p, Lf, bx, by, b, hw[b], (T)a.b1, (T)a.b2, gtid);
+        return true;
+    }
+    return false;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kFcThreads, 1) k_fcycle(const __grid_constant__ FcArgs a, const RhsState* st) {
     extern __shared__ __align__(16) unsigned char fc_smem[];
     const int g = threadIdx.x / kFcGroup, gtid = threadIdx.x - g * kFcGroup;
     FcGroupSmem<T>& sm = reinterpret_cast<FcGroupSmem<T>*>(fc_smem)[g];
     const GroupSync gsync{1 + g, kFcGroup};
-    const int gid = blockIdx.x * 2 + g, ngr = gridDim.x * 2;
+    const int gid = blockIdx.x * kFcGroups + g, ngr = gridDim.x * kFcGroups;
     const T* hw = static_cast<const T*>(a.hw);
     const T b1 = (T)a.b1, b2 = (T)a.b2, wj = (T)a.wj;
+    const FcBarrier bar{a.bar, a.err};
+    bool staged = fc_stage_first<T>(a, sm, a.ops[0], gid, gtid, st);
     for (int k = 0; k < a.nops; ++k) {
         const int op = a.ops[k], type = op & 15, acc = (op & FC_ACC) ? 1 : 0, l = op >> 8;
         if (type == FC_RESTRICT || type == FC_CORRECT_RESTRICT) {
@@ -60,13 +125,14 @@ __global__ void __launch_bounds__(kFcThreads, 2) k_fcycle(const __grid_constant_
             for (int t = gid; t < nt; t += ngr) {
                 const int b = t / per, r = t - b * per, by = r / tx, bx = r - by * tx;
                 if (!rhs_active(st, b)) continue;
-                restrict_tile_stage<T, kFcRCX, kFcRCZ>(sm.r, Lf, bx, by, b, hw[b], b1, b2, gtid);
+                if (!(staged && t == gid))
+                    restrict_tile_stage<T, kFcRCX, kFcRCZ, kFcRNT>(sm.r, Lf, bx, by, b, hw[b], b1, b2, gtid);
                 if (type == FC_CORRECT_RESTRICT)
-                    restrict_tile_work<T, true, kFcRCX, kFcRCZ, true>(sm.r, Lf, Lc, wj, f, ec, fc, bx, by, b, gtid,
-                                                                      gsync);
+                    restrict_tile_work<T, true, kFcRCX, kFcRCZ, kFcRNT, true>(sm.r, Lf, Lc, wj, f, ec, fc, bx, by, b,
+                                                                              gtid, gsync);
                 else
-                    restrict_tile_work<T, false, kFcRCX, kFcRCZ, true>(sm.r, Lf, Lc, wj, f, ec, fc, bx, by, b, gtid,
-                                                                       gsync);
+                    restrict_tile_work<T, false, kFcRCX, kFcRCZ, kFcRNT, true>(sm.r, Lf, Lc, wj, f, ec, fc, bx, by, b,
+                                                                               gtid, gsync);
                 gsync();   // the next tile's staging overwrites this tile's shared memory
             }
         } else if (type == FC_PROLONG) {
@@ -80,7 +146,7 @@ __global__ void __launch_bounds__(kFcThreads, 2) k_fcycle(const __grid_constant_
             for (int t = gid; t < nt; t += ngr) {
                 const int b = t / per, r = t - b * per, by = r / tx, bx = r - by * tx;
                 if (!rhs_active(st, b)) continue;
-                prolong_tile_stage<T, kFcPX, kFcPZ>(sm.p, Lf, bx, by, b, hw[b], b1, b2, gtid);
+                if (!(staged && t == gid)) prolong_tile_stage<T, kFcPX, kFcPZ>(sm.p, Lf, bx, by, b, hw[b], b1, b2, gtid);
                 prolong_tile_work<T, kFcPX, kFcPZ, true>(sm.p, Lf, Lc, wj, f, ec, out, acc, bx, by, b, gtid, gsync);
                 gsync();
             }
@@ -98,18 +164,30 @@ __global__ void __launch_bounds__(kFcThreads, 2) k_fcycle(const __grid_constant_
                     fs[idx] = ldv<true>(fl, (size_t)r0 * n + idx);
                 __syncthreads();
                 const T* Mb = static_cast<const T*>(a.minv) + 2 * (size_t)a.slot[r0] * n * n;
-                for (int row = blockIdx.x * 8 + warp; row < n; row += gridDim.x * 8) {
+                for (int row = blockIdx.x * (kFcThreads / 32) + warp; row < n; row += gridDim.x * (kFcThreads / 32)) {
                     T are[8], aim[8];
 #pragma unroll
                     for (int r = 0; r < 8; ++r) { are[r] = T(0); aim[r] = T(0); }
-                    for (int j = lane; j < n; j += 32) {
-                        const cx<T> m = ldc(Mb, (size_t)row * n + j);
+                    // the row in chunks of 16 values per lane, each chunk's loads issued together
+                    constexpr int CH = 16;
+                    for (int j0 = 0; j0 < n; j0 += 32 * CH) {
+                        cx<T> m[CH];
 #pragma unroll
-                        for (int r = 0; r < 8; ++r) {
-                            if (r >= nb) break;
-                            const cx<T> v = fs[(size_t)r * n + j];
-                            are[r] += m.re * v.re - m.im * v.im;
-                            aim[r] += m.re * v.im + m.im * v.re;
+                        for (int q = 0; q < CH; ++q) {
+                            const int j = j0 + lane + 32 * q;
+                            m[q] = j < n ? ldc(Mb, (size_t)row * n + j) : cx<T>(0, 0);
+                        }
+#pragma unroll
+                        for (int q = 0; q < CH; ++q) {
+                            const int j = j0 + lane + 32 * q;
+                            if (j >= n) break;
+#pragma unroll
+                            for (int r = 0; r < 8; ++r) {
+                                if (r >= nb) break;
+                                const cx<T> v = fs[(size_t)r * n + j];
+                                are[r] += m[q].re * v.re - m[q].im * v.im;
+                                aim[r] += m[q].re * v.im + m[q].im * v.re;
+                            }
                         }
                     }
 #pragma unroll
@@ -130,12 +208,16 @@ __global__ void __launch_bounds__(kFcThreads, 2) k_fcycle(const __grid_constant_
                 }
             }
         }
-        // the next step reads what this one wrote anywhere on the grid
-        if (k + 1 < a.nops && !coop_barrier(a.bar, (unsigned)((k + 1) * gridDim.x), a.err, kFcSpins)) return;
+        if (k + 1 == a.nops) break;
+        // the next step reads what this one wrote anywhere on the grid: arrive, stage the next
+        // step's first tile (model data only) while the other blocks finish, then wait
+        bar.arrive();
+        staged = fc_stage_first<T>(a, sm, a.ops[k + 1], gid, gtid, st);
+        if (!bar.wait((unsigned)(k + 1))) return;
     }
 }
 
-size_t fc_smem_bytes() { return 2 * sizeof(FcGroupSmem<float>); }
+size_t fc_smem_bytes() { return kFcGroups * sizeof(FcGroupSmem<float>); }
 
 }  // namespace
 
@@ -175,7 +257,7 @@ int fcycle_grid(int dense_n, int maxg) {
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    return std::min(per_sm, 2) * sms;
+    return per_sm >= 1 ? sms : 0;   // one block per SM
 }
 
 cudaError_t launch_fcycle(const FcArgs& a, int grid, const RhsState* st, cudaStream_t s) {

@@ -70,13 +70,17 @@ struct GalTile {
     cx<T> c[5][H][W];   // centre, east, north, north-east, north-west
 };
 
-template <typename T, int W, int H>
+template <typename T, int W, int H, int NT>
 __device__ __forceinline__ void stage_gal(GalTile<T, W, H>& t, const LevelDev& L, int b, T hb1, T hb2, int gx0,
-                                          int gz0, int tid, int nt) {
+                                          int gz0, int tid) {
     const T* gk = static_cast<const T*>(L.gk) + (size_t)b * L.gkstride;
     const size_t n = (size_t)L.nx * L.nz;
-    // one node per iteration, its ten coefficients loaded independently
-    for (int idx = tid; idx < W * H; idx += nt) {
+    // one node per step, its ten coefficients loaded independently; the steps have a fixed
+    // count so that the loads of all of them can be in flight together
+#pragma unroll
+    for (int k = 0; k < (W * H + NT - 1) / NT; ++k) {
+        const int idx = tid + k * NT;
+        if (idx >= W * H) break;
         const int lz = idx / W, lx = idx - lz * W;
         const int gx = gx0 + lx, gz = gz0 + lz;
         T g[5], q[5];
@@ -121,36 +125,37 @@ template <typename T> struct GTile {
 };
 
 // ------------------------------------------------------------ restriction
-// Coarse tile (I0, K0) of GRCX x GRCZ nodes, GRCX * GRCZ threads: from the fine
+// Coarse tile (I0, K0) of GRCX x GRCZ nodes, NT >= GRCX * GRCZ threads: from the fine
 // level's right-hand side f (zero initial guess), one damped-Jacobi sweep
 // u1 = wj D^-1 f (CORRECT: u2 = wj D^-1 f + P e, e the first coarse correction of
 // an F-cycle), the residual r = f - M u on the fine region, and its restriction
 // P^T r (full weighting times 4) to the coarse tile.
-template <typename T, int GRCX, int GRCZ_ = GTile<T>::RCZ>
+template <typename T, int GRCX, int GRCZ_ = GTile<T>::RCZ, int NT_ = GRCX * GRCZ_>
 struct RestrictTile {
     static constexpr int GRCZ = GRCZ_;
     static constexpr int GRFW = 2 * GRCX + 3, GRFH = 2 * GRCZ + 3;
     static constexpr int CEW = GRCX + 2, CEH = GRCZ + 2;
-    static constexpr int NT = GRCX * GRCZ;
+    static constexpr int NT = NT_;   // threads of the tile (more than its coarse nodes spreads the fine work)
+    static_assert(NT >= GRCX * GRCZ, "one thread per coarse node at least");
     GalTile<T, GRFW, GRFH> C;
     cx<T> F[GRFH][GRFW];
     cx<T> U[GRFH][GRFW];
     cx<T> E[CEH][CEW];
 };
 
-template <typename T, int GRCX, int GRCZ>
-__device__ __forceinline__ void restrict_tile_stage(RestrictTile<T, GRCX, GRCZ>& sm, const LevelDev& Lf, int bx,
+template <typename T, int GRCX, int GRCZ, int NT>
+__device__ __forceinline__ void restrict_tile_stage(RestrictTile<T, GRCX, GRCZ, NT>& sm, const LevelDev& Lf, int bx,
                                                     int by, int b, T hw, T b1, T b2, int tid) {
-    using RT = RestrictTile<T, GRCX, GRCZ>;
+    using RT = RestrictTile<T, GRCX, GRCZ, NT>;
     const int I0 = bx * GRCX, K0 = by * RT::GRCZ;
-    stage_gal<T, RT::GRFW, RT::GRFH>(sm.C, Lf, b, hw * b1, hw * b2, 2 * I0 - 1, 2 * K0 - 1, tid, RT::NT);
+    stage_gal<T, RT::GRFW, RT::GRFH, RT::NT>(sm.C, Lf, b, hw * b1, hw * b2, 2 * I0 - 1, 2 * K0 - 1, tid);
 }
 
-template <typename T, bool CORRECT, int GRCX, int GRCZ, bool COH, class Sync>
-__device__ __forceinline__ void restrict_tile_work(RestrictTile<T, GRCX, GRCZ>& sm, const LevelDev& Lf,
+template <typename T, bool CORRECT, int GRCX, int GRCZ, int NT_, bool COH, class Sync>
+__device__ __forceinline__ void restrict_tile_work(RestrictTile<T, GRCX, GRCZ, NT_>& sm, const LevelDev& Lf,
                                                    const LevelDev& Lc, T wj, const T* f, const T* ec, T* fc, int bx,
                                                    int by, int b, int tid, Sync sync) {
-    using RT = RestrictTile<T, GRCX, GRCZ>;
+    using RT = RestrictTile<T, GRCX, GRCZ, NT_>;
     constexpr int GRFW = RT::GRFW, GRFH = RT::GRFH, CEW = RT::CEW, CEH = RT::CEH;
     const int I0 = bx * GRCX, K0 = by * GRCZ;
     const int gx0 = 2 * I0 - 1, gz0 = 2 * K0 - 1;
@@ -215,7 +220,7 @@ __device__ __forceinline__ void restrict_tile_work(RestrictTile<T, GRCX, GRCZ>& 
     sync();
     const int cxl = tid % GRCX, czl = tid / GRCX;
     const int I = I0 + cxl, K = K0 + czl;
-    if (I < Lc.nx && K < Lc.nz) {
+    if (tid < GRCX * GRCZ && I < Lc.nx && K < Lc.nz) {
         const int lx = 2 * cxl + 2, lz = 2 * czl + 2;
         cx<T> a = T(4) * sm.F[lz][lx];
         a = a + T(2) * (sm.F[lz][lx - 1] + sm.F[lz][lx + 1] + sm.F[lz - 1][lx] + sm.F[lz + 1][lx]);
@@ -244,7 +249,7 @@ template <typename T, int GPX, int GPZ>
 __device__ __forceinline__ void prolong_tile_stage(ProlongTile<T, GPX, GPZ>& sm, const LevelDev& Lf, int bx, int by,
                                                    int b, T hw, T b1, T b2, int tid) {
     using PT = ProlongTile<T, GPX, GPZ>;
-    stage_gal<T, PT::RW, PT::RH>(sm.C, Lf, b, hw * b1, hw * b2, bx * GPX - 1, by * PT::GPZ - 1, tid, PT::NT);
+    stage_gal<T, PT::RW, PT::RH, PT::NT>(sm.C, Lf, b, hw * b1, hw * b2, bx * GPX - 1, by * PT::GPZ - 1, tid);
 }
 
 template <typename T, int GPX, int GPZ, bool COH, class Sync>

@@ -29,11 +29,12 @@ constexpr int kMaxRestart = 32;
 // tile-shape choices of the complex64 Galerkin kernels (launch_prolong_g / launch_restrict_g);
 // 1 is the default shape
 constexpr int kProlongTiles = 5;
-constexpr int kRestrictTiles = 4;
+constexpr int kRestrictTiles = 5;
 constexpr int kGalerkinCoefs = 10;
 // the first level with at most this many nodes is solved exactly by its dense inverse
 // (few right-hand sides; see helm_dense.cu)
-constexpr int kDenseMaxPoints = 1200;      // per coarse node: G (c, e, n, ne, nw) then K (c, e, n, ne, nw)
+constexpr int kDenseMaxPoints = 1200;
+constexpr int kDenseAutoMaxRhs = 16;   // HELM_COARSE_AUTO takes the dense level for batches up to this size      // per coarse node: G (c, e, n, ne, nw) then K (c, e, n, ne, nw)
 
 // One multigrid level as the kernels see it. The finest level carries the
 // squared slowness m2 and the 5-point operator; every coarser level carries
@@ -356,6 +357,9 @@ constexpr int kFgTimedStep = 4;   // Arnoldi step that helm_time_kernel times (t
 template <typename T>
 void launch_fg_update(const T* Z, size_t zstride, T* x, const RhsState* st, const FgDev& fg, size_t n, int nrhs,
                       cudaStream_t s);
+
+// FP64 throughput probe: blocks x 256 threads x 8 chains x iters fused multiply-adds
+void launch_fma64(double* out, int blocks, int iters, cudaStream_t s);
 
 // right-hand sides and gradient
 void launch_point_rhs(double* f, const int* src_flat, int nrhs, size_t n, cudaStream_t s);

@@ -852,19 +852,18 @@ void launch_galerkin(const helm_model* m, int l, cudaStream_t s) {
 // wait on the previous kernel (programmatic dependent launch).
 
 // restriction (CORRECT = false: zero-guess smoothing; true: u2 = wj D^-1 f + P e)
-template <typename T, bool CORRECT, int GRCX, int GRCZ>
-__global__ void __launch_bounds__(GRCX * GRCZ) k_restrict_g(LevelDev Lf, LevelDev Lc, const T* __restrict__ hwv, T b1,
-                                                            T b2, T wj, const T* __restrict__ f,
-                                                            const T* __restrict__ ec, T* __restrict__ fc,
-                                                            const RhsState* st) {
-    __shared__ RestrictTile<T, GRCX, GRCZ> sm;
+template <typename T, bool CORRECT, int GRCX, int GRCZ, int NT>
+__global__ void __launch_bounds__(NT) k_restrict_g(LevelDev Lf, LevelDev Lc, const T* __restrict__ hwv, T b1, T b2,
+                                                   T wj, const T* __restrict__ f, const T* __restrict__ ec,
+                                                   T* __restrict__ fc, const RhsState* st) {
+    __shared__ RestrictTile<T, GRCX, GRCZ, NT> sm;
     pdl_trigger();
     const int b = blockIdx.z;
-    restrict_tile_stage<T, GRCX, GRCZ>(sm, Lf, blockIdx.x, blockIdx.y, b, hwv[b], b1, b2, threadIdx.x);   // model data
+    restrict_tile_stage<T, GRCX, GRCZ, NT>(sm, Lf, blockIdx.x, blockIdx.y, b, hwv[b], b1, b2, threadIdx.x);   // model data
     pdl_wait();
     if (!rhs_active(st, b)) return;
-    restrict_tile_work<T, CORRECT, GRCX, GRCZ, false>(sm, Lf, Lc, wj, f, ec, fc, blockIdx.x, blockIdx.y, b,
-                                                      threadIdx.x, BlockSync{});
+    restrict_tile_work<T, CORRECT, GRCX, GRCZ, NT, false>(sm, Lf, Lc, wj, f, ec, fc, blockIdx.x, blockIdx.y, b,
+                                                          threadIdx.x, BlockSync{});
 }
 
 template <typename T, int GPX, int GPZ>
@@ -885,13 +884,14 @@ __global__ void __launch_bounds__(GPX * GPZ) k_prolong_g(LevelDev Lf, LevelDev L
 // per level (kGalTiles choices; 1 is the default): restriction coarse tile
 // (x, z) and prolongation fine tile (x, z), one thread per node of the tile. The
 // shapes keep each block's shared memory within 48 KB.
-//   0: 8 x 8 / 16 x 8,  1: 16 x 8 / 32 x 8,  2: 32 x 4 / 64 x 4,  3: 8 x 16 / 32 x 16,  4: 16 x 8 / 128 x 2
-template <typename T, bool CORRECT, int GRCX, int GRCZ>
+//   0: 8 x 8 / 16 x 8,  1: 16 x 8 / 32 x 8,  2: 32 x 4 / 64 x 4,  3: 8 x 16 / 32 x 16,  4: 8 x 8 on 128
+//   threads (two per coarse node, for short per-thread chains on small levels) / 128 x 2
+template <typename T, bool CORRECT, int GRCX, int GRCZ, int NT = GRCX * GRCZ>
 void launch_restrict_g_shape(const LevelDev& Lf, const LevelDev& Lc, const T* w2, double b1, double b2, double wj,
                              const T* f, const T* ec, T* fc, const RhsState* st, int nrhs, cudaStream_t s) {
     dim3 grd((Lc.nx + GRCX - 1) / GRCX, (Lc.nz + GRCZ - 1) / GRCZ, nrhs);
-    launch_pdl(k_restrict_g<T, CORRECT, GRCX, GRCZ>, grd, dim3(GRCX * GRCZ), 0, s, Lf, Lc, w2, (T)b1, (T)b2, (T)wj,
-               f, ec, fc, st);
+    launch_pdl(k_restrict_g<T, CORRECT, GRCX, GRCZ, NT>, grd, dim3(NT), 0, s, Lf, Lc, w2, (T)b1, (T)b2, (T)wj, f,
+               ec, fc, st);
 }
 template <typename T, bool CORRECT>
 void launch_restrict_g(int tile, const LevelDev& Lf, const LevelDev& Lc, const T* w2, double b1, double b2, double wj,
@@ -901,6 +901,7 @@ void launch_restrict_g(int tile, const LevelDev& Lf, const LevelDev& Lc, const T
             case 0: launch_restrict_g_shape<T, CORRECT, 8, 8>(Lf, Lc, w2, b1, b2, wj, f, ec, fc, st, nrhs, s); return;
             case 2: launch_restrict_g_shape<T, CORRECT, 32, 4>(Lf, Lc, w2, b1, b2, wj, f, ec, fc, st, nrhs, s); return;
             case 3: launch_restrict_g_shape<T, CORRECT, 8, 16>(Lf, Lc, w2, b1, b2, wj, f, ec, fc, st, nrhs, s); return;
+            case 4: launch_restrict_g_shape<T, CORRECT, 8, 8, 128>(Lf, Lc, w2, b1, b2, wj, f, ec, fc, st, nrhs, s); return;
             default: break;
         }
     }
@@ -1859,6 +1860,27 @@ template void launch_correct_restrict<float>(const LevelDev&, const LevelDev&, c
 template void launch_correct_restrict<double>(const LevelDev&, const LevelDev&, const double*, double, double, double,
                                               const double*, const double*, double*, const RhsState*, int,
                                               cudaStream_t, int);
+
+// ======================================================= FP64 throughput probe
+// Peak rate of FP64 fused multiply-adds (helm_time_kernel HELM_KERNEL_FMA64): each
+// thread runs eight independent chains x <- a x + b of `iters` steps; the sum is
+// stored only under a condition the values never meet, which keeps the chains.
+__global__ void __launch_bounds__(256) k_fma64(double* out, int iters, double a, double b) {
+    double x[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) x[k] = 1e-3 * threadIdx.x + k;
+    for (int i = 0; i < iters; ++i)
+#pragma unroll
+        for (int k = 0; k < 8; ++k) x[k] = fma(x[k], a, b);
+    double sum = 0.0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) sum += x[k];
+    if (sum == -1.0) out[blockIdx.x] = sum;
+}
+
+void launch_fma64(double* out, int blocks, int iters, cudaStream_t s) {
+    k_fma64<<<blocks, 256, 0, s>>>(out, iters, 0.9999999, 1e-7);
+}
 
 // ============================================================ right-hand sides
 __global__ void k_point_rhs(double* f, const int* __restrict__ src_flat, size_t n) {

@@ -23,6 +23,7 @@ namespace {
 constexpr size_t kNoAllocScratchBytes = 64ull << 20;   // 64 MiB
 constexpr int kNoAllocMaxRhs = 256;
 constexpr int kMaxDevices = 64;
+constexpr int kNoAllocCoarse = HELM_COARSE_AUTO;   // the coarse end helm_vcycle's defaults choose
 
 // The scratch area. In host code `g_noalloc_scratch` names a host-side stand-in,
 // not device memory: kernels get the device address from cudaGetSymbolAddress.
@@ -83,7 +84,8 @@ extern "C" int helm_vcycle_noalloc(helm_model* m, int nrhs, const double* omega,
     // the coarse end of the cycle helm_vcycle would use: the dense inverse of level m->ld where it
     // applies (beta2 != 0 and the inversion fits the GPU), else the shared-memory tail
     int W = 0, per = 0;
-    const bool dense = beta2 != 0.0 && m->ld > 0 && dense_invert_plan((int)m->lv[m->ld].n(), false, &W, &per);
+    const bool dense = nrhs <= kDenseAutoMaxRhs && beta2 != 0.0 && m->ld > 0 &&
+                       dense_invert_plan((int)m->lv[m->ld].n(), false, &W, &per);
     // groups of consecutive right-hand sides sharing a slot, at most 8 each
     int grp[kNoAllocMaxRhs + 1];
     int ngroups = 0, maxg = 0;
@@ -121,7 +123,7 @@ extern "C" int helm_vcycle_noalloc(helm_model* m, int nrhs, const double* omega,
             p.dinv = take(sizeof(float2) * 2 * (size_t)W * W * nl);
             p.bar = take(sizeof(unsigned) * nl);
             p.err = take(sizeof(int));
-            p.fbar = take(sizeof(unsigned));   // the persistent F-cycle's barrier counter and error flag
+            p.fbar = take(sizeof(unsigned));   // the persistent F-cycle's barrier and error flag
             p.ferr = take(sizeof(int));
             p.top = m->ld;
         } else {
@@ -216,12 +218,13 @@ extern "C" int helm_vcycle_noalloc(helm_model* m, int nrhs, const double* omega,
             B.f[l] = reinterpret_cast<float*>(base + plan.f[l]);
             B.e[l] = reinterpret_cast<float*>(base + plan.e[l]);
         }
-        // as helm_vcycle: the F-cycle part as one persistent kernel where it applies
+        // as helm_vcycle (HELM_COARSE_AUTO: one launch per step; the persistent F-cycle kernel
+        // only runs for HELM_COARSE_FUSED)
         FcArgs fa;
-        if (use_dense) {
+        if (use_dense && kNoAllocCoarse == HELM_COARSE_FUSED) {
             int* ferr = reinterpret_cast<int*>(base + plan.ferr);
             e = cudaMemsetAsync(ferr, 0, sizeof(int), s);
-            const int grid = e == cudaSuccess ? fcycle_setup(m, mc, HELM_COARSE_AUTO, B.f, B.e,
+            const int grid = e == cudaSuccess ? fcycle_setup(m, mc, kNoAllocCoarse, B.f, B.e,
                                                              reinterpret_cast<unsigned*>(base + plan.fbar), ferr, &fa)
                                               : 0;
             if (grid > 0) {

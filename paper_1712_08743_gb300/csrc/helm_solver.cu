@@ -224,7 +224,7 @@ int mg_kernels_per_apply(const helm_model* m, bool dbl, int lf, int ld, int fl) 
 
 int fcycle_setup(const helm_model* m, const MgCall& c, int coarse, float* const* f, float* const* e, unsigned* bar,
                  int* err, FcArgs* fa) {
-    if (coarse != HELM_COARSE_AUTO || c.ld <= 0 || c.nrhs > kFcMaxRhs || c.lf >= c.ld || !bar || !err) return 0;
+    if (coarse != HELM_COARSE_FUSED || c.ld <= 0 || c.nrhs > kFcMaxRhs || c.lf >= c.ld || !bar || !err) return 0;
     const int nd = (int)m->lv[c.ld].n();
     const int grid = fcycle_grid(nd, c.maxg);
     if (grid <= 0) return 0;
@@ -314,7 +314,7 @@ template <typename T>
 static int setup_fcycle(SolveCtx& c, Inner<T>& w, int coarse, DBuf& bar, DBuf& err, FcArgs* fa) {
     c.fca = nullptr;
     if constexpr (sizeof(T) == 4) {
-        if (coarse != HELM_COARSE_AUTO || c.ld <= 0) return HELM_OK;
+        if (coarse != HELM_COARSE_FUSED || c.ld <= 0) return HELM_OK;
         if (!bar.p) {
             TRY_ALLOC(bar, sizeof(unsigned), c.s);
             TRY_ALLOC(err, sizeof(int), c.s);
@@ -634,7 +634,9 @@ static int build_coarse(const helm_model* m, cudaStream_t s, int nrhs, const dou
     HELM_CUDA_TRY(cudaMemcpyAsync(cs.mods.p, mods.data(), sizeof(int) * cs.nslots, cudaMemcpyHostToDevice, s));
 
     int W = 0, per = 0;
-    if (coarse != HELM_COARSE_TAIL && b2 != 0.0 && m->ld > 0 && dense_invert_plan((int)m->lv[m->ld].n(), dbl, &W, &per)) {
+    const bool want_dense = coarse == HELM_COARSE_DENSE || coarse == HELM_COARSE_FUSED ||
+                            (coarse == HELM_COARSE_AUTO && nrhs <= kDenseAutoMaxRhs);
+    if (want_dense && b2 != 0.0 && m->ld > 0 && dense_invert_plan((int)m->lv[m->ld].n(), dbl, &W, &per)) {
         const int ld = m->ld, n = (int)m->lv[ld].n();
         const size_t es = dbl ? sizeof(double2) : sizeof(float2);
         const int nl = std::min(per, cs.nslots);
@@ -1052,6 +1054,16 @@ int time_kernel(const helm_model* m, cudaStream_t s, int kernel, int nrhs, doubl
                                                 1.0, 0.5, 0.8);
             launch = [&, a] { launch_tail<float>(a, m->tail_smem[0], nrhs, S, s); };
             *bytes = 16.0 * B * (double)nt;
+            break;
+        }
+        case HELM_KERNEL_FMA64: {
+            // eight blocks of 256 threads per SM, each thread 8 chains of 2048 FP64 FMAs
+            int dev = 0, sms = 0;
+            cudaGetDevice(&dev);
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            const int blocks = 8 * sms, iters = 2048;
+            launch = [&, blocks] { launch_fma64(D(0), blocks, iters, s); };
+            *bytes = 2.0 * blocks * 256.0 * 8.0 * iters;   // FP64 operations (2 per fused multiply-add)
             break;
         }
         default:

@@ -70,11 +70,11 @@ def test_vcycle_matches_restatement(hg, ctx, name, make):
     rng = np.random.default_rng(2)
     om = 2 * np.pi * np.array([4.0, 6.0])
     r = models.random_complex(rng, (2, model.nz, model.nx), np.complex64)
-    # default coarse end (the first level with at most 1200 nodes solved by its dense inverse;
-    # for these few right-hand sides the F-cycle part runs as one persistent kernel), the same
-    # cycle with one launch per step, and the shared-memory tail over the whole hierarchy
+    # default coarse end (for these few right-hand sides the first level with at most 1200
+    # nodes solved by its dense inverse, one launch per step), the same cycle with its F-cycle
+    # part in one persistent kernel, and the shared-memory tail over the whole hierarchy
     z_auto = {}
-    for coarse, kind in [(None, "dense"), (hg.HELM_COARSE_DENSE, "dense"), (hg.HELM_COARSE_TAIL, "tail")]:
+    for coarse, kind in [(None, "dense"), (hg.HELM_COARSE_FUSED, "dense"), (hg.HELM_COARSE_TAIL, "tail")]:
         for beta, wj in [((1.0, 0.5), 0.8), ((1.0, 1.0), 0.6)]:
             z = hg.helm_vcycle(model, om, r, beta, wj, coarse=coarse)
             m2 = oracle.pad_slowness(mdl.slowness, mdl.npml) ** 2
@@ -85,7 +85,7 @@ def test_vcycle_matches_restatement(hg, ctx, name, make):
                 assert rel(z[k], ref) < 2e-5, (name, kind, beta, k, rel(z[k], ref))
             if coarse is None:
                 z_auto[beta] = z
-            elif coarse == hg.HELM_COARSE_DENSE:
+            elif coarse == hg.HELM_COARSE_FUSED:
                 # the persistent kernel does each node's operations as the one-launch kernels do
                 # (the compiler may contract them into fused multiply-adds differently: the two
                 # agree to the rounding of complex64 arithmetic)
@@ -217,11 +217,11 @@ def test_autotuned_tiles_give_the_same_wavefields(hg, ctx, tmp_path):
     tiles = autotune.autotune(model, len(om), float(om[0]), str(tmp_path / "t.json"))
     n = autotune.NTILES // 2
     assert len(tiles) == autotune.NTILES
-    assert all(0 <= t <= 3 for t in tiles[:n]) and all(0 <= t <= 4 for t in tiles[n:]) and tiles[n] <= 1
+    assert all(0 <= t <= 4 for t in tiles[:n]) and all(0 <= t <= 4 for t in tiles[n:]) and tiles[n] <= 1
     import ctypes as C
     for code in [None, 0, 2, 3, 4]:
         if code is not None:   # the same shape code on every level (finest prolongation: 0 or 1)
-            arr = [min(code, 3)] * n + [min(code, 1)] + [code] * (n - 1)
+            arr = [code] * n + [min(code, 1)] + [code] * (n - 1)
             assert model.lib.helm_set_tiles(model.handle, (C.c_int * autotune.NTILES)(*arr)) == 0
         u1, st, _ = hg.helm_solve(model, om, src, opts=opts)
         assert all(s["converged"] for s in st)

@@ -35,7 +35,7 @@ def test_time_kernel_bytes_and_times(hg):
         _lib.HELM_KERNEL_FG_DOTS: n * nrhs * 8.0 * 6,
         _lib.HELM_KERNEL_FG_AXPY: n * nrhs * 8.0 * 7,
     }
-    for kid in range(10):
+    for kid in range(11):
         ms, byt = C.c_double(), C.c_double()
         api.check(lib.helm_time_kernel(model.handle, kid, nrhs, 2 * np.pi * 5.0, 3, C.byref(ms), C.byref(byt)),
                   "helm_time_kernel")
@@ -49,7 +49,15 @@ def test_time_kernel_bytes_and_times(hg):
                                    C.byref(byt)), "helm_time_kernel")
     nodes = byt.value / (16.0 * nrhs)
     assert nodes == int(nodes) and 1 <= nodes <= 2048
-    assert lib.helm_time_kernel(model.handle, 10, nrhs, 2 * np.pi * 5.0, 3, C.byref(ms), C.byref(byt)) == \
+    # the FP64 probe reports its FP64 operations: 8 blocks of 256 threads per SM, 8 chains of
+    # 2048 fused multiply-adds each, 2 operations per multiply-add
+    import torch
+
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    api.check(lib.helm_time_kernel(model.handle, _lib.HELM_KERNEL_FMA64, 1, 1.0, 3, C.byref(ms), C.byref(byt)),
+              "helm_time_kernel")
+    assert byt.value == 2.0 * 8 * sms * 256 * 8 * 2048
+    assert lib.helm_time_kernel(model.handle, 11, nrhs, 2 * np.pi * 5.0, 3, C.byref(ms), C.byref(byt)) == \
         _lib.HELM_E_INVALID
     model.close()
     ctx.close()
