@@ -372,7 +372,10 @@ int helm_profile_end(helm_profile_entry* out, int cap, int* n_out);
  *  - Sizes whose level vectors and coarsest-level inverses do not fit in the
  *    64 MiB return HELM_E_INVALID (helm_last_error() gives the bytes needed).
  *  - The first call on a device looks up the scratch array's device address
- *    (cudaGetSymbolAddress); make that first call before any stream capture.
+ *    (cudaGetSymbolAddress) and keeps it for the process; make that first call
+ *    before any stream capture. A cudaDeviceReset of that device invalidates
+ *    the kept address: do not call this entry point on that device afterwards
+ *    (reload the library instead).
  *  - Every call on a device shares the one array and leaves its contents
  *    behind; each call writes every byte it reads, so nothing needs clearing.
  *    Calls that overlap on the GPU (other threads or streams) race: serialise

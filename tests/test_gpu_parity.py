@@ -374,6 +374,10 @@ def test_autograd_backward_runs_adjoint(hg, ctx):
 
 
 def test_served_results_equal_lone_solves(hg):
+    """Each served result equals the lone helm_solve of its request within the wavefield bar
+    (1e-6, solves to relres 1e-10). Not bit for bit: a batch whose member stalls continues with
+    the (1, 1) shift as a whole (the stall guard), so a request can take another Krylov path in
+    a batch than alone; both reach the tolerance."""
     ctx = hg.Context(0)
     hg.helm_serve_config(ctx, max_batch=4, max_slots=2)
     reqs = []
@@ -384,14 +388,14 @@ def test_served_results_equal_lone_solves(hg):
         h = 1500.0 / (12 * f)
         c = models.layered_model(rng, n, n, h, 5)
         reqs.append((1 / c, h, 2 * np.pi * f, (n // 2, 2)))
-    opts = dict(tol=1e-8)
+    opts = dict(tol=1e-10)
     tickets = [hg.helm_submit(ctx, m, h, w, s, opts=opts) for (m, h, w, s) in reqs]
     served = [hg.helm_poll(ctx, t, 120000) for t in tickets]
     for (m, h, w, s), res, t in zip(reqs, served, tickets):
         assert res is not None and res.status == hg.HELM_OK and res.latency_ms >= res.queue_ms >= 0
         model = hg.helm_create_model(ctx, m, h)
         u, st, _ = hg.helm_solve(model, [w], [s], opts=opts)
-        assert rel(res.u, u[0]) < 1e-8
+        assert rel(res.u, u[0]) < 1e-6, (rel(res.u, u[0]), res.stats, st[0])
         model.close()
         hg.helm_release(ctx, t)
     assert max(r.batch_size for r in served) >= 2
