@@ -131,3 +131,45 @@ def test_density_cycle_converges_to_direct_solution():
     V1 = mg.VCycle(m_pad ** 2, hw2, beta=(1.0, 0.5), rho_pad=np.ones_like(rho))
     V0 = mg.VCycle(m_pad ** 2, hw2, beta=(1.0, 0.5))
     assert np.array_equal(V1.apply(f), V0.apply(f))
+
+
+def test_dense_level_rule():
+    """With a complex shift the first level below the finest with at most 1200 nodes is
+    solved exactly (32^2 for 1041^2, 27 x 15 for 441 x 241, 17^2 for the padded small case);
+    without the imaginary part of the shift the coarsest level is."""
+    hw2 = (5.0 * 2 * np.pi * 15.0) ** 2
+    shapes = mg.level_shapes(1041, 1041)
+    first = next(l for l in range(1, len(shapes)) if shapes[l][0] * shapes[l][1] <= 1200)
+    assert shapes[first] == (32, 32) and first == 5
+    assert mg.level_shapes(441, 241)[4] == (27, 15)
+    small = mg.VCycle(np.full((141, 141), (1 / 2000.0) ** 2), hw2, beta=(1.0, 0.5))
+    assert small.shapes[small.exact] == (17, 17)
+    assert mg.VCycle(np.full((141, 141), (1 / 2000.0) ** 2), hw2, beta=(1.0, 0.0)).exact == len(small.shapes) - 1
+
+
+def test_dense_level_is_solved_exactly_and_the_cycle_converges():
+    """The level the dense coarse end solves returns M_l^{-1} f, checked against a dense
+    LAPACK solve of the assembled level matrix (not the oracle's own sparse LU), and the
+    cycle with that coarse end, used as a stationary iteration, converges to the direct
+    solution of M u = f like the cycle with the coarsest level exact."""
+    rng = np.random.default_rng(7)
+    mdl = models.c1_model()
+    m_pad = np.pad(mdl.slowness, 20, mode="edge")
+    hw2 = (mdl.h * mdl.omegas[0]) ** 2
+    V = mg.VCycle(m_pad ** 2, hw2, beta=(1.0, 0.5), coarse="dense")
+    T = mg.VCycle(m_pad ** 2, hw2, beta=(1.0, 0.5), coarse="tail")
+    assert V.exact < T.exact
+    Ml = V.M[V.exact].toarray()
+    g = models.random_complex(rng, Ml.shape[0])
+    e = V.cycle(g, V.exact, "V")
+    assert np.linalg.norm(e - np.linalg.solve(Ml, g)) < 1e-12 * np.linalg.norm(e)
+    M = V.M[0]
+    f = models.random_complex(rng, M.shape[0])
+    exact = spla.spsolve(M.tocsc(), f)
+    for cyc in (V, T):
+        u = np.zeros_like(f)
+        for _ in range(200):
+            u = u + cyc.apply(f - M @ u)
+        assert np.linalg.norm(u - exact) < 1e-6 * np.linalg.norm(exact)
+    # one application differs between the two coarse ends (the dense one is exact lower down)
+    assert np.linalg.norm(V.apply(f) - T.apply(f)) > 1e-8 * np.linalg.norm(T.apply(f))
