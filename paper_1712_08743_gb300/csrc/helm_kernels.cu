@@ -364,7 +364,16 @@ template void launch_apply_dots<double>(int, const LevelDev&, int, double, const
 
 // ======================================================= FP64 outer residual
 // r = f - A u in FP64; writes the inner right-hand side rin = r in precision TI
-// and decides, per right-hand side, whether refinement continues.
+// and decides, per right-hand side, whether refinement continues. GB300 issues
+// FP64 at a small fraction of its FP32 rate, so this kernel is bound by FP64
+// instructions, not bytes (GB300: about 1.7 FP64 operations per clock per SM,
+// DADD, DMUL, DFMA and the double-to-float conversion alike). Each thread takes
+// R64_ROWS consecutive rows of one column, so the block sum is paid once for all
+// of them; interior nodes (outside the absorbing layer, four neighbours) sum
+// the neighbours pairwise and fuse the diagonal product and the squared norm
+// into FMAs; ||f||^2 is formed only on the first call of a solve.
+constexpr int R64_ROWS = 8;
+
 template <typename TI, bool VD>
 __global__ void __launch_bounds__(256) k_resid64(LevelDev L, int npml, double acoef, const double* __restrict__ w2,
                                                  const double* __restrict__ f, const double* __restrict__ u,
@@ -373,24 +382,51 @@ __global__ void __launch_bounds__(256) k_resid64(LevelDev L, int npml, double ac
     __shared__ double sh[64];
     const int b = blockIdx.z;
     if (!st[b].outer_active) return;
-    const int tid = threadIdx.y * 32 + threadIdx.x;
-    const int ix = blockIdx.x * 32 + threadIdx.x, iz = blockIdx.y * 8 + threadIdx.y;
-    const size_t n = (size_t)L.nx * L.nz;
+    const int nx = L.nx, nz = L.nz;
+    const int ix = blockIdx.x * 32 + threadIdx.x, iz0 = (blockIdx.y * 8 + threadIdx.y) * R64_ROWS;
+    const size_t n = (size_t)nx * nz;
+    const double* ub = u + 2 * n * b;
+    const double* fb = f + 2 * n * b;
+    const double* mb = static_cast<const double*>(L.m2) + (size_t)b * L.mstride;
+    typename C2<TI>::type* rb = reinterpret_cast<typename C2<TI>::type*>(rin) + n * b;
+    const double sw = L.h2 * w2[b];
     double v[2] = {0.0, 0.0};
-    if (ix < L.nx && iz < L.nz) {
-        const double* ub = u + 2 * n * b;
-        const size_t i = (size_t)iz * L.nx + ix;
-        const double s = L.h2 * w2[b] * (static_cast<const double*>(L.m2) + (size_t)b * L.mstride)[i];
-        const double a = layer_alpha_t<double>(ix, iz, L.nx, L.nz, npml, acoef);
-        const cx<double> c = ldc(ub, i);
-        const cx<double> acc = fine_apply_point<double, VD>(L, ub, i, ix, iz, s, a, c);
-        cx<double> fv = ldc(f + 2 * n * b, i);
-        cx<double> r = fv - acc;
-        v[0] = r.re * r.re + r.im * r.im;
-        v[1] = fv.re * fv.re + fv.im * fv.im;
-        reinterpret_cast<typename C2<TI>::type*>(rin)[n * b + i] = {(TI)r.re, (TI)r.im};
+    if (ix < nx) {
+#pragma unroll
+        for (int k = 0; k < R64_ROWS; ++k) {
+            const int iz = iz0 + k;
+            if (iz >= nz) break;
+            const size_t i = (size_t)iz * nx + ix;
+            const double s = sw * mb[i];
+            const cx<double> c = ldc(ub, i);
+            const cx<double> fv = ldc(fb, i);
+            cx<double> r;
+            if constexpr (VD) {
+                const double a = layer_alpha_t<double>(ix, iz, nx, nz, npml, acoef);
+                r = fv - fine_apply_point<double, true>(L, ub, i, ix, iz, s, a, c);
+            } else {
+                // f - (4 - s) u + N u (+ the damping term in the layer), N u the sum of the neighbours
+                const double g = 4.0 - s;
+                const int d = layer_depth(ix, iz, nx, nz, npml);
+                if (d == 0 && ix > 0 && ix + 1 < nx && iz > 0 && iz + 1 < nz) {
+                    const cx<double> w = ldc(ub, i - 1), e = ldc(ub, i + 1), no = ldc(ub, i - nx), so = ldc(ub, i + nx);
+                    const cx<double> nb = (w + e) + (no + so);
+                    r = cx<double>(fma(-g, c.re, fv.re) + nb.re, fma(-g, c.im, fv.im) + nb.im);
+                } else {
+                    cx<double> nb(0.0, 0.0);
+                    if (ix > 0) nb = nb + ldc(ub, i - 1);
+                    if (ix + 1 < nx) nb = nb + ldc(ub, i + 1);
+                    if (iz > 0) nb = nb + ldc(ub, i - nx);
+                    if (iz + 1 < nz) nb = nb + ldc(ub, i + nx);
+                    const double sa = s * (acoef * (double)(d * d));
+                    r = cx<double>((fv.re - (g * c.re - sa * c.im)) + nb.re, (fv.im - (g * c.im + sa * c.re)) + nb.im);
+                }
+            }
+            v[0] = fma(r.re, r.re, fma(r.im, r.im, v[0]));
+            if (first) v[1] = fma(fv.re, fv.re, fma(fv.im, fv.im, v[1]));
+            rb[i] = {(TI)r.re, (TI)r.im};
+        }
     }
-    (void)tid;
     const int nblk = gridDim.x * gridDim.y, blk = blockIdx.y * gridDim.x + blockIdx.x;
     if (last_block_reduce<2>(v, sh, partials + (size_t)b * pstride, nblk, blk, &st[b].counter[0])) {
         if (threadIdx.x == 0 && threadIdx.y == 0) {
@@ -414,7 +450,7 @@ void launch_resid64(const LevelDev& L0, int npml, double amax, const double* w2,
     const double n0 = (double)L0.nx * L0.nz;
     ProfScope prof(PK_RESID64, L0.nx, L0.nz,
                    n0 * ((32.0 + 2 * sizeof(TI)) * nrhs + 8.0 * (L0.mstride ? nrhs : 1) * (L0.rho ? 4 : 1)), s);
-    dim3 blk(32, 8), grd((L0.nx + 31) / 32, (L0.nz + 7) / 8, nrhs);
+    dim3 blk(32, 8), grd((L0.nx + 31) / 32, (L0.nz + 8 * R64_ROWS - 1) / (8 * R64_ROWS), nrhs);
     if (L0.rho)
         k_resid64<TI, true><<<grd, blk, 0, s>>>(L0, npml, layer_coef(npml, amax), w2, f, u, rin, partials, pstride,
                                                 st, tol, inner_floor, inner_fac, first);
