@@ -7,8 +7,8 @@ no code with the CUDA library; both sides take their inputs from ``synth``.
 
 The oracle is the plain definition of what the method computes: the exact
 discrete solution ``u = B^{-1} f`` of Eq. 2/3 by a direct sparse LU
-factorisation (the paper also generates its observed data "via LU
-factorization", Section "Examples"), and the exact derivative of the discrete
+factorisation (the paper, too, makes its observed data with a finite-difference
+solve by LU factorisation, Examples section), and the exact derivative of the discrete
 misfit of Eq. 4 by the adjoint formula behind Eq. 7.
 """
 from .helmholtz import (  # noqa: F401

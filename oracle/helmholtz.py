@@ -142,7 +142,7 @@ def point_sources(nx: int, nz: int, h: float, src_pad: np.ndarray) -> np.ndarray
 
 class Factorised:
     """One sparse LU factorisation of B(m, omega), reused for every right-hand side
-    of that frequency (the paper's direct "LU factorization" modelling)."""
+    of that frequency (the paper models its data with a direct LU solve, Examples section)."""
 
     def __init__(self, m_pad: np.ndarray, h: float, omega: float, alpha: np.ndarray, rho_pad=None):
         self.shape = m_pad.shape

@@ -3,8 +3,8 @@
 //
 // From the F-cycle start level ls down to the level ld that the dense inverse
 // solves, a preconditioner application is a chain of about twenty dependent
-// steps on small grids (restriction, F-cycle correction + restriction,
-// prolongation + smoothing, dense coarse solve). Launched one kernel per step,
+// steps on small grids (restriction, restriction of the second coarse
+// correction, prolongation + smoothing, dense coarse solve). Launched one kernel per step,
 // each step pays a kernel launch and completion on the critical path; here the
 // whole chain runs in one cooperative launch whose blocks stay resident and
 // separate the steps with a grid barrier. One block per SM holds four groups of 128
@@ -37,6 +37,7 @@ constexpr int kFcRNT = kFcGroup;
 template <typename T>
 union FcGroupSmem {
     RestrictTile<T, kFcRCX, kFcRCZ, kFcRNT> r;
+    ResidRestrictTile<T, kFcRCX, kFcRCZ, kFcRNT> q;
     ProlongTile<T, kFcPX, kFcPZ> p;
 };
 
@@ -89,6 +90,16 @@ __device__ __forceinline__ bool fc_stage_first(const FcArgs& a, FcGroupSmem<T>& 
         restrict_tile_stage<T, kFcRCX, kFcRCZ, kFcRNT>(sm.r, a.lv[l], bx, by, b, hw[b], (T)a.b1, (T)a.b2, gtid);
         return true;
     }
+    if (type == FC_RESID_RESTRICT) {
+        const LevelDev& Lc = a.lv[l + 1];
+        const int tx = (Lc.nx + kFcRCX - 1) / kFcRCX, tz = (Lc.nz + kFcRCZ - 1) / kFcRCZ, per = tx * tz;
+        if (gid >= per * a.nrhs) return false;
+        const int b = gid / per, r = gid - b * per, by = r / tx, bx = r - by * tx;
+        if (!rhs_active(st, b)) return false;
+        resid_restrict_tile_stage<T, kFcRCX, kFcRCZ, kFcRNT>(sm.q, a.lv[l], bx, by, b, hw[b], (T)a.b1, (T)a.b2,
+                                                             gtid);
+        return true;
+    }
     if (type == FC_PROLONG) {
         const LevelDev& Lf = a.lv[l];
         const int tx = (Lf.nx + kFcPX - 1) / kFcPX, tz = (Lf.nz + kFcPZ - 1) / kFcPZ, per = tx * tz;
@@ -135,12 +146,30 @@ __global__ void __launch_bounds__(kFcThreads, 1) k_fcycle(const __grid_constant_
                                                                                gtid, gsync);
                 gsync();   // the next tile's staging overwrites this tile's shared memory
             }
+        } else if (type == FC_RESID_RESTRICT) {
+            const LevelDev& Lf = a.lv[l];
+            const LevelDev& Lc = a.lv[l + 1];
+            const int tx = (Lc.nx + kFcRCX - 1) / kFcRCX, tz = (Lc.nz + kFcRCZ - 1) / kFcRCZ;
+            const int per = tx * tz, nt = per * a.nrhs;
+            const T* f = static_cast<const T*>(a.f[l]);
+            const T* e = static_cast<const T*>(a.e[l]);
+            T* gl = static_cast<T*>(a.g[l]);
+            T* fc = static_cast<T*>(a.f[l + 1]);
+            for (int t = gid; t < nt; t += ngr) {
+                const int b = t / per, r = t - b * per, by = r / tx, bx = r - by * tx;
+                if (!rhs_active(st, b)) continue;
+                if (!(staged && t == gid))
+                    resid_restrict_tile_stage<T, kFcRCX, kFcRCZ, kFcRNT>(sm.q, Lf, bx, by, b, hw[b], b1, b2, gtid);
+                resid_restrict_tile_work<T, kFcRCX, kFcRCZ, kFcRNT, true>(sm.q, Lf, Lc, wj, f, e, gl, fc, bx, by, b,
+                                                                          gtid, gsync);
+                gsync();
+            }
         } else if (type == FC_PROLONG) {
             const LevelDev& Lf = a.lv[l];
             const LevelDev& Lc = a.lv[l + 1];
             const int tx = (Lf.nx + kFcPX - 1) / kFcPX, tz = (Lf.nz + kFcPZ - 1) / kFcPZ;
             const int per = tx * tz, nt = per * a.nrhs;
-            const T* f = static_cast<const T*>(a.f[l]);
+            const T* f = static_cast<const T*>((op & FC_G) ? a.g[l] : a.f[l]);
             const T* ec = static_cast<const T*>(a.e[l + 1]);
             T* out = static_cast<T*>(a.e[l]);
             for (int t = gid; t < nt; t += ngr) {
@@ -225,17 +254,16 @@ size_t fc_smem_bytes() { return kFcGroups * sizeof(FcGroupSmem<float>); }
 // F-cycle from level lf: the order of mg_cycle's launches.
 std::vector<int> fcycle_schedule(int l, int lf, int ld, bool F, int acc) {
     std::vector<int> ops;
-    std::function<void(int, bool, int)> cyc = [&](int q, bool f, int a) {
+    std::function<void(int, bool, int, bool)> cyc = [&](int q, bool f, int a, bool resid) {
         if (q == ld) { ops.push_back(FC_DENSE | (a ? FC_ACC : 0) | (q << 8)); return; }
-        ops.push_back(FC_RESTRICT | (q << 8));
-        cyc(q + 1, f || (q + 1 == lf), 0);
-        if (f) {
-            ops.push_back(FC_CORRECT_RESTRICT | (q << 8));
-            cyc(q + 1, false, 1);
-        }
-        ops.push_back(FC_PROLONG | (a ? FC_ACC : 0) | (q << 8));
+        ops.push_back((resid ? FC_RESID_RESTRICT : FC_RESTRICT) | (q << 8));
+        cyc(q + 1, f || (q + 1 == lf), 0, false);
+        // second correction: none above the dense level (its right-hand side is zero there),
+        // else a V-cycle whose first restriction forms its right-hand side
+        if (f && q + 1 < ld) cyc(q + 1, false, 1, true);
+        ops.push_back(FC_PROLONG | (a ? FC_ACC : 0) | (resid ? FC_G : 0) | (q << 8));
     };
-    cyc(l, F, acc);
+    cyc(l, F, acc, false);
     return ops;
 }
 

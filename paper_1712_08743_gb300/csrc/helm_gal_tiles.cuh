@@ -229,6 +229,110 @@ __device__ __forceinline__ void restrict_tile_work(RestrictTile<T, GRCX, GRCZ, N
     }
 }
 
+// ------------------------------ restriction of the second coarse correction
+// In an F-cycle at level l the second coarse correction solves M_{l+1} d = P^T (f_l - M_l u2)
+// with u2 = wj D^-1 f_l + P e (e the first correction). With the Galerkin operator
+// M_{l+1} = P^T M_l P and the restriction P^T this right-hand side is
+// g = f_{l+1} - M_{l+1} e, where f_{l+1} = P^T (f_l - M_l wj D^-1 f_l) is what the first
+// restriction wrote: level l + 1 data only. The V-cycle of that correction starts at
+// level l + 1, so this tile (level l + 1 -> l + 2) forms g on its fine region, writes
+// the nodes it owns to `g` (the V-cycle's prolongation reads them again), and goes
+// on as the plain restriction: u1 = wj D^-1 g, r = g - M u1, P^T r to the coarse tile.
+// Fields and coefficients share one pitch: the fine region of the plain tile plus a
+// halo of one node, which g = f - M e needs on the region's border.
+template <typename T, int GRCX, int GRCZ, int NT_>
+struct ResidRestrictTile {
+    static constexpr int XW = 2 * GRCX + 5, XH = 2 * GRCZ + 5;   // region + halo
+    static constexpr int NT = NT_;
+    static_assert(NT >= GRCX * GRCZ, "one thread per coarse node at least");
+    GalTile<T, XW, XH> C;
+    cx<T> E[XH][XW];
+    cx<T> F[XH][XW];
+    cx<T> U[XH][XW];
+};
+
+template <typename T, int GRCX, int GRCZ, int NT>
+__device__ __forceinline__ void resid_restrict_tile_stage(ResidRestrictTile<T, GRCX, GRCZ, NT>& sm, const LevelDev& Lf,
+                                                          int bx, int by, int b, T hw, T b1, T b2, int tid) {
+    using RT = ResidRestrictTile<T, GRCX, GRCZ, NT>;
+    stage_gal<T, RT::XW, RT::XH, NT>(sm.C, Lf, b, hw * b1, hw * b2, 2 * bx * GRCX - 2, 2 * by * GRCZ - 2, tid);
+}
+
+template <typename T, int GRCX, int GRCZ, int NT, bool COH, class Sync>
+__device__ __forceinline__ void resid_restrict_tile_work(ResidRestrictTile<T, GRCX, GRCZ, NT>& sm, const LevelDev& Lf,
+                                                         const LevelDev& Lc, T wj, const T* f, const T* e, T* g,
+                                                         T* fc, int bx, int by, int b, int tid, Sync sync) {
+    using RT = ResidRestrictTile<T, GRCX, GRCZ, NT>;
+    constexpr int XW = RT::XW, XH = RT::XH, NX = XW * XH, NPT = (NX + NT - 1) / NT;
+    const int I0 = bx * GRCX, K0 = by * GRCZ;
+    const int xx0 = 2 * I0 - 2, xz0 = 2 * K0 - 2;   // global position of the halo's corner
+    const size_t nf = (size_t)Lf.nx * Lf.nz, nc = (size_t)Lc.nx * Lc.nz;
+    const T* fb = f + 2 * nf * b;
+    const T* eb = e + 2 * nf * b;
+    // fine nodes this tile writes to g: x in [2 I0, 2 (I0 + GRCX)), the last tile of a row up to
+    // the grid's edge (likewise in z), so every node of the level has one owner
+    const int ox1 = (I0 + GRCX >= Lc.nx) ? Lf.nx : 2 * (I0 + GRCX);
+    const int oz1 = (K0 + GRCZ >= Lc.nz) ? Lf.nz : 2 * (K0 + GRCZ);
+    // e on the region and its halo, f on the region: all loads issued before use
+    cx<T> epre[NPT], fpre[NPT];
+#pragma unroll
+    for (int k = 0; k < NPT; ++k) {
+        const int idx = tid + k * NT;
+        const int lz = idx / XW, lx = idx - lz * XW;
+        const int gx = xx0 + lx, gz = xz0 + lz;
+        const bool in = idx < NX && gx >= 0 && gx < Lf.nx && gz >= 0 && gz < Lf.nz;
+        const size_t i = in ? (size_t)gz * Lf.nx + gx : 0;
+        const bool reg = in && lx >= 1 && lx <= XW - 2 && lz >= 1 && lz <= XH - 2;
+        epre[k] = in ? ldv<COH>(eb, i) : cx<T>(0, 0);
+        fpre[k] = reg ? ldv<COH>(fb, i) : cx<T>(0, 0);
+    }
+#pragma unroll
+    for (int k = 0; k < NPT; ++k) {
+        const int idx = tid + k * NT;
+        if (idx >= NX) break;
+        const int lz = idx / XW, lx = idx - lz * XW;
+        sm.E[lz][lx] = epre[k];
+        sm.F[lz][lx] = fpre[k];
+    }
+    sync();
+    // g = f - M e and u1 = wj D^-1 g on the region
+    T* gb = g + 2 * nf * b;
+    constexpr int RW = XW - 2, RH = XH - 2;
+    for (int idx = tid; idx < RW * RH; idx += NT) {
+        const int lz = 1 + idx / RW, lx = 1 + idx % RW;
+        const int gx = xx0 + lx, gz = xz0 + lz;
+        cx<T> gv(0, 0), uv(0, 0);
+        if (gx >= 0 && gx < Lf.nx && gz >= 0 && gz < Lf.nz) {
+            gv = sm.F[lz][lx] - mop9_staged<T, XW, XH>(sm.C, Lf.nx, Lf.nz, gx, gz, lx, lz, &sm.E[lz][lx]);
+            uv = wj * cdiv(gv, sm.C.c[0][lz][lx]);
+            if (gx >= 2 * I0 && gx < ox1 && gz >= 2 * K0 && gz < oz1) stc(gb, (size_t)gz * Lf.nx + gx, gv);
+        }
+        sm.F[lz][lx] = gv;
+        sm.U[lz][lx] = uv;
+    }
+    sync();
+    // r = g - M u1 on the nodes the restriction reads
+    constexpr int W2 = XW - 4, H2 = XH - 4;
+    for (int idx = tid; idx < W2 * H2; idx += NT) {
+        const int lz = 2 + idx / W2, lx = 2 + idx % W2;
+        const int gx = xx0 + lx, gz = xz0 + lz;
+        cx<T> r(0, 0);
+        if (gx < Lf.nx && gz < Lf.nz)
+            r = sm.F[lz][lx] - mop9_staged<T, XW, XH>(sm.C, Lf.nx, Lf.nz, gx, gz, lx, lz, &sm.U[lz][lx]);
+        sm.F[lz][lx] = r;
+    }
+    sync();
+    const int cxl = tid % GRCX, czl = tid / GRCX;
+    const int I = I0 + cxl, K = K0 + czl;
+    if (tid < GRCX * GRCZ && I < Lc.nx && K < Lc.nz) {
+        const int lx = 2 * cxl + 3, lz = 2 * czl + 3;
+        cx<T> a = T(4) * sm.F[lz][lx];
+        a = a + T(2) * (sm.F[lz][lx - 1] + sm.F[lz][lx + 1] + sm.F[lz - 1][lx] + sm.F[lz + 1][lx]);
+        a = a + sm.F[lz - 1][lx - 1] + sm.F[lz - 1][lx + 1] + sm.F[lz + 1][lx - 1] + sm.F[lz + 1][lx + 1];
+        stc(fc + 2 * nc * b, (size_t)K * Lc.nx + I, T(0.25) * a);
+    }
+}
+
 // ----------------------------------------------------------- prolongation
 // Fine tile (x0, z0) of GPX x GPZ nodes, GPX * GPZ threads: u = wj D^-1 f + P e
 // on the tile and its halo, then the post-smoothing sweep u + wj D^-1 (f - M u),

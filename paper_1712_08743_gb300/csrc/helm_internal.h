@@ -145,7 +145,7 @@ class NvtxRange {
 // its scope, with the kernel class, the grid and the launch's algorithmic bytes.
 enum ProfKernel : int {
     PK_APPLY, PK_APPLY_DOTS, PK_RESID64, PK_REFINE, PK_BICG_INIT, PK_BICG_RESUME, PK_BICG_P, PK_BICG_S, PK_BICG_XR,
-    PK_RESTRICT, PK_PROLONG, PK_RESTRICT_G, PK_CORRECT_RESTRICT, PK_PROLONG_G, PK_TAIL, PK_COARSE_DENSE,
+    PK_RESTRICT, PK_PROLONG, PK_RESTRICT_G, PK_CORRECT_RESTRICT, PK_RESID_RESTRICT, PK_PROLONG_G, PK_TAIL, PK_COARSE_DENSE,
     PK_DENSE_INVERT, PK_COARSE_INVERT, PK_FG_NORM, PK_FG_SCALE, PK_FG_DOTS, PK_FG_AXPY, PK_FG_FINISH,
     PK_FG_BACKSOLVE, PK_FG_UPDATE, PK_FCYCLE, PK_OTHER, PK_COUNT
 };
@@ -270,6 +270,13 @@ void launch_correct_restrict(const LevelDev& Lf, const LevelDev& Lc, const T* w2
 template <typename T>
 void launch_restrict(const LevelDev& Lf, const LevelDev& Lc, const T* w2, double b1, double b2,
                      double wj, const T* f, T* fc, const RhsState* st, int nrhs, cudaStream_t s, int tile = 1);
+// The restriction that starts the second coarse correction of an F-cycle, on a
+// Galerkin level: g = f - M e (f this level's first right-hand side, e its first
+// correction) written to g, then restricted like launch_restrict does to fc.
+template <typename T>
+void launch_resid_restrict(const LevelDev& Lf, const LevelDev& Lc, const T* w2, double b1, double b2, double wj,
+                           const T* f, const T* e, T* g, T* fc, const RhsState* st, int nrhs, cudaStream_t s,
+                           int tile);
 // mode 0: out = smoothed correction; 1: out = p^, y = A p^, alpha = rho/<rh, y>;
 // 2: out = s^, y = A s^, omega = <y, s>/<y, y>; 3: out = z, y = A z (no dots).
 template <typename T>
@@ -301,13 +308,17 @@ void launch_coarse_invert(const LevelDev& Lc, const double* w2_slots, const int*
 // output) | level << 8.
 constexpr int kFcMaxOps = 96;
 constexpr int kFcMaxRhs = 8;      // right-hand sides a batch may have for the persistent path
-enum FcOpType : int { FC_RESTRICT = 1, FC_CORRECT_RESTRICT = 2, FC_PROLONG = 3, FC_DENSE = 4, FC_ACC = 16 };
+enum FcOpType : int {
+    FC_RESTRICT = 1, FC_CORRECT_RESTRICT = 2, FC_PROLONG = 3, FC_DENSE = 4, FC_RESID_RESTRICT = 5,
+    FC_ACC = 16, FC_G = 32   // FC_G: the step's right-hand side on its level is g (second correction)
+};
 struct FcArgs {
     int nops, nrhs;
     int ops[kFcMaxOps];
     LevelDev lv[kMaxLevels];
     void* f[kMaxLevels];      // per level: right-hand side and correction [nrhs][n_l] (complex64)
     void* e[kMaxLevels];
+    void* g[kMaxLevels];      // right-hand side of an F-cycle's second coarse correction
     const void* hw;           // (h_0 omega_b)^2 per RHS, FP32
     double b1, b2, wj;
     const void* minv;         // dense inverses of level ld, [nslots][n][n]

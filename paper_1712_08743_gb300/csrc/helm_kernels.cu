@@ -916,6 +916,56 @@ __global__ void __launch_bounds__(GPX * GPZ) k_prolong_g(LevelDev Lf, LevelDev L
                                           threadIdx.x, BlockSync{});
 }
 
+// restriction that starts the second coarse correction of an F-cycle (tile body
+// resid_restrict_tile_work): right-hand side g = f - M e, written to g, then
+// restricted as k_restrict_g does
+template <typename T, int GRCX, int GRCZ, int NT>
+__global__ void __launch_bounds__(NT) k_resid_restrict_g(LevelDev Lf, LevelDev Lc, const T* __restrict__ hwv, T b1,
+                                                         T b2, T wj, const T* __restrict__ f, const T* __restrict__ e,
+                                                         T* __restrict__ g, T* __restrict__ fc, const RhsState* st) {
+    __shared__ ResidRestrictTile<T, GRCX, GRCZ, NT> sm;
+    pdl_trigger();
+    const int b = blockIdx.z;
+    resid_restrict_tile_stage<T, GRCX, GRCZ, NT>(sm, Lf, blockIdx.x, blockIdx.y, b, hwv[b], b1, b2, threadIdx.x);
+    pdl_wait();
+    if (!rhs_active(st, b)) return;
+    resid_restrict_tile_work<T, GRCX, GRCZ, NT, false>(sm, Lf, Lc, wj, f, e, g, fc, blockIdx.x, blockIdx.y, b,
+                                                       threadIdx.x, BlockSync{});
+}
+
+template <typename T, int GRCX, int GRCZ, int NT>
+static void launch_resid_restrict_shape(const LevelDev& Lf, const LevelDev& Lc, const T* w2, double b1, double b2,
+                                        double wj, const T* f, const T* e, T* g, T* fc, const RhsState* st, int nrhs,
+                                        cudaStream_t s) {
+    dim3 grd((Lc.nx + GRCX - 1) / GRCX, (Lc.nz + GRCZ - 1) / GRCZ, nrhs);
+    launch_pdl(k_resid_restrict_g<T, GRCX, GRCZ, NT>, grd, dim3(NT), 0, s, Lf, Lc, w2, (T)b1, (T)b2, (T)wj, f, e, g,
+               fc, st);
+}
+
+template <typename T>
+void launch_resid_restrict(const LevelDev& Lf, const LevelDev& Lc, const T* w2, double b1, double b2, double wj,
+                           const T* f, const T* e, T* g, T* fc, const RhsState* st, int nrhs, cudaStream_t s,
+                           int tile) {
+    const double nf = (double)Lf.nx * Lf.nz, nc = (double)Lc.nx * Lc.nz, es = 2.0 * sizeof(T);
+    // f, e and g on this level, the coarse output, the ten Galerkin coefficients per node and model
+    ProfScope prof(PK_RESID_RESTRICT, Lf.nx, Lf.nz,
+                   (3 * nf + nc) * es * nrhs + nf * sizeof(T) * kGalerkinCoefs * (Lf.gkstride ? nrhs : 1), s);
+    if constexpr (sizeof(T) == 4) {
+        if (tile == 0)
+            launch_resid_restrict_shape<T, 8, 8, 64>(Lf, Lc, w2, b1, b2, wj, f, e, g, fc, st, nrhs, s);
+        else
+            launch_resid_restrict_shape<T, 8, 8, 128>(Lf, Lc, w2, b1, b2, wj, f, e, g, fc, st, nrhs, s);
+    } else {
+        launch_resid_restrict_shape<T, 8, 4, 64>(Lf, Lc, w2, b1, b2, wj, f, e, g, fc, st, nrhs, s);
+    }
+}
+template void launch_resid_restrict<float>(const LevelDev&, const LevelDev&, const float*, double, double, double,
+                                           const float*, const float*, float*, float*, const RhsState*, int,
+                                           cudaStream_t, int);
+template void launch_resid_restrict<double>(const LevelDev&, const LevelDev&, const double*, double, double, double,
+                                            const double*, const double*, double*, double*, const RhsState*, int,
+                                            cudaStream_t, int);
+
 // Tile shapes of the complex64 Galerkin kernels, by the code the autotuner stores
 // per level (kGalTiles choices; 1 is the default): restriction coarse tile
 // (x, z) and prolongation fine tile (x, z), one thread per node of the tile. The

@@ -108,7 +108,7 @@ extern "C" int helm_vcycle_noalloc(helm_model* m, int nrhs, const double* omega,
     const size_t common = off;
     struct Plan {
         size_t minv = 0, work = 0, md = 0, panel = 0, dinv = 0, bar = 0, err = 0, fbar = 0, ferr = 0;
-        size_t f[kMaxLevels] = {}, e[kMaxLevels] = {};
+        size_t f[kMaxLevels] = {}, e[kMaxLevels] = {}, g[kMaxLevels] = {};
         int top = 0;
         size_t end = 0;
     };
@@ -136,6 +136,7 @@ extern "C" int helm_vcycle_noalloc(helm_model* m, int nrhs, const double* omega,
         for (int l = 1; l <= p.top; ++l) {
             p.f[l] = take(sizeof(float) * 2 * m->lv[l].n() * nrhs);
             p.e[l] = take(sizeof(float) * 2 * m->lv[l].n() * nrhs);
+            if (l >= 2 && l < p.top) p.g[l] = take(sizeof(float) * 2 * m->lv[l].n() * nrhs);
         }
         p.end = off;
         return p;
@@ -217,6 +218,7 @@ extern "C" int helm_vcycle_noalloc(helm_model* m, int nrhs, const double* omega,
         for (int l = 1; l <= plan.top; ++l) {
             B.f[l] = reinterpret_cast<float*>(base + plan.f[l]);
             B.e[l] = reinterpret_cast<float*>(base + plan.e[l]);
+            B.g[l] = plan.g[l] ? reinterpret_cast<float*>(base + plan.g[l]) : nullptr;
         }
         // as helm_vcycle (HELM_COARSE_AUTO: one launch per step; the persistent F-cycle kernel
         // only runs for HELM_COARSE_FUSED)
@@ -224,7 +226,7 @@ extern "C" int helm_vcycle_noalloc(helm_model* m, int nrhs, const double* omega,
         if (use_dense && kNoAllocCoarse == HELM_COARSE_FUSED) {
             int* ferr = reinterpret_cast<int*>(base + plan.ferr);
             e = cudaMemsetAsync(ferr, 0, sizeof(int), s);
-            const int grid = e == cudaSuccess ? fcycle_setup(m, mc, kNoAllocCoarse, B.f, B.e,
+            const int grid = e == cudaSuccess ? fcycle_setup(m, mc, kNoAllocCoarse, B.f, B.e, B.g,
                                                              reinterpret_cast<unsigned*>(base + plan.fbar), ferr, &fa)
                                               : 0;
             if (grid > 0) {

@@ -71,8 +71,9 @@ template <typename T>
 struct Inner {
     DBuf x, r, rh, p, v, sv, t, ph, shv;
     // per level 1 <= l <= lt: right-hand side and correction (deeper levels live
-    // in the tail kernel's shared memory)
-    std::vector<std::unique_ptr<DBuf>> fl, el;
+    // in the tail kernel's shared memory), and on levels 2 <= l < lt the right-hand
+    // side of an F-cycle's second coarse correction
+    std::vector<std::unique_ptr<DBuf>> fl, el, gl;
 };
 
 // Per-solve state shared by the outer and inner loops.
@@ -151,8 +152,19 @@ static const char* const kLevelNames[kMaxLevels] = {
     "mg level 15", "mg level 16", "mg level 17", "mg level 18", "mg level 19", "mg level 20", "mg level 21",
     "mg level 22", "mg level 23"};
 
+// Whether the cycle of level l runs on the grid-level kernels (not the dense
+// inverse, not the shared-memory tail).
+static bool grid_level(const helm_model* m, const MgCall& c, int l, bool dbl) {
+    return c.ld > 0 ? l < c.ld : l < m->tail_level(dbl);
+}
+
+// One cycle at level l (F or V) from the right-hand side B.f[l] into B.e[l] (added
+// to it when acc). resid: the right-hand side is B.f[l] - M_l B.e[l] instead (the
+// second coarse correction of the F-cycle one level up, always a V-cycle that
+// accumulates), formed by the first restriction and kept in B.g[l].
 template <typename T>
-static void mg_cycle(const helm_model* m, const MgCall& c, const MgLevels<T>& B, int l, bool F, int acc) {
+static void mg_cycle(const helm_model* m, const MgCall& c, const MgLevels<T>& B, int l, bool F, int acc,
+                     bool resid = false) {
     NvtxRange nv(kLevelNames[l]);
     const bool dbl = sizeof(T) == 8;
     const T* hw = hw_of<T>(c);
@@ -172,15 +184,27 @@ static void mg_cycle(const helm_model* m, const MgCall& c, const MgLevels<T>& B,
         return;
     }
     const LevelDev Lf = level_dev(m, l, dbl), Lc = level_dev(m, l + 1, dbl);
-    launch_restrict<T>(Lf, Lc, hw, c.b1, c.b2, c.wj, B.f[l], B.f[l + 1], c.st, c.nrhs, c.s, m->tile_restrict[l]);
+    if (resid)
+        launch_resid_restrict<T>(Lf, Lc, hw, c.b1, c.b2, c.wj, B.f[l], B.e[l], B.g[l], B.f[l + 1], c.st, c.nrhs, c.s,
+                                 m->tile_restrict[l]);
+    else
+        launch_restrict<T>(Lf, Lc, hw, c.b1, c.b2, c.wj, B.f[l], B.f[l + 1], c.st, c.nrhs, c.s, m->tile_restrict[l]);
     mg_cycle<T>(m, c, B, l + 1, F || (l + 1 == c.lf), 0);
     if (F) {
-        launch_correct_restrict<T>(Lf, Lc, hw, c.b1, c.b2, c.wj, B.f[l], B.e[l + 1], B.f[l + 1], c.st, c.nrhs, c.s,
-                                   m->tile_restrict[l]);
-        mg_cycle<T>(m, c, B, l + 1, false, 1);
+        // second coarse correction, for P^T (f - M (wj D^-1 f + P e)) = f_{l+1} - M_{l+1} e_{l+1}
+        // (Galerkin M_{l+1} = P^T M P): zero when level l + 1 was solved exactly by its dense
+        // inverse, so nothing is done then; on a grid level it is formed there, by the first
+        // restriction of the correction's V-cycle
+        if (grid_level(m, c, l + 1, dbl)) {
+            mg_cycle<T>(m, c, B, l + 1, false, 1, true);
+        } else if (c.ld <= 0) {
+            launch_correct_restrict<T>(Lf, Lc, hw, c.b1, c.b2, c.wj, B.f[l], B.e[l + 1], B.f[l + 1], c.st, c.nrhs,
+                                       c.s, m->tile_restrict[l]);
+            mg_cycle<T>(m, c, B, l + 1, false, 1);
+        }
     }
-    launch_prolong<T>(0, Lf, Lc, m->npml, m->alpha_max, hw, c.b1, c.b2, c.wj, B.f[l], B.e[l + 1], B.e[l], nullptr,
-                      nullptr, nullptr, 0, c.st, c.nrhs, c.s, acc, m->tile_prolong[l]);
+    launch_prolong<T>(0, Lf, Lc, m->npml, m->alpha_max, hw, c.b1, c.b2, c.wj, resid ? B.g[l] : B.f[l], B.e[l + 1],
+                      B.e[l], nullptr, nullptr, nullptr, 0, c.st, c.nrhs, c.s, acc, m->tile_prolong[l]);
 }
 
 template <typename T>
@@ -215,15 +239,19 @@ static int count_cycle(const helm_model* m, int lt, int l, bool F, int lf, int l
     if (fl > 0 && l == fl) return 1;
     if (ld > 0 ? l == ld : l >= lt) return 1;
     int k = 2 + count_cycle(m, lt, l + 1, F || (l + 1 == lf), lf, ld, fl);
-    if (F) k += 1 + count_cycle(m, lt, l + 1, false, lf, ld, fl);
+    if (F) {   // as mg_cycle: nothing above the dense level, the correction's V-cycle on a grid level
+        const bool grid = ld > 0 ? l + 1 < ld : l + 1 < lt;
+        if (grid) k += count_cycle(m, lt, l + 1, false, lf, ld, fl);
+        else if (ld <= 0) k += 1 + count_cycle(m, lt, l + 1, false, lf, ld, fl);
+    }
     return k;
 }
 int mg_kernels_per_apply(const helm_model* m, bool dbl, int lf, int ld, int fl) {
     return 2 + (m->vd ? 1 : 0) + count_cycle(m, m->tail_level(dbl), 1, lf == 1, lf, ld, fl);
 }
 
-int fcycle_setup(const helm_model* m, const MgCall& c, int coarse, float* const* f, float* const* e, unsigned* bar,
-                 int* err, FcArgs* fa) {
+int fcycle_setup(const helm_model* m, const MgCall& c, int coarse, float* const* f, float* const* e,
+                 float* const* g, unsigned* bar, int* err, FcArgs* fa) {
     if (coarse != HELM_COARSE_FUSED || c.ld <= 0 || c.nrhs > kFcMaxRhs || c.lf >= c.ld || !bar || !err) return 0;
     const int nd = (int)m->lv[c.ld].n();
     const int grid = fcycle_grid(nd, c.maxg);
@@ -240,12 +268,13 @@ int fcycle_setup(const helm_model* m, const MgCall& c, int coarse, float* const*
         const double n = (double)m->lv[l].n(), nc = l + 1 < (int)m->lv.size() ? (double)m->lv[l + 1].n() : 0.0;
         const double coef = n * sizeof(float) * kGalerkinCoefs * (m->nmodels > 1 ? c.nrhs : 1);
         if (type == FC_RESTRICT) bytes += (n + nc) * 8.0 * c.nrhs + coef;
+        else if (type == FC_RESID_RESTRICT) bytes += (3 * n + nc) * 8.0 * c.nrhs + coef;
         else if (type == FC_CORRECT_RESTRICT) bytes += (n + 2 * nc) * 8.0 * c.nrhs + coef;
         else if (type == FC_PROLONG) bytes += (n * (2 + acc) + nc) * 8.0 * c.nrhs + coef;
         else bytes += n * n * 8.0 * c.ngroups + n * (2 + acc) * 8.0 * c.nrhs;
     }
     for (int l = 0; l < (int)m->lv.size(); ++l) fa->lv[l] = level_dev(m, l, false);
-    for (int l = 1; l <= c.ld; ++l) { fa->f[l] = f[l]; fa->e[l] = e[l]; }
+    for (int l = 1; l <= c.ld; ++l) { fa->f[l] = f[l]; fa->e[l] = e[l]; fa->g[l] = g[l]; }
     fa->hw = c.w2f;
     fa->b1 = c.b1;
     fa->b2 = c.b2;
@@ -304,6 +333,7 @@ static void vcycle(const SolveCtx& c, Inner<T>& w, const T* in, T* out, int mode
     for (int l = 1; l <= top; ++l) {
         B.f[l] = w.fl[l]->template as<T>();
         B.e[l] = w.el[l]->template as<T>();
+        B.g[l] = w.gl[l] ? w.gl[l]->template as<T>() : nullptr;
     }
     mg_apply<T>(c.m, mc, B, in, out, mode, y, aux);
 }
@@ -322,11 +352,13 @@ static int setup_fcycle(SolveCtx& c, Inner<T>& w, int coarse, DBuf& bar, DBuf& e
         }
         float* f[kMaxLevels] = {};
         float* e[kMaxLevels] = {};
+        float* g[kMaxLevels] = {};
         for (int l = 1; l <= c.ld; ++l) {
             f[l] = w.fl[l]->template as<float>();
             e[l] = w.el[l]->template as<float>();
+            g[l] = w.gl[l] ? w.gl[l]->template as<float>() : nullptr;
         }
-        const int grid = fcycle_setup(c.m, mgcall_of(c), coarse, f, e, bar.as<unsigned>(), err.as<int>(), fa);
+        const int grid = fcycle_setup(c.m, mgcall_of(c), coarse, f, e, g, bar.as<unsigned>(), err.as<int>(), fa);
         if (grid > 0) {
             c.fca = fa;
             c.fca_level = c.lf;
@@ -355,12 +387,17 @@ static int alloc_levels(const helm_model* m, cudaStream_t s, int nrhs, Inner<T>&
     const int nl = (int)m->lv.size();
     w.fl.resize(nl);
     w.el.resize(nl);
+    w.gl.resize(nl);
     for (int l = 1; l < nl && l <= top; ++l) {
         const size_t b = sizeof(T) * 2 * m->lv[l].n() * nrhs;
         w.fl[l].reset(new DBuf());
         w.el[l].reset(new DBuf());
         TRY_ALLOC(*w.fl[l], b, s);
         TRY_ALLOC(*w.el[l], b, s);
+        if (l >= 2 && l < top) {
+            w.gl[l].reset(new DBuf());
+            TRY_ALLOC(*w.gl[l], b, s);
+        }
     }
     return HELM_OK;
 }

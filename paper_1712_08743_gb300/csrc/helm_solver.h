@@ -76,8 +76,8 @@ struct MgCall {
 // c.lf .. c.ld) when it applies: the dense path is on, coarse is HELM_COARSE_AUTO,
 // nrhs <= kFcMaxRhs and the cooperative grid fits; returns its grid size, or 0.
 // f, e: the batch's level vectors; bar, err: one device counter and flag.
-int fcycle_setup(const helm_model* m, const MgCall& c, int coarse, float* const* f, float* const* e, unsigned* bar,
-                 int* err, FcArgs* fa);
+int fcycle_setup(const helm_model* m, const MgCall& c, int coarse, float* const* f, float* const* e,
+                 float* const* g, unsigned* bar, int* err, FcArgs* fa);
 // First level of the F-cycle for a batch with grid-scaled (h omega_b)^2 = h_w2[b]:
 // the first level l >= 1 whose spacing 2^l h gives k h >= kFcycleKh for the
 // shortest wavelength of the lowest frequency (omega_min 2^l h m_max >= 0.7,
@@ -88,6 +88,7 @@ template <typename T>
 struct MgLevels {
     T* f[kMaxLevels];
     T* e[kMaxLevels];
+    T* g[kMaxLevels];   // right-hand side of an F-cycle's second coarse correction (levels 2 .. top - 1)
 };
 template <typename T>
 void mg_apply(const helm_model* m, const MgCall& c, const MgLevels<T>& B, const T* in, T* out, int mode, T* y,

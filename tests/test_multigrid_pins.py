@@ -173,3 +173,37 @@ def test_dense_level_is_solved_exactly_and_the_cycle_converges():
         assert np.linalg.norm(u - exact) < 1e-6 * np.linalg.norm(exact)
     # one application differs between the two coarse ends (the dense one is exact lower down)
     assert np.linalg.norm(V.apply(f) - T.apply(f)) > 1e-8 * np.linalg.norm(T.apply(f))
+
+
+def test_second_coarse_correction_right_hand_side():
+    """The F-cycle's second coarse correction at level l solves for
+    P^T (f - M_l (wj D^-1 f + P e)), e the first correction. Because the coarse operator
+    is the Galerkin product P^T M_l P and the restriction is P^T, this equals
+    f_{l+1} - M_{l+1} e with f_{l+1} = P^T (f - M_l wj D^-1 f) (level l + 1 data only),
+    and it vanishes when the first correction solved level l + 1 exactly. The CUDA cycle
+    uses both facts (it forms the right-hand side on level l + 1 and does nothing above
+    the dense level); here they are checked on the oracle's assembled operators against
+    the textbook form, which the oracle's cycle keeps."""
+    rng = np.random.default_rng(11)
+    mdl = models.c1_model()
+    m_pad = np.pad(mdl.slowness, 20, mode="edge")
+    hw2 = (mdl.h * mdl.omegas[0]) ** 2
+    V = mg.VCycle(m_pad ** 2, hw2, beta=(1.0, 0.5), omega_jacobi=0.5, coarse="dense")
+    for l in range(V.exact):
+        M, P, Mc = V.M[l], V.P[l], V.M[l + 1]
+        D = M.diagonal()
+        f = models.random_complex(rng, M.shape[0])
+        e = models.random_complex(rng, Mc.shape[0])
+        u1 = V.wj * f / D
+        fc = P.T @ (f - M @ u1)
+        textbook = P.T @ (f - M @ (u1 + P @ e))
+        assert np.linalg.norm(textbook - (fc - Mc @ e)) < 1e-12 * np.linalg.norm(textbook), l
+        if l + 1 == V.exact:
+            e_exact = V.cycle(fc, l + 1, "V")
+            r2 = P.T @ (f - M @ (u1 + P @ e_exact))
+            assert np.linalg.norm(r2) < 1e-12 * np.linalg.norm(fc)
+    # a planted mistake is seen: the identity fails if the coarse operator is not P^T M P
+    M, P = V.M[0], V.P[0]
+    e = models.random_complex(rng, P.shape[1])
+    wrong = 1.01 * V.M[1]
+    assert np.linalg.norm(P.T @ (M @ (P @ e)) - wrong @ e) > 1e-3 * np.linalg.norm(wrong @ e)
