@@ -432,4 +432,183 @@ __device__ __forceinline__ void prolong_tile_work(ProlongTile<T, GPX, GPZ>& sm, 
     }
 }
 
+// ------------------------------------------- two prolongations in one tile
+// The prolongation of level l + 1 (from e of level l + 2) followed by that of
+// level l, for the fine tile (x0, z0) of GPX x GPZ nodes of level l: the level l
+// + 1 values the tile's prolongation reads (ProlongTile::E, the tile's coarse
+// footprint) are computed in shared memory instead of being read back from a
+// kernel launched before: u2 = wj D^-1 f + P e on that footprint and a halo of
+// one, then u2 + wj D^-1 (f - M u2) (added to the level's previous correction when
+// acc_m). Each node's arithmetic is the one-level tile's, so the result is that of
+// the two launches; level l + 1's correction is not written (nothing reads it).
+template <typename T, int GPX, int GPZ>
+struct Prolong2Tile {
+    using PT = ProlongTile<T, GPX, GPZ>;
+    static constexpr int EW = PT::EW, EH = PT::EH;            // level l + 1 nodes the level l tile reads
+    static constexpr int MW = EW + 2, MH = EH + 2;            // their u2 region
+    static constexpr int CW = EW / 2 + 3, CH = EH / 2 + 3;    // level l + 2 footprint of that region (bound)
+    PT fine;
+    GalTile<T, MW, MH> MC;
+    cx<T> MF[MH][MW];
+    cx<T> MU[MH][MW];
+    cx<T> CE[CH][CW];
+};
+
+template <typename T, int GPX, int GPZ>
+__device__ __forceinline__ void prolong2_tile_stage(Prolong2Tile<T, GPX, GPZ>& sm, const LevelDev& Lf,
+                                                    const LevelDev& Lm, int bx, int by, int b, T hw, T b1, T b2,
+                                                    int tid) {
+    using P2 = Prolong2Tile<T, GPX, GPZ>;
+    prolong_tile_stage<T, GPX, GPZ>(sm.fine, Lf, bx, by, b, hw, b1, b2, tid);
+    const int ax0 = bx * GPX / 2 - 1, az0 = by * GPZ / 2 - 1;
+    stage_gal<T, P2::MW, P2::MH, GPX * GPZ>(sm.MC, Lm, b, hw * b1, hw * b2, ax0 - 1, az0 - 1, tid);
+}
+
+// fl, fm: right-hand sides of levels l and l + 1; ec: correction of level l + 2;
+// out: level l's correction (added to when acc_f); em: level l + 1's previous
+// correction (added when acc_m).
+template <typename T, int GPX, int GPZ, bool COH, class Sync>
+__device__ __forceinline__ void prolong2_tile_work(Prolong2Tile<T, GPX, GPZ>& sm, const LevelDev& Lf,
+                                                   const LevelDev& Lm, const LevelDev& Lc, T wj, const T* fl,
+                                                   const T* fm, const T* ec, const T* em, T* out, int acc_f,
+                                                   int acc_m, int bx, int by, int b, int tid, Sync sync) {
+    using P2 = Prolong2Tile<T, GPX, GPZ>;
+    using PT = typename P2::PT;
+    constexpr int NT = PT::NT, RW = PT::RW, RH = PT::RH, EW = P2::EW, EH = P2::EH;
+    constexpr int MW = P2::MW, MH = P2::MH, CW = P2::CW, CH = P2::CH;
+    constexpr int NF = RW * RH, NPT = (NF + NT - 1) / NT, NM = MW * MH, NMP = (NM + NT - 1) / NT;
+    const int x0 = bx * GPX, z0 = by * GPZ;
+    const int gx0 = x0 - 1, gz0 = z0 - 1;                  // level l region
+    const int ax0 = x0 / 2 - 1, az0 = z0 / 2 - 1;          // level l + 1 nodes read by the tile
+    const int mx0 = ax0 - 1, mz0 = az0 - 1;                // their u2 region
+    const int kx0 = (mx0 - 1) >> 1, kz0 = (mz0 - 1) >> 1;  // level l + 2 footprint
+    const size_t nf = (size_t)Lf.nx * Lf.nz, nm = (size_t)Lm.nx * Lm.nz, nc = (size_t)Lc.nx * Lc.nz;
+    const T* fb = fl + 2 * nf * b;
+    const T* mb = fm + 2 * nm * b;
+    // every global load of the tile, issued before any is used
+    cx<T> fpre[NPT], mpre[NMP];
+#pragma unroll
+    for (int k = 0; k < NPT; ++k) {
+        const int idx = tid + k * NT;
+        const int lz = idx / RW, lx = idx - lz * RW;
+        const int gx = gx0 + lx, gz = gz0 + lz;
+        fpre[k] = (idx < NF && gx >= 0 && gx < Lf.nx && gz >= 0 && gz < Lf.nz)
+                      ? ldv<COH>(fb, (size_t)gz * Lf.nx + gx) : cx<T>(0, 0);
+    }
+#pragma unroll
+    for (int k = 0; k < NMP; ++k) {
+        const int idx = tid + k * NT;
+        const int lz = idx / MW, lx = idx - lz * MW;
+        const int gx = mx0 + lx, gz = mz0 + lz;
+        mpre[k] = (idx < NM && gx >= 0 && gx < Lm.nx && gz >= 0 && gz < Lm.nz)
+                      ? ldv<COH>(mb, (size_t)gz * Lm.nx + gx) : cx<T>(0, 0);
+    }
+    T* ob = out + 2 * nf * b;
+    cx<T> opre(0, 0);
+    {
+        const int tz = tid / GPX, tx = tid - tz * GPX;
+        if (acc_f && x0 + tx < Lf.nx && z0 + tz < Lf.nz) {
+            const size_t i = (size_t)(z0 + tz) * Lf.nx + x0 + tx;
+            opre = COH ? ldv<true>(ob, i) : ldcc(ob, i);
+        }
+    }
+    // the previous level l + 1 correction at the nodes this thread finishes below
+    constexpr int NE = EW * EH, NEP = (NE + NT - 1) / NT;
+    const T* emb = em + 2 * nm * b;
+    cx<T> epre[NEP];
+#pragma unroll
+    for (int k = 0; k < NEP; ++k) {
+        const int idx = tid + k * NT;
+        const int lz = idx / EW, lx = idx - lz * EW;
+        const int I = ax0 + lx, K = az0 + lz;
+        epre[k] = (acc_m && idx < NE && I >= 0 && I < Lm.nx && K >= 0 && K < Lm.nz)
+                      ? (COH ? ldv<true>(emb, (size_t)K * Lm.nx + I) : ldcc(emb, (size_t)K * Lm.nx + I))
+                      : cx<T>(0, 0);
+    }
+    const T* eb = ec + 2 * nc * b;
+    for (int idx = tid; idx < CW * CH; idx += NT) {
+        const int lz = idx / CW, lx = idx - lz * CW;
+        const int I = kx0 + lx, K = kz0 + lz;
+        cx<T> e(0, 0);
+        if (I >= 0 && I < Lc.nx && K >= 0 && K < Lc.nz) e = ldv<COH>(eb, (size_t)K * Lc.nx + I);
+        sm.CE[lz][lx] = e;
+    }
+    sync();
+    // level l + 1: u2 = wj D^-1 f + P e on its region
+#pragma unroll
+    for (int k = 0; k < NMP; ++k) {
+        const int idx = tid + k * NT;
+        if (idx >= NM) break;
+        const int lz = idx / MW, lx = idx - lz * MW;
+        const int gx = mx0 + lx, gz = mz0 + lz;
+        const cx<T> fv = mpre[k];
+        cx<T> u(0, 0);
+        if (gx >= 0 && gx < Lm.nx && gz >= 0 && gz < Lm.nz) {
+            u = wj * cdiv(fv, sm.MC.c[0][lz][lx]);
+            int ia, ib, ka, kb;
+            T wa, wb, va, vb;
+            bil_axis<T>(gx, ia, ib, wa, wb);
+            bil_axis<T>(gz, ka, kb, va, vb);
+            ia -= kx0; ib -= kx0; ka -= kz0; kb -= kz0;
+            u = u + (va * wa) * sm.CE[ka][ia] + (va * wb) * sm.CE[ka][ib] + (vb * wa) * sm.CE[kb][ia] +
+                (vb * wb) * sm.CE[kb][ib];
+        }
+        sm.MF[lz][lx] = fv;
+        sm.MU[lz][lx] = u;
+    }
+    sync();
+    // level l + 1: the post-sweep on the nodes the level l tile reads, into its E
+#pragma unroll
+    for (int k = 0; k < NEP; ++k) {
+        const int idx = tid + k * NT;
+        if (idx >= NE) break;
+        const int lz = idx / EW, lx = idx - lz * EW;
+        const int gx = ax0 + lx, gz = az0 + lz;
+        cx<T> e(0, 0);
+        if (gx >= 0 && gx < Lm.nx && gz >= 0 && gz < Lm.nz) {
+            const int mx = lx + 1, mz = lz + 1;
+            const cx<T> c = sm.MU[mz][mx];
+            const cx<T> mu = mop9_staged<T, MW, MH>(sm.MC, Lm.nx, Lm.nz, gx, gz, mx, mz, &sm.MU[mz][mx]);
+            const cx<T> v = c + wj * cdiv(sm.MF[mz][mx] - mu, sm.MC.c[0][mz][mx]);
+            e = acc_m ? epre[k] + v : v;
+        }
+        sm.fine.E[lz][lx] = e;
+    }
+    sync();
+    // level l, as prolong_tile_work with its E above
+    const int cx0 = ax0, cz0 = az0;
+#pragma unroll
+    for (int k = 0; k < NPT; ++k) {
+        const int idx = tid + k * NT;
+        if (idx >= NF) break;
+        const int lz = idx / RW, lx = idx - lz * RW;
+        const int gx = gx0 + lx, gz = gz0 + lz;
+        const cx<T> fv = fpre[k];
+        cx<T> u(0, 0);
+        if (gx >= 0 && gx < Lf.nx && gz >= 0 && gz < Lf.nz) {
+            u = wj * cdiv(fv, sm.fine.C.c[0][lz][lx]);
+            int ia, ib, ka, kb;
+            T wa, wb, va, vb;
+            bil_axis<T>(gx, ia, ib, wa, wb);
+            bil_axis<T>(gz, ka, kb, va, vb);
+            ia -= cx0; ib -= cx0; ka -= cz0; kb -= cz0;
+            u = u + (va * wa) * sm.fine.E[ka][ia] + (va * wb) * sm.fine.E[ka][ib] + (vb * wa) * sm.fine.E[kb][ia] +
+                (vb * wb) * sm.fine.E[kb][ib];
+        }
+        sm.fine.F[lz][lx] = fv;
+        sm.fine.U2[lz][lx] = u;
+    }
+    sync();
+    const int tz = tid / GPX, tx = tid - tz * GPX;
+    const int gx = x0 + tx, gz = z0 + tz;
+    if (gx < Lf.nx && gz < Lf.nz) {
+        const int lx = tx + 1, lz = tz + 1;
+        const size_t i = (size_t)gz * Lf.nx + gx;
+        const cx<T> c = sm.fine.U2[lz][lx];
+        const cx<T> mu = mop9_staged<T, RW, RH>(sm.fine.C, Lf.nx, Lf.nz, gx, gz, lx, lz, &sm.fine.U2[lz][lx]);
+        const cx<T> v = c + wj * cdiv(sm.fine.F[lz][lx] - mu, sm.fine.C.c[0][lz][lx]);
+        stc(ob, i, acc_f ? opre + v : v);
+    }
+}
+
 }  // namespace helm

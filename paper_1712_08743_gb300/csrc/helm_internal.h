@@ -145,7 +145,7 @@ class NvtxRange {
 // its scope, with the kernel class, the grid and the launch's algorithmic bytes.
 enum ProfKernel : int {
     PK_APPLY, PK_APPLY_DOTS, PK_RESID64, PK_REFINE, PK_BICG_INIT, PK_BICG_RESUME, PK_BICG_P, PK_BICG_S, PK_BICG_XR,
-    PK_RESTRICT, PK_PROLONG, PK_RESTRICT_G, PK_CORRECT_RESTRICT, PK_RESID_RESTRICT, PK_PROLONG_G, PK_TAIL, PK_COARSE_DENSE,
+    PK_RESTRICT, PK_PROLONG, PK_RESTRICT_G, PK_CORRECT_RESTRICT, PK_RESID_RESTRICT, PK_PROLONG_G, PK_PROLONG2_G, PK_TAIL, PK_COARSE_DENSE,
     PK_DENSE_INVERT, PK_COARSE_INVERT, PK_FG_NORM, PK_FG_SCALE, PK_FG_DOTS, PK_FG_AXPY, PK_FG_FINISH,
     PK_FG_BACKSOLVE, PK_FG_UPDATE, PK_FCYCLE, PK_OTHER, PK_COUNT
 };
@@ -270,6 +270,14 @@ void launch_correct_restrict(const LevelDev& Lf, const LevelDev& Lc, const T* w2
 template <typename T>
 void launch_restrict(const LevelDev& Lf, const LevelDev& Lc, const T* w2, double b1, double b2,
                      double wj, const T* f, T* fc, const RhsState* st, int nrhs, cudaStream_t s, int tile = 1);
+// The prolongation of Galerkin level l + 1 (from e of level l + 2; right-hand side
+// fm, added to em when acc_m) and then that of level l (right-hand side fl, into
+// out, added to it when acc_f), in one launch; level l + 1's correction stays in
+// shared memory. tile: level l's prolongation tile code (0: 16 x 8, else 32 x 8).
+template <typename T>
+void launch_prolong2(const LevelDev& Lf, const LevelDev& Lm, const LevelDev& Lc, const T* w2, double b1, double b2,
+                     double wj, const T* fl, const T* fm, const T* ec, const T* em, T* out, const RhsState* st,
+                     int nrhs, cudaStream_t s, int acc_f, int acc_m, int tile);
 // The restriction that starts the second coarse correction of an F-cycle, on a
 // Galerkin level: g = f - M e (f this level's first right-hand side, e its first
 // correction) written to g, then restricted like launch_restrict does to fc.

@@ -966,6 +966,61 @@ template void launch_resid_restrict<double>(const LevelDev&, const LevelDev&, co
                                             const double*, const double*, double*, double*, const RhsState*, int,
                                             cudaStream_t, int);
 
+// two prolongations in one launch (tile body prolong2_tile_work): level l + 1's
+// from e of level l + 2, then level l's
+template <typename T, int GPX, int GPZ>
+__global__ void __launch_bounds__(GPX * GPZ) k_prolong2_g(LevelDev Lf, LevelDev Lm, LevelDev Lc,
+                                                          const T* __restrict__ hwv, T b1, T b2, T wj,
+                                                          const T* __restrict__ fl, const T* __restrict__ fm,
+                                                          const T* __restrict__ ec, const T* em, T* out,
+                                                          const RhsState* st, int acc_f, int acc_m) {
+    __shared__ Prolong2Tile<T, GPX, GPZ> sm;
+    pdl_trigger();
+    const int b = blockIdx.z;
+    prolong2_tile_stage<T, GPX, GPZ>(sm, Lf, Lm, blockIdx.x, blockIdx.y, b, hwv[b], b1, b2, threadIdx.x);
+    pdl_wait();
+    if (!rhs_active(st, b)) return;
+    prolong2_tile_work<T, GPX, GPZ, false>(sm, Lf, Lm, Lc, wj, fl, fm, ec, em, out, acc_f, acc_m, blockIdx.x,
+                                           blockIdx.y, b, threadIdx.x, BlockSync{});
+}
+
+template <typename T, int GPX, int GPZ>
+static void launch_prolong2_shape(const LevelDev& Lf, const LevelDev& Lm, const LevelDev& Lc, const T* w2, double b1,
+                                  double b2, double wj, const T* fl, const T* fm, const T* ec, const T* em, T* out,
+                                  const RhsState* st, int nrhs, cudaStream_t s, int acc_f, int acc_m) {
+    dim3 grd((Lf.nx + GPX - 1) / GPX, (Lf.nz + GPZ - 1) / GPZ, nrhs);
+    launch_pdl(k_prolong2_g<T, GPX, GPZ>, grd, dim3(GPX * GPZ), 0, s, Lf, Lm, Lc, w2, (T)b1, (T)b2, (T)wj, fl, fm, ec,
+               em, out, st, acc_f, acc_m);
+}
+
+template <typename T>
+void launch_prolong2(const LevelDev& Lf, const LevelDev& Lm, const LevelDev& Lc, const T* w2, double b1, double b2,
+                     double wj, const T* fl, const T* fm, const T* ec, const T* em, T* out, const RhsState* st,
+                     int nrhs, cudaStream_t s, int acc_f, int acc_m, int tile) {
+    const double nf = (double)Lf.nx * Lf.nz, nm = (double)Lm.nx * Lm.nz, nc = (double)Lc.nx * Lc.nz;
+    const double es = 2.0 * sizeof(T);
+    // the two prolongations' bytes without the level l + 1 correction between them:
+    // f and the output of both levels (the outputs read too when accumulating), e of
+    // level l + 2, the Galerkin coefficients of levels l and l + 1
+    ProfScope prof(PK_PROLONG2_G, Lf.nx, Lf.nz,
+                   (nf * (2 + acc_f) + nm * (1 + acc_m) + nc) * es * nrhs +
+                       (nf + nm) * sizeof(T) * kGalerkinCoefs * (Lf.gkstride ? nrhs : 1),
+                   s);
+    if constexpr (sizeof(T) == 4) {
+        if (tile != 0) {
+            launch_prolong2_shape<T, 32, 8>(Lf, Lm, Lc, w2, b1, b2, wj, fl, fm, ec, em, out, st, nrhs, s, acc_f, acc_m);
+            return;
+        }
+    }
+    launch_prolong2_shape<T, 16, 8>(Lf, Lm, Lc, w2, b1, b2, wj, fl, fm, ec, em, out, st, nrhs, s, acc_f, acc_m);
+}
+template void launch_prolong2<float>(const LevelDev&, const LevelDev&, const LevelDev&, const float*, double, double,
+                                     double, const float*, const float*, const float*, const float*, float*,
+                                     const RhsState*, int, cudaStream_t, int, int, int);
+template void launch_prolong2<double>(const LevelDev&, const LevelDev&, const LevelDev&, const double*, double, double,
+                                      double, const double*, const double*, const double*, const double*, double*,
+                                      const RhsState*, int, cudaStream_t, int, int, int);
+
 // Tile shapes of the complex64 Galerkin kernels, by the code the autotuner stores
 // per level (kGalTiles choices; 1 is the default): restriction coarse tile
 // (x, z) and prolongation fine tile (x, z), one thread per node of the tile. The

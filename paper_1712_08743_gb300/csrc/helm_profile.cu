@@ -48,8 +48,8 @@ cudaEvent_t prof_event() {
 const char* const kProfNames[PK_COUNT] = {
     "k_apply", "k_apply_dots", "k_resid64", "k_refine", "k_bicg_init", "k_bicg_resume", "k_bicg_p", "k_bicg_s",
     "k_bicg_xr", "k_restrict", "k_prolong", "k_restrict_g", "k_correct_restrict", "k_resid_restrict_g",
-    "k_prolong_g", "k_tail", "k_coarse_dense", "k_dense_invert", "k_coarse_invert", "k_fg_norm", "k_fg_scale", "k_fg_dots", "k_fg_axpy",
-    "k_fg_finish", "k_fg_backsolve", "k_fg_update", "k_fcycle", "k_other"};
+    "k_prolong_g", "k_prolong2_g", "k_tail", "k_coarse_dense", "k_dense_invert", "k_coarse_invert", "k_fg_norm",
+    "k_fg_scale", "k_fg_dots", "k_fg_axpy", "k_fg_finish", "k_fg_backsolve", "k_fg_update", "k_fcycle", "k_other"};
 
 }  // namespace
 

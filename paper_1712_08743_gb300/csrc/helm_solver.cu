@@ -158,30 +158,43 @@ static bool grid_level(const helm_model* m, const MgCall& c, int l, bool dbl) {
     return c.ld > 0 ? l < c.ld : l < m->tail_level(dbl);
 }
 
+// The prolongation that ends a cycle at level l, left to the caller (the cycle one
+// level up), which runs it together with its own in one launch (launch_prolong2).
+template <typename T>
+struct PendingProlong {
+    bool on = false;
+    const T* f = nullptr;   // the level's right-hand side
+    int acc = 0;            // added to the level's previous correction
+};
+
 // One cycle at level l (F or V) from the right-hand side B.f[l] into B.e[l] (added
 // to it when acc). resid: the right-hand side is B.f[l] - M_l B.e[l] instead (the
 // second coarse correction of the F-cycle one level up, always a V-cycle that
-// accumulates), formed by the first restriction and kept in B.g[l].
+// accumulates), formed by the first restriction and kept in B.g[l]. may_defer: the
+// caller fuses this cycle's last prolongation with its own; it is then returned,
+// not launched. A cycle fuses its last recursion's pending prolongation with its
+// own; the first recursion of an F-cycle never defers (its correction is read by
+// the restriction that follows).
 template <typename T>
-static void mg_cycle(const helm_model* m, const MgCall& c, const MgLevels<T>& B, int l, bool F, int acc,
-                     bool resid = false) {
+static PendingProlong<T> mg_cycle(const helm_model* m, const MgCall& c, const MgLevels<T>& B, int l, bool F, int acc,
+                                  bool resid, bool may_defer) {
     NvtxRange nv(kLevelNames[l]);
     const bool dbl = sizeof(T) == 8;
     const T* hw = hw_of<T>(c);
     if (c.fca && l == c.fca_level) {   // the whole cycle from here down in one persistent launch
         launch_fcycle(*c.fca, c.fca_grid, c.st, c.s);
-        return;
+        return {};
     }
     if (c.ld > 0 && l == c.ld) {   // exact solve of this level by its dense inverse
         launch_coarse_dense<T>((int)m->lv[l].n(), static_cast<const T*>(c.minv), c.slot, c.grp, c.ngroups, c.maxg,
                                B.f[l], B.e[l], acc, c.st, c.s);
-        return;
+        return {};
     }
     const int lt = m->tail_level(dbl);
     if (c.ld <= 0 && l >= lt) {
         const TailArgs a = tail_args<T>(m, F, B.f[l], B.e[l], acc, c.minv, c.slot, c.w2, c.b1, c.b2, c.wj);
         launch_tail<T>(a, m->tail_smem[dbl], c.nrhs, c.st, c.s);
-        return;
+        return {};
     }
     const LevelDev Lf = level_dev(m, l, dbl), Lc = level_dev(m, l + 1, dbl);
     if (resid)
@@ -189,22 +202,40 @@ static void mg_cycle(const helm_model* m, const MgCall& c, const MgLevels<T>& B,
                                  m->tile_restrict[l]);
     else
         launch_restrict<T>(Lf, Lc, hw, c.b1, c.b2, c.wj, B.f[l], B.f[l + 1], c.st, c.nrhs, c.s, m->tile_restrict[l]);
-    mg_cycle<T>(m, c, B, l + 1, F || (l + 1 == c.lf), 0);
+    PendingProlong<T> pend;
     if (F) {
+        mg_cycle<T>(m, c, B, l + 1, true, 0, false, false);
         // second coarse correction, for P^T (f - M (wj D^-1 f + P e)) = f_{l+1} - M_{l+1} e_{l+1}
         // (Galerkin M_{l+1} = P^T M P): zero when level l + 1 was solved exactly by its dense
         // inverse, so nothing is done then; on a grid level it is formed there, by the first
         // restriction of the correction's V-cycle
         if (grid_level(m, c, l + 1, dbl)) {
-            mg_cycle<T>(m, c, B, l + 1, false, 1, true);
+            pend = mg_cycle<T>(m, c, B, l + 1, false, 1, true, true);
         } else if (c.ld <= 0) {
             launch_correct_restrict<T>(Lf, Lc, hw, c.b1, c.b2, c.wj, B.f[l], B.e[l + 1], B.f[l + 1], c.st, c.nrhs,
                                        c.s, m->tile_restrict[l]);
-            mg_cycle<T>(m, c, B, l + 1, false, 1);
+            pend = mg_cycle<T>(m, c, B, l + 1, false, 1, false, true);
         }
+    } else {
+        pend = mg_cycle<T>(m, c, B, l + 1, l + 1 == c.lf, 0, false, true);
     }
-    launch_prolong<T>(0, Lf, Lc, m->npml, m->alpha_max, hw, c.b1, c.b2, c.wj, resid ? B.g[l] : B.f[l], B.e[l + 1],
-                      B.e[l], nullptr, nullptr, nullptr, 0, c.st, c.nrhs, c.s, acc, m->tile_prolong[l]);
+    const T* fl = resid ? B.g[l] : B.f[l];
+    if (pend.on) {   // level l + 1's prolongation and this level's in one launch
+        const LevelDev Lk = level_dev(m, l + 2, dbl);
+        launch_prolong2<T>(Lf, Lc, Lk, hw, c.b1, c.b2, c.wj, fl, pend.f, B.e[l + 2], B.e[l + 1], B.e[l], c.st,
+                           c.nrhs, c.s, acc, pend.acc, m->tile_prolong[l]);
+        return {};
+    }
+    if (may_defer) {
+        PendingProlong<T> mine;
+        mine.on = true;
+        mine.f = fl;
+        mine.acc = acc;
+        return mine;
+    }
+    launch_prolong<T>(0, Lf, Lc, m->npml, m->alpha_max, hw, c.b1, c.b2, c.wj, fl, B.e[l + 1], B.e[l], nullptr,
+                      nullptr, nullptr, 0, c.st, c.nrhs, c.s, acc, m->tile_prolong[l]);
+    return {};
 }
 
 template <typename T>
@@ -214,7 +245,7 @@ void mg_apply(const helm_model* m, const MgCall& c, const MgLevels<T>& B, const 
     const T* hw = hw_of<T>(c);
     const LevelDev L0 = level_dev(m, 0, dbl), L1 = level_dev(m, 1, dbl);
     launch_restrict<T>(L0, L1, hw, c.b1, c.b2, c.wj, in, B.f[1], c.st, c.nrhs, c.s);
-    mg_cycle<T>(m, c, B, 1, c.lf == 1, 0);
+    mg_cycle<T>(m, c, B, 1, c.lf == 1, 0, false, false);
     if (m->vd && mode != 0) {
         // variable density: the stored-level prolongation, then y = A out (with the
         // dots of modes 1 and 2) in a separate kernel
@@ -235,19 +266,30 @@ template void mg_apply<float>(const helm_model*, const MgCall&, const MgLevels<f
 template void mg_apply<double>(const helm_model*, const MgCall&, const MgLevels<double>&, const double*, double*, int,
                                double*, const double*);
 
-static int count_cycle(const helm_model* m, int lt, int l, bool F, int lf, int ld, int fl = 0) {
+// Launches of mg_cycle at level l; *pend: its last prolongation is left to the caller.
+static int count_cycle(const helm_model* m, int lt, int l, bool F, int lf, int ld, int fl, bool may_defer,
+                       bool* pend) {
+    *pend = false;
     if (fl > 0 && l == fl) return 1;
     if (ld > 0 ? l == ld : l >= lt) return 1;
-    int k = 2 + count_cycle(m, lt, l + 1, F || (l + 1 == lf), lf, ld, fl);
-    if (F) {   // as mg_cycle: nothing above the dense level, the correction's V-cycle on a grid level
+    int k = 1;
+    bool cp = false;
+    if (F) {
+        k += count_cycle(m, lt, l + 1, true, lf, ld, fl, false, &cp);
         const bool grid = ld > 0 ? l + 1 < ld : l + 1 < lt;
-        if (grid) k += count_cycle(m, lt, l + 1, false, lf, ld, fl);
-        else if (ld <= 0) k += 1 + count_cycle(m, lt, l + 1, false, lf, ld, fl);
+        if (grid) k += count_cycle(m, lt, l + 1, false, lf, ld, fl, true, &cp);
+        else if (ld <= 0) k += 1 + count_cycle(m, lt, l + 1, false, lf, ld, fl, true, &cp);
+        else cp = false;
+    } else {
+        k += count_cycle(m, lt, l + 1, l + 1 == lf, lf, ld, fl, true, &cp);
     }
-    return k;
+    if (cp) return k + 1;
+    if (may_defer) { *pend = true; return k; }
+    return k + 1;
 }
 int mg_kernels_per_apply(const helm_model* m, bool dbl, int lf, int ld, int fl) {
-    return 2 + (m->vd ? 1 : 0) + count_cycle(m, m->tail_level(dbl), 1, lf == 1, lf, ld, fl);
+    bool pend = false;
+    return 2 + (m->vd ? 1 : 0) + count_cycle(m, m->tail_level(dbl), 1, lf == 1, lf, ld, fl, false, &pend);
 }
 
 int fcycle_setup(const helm_model* m, const MgCall& c, int coarse, float* const* f, float* const* e,
