@@ -302,9 +302,10 @@ def profile_solve(lib, _lib, step_fn):
     return per, grids
 
 
-def traffic_for(kernel: str, grid: str):
-    """DRAM bytes per launch of `kernel` on `grid` from the committed ncu summary,
-    when the summary was taken of the kernel's current source (else None)."""
+def traffic_for(kernel: str, grids):
+    """DRAM bytes per launch of `kernel` in the profiled solve: the committed ncu summary
+    of its launches, per level grid, weighted by the solve's own launches on each grid,
+    when the summary was taken of the kernel's current sources (else None)."""
     import hashlib
 
     prof = os.path.join(ROOT, "profiles", "traffic.json")
@@ -313,14 +314,20 @@ def traffic_for(kernel: str, grid: str):
     with open(prof) as f:
         tr = json.load(f)
     e = tr.get(kernel)
-    if not isinstance(e, dict) or e.get("grid") != grid:
+    if not isinstance(e, dict) or "by_grid" not in e:
         return None
-    src = os.path.join(ROOT, "paper_1712_08743_gb300", "csrc", e.get("file", ""))
-    if not os.path.exists(src):
+    for fn, sha in e.get("src_sha1", {}).items():
+        src = os.path.join(ROOT, "paper_1712_08743_gb300", "csrc", fn)
+        if not os.path.exists(src):
+            return None
+        with open(src, "rb") as f:
+            if hashlib.sha1(f.read()).hexdigest() != sha:
+                return None
+    mine = [g for g in grids if g["kernel"] == kernel]
+    if not mine or any(g["grid"] not in e["by_grid"] for g in mine):
         return None
-    with open(src, "rb") as f:
-        sha = hashlib.sha1(f.read()).hexdigest()
-    return e.get("traffic") if e.get("src_sha1") == sha else None
+    n = sum(g["launches"] for g in mine)
+    return sum(g["launches"] * e["by_grid"][g["grid"]] for g in mine) / n
 
 
 def run_kernels_only(args):
@@ -579,11 +586,10 @@ def run_ours(args):
     total_ms = sum(d["ms"] for d in per.values())
     total_bytes = sum(d["bytes"] for d in per.values())
     dom = max(per, key=lambda k: per[k]["ms"])
-    dgrid = max((g for g in grids if g["kernel"] == dom), key=lambda g: g["ms"])
     achieved = per[dom]["bytes"] / (per[dom]["ms"] * 1e-3) / 1e9
     kern = time_kernels(lib, api, _lib, model, float(om[0]))
     roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": achieved / peak, "traffic": traffic_for(dom, dgrid["grid"]),
+            "frac": achieved / peak, "traffic": traffic_for(dom, grids),
             "peak_kind": f"{peak_kind} burst copy",
             "bytes_per_launch": per[dom]["bytes"] / per[dom]["launches"],
             "ms_per_launch": per[dom]["ms"] / per[dom]["launches"], "launches": per[dom]["launches"],
