@@ -474,6 +474,10 @@ void launch_fg_dots(const T* V, size_t vstride, const T* w, int j, int add, int 
     if (j < 1) fg_dots_nv<T, 1>(V, vstride, w, j, add, wnorm, check, partials, pstride, st, fg, n, nrhs, s);
     else if (j < 2) fg_dots_nv<T, 2>(V, vstride, w, j, add, wnorm, check, partials, pstride, st, fg, n, nrhs, s);
     else if (j < 4) fg_dots_nv<T, 4>(V, vstride, w, j, add, wnorm, check, partials, pstride, st, fg, n, nrhs, s);
+    else if (j < kChunk) fg_dots_nv<T, kChunk>(V, vstride, w, j, add, wnorm, check, partials, pstride, st, fg, n, nrhs, s);
+    // 9 .. 12 vectors in one pass over w (two chunks of eight would read w twice, and the second,
+    // short chunk would run as a second, light wave)
+    else if (j < 12) fg_dots_nv<T, 12>(V, vstride, w, j, add, wnorm, check, partials, pstride, st, fg, n, nrhs, s);
     else fg_dots_nv<T, kChunk>(V, vstride, w, j, add, wnorm, check, partials, pstride, st, fg, n, nrhs, s);
 }
 template <typename T, int NV>
