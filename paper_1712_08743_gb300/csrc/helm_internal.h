@@ -30,11 +30,13 @@ constexpr int kMaxRestart = 32;
 // 1 is the default shape
 constexpr int kProlongTiles = 5;
 constexpr int kRestrictTiles = 5;
-constexpr int kGalerkinCoefs = 10;
+constexpr int kGalerkinCoefs = 10;   // per coarse node: G (c, e, n, ne, nw) then K (c, e, n, ne, nw)
 // the first level with at most this many nodes is solved exactly by its dense inverse
 // (few right-hand sides; see helm_dense.cu)
 constexpr int kDenseMaxPoints = 1200;
-constexpr int kDenseAutoMaxRhs = 16;   // HELM_COARSE_AUTO takes the dense level for batches up to this size      // per coarse node: G (c, e, n, ne, nw) then K (c, e, n, ne, nw)
+constexpr int kDenseAutoMaxRhs = 16;   // HELM_COARSE_AUTO takes the dense level for batches up to this size
+// the cycle fuses consecutive Galerkin prolongations (launch_prolong2) for batches up to this size
+constexpr int kProlong2MaxRhs = kDenseAutoMaxRhs;
 
 // One multigrid level as the kernels see it. The finest level carries the
 // squared slowness m2 and the 5-point operator; every coarser level carries

@@ -202,6 +202,9 @@ static PendingProlong<T> mg_cycle(const helm_model* m, const MgCall& c, const Mg
                                  m->tile_restrict[l]);
     else
         launch_restrict<T>(Lf, Lc, hw, c.b1, c.b2, c.wj, B.f[l], B.f[l + 1], c.st, c.nrhs, c.s, m->tile_restrict[l]);
+    // prolongation pairs for small batches only: there the launches are latency chains; with
+    // many right-hand sides the recomputed level l + 1 footprint costs more than it saves
+    const bool pair = c.nrhs <= kProlong2MaxRhs;
     PendingProlong<T> pend;
     if (F) {
         mg_cycle<T>(m, c, B, l + 1, true, 0, false, false);
@@ -210,14 +213,14 @@ static PendingProlong<T> mg_cycle(const helm_model* m, const MgCall& c, const Mg
         // inverse, so nothing is done then; on a grid level it is formed there, by the first
         // restriction of the correction's V-cycle
         if (grid_level(m, c, l + 1, dbl)) {
-            pend = mg_cycle<T>(m, c, B, l + 1, false, 1, true, true);
+            pend = mg_cycle<T>(m, c, B, l + 1, false, 1, true, pair);
         } else if (c.ld <= 0) {
             launch_correct_restrict<T>(Lf, Lc, hw, c.b1, c.b2, c.wj, B.f[l], B.e[l + 1], B.f[l + 1], c.st, c.nrhs,
                                        c.s, m->tile_restrict[l]);
-            pend = mg_cycle<T>(m, c, B, l + 1, false, 1, false, true);
+            pend = mg_cycle<T>(m, c, B, l + 1, false, 1, false, pair);
         }
     } else {
-        pend = mg_cycle<T>(m, c, B, l + 1, l + 1 == c.lf, 0, false, true);
+        pend = mg_cycle<T>(m, c, B, l + 1, l + 1 == c.lf, 0, false, pair);
     }
     const T* fl = resid ? B.g[l] : B.f[l];
     if (pend.on) {   // level l + 1's prolongation and this level's in one launch
@@ -268,28 +271,29 @@ template void mg_apply<double>(const helm_model*, const MgCall&, const MgLevels<
 
 // Launches of mg_cycle at level l; *pend: its last prolongation is left to the caller.
 static int count_cycle(const helm_model* m, int lt, int l, bool F, int lf, int ld, int fl, bool may_defer,
-                       bool* pend) {
+                       bool pair, bool* pend) {
     *pend = false;
     if (fl > 0 && l == fl) return 1;
     if (ld > 0 ? l == ld : l >= lt) return 1;
     int k = 1;
     bool cp = false;
     if (F) {
-        k += count_cycle(m, lt, l + 1, true, lf, ld, fl, false, &cp);
+        k += count_cycle(m, lt, l + 1, true, lf, ld, fl, false, pair, &cp);
         const bool grid = ld > 0 ? l + 1 < ld : l + 1 < lt;
-        if (grid) k += count_cycle(m, lt, l + 1, false, lf, ld, fl, true, &cp);
-        else if (ld <= 0) k += 1 + count_cycle(m, lt, l + 1, false, lf, ld, fl, true, &cp);
+        if (grid) k += count_cycle(m, lt, l + 1, false, lf, ld, fl, pair, pair, &cp);
+        else if (ld <= 0) k += 1 + count_cycle(m, lt, l + 1, false, lf, ld, fl, pair, pair, &cp);
         else cp = false;
     } else {
-        k += count_cycle(m, lt, l + 1, l + 1 == lf, lf, ld, fl, true, &cp);
+        k += count_cycle(m, lt, l + 1, l + 1 == lf, lf, ld, fl, pair, pair, &cp);
     }
     if (cp) return k + 1;
     if (may_defer) { *pend = true; return k; }
     return k + 1;
 }
-int mg_kernels_per_apply(const helm_model* m, bool dbl, int lf, int ld, int fl) {
+int mg_kernels_per_apply(const helm_model* m, bool dbl, int lf, int ld, int fl, int nrhs) {
     bool pend = false;
-    return 2 + (m->vd ? 1 : 0) + count_cycle(m, m->tail_level(dbl), 1, lf == 1, lf, ld, fl, false, &pend);
+    return 2 + (m->vd ? 1 : 0) +
+           count_cycle(m, m->tail_level(dbl), 1, lf == 1, lf, ld, fl, false, nrhs <= kProlong2MaxRhs, &pend);
 }
 
 int fcycle_setup(const helm_model* m, const MgCall& c, int coarse, float* const* f, float* const* e,
@@ -458,8 +462,8 @@ static int alloc_inner(const SolveCtx& c, Inner<T>& w) {
 
 // kernels one BiCGSTAB iteration launches: p, s and x/r updates plus two
 // preconditioner applications
-static int kernels_per_iteration(const helm_model* m, bool dbl, int precond, int lf, int ld, int fl) {
-    return precond == HELM_PRECOND_NONE ? 5 : 3 + 2 * mg_kernels_per_apply(m, dbl, lf, ld, fl);
+static int kernels_per_iteration(const helm_model* m, bool dbl, int precond, int lf, int ld, int fl, int nrhs) {
+    return precond == HELM_PRECOND_NONE ? 5 : 3 + 2 * mg_kernels_per_apply(m, dbl, lf, ld, fl, nrhs);
 }
 
 template <typename T>
@@ -532,7 +536,8 @@ static int inner_solve(const SolveCtx& c, Inner<T>& w, const T* rin, cudaGraphEx
         } else {
             for (int k = 0; k < chunk; ++k) bicg_iteration<T>(c, w);
         }
-        count_launches((unsigned long long)chunk * kernels_per_iteration(c.m, sizeof(T) == 8, c.o.precond, c.lf, c.ld, c.fca ? c.fca_level : 0));
+        count_launches((unsigned long long)chunk * kernels_per_iteration(c.m, sizeof(T) == 8, c.o.precond, c.lf, c.ld, c.fca ? c.fca_level : 0,
+                                                             c.nrhs));
         done += chunk;
         HELM_CUDA_TRY(cudaMemcpyAsync(&h_active, c.nactive, sizeof(int), cudaMemcpyDeviceToHost, c.s));
         if (guard_iters > 0)
@@ -663,7 +668,7 @@ static int fgmres_inner(const SolveCtx& c, Inner<T>& w, FgBufs<T>& f, const T* r
         fgmres_cycle<T>(c, w, f, rin);
     }
     const int m = f.dev.m;
-    count_launches(4 + (unsigned long long)m * ((c.o.precond == HELM_PRECOND_NONE ? 1 : mg_kernels_per_apply(c.m, sizeof(T) == 8, c.lf, c.ld, c.fca ? c.fca_level : 0)) +
+    count_launches(4 + (unsigned long long)m * ((c.o.precond == HELM_PRECOND_NONE ? 1 : mg_kernels_per_apply(c.m, sizeof(T) == 8, c.lf, c.ld, c.fca ? c.fca_level : 0, c.nrhs)) +
                                                 (c.o.reorth == HELM_REORTH_NEVER ? 3 : c.o.reorth == HELM_REORTH_ALWAYS ? 5 : 4)));
     HELM_CUDA_TRY(cudaGetLastError());
     *iters_done += m;

@@ -93,7 +93,7 @@ struct MgLevels {
 template <typename T>
 void mg_apply(const helm_model* m, const MgCall& c, const MgLevels<T>& B, const T* in, T* out, int mode, T* y,
               const T* aux);
-int mg_kernels_per_apply(const helm_model* m, bool dbl, int lf, int ld, int fl = 0);
+int mg_kernels_per_apply(const helm_model* m, bool dbl, int lf, int ld, int fl = 0, int nrhs = 1);
 
 int autotune(helm_model* m, cudaStream_t s, int nrhs, double hw2, int reps, int* out);
 int time_kernel(const helm_model* m, cudaStream_t s, int kernel, int nrhs, double hw2, int reps, double* ms,
