@@ -384,35 +384,44 @@ __global__ void __launch_bounds__(256) k_fg_finish(const double* partials, int p
 // stages the triangle and g in shared memory with all its loads in flight, then
 // lane 0 substitutes backwards.
 __global__ void __launch_bounds__(32) k_fg_backsolve(const RhsState* st, FgDev fg) {
-    extern __shared__ double2 fg_tri[];                  // R [k][k] (upper part), then g [k]
+    // y = R^-1 g by columns: lane q holds the right-hand side entry q; at step i the lane
+    // holding row i finishes y_i with the reciprocal of R_ii (all reciprocals formed
+    // together beforehand, so no division sits on the chain) and every lane q < i
+    // subtracts R_qi y_i. The chain is k steps of one complex product, one shuffle and
+    // one complex multiply-add in FP64, instead of k divisions and k (k - 1) / 2
+    // sequential multiply-adds on one thread.
     const int b = blockIdx.x;
     if (!st[b].outer_active) return;
-    const int m = fg.m, k = st[b].kfg;
+    const int m = fg.m, k = st[b].kfg, lane = threadIdx.x;   // k <= kMaxRestart = 32
     const size_t col = (size_t)b * (m + 1);
     const double2* H = fg.H + col * m;
-    double2* R = fg_tri;
-    double2* gk = fg_tri + k * k;
-    for (int idx = threadIdx.x; idx < k * k; idx += 32) {
+    __shared__ double2 R[kMaxRestart][kMaxRestart + 1];   // the triangle, staged once
+    for (int idx = lane; idx < k * k; idx += 32) {
         const int i = idx / k, q = idx - i * k;
-        if (q >= i) R[idx] = H[(size_t)i * m + q];
+        if (q >= i) R[i][q] = H[(size_t)i * m + q];
     }
-    for (int i = threadIdx.x; i < k; i += 32) gk[i] = fg.g[col + i];
     __syncwarp();
-    if (threadIdx.x != 0) return;
+    double2 acc = lane < k ? fg.g[col + lane] : make_double2(0.0, 0.0);
+    double2 rinv = make_double2(0.0, 0.0);
+    if (lane < k) {
+        const double2 d = R[lane][lane];
+        const double dd = d.x * d.x + d.y * d.y;
+        if (dd > 0.0) {
+            const double inv = 1.0 / dd;
+            rinv = make_double2(d.x * inv, -d.y * inv);
+        }
+    }
     double2* y = fg.y + (size_t)b * m;
     for (int i = k - 1; i >= 0; --i) {
-        double2 acc = gk[i];
-        for (int q = i + 1; q < k; ++q) {
-            const double2 h = R[i * k + q], yq = gk[q];      // gk[q] holds y_q once solved
-            acc.x -= h.x * yq.x - h.y * yq.y;
-            acc.y -= h.x * yq.y + h.y * yq.x;
+        double2 yi = make_double2(acc.x * rinv.x - acc.y * rinv.y, acc.x * rinv.y + acc.y * rinv.x);
+        yi.x = __shfl_sync(0xffffffffu, yi.x, i);
+        yi.y = __shfl_sync(0xffffffffu, yi.y, i);
+        if (lane == i) y[i] = yi;
+        if (lane < i) {
+            const double2 h = R[lane][i];
+            acc.x -= h.x * yi.x - h.y * yi.y;
+            acc.y -= h.x * yi.y + h.y * yi.x;
         }
-        const double2 d = R[i * k + i];
-        const double dd = d.x * d.x + d.y * d.y;
-        const double2 yi = dd > 0.0 ? make_double2((acc.x * d.x + acc.y * d.y) / dd, (acc.y * d.x - acc.x * d.y) / dd)
-                                    : make_double2(0.0, 0.0);
-        gk[i] = yi;
-        y[i] = yi;
     }
 }
 
@@ -505,8 +514,7 @@ void launch_fg_finish(const double* partials, int pstride, int nblk, RhsState* s
 }
 void launch_fg_backsolve(const RhsState* st, const FgDev& fg, int nrhs, cudaStream_t s) {
     ProfScope prof(PK_FG_BACKSOLVE, fg.m, 1, (double)fg.m * fg.m * nrhs * 16.0, s);
-    const size_t smem = sizeof(double2) * ((size_t)fg.m * fg.m + fg.m);
-    k_fg_backsolve<<<nrhs, 32, smem, s>>>(st, fg);
+    k_fg_backsolve<<<nrhs, 32, 0, s>>>(st, fg);
 }
 template <typename T>
 void launch_fg_update(const T* Z, size_t zstride, T* x, const RhsState* st, const FgDev& fg, size_t n, int nrhs,
