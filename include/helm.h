@@ -387,8 +387,8 @@ int helm_vcycle_noalloc(helm_model* model, int nrhs, const double* omega, double
  * multigrid kernel on the grid levels of this model for nrhs right-hand sides at
  * angular frequency omega, keeps the fastest in the model, and writes the choices
  * to tiles_out (nullable): int[48], restriction tiles per level then prolongation
- * tiles per level. Galerkin levels: restriction 0..4 (coarse tiles 8x8, 16x8,
- * 32x4, 8x16, and 8x8 on two threads per node), prolongation 0..4 (fine tiles
+ * tiles per level. Galerkin levels: restriction 0..5 (coarse tiles 8x8, 16x8,
+ * 32x4, 8x16, 8x8 on two threads per node, 8x16 on two threads per node), prolongation 0..4 (fine tiles
  * 16x8, 32x8, 64x4, 32x16, 128x2);
  * the finest level's prolongation 0..1 (row segments of 16 or 32 rows); 1 is
  * the default everywhere. helm_set_tiles applies a stored choice. Tile shapes

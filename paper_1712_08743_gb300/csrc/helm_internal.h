@@ -29,7 +29,7 @@ constexpr int kMaxRestart = 32;
 // tile-shape choices of the complex64 Galerkin kernels (launch_prolong_g / launch_restrict_g);
 // 1 is the default shape
 constexpr int kProlongTiles = 5;
-constexpr int kRestrictTiles = 5;
+constexpr int kRestrictTiles = 6;
 constexpr int kGalerkinCoefs = 10;   // per coarse node: G (c, e, n, ne, nw) then K (c, e, n, ne, nw)
 // the first level with at most this many nodes is solved exactly by its dense inverse
 // (few right-hand sides; see helm_dense.cu)

@@ -1026,7 +1026,8 @@ template void launch_prolong2<double>(const LevelDev&, const LevelDev&, const Le
 // (x, z) and prolongation fine tile (x, z), one thread per node of the tile. The
 // shapes keep each block's shared memory within 48 KB.
 //   0: 8 x 8 / 16 x 8,  1: 16 x 8 / 32 x 8,  2: 32 x 4 / 64 x 4,  3: 8 x 16 / 32 x 16,  4: 8 x 8 on 128
-//   threads (two per coarse node, for short per-thread chains on small levels) / 128 x 2
+//   threads (two per coarse node, for short per-thread chains on small levels) / 128 x 2,
+//   5 (restriction only): 8 x 16 on 256 threads (two per coarse node)
 template <typename T, bool CORRECT, int GRCX, int GRCZ, int NT = GRCX * GRCZ>
 void launch_restrict_g_shape(const LevelDev& Lf, const LevelDev& Lc, const T* w2, double b1, double b2, double wj,
                              const T* f, const T* ec, T* fc, const RhsState* st, int nrhs, cudaStream_t s) {
@@ -1043,6 +1044,7 @@ void launch_restrict_g(int tile, const LevelDev& Lf, const LevelDev& Lc, const T
             case 2: launch_restrict_g_shape<T, CORRECT, 32, 4>(Lf, Lc, w2, b1, b2, wj, f, ec, fc, st, nrhs, s); return;
             case 3: launch_restrict_g_shape<T, CORRECT, 8, 16>(Lf, Lc, w2, b1, b2, wj, f, ec, fc, st, nrhs, s); return;
             case 4: launch_restrict_g_shape<T, CORRECT, 8, 8, 128>(Lf, Lc, w2, b1, b2, wj, f, ec, fc, st, nrhs, s); return;
+            case 5: launch_restrict_g_shape<T, CORRECT, 8, 16, 256>(Lf, Lc, w2, b1, b2, wj, f, ec, fc, st, nrhs, s); return;
             default: break;
         }
     }

@@ -217,17 +217,19 @@ def test_autotuned_tiles_give_the_same_wavefields(hg, ctx, tmp_path):
     tiles = autotune.autotune(model, len(om), float(om[0]), str(tmp_path / "t.json"))
     n = autotune.NTILES // 2
     assert len(tiles) == autotune.NTILES
-    assert all(0 <= t <= 4 for t in tiles[:n]) and all(0 <= t <= 4 for t in tiles[n:]) and tiles[n] <= 1
+    assert all(0 <= t <= 5 for t in tiles[:n]) and all(0 <= t <= 4 for t in tiles[n:]) and tiles[n] <= 1
     import ctypes as C
-    for code in [None, 0, 2, 3, 4]:
-        if code is not None:   # the same shape code on every level (finest prolongation: 0 or 1)
-            arr = [code] * n + [min(code, 1)] + [code] * (n - 1)
+    for code in [None, 0, 2, 3, 4, 5]:
+        if code is not None:   # the same shape code on every level (finest prolongation: 0 or 1;
+            # restriction-only code 5: prolongation code 1)
+            pc = min(code, 4) if code < 5 else 1
+            arr = [code] * n + [min(pc, 1)] + [pc] * (n - 1)
             assert model.lib.helm_set_tiles(model.handle, (C.c_int * autotune.NTILES)(*arr)) == 0
         u1, st, _ = hg.helm_solve(model, om, src, opts=opts)
         assert all(s["converged"] for s in st)
         for k in range(len(om)):
             assert rel(u1[k], u0[k]) < 1e-6   # dot products sum in another order; tol 1e-9 solves
-    bad = (C.c_int * autotune.NTILES)(*([5] * autotune.NTILES))
+    bad = (C.c_int * autotune.NTILES)(*([6] * autotune.NTILES))
     assert model.lib.helm_set_tiles(model.handle, bad) == hg.HELM_E_INVALID
     model.close()
 
