@@ -90,7 +90,9 @@ typedef enum { HELM_REORTH_ALWAYS = 0, HELM_REORTH_NEVER = 1, HELM_REORTH_IFNEED
  *  - HELM_COARSE_DENSE: the first level with at most 1200 nodes is solved
  *    exactly by its dense inverse (computed once per solve for each distinct
  *    model and frequency by block Gauss-Jordan, applied by a matrix-vector
- *    kernel); the cycle above it runs one kernel launch per step. It needs
+ *    kernel); the cycle above it runs one kernel launch per step (for batches
+ *    of at most 16 right-hand sides two consecutive prolongations share one
+ *    launch). It needs
  *    beta2 != 0, which keeps every pivot away from zero, and falls back to the
  *    tail otherwise.
  *  - HELM_COARSE_TAIL: the levels from the first with at most 2048 (complex64)

@@ -93,6 +93,26 @@ def test_vcycle_matches_restatement(hg, ctx, name, make):
     model.close()
 
 
+@pytest.mark.parametrize("name,make", GRIDS)
+def test_fused_prolongation_pairs_equal_separate_launches(hg, ctx, name, make):
+    """Batches of at most 16 right-hand sides prolong two consecutive Galerkin levels in one
+    launch (the finer level's correction recomputed in shared memory); larger batches launch
+    them one by one. The same right-hand side alone and as the first of a batch of 17 (dense
+    coarse end in both) must give the same cycle to complex64 rounding."""
+    mdl = make()
+    model = hg.helm_create_model(ctx, mdl.slowness, mdl.h, mdl.npml, mdl.alpha_max)
+    rng = np.random.default_rng(5)
+    r = models.random_complex(rng, (1, model.nz, model.nx), np.complex64)
+    om = 2 * np.pi * np.array([5.0])
+    z1 = hg.helm_vcycle(model, om, r, (1.0, 0.5), 0.8, coarse=hg.HELM_COARSE_DENSE)
+    z17 = hg.helm_vcycle(model, np.repeat(om, 17), np.repeat(r, 17, axis=0), (1.0, 0.5), 0.8,
+                         coarse=hg.HELM_COARSE_DENSE)
+    assert np.all(np.isfinite(z1))
+    for k in (0, 16):
+        assert rel(z17[k], z1[0]) < 1e-6, (name, k, rel(z17[k], z1[0]))
+    model.close()
+
+
 @pytest.mark.parametrize("precision,tol,bound", [("fp64", 1e-10, 1e-6), ("mixed", 1e-10, 1e-6), ("fp32", 5e-5, 1e-4)])
 def test_c1_wavefield_matches_oracle(hg, ctx, precision, tol, bound):
     mdl = models.c1_model()
