@@ -96,6 +96,48 @@ __device__ __forceinline__ void stage_gal(GalTile<T, W, H>& t, const LevelDev& L
     }
 }
 
+// The real Galerkin coefficients of a tile region (G then K, five entries each),
+// which do not depend on the frequency: a block working on several right-hand
+// sides of one model stages them once, then forms each right-hand side's complex
+// coefficients from shared memory (form_gal) instead of reading them again.
+template <typename T, int W, int H>
+struct GalReal {
+    T g[kGalerkinCoefs][H][W];
+};
+
+template <typename T, int W, int H, int NT>
+__device__ __forceinline__ void stage_gal_real(GalReal<T, W, H>& t, const LevelDev& L, int gx0, int gz0, int tid) {
+    const T* gk = static_cast<const T*>(L.gk);
+    const size_t n = (size_t)L.nx * L.nz;
+#pragma unroll
+    for (int k = 0; k < (W * H + NT - 1) / NT; ++k) {
+        const int idx = tid + k * NT;
+        if (idx >= W * H) break;
+        const int lz = idx / W, lx = idx - lz * W;
+        const int gx = gx0 + lx, gz = gz0 + lz;
+        const bool in = gx >= 0 && gx < L.nx && gz >= 0 && gz < L.nz;
+        const size_t i = in ? (size_t)gz * L.nx + gx : 0;
+        T v[kGalerkinCoefs];
+#pragma unroll
+        for (int q = 0; q < kGalerkinCoefs; ++q) v[q] = in ? __ldg(gk + (size_t)q * n + i) : T(0);
+#pragma unroll
+        for (int q = 0; q < kGalerkinCoefs; ++q) t.g[q][lz][lx] = v[q];
+    }
+}
+
+// M_k = G_k - hw (b1 - j b2) K_k of the staged region, as stage_gal forms it
+template <typename T, int W, int H, int NT>
+__device__ __forceinline__ void form_gal(GalTile<T, W, H>& t, const GalReal<T, W, H>& r, T hb1, T hb2, int tid) {
+    for (int idx = tid; idx < W * H; idx += NT) {
+        const int lz = idx / W, lx = idx - lz * W;
+#pragma unroll
+        for (int k = 0; k < 5; ++k) {
+            const T q = r.g[5 + k][lz][lx];
+            t.c[k][lz][lx] = cx<T>(r.g[k][lz][lx] - hb1 * q, hb2 * q);
+        }
+    }
+}
+
 // M u at tile point (lx, lz) (global (gx, gz)); U row pitch W; coefficients of
 // the neighbours come from the staged tile (the point must not lie on the
 // tile border).

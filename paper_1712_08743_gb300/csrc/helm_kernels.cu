@@ -1021,6 +1021,75 @@ template void launch_prolong2<double>(const LevelDev&, const LevelDev&, const Le
                                       double, const double*, const double*, const double*, const double*, double*,
                                       const RhsState*, int, cudaStream_t, int, int, int);
 
+// Several right-hand sides of one model per block (large batches): the tile's real
+// Galerkin coefficients are staged once, before the wait on the previous kernel,
+// and each right-hand side's complex coefficients are formed from them in shared
+// memory; the tile work is that of the one-RHS kernels.
+constexpr int kGalMultiRhs = 4;        // right-hand sides per block (2 and 8 measured slower)
+constexpr int kGalMultiMinRhs = 16;    // batches above this size (one model) take these kernels
+
+template <typename T, bool CORRECT, int GRCX, int GRCZ, int NT, int RB>
+__global__ void __launch_bounds__(NT) k_restrict_gm(LevelDev Lf, LevelDev Lc, const T* __restrict__ hwv, T b1, T b2,
+                                                    T wj, const T* __restrict__ f, const T* __restrict__ ec,
+                                                    T* __restrict__ fc, const RhsState* st, int nrhs) {
+    using RT = RestrictTile<T, GRCX, GRCZ, NT>;
+    __shared__ RT sm;
+    __shared__ GalReal<T, RT::GRFW, RT::GRFH> gr;
+    pdl_trigger();
+    stage_gal_real<T, RT::GRFW, RT::GRFH, NT>(gr, Lf, 2 * blockIdx.x * GRCX - 1, 2 * blockIdx.y * GRCZ - 1,
+                                              threadIdx.x);
+    pdl_wait();
+    for (int r = 0; r < RB; ++r) {
+        const int b = blockIdx.z * RB + r;
+        if (b >= nrhs) break;
+        if (!rhs_active(st, b)) continue;   // uniform in the block
+        __syncthreads();                    // staging done; the previous right-hand side is done with sm
+        const T hw = hwv[b];
+        form_gal<T, RT::GRFW, RT::GRFH, NT>(sm.C, gr, hw * b1, hw * b2, threadIdx.x);
+        restrict_tile_work<T, CORRECT, GRCX, GRCZ, NT, false>(sm, Lf, Lc, wj, f, ec, fc, blockIdx.x, blockIdx.y, b,
+                                                              threadIdx.x, BlockSync{});
+    }
+}
+
+template <typename T, int GPX, int GPZ, int RB>
+__global__ void __launch_bounds__(GPX * GPZ) k_prolong_gm(LevelDev Lf, LevelDev Lc, const T* __restrict__ hwv, T b1,
+                                                          T b2, T wj, const T* __restrict__ f,
+                                                          const T* __restrict__ ec, T* __restrict__ out,
+                                                          const RhsState* st, int accumulate, int nrhs) {
+    using PT = ProlongTile<T, GPX, GPZ>;
+    __shared__ PT sm;
+    __shared__ GalReal<T, PT::RW, PT::RH> gr;
+    pdl_trigger();
+    stage_gal_real<T, PT::RW, PT::RH, PT::NT>(gr, Lf, blockIdx.x * GPX - 1, blockIdx.y * GPZ - 1, threadIdx.x);
+    pdl_wait();
+    for (int r = 0; r < RB; ++r) {
+        const int b = blockIdx.z * RB + r;
+        if (b >= nrhs) break;
+        if (!rhs_active(st, b)) continue;   // uniform in the block
+        __syncthreads();
+        const T hw = hwv[b];
+        form_gal<T, PT::RW, PT::RH, PT::NT>(sm.C, gr, hw * b1, hw * b2, threadIdx.x);
+        prolong_tile_work<T, GPX, GPZ, false>(sm, Lf, Lc, wj, f, ec, out, accumulate, blockIdx.x, blockIdx.y, b,
+                                              threadIdx.x, BlockSync{});
+    }
+}
+
+template <typename T, bool CORRECT, int NT>
+static void launch_restrict_gm(const LevelDev& Lf, const LevelDev& Lc, const T* w2, double b1, double b2, double wj,
+                               const T* f, const T* ec, T* fc, const RhsState* st, int nrhs, cudaStream_t s) {
+    dim3 grd((Lc.nx + 7) / 8, (Lc.nz + 7) / 8, (nrhs + kGalMultiRhs - 1) / kGalMultiRhs);
+    launch_pdl(k_restrict_gm<T, CORRECT, 8, 8, NT, kGalMultiRhs>, grd, dim3(NT), 0, s, Lf, Lc, w2, (T)b1, (T)b2,
+               (T)wj, f, ec, fc, st, nrhs);
+}
+template <typename T, int GPX, int GPZ>
+static void launch_prolong_gm(const LevelDev& Lf, const LevelDev& Lc, const T* w2, double b1, double b2, double wj,
+                              const T* f, const T* ec, T* out, const RhsState* st, int nrhs, cudaStream_t s,
+                              int accumulate) {
+    dim3 grd((Lf.nx + GPX - 1) / GPX, (Lf.nz + GPZ - 1) / GPZ, (nrhs + kGalMultiRhs - 1) / kGalMultiRhs);
+    launch_pdl(k_prolong_gm<T, GPX, GPZ, kGalMultiRhs>, grd, dim3(GPX * GPZ), 0, s, Lf, Lc, w2, (T)b1, (T)b2, (T)wj,
+               f, ec, out, st, accumulate, nrhs);
+}
+
 // Tile shapes of the complex64 Galerkin kernels, by the code the autotuner stores
 // per level (kGalTiles choices; 1 is the default): restriction coarse tile
 // (x, z) and prolongation fine tile (x, z), one thread per node of the tile. The
@@ -1039,6 +1108,11 @@ template <typename T, bool CORRECT>
 void launch_restrict_g(int tile, const LevelDev& Lf, const LevelDev& Lc, const T* w2, double b1, double b2, double wj,
                        const T* f, const T* ec, T* fc, const RhsState* st, int nrhs, cudaStream_t s) {
     if constexpr (sizeof(T) == 4) {
+        if (nrhs > kGalMultiMinRhs && Lf.gkstride == 0) {   // 8 x 8 coarse tiles, 64 or 128 threads
+            if (tile == 0) launch_restrict_gm<T, CORRECT, 64>(Lf, Lc, w2, b1, b2, wj, f, ec, fc, st, nrhs, s);
+            else launch_restrict_gm<T, CORRECT, 128>(Lf, Lc, w2, b1, b2, wj, f, ec, fc, st, nrhs, s);
+            return;
+        }
         switch (tile) {
             case 0: launch_restrict_g_shape<T, CORRECT, 8, 8>(Lf, Lc, w2, b1, b2, wj, f, ec, fc, st, nrhs, s); return;
             case 2: launch_restrict_g_shape<T, CORRECT, 32, 4>(Lf, Lc, w2, b1, b2, wj, f, ec, fc, st, nrhs, s); return;
@@ -1062,6 +1136,12 @@ template <typename T>
 void launch_prolong_g(int tile, const LevelDev& Lf, const LevelDev& Lc, const T* w2, double b1, double b2, double wj,
                       const T* f, const T* ec, T* out, const RhsState* st, int nrhs, cudaStream_t s, int accumulate) {
     if constexpr (sizeof(T) == 4) {
+        if (nrhs > kGalMultiMinRhs && Lf.gkstride == 0) {   // fine tiles 16 x 8, 32 x 8 or 64 x 4
+            if (tile == 0) launch_prolong_gm<T, 16, 8>(Lf, Lc, w2, b1, b2, wj, f, ec, out, st, nrhs, s, accumulate);
+            else if (tile == 2) launch_prolong_gm<T, 64, 4>(Lf, Lc, w2, b1, b2, wj, f, ec, out, st, nrhs, s, accumulate);
+            else launch_prolong_gm<T, 32, 8>(Lf, Lc, w2, b1, b2, wj, f, ec, out, st, nrhs, s, accumulate);
+            return;
+        }
         switch (tile) {
             case 0: launch_prolong_g_shape<T, 16, 8>(Lf, Lc, w2, b1, b2, wj, f, ec, out, st, nrhs, s, accumulate); return;
             case 2: launch_prolong_g_shape<T, 64, 4>(Lf, Lc, w2, b1, b2, wj, f, ec, out, st, nrhs, s, accumulate); return;
