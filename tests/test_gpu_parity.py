@@ -113,6 +113,34 @@ def test_fused_prolongation_pairs_equal_separate_launches(hg, ctx, name, make):
     model.close()
 
 
+@pytest.mark.parametrize("coarse", [None, "dense"])
+def test_large_batch_galerkin_kernels_equal_each_alone(hg, ctx, coarse):
+    """Above 16 right-hand sides of one model the Galerkin kernels work on four per block and form
+    each one's complex coefficients from the tile's real ones staged once. A batch of 20 with
+    different frequencies (neighbours in a block differ) must give, for every member, the cycle
+    of that right-hand side alone (the one-per-block kernels), to complex64 rounding; with the
+    default coarse end the batch also takes the shared-memory tail, so only the dense end is
+    compared member by member with the lone cycle, and the default end against the oracle cycle."""
+    mdl = models.c3_model()
+    model = hg.helm_create_model(ctx, mdl.slowness, mdl.h, mdl.npml, mdl.alpha_max)
+    rng = np.random.default_rng(9)
+    om = 2 * np.pi * rng.uniform(3.0, 7.0, 20)
+    r = models.random_complex(rng, (20, model.nz, model.nx), np.complex64)
+    if coarse == "dense":
+        z = hg.helm_vcycle(model, om, r, (1.0, 0.5), 0.8, coarse=hg.HELM_COARSE_DENSE)
+        for k in (0, 1, 2, 3, 7, 19):
+            z1 = hg.helm_vcycle(model, om[k:k + 1], r[k:k + 1], (1.0, 0.5), 0.8, coarse=hg.HELM_COARSE_DENSE)
+            assert rel(z[k], z1[0]) < 1e-6, (k, rel(z[k], z1[0]))
+    else:
+        z = hg.helm_vcycle(model, om, r, (1.0, 0.5), 0.8)
+        m2 = oracle.pad_slowness(mdl.slowness, mdl.npml) ** 2
+        for k in (0, 5, 19):
+            V = mg.VCycle(m2, (mdl.h * om[k]) ** 2, (1.0, 0.5), 0.8, coarse="tail")
+            ref = V.apply(r[k].astype(np.complex128).ravel()).reshape(model.nz, model.nx)
+            assert rel(z[k], ref) < 2e-5, (k, rel(z[k], ref))
+    model.close()
+
+
 @pytest.mark.parametrize("precision,tol,bound", [("fp64", 1e-10, 1e-6), ("mixed", 1e-10, 1e-6), ("fp32", 5e-5, 1e-4)])
 def test_c1_wavefield_matches_oracle(hg, ctx, precision, tol, bound):
     mdl = models.c1_model()
